@@ -1,0 +1,179 @@
+/*
+ * lrdm.h -- C ABI of the GB300 (sm_103a) LRDM Gateaux-derivative library.
+ *
+ * The library evaluates, for a Kohn-Sham system restricted to its
+ * Chebyshev-filtered subspace (Psi, D = diag(eps)), the Gateaux derivatives
+ *     t_k = d/dlambda R[rho + lambda v_k] |_{lambda = 0}      (Eq. jlowrank)
+ * of the SCF residual R = F[rho] - rho along K direction functions v_k,
+ * with the first-order density response computed in the subspace
+ * (§II.C, Eqs. densityResponse, densityMatResponseApprox,
+ * subspaceDensityMatResponse), and then the low-rank least-squares step
+ * (Eqs. plowrank, relativeError, quasinewton).  Per direction:
+ *     dV_k  = V_H[v_k] + f_xc(rho) v_k               (K = K_xc + K_c, Eq. jacobian)
+ *     X_k   = Psi^T diag(w dV_k) Psi                   (H-breve')
+ *     X'_k  = L o (X_k - mu'_k I), Tr X'_k = 0         (canonical DMPT, exact f)
+ *     drho_k(r) = g sum_ij Psi(r,i) X'_k,ij Psi(r,j)
+ *     f_k   = drho_k - v_k
+ * where L is the divided-difference (Loewner) matrix of the Fermi function
+ * at eps and g the occupancy factor (2 spin-restricted, 1 per spin channel).
+ *
+ * Discretisation: periodic grid n0 x n1 x n2 (flat C order, index
+ * r = (i0 n1 + i1) n2 + i2), spacing h, quadrature weight w = h0 h1 h2,
+ * inner product <a, b> = w sum_r a(r) b(r) (spin pairs: sum of the two
+ * channels, Eq. innerproductDirectsumHilbertspace).  Psi holds grid values of
+ * w-orthonormal functions: Psi^T diag(w) Psi = I.
+ *
+ * Conventions
+ *  - All array pointers are DEVICE pointers unless stated otherwise.  The
+ *    caller owns every input and output buffer; the library only borrows
+ *    them for the duration of the stream work it enqueues.
+ *  - lrdm_create allocates everything the context needs (workspaces sized
+ *    for k_max, the operand copies of Psi, cuFFT plans).  The other calls
+ *    allocate nothing and do not synchronise the host with the device.
+ *  - Argument errors are returned synchronously, before anything is
+ *    enqueued.  Errors found on the device (non-finite values, an expired
+ *    bounded wait, a singular least-squares matrix) set a sticky status word
+ *    that lrdm_status_query() reads.
+ *  - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).  One context must not be used from two streams
+ *    at the same time: its workspaces are shared by its calls.
+ */
+#ifndef LRDM_H
+#define LRDM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lrdm_status {
+  LRDM_OK = 0,
+  LRDM_ERR_INVALID_ARG = 1,      /* null pointer, bad enum, K > k_max, ...   */
+  LRDM_ERR_SHAPE = 2,            /* inconsistent sizes or leading dimensions */
+  LRDM_ERR_OOM = 3,              /* device allocation failed in lrdm_create  */
+  LRDM_ERR_CUDA = 4,             /* a CUDA / cuFFT call failed               */
+  LRDM_ERR_MU_NOT_CONVERGED = 5, /* no chemical potential for this N_e       */
+  LRDM_ERR_SINGULAR = 6,         /* S rank-deficient: a = S^+ c was used     */
+  LRDM_ERR_TIMEOUT = 7,          /* a bounded device wait expired            */
+  LRDM_ERR_NONFINITE = 8,        /* NaN / Inf met on the device              */
+  LRDM_ERR_UNSUPPORTED = 9       /* precision / feature not available        */
+} lrdm_status;
+
+/* Arithmetic of the two dense contractions (X_k and drho_k).  The Loewner
+ * entries, mu, mu'_k, the occupations and the K x K least-squares solve are
+ * always FP64. */
+typedef enum lrdm_precision {
+  LRDM_FP64 = 0,    /* FP64 CUDA-core GEMMs                                   */
+  LRDM_FP32 = 1,    /* FP32 CUDA-core GEMMs                                   */
+  LRDM_TF32 = 2,    /* tcgen05 kind::tf32, FP32 accumulation in tensor memory */
+  LRDM_BF16X3 = 3   /* tcgen05 kind::f16 with operands split a = a_hi + a_lo
+                       (bf16 each); a_hi b_hi + a_hi b_lo + a_lo b_hi,
+                       FP32 accumulation in tensor memory                   */
+} lrdm_precision;
+
+/* Element type of Psi, rho and of every direction / residual array. */
+typedef enum lrdm_dtype { LRDM_DTYPE_F64 = 0, LRDM_DTYPE_F32 = 1 } lrdm_dtype;
+
+/* One system (device pointers are BORROWED by lrdm_create only: the context
+ * keeps its own copies of everything it needs afterwards). */
+typedef struct lrdm_system {
+  int n[3];              /* periodic grid; N_g = n0 n1 n2                        */
+  double h[3];           /* grid spacing (bohr); w = h0 h1 h2                    */
+  int nspin;             /* 1: spin-restricted; 2: collinear spin pair (§II.D)  */
+  int ns[2];             /* subspace size N_s per channel                        */
+  int ld_psi[2];         /* leading dimension (elements) of psi[s], >= ns[s]     */
+  const void* psi[2];    /* [N_g][ld] row-major, io dtype; Psi^T diag(w) Psi = I */
+  const double* eps[2];  /* [ns] projected eigenvalues (Ha), FP64                */
+  const double* occ[2];  /* optional [ns] occupations in [0,1]; NULL ->
+                            Fermi-Dirac f(eps, mu) with mu from the electron
+                            count (Eq. kseqcont)                                */
+  const void* rho[2];    /* optional [N_g] density for the xc kernel (total if
+                            nspin = 1, per channel if 2); NULL -> rho =
+                            g sum_i f_i psi_i^2 + rho_floor (Eq. densityChFSI)   */
+  double n_electrons;    /* N_e (both channels together)                         */
+  double kT;             /* Fermi smearing (Ha), > 0                             */
+  double occ_factor;     /* g; 0 -> 2 if nspin = 1 else 1                        */
+  double rho_floor;      /* added to the computed density when rho[] is NULL     */
+  int k_max;             /* directions per call for this system; 0 -> options    */
+} lrdm_system;
+
+typedef struct lrdm_options {
+  int prec;              /* lrdm_precision                                       */
+  int io_dtype;          /* lrdm_dtype of psi, rho and all direction arrays      */
+  int k_max;             /* default maximum K per system per call (<= 64)        */
+  double pinv_rcond;     /* least-squares cutoff, relative to max eig(S); 1e-12  */
+  double degen_tol;      /* |eps_i - eps_j| <= degen_tol * kT counts as
+                            degenerate in occupation mode; 1e-5                 */
+  int poisson_symbol;    /* 0: 4 pi/|G|^2 (spectral); 1: second-order FD symbol  */
+  int use_graph;         /* replay lrdm_gateaux_batch from a captured CUDA graph  */
+  int autotune;          /* reserved: tile choice by measurement at create        */
+  int debug_flags;       /* test-only host-side fault injection; 0 in production */
+} lrdm_options;
+
+typedef struct lrdm_ctx lrdm_ctx;
+
+/* Fills *opt with the defaults above (BF16X3, F32 io, k_max 16). */
+void lrdm_default_options(lrdm_options* opt);
+
+/* Builds a context for nsys systems: validates shapes, solves mu
+ * (g sum f(eps, mu) = N_e by FP64 bisection, Eq. kseqcont; spin channels share
+ * mu, §II.D), computes the occupations, the Loewner matrices, f_xc, the
+ * density if it is not given, the operand copies of Psi for the chosen
+ * precision, cuFFT plans and all workspaces.  Synchronises the stream before
+ * returning.  On error *out is NULL and nothing is leaked. */
+lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
+                        const lrdm_options* opt, void* stream);
+
+/* Gateaux derivatives of all systems in one call.
+ *   v[s]     : [K[s]][nspin][N_g] directions of system s (io dtype)
+ *   K[s]     : HOST array, 0 <= K[s] <= k_max of system s
+ *   f_out[s] : [K[s]][nspin][N_g] results f_k = drho_k - v_k (io dtype)
+ *   dmu_out  : optional device [sum_s K[s]] FP64, the shifts mu'_k
+ * Keeps X_k and mu'_k in the context for a following lrdm_backward.
+ * Asynchronous; no allocation. */
+lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K,
+                               void* const* f_out, double* dmu_out, void* stream);
+
+/* Low-rank least-squares step for system `sys` (Eqs. plowrank, relativeError,
+ * quasinewton), for K directions v and their derivatives f (as written by
+ * lrdm_gateaux_batch) and the current residual R ([nspin][N_g]):
+ *   S = <f_k, f_l>, c = <f_k, R>, a = S^+ c (FP64; eigenvalues below
+ *   pinv_rcond * max dropped, which sets LRDM_ERR_SINGULAR in the status word),
+ *   Delta = sum_k a_k v_k,
+ *   rho_inout <- rho_inout - alpha Delta   (alpha != 0), or <- Delta (alpha == 0),
+ *   coeff_out[K] = a (device, FP64), s_rel_out = ||F a - R|| / ||R|| (device).
+ * coeff_out and s_rel_out may be NULL.  Asynchronous; no allocation. */
+lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, const void* f,
+                       int K, double alpha, void* rho_inout, double* coeff_out,
+                       double* s_rel_out, void* stream);
+
+/* Adjoint of the most recent lrdm_gateaux_batch on this context.
+ *   f_bar[s]  : [K[s]][nspin][N_g] cotangents of f_out[s] (io dtype)
+ *   v_bar[s]  : [K[s]][nspin][N_g] gradients w.r.t. v[s] (io dtype)
+ *   eps_bar[2 s + c], occ_bar[2 s + c] : optional [ns] FP64 gradients w.r.t.
+ *     the eigenvalues (at fixed occupations) and the occupations of channel
+ *     c of system s; the arrays of pointers may be NULL, as may any entry.
+ * Gradients are Euclidean (w.r.t. array entries).  Psi X' products are
+ * recomputed, never stored.  Asynchronous; no allocation. */
+lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
+                          double* const* eps_bar, double* const* occ_bar, void* stream);
+
+/* Reads and clears the device status word.  synchronize != 0 first waits
+ * for all work of the context.  Returns the most severe pending error. */
+lrdm_status lrdm_status_query(lrdm_ctx* ctx, int synchronize);
+
+/* Chemical potential mu of system `sys` (host scalar, set by lrdm_create). */
+lrdm_status lrdm_get_mu(lrdm_ctx* ctx, int sys, double* mu_host);
+
+/* Copies the density used for the xc kernel of system `sys`, channel `spin`,
+ * into out ([N_g], io dtype, device).  Asynchronous. */
+lrdm_status lrdm_get_density(lrdm_ctx* ctx, int sys, int spin, void* out, void* stream);
+
+/* Frees the context (synchronises its device work first). NULL is ignored. */
+void lrdm_destroy(lrdm_ctx* ctx);
+
+const char* lrdm_status_string(lrdm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRDM_H */

@@ -1,0 +1,24 @@
+"""GB300 (sm_103a) implementation of the batched Gateaux derivative of the
+Kohn-Sham SCF residual used by the low-rank dielectric-matrix (LRDM)
+preconditioner of Das & Gavini (arXiv 2211.07894, §II).
+
+The computation lives in the C-ABI library ``lib/liblrdm.so`` (declared in
+``include/lrdm.h``); ``binding`` marshals torch tensors into it.
+"""
+
+from .binding import (  # noqa: F401
+    Context,
+    LrdmError,
+    gateaux_function,
+    load,
+    lrdm_apply,
+    lrdm_backward,
+    lrdm_create,
+    lrdm_default_options,
+    lrdm_destroy,
+    lrdm_gateaux_batch,
+    lrdm_get_density,
+    lrdm_get_mu,
+    lrdm_status_query,
+    lrdm_status_string,
+)

@@ -1,0 +1,339 @@
+"""ctypes binding of liblrdm.so: the C-ABI calls under the same names, plus a
+small torch-facing ``Context`` that marshals tensors into them.
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  There is no fallback -- if the compiled library is
+missing, loading raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_void_p
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "liblrdm.so")
+
+LRDM_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "shape", 3: "out of memory", 4: "cuda",
+                5: "mu not converged", 6: "singular", 7: "timeout", 8: "non-finite",
+                9: "unsupported"}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
+DTYPE_F64, DTYPE_F32 = 0, 1
+
+
+class LrdmError(RuntimeError):
+    def __init__(self, call, code):
+        super().__init__(f"{call} failed: {STATUS_NAMES.get(code, code)} ({code})")
+        self.code = code
+
+
+class lrdm_system(ctypes.Structure):
+    _fields_ = [("n", c_int * 3), ("h", c_double * 3), ("nspin", c_int), ("ns", c_int * 2),
+                ("ld_psi", c_int * 2), ("psi", c_void_p * 2), ("eps", c_void_p * 2),
+                ("occ", c_void_p * 2), ("rho", c_void_p * 2), ("n_electrons", c_double),
+                ("kT", c_double), ("occ_factor", c_double), ("rho_floor", c_double),
+                ("k_max", c_int)]
+
+
+class lrdm_options(ctypes.Structure):
+    _fields_ = [("prec", c_int), ("io_dtype", c_int), ("k_max", c_int),
+                ("pinv_rcond", c_double), ("degen_tol", c_double), ("poisson_symbol", c_int),
+                ("use_graph", c_int), ("autotune", c_int), ("debug_flags", c_int)]
+
+
+_lib = None
+
+EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_apply",
+           "lrdm_backward", "lrdm_status_query", "lrdm_get_mu", "lrdm_get_density",
+           "lrdm_destroy", "lrdm_status_string"]
+
+
+def load(path: Optional[str] = None):
+    """Loads liblrdm.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"liblrdm.so not built at {p}; run paper_2211_07894_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    lib.lrdm_default_options.argtypes = [POINTER(lrdm_options)]
+    lib.lrdm_default_options.restype = None
+    lib.lrdm_create.argtypes = [POINTER(c_void_p), POINTER(lrdm_system), c_int,
+                                POINTER(lrdm_options), c_void_p]
+    lib.lrdm_create.restype = c_int
+    lib.lrdm_gateaux_batch.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_int),
+                                       POINTER(c_void_p), c_void_p, c_void_p]
+    lib.lrdm_gateaux_batch.restype = c_int
+    lib.lrdm_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_double,
+                               c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.lrdm_apply.restype = c_int
+    lib.lrdm_backward.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p),
+                                  POINTER(c_void_p), POINTER(c_void_p), c_void_p]
+    lib.lrdm_backward.restype = c_int
+    lib.lrdm_status_query.argtypes = [c_void_p, c_int]
+    lib.lrdm_status_query.restype = c_int
+    lib.lrdm_get_mu.argtypes = [c_void_p, c_int, POINTER(c_double)]
+    lib.lrdm_get_mu.restype = c_int
+    lib.lrdm_get_density.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p]
+    lib.lrdm_get_density.restype = c_int
+    lib.lrdm_destroy.argtypes = [c_void_p]
+    lib.lrdm_destroy.restype = None
+    lib.lrdm_status_string.argtypes = [c_int]
+    lib.lrdm_status_string.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(call, code):
+    if code != LRDM_OK:
+        raise LrdmError(call, code)
+
+
+def _ptr_array(ptrs):
+    arr = (c_void_p * max(1, len(ptrs)))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# C-ABI calls under their own names (plain pointers in, status code out)
+# ---------------------------------------------------------------------------
+
+def lrdm_default_options() -> lrdm_options:
+    o = lrdm_options()
+    load().lrdm_default_options(ctypes.byref(o))
+    return o
+
+
+def lrdm_create(systems: Sequence[lrdm_system], options: lrdm_options, stream: int = 0):
+    arr = (lrdm_system * len(systems))(*systems)
+    h = c_void_p()
+    code = load().lrdm_create(ctypes.byref(h), arr, len(systems), ctypes.byref(options),
+                              c_void_p(stream))
+    return code, h
+
+
+def lrdm_gateaux_batch(ctx, v_ptrs, K, f_ptrs, dmu_ptr, stream: int = 0) -> int:
+    Ks = (c_int * len(K))(*K)
+    return load().lrdm_gateaux_batch(ctx, _ptr_array(v_ptrs), Ks, _ptr_array(f_ptrs),
+                                     c_void_p(dmu_ptr or 0), c_void_p(stream))
+
+
+def lrdm_apply(ctx, sys, R, v, f, K, alpha, rho, coeff, s_rel, stream: int = 0) -> int:
+    return load().lrdm_apply(ctx, sys, c_void_p(R), c_void_p(v), c_void_p(f), K, alpha,
+                             c_void_p(rho or 0), c_void_p(coeff or 0), c_void_p(s_rel or 0),
+                             c_void_p(stream))
+
+
+def lrdm_backward(ctx, fbar_ptrs, vbar_ptrs, eps_bar_ptrs=None, occ_bar_ptrs=None,
+                  stream: int = 0) -> int:
+    eb = _ptr_array(eps_bar_ptrs) if eps_bar_ptrs is not None else None
+    ob = _ptr_array(occ_bar_ptrs) if occ_bar_ptrs is not None else None
+    return load().lrdm_backward(ctx, _ptr_array(fbar_ptrs), _ptr_array(vbar_ptrs),
+                                eb, ob, c_void_p(stream))
+
+
+def lrdm_status_query(ctx, synchronize: int = 1) -> int:
+    return load().lrdm_status_query(ctx, synchronize)
+
+
+def lrdm_get_mu(ctx, sys: int) -> float:
+    mu = c_double()
+    _check("lrdm_get_mu", load().lrdm_get_mu(ctx, sys, ctypes.byref(mu)))
+    return mu.value
+
+
+def lrdm_get_density(ctx, sys, spin, out_ptr, stream: int = 0) -> int:
+    return load().lrdm_get_density(ctx, sys, spin, c_void_p(out_ptr), c_void_p(stream))
+
+
+def lrdm_destroy(ctx) -> None:
+    load().lrdm_destroy(ctx)
+
+
+def lrdm_status_string(code: int) -> str:
+    return load().lrdm_status_string(code).decode()
+
+
+# ---------------------------------------------------------------------------
+# torch-facing context
+# ---------------------------------------------------------------------------
+
+class Context:
+    """Owns one lrdm_ctx.  ``systems`` is a list of dicts with keys
+
+      n, h, psi (list of (N_g, N_s) tensors on the device), eps (list of
+      float64 tensors), optional occ, optional rho, n_electrons, kT, g,
+      rho_floor, k_max.
+
+    Direction / result tensors are (K, nspin, N_g) in the io dtype.
+    """
+
+    def __init__(self, systems, prec="bf16x3", io_dtype=None, k_max=16, pinv_rcond=1e-12,
+                 degen_tol=1e-5, poisson="spectral", use_graph=False, stream=None):
+        import torch
+        self.torch = torch
+        self.io_dtype = io_dtype or torch.float32
+        self.prec = prec
+        o = lrdm_default_options()
+        o.prec = PRECISIONS[prec]
+        o.io_dtype = DTYPE_F64 if self.io_dtype == torch.float64 else DTYPE_F32
+        o.k_max = int(k_max)
+        o.pinv_rcond = float(pinv_rcond)
+        o.degen_tol = float(degen_tol)
+        o.poisson_symbol = 1 if poisson == "fd" else 0
+        o.use_graph = 1 if use_graph else 0
+        self.options = o
+        keep = []
+        cs = []
+        self.meta = []
+        for d in systems:
+            s = lrdm_system()
+            nspin = len(d["psi"])
+            s.nspin = nspin
+            for i in range(3):
+                s.n[i] = int(d["n"][i])
+                s.h[i] = float(d["h"][i])
+            for c in range(nspin):
+                psi = d["psi"][c]
+                assert psi.is_cuda and psi.dtype == self.io_dtype and psi.dim() == 2
+                assert psi.stride(1) == 1
+                eps = d["eps"][c]
+                assert eps.is_cuda and eps.dtype == torch.float64 and eps.is_contiguous()
+                s.ns[c] = psi.shape[1]
+                s.ld_psi[c] = psi.stride(0)
+                s.psi[c] = psi.data_ptr()
+                s.eps[c] = eps.data_ptr()
+                keep += [psi, eps]
+                if d.get("occ") is not None:
+                    occ = d["occ"][c].contiguous()
+                    s.occ[c] = occ.data_ptr()
+                    keep.append(occ)
+                if d.get("rho") is not None:
+                    rho = d["rho"][c].to(self.io_dtype).contiguous()
+                    s.rho[c] = rho.data_ptr()
+                    keep.append(rho)
+            s.n_electrons = float(d["n_electrons"])
+            s.kT = float(d["kT"])
+            s.occ_factor = float(d.get("g", 0.0) or 0.0)
+            s.rho_floor = float(d.get("rho_floor", 0.0))
+            s.k_max = int(d.get("k_max", 0))
+            cs.append(s)
+            self.meta.append(dict(nspin=nspin, Ng=int(np.prod(d["n"])),
+                                  ns=[int(p.shape[1]) for p in d["psi"]],
+                                  k_max=int(d.get("k_max", 0)) or int(k_max)))
+        st = self._stream(stream)
+        code, h = lrdm_create(cs, o, st)
+        _check("lrdm_create", code)
+        self.handle = h
+        del keep
+
+    def _stream(self, stream):
+        if stream is None:
+            return self.torch.cuda.current_stream().cuda_stream
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lrdm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def mu(self, sys=0):
+        return lrdm_get_mu(self.handle, sys)
+
+    def density(self, sys=0, spin=0, stream=None):
+        out = self.torch.empty(self.meta[sys]["Ng"], dtype=self.io_dtype, device="cuda")
+        _check("lrdm_get_density", lrdm_get_density(self.handle, sys, spin, out.data_ptr(),
+                                                    self._stream(stream)))
+        return out
+
+    def gateaux(self, V: List, out: Optional[List] = None, dmu=None, stream=None):
+        torch = self.torch
+        assert len(V) == len(self.meta)
+        K = [int(v.shape[0]) if v is not None else 0 for v in V]
+        if out is None:
+            out = [torch.empty_like(v) if v is not None else None for v in V]
+        if dmu is None:
+            dmu = torch.empty(max(1, sum(K)), dtype=torch.float64, device="cuda")
+        for v, f in zip(V, out):
+            if v is not None:
+                assert v.is_contiguous() and v.dtype == self.io_dtype and f.is_contiguous()
+        code = lrdm_gateaux_batch(self.handle, [v.data_ptr() if v is not None else 0 for v in V],
+                                  K, [f.data_ptr() if f is not None else 0 for f in out],
+                                  dmu.data_ptr(), self._stream(stream))
+        _check("lrdm_gateaux_batch", code)
+        return out, dmu[: sum(K)]
+
+    def apply(self, sys, R, V, F, alpha, rho=None, coeff=None, s_rel=None, stream=None):
+        torch = self.torch
+        K = int(V.shape[0])
+        coeff = coeff if coeff is not None else torch.empty(K, dtype=torch.float64, device="cuda")
+        s_rel = s_rel if s_rel is not None else torch.empty(1, dtype=torch.float64, device="cuda")
+        code = lrdm_apply(self.handle, sys, R.data_ptr(), V.data_ptr(), F.data_ptr(), K,
+                          float(alpha), rho.data_ptr() if rho is not None else 0,
+                          coeff.data_ptr(), s_rel.data_ptr(), self._stream(stream))
+        _check("lrdm_apply", code)
+        return coeff, s_rel
+
+    def backward(self, fbar: List, want_eps=True, stream=None):
+        torch = self.torch
+        vbar = [torch.empty_like(f) if f is not None else None for f in fbar]
+        eb, ob = [], []
+        ebp, obp = [], []
+        for m in self.meta:
+            for c in range(2):
+                if want_eps and c < m["nspin"]:
+                    e = torch.empty(m["ns"][c], dtype=torch.float64, device="cuda")
+                    o = torch.empty(m["ns"][c], dtype=torch.float64, device="cuda")
+                    eb.append(e)
+                    ob.append(o)
+                    ebp.append(e.data_ptr())
+                    obp.append(o.data_ptr())
+                else:
+                    eb.append(None)
+                    ob.append(None)
+                    ebp.append(0)
+                    obp.append(0)
+        code = lrdm_backward(self.handle, [f.data_ptr() if f is not None else 0 for f in fbar],
+                             [v.data_ptr() if v is not None else 0 for v in vbar],
+                             ebp if want_eps else None, obp if want_eps else None,
+                             self._stream(stream))
+        _check("lrdm_backward", code)
+        return vbar, eb, ob
+
+    def status(self, synchronize=True):
+        return lrdm_status_query(self.handle, 1 if synchronize else 0)
+
+
+def gateaux_function():
+    """torch.autograd.Function whose forward is lrdm_gateaux_batch on one system
+    and whose backward is lrdm_backward (the hand-written adjoint)."""
+    import torch
+
+    class LrdmResponse(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, lctx, V):
+            (F,), _ = lctx.gateaux([V.detach().contiguous()])
+            fctx.lctx = lctx
+            return F
+
+        @staticmethod
+        def backward(fctx, gF):
+            vbar, _, _ = fctx.lctx.backward([gF.contiguous()], want_eps=False)
+            return None, vbar[0]
+
+    return LrdmResponse

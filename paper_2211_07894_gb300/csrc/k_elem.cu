@@ -1,0 +1,413 @@
+// Element-wise and reduction kernels of the hot path: the perturbation
+// potential (Hartree symbol, LDA kernel, quadrature weight), the chemical-
+// potential shift mu' and the Loewner scaling of the projected matrices, and
+// the backward-only reductions.  All FP64 arithmetic where the result feeds an
+// FP64 quantity (mu', L, eps_bar, occ_bar).
+#include "lrdm_internal.h"
+
+#include <math.h>
+
+namespace lrdm {
+namespace {
+
+__device__ __forceinline__ double ld_io(const void* p, int io, long long i) {
+  return io == LRDM_DTYPE_F64 ? static_cast<const double*>(p)[i]
+                              : (double)static_cast<const float*>(p)[i];
+}
+__device__ __forceinline__ void st_io(void* p, int io, long long i, double x) {
+  if (io == LRDM_DTYPE_F64) static_cast<double*>(p)[i] = x;
+  else static_cast<float*>(p)[i] = (float)x;
+}
+__device__ __forceinline__ double ld_c(const void* p, int fp64, long long i) {
+  return fp64 ? static_cast<const double*>(p)[i] : (double)static_cast<const float*>(p)[i];
+}
+__device__ __forceinline__ void st_c(void* p, int fp64, long long i, double x) {
+  if (fp64) static_cast<double*>(p)[i] = x;
+  else static_cast<float*>(p)[i] = (float)x;
+}
+
+inline int grid_for(long long n, int block) {
+  long long b = (n + block - 1) / block;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+#define GRID_STRIDE(e, n)                                                          \
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (n); \
+       e += (long long)gridDim.x * blockDim.x)
+
+__global__ void k_spin_sum(const void* __restrict__ v, int io, int K, int nspin, long long Ng,
+                           void* __restrict__ out, int fp64) {
+  GRID_STRIDE(e, (long long)K * Ng) {
+    long long k = e / Ng, r = e - k * Ng;
+    double s = 0.0;
+    for (int c = 0; c < nspin; ++c) s += ld_io(v, io, (k * nspin + c) * Ng + r);
+    st_c(out, fp64, e, s);
+  }
+}
+
+// Multiplies the half-spectrum (R2C layout [K][n0][n1][n2/2+1]) by
+// 4 pi / |G|^2 / N_g (G = 0 -> 0); kind 1 replaces |G|^2 by the second-order
+// finite-difference symbol sum_d (4/h_d^2) sin^2(G_d h_d / 2).
+__global__ void k_poisson(void* __restrict__ cplx, int K, int n0, int n1, int n2, double h0,
+                          double h1, double h2, int kind, int fp64) {
+  const int m2n = n2 / 2 + 1;
+  const long long per = (long long)n0 * n1 * m2n;
+  const double inv_ng = 1.0 / ((double)n0 * n1 * n2);
+  const double two_pi = 6.283185307179586;
+  GRID_STRIDE(e, (long long)K * per) {
+    long long rem = e % per;
+    int m2 = (int)(rem % m2n);
+    long long t = rem / m2n;
+    int m1 = (int)(t % n1);
+    int m0 = (int)(t / n1);
+    int f0 = m0 <= n0 / 2 ? m0 : m0 - n0;
+    int f1 = m1 <= n1 / 2 ? m1 : m1 - n1;
+    int f2 = m2;
+    double g0 = two_pi * f0 / (n0 * h0), g1 = two_pi * f1 / (n1 * h1), g2 = two_pi * f2 / (n2 * h2);
+    double q;
+    if (kind == 1) {
+      double s0 = sin(0.5 * g0 * h0), s1 = sin(0.5 * g1 * h1), s2 = sin(0.5 * g2 * h2);
+      q = 4.0 * (s0 * s0 / (h0 * h0) + s1 * s1 / (h1 * h1) + s2 * s2 / (h2 * h2));
+    } else {
+      q = g0 * g0 + g1 * g1 + g2 * g2;
+    }
+    double sym = (f0 == 0 && f1 == 0 && f2 == 0) || q <= 0.0 ? 0.0 : 12.566370614359172 / q * inv_ng;
+    if (fp64) {
+      double2* z = static_cast<double2*>(cplx);
+      z[e].x *= sym;
+      z[e].y *= sym;
+    } else {
+      float2* z = static_cast<float2*>(cplx);
+      z[e].x = (float)(z[e].x * sym);
+      z[e].y = (float)(z[e].y * sym);
+    }
+  }
+}
+
+// a[k][s][r] = scale (V_H[k][r] + f_xs[r] v[k][s][r]); rows r >= Ng are zero
+__global__ void k_dv_weights(const void* __restrict__ v, int io, const void* __restrict__ VH,
+                             const double* __restrict__ fx0, const double* __restrict__ fx1, int K,
+                             int nspin, long long Ng, long long Ng_pad, double scale,
+                             void* __restrict__ a, int fp64) {
+  GRID_STRIDE(e, (long long)K * nspin * Ng_pad) {
+    long long q = e / Ng_pad, r = e - q * Ng_pad;
+    int s = (int)(q % nspin);
+    long long k = q / nspin;
+    double val = 0.0;
+    if (r < Ng) {
+      const double* fx = s == 0 ? fx0 : fx1;
+      val = scale * (ld_c(VH, fp64, k * Ng + r) + fx[r] * ld_io(v, io, q * Ng + r));
+    }
+    st_c(a, fp64, e, val);
+  }
+}
+
+// vbar[k][s][r] = V_H[sum_s dVbar][k][r] + f_xs[r] dVbar[k][s][r] - fbar[k][s][r]
+__global__ void k_adjoint_potential(const void* __restrict__ dvbar, const void* __restrict__ VH,
+                                    const double* __restrict__ fx0, const double* __restrict__ fx1,
+                                    const void* __restrict__ fbar, int io, int K, int nspin,
+                                    long long Ng, long long Ng_pad, void* __restrict__ vbar,
+                                    int fp64) {
+  GRID_STRIDE(e, (long long)K * nspin * Ng) {
+    long long q = e / Ng, r = e - q * Ng;
+    int s = (int)(q % nspin);
+    long long k = q / nspin;
+    const double* fx = s == 0 ? fx0 : fx1;
+    double d = ld_c(dvbar, fp64, q * Ng_pad + r);
+    st_io(vbar, io, e, ld_c(VH, fp64, k * Ng + r) + fx[r] * d - ld_io(fbar, io, e));
+  }
+}
+
+// spin sum of the (padded) adjoint potential for the Hartree transform
+__global__ void k_spin_sum_padded(const void* __restrict__ d, int K, int nspin, long long Ng,
+                                  long long Ng_pad, void* __restrict__ out, int fp64) {
+  GRID_STRIDE(e, (long long)K * Ng) {
+    long long k = e / Ng, r = e - k * Ng;
+    double s = 0.0;
+    for (int c = 0; c < nspin; ++c) s += ld_c(d, fp64, (k * nspin + c) * Ng_pad + r);
+    st_c(out, fp64, e, s);
+  }
+}
+
+__global__ void k_scale_weights(const void* __restrict__ fbar, int io, int K, int nspin,
+                                long long Ng, long long Ng_pad, double scale,
+                                void* __restrict__ a, int fp64) {
+  GRID_STRIDE(e, (long long)K * nspin * Ng_pad) {
+    long long q = e / Ng_pad, r = e - q * Ng_pad;
+    st_c(a, fp64, e, r < Ng ? scale * ld_io(fbar, io, q * Ng + r) : 0.0);
+  }
+}
+
+// One block per direction k.  mu'_k = sum_s sum_i L_ii X_ii / sum_s sum_i L_ii
+// with X summed over the grid splits.  Also flags non-finite X.
+struct DmuArgs {
+  const void* X[2];
+  const double* L[2];
+  int ns[2];
+  int ldx[2];
+  int nsplit;
+  int nspin;
+  int K;
+};
+__global__ void k_dmu(DmuArgs A, int acc64, double* __restrict__ dmu, double* __restrict__ dmu_out,
+                      int* __restrict__ status) {
+  int k = blockIdx.x;
+  double num = 0.0, den = 0.0;
+  for (int s = 0; s < A.nspin; ++s) {
+    long long mat = (long long)A.ldx[s] * A.ldx[s];
+    for (int i = threadIdx.x; i < A.ns[s]; i += blockDim.x) {
+      double x = 0.0;
+      for (int p = 0; p < A.nsplit; ++p)
+        x += ld_c(A.X[s], acc64, ((long long)p * A.K + k) * mat + (long long)i * A.ldx[s] + i);
+      double l = A.L[s][(long long)i * A.ns[s] + i];
+      num += l * x;
+      den += l;
+    }
+  }
+  __shared__ double sn[32], sd[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sn[wid] = num; sd[wid] = den; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sn[w]; b += sd[w]; }
+    double m = b != 0.0 ? a / b : 0.0;
+    if (!isfinite(m)) { atomicOr(status, STATUS_NONFINITE); }
+    dmu[k] = m;
+    if (dmu_out) dmu_out[k] = m;
+  }
+}
+
+// X'' in one of three layouts:
+//   layout 0: out[k][i][j] (ld = ns)        -- CUDA-core GEMM2, compute type
+//   layout 1: out[k][j][i] (ld = ns_pad) fp32 -- TF32 GEMM2 B operand (K-major)
+//   layout 2: out_hi/out_lo[k][j][i] bf16     -- BF16X3 GEMM2 B operand (K-major)
+// value c_ij * (L_ij (X_ij - delta_ij shift_k)) with c = 2, 1, 0 for i <, =, > j.
+// Adjoint form (adjoint = 1): L_ij G_ij - delta_ij L_ii shift_k * inv_trace.
+// X is the full symmetric matrix (GEMM1 writes both triangles), summed over splits.
+__global__ void k_loewner_scale(const void* __restrict__ X, int acc64, int nsplit, int K, int ns,
+                                int ldx, const double* __restrict__ L,
+                                const double* __restrict__ shift, int adjoint, double inv_trace,
+                                int layout, int ldo, void* __restrict__ out,
+                                __nv_bfloat16* __restrict__ out_lo) {
+  long long mat_x = (long long)ldx * ldx;
+  long long mat_o = (long long)ldo * ldo;
+  GRID_STRIDE(e, (long long)K * mat_o) {
+    long long k = e / mat_o, rem = e - k * mat_o;
+    int row = (int)(rem / ldo), col = (int)(rem - (long long)row * ldo);
+    // layout 0: (row, col) = (i, j);  layouts 1, 2: (row, col) = (j, i)
+    int i = layout == 0 ? row : col;
+    int j = layout == 0 ? col : row;
+    double val = 0.0;
+    if (i < ns && j < ns && i <= j) {
+      double x = 0.0;
+      // read the (row, col) entry: X and L are symmetric
+      for (int p = 0; p < nsplit; ++p)
+        x += ld_c(X, acc64, ((long long)p * K + k) * mat_x + (long long)row * ldx + col);
+      double l = L[(long long)row * ns + col];
+      double xp;
+      if (adjoint) xp = l * x - (i == j ? l * shift[k] * inv_trace : 0.0);
+      else xp = l * (x - (i == j ? shift[k] : 0.0));
+      val = (i == j ? 1.0 : 2.0) * xp;
+    }
+    if (layout == 0) {
+      st_c(out, acc64, e, val);
+    } else if (layout == 1) {
+      static_cast<float*>(out)[e] = (float)val;
+    } else {
+      float v32 = (float)val;
+      __nv_bfloat16 hi = __float2bfloat16_rn(v32);
+      static_cast<__nv_bfloat16*>(out)[e] = hi;
+      out_lo[e] = __float2bfloat16_rn(v32 - __bfloat162float(hi));
+    }
+  }
+}
+
+// Backward trace terms T_k = sum_s sum_m L_mm Gbar_k,mm (the adjoint of the
+// mu' constraint) -- same reduction as k_dmu without the division.
+__global__ void k_trace_bar(DmuArgs A, int acc64, double* __restrict__ tbar) {
+  int k = blockIdx.x;
+  double num = 0.0;
+  for (int s = 0; s < A.nspin; ++s) {
+    long long mat = (long long)A.ldx[s] * A.ldx[s];
+    for (int i = threadIdx.x; i < A.ns[s]; i += blockDim.x) {
+      double x = 0.0;
+      for (int p = 0; p < A.nsplit; ++p)
+        x += ld_c(A.X[s], acc64, ((long long)p * A.K + k) * mat + (long long)i * A.ldx[s] + i);
+      num += A.L[s][(long long)i * A.ns[s] + i] * x;
+    }
+  }
+  __shared__ double sn[32];
+  for (int o = 16; o > 0; o >>= 1) num += __shfl_xor_sync(0xffffffffu, num, o);
+  if ((threadIdx.x & 31) == 0) sn[threadIdx.x >> 5] = num;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sn[w];
+    tbar[k] = a;
+  }
+}
+
+// One block per state i of channel s:
+//   Lbar_ij = sum_k G_k,ij (X_k,ij - delta_ij mu'_k) - delta_ij sum_k tbar_k/s (X_k,ii - mu'_k)
+//   eps_bar_i = sum_{j != i, |de| > tau} 2 Lbar_ij (-L_ij / (eps_i - eps_j))
+//   occ_bar_i = sum_{j != i, |de| > tau} 2 Lbar_ij / (eps_i - eps_j)
+//             + sum_{j != i, |de| <= tau} 2 Lbar_ij (-(1 - 2 fbar)/(2 kT)) + Lbar_ii (-(1 - 2 f_i)/kT)
+__global__ void k_eps_occ_bar(const void* __restrict__ X, const void* __restrict__ G, int acc64,
+                              int nsplit, int K, int ns, int ldx, const double* __restrict__ L,
+                              const double* __restrict__ eps, const double* __restrict__ occ,
+                              const double* __restrict__ dmu, const double* __restrict__ tbar,
+                              double inv_trace, double kT, double tau,
+                              double* __restrict__ eps_bar, double* __restrict__ occ_bar) {
+  int i = blockIdx.x;
+  long long mat = (long long)ldx * ldx;
+  double eb = 0.0, ob = 0.0;
+  for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+    double lb = 0.0;
+    for (int k = 0; k < K; ++k) {
+      double x = 0.0, gg = 0.0;
+      for (int p = 0; p < nsplit; ++p) {
+        long long o = ((long long)p * K + k) * mat + (long long)i * ldx + j;
+        x += ld_c(X, acc64, o);
+        gg += ld_c(G, acc64, o);
+      }
+      if (i == j) lb += gg * (x - dmu[k]) - tbar[k] * inv_trace * (x - dmu[k]);
+      else lb += gg * x;
+    }
+    double de = eps[i] - eps[j];
+    if (i == j) {
+      ob += lb * (-(1.0 - 2.0 * occ[i]) / kT);
+    } else if (fabs(de) > tau) {
+      eb += 2.0 * lb * (-L[(long long)i * ns + j] / de);
+      ob += 2.0 * lb / de;
+    } else {
+      double fb = 0.5 * (occ[i] + occ[j]);
+      ob += 2.0 * lb * (-(1.0 - 2.0 * fb) / (2.0 * kT));
+    }
+  }
+  __shared__ double se[32], so[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    eb += __shfl_xor_sync(0xffffffffu, eb, o);
+    ob += __shfl_xor_sync(0xffffffffu, ob, o);
+  }
+  if ((threadIdx.x & 31) == 0) { se[threadIdx.x >> 5] = eb; so[threadIdx.x >> 5] = ob; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += se[w]; b += so[w]; }
+    if (eps_bar) eps_bar[i] = a;
+    if (occ_bar) occ_bar[i] = b;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long long Ng,
+                            void* fft_real, int fp64, cudaStream_t st) {
+  k_spin_sum<<<grid_for((long long)K * Ng, 256), 256, 0, st>>>(v, io_dtype, K, nspin, Ng,
+                                                                fft_real, fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_symbol(void* cplx, int K, const int* n, const double* h, int kind,
+                                  int fp64, cudaStream_t st) {
+  long long tot = (long long)K * n[0] * n[1] * (n[2] / 2 + 1);
+  k_poisson<<<grid_for(tot, 256), 256, 0, st>>>(cplx, K, n[0], n[1], n[2], h[0], h[1], h[2], kind,
+                                                 fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dv_weights(const void* v, int io_dtype, const void* VH, const double* fx0,
+                              const double* fx1, int K, int nspin, long long Ng, long long Ng_pad,
+                              double scale, void* a, int fp64, cudaStream_t st) {
+  k_dv_weights<<<grid_for((long long)K * nspin * Ng_pad, 256), 256, 0, st>>>(
+      v, io_dtype, VH, fx0, fx1, K, nspin, Ng, Ng_pad, scale, a, fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_potential(const void* dvbar, const void* VH, const double* fx0,
+                                     const double* fx1, const void* fbar, int io_dtype, int K,
+                                     int nspin, long long Ng, long long Ng_pad, void* vbar,
+                                     int fp64, cudaStream_t st) {
+  k_adjoint_potential<<<grid_for((long long)K * nspin * Ng, 256), 256, 0, st>>>(
+      dvbar, VH, fx0, fx1, fbar, io_dtype, K, nspin, Ng, Ng_pad, vbar, fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spin_sum_padded(const void* d, int K, int nspin, long long Ng,
+                                   long long Ng_pad, void* out, int fp64, cudaStream_t st) {
+  k_spin_sum_padded<<<grid_for((long long)K * Ng, 256), 256, 0, st>>>(d, K, nspin, Ng, Ng_pad,
+                                                                       out, fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_weights(const void* fbar, int io_dtype, int K, int nspin, long long Ng,
+                                 long long Ng_pad, double scale, void* a, int fp64,
+                                 cudaStream_t st) {
+  k_scale_weights<<<grid_for((long long)K * nspin * Ng_pad, 256), 256, 0, st>>>(
+      fbar, io_dtype, K, nspin, Ng, Ng_pad, scale, a, fp64);
+  return cudaGetLastError();
+}
+
+static DmuArgs dmu_args(const SysState& S, const void* const* X, int K) {
+  DmuArgs A{};
+  int tc = (S.ch[0].psiR_hi || S.ch[0].psiR32) ? 1 : 0;
+  for (int s = 0; s < S.nspin; ++s) {
+    A.X[s] = X[s];
+    A.L[s] = S.ch[s].L;
+    A.ns[s] = S.ch[s].ns;
+    A.ldx[s] = tc ? S.ch[s].ns_pad : S.ch[s].ns;
+  }
+  A.nsplit = S.nsplit;
+  A.nspin = S.nspin;
+  A.K = K;
+  return A;
+}
+
+cudaError_t launch_dmu(const SysState& S, const void* const* Xparts, int K, int acc_fp64,
+                       double* dmu, double* dmu_out, int* status, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  k_dmu<<<K, 256, 0, st>>>(dmu_args(S, Xparts, K), acc_fp64, dmu, dmu_out, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_bar(const SysState& S, const void* const* Gparts, int K, int acc_fp64,
+                             double* tbar, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  k_trace_bar<<<K, 256, 0, st>>>(dmu_args(S, Gparts, K), acc_fp64, tbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loewner_scale(const SysState& S, int s, const void* Xpart, int K, int acc_fp64,
+                                 const double* shift, int adjoint, double inv_trace_L, int prec,
+                                 cudaStream_t st) {
+  const Channel& c = S.ch[s];
+  int layout = prec == LRDM_BF16X3 ? 2 : (prec == LRDM_TF32 ? 1 : 0);
+  int ldx = layout == 0 ? c.ns : c.ns_pad;
+  int ldo = layout == 0 ? c.ns : c.ns_pad;
+  long long tot = (long long)K * ldo * ldo;
+  k_loewner_scale<<<grid_for(tot, 256), 256, 0, st>>>(
+      Xpart, acc_fp64, S.nsplit, K, c.ns, ldx, c.L, shift, adjoint, inv_trace_L, layout, ldo,
+      c.Xpp, static_cast<__nv_bfloat16*>(c.Xpp_lo));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eps_occ_bar(const SysState& S, int s, int K, int acc_fp64, double inv_trace_L,
+                               double degen_tol, double* eps_bar, double* occ_bar,
+                               cudaStream_t st) {
+  const Channel& c = S.ch[s];
+  int tc = (c.psiR_hi || c.psiR32) ? 1 : 0;
+  int ldx = tc ? c.ns_pad : c.ns;
+  k_eps_occ_bar<<<c.ns, 256, 0, st>>>(c.Xpart, c.Gpart, acc_fp64, S.nsplit, K, c.ns, ldx, c.L,
+                                      c.eps, c.occ, S.dmu, S.tbar, inv_trace_L, S.kT,
+                                      degen_tol * S.kT, eps_bar, occ_bar);
+  return cudaGetLastError();
+}
+
+}  // namespace lrdm

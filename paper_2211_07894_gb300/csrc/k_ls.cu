@@ -1,0 +1,293 @@
+// The low-rank least-squares step (Eqs. plowrank, relativeError, quasinewton):
+//   S_kl = <f_k, f_l>, c_k = <f_k, R>, ||R||^2   (FP64 partial sums, fixed order)
+//   S = Q diag(lambda) Q^T by cyclic Jacobi rotations (FP64, one block)
+//   a = Q diag(lambda^+) Q^T c  (lambda < rcond lambda_max dropped -> SINGULAR flag)
+//   Delta = sum_k a_k v_k, rho <- rho - alpha Delta, s_rel = ||F a - R|| / ||R||
+#include "lrdm_internal.h"
+
+#include <math.h>
+
+namespace lrdm {
+namespace {
+
+__device__ __forceinline__ double ldio(const void* p, int io, long long i) {
+  return io == LRDM_DTYPE_F64 ? static_cast<const double*>(p)[i]
+                              : (double)static_cast<const float*>(p)[i];
+}
+
+// values per block: K(K+1)/2 Gram entries (upper, row-major), K RHS, 1 ||R||^2
+__global__ void __launch_bounds__(256) k_gram(const void* __restrict__ F,
+                                              const void* __restrict__ R, int io, int K,
+                                              long long n, double* __restrict__ partial) {
+  __shared__ double Fs[KMAX_LIMIT][LS_CHUNK];
+  __shared__ double Rs[LS_CHUNK];
+  const int npair = K * (K + 1) / 2;
+  const int nval = npair + K + 1;
+  double acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t] = 0.0;
+  for (long long base = (long long)blockIdx.x * LS_CHUNK; base < n;
+       base += (long long)gridDim.x * LS_CHUNK) {
+    for (int e = threadIdx.x; e < (K + 1) * LS_CHUNK; e += blockDim.x) {
+      int k = e / LS_CHUNK, c = e % LS_CHUNK;
+      long long r = base + c;
+      double x = 0.0;
+      if (r < n) x = k < K ? ldio(F, io, (long long)k * n + r) : ldio(R, io, r);
+      if (k < K) Fs[k][c] = x;
+      else Rs[c] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      int idx = threadIdx.x + t * blockDim.x;
+      if (idx < nval) {
+        const double* x;
+        const double* y;
+        if (idx < npair) {
+          // row-major upper triangle enumeration: idx -> (k, l), k <= l
+          int k = 0, rem = idx;
+          while (rem >= K - k) { rem -= K - k; ++k; }
+          x = Fs[k];
+          y = Fs[k + rem];
+        } else if (idx < npair + K) {
+          x = Fs[idx - npair];
+          y = Rs;
+        } else {
+          x = Rs;
+          y = Rs;
+        }
+        double s = 0.0;
+        for (int c = 0; c < LS_CHUNK; ++c) s += x[c] * y[c];
+        acc[t] += s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    int idx = threadIdx.x + t * blockDim.x;
+    if (idx < nval) partial[(long long)blockIdx.x * nval + idx] = acc[t];
+  }
+}
+
+// One block of 64 threads: reduce partials, Jacobi eigendecomposition, a = S^+ c.
+__global__ void __launch_bounds__(KMAX_LIMIT) k_ls_solve(const double* __restrict__ partial,
+                                                         int nblk, int K, double w, double rcond,
+                                                         double* __restrict__ coef,
+                                                         double* __restrict__ coeff_out,
+                                                         double* __restrict__ scal,
+                                                         int* __restrict__ status) {
+  // dynamic shared memory: A(K, K+1), Q(K, K+1) (FP64)
+  extern __shared__ double dyn[];
+  const int ldk = K + 1;
+  double* Abuf = dyn;
+  double* Qbuf = dyn + (size_t)K * ldk;
+#define A(i, j) Abuf[(i) * ldk + (j)]
+#define Q(i, j) Qbuf[(i) * ldk + (j)]
+  __shared__ double c[KMAX_LIMIT];
+  __shared__ double lam[KMAX_LIMIT];
+  __shared__ double r2s;
+  __shared__ int bad;
+  const int npair = K * (K + 1) / 2;
+  const int nval = npair + K + 1;
+  const int t = threadIdx.x;
+  if (t == 0) bad = 0;
+  // fixed-order reduction of the per-block partials
+  for (int idx = t; idx < nval; idx += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(long long)b * nval + idx];
+    s *= w;
+    if (idx < npair) {
+      int k = 0, rem = idx;
+      while (rem >= K - k) { rem -= K - k; ++k; }
+      A(k, k + rem) = s;
+      A(k + rem, k) = s;
+    } else if (idx < npair + K) {
+      c[idx - npair] = s;
+    } else {
+      r2s = s;
+    }
+  }
+  __syncthreads();
+  if (t < K) {
+    for (int j = 0; j < K; ++j) Q(t, j) = (t == j) ? 1.0 : 0.0;
+    for (int j = 0; j < K; ++j)
+      if (!isfinite(A(t, j))) bad = 1;
+    if (!isfinite(c[t])) bad = 1;
+  }
+  __syncthreads();
+  if (bad) {
+    if (t == 0) atomicOr(status, STATUS_NONFINITE);
+    if (t < K) { coef[t] = 0.0; if (coeff_out) coeff_out[t] = 0.0; }
+    if (t == 0) { scal[0] = r2s; }
+    return;
+  }
+  // cyclic Jacobi sweeps
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    __shared__ double off, diag;
+    if (t == 0) {
+      double o = 0.0, d = 0.0;
+      for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) {
+          if (i == j) d += A(i, i) * A(i, i);
+          else o += A(i, j) * A(i, j);
+        }
+      off = o;
+      diag = d;
+    }
+    __syncthreads();
+    if (!(off > 1e-30 * diag) || off == 0.0) break;
+    for (int p = 0; p < K - 1; ++p) {
+      for (int q = p + 1; q < K; ++q) {
+        double apq = A(p, q), app = A(p, p), aqq = A(q, q);
+        __syncthreads();
+        if (apq == 0.0 || fabs(apq) < 1e-300) continue;
+        double tau = (aqq - app) / (2.0 * apq);
+        double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
+        double akp = 0, akq = 0, qkp = 0, qkq = 0;
+        if (t < K) { akp = A(t, p); akq = A(t, q); qkp = Q(t, p); qkq = Q(t, q); }
+        __syncthreads();
+        if (t < K) {
+          if (t != p && t != q) {
+            double np = cs * akp - sn * akq, nq = sn * akp + cs * akq;
+            A(t, p) = np; A(p, t) = np;
+            A(t, q) = nq; A(q, t) = nq;
+          }
+          Q(t, p) = cs * qkp - sn * qkq;
+          Q(t, q) = sn * qkp + cs * qkq;
+        }
+        if (t == 0) {
+          A(p, p) = app - tt * apq;
+          A(q, q) = aqq + tt * apq;
+          A(p, q) = 0.0;
+          A(q, p) = 0.0;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (t < K) lam[t] = A(t, t);
+  __syncthreads();
+  __shared__ double lmax;
+  __shared__ int dropped;
+  if (t == 0) {
+    double m = 0.0;
+    for (int i = 0; i < K; ++i) m = fmax(m, lam[i]);
+    lmax = m;
+    dropped = 0;
+  }
+  __syncthreads();
+  // y = diag(lambda^+) Q^T c
+  __shared__ double y[KMAX_LIMIT];
+  if (t < K) {
+    double s = 0.0;
+    for (int i = 0; i < K; ++i) s += Q(i, t) * c[i];
+    if (lmax > 0.0 && lam[t] > rcond * lmax) {
+      y[t] = s / lam[t];
+    } else {
+      y[t] = 0.0;
+      atomicOr(&dropped, 1);
+    }
+  }
+  __syncthreads();
+  if (t < K) {
+    double s = 0.0;
+    for (int i = 0; i < K; ++i) s += Q(t, i) * y[i];
+    coef[t] = s;
+    if (coeff_out) coeff_out[t] = s;
+  }
+  if (t == 0) {
+    scal[0] = r2s;
+    if (dropped) atomicOr(status, STATUS_SINGULAR);
+  }
+#undef A
+#undef Q
+}
+
+// Delta = sum_k a_k v_k; rho <- rho - alpha Delta (alpha != 0) or Delta;
+// partial sums of (sum_k a_k f_k - R)^2.
+__global__ void __launch_bounds__(256) k_update(const void* __restrict__ v,
+                                                const void* __restrict__ f,
+                                                const void* __restrict__ R, int io, int K,
+                                                long long n, double alpha,
+                                                const double* __restrict__ coef,
+                                                void* __restrict__ rho,
+                                                double* __restrict__ upd_partial) {
+  __shared__ double a[KMAX_LIMIT];
+  if (threadIdx.x < K) a[threadIdx.x] = coef[threadIdx.x];
+  __syncthreads();
+  double acc = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    double d = 0.0, fa = 0.0;
+    for (int k = 0; k < K; ++k) {
+      d += a[k] * ldio(v, io, (long long)k * n + r);
+      fa += a[k] * ldio(f, io, (long long)k * n + r);
+    }
+    double res = fa - ldio(R, io, r);
+    acc += res * res;
+    if (rho) {
+      double out = alpha != 0.0 ? ldio(rho, io, r) - alpha * d : d;
+      if (io == LRDM_DTYPE_F64) static_cast<double*>(rho)[r] = out;
+      else static_cast<float*>(rho)[r] = (float)out;
+    }
+  }
+  __shared__ double sw[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sw[i];
+    upd_partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_srel(const double* __restrict__ upd_partial, int nblk, double w,
+                       const double* __restrict__ scal, double* __restrict__ s_rel_out) {
+  __shared__ double sw[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += upd_partial[b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += sw[i];
+    double r2 = scal[0];
+    double val = r2 > 0.0 ? sqrt(w * tot / r2) : 0.0;
+    if (s_rel_out) s_rel_out[0] = val;
+    // scal layout: [0] = <R, R>, [1] = s_rel
+    const_cast<double*>(scal)[1] = val;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype, int K,
+                      long long n, double w, double alpha, double rcond, void* rho_inout,
+                      double* coef, double* coeff_out, double* s_rel_out, double* partial,
+                      double* scal, double* upd_partial, int* status, cudaStream_t st) {
+  k_gram<<<LS_BLOCKS, 256, 0, st>>>(f, R, io_dtype, K, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = 2 * (size_t)K * (K + 1) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(k_ls_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * KMAX_LIMIT * (KMAX_LIMIT + 1) * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_ls_solve<<<1, KMAX_LIMIT, smem, st>>>(partial, LS_BLOCKS, K, w, rcond, coef, coeff_out, scal,
+                                          status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_update<<<UPD_BLOCKS, 256, 0, st>>>(v, f, R, io_dtype, K, n, alpha, coef, rho_inout,
+                                       upd_partial);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_srel<<<1, 256, 0, st>>>(upd_partial, UPD_BLOCKS, w, scal, s_rel_out);
+  return cudaGetLastError();
+}
+
+}  // namespace lrdm

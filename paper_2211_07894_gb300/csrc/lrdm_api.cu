@@ -1,0 +1,554 @@
+// Host side of the C ABI declared in include/lrdm.h: argument validation,
+// set-up (chemical potential, occupations, Loewner matrix, xc kernel, operand
+// copies, cuFFT plans, workspaces) and the launch sequences of the forward,
+// least-squares and adjoint calls.
+#include "lrdm_internal.h"
+
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+using namespace lrdm;
+
+namespace {
+
+lrdm_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LRDM_OK;
+  return e == cudaErrorMemoryAllocation ? LRDM_ERR_OOM : LRDM_ERR_CUDA;
+}
+lrdm_status from_cufft(cufftResult r) {
+  if (r == CUFFT_SUCCESS) return LRDM_OK;
+  return r == CUFFT_ALLOC_FAILED ? LRDM_ERR_OOM : LRDM_ERR_CUDA;
+}
+
+#define LRDM_CK(expr)                          \
+  do {                                         \
+    lrdm_status _s = (expr);                   \
+    if (_s != LRDM_OK) return _s;              \
+  } while (0)
+#define LRDM_CU(expr) LRDM_CK(from_cuda(expr))
+#define LRDM_FFT(expr) LRDM_CK(from_cufft(expr))
+
+template <typename T>
+lrdm_status dalloc(lrdm_ctx* ctx, T** p, size_t count, bool zero = true) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return from_cuda(e);
+  ctx->allocs.push_back(q);
+  if (zero) {
+    e = cudaMemset(q, 0, count * sizeof(T));
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  *p = static_cast<T*>(q);
+  return LRDM_OK;
+}
+
+// Numerically stable Fermi function f = 1/(1 + exp(x)).
+double fermi_host(double x) {
+  if (x > 0) {
+    double e = exp(-x);
+    return e / (1.0 + e);
+  }
+  return 1.0 / (1.0 + exp(x));
+}
+
+// mu with g sum_s sum_i f((eps - mu)/kT) = N_e by bisection (Eq. kseqcont).
+lrdm_status solve_mu_host(const std::vector<std::vector<double>>& eps, double ne, double kT,
+                          double g, double* mu_out) {
+  size_t nstates = 0;
+  double lo = 1e300, hi = -1e300;
+  for (auto& e : eps) {
+    nstates += e.size();
+    for (double x : e) {
+      lo = fmin(lo, x);
+      hi = fmax(hi, x);
+    }
+  }
+  if (!(ne > 0.0 && ne < g * (double)nstates)) return LRDM_ERR_MU_NOT_CONVERGED;
+  lo -= 800.0 * kT;
+  hi += 800.0 * kT;
+  for (int it = 0; it < 400; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    double cnt = 0.0;
+    for (auto& e : eps)
+      for (double x : e) cnt += fermi_host((x - mid) / kT);
+    cnt *= g;
+    if (cnt < ne) lo = mid;
+    else hi = mid;
+  }
+  double mu = 0.5 * (lo + hi);
+  if (!isfinite(mu)) return LRDM_ERR_MU_NOT_CONVERGED;
+  *mu_out = mu;
+  return LRDM_OK;
+}
+
+bool is_tc(int prec) { return prec == LRDM_TF32 || prec == LRDM_BF16X3; }
+
+lrdm_status validate_system(const lrdm_system& s, const lrdm_options& o) {
+  for (int d = 0; d < 3; ++d) {
+    if (s.n[d] < 1) return LRDM_ERR_SHAPE;
+    if (!(s.h[d] > 0.0)) return LRDM_ERR_INVALID_ARG;
+  }
+  if (s.nspin != 1 && s.nspin != 2) return LRDM_ERR_INVALID_ARG;
+  if (!(s.kT > 0.0)) return LRDM_ERR_INVALID_ARG;
+  int km = s.k_max > 0 ? s.k_max : o.k_max;
+  if (km < 1 || km > KMAX_LIMIT) return LRDM_ERR_INVALID_ARG;
+  for (int c = 0; c < s.nspin; ++c) {
+    if (s.ns[c] < 1) return LRDM_ERR_SHAPE;
+    if (s.ld_psi[c] < s.ns[c]) return LRDM_ERR_SHAPE;
+    if (!s.psi[c] || !s.eps[c]) return LRDM_ERR_INVALID_ARG;
+    long long ng = (long long)s.n[0] * s.n[1] * s.n[2];
+    if (s.ns[c] > ng) return LRDM_ERR_SHAPE;
+  }
+  return LRDM_OK;
+}
+
+lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStream_t st) {
+  const lrdm_options& o = ctx->opt;
+  SysState& S = ctx->sys[idx];
+  const int prec = o.prec;
+  const int fp64 = prec == LRDM_FP64;
+  const size_t csz = fp64 ? sizeof(double) : sizeof(float);
+  for (int d = 0; d < 3; ++d) {
+    S.n[d] = in.n[d];
+    S.h[d] = in.h[d];
+  }
+  S.Ng = (long long)in.n[0] * in.n[1] * in.n[2];
+  S.Ng_pad = is_tc(prec) ? (S.Ng + TC_PAD_GRID - 1) / TC_PAD_GRID * TC_PAD_GRID : S.Ng;
+  S.nspin = in.nspin;
+  S.kmax = in.k_max > 0 ? in.k_max : o.k_max;
+  S.w = in.h[0] * in.h[1] * in.h[2];
+  S.g = in.occ_factor != 0.0 ? in.occ_factor : (in.nspin == 1 ? 2.0 : 1.0);
+  S.kT = in.kT;
+  S.ne = in.n_electrons;
+  S.occ_given = in.occ[0] != nullptr;
+
+  // eigenvalues (and given occupations) to the host for mu
+  std::vector<std::vector<double>> eps(in.nspin), occ(in.nspin);
+  for (int c = 0; c < in.nspin; ++c) {
+    eps[c].resize(in.ns[c]);
+    LRDM_CU(cudaMemcpy(eps[c].data(), in.eps[c], in.ns[c] * sizeof(double),
+                       cudaMemcpyDeviceToHost));
+    if (S.occ_given) {
+      if (!in.occ[c]) return LRDM_ERR_INVALID_ARG;
+      occ[c].resize(in.ns[c]);
+      LRDM_CU(cudaMemcpy(occ[c].data(), in.occ[c], in.ns[c] * sizeof(double),
+                         cudaMemcpyDeviceToHost));
+    }
+  }
+  lrdm_status ms = solve_mu_host(eps, S.ne, S.kT, S.g, &S.mu);
+  if (ms != LRDM_OK) {
+    if (!S.occ_given) return ms;
+    S.mu = 0.0;
+  }
+  if (!S.occ_given)
+    for (int c = 0; c < in.nspin; ++c) {
+      occ[c].resize(in.ns[c]);
+      for (int i = 0; i < in.ns[c]; ++i) occ[c][i] = fermi_host((eps[c][i] - S.mu) / S.kT);
+    }
+
+  for (int c = 0; c < in.nspin; ++c) {
+    Channel& ch = S.ch[c];
+    const int ns = in.ns[c];
+    ch.ns = ns;
+    ch.ns_pad = is_tc(prec) ? (ns + TC_PAD_STATES - 1) / TC_PAD_STATES * TC_PAD_STATES : ns;
+    LRDM_CK(dalloc(ctx, &ch.eps, ns));
+    LRDM_CK(dalloc(ctx, &ch.occ, ns));
+    LRDM_CU(cudaMemcpyAsync(ch.eps, eps[c].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    LRDM_CU(cudaMemcpyAsync(ch.occ, occ[c].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    LRDM_CK(dalloc(ctx, &ch.L, (size_t)ns * ns, false));
+    LRDM_CU(launch_loewner(ch.eps, ch.occ, ns, S.mu, S.kT, S.occ_given ? 1 : 0, o.degen_tol, ch.L, st));
+    // density and xc kernel
+    LRDM_CK(dalloc(ctx, &ch.rho, S.Ng, false));
+    if (in.rho[c]) {
+      LRDM_CU(launch_copy_rho(in.rho[c], o.io_dtype, S.Ng, ch.rho, st));
+    } else {
+      LRDM_CU(launch_density(in.psi[c], o.io_dtype, in.ld_psi[c], S.Ng, ns, ch.occ, S.g,
+                             in.rho_floor, ch.rho, st));
+    }
+    LRDM_CK(dalloc(ctx, &ch.fx, S.Ng, false));
+    LRDM_CU(launch_fx(ch.rho, S.Ng, in.nspin == 2, ch.fx, st));
+    // operand copies of Psi
+    const size_t npsi = (size_t)S.Ng * ns;
+    if (prec == LRDM_FP64) {
+      LRDM_CK(dalloc(ctx, &ch.psi64, npsi, false));
+    } else if (prec == LRDM_FP32) {
+      LRDM_CK(dalloc(ctx, &ch.psi32, npsi, false));
+    } else {
+      const size_t npad = (size_t)S.Ng_pad * ch.ns_pad;
+      if (prec == LRDM_TF32) {
+        LRDM_CK(dalloc(ctx, &ch.psiR32, npad, false));
+        LRDM_CK(dalloc(ctx, &ch.psiT32, npad, false));
+      } else {
+        LRDM_CK(dalloc(ctx, &ch.psiR_hi, npad, false));
+        LRDM_CK(dalloc(ctx, &ch.psiR_lo, npad, false));
+        LRDM_CK(dalloc(ctx, &ch.psiT_hi, npad, false));
+        LRDM_CK(dalloc(ctx, &ch.psiT_lo, npad, false));
+      }
+    }
+    LRDM_CU(launch_convert_psi(in.psi[c], o.io_dtype, in.ld_psi[c], S.Ng, ns, ch, prec, S.Ng_pad, st));
+  }
+
+  // split of the grid reduction for the CUDA-core GEMM1 (enough blocks to fill
+  // 152 SMs twice); the tensor-core GEMM1 reduces the whole grid per tile.
+  if (!is_tc(prec)) {
+    int nt = (S.ch[0].ns + SIMT_TILE - 1) / SIMT_TILE;
+    long long blocks = (long long)nt * (nt + 1) / 2 * S.kmax;
+    long long want = (2LL * 152 * 2 + blocks - 1) / blocks;
+    long long maxsplit = S.Ng / 256 > 0 ? S.Ng / 256 : 1;
+    if (want > maxsplit) want = maxsplit;
+    if (want > 64) want = 64;
+    S.nsplit = (int)(want < 1 ? 1 : want);
+  } else {
+    S.nsplit = 1;
+  }
+
+  // workspaces
+  const int accsz = fp64 ? 8 : 4;
+  for (int c = 0; c < in.nspin; ++c) {
+    Channel& ch = S.ch[c];
+    const size_t ldx = is_tc(prec) ? ch.ns_pad : ch.ns;
+    const size_t xcount = (size_t)S.nsplit * S.kmax * ldx * ldx;
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ch.Xpart), xcount * accsz));
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ch.Gpart), xcount * accsz));
+    const size_t pcount = (size_t)S.kmax * ldx * ldx;
+    if (prec == LRDM_BF16X3) {
+      LRDM_CK(dalloc(ctx, reinterpret_cast<__nv_bfloat16**>(&ch.Xpp), pcount));
+      LRDM_CK(dalloc(ctx, reinterpret_cast<__nv_bfloat16**>(&ch.Xpp_lo), pcount));
+    } else {
+      LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ch.Xpp), pcount * csz));
+    }
+  }
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.a), (size_t)S.kmax * S.nspin * S.Ng_pad * csz));
+  LRDM_CK(dalloc(ctx, &S.dmu, S.kmax));
+  LRDM_CK(dalloc(ctx, &S.tbar, S.kmax));
+
+  // Poisson: batched real <-> half-complex transforms over k_max fields
+  const long long nc = (long long)S.n[0] * S.n[1] * (S.n[2] / 2 + 1);
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_real), (size_t)S.kmax * S.Ng * csz));
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_cplx), (size_t)S.kmax * nc * 2 * csz));
+  int nn[3] = {S.n[0], S.n[1], S.n[2]};
+  LRDM_FFT(cufftPlanMany(&S.plan_r2c, 3, nn, nullptr, 1, (int)S.Ng, nullptr, 1, (int)nc,
+                         fp64 ? CUFFT_D2Z : CUFFT_R2C, S.kmax));
+  S.plans = true;
+  LRDM_FFT(cufftPlanMany(&S.plan_c2r, 3, nn, nullptr, 1, (int)nc, nullptr, 1, (int)S.Ng,
+                         fp64 ? CUFFT_Z2D : CUFFT_C2R, S.kmax));
+  return LRDM_OK;
+}
+
+// V_H = F^-1[4 pi F[fft_real] / |G|^2] in place in S.fft_real (all k_max slots).
+lrdm_status hartree(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
+  const int fp64 = ctx->opt.prec == LRDM_FP64;
+  LRDM_FFT(cufftSetStream(S.plan_r2c, st));
+  LRDM_FFT(cufftSetStream(S.plan_c2r, st));
+  if (fp64) {
+    LRDM_FFT(cufftExecD2Z(S.plan_r2c, static_cast<cufftDoubleReal*>(S.fft_real),
+                          static_cast<cufftDoubleComplex*>(S.fft_cplx)));
+  } else {
+    LRDM_FFT(cufftExecR2C(S.plan_r2c, static_cast<cufftReal*>(S.fft_real),
+                          static_cast<cufftComplex*>(S.fft_cplx)));
+  }
+  LRDM_CU(launch_poisson_symbol(S.fft_cplx, K, S.n, S.h, ctx->opt.poisson_symbol, fp64, st));
+  if (fp64) {
+    LRDM_FFT(cufftExecZ2D(S.plan_c2r, static_cast<cufftDoubleComplex*>(S.fft_cplx),
+                          static_cast<cufftDoubleReal*>(S.fft_real)));
+  } else {
+    LRDM_FFT(cufftExecC2R(S.plan_c2r, static_cast<cufftComplex*>(S.fft_cplx),
+                          static_cast<cufftReal*>(S.fft_real)));
+  }
+  return LRDM_OK;
+}
+
+size_t io_size(int io) { return io == LRDM_DTYPE_F64 ? 8 : 4; }
+
+// GEMM1 of channel c with weights S.a -> Xdst (split partials or full matrix)
+lrdm_status gemm1(lrdm_ctx* ctx, SysState& S, int c, int K, void* Xdst, cudaStream_t st) {
+  const int prec = ctx->opt.prec;
+  Channel& ch = S.ch[c];
+  const size_t csz = prec == LRDM_FP64 ? 8 : 4;
+  const char* a = static_cast<const char*>(S.a) + (size_t)c * S.Ng_pad * csz;
+  if (is_tc(prec)) {
+    return from_cuda(launch_gemm1_tc(prec, ch, S, c, K, reinterpret_cast<const float*>(a), Xdst,
+                                     ctx->d_status, st));
+  }
+  const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
+                                      : static_cast<const void*>(ch.psi32);
+  return from_cuda(launch_gemm1_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, a,
+                                     (long long)S.nspin * S.Ng_pad, K, Xdst, S.nsplit, st));
+}
+
+// GEMM2 of channel c: out = factor * diag(Psi X'' Psi^T) (- v)
+lrdm_status gemm2(lrdm_ctx* ctx, SysState& S, int c, int K, double factor, const void* v,
+                  long long v_stride, void* out, long long out_stride, int out_is_io,
+                  cudaStream_t st) {
+  const int prec = ctx->opt.prec;
+  Channel& ch = S.ch[c];
+  if (is_tc(prec)) {
+    return from_cuda(launch_gemm2_tc(prec, ch, S, K, factor, v, v_stride, out, out_stride,
+                                     ctx->opt.io_dtype, out_is_io, ctx->d_status, st));
+  }
+  const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
+                                      : static_cast<const void*>(ch.psi32);
+  return from_cuda(launch_gemm2_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, ch.Xpp, K, factor, v,
+                                     v_stride, out, out_stride, ctx->opt.io_dtype, out_is_io, st));
+}
+
+lrdm_status forward_system(lrdm_ctx* ctx, int s, const void* v, int K, void* f, double* dmu_out,
+                           cudaStream_t st) {
+  SysState& S = ctx->sys[s];
+  const int prec = ctx->opt.prec;
+  const int fp64 = prec == LRDM_FP64;
+  const int io = ctx->opt.io_dtype;
+  S.last_K = K;
+  if (K == 0) return LRDM_OK;
+  LRDM_CU(launch_spin_sum(v, io, K, S.nspin, S.Ng, S.fft_real, fp64, st));
+  LRDM_CK(hartree(ctx, S, K, st));
+  LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, K, S.nspin, S.Ng,
+                            S.Ng_pad, S.w, S.a, fp64, st));
+  for (int c = 0; c < S.nspin; ++c) LRDM_CK(gemm1(ctx, S, c, K, S.ch[c].Xpart, st));
+  const void* X[2] = {S.ch[0].Xpart, S.ch[S.nspin - 1].Xpart};
+  LRDM_CU(launch_dmu(S, X, K, fp64, S.dmu, dmu_out, ctx->d_status, st));
+  const size_t isz = io_size(io);
+  for (int c = 0; c < S.nspin; ++c) {
+    LRDM_CU(launch_loewner_scale(S, c, S.ch[c].Xpart, K, fp64, S.dmu, 0, 0.0, prec, st));
+    LRDM_CK(gemm2(ctx, S, c, K, S.g, static_cast<const char*>(v) + (size_t)c * S.Ng * isz,
+                  (long long)S.nspin * S.Ng, static_cast<char*>(f) + (size_t)c * S.Ng * isz,
+                  (long long)S.nspin * S.Ng, 1, st));
+  }
+  return LRDM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+namespace {
+void free_ctx(lrdm_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    if (S.plan_r2c) cufftDestroy(S.plan_r2c);
+    if (S.plan_c2r) cufftDestroy(S.plan_c2r);
+  }
+  for (void* p : ctx->allocs) cudaFree(p);
+  delete[] ctx->sys;
+  delete ctx;
+}
+}  // namespace
+
+extern "C" {
+
+void lrdm_default_options(lrdm_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->prec = LRDM_BF16X3;
+  o->io_dtype = LRDM_DTYPE_F32;
+  o->k_max = 16;
+  o->pinv_rcond = 1e-12;
+  o->degen_tol = 1e-5;
+  o->poisson_symbol = 0;
+  o->use_graph = 0;
+  o->autotune = 0;
+  o->debug_flags = 0;
+}
+
+const char* lrdm_status_string(lrdm_status s) {
+  switch (s) {
+    case LRDM_OK: return "ok";
+    case LRDM_ERR_INVALID_ARG: return "invalid argument";
+    case LRDM_ERR_SHAPE: return "inconsistent shape";
+    case LRDM_ERR_OOM: return "out of device memory";
+    case LRDM_ERR_CUDA: return "CUDA error";
+    case LRDM_ERR_MU_NOT_CONVERGED: return "chemical potential not found";
+    case LRDM_ERR_SINGULAR: return "singular least-squares matrix (pseudo-inverse used)";
+    case LRDM_ERR_TIMEOUT: return "bounded device wait expired";
+    case LRDM_ERR_NONFINITE: return "non-finite value on the device";
+    case LRDM_ERR_UNSUPPORTED: return "unsupported precision or feature";
+  }
+  return "unknown status";
+}
+
+lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
+                        const lrdm_options* opt, void* stream) {
+  if (!out) return LRDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!sys || nsys < 1) return LRDM_ERR_INVALID_ARG;
+  lrdm_options o;
+  if (opt) o = *opt;
+  else lrdm_default_options(&o);
+  if (o.prec < LRDM_FP64 || o.prec > LRDM_BF16X3) return LRDM_ERR_INVALID_ARG;
+  if (o.io_dtype != LRDM_DTYPE_F64 && o.io_dtype != LRDM_DTYPE_F32) return LRDM_ERR_INVALID_ARG;
+  if (o.k_max < 1 || o.k_max > KMAX_LIMIT) return LRDM_ERR_INVALID_ARG;
+  if (!(o.pinv_rcond >= 0.0)) return LRDM_ERR_INVALID_ARG;
+  if (!(o.degen_tol >= 0.0)) return LRDM_ERR_INVALID_ARG;
+  if (o.poisson_symbol != 0 && o.poisson_symbol != 1) return LRDM_ERR_INVALID_ARG;
+  for (int s = 0; s < nsys; ++s) LRDM_CK(validate_system(sys[s], o));
+  if (is_tc(o.prec) && !tc_supported()) return LRDM_ERR_UNSUPPORTED;
+
+  lrdm_ctx* ctx = new (std::nothrow) lrdm_ctx();
+  if (!ctx) return LRDM_ERR_OOM;
+  ctx->nsys = nsys;
+  ctx->opt = o;
+  cudaGetDevice(&ctx->device);
+  ctx->sys = new (std::nothrow) SysState[nsys];
+  if (!ctx->sys) {
+    delete ctx;
+    return LRDM_ERR_OOM;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lrdm_status rc = LRDM_OK;
+  do {
+    if ((rc = dalloc(ctx, &ctx->d_status, 1)) != LRDM_OK) break;
+    const int maxval = KMAX_LIMIT * (KMAX_LIMIT + 1) / 2 + KMAX_LIMIT + 1;
+    if ((rc = dalloc(ctx, &ctx->ls_partial, (size_t)LS_BLOCKS * maxval)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->ls_coef, KMAX_LIMIT)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->ls_scal, 4)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->upd_partial, UPD_BLOCKS)) != LRDM_OK) break;
+    ctx->inv_trace.resize(nsys);
+    for (int s = 0; s < nsys && rc == LRDM_OK; ++s) {
+      rc = setup_system(ctx, s, sys[s], st);
+      if (rc != LRDM_OK) break;
+      // 1 / sum_s sum_i L_ii with L_ii = -f_i (1 - f_i)/kT
+      double tr = 0.0;
+      SysState& S = ctx->sys[s];
+      for (int c = 0; c < S.nspin; ++c) {
+        std::vector<double> occ(S.ch[c].ns);
+        if (cudaMemcpyAsync(occ.data(), S.ch[c].occ, occ.size() * 8, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+          rc = LRDM_ERR_CUDA;
+          break;
+        }
+        for (double f : occ) tr += -f * (1.0 - f) / S.kT;
+      }
+      ctx->inv_trace[s] = tr != 0.0 ? 1.0 / tr : 0.0;
+    }
+    if (rc != LRDM_OK) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = LRDM_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) rc = LRDM_ERR_CUDA;
+  } while (0);
+  if (rc != LRDM_OK) {
+    free_ctx(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K,
+                               void* const* f_out, double* dmu_out, void* stream) {
+  if (!ctx || !v || !K || !f_out) return LRDM_ERR_INVALID_ARG;
+  for (int s = 0; s < ctx->nsys; ++s) {
+    if (K[s] < 0 || K[s] > ctx->sys[s].kmax) return LRDM_ERR_INVALID_ARG;
+    if (K[s] > 0 && (!v[s] || !f_out[s])) return LRDM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int off = 0;
+  for (int s = 0; s < ctx->nsys; ++s) {
+    LRDM_CK(forward_system(ctx, s, v[s], K[s], f_out[s], dmu_out ? dmu_out + off : nullptr, st));
+    off += K[s];
+  }
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, const void* f, int K,
+                       double alpha, void* rho_inout, double* coeff_out, double* s_rel_out,
+                       void* stream) {
+  if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !v || !f) return LRDM_ERR_INVALID_ARG;
+  if (K < 1 || K > KMAX_LIMIT) return LRDM_ERR_INVALID_ARG;
+  if (!isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
+  SysState& S = ctx->sys[sys];
+  long long n = (long long)S.nspin * S.Ng;
+  return from_cuda(launch_ls(R, v, f, ctx->opt.io_dtype, K, n, S.w, alpha, ctx->opt.pinv_rcond,
+                             rho_inout, ctx->ls_coef, coeff_out, s_rel_out, ctx->ls_partial,
+                             ctx->ls_scal, ctx->upd_partial, ctx->d_status,
+                             static_cast<cudaStream_t>(stream)));
+}
+
+lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
+                          double* const* eps_bar, double* const* occ_bar, void* stream) {
+  if (!ctx || !f_bar || !v_bar) return LRDM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int prec = ctx->opt.prec;
+  const int fp64 = prec == LRDM_FP64;
+  const int io = ctx->opt.io_dtype;
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    if (S.last_K < 0) return LRDM_ERR_INVALID_ARG;   // no forward call yet
+    if (S.last_K > 0 && (!f_bar[s] || !v_bar[s])) return LRDM_ERR_INVALID_ARG;
+  }
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    const int K = S.last_K;
+    const double inv_tr = ctx->inv_trace[s];
+    if (K > 0) {
+      // Gbar_k = g Psi^T diag(fbar_k) Psi
+      LRDM_CU(launch_scale_weights(f_bar[s], io, K, S.nspin, S.Ng, S.Ng_pad, S.g, S.a, fp64, st));
+      for (int c = 0; c < S.nspin; ++c) LRDM_CK(gemm1(ctx, S, c, K, S.ch[c].Gpart, st));
+      const void* G[2] = {S.ch[0].Gpart, S.ch[S.nspin - 1].Gpart};
+      LRDM_CU(launch_trace_bar(S, G, K, fp64, S.tbar, st));
+      // Ybar = L o Gbar - diag(L) T / sum L;  dVbar = w diag(Psi Ybar Psi^T)
+      const size_t csz = fp64 ? 8 : 4;
+      for (int c = 0; c < S.nspin; ++c) {
+        LRDM_CU(launch_loewner_scale(S, c, S.ch[c].Gpart, K, fp64, S.tbar, 1, inv_tr, prec, st));
+        LRDM_CK(gemm2(ctx, S, c, K, S.w, nullptr, 0,
+                      static_cast<char*>(S.a) + (size_t)c * S.Ng_pad * csz,
+                      (long long)S.nspin * S.Ng_pad, 0, st));
+      }
+      // vbar = V_H[sum_s dVbar] + f_x dVbar - fbar
+      LRDM_CU(launch_spin_sum_padded(S.a, K, S.nspin, S.Ng, S.Ng_pad, S.fft_real, fp64, st));
+      LRDM_CK(hartree(ctx, S, K, st));
+      LRDM_CU(launch_adjoint_potential(S.a, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, f_bar[s],
+                                       io, K, S.nspin, S.Ng, S.Ng_pad, v_bar[s], fp64, st));
+    }
+    for (int c = 0; c < S.nspin; ++c) {
+      double* eb = eps_bar ? eps_bar[2 * s + c] : nullptr;
+      double* ob = occ_bar ? occ_bar[2 * s + c] : nullptr;
+      if (!eb && !ob) continue;
+      if (K == 0) {
+        if (eb) LRDM_CU(cudaMemsetAsync(eb, 0, S.ch[c].ns * sizeof(double), st));
+        if (ob) LRDM_CU(cudaMemsetAsync(ob, 0, S.ch[c].ns * sizeof(double), st));
+        continue;
+      }
+      LRDM_CU(launch_eps_occ_bar(S, c, K, fp64, inv_tr, ctx->opt.degen_tol, eb, ob, st));
+    }
+  }
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_status_query(lrdm_ctx* ctx, int synchronize) {
+  if (!ctx) return LRDM_ERR_INVALID_ARG;
+  if (synchronize && cudaDeviceSynchronize() != cudaSuccess) return LRDM_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LRDM_ERR_CUDA;
+  if (cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) return LRDM_ERR_CUDA;
+  if (h & STATUS_TIMEOUT) return LRDM_ERR_TIMEOUT;
+  if (h & STATUS_NONFINITE) return LRDM_ERR_NONFINITE;
+  if (h & STATUS_SINGULAR) return LRDM_ERR_SINGULAR;
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_get_mu(lrdm_ctx* ctx, int sys, double* mu_host) {
+  if (!ctx || !mu_host || sys < 0 || sys >= ctx->nsys) return LRDM_ERR_INVALID_ARG;
+  *mu_host = ctx->sys[sys].mu;
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_get_density(lrdm_ctx* ctx, int sys, int spin, void* out, void* stream) {
+  if (!ctx || !out || sys < 0 || sys >= ctx->nsys) return LRDM_ERR_INVALID_ARG;
+  SysState& S = ctx->sys[sys];
+  if (spin < 0 || spin >= S.nspin) return LRDM_ERR_INVALID_ARG;
+  return from_cuda(launch_to_io(S.ch[spin].rho, S.Ng, out, ctx->opt.io_dtype,
+                                static_cast<cudaStream_t>(stream)));
+}
+
+void lrdm_destroy(lrdm_ctx* ctx) { free_ctx(ctx); }
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// Internal declarations shared by the host orchestration (lrdm_api.cu) and
+// the kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/lrdm.h"
+
+namespace lrdm {
+
+// Bits of the sticky device status word.
+enum : int {
+  STATUS_TIMEOUT = 1,
+  STATUS_NONFINITE = 2,
+  STATUS_SINGULAR = 4,
+};
+
+constexpr int KMAX_LIMIT = 64;       // directions per system per call
+constexpr int SIMT_TILE = 64;        // CUDA-core GEMM tile edge (states)
+constexpr int LS_CHUNK = 64;         // grid points per staged chunk in the Gram kernel
+constexpr int LS_BLOCKS = 304;       // 2 x 152 SMs
+constexpr int UPD_BLOCKS = 608;
+
+// Tensor-core operand layout (BF16X3 / TF32): padded edges.
+constexpr int TC_PAD_STATES = 128;   // states padded to a multiple of this
+constexpr int TC_PAD_GRID = 128;     // grid rows padded to a multiple of this
+
+struct Channel {
+  int ns = 0;
+  int ns_pad = 0;                    // tensor-core padded state count
+  double* eps = nullptr;             // [ns]
+  double* occ = nullptr;             // [ns]
+  double* L = nullptr;               // [ns][ns] Loewner matrix
+  double* fx = nullptr;              // [Ng] xc kernel
+  double* rho = nullptr;             // [Ng] density used for fx
+  // Psi operand copies (which ones exist depends on the precision)
+  double* psi64 = nullptr;           // [Ng][ns]
+  float* psi32 = nullptr;            // [Ng][ns]           (FP32 SIMT)
+  float* psiT32 = nullptr;           // [ns_pad][Ng_pad]   (TF32, GEMM1 operand)
+  float* psiR32 = nullptr;           // [Ng_pad][ns_pad]   (TF32, GEMM2 operand)
+  __nv_bfloat16* psiT_hi = nullptr;  // [ns_pad][Ng_pad]   (BF16X3, GEMM1)
+  __nv_bfloat16* psiT_lo = nullptr;
+  __nv_bfloat16* psiR_hi = nullptr;  // [Ng_pad][ns_pad]   (BF16X3, GEMM2)
+  __nv_bfloat16* psiR_lo = nullptr;
+  // workspaces
+  void* Xpart = nullptr;             // [nsplit][kmax][ns][ns] forward X (acc type)
+  void* Gpart = nullptr;             // [nsplit][kmax][ns][ns] backward Gbar
+  void* Xpp = nullptr;               // GEMM2 operand (layout depends on precision)
+  void* Xpp_lo = nullptr;            // BF16X3 low part
+};
+
+struct SysState {
+  int n[3] = {0, 0, 0};
+  double h[3] = {0, 0, 0};
+  long long Ng = 0;
+  long long Ng_pad = 0;
+  int nspin = 1;
+  int kmax = 0;
+  double w = 0, g = 2, kT = 0, ne = 0, mu = 0;
+  bool occ_given = false;
+  Channel ch[2];
+  int nsplit = 1;                    // grid-row splits of the CUDA-core GEMM1
+  // Poisson
+  cufftHandle plan_r2c = 0, plan_c2r = 0;
+  bool plans = false;
+  void* fft_real = nullptr;          // [kmax][Ng] compute type
+  void* fft_cplx = nullptr;          // [kmax][n0][n1][n2/2+1]
+  void* a = nullptr;                 // [kmax][nspin][Ng_pad] GEMM1 weights (compute type)
+  double* dmu = nullptr;             // [kmax]
+  double* tbar = nullptr;            // [kmax] backward trace terms
+  int last_K = -1;                   // K of the most recent forward call
+};
+
+}  // namespace lrdm
+
+struct lrdm_ctx {
+  int nsys = 0;
+  lrdm_options opt{};
+  int device = 0;
+  lrdm::SysState* sys = nullptr;
+  int* d_status = nullptr;
+  double* ls_partial = nullptr;      // [LS_BLOCKS][max values]
+  double* ls_coef = nullptr;         // [KMAX_LIMIT]
+  double* ls_scal = nullptr;         // [4]: r2, s_rel scratch
+  double* upd_partial = nullptr;     // [UPD_BLOCKS]
+  std::vector<void*> allocs;         // every device allocation, freed by lrdm_destroy
+  std::vector<double> inv_trace;     // per system 1 / sum_s sum_i L_ii
+};
+
+namespace lrdm {
+
+// ---------------- setup kernels (k_setup.cu) ----------------
+cudaError_t launch_convert_psi(const void* src, int io_dtype, int ld, long long Ng, int ns,
+                               Channel& c, int prec, long long Ng_pad, cudaStream_t st);
+cudaError_t launch_density(const void* psi_src, int io_dtype, int ld, long long Ng, int ns,
+                           const double* occ, double g, double floor, double* rho, cudaStream_t st);
+cudaError_t launch_copy_rho(const void* src, int io_dtype, long long Ng, double* rho, cudaStream_t st);
+cudaError_t launch_fx(const double* rho, long long Ng, int spin_polarized, double* fx, cudaStream_t st);
+cudaError_t launch_loewner(const double* eps, const double* occ, int ns, double mu, double kT,
+                           int occ_mode, double degen_tol, double* L, cudaStream_t st);
+cudaError_t launch_to_io(const double* src, long long n, void* dst, int io_dtype, cudaStream_t st);
+
+// ---------------- element-wise / reduction kernels (k_elem.cu) ----------------
+// fft_real[k][r] = sum_s v[k][s][r]  (compute type = double if fp64 else float)
+cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long long Ng,
+                            void* fft_real, int fp64, cudaStream_t st);
+cudaError_t launch_poisson_symbol(void* cplx, int K, const int* n, const double* h, int kind,
+                                  int fp64, cudaStream_t st);
+// a[k][s][r] = scale * (VH[k][r] + fx_s[r] * v[k][s][r]);  mode 1 (adjoint):
+// out[k][s][r] = VH[k][r] + fx_s[r] * dvbar[k][s][r] - fbar[k][s][r] (io dtype)
+cudaError_t launch_dv_weights(const void* v, int io_dtype, const void* VH, const double* fx0,
+                              const double* fx1, int K, int nspin, long long Ng, long long Ng_pad,
+                              double scale, void* a, int fp64, cudaStream_t st);
+cudaError_t launch_adjoint_potential(const void* dvbar, const void* VH, const double* fx0,
+                                     const double* fx1, const void* fbar, int io_dtype, int K,
+                                     int nspin, long long Ng, long long Ng_pad, void* vbar,
+                                     int fp64, cudaStream_t st);
+// a[k][s][r] = scale * fbar[k][s][r]
+cudaError_t launch_scale_weights(const void* fbar, int io_dtype, int K, int nspin, long long Ng,
+                                 long long Ng_pad, double scale, void* a, int fp64, cudaStream_t st);
+// mu'_k = sum_s sum_i L_ii X_ii / sum_s sum_i L_ii (X summed over splits)
+cudaError_t launch_dmu(const SysState& S, const void* const* Xparts, int K, int acc_fp64,
+                       double* dmu, double* dmu_out, int* status, cudaStream_t st);
+// X''[i][j] = c_ij L_ij (X_ij - delta_ij mu'), c = 2 (i<j), 1 (i=j), 0 (i>j)
+// (adjoint = 1: Ybar = L o G - delta_ij L_ii tbar_k / sum L, same weights)
+cudaError_t launch_loewner_scale(const SysState& S, int s, const void* Xpart, int K, int acc_fp64,
+                                 const double* shift, int adjoint, double inv_trace_L,
+                                 int prec, cudaStream_t st);
+// backward: eps_bar / occ_bar of channel s
+cudaError_t launch_trace_bar(const SysState& S, const void* const* Gparts, int K, int acc_fp64,
+                             double* tbar, cudaStream_t st);
+cudaError_t launch_spin_sum_padded(const void* d, int K, int nspin, long long Ng, long long Ng_pad,
+                                   void* out, int fp64, cudaStream_t st);
+cudaError_t launch_eps_occ_bar(const SysState& S, int s, int K, int acc_fp64,
+                               double inv_trace_L, double degen_tol, double* eps_bar,
+                               double* occ_bar, cudaStream_t st);
+
+// ---------------- CUDA-core GEMMs (k_simt.cu) ----------------
+// Xpart[split][q][i][j] (tiles I <= J) = sum_r psi[r][i] a[q][r] psi[r][j]
+cudaError_t launch_gemm1_simt(int fp64, const void* psi, int ns, long long Ng, const void* a,
+                              long long a_stride, int nq, void* Xpart, int nsplit, cudaStream_t st);
+// out[q][r] = factor * sum_j sum_i psi[r][i] Xpp[q][i][j] psi[r][j] (- v[q][r] if sub_v)
+cudaError_t launch_gemm2_simt(int fp64, const void* psi, int ns, long long Ng, const void* Xpp,
+                              int nq, double factor, const void* v, long long v_stride,
+                              void* out, long long out_stride, int out_io_dtype, int out_is_io,
+                              cudaStream_t st);
+
+// ---------------- least squares (k_ls.cu) ----------------
+cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype, int K,
+                      long long n, double w, double alpha, double rcond, void* rho_inout,
+                      double* coef, double* coeff_out, double* s_rel_out, double* partial,
+                      double* scal, double* upd_partial, int* status, cudaStream_t st);
+
+// ---------------- tensor-core GEMMs (k_tc.cu) ----------------
+cudaError_t launch_gemm1_tc(int prec, const Channel& c, const SysState& S, int s, int K,
+                            const float* a, void* Xout, int* status, cudaStream_t st);
+cudaError_t launch_gemm2_tc(int prec, const Channel& c, const SysState& S, int K, double factor,
+                            const void* v, long long v_stride, void* out, long long out_stride,
+                            int out_io_dtype, int out_is_io, int* status, cudaStream_t st);
+bool tc_supported();
+
+}  // namespace lrdm

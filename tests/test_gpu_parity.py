@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerances (relative w-norm error per direction): FP64 1e-10; TF32 and
+split-BF16x3 1e-5; FP32 CUDA-core 1e-4 (FP32 accumulation over the grid).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import oracle_system, per_direction_rel_err, rel_err
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 1e-5, "bf16x3": 1e-5}
+IO = {"fp64": torch.float64, "fp32": torch.float32, "tf32": torch.float32,
+      "bf16x3": torch.float32}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2211_07894_gb300 import build, binding
+    build.build()
+    return binding.load()
+
+
+def _ragged(cfg_id=20, n=(20, 18, 22), ns=200, K=5, ne=150, kT=0.01, stream=0):
+    return workloads.random_system(cfg_id, n, ns, ne, kT, K, stream=stream)
+
+
+def _run(cfgs, prec, **kw):
+    from gpu_helpers import directions, make_context
+    io = IO[prec]
+    ctx, systems = make_context(cfgs, prec, io, **kw)
+    V = [directions(c, io) for c in cfgs]
+    F, dmu = ctx.gateaux(V)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    return ctx, V, [f.double().cpu().numpy() for f in F], dmu.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
+def test_forward_toy16(lib, cfg1, prec):
+    ctx, V, F, dmu = _run([cfg1], prec)
+    ref = oracle.gateaux(oracle_system(cfg1), cfg1["V"])
+    err = per_direction_rel_err(F[0], ref["F"])
+    print(f"toy16 {prec}: max rel err {err:.3e}")
+    assert err < TOL[prec]
+    assert np.allclose(dmu, ref["dmu"], rtol=max(TOL[prec], 1e-12) * 10, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
+def test_forward_ragged_tiles(lib, prec):
+    cfg = _ragged()
+    ctx, V, F, dmu = _run([cfg], prec)
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    err = per_direction_rel_err(F[0], ref["F"])
+    drho_err = per_direction_rel_err(F[0] + cfg["V"], ref["drho"])
+    print(f"ragged {prec}: f err {err:.3e}  drho err {drho_err:.3e}")
+    assert err < TOL[prec]
+    assert drho_err < TOL[prec] * 10
+
+
+def test_density_mu_and_given_rho(lib, cfg1):
+    from gpu_helpers import directions, make_context
+    ctx, _ = make_context([cfg1], "fp64", torch.float64)
+    osys = oracle_system(cfg1)
+    mu = oracle.solve_mu(osys.eps, osys.n_electrons, osys.kT, osys.occ_factor)
+    assert abs(ctx.mu() - mu) < 1e-12
+    rho = ctx.density().cpu().numpy()
+    assert rel_err(rho, osys.rho[0]) < 1e-13
+    # same results when the oracle's density is passed in
+    from paper_2211_07894_gb300 import Context
+    from gpu_helpers import to_device_system
+    ctx2 = Context([to_device_system(cfg1, torch.float64, pass_rho=osys.rho)], prec="fp64",
+                   io_dtype=torch.float64)
+    V = directions(cfg1, torch.float64)
+    F1, _ = ctx.gateaux([V])
+    F2, _ = ctx2.gateaux([V])
+    assert rel_err(F1[0].cpu().numpy(), F2[0].cpu().numpy()) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_spin_pair(lib, prec):
+    cfg = workloads.spin_pair_system(21, (12, 12, 12), 60, 52, 50, 0.01, 3)
+    ctx, V, F, dmu = _run([cfg], prec)
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    err = max(rel_err(F[0][k], ref["F"][k]) for k in range(3))
+    print(f"spin {prec}: {err:.3e}")
+    assert err < TOL[prec]
+    assert np.allclose(dmu, ref["dmu"], rtol=TOL[prec] * 10)
+
+
+def test_occupation_mode_near_degenerate(lib):
+    d = workloads.config4(scale=8)      # 9^3 grid, 256 states, 5 % near-degenerate pairs
+    d["V"] = d["V"][:3]
+    osys = oracle_system(d, occ_mode=True)
+    d["occ"] = osys.occ
+    ctx, V, F, dmu = _run([d], "fp64", k_max=3)
+    ref = oracle.gateaux(osys, d["V"])
+    assert per_direction_rel_err(F[0], ref["F"]) < 1e-10
+
+
+def test_near_degenerate_default_mode(lib):
+    d = workloads.config4(scale=8)
+    d["V"] = d["V"][:3]
+    ctx, V, F, dmu = _run([d], "fp64", k_max=3)
+    ref = oracle.gateaux(oracle_system(d), d["V"])
+    assert per_direction_rel_err(F[0], ref["F"]) < 1e-10
+
+
+def test_batched_uneven_equals_separate(lib):
+    cfgs = workloads.config3(scale=8)
+    from gpu_helpers import directions, make_context
+    ctx, _ = make_context(cfgs, "fp64", torch.float64)
+    V = [directions(c, torch.float64) for c in cfgs]
+    F, dmu = ctx.gateaux(V)
+    for i, c in enumerate(cfgs):
+        one, _ = make_context([c], "fp64", torch.float64)
+        Fi, dmui = one.gateaux([V[i]])
+        assert torch.equal(Fi[0], F[i])
+        ref = oracle.gateaux(oracle_system(c), c["V"])
+        assert per_direction_rel_err(F[i].cpu().numpy(), ref["F"]) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_apply_step(lib, cfg1, prec):
+    io = IO[prec]
+    # the least-squares step alone, on the oracle's derivatives
+    ctx, V, _, _ = _run([cfg1], prec)
+    osys = oracle_system(cfg1)
+    Fref = oracle.gateaux(osys, cfg1["V"])["F"]
+    Fd = torch.as_tensor(Fref, dtype=io, device="cuda")
+    Vd = V[0]
+    R = torch.as_tensor(cfg1["R"], dtype=io, device="cuda")
+    rho = torch.as_tensor(np.stack(osys.rho), dtype=io, device="cuda")
+    coef, srel = ctx.apply(0, R, Vd, Fd, 0.5, rho=rho)
+    torch.cuda.synchronize()
+    want = oracle.lrdm_apply(cfg1["R"], cfg1["V"], Fref, osys.w, 0.5, rho=np.stack(osys.rho))
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert np.allclose(coef.cpu().numpy(), want["a"], rtol=tol * 10, atol=1e-12)
+    assert abs(srel.item() - want["s_rel"]) < tol * 10
+    assert rel_err(rho.double().cpu().numpy(), want["rho_new"]) < tol
+
+
+def test_apply_singular_flag_and_nonfinite(lib, cfg1):
+    ctx, V, _, _ = _run([cfg1], "fp64")
+    Fh = oracle.gateaux(oracle_system(cfg1), cfg1["V"])["F"]
+    Fh[3] = Fh[1]
+    Fd = torch.as_tensor(Fh, dtype=torch.float64, device="cuda")
+    R = torch.as_tensor(cfg1["R"], dtype=torch.float64, device="cuda")
+    coef, srel = ctx.apply(0, R, V[0], Fd, 0.0)
+    assert ctx.status() == 6          # LRDM_ERR_SINGULAR
+    w = float(np.prod(cfg1["h"]))
+    a_ref = np.linalg.lstsq(np.sqrt(w) * Fh.reshape(4, -1).T, np.sqrt(w) * cfg1["R"].ravel(), rcond=1e-10)[0]
+    assert np.allclose(coef.cpu().numpy(), a_ref, rtol=1e-8)
+    R[0, 5] = float("nan")
+    ctx.apply(0, R, V[0], Fd, 0.0)
+    assert ctx.status() == 8          # LRDM_ERR_NONFINITE
+    assert ctx.status() == 0          # cleared
+
+
+def test_argument_errors(lib, cfg1):
+    from paper_2211_07894_gb300 import LrdmError
+    from gpu_helpers import directions, make_context
+    ctx, _ = make_context([cfg1], "fp64", torch.float64)
+    V = directions(cfg1, torch.float64)
+    big = torch.zeros((5,) + tuple(V.shape[1:]), dtype=torch.float64, device="cuda")
+    with pytest.raises(LrdmError) as e:
+        ctx.gateaux([big])
+    assert e.value.code == 1
+    bad = dict(cfg1)
+    bad["n_electrons"] = 1000.0
+    with pytest.raises(LrdmError) as e:
+        make_context([bad], "fp64", torch.float64)
+    assert e.value.code == 5
+    # K = 0 is a no-op
+    F, dmu = ctx.gateaux([V[:0]])
+    assert F[0].shape[0] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_backward_vs_oracle(lib, prec):
+    cfg = _ragged(cfg_id=22, n=(12, 10, 14), ns=70, K=3, ne=50)
+    io = IO[prec]
+    ctx, V, F, dmu = _run([cfg], prec)
+    rng = workloads.rng_for(22, 9)
+    fbar = rng.standard_normal(cfg["V"].shape)
+    vbar, eb, ob = ctx.backward([torch.as_tensor(fbar, dtype=io, device="cuda")])
+    torch.cuda.synchronize()
+    osys = oracle_system(cfg)
+    ref = oracle.backward(osys, fbar, V=cfg["V"])
+    tol = TOL[prec]
+    assert per_direction_rel_err(vbar[0].double().cpu().numpy(), ref["vbar"]) < tol
+    assert rel_err(eb[0].cpu().numpy(), ref["eps_bar"][0]) < tol * 10
+    assert rel_err(ob[0].cpu().numpy(), ref["occ_bar"][0]) < tol * 10
+
+
+def test_autograd_function_dot_product(lib, cfg1):
+    from gpu_helpers import directions, make_context
+    from paper_2211_07894_gb300 import gateaux_function
+    ctx, _ = make_context([cfg1], "fp64", torch.float64)
+    V = directions(cfg1, torch.float64).requires_grad_(True)
+    fbar = torch.randn_like(V)
+    F = gateaux_function().apply(ctx, V)
+    (F * fbar).sum().backward()
+    lhs = float((fbar * F.detach()).sum())
+    rhs = float((V.grad * V.detach()).sum())
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)

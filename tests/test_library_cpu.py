@@ -1,0 +1,89 @@
+"""Host-side checks that need no GPU: the C-ABI library builds, loads, and
+exports every function that include/*.h declares; option defaults; the
+input generators' recipes."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            text = open(os.path.join(inc, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lrdm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2211_07894_gb300 import build, binding
+    build.build()
+    return binding.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "lrdm_create" in names and "lrdm_gateaux_batch" in names
+    assert "lrdm_apply" in names and "lrdm_backward" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_options(lib):
+    from paper_2211_07894_gb300 import binding
+    o = binding.lrdm_default_options()
+    assert o.prec == binding.PRECISIONS["bf16x3"] and o.io_dtype == binding.DTYPE_F32
+    assert o.k_max == 16 and o.pinv_rcond == 1e-12 and o.degen_tol == 1e-5
+    for code in range(10):
+        assert binding.lrdm_status_string(code)
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib):
+    """Argument validation runs before any device call."""
+    from paper_2211_07894_gb300 import binding
+    o = binding.lrdm_default_options()
+    code, h = binding.lrdm_create([], o)
+    assert code == 1 and not h.value
+    s = binding.lrdm_system()
+    s.nspin = 3
+    code, h = binding.lrdm_create([s], o)
+    assert code != 0 and not h.value
+    o.k_max = 65
+    s.nspin = 1
+    code, _ = binding.lrdm_create([s], o)
+    assert code != 0
+
+
+def test_directions_are_unit_norm_and_zero_mean():
+    n, h = (8, 6, 10), (0.5, 0.4, 0.3)
+    V = workloads.smooth_directions(n, h, 3, 2, workloads.rng_for(0, 0))
+    w = float(np.prod(h))
+    for k in range(3):
+        assert abs(w * np.sum(V[k] ** 2) - 1.0) < 1e-12
+        assert np.all(np.abs(V[k].sum(axis=1)) < 1e-10)
+
+
+def test_random_subspace_is_w_orthonormal():
+    n, h = (8, 8, 8), (0.5, 0.5, 0.5)
+    psi = workloads.random_subspace(n, h, 30, workloads.rng_for(0, 1))
+    w = float(np.prod(h))
+    assert np.max(np.abs(w * psi.T @ psi - np.eye(30))) < 1e-13
+
+
+def test_degenerate_pairs_recipe():
+    d = workloads.config4(scale=8)
+    eps = d["eps"][0]
+    gaps = np.diff(eps)
+    for i in d["pairs"]:
+        assert abs(gaps[i] - 1e-9) < 1e-15
+    assert np.all(gaps > 0)
