@@ -168,6 +168,18 @@ lrdm_status lrdm_get_mu(lrdm_ctx* ctx, int sys, double* mu_host);
  * into out ([N_g], io dtype, device).  Asynchronous. */
 lrdm_status lrdm_get_density(lrdm_ctx* ctx, int sys, int spin, void* out, void* stream);
 
+/* Benchmark instrumentation.  While enabled, each contraction launch is
+ * bracketed by CUDA events recorded on its launching stream (at most 4096
+ * launches are kept), and the library counts the kernels it launches itself
+ * (cuFFT's own kernels are not counted).  lrdm_profile_read synchronises
+ * those events and returns the summed device times (ms) and counts of the
+ * projection GEMM (X_k) and the response GEMM (drho_k) launches, and the total
+ * number of library kernel launches; reset != 0 clears the record. */
+lrdm_status lrdm_profile_enable(lrdm_ctx* ctx, int on);
+lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_launches,
+                              double* gemm2_ms, long long* gemm2_launches,
+                              long long* kernel_launches, int reset);
+
 /* Frees the context (synchronises its device work first). NULL is ignored. */
 void lrdm_destroy(lrdm_ctx* ctx);
 

@@ -19,6 +19,8 @@ from .binding import (  # noqa: F401
     lrdm_gateaux_batch,
     lrdm_get_density,
     lrdm_get_mu,
+    lrdm_profile_enable,
+    lrdm_profile_read,
     lrdm_status_query,
     lrdm_status_string,
 )

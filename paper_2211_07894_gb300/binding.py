@@ -50,7 +50,7 @@ _lib = None
 
 EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_apply",
            "lrdm_backward", "lrdm_status_query", "lrdm_get_mu", "lrdm_get_density",
-           "lrdm_destroy", "lrdm_status_string"]
+           "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string"]
 
 
 def load(path: Optional[str] = None):
@@ -82,6 +82,12 @@ def load(path: Optional[str] = None):
     lib.lrdm_get_mu.restype = c_int
     lib.lrdm_get_density.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p]
     lib.lrdm_get_density.restype = c_int
+    lib.lrdm_profile_enable.argtypes = [c_void_p, c_int]
+    lib.lrdm_profile_enable.restype = c_int
+    lib.lrdm_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(ctypes.c_longlong),
+                                      POINTER(c_double), POINTER(ctypes.c_longlong),
+                                      POINTER(ctypes.c_longlong), c_int]
+    lib.lrdm_profile_read.restype = c_int
     lib.lrdm_destroy.argtypes = [c_void_p]
     lib.lrdm_destroy.restype = None
     lib.lrdm_status_string.argtypes = [c_int]
@@ -153,6 +159,20 @@ def lrdm_get_mu(ctx, sys: int) -> float:
 
 def lrdm_get_density(ctx, sys, spin, out_ptr, stream: int = 0) -> int:
     return load().lrdm_get_density(ctx, sys, spin, c_void_p(out_ptr), c_void_p(stream))
+
+
+def lrdm_profile_enable(ctx, on: int) -> int:
+    return load().lrdm_profile_enable(ctx, on)
+
+
+def lrdm_profile_read(ctx, reset: int = 1):
+    t1, t2 = c_double(), c_double()
+    n1, n2, nk = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check("lrdm_profile_read", load().lrdm_profile_read(ctx, ctypes.byref(t1), ctypes.byref(n1),
+                                                         ctypes.byref(t2), ctypes.byref(n2),
+                                                         ctypes.byref(nk), reset))
+    return dict(gemm1_ms=t1.value, gemm1_launches=n1.value, gemm2_ms=t2.value,
+                gemm2_launches=n2.value, kernel_launches=nk.value)
 
 
 def lrdm_destroy(ctx) -> None:
@@ -314,6 +334,12 @@ class Context:
                              self._stream(stream))
         _check("lrdm_backward", code)
         return vbar, eb, ob
+
+    def profile(self, on=True):
+        _check("lrdm_profile_enable", lrdm_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        return lrdm_profile_read(self.handle, 1 if reset else 0)
 
     def status(self, synchronize=True):
         return lrdm_status_query(self.handle, 1 if synchronize else 0)

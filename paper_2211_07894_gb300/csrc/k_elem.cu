@@ -219,7 +219,9 @@ __global__ void k_loewner_scale(const void* __restrict__ X, int acc64, int nspli
     if (layout == 0) {
       st_c(out, acc64, e, val);
     } else if (layout == 1) {
-      static_cast<float*>(out)[e] = (float)val;
+      uint32_t t;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"((float)val));
+      static_cast<float*>(out)[e] = __uint_as_float(t);
     } else {
       float v32 = (float)val;
       __nv_bfloat16 hi = __float2bfloat16_rn(v32);

@@ -7,6 +7,13 @@
 namespace lrdm {
 namespace {
 
+// round-to-nearest into the TF32 format (the tensor cores read 10 mantissa bits)
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ double load_io(const void* p, int io_dtype, long long i) {
   return io_dtype == LRDM_DTYPE_F64 ? static_cast<const double*>(p)[i]
                                     : (double)static_cast<const float*>(p)[i];
@@ -46,7 +53,7 @@ __global__ void k_copy_tc(const void* __restrict__ src, int io_dtype, int ld, lo
     tile[yy][tx] = x;
     if (r < Ng_pad && i < ns_pad) {
       long long o = r * ns_pad + i;
-      if (R32) R32[o] = x;
+      if (R32) R32[o] = to_tf32(x);
       if (Rhi) {
         __nv_bfloat16 hi = __float2bfloat16_rn(x);
         Rhi[o] = hi;
@@ -61,7 +68,7 @@ __global__ void k_copy_tc(const void* __restrict__ src, int io_dtype, int ld, lo
     if (i < ns_pad && r < Ng_pad) {
       float x = tile[tx][yy];
       long long o = (long long)i * Ng_pad + r;
-      if (T32) T32[o] = x;
+      if (T32) T32[o] = to_tf32(x);
       if (Thi) {
         __nv_bfloat16 hi = __float2bfloat16_rn(x);
         Thi[o] = hi;

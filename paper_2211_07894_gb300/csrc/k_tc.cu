@@ -1,18 +1,682 @@
-// Tensor-core (tcgen05) forms of the two contractions.
+// Tensor-core (tcgen05) forms of the two contractions on sm_103a.
+//
+// GEMM1  X_k[i, j] = sum_r (a_k[r] Psi[r, i]) Psi[r, j]     (H-breve', §II.C)
+//        tile 128 (i) x 256 (j), i-blocks with i0 < j0 + 256 only (upper part);
+//        the whole grid reduction runs inside one tile; the a_k weighting is
+//        applied to the A tile in shared memory between its TMA load and the
+//        MMAs (one Psi^T tile load per r-chunk, scaled per direction).
+// GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
+//        tile 128 (r) x 256 (j); for each j-block the i-reduction stops at the
+//        block's end (X'' is zero below the diagonal); two TMEM accumulators so
+//        the row-dot epilogue of one j-block overlaps the MMAs of the next.
+//        Psi X'' only ever lives in tensor memory.
+//
+// Both: A and B K-major in 128-byte-swizzled shared memory, loaded by TMA;
+// one thread issues tcgen05.mma, accumulators (FP32) in tensor memory, read
+// back with tcgen05.ld.  Precisions: split BF16x3 (a = a_hi + a_lo, three
+// bf16 products a_hi b_hi + a_hi b_lo + a_lo b_hi) and TF32.  Persistent
+// grids (one CTA per SM) over work items; every wait is bounded (4 s), after
+// which the kernel raises the timeout status bit, drains its own copies and
+// MMAs, frees its tensor memory and returns.
 #include "lrdm_internal.h"
+#include "tc_ptx.cuh"
+
+#include <cudaTypedefs.h>
 
 namespace lrdm {
+namespace {
 
-bool tc_supported() { return false; }
+constexpr int BM = 128;                 // MMA M = tensor-memory lanes
+constexpr int BN = 256;                 // MMA N
+constexpr int ROWB = 128;               // bytes per swizzled smem row
+constexpr int TILE_A = BM * ROWB;       // 16 KB per operand part
+constexpr int TILE_B = BN * ROWB;       // 32 KB per operand part
+constexpr int NTHREADS = 192;           // warp 0 TMA, warp 1 MMA, warps 2-5 math / epilogue
+constexpr uint64_t WAIT_NS = 4000000000ull;
 
-cudaError_t launch_gemm1_tc(int, const Channel&, const SysState&, int, int, const float*, void*,
-                            int*, cudaStream_t) {
-  return cudaErrorNotSupported;
+template <int PREC>
+struct Tr;
+template <>
+struct Tr<LRDM_BF16X3> {
+  static constexpr int BK = 64;          // bf16 per 128-byte row
+  static constexpr int PARTS = 2;        // hi, lo
+  static constexpr int STAGES = 2;
+  static constexpr uint32_t IDESC = ptx::idesc_make(1, BM, BN);
+};
+template <>
+struct Tr<LRDM_TF32> {
+  static constexpr int BK = 32;          // fp32 per 128-byte row
+  static constexpr int PARTS = 1;
+  static constexpr int STAGES = 4;
+  static constexpr uint32_t IDESC = ptx::idesc_make(2, BM, BN);
+};
+
+template <int PREC>
+__host__ __device__ constexpr int stage_bytes() { return Tr<PREC>::PARTS * (TILE_A + TILE_B); }
+template <int PREC>
+__host__ __device__ constexpr int smem_bytes() { return Tr<PREC>::STAGES * stage_bytes<PREC>() + 1024 + 256; }
+
+struct Bars {
+  uint64_t* full;      // [STAGES] TMA landed
+  uint64_t* empty;     // [STAGES] MMAs done with the stage
+  uint64_t* ready;     // [STAGES] A tile scaled (GEMM1 only)
+  uint64_t* acc_full;  // [2]
+  uint64_t* acc_empty; // [2]
+  uint64_t* drain;     // [1]
+  uint32_t* tmem_slot;
+  volatile int* abort;
+};
+
+template <int STAGES>
+__device__ __forceinline__ Bars carve(uint8_t* tail) {
+  Bars b;
+  uint64_t* p = reinterpret_cast<uint64_t*>(tail);
+  b.full = p;
+  b.empty = p + STAGES;
+  b.ready = p + 2 * STAGES;
+  b.acc_full = p + 3 * STAGES;
+  b.acc_empty = p + 3 * STAGES + 2;
+  b.drain = p + 3 * STAGES + 4;
+  b.tmem_slot = reinterpret_cast<uint32_t*>(p + 3 * STAGES + 5);
+  b.abort = reinterpret_cast<volatile int*>(p + 3 * STAGES + 6);
+  return b;
 }
 
-cudaError_t launch_gemm2_tc(int, const Channel&, const SysState&, int, double, const void*,
-                            long long, void*, long long, int, int, int*, cudaStream_t) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ bool wait1(uint64_t* bar, uint32_t parity, const Bars& B, int* status) {
+  return ptx::mbar_wait(bar, parity, B.abort, status, WAIT_NS, STATUS_TIMEOUT);
+}
+// Warp-uniform bounded wait: every lane polls, the decision is unanimous.
+__device__ __forceinline__ bool waitw(uint64_t* bar, uint32_t parity, const Bars& B, int* status) {
+  bool ok = ptx::mbar_wait(bar, parity, B.abort, status, WAIT_NS, STATUS_TIMEOUT);
+  return __all_sync(0xffffffffu, ok);
+}
+// Wait that ignores the abort flag (used to drain in-flight work on exit).
+__device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity) {
+  volatile int never = 0;
+  ptx::mbar_wait(bar, parity, &never, nullptr, 200000000ull, 0);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int PREC>
+__device__ __forceinline__ void issue_stage_mmas(uint32_t d, uint32_t sa, uint32_t first) {
+  constexpr int PARTS = Tr<PREC>::PARTS;
+  const uint32_t a0 = sa, a1 = sa + TILE_A;
+  const uint32_t b0 = sa + PARTS * TILE_A, b1 = b0 + TILE_B;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {          // 4 x 32-byte K steps per 128-byte row
+    const uint32_t off = kk * 32;
+    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+    if (PREC == LRDM_BF16X3) {
+      ptx::mma_f16(d, ptx::desc_k_sw128(a0 + off), ptx::desc_k_sw128(b0 + off), Tr<PREC>::IDESC, acc);
+      ptx::mma_f16(d, ptx::desc_k_sw128(a0 + off), ptx::desc_k_sw128(b1 + off), Tr<PREC>::IDESC, 1);
+      ptx::mma_f16(d, ptx::desc_k_sw128(a1 + off), ptx::desc_k_sw128(b0 + off), Tr<PREC>::IDESC, 1);
+    } else {
+      ptx::mma_tf32(d, ptx::desc_k_sw128(a0 + off), ptx::desc_k_sw128(b0 + off), Tr<PREC>::IDESC, acc);
+    }
+  }
+}
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// ===========================================================================
+// GEMM2: response contraction with the row-dot epilogue
+// ===========================================================================
+
+struct G2Params {
+  int K, ns_pad, nR, NJ;
+  long long Ng;
+  const void* psi0;        // epilogue Psi rows: bf16 hi (BF16X3) or fp32 (TF32), [Ng_pad][ns_pad]
+  const void* psi1;        // bf16 lo (BF16X3)
+  double factor;
+  const void* v;
+  long long v_stride;
+  void* out;
+  long long out_stride;
+  int out_io, out_is_io;
+  int* status;
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm2_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+               const G2Params P) {
+  using T = Tr<PREC>;
+  constexpr int STAGES = T::STAGES, PARTS = T::PARTS, BK = T::BK;
+  constexpr int SB = stage_bytes<PREC>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const Bars B = carve<STAGES>(smem + STAGES * SB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = P.K * P.nR;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&B.full[s], 1);
+      ptx::mbar_init(&B.empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      ptx::mbar_init(&B.acc_full[a], 1);
+      ptx::mbar_init(&B.acc_empty[a], 4);
+    }
+    ptx::mbar_init(B.drain, 1);
+    *B.abort = 0;
+    ptx::fence_barrier_init();
+    ptx::fence_proxy_async_smem();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(B.tmem_slot, 2 * BN);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *B.tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    ptx::prefetch_tmap(&mA0);
+    ptx::prefetch_tmap(&mB0);
+    int s = 0;
+    uint32_t ph = 0;
+    int pending[STAGES];
+    for (int i = 0; i < STAGES; ++i) pending[i] = -1;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+      const int k = item / P.nR, R = item - k * P.nR;
+      bool ok = true;
+      for (int J = 0; J < P.NJ && ok; ++J) {
+        const int nch = min((J + 1) * BN, P.ns_pad) / BK;
+        for (int ic = 0; ic < nch; ++ic) {
+          if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
+          uint8_t* st = smem + s * SB;
+          ptx::mbar_arrive_expect_tx(&B.full[s], SB);
+          ptx::tma_load_2d(st, &mA0, &B.full[s], ic * BK, R * BM);
+          if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, &mA1, &B.full[s], ic * BK, R * BM);
+          ptx::tma_load_3d(st + PARTS * TILE_A, &mB0, &B.full[s], ic * BK, J * BN, k);
+          if (PARTS == 2)
+            ptx::tma_load_3d(st + PARTS * TILE_A + TILE_B, &mB1, &B.full[s], ic * BK, J * BN, k);
+          pending[s] = (int)ph;
+          if (++s == STAGES) { s = 0; ph ^= 1; }
+        }
+      }
+      if (!ok) break;
+    }
+    for (int i = 0; i < STAGES; ++i)
+      if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int s = 0, a = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      for (int J = 0; J < P.NJ && ok; ++J) {
+        if (!wait1(&B.acc_empty[a], aph ^ 1, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * BN);
+        const int nch = min((J + 1) * BN, P.ns_pad) / BK;
+        for (int ic = 0; ic < nch; ++ic) {
+          if (!wait1(&B.full[s], ph, B, P.status)) { ok = false; break; }
+          ptx::tc_fence_after();
+          issue_stage_mmas<PREC>(d, ptx::smem_u32(smem + s * SB), ic == 0);
+          ptx::mma_commit(&B.empty[s]);
+          if (++s == STAGES) { s = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&B.acc_full[a]);
+        if (++a == 2) { a = 0; aph ^= 1; }
+      }
+    }
+    ptx::mma_commit(B.drain);
+    wait_drain(B.drain, 0);
+  } else if (warp >= 2) {
+    // ---------------- row-dot epilogue (TMEM lane quarter = warp % 4) ----------------
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int a = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const int k = item / P.nR, R = item - k * P.nR;
+      const long long r = (long long)R * BM + row;
+      double acc_row = 0.0;
+      for (int J = 0; J < P.NJ; ++J) {
+        if (!waitw(&B.acc_full[a], aph, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        float part = 0.f;
+        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          ptx::tmem_ld32(tb + c * 32, v);
+          const int j0 = J * BN + c * 32;
+          if (r < P.Ng && j0 < P.ns_pad) {
+            const long long o = r * P.ns_pad + j0;
+            if (PREC == LRDM_BF16X3) {
+              const uint4* ph = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(P.psi0) + o);
+              const uint4* pl = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(P.psi1) + o);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const uint4 h = __ldg(ph + u), l = __ldg(pl + u);
+                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  part += v[u * 8 + 2 * e] * (bf_lo(hw[e]) + bf_lo(lw[e]));
+                  part += v[u * 8 + 2 * e + 1] * (bf_hi(hw[e]) + bf_hi(lw[e]));
+                }
+              }
+            } else {
+              const float4* pf = reinterpret_cast<const float4*>(static_cast<const float*>(P.psi0) + o);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const float4 x = __ldg(pf + u);
+                part += v[u * 4] * x.x + v[u * 4 + 1] * x.y + v[u * 4 + 2] * x.z + v[u * 4 + 3] * x.w;
+              }
+            }
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&B.acc_empty[a]);
+        acc_row += (double)part;
+        if (++a == 2) { a = 0; aph ^= 1; }
+      }
+      if (!ok) break;
+      if (r < P.Ng) {
+        const double d = P.factor * acc_row;
+        const long long o = (long long)k * P.out_stride + r;
+        if (P.out_is_io) {
+          const long long ov = (long long)k * P.v_stride + r;
+          if (P.out_io == LRDM_DTYPE_F64)
+            static_cast<double*>(P.out)[o] = d - static_cast<const double*>(P.v)[ov];
+          else
+            static_cast<float*>(P.out)[o] = (float)(d - (double)static_cast<const float*>(P.v)[ov]);
+        } else {
+          static_cast<float*>(P.out)[o] = (float)d;
+        }
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
+// ===========================================================================
+// GEMM1: projection with the per-direction weights applied in shared memory
+// ===========================================================================
+
+struct G1Params {
+  int K, ns, ns_pad, nI, NJ, items_per_k, nch;
+  const float* a;          // weights of this channel, direction stride a_stride
+  long long a_stride;
+  float* X;                // [K][ns_pad][ns_pad]
+  int* status;
+};
+
+__device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k, int& I, int& J) {
+  k = item / P.items_per_k;
+  int idx = item - k * P.items_per_k;
+  int j = 0;
+  for (;;) {
+    const int cnt = min(2 * (j + 1), P.nI);     // i-blocks of 128 below the end of j-block j
+    if (idx < cnt) break;
+    idx -= cnt;
+    ++j;
+  }
+  J = j;
+  I = idx;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm1_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+               const G1Params P) {
+  using T = Tr<PREC>;
+  constexpr int STAGES = T::STAGES, PARTS = T::PARTS, BK = T::BK;
+  constexpr int SB = stage_bytes<PREC>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const Bars B = carve<STAGES>(smem + STAGES * SB);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = P.K * P.items_per_k;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&B.full[s], 1);
+      ptx::mbar_init(&B.empty[s], 1);
+      ptx::mbar_init(&B.ready[s], 4);
+    }
+    ptx::mbar_init(&B.acc_full[0], 1);
+    ptx::mbar_init(&B.acc_empty[0], 4);
+    ptx::mbar_init(B.drain, 1);
+    *B.abort = 0;
+    ptx::fence_barrier_init();
+    ptx::fence_proxy_async_smem();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(B.tmem_slot, BN);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *B.tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    ptx::prefetch_tmap(&mA0);
+    ptx::prefetch_tmap(&mB0);
+    int s = 0;
+    uint32_t ph = 0;
+    int pending[STAGES];
+    for (int i = 0; i < STAGES; ++i) pending[i] = -1;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      int k, I, J;
+      g1_item(P, item, k, I, J);
+      for (int rc = 0; rc < P.nch; ++rc) {
+        if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
+        uint8_t* st = smem + s * SB;
+        ptx::mbar_arrive_expect_tx(&B.full[s], SB);
+        ptx::tma_load_2d(st, &mA0, &B.full[s], rc * BK, I * BM);
+        if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, &mA1, &B.full[s], rc * BK, I * BM);
+        ptx::tma_load_2d(st + PARTS * TILE_A, &mB0, &B.full[s], rc * BK, J * BN);
+        if (PARTS == 2) ptx::tma_load_2d(st + PARTS * TILE_A + TILE_B, &mB1, &B.full[s], rc * BK, J * BN);
+        pending[s] = (int)ph;
+        if (++s == STAGES) { s = 0; ph ^= 1; }
+      }
+    }
+    for (int i = 0; i < STAGES; ++i)
+      if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int s = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      if (!wait1(&B.acc_empty[0], aph ^ 1, B, P.status)) break;
+      ptx::tc_fence_after();
+      for (int rc = 0; rc < P.nch; ++rc) {
+        if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        issue_stage_mmas<PREC>(tmem, ptx::smem_u32(smem + s * SB), rc == 0);
+        ptx::mma_commit(&B.empty[s]);
+        if (++s == STAGES) { s = 0; ph ^= 1; }
+      }
+      if (!ok) break;
+      ptx::mma_commit(&B.acc_full[0]);
+      aph ^= 1;
+    }
+    ptx::mma_commit(B.drain);
+    wait_drain(B.drain, 0);
+  } else if (warp >= 2) {
+    // -------- weighting of the A tile (in place), then the tile epilogue --------
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int s = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      int k, I, J;
+      g1_item(P, item, k, I, J);
+      const float* ak = P.a + (long long)k * P.a_stride;
+      for (int rc = 0; rc < P.nch; ++rc) {
+        if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
+        uint8_t* st = smem + s * SB;
+        uint8_t* r0 = st + row * ROWB;
+        const float* ar = ak + (long long)rc * BK;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int p = (it + row) & 7;         // physical 16-byte chunk of this row
+          const int c = p ^ (row & 7);          // its logical chunk under the 128B swizzle
+          if (PREC == LRDM_BF16X3) {
+            uint4* hp = reinterpret_cast<uint4*>(r0 + p * 16);
+            uint4* lp = reinterpret_cast<uint4*>(r0 + TILE_A + p * 16);
+            const uint4 h = *hp, l = *lp;
+            const float4 s0 = __ldg(reinterpret_cast<const float4*>(ar + c * 8));
+            const float4 s1 = __ldg(reinterpret_cast<const float4*>(ar + c * 8 + 4));
+            const float sc[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+            const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+            uint32_t oh[4], ol[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float x0 = (bf_lo(hw[e]) + bf_lo(lw[e])) * sc[2 * e];
+              const float x1 = (bf_hi(hw[e]) + bf_hi(lw[e])) * sc[2 * e + 1];
+              const __nv_bfloat162 hi2 = __floats2bfloat162_rn(x0, x1);
+              const float2 hf = __bfloat1622float2(hi2);
+              const __nv_bfloat162 lo2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+              oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
+              ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
+            }
+            *hp = make_uint4(oh[0], oh[1], oh[2], oh[3]);
+            *lp = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+          } else {
+            float4* xp = reinterpret_cast<float4*>(r0 + p * 16);
+            const float4 x = *xp;
+            const float4 sc = __ldg(reinterpret_cast<const float4*>(ar + c * 4));
+            *xp = make_float4(tf32_round(x.x * sc.x), tf32_round(x.y * sc.y),
+                              tf32_round(x.z * sc.z), tf32_round(x.w * sc.w));
+          }
+        }
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&B.ready[s]);
+        if (++s == STAGES) { s = 0; ph ^= 1; }
+      }
+      if (!ok) break;
+      // epilogue: X[i][j] and X[j][i] for i <= j of this tile
+      if (!waitw(&B.acc_full[0], aph, B, P.status)) break;
+      ptx::tc_fence_after();
+      const int i = I * BM + row;
+      float* Xk = P.X + (long long)k * P.ns_pad * P.ns_pad;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+        const int j0 = J * BN + c * 32;
+        if (i < P.ns) {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int j = j0 + e;
+            if (j >= i && j < P.ns) {
+              Xk[(long long)i * P.ns_pad + j] = v[e];
+              Xk[(long long)j * P.ns_pad + i] = v[e];
+            }
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&B.acc_empty[0]);
+      aph ^= 1;
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, BN);
+  }
+}
+
+// ===========================================================================
+// host side
+// ===========================================================================
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D (rank 2) or 3D map over a row-major array; box inner extent = 128 bytes.
+bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int rank, const uint64_t* dims,
+              const uint64_t* strides_bytes, const uint32_t* box) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gd[3];
+  cuuint64_t gs[2];
+  cuuint32_t bx[3], es[3] = {1, 1, 1};
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bx[i] = box[i];
+  }
+  for (int i = 0; i < rank - 1; ++i) gs[i] = strides_bytes[i];
+  CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  rank, const_cast<void*>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <typename Kern>
+cudaError_t set_smem(Kern k, int bytes, bool& done) {
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int PREC>
+cudaError_t gemm1(const Channel& c, const SysState& S, int s, int K, const float* a, void* Xout,
+                  int* status, cudaStream_t st) {
+  constexpr int BK = Tr<PREC>::BK;
+  const int eb = PREC == LRDM_BF16X3 ? 2 : 4;
+  const void* p0 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_hi : (const void*)c.psiT32;
+  const void* p1 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_lo : (const void*)c.psiT32;
+  CUtensorMap mA0, mA1, mB0, mB1;
+  const uint64_t dims[2] = {(uint64_t)S.Ng_pad, (uint64_t)c.ns_pad};
+  const uint64_t strides[1] = {(uint64_t)S.Ng_pad * eb};
+  const uint32_t boxA[2] = {(uint32_t)BK, (uint32_t)BM}, boxB[2] = {(uint32_t)BK, (uint32_t)BN};
+  if (!make_map(&mA0, p0, eb, 2, dims, strides, boxA) || !make_map(&mA1, p1, eb, 2, dims, strides, boxA) ||
+      !make_map(&mB0, p0, eb, 2, dims, strides, boxB) || !make_map(&mB1, p1, eb, 2, dims, strides, boxB))
+    return cudaErrorInvalidValue;
+  G1Params P;
+  P.K = K;
+  P.ns = c.ns;
+  P.ns_pad = c.ns_pad;
+  P.nI = c.ns_pad / BM;
+  P.NJ = (c.ns_pad + BN - 1) / BN;
+  P.items_per_k = 0;
+  for (int j = 0; j < P.NJ; ++j) P.items_per_k += (2 * (j + 1) < P.nI ? 2 * (j + 1) : P.nI);
+  P.nch = (int)(S.Ng_pad / BK);
+  P.a = a;
+  P.a_stride = (long long)S.nspin * S.Ng_pad;
+  P.X = static_cast<float*>(Xout);
+  P.status = status;
+  static bool attr = false;
+  const int smem = smem_bytes<PREC>();
+  cudaError_t e = set_smem(k_gemm1_tc<PREC>, smem, attr);
+  if (e != cudaSuccess) return e;
+  const int items = K * P.items_per_k;
+  const int grid = items < num_sms() ? items : num_sms();
+  if (grid <= 0) return cudaSuccess;
+  k_gemm1_tc<PREC><<<grid, NTHREADS, smem, st>>>(mA0, mA1, mB0, mB1, P);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t gemm2(const Channel& c, const SysState& S, int K, double factor, const void* v,
+                  long long v_stride, void* out, long long out_stride, int out_io, int out_is_io,
+                  int* status, cudaStream_t st) {
+  constexpr int BK = Tr<PREC>::BK;
+  const int eb = PREC == LRDM_BF16X3 ? 2 : 4;
+  const void* a0 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_hi : (const void*)c.psiR32;
+  const void* a1 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_lo : (const void*)c.psiR32;
+  const void* b0 = c.Xpp;
+  const void* b1 = PREC == LRDM_BF16X3 ? c.Xpp_lo : c.Xpp;
+  CUtensorMap mA0, mA1, mB0, mB1;
+  const uint64_t dA[2] = {(uint64_t)c.ns_pad, (uint64_t)S.Ng_pad};
+  const uint64_t sA[1] = {(uint64_t)c.ns_pad * eb};
+  const uint32_t boxA[2] = {(uint32_t)BK, (uint32_t)BM};
+  const uint64_t dB[3] = {(uint64_t)c.ns_pad, (uint64_t)c.ns_pad, (uint64_t)K};
+  const uint64_t sB[2] = {(uint64_t)c.ns_pad * eb, (uint64_t)c.ns_pad * c.ns_pad * eb};
+  const uint32_t boxB[3] = {(uint32_t)BK, (uint32_t)BN, 1};
+  if (!make_map(&mA0, a0, eb, 2, dA, sA, boxA) || !make_map(&mA1, a1, eb, 2, dA, sA, boxA) ||
+      !make_map(&mB0, b0, eb, 3, dB, sB, boxB) || !make_map(&mB1, b1, eb, 3, dB, sB, boxB))
+    return cudaErrorInvalidValue;
+  G2Params P;
+  P.K = K;
+  P.ns_pad = c.ns_pad;
+  P.nR = (int)(S.Ng_pad / BM);
+  P.NJ = (c.ns_pad + BN - 1) / BN;
+  P.Ng = S.Ng;
+  P.psi0 = a0;
+  P.psi1 = a1;
+  P.factor = factor;
+  P.v = v;
+  P.v_stride = v_stride;
+  P.out = out;
+  P.out_stride = out_stride;
+  P.out_io = out_io;
+  P.out_is_io = out_is_io;
+  P.status = status;
+  static bool attr = false;
+  const int smem = smem_bytes<PREC>();
+  cudaError_t e = set_smem(k_gemm2_tc<PREC>, smem, attr);
+  if (e != cudaSuccess) return e;
+  const int items = K * P.nR;
+  const int grid = items < num_sms() ? items : num_sms();
+  if (grid <= 0) return cudaSuccess;
+  k_gemm2_tc<PREC><<<grid, NTHREADS, smem, st>>>(mA0, mA1, mB0, mB1, P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_gemm1_tc(int prec, const Channel& c, const SysState& S, int s, int K,
+                            const float* a, void* Xout, int* status, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  if (prec == LRDM_BF16X3) return gemm1<LRDM_BF16X3>(c, S, s, K, a, Xout, status, st);
+  return gemm1<LRDM_TF32>(c, S, s, K, a, Xout, status, st);
+}
+
+cudaError_t launch_gemm2_tc(int prec, const Channel& c, const SysState& S, int K, double factor,
+                            const void* v, long long v_stride, void* out, long long out_stride,
+                            int out_io_dtype, int out_is_io, int* status, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  if (prec == LRDM_BF16X3)
+    return gemm2<LRDM_BF16X3>(c, S, K, factor, v, v_stride, out, out_stride, out_io_dtype,
+                              out_is_io, status, st);
+  return gemm2<LRDM_TF32>(c, S, K, factor, v, v_stride, out, out_stride, out_io_dtype, out_is_io,
+                          status, st);
 }
 
 }  // namespace lrdm

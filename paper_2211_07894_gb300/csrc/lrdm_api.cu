@@ -89,6 +89,23 @@ lrdm_status solve_mu_host(const std::vector<std::vector<double>>& eps, double ne
 
 bool is_tc(int prec) { return prec == LRDM_TF32 || prec == LRDM_BF16X3; }
 
+constexpr int PROF_MAX = 4096;
+
+// Records the start event of a timed contraction; returns the pair index or -1.
+int prof_begin(lrdm_ctx* ctx, int kind, cudaStream_t st) {
+  if (!ctx->prof_on || ctx->prof_n >= PROF_MAX) return -1;
+  int i = ctx->prof_n++;
+  ctx->prof_kind[i] = kind;
+  cudaEventRecord(ctx->prof_ev[2 * i], st);
+  return i;
+}
+void prof_end(lrdm_ctx* ctx, int i, cudaStream_t st) {
+  if (i >= 0) cudaEventRecord(ctx->prof_ev[2 * i + 1], st);
+}
+void count(lrdm_ctx* ctx, int n) {
+  if (ctx->prof_on) ctx->launches += n;
+}
+
 lrdm_status validate_system(const lrdm_system& s, const lrdm_options& o) {
   for (int d = 0; d < 3; ++d) {
     if (s.n[d] < 1) return LRDM_ERR_SHAPE;
@@ -272,14 +289,20 @@ lrdm_status gemm1(lrdm_ctx* ctx, SysState& S, int c, int K, void* Xdst, cudaStre
   Channel& ch = S.ch[c];
   const size_t csz = prec == LRDM_FP64 ? 8 : 4;
   const char* a = static_cast<const char*>(S.a) + (size_t)c * S.Ng_pad * csz;
+  int pi = prof_begin(ctx, 1, st);
+  count(ctx, 1);
+  cudaError_t e;
   if (is_tc(prec)) {
-    return from_cuda(launch_gemm1_tc(prec, ch, S, c, K, reinterpret_cast<const float*>(a), Xdst,
-                                     ctx->d_status, st));
+    e = launch_gemm1_tc(prec, ch, S, c, K, reinterpret_cast<const float*>(a), Xdst, ctx->d_status,
+                        st);
+  } else {
+    const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
+                                        : static_cast<const void*>(ch.psi32);
+    e = launch_gemm1_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, a, (long long)S.nspin * S.Ng_pad,
+                          K, Xdst, S.nsplit, st);
   }
-  const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
-                                      : static_cast<const void*>(ch.psi32);
-  return from_cuda(launch_gemm1_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, a,
-                                     (long long)S.nspin * S.Ng_pad, K, Xdst, S.nsplit, st));
+  prof_end(ctx, pi, st);
+  return from_cuda(e);
 }
 
 // GEMM2 of channel c: out = factor * diag(Psi X'' Psi^T) (- v)
@@ -288,14 +311,20 @@ lrdm_status gemm2(lrdm_ctx* ctx, SysState& S, int c, int K, double factor, const
                   cudaStream_t st) {
   const int prec = ctx->opt.prec;
   Channel& ch = S.ch[c];
+  int pi = prof_begin(ctx, 2, st);
+  count(ctx, 1);
+  cudaError_t e;
   if (is_tc(prec)) {
-    return from_cuda(launch_gemm2_tc(prec, ch, S, K, factor, v, v_stride, out, out_stride,
-                                     ctx->opt.io_dtype, out_is_io, ctx->d_status, st));
+    e = launch_gemm2_tc(prec, ch, S, K, factor, v, v_stride, out, out_stride, ctx->opt.io_dtype,
+                        out_is_io, ctx->d_status, st);
+  } else {
+    const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
+                                        : static_cast<const void*>(ch.psi32);
+    e = launch_gemm2_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, ch.Xpp, K, factor, v, v_stride,
+                          out, out_stride, ctx->opt.io_dtype, out_is_io, st);
   }
-  const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
-                                      : static_cast<const void*>(ch.psi32);
-  return from_cuda(launch_gemm2_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, ch.Xpp, K, factor, v,
-                                     v_stride, out, out_stride, ctx->opt.io_dtype, out_is_io, st));
+  prof_end(ctx, pi, st);
+  return from_cuda(e);
 }
 
 lrdm_status forward_system(lrdm_ctx* ctx, int s, const void* v, int K, void* f, double* dmu_out,
@@ -310,6 +339,7 @@ lrdm_status forward_system(lrdm_ctx* ctx, int s, const void* v, int K, void* f, 
   LRDM_CK(hartree(ctx, S, K, st));
   LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, K, S.nspin, S.Ng,
                             S.Ng_pad, S.w, S.a, fp64, st));
+  count(ctx, 4 + S.nspin);   // spin sum, symbol, weights, mu', Loewner scale per channel
   for (int c = 0; c < S.nspin; ++c) LRDM_CK(gemm1(ctx, S, c, K, S.ch[c].Xpart, st));
   const void* X[2] = {S.ch[0].Xpart, S.ch[S.nspin - 1].Xpart};
   LRDM_CU(launch_dmu(S, X, K, fp64, S.dmu, dmu_out, ctx->d_status, st));
@@ -336,6 +366,7 @@ void free_ctx(lrdm_ctx* ctx) {
     if (S.plan_r2c) cufftDestroy(S.plan_r2c);
     if (S.plan_c2r) cufftDestroy(S.plan_c2r);
   }
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
   delete[] ctx->sys;
   delete ctx;
@@ -465,6 +496,7 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
   if (!isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
   SysState& S = ctx->sys[sys];
   long long n = (long long)S.nspin * S.Ng;
+  count(ctx, 4);
   return from_cuda(launch_ls(R, v, f, ctx->opt.io_dtype, K, n, S.w, alpha, ctx->opt.pinv_rcond,
                              rho_inout, ctx->ls_coef, coeff_out, s_rel_out, ctx->ls_partial,
                              ctx->ls_scal, ctx->upd_partial, ctx->d_status,
@@ -547,6 +579,44 @@ lrdm_status lrdm_get_density(lrdm_ctx* ctx, int sys, int spin, void* out, void* 
   if (spin < 0 || spin >= S.nspin) return LRDM_ERR_INVALID_ARG;
   return from_cuda(launch_to_io(S.ch[spin].rho, S.Ng, out, ctx->opt.io_dtype,
                                 static_cast<cudaStream_t>(stream)));
+}
+
+lrdm_status lrdm_profile_enable(lrdm_ctx* ctx, int on) {
+  if (!ctx) return LRDM_ERR_INVALID_ARG;
+  if (on && ctx->prof_ev.empty()) {
+    ctx->prof_ev.resize(2 * PROF_MAX);
+    ctx->prof_kind.resize(PROF_MAX);
+    for (auto& e : ctx->prof_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return LRDM_ERR_CUDA;
+  }
+  ctx->prof_on = on != 0;
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_launches,
+                              double* gemm2_ms, long long* gemm2_launches,
+                              long long* kernel_launches, int reset) {
+  if (!ctx) return LRDM_ERR_INVALID_ARG;
+  double t[3] = {0, 0, 0};
+  long long n[3] = {0, 0, 0};
+  for (int i = 0; i < ctx->prof_n; ++i) {
+    if (cudaEventSynchronize(ctx->prof_ev[2 * i + 1]) != cudaSuccess) return LRDM_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]) != cudaSuccess)
+      return LRDM_ERR_CUDA;
+    t[ctx->prof_kind[i]] += ms;
+    n[ctx->prof_kind[i]] += 1;
+  }
+  if (gemm1_ms) *gemm1_ms = t[1];
+  if (gemm1_launches) *gemm1_launches = n[1];
+  if (gemm2_ms) *gemm2_ms = t[2];
+  if (gemm2_launches) *gemm2_launches = n[2];
+  if (kernel_launches) *kernel_launches = ctx->launches;
+  if (reset) {
+    ctx->prof_n = 0;
+    ctx->launches = 0;
+  }
+  return LRDM_OK;
 }
 
 void lrdm_destroy(lrdm_ctx* ctx) { free_ctx(ctx); }

@@ -90,6 +90,12 @@ struct lrdm_ctx {
   double* upd_partial = nullptr;     // [UPD_BLOCKS]
   std::vector<void*> allocs;         // every device allocation, freed by lrdm_destroy
   std::vector<double> inv_trace;     // per system 1 / sum_s sum_i L_ii
+  // profiling (lrdm_profile_enable / lrdm_profile_read)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs: [2 i] start, [2 i + 1] end
+  std::vector<int> prof_kind;        // 1 = GEMM1, 2 = GEMM2 per pair
+  int prof_n = 0;
+  long long launches = 0;            // library kernel launches while profiling
 };
 
 namespace lrdm {
