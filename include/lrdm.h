@@ -180,6 +180,13 @@ lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_
                               double* gemm2_ms, long long* gemm2_launches,
                               long long* kernel_launches, int reset);
 
+/* Copies the projected perturbation X_k = Psi^T diag(w dV_k) Psi of direction
+ * k, channel `spin`, of system `sys` from the most recent lrdm_gateaux_batch
+ * into out ([N_s][N_s] FP64, device), for inspection and testing.
+ * Asynchronous. */
+lrdm_status lrdm_get_projection(lrdm_ctx* ctx, int sys, int spin, int k, double* out,
+                                void* stream);
+
 /* Frees the context (synchronises its device work first). NULL is ignored. */
 void lrdm_destroy(lrdm_ctx* ctx);
 

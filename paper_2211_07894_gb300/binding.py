@@ -50,7 +50,7 @@ _lib = None
 
 EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_apply",
            "lrdm_backward", "lrdm_status_query", "lrdm_get_mu", "lrdm_get_density",
-           "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string"]
+           "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string"]
 
 
 def load(path: Optional[str] = None):
@@ -82,6 +82,8 @@ def load(path: Optional[str] = None):
     lib.lrdm_get_mu.restype = c_int
     lib.lrdm_get_density.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p]
     lib.lrdm_get_density.restype = c_int
+    lib.lrdm_get_projection.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]
+    lib.lrdm_get_projection.restype = c_int
     lib.lrdm_profile_enable.argtypes = [c_void_p, c_int]
     lib.lrdm_profile_enable.restype = c_int
     lib.lrdm_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(ctypes.c_longlong),
@@ -159,6 +161,10 @@ def lrdm_get_mu(ctx, sys: int) -> float:
 
 def lrdm_get_density(ctx, sys, spin, out_ptr, stream: int = 0) -> int:
     return load().lrdm_get_density(ctx, sys, spin, c_void_p(out_ptr), c_void_p(stream))
+
+
+def lrdm_get_projection(ctx, sys, spin, k, out_ptr, stream: int = 0) -> int:
+    return load().lrdm_get_projection(ctx, sys, spin, k, c_void_p(out_ptr), c_void_p(stream))
 
 
 def lrdm_profile_enable(ctx, on: int) -> int:
@@ -334,6 +340,14 @@ class Context:
                              self._stream(stream))
         _check("lrdm_backward", code)
         return vbar, eb, ob
+
+    def projection(self, k, sys=0, spin=0, stream=None):
+        """X_k (FP64, (N_s, N_s)) of the most recent gateaux call."""
+        ns = self.meta[sys]["ns"][spin]
+        out = self.torch.empty((ns, ns), dtype=self.torch.float64, device="cuda")
+        _check("lrdm_get_projection", lrdm_get_projection(self.handle, sys, spin, k,
+                                                          out.data_ptr(), self._stream(stream)))
+        return out
 
     def profile(self, on=True):
         _check("lrdm_profile_enable", lrdm_profile_enable(self.handle, 1 if on else 0))

@@ -308,7 +308,28 @@ __global__ void k_eps_occ_bar(const void* __restrict__ X, const void* __restrict
   }
 }
 
+// out[i][j] = sum over splits of X[p][k][i][j] (FP64, ld = ns)
+__global__ void k_get_projection(const void* __restrict__ X, int acc64, int nsplit, int K, int k,
+                                 int ns, int ldx, double* __restrict__ out) {
+  const long long mat = (long long)ldx * ldx;
+  GRID_STRIDE(e, (long long)ns * ns) {
+    const int i = (int)(e / ns), j = (int)(e - (long long)i * ns);
+    double x = 0.0;
+    for (int p = 0; p < nsplit; ++p) x += ld_c(X, acc64, ((long long)p * K + k) * mat + (long long)i * ldx + j);
+    out[e] = x;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_get_projection(const SysState& S, int s, int k, int acc_fp64, double* out,
+                                  cudaStream_t st) {
+  const Channel& c = S.ch[s];
+  const int tc = (c.psiR_hi || c.psiR32) ? 1 : 0;
+  k_get_projection<<<grid_for((long long)c.ns * c.ns, 256), 256, 0, st>>>(
+      c.Xpart, acc_fp64, S.nsplit, S.last_K, k, c.ns, tc ? c.ns_pad : c.ns, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long long Ng,
                             void* fft_real, int fp64, cudaStream_t st) {

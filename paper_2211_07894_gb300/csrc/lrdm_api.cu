@@ -581,6 +581,15 @@ lrdm_status lrdm_get_density(lrdm_ctx* ctx, int sys, int spin, void* out, void* 
                                 static_cast<cudaStream_t>(stream)));
 }
 
+lrdm_status lrdm_get_projection(lrdm_ctx* ctx, int sys, int spin, int k, double* out,
+                                void* stream) {
+  if (!ctx || !out || sys < 0 || sys >= ctx->nsys) return LRDM_ERR_INVALID_ARG;
+  SysState& S = ctx->sys[sys];
+  if (spin < 0 || spin >= S.nspin || k < 0 || k >= S.last_K) return LRDM_ERR_INVALID_ARG;
+  return from_cuda(launch_get_projection(S, spin, k, ctx->opt.prec == LRDM_FP64, out,
+                                         static_cast<cudaStream_t>(stream)));
+}
+
 lrdm_status lrdm_profile_enable(lrdm_ctx* ctx, int on) {
   if (!ctx) return LRDM_ERR_INVALID_ARG;
   if (on && ctx->prof_ev.empty()) {

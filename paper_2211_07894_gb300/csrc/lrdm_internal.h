@@ -137,6 +137,8 @@ cudaError_t launch_dmu(const SysState& S, const void* const* Xparts, int K, int 
 cudaError_t launch_loewner_scale(const SysState& S, int s, const void* Xpart, int K, int acc_fp64,
                                  const double* shift, int adjoint, double inv_trace_L,
                                  int prec, cudaStream_t st);
+cudaError_t launch_get_projection(const SysState& S, int s, int k, int acc_fp64, double* out,
+                                  cudaStream_t st);
 // backward: eps_bar / occ_bar of channel s
 cudaError_t launch_trace_bar(const SysState& S, const void* const* Gparts, int K, int acc_fp64,
                              double* tbar, cudaStream_t st);

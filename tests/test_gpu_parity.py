@@ -1,8 +1,11 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle,
 element by element on the same seeded inputs.
 
-Tolerances (relative w-norm error per direction): FP64 1e-10; TF32 and
-split-BF16x3 1e-5; FP32 CUDA-core 1e-4 (FP32 accumulation over the grid).
+Tolerances (relative w-norm error per direction): FP64 1e-10; split-BF16x3
+1e-5; FP32 CUDA-core 1e-4 (FP32 accumulation over the grid); TF32 5e-3 (its
+operands carry 10 mantissa bits, unit roundoff 2^-11 = 4.9e-4, and the
+contractions sum ~10^4-10^6 products with cancellation) -- the measured TF32
+error is printed.
 """
 
 import numpy as np
@@ -16,7 +19,11 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 1e-5, "bf16x3": 1e-5}
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 5e-3, "bf16x3": 1e-5}
+# intermediates (X_k, drho_k, mu'_k): split-BF16x3 carries three error terms of
+# up to 2^-16 per product (the two splits and the dropped lo*lo product), so
+# its bound on X is 3 * 2^-16 = 4.6e-5 -> 1e-4; the other precisions as TOL.
+TOL_X = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 5e-3, "bf16x3": 1e-4}
 IO = {"fp64": torch.float64, "fp32": torch.float32, "tf32": torch.float32,
       "bf16x3": torch.float32}
 
@@ -43,6 +50,28 @@ def _run(cfgs, prec, **kw):
     return ctx, V, [f.double().cpu().numpy() for f in F], dmu.cpu().numpy()
 
 
+def _check_dmu(dmu, ref, prec):
+    """mu'_k is a weighted mean of the X_k,ii, so its error is bounded by the
+    error of those entries: |dmu - ref| <= TOL_X * max_i |X_k,ii|."""
+    for k in range(len(dmu)):
+        scale = max(np.max(np.abs(np.diag(X[k]))) for X in ref["X"])
+        assert abs(dmu[k] - ref["dmu"][k]) <= TOL_X[prec] * scale + 1e-300
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
+def test_projection_ragged_tiles(lib, prec):
+    """X_k = Psi^T diag(w dV_k) Psi alone (the first contraction)."""
+    cfg = _ragged()
+    ctx, V, F, dmu = _run([cfg], prec)
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    errs = []
+    for k in range(cfg["V"].shape[0]):
+        X = ctx.projection(k).cpu().numpy()
+        errs.append(rel_err(X, ref["X"][0][k]))
+    print(f"projection {prec}: max rel err {max(errs):.3e}")
+    assert max(errs) < TOL_X[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
 def test_forward_toy16(lib, cfg1, prec):
     ctx, V, F, dmu = _run([cfg1], prec)
@@ -50,7 +79,7 @@ def test_forward_toy16(lib, cfg1, prec):
     err = per_direction_rel_err(F[0], ref["F"])
     print(f"toy16 {prec}: max rel err {err:.3e}")
     assert err < TOL[prec]
-    assert np.allclose(dmu, ref["dmu"], rtol=max(TOL[prec], 1e-12) * 10, atol=1e-14)
+    _check_dmu(dmu, ref, prec)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
@@ -62,7 +91,8 @@ def test_forward_ragged_tiles(lib, prec):
     drho_err = per_direction_rel_err(F[0] + cfg["V"], ref["drho"])
     print(f"ragged {prec}: f err {err:.3e}  drho err {drho_err:.3e}")
     assert err < TOL[prec]
-    assert drho_err < TOL[prec] * 10
+    assert drho_err < TOL_X[prec]
+    _check_dmu(dmu, ref, prec)
 
 
 def test_density_mu_and_given_rho(lib, cfg1):
@@ -92,7 +122,7 @@ def test_spin_pair(lib, prec):
     err = max(rel_err(F[0][k], ref["F"][k]) for k in range(3))
     print(f"spin {prec}: {err:.3e}")
     assert err < TOL[prec]
-    assert np.allclose(dmu, ref["dmu"], rtol=TOL[prec] * 10)
+    _check_dmu(dmu, ref, prec)
 
 
 def test_occupation_mode_near_degenerate(lib):
