@@ -146,6 +146,31 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
                        int K, double alpha, void* rho_inout, double* coeff_out,
                        double* s_rel_out, void* stream);
 
+/* The least-squares step of lrdm_apply without a context and without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc -- code whose device memory is all
+ * owned by another allocator (a framework's caching pool or a fixed arena),
+ * or code on a latency-critical path where cudaMalloc's implicit device
+ * synchronisation is not acceptable.  The caller still passes every input
+ * and output:
+ *   R [n], v [K][n], f [K][n] (io_dtype; n = nspin * N_g, the two channels of
+ *   a spin pair side by side), w the quadrature weight, alpha, pinv_rcond and
+ *   rho_inout / coeff_out / s_rel_out exactly as for lrdm_apply; status_out
+ *   (optional, device int) receives the call's status bits (4 = singular S,
+ *   2 = non-finite input), cleared at the start of every call.
+ * Scratch lives in one file-scope device array of the library (about 370 KB,
+ * held by every GPU that loads the library until the process exits), so
+ * K is limited to 16: larger K returns LRDM_ERR_INVALID_ARG before anything is
+ * enqueued.  The first call on each device looks the array's device address
+ * up (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Asynchronous. */
+lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int io_dtype, int K,
+                              long long n, double w, double alpha, double pinv_rcond,
+                              void* rho_inout, double* coeff_out, double* s_rel_out,
+                              int* status_out, void* stream);
+
 /* Adjoint of the most recent lrdm_gateaux_batch on this context.
  *   f_bar[s]  : [K[s]][nspin][N_g] cotangents of f_out[s] (io dtype)
  *   v_bar[s]  : [K[s]][nspin][N_g] gradients w.r.t. v[s] (io dtype)

@@ -49,6 +49,7 @@ class lrdm_options(ctypes.Structure):
 _lib = None
 
 EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_apply",
+           "lrdm_apply_static",
            "lrdm_backward", "lrdm_status_query", "lrdm_get_mu", "lrdm_get_density",
            "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string"]
 
@@ -73,6 +74,10 @@ def load(path: Optional[str] = None):
     lib.lrdm_apply.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int, c_double,
                                c_void_p, c_void_p, c_void_p, c_void_p]
     lib.lrdm_apply.restype = c_int
+    lib.lrdm_apply_static.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int,
+                                      ctypes.c_longlong, c_double, c_double, c_double, c_void_p,
+                                      c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.lrdm_apply_static.restype = c_int
     lib.lrdm_backward.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_void_p),
                                   POINTER(c_void_p), POINTER(c_void_p), c_void_p]
     lib.lrdm_backward.restype = c_int
@@ -139,6 +144,13 @@ def lrdm_apply(ctx, sys, R, v, f, K, alpha, rho, coeff, s_rel, stream: int = 0) 
     return load().lrdm_apply(ctx, sys, c_void_p(R), c_void_p(v), c_void_p(f), K, alpha,
                              c_void_p(rho or 0), c_void_p(coeff or 0), c_void_p(s_rel or 0),
                              c_void_p(stream))
+
+
+def lrdm_apply_static(R, v, f, io_dtype, K, n, w, alpha, pinv_rcond, rho, coeff, s_rel,
+                      status, stream: int = 0) -> int:
+    return load().lrdm_apply_static(c_void_p(R), c_void_p(v), c_void_p(f), io_dtype, K, n, w,
+                                    alpha, pinv_rcond, c_void_p(rho or 0), c_void_p(coeff or 0),
+                                    c_void_p(s_rel or 0), c_void_p(status or 0), c_void_p(stream))
 
 
 def lrdm_backward(ctx, fbar_ptrs, vbar_ptrs, eps_bar_ptrs=None, occ_bar_ptrs=None,

@@ -290,4 +290,84 @@ cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free form of the least-squares step (lrdm_apply_static).
+//
+// Its scratch -- the per-block partial sums, the coefficients, <R, R> and
+// s_rel, the per-block residual sums and the status word -- lives in one
+// file-scope device array instead of a context's workspaces, so a call needs
+// no lrdm_create and allocates nothing.  The array is sized for at most
+// STATIC_K_MAX directions (about 370 KB) and is held by every GPU that loads
+// this library until the process exits.  All calls share it: the partial sums
+// are fully rewritten by every call and the status word is cleared at its
+// start, but two calls that overlap on the GPU (different streams, or several
+// host threads) race on it.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int STATIC_K_MAX = 16;
+constexpr int STATIC_NVAL = STATIC_K_MAX * (STATIC_K_MAX + 1) / 2 + STATIC_K_MAX + 1;
+constexpr int SC_PARTIAL = 0;                                   // [LS_BLOCKS][STATIC_NVAL]
+constexpr int SC_COEF = SC_PARTIAL + LS_BLOCKS * STATIC_NVAL;   // [STATIC_K_MAX]
+constexpr int SC_SCAL = SC_COEF + STATIC_K_MAX;                 // [4]
+constexpr int SC_UPD = SC_SCAL + 4;                             // [UPD_BLOCKS]
+constexpr int SC_STATUS = SC_UPD + UPD_BLOCKS;                  // one double slot for the int status
+constexpr int SC_TOTAL = SC_STATUS + 1;
+
+static __device__ __align__(256) double g_ls_scratch[SC_TOTAL];
+
+constexpr int MAX_DEVICES = 64;
+double* g_scratch_addr[MAX_DEVICES] = {nullptr};
+
+// Device address of g_ls_scratch on the current device (looked up once per
+// device; the host-side symbol is not a device address).
+cudaError_t static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_ls_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int static_k_max() { return STATIC_K_MAX; }
+
+cudaError_t launch_ls_static(const void* R, const void* v, const void* f, int io_dtype, int K,
+                             long long n, double w, double alpha, double rcond, void* rho_inout,
+                             double* coeff_out, double* s_rel_out, int* status_out,
+                             cudaStream_t st) {
+  double* sc = nullptr;
+  cudaError_t e = static_scratch(&sc);
+  if (e != cudaSuccess) return e;
+  int* status = reinterpret_cast<int*>(sc + SC_STATUS);
+  e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  double* partial = sc + SC_PARTIAL;
+  double* coef = sc + SC_COEF;
+  double* scal = sc + SC_SCAL;
+  double* upd = sc + SC_UPD;
+  k_gram<<<LS_BLOCKS, 256, 0, st>>>(f, R, io_dtype, K, n, partial);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smem = 2 * (size_t)K * (K + 1) * sizeof(double);   // <= 4352 bytes for K <= 16
+  k_ls_solve<<<1, KMAX_LIMIT, smem, st>>>(partial, LS_BLOCKS, K, w, rcond, coef, coeff_out, scal,
+                                          status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_update<<<UPD_BLOCKS, 256, 0, st>>>(v, f, R, io_dtype, K, n, alpha, coef, rho_inout, upd);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_srel<<<1, 256, 0, st>>>(upd, UPD_BLOCKS, w, scal, s_rel_out);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (status_out)
+    e = cudaMemcpyAsync(status_out, status, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  return e;
+}
+
 }  // namespace lrdm

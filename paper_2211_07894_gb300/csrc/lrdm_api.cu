@@ -503,6 +503,19 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
                              static_cast<cudaStream_t>(stream)));
 }
 
+lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int io_dtype, int K,
+                              long long n, double w, double alpha, double pinv_rcond,
+                              void* rho_inout, double* coeff_out, double* s_rel_out,
+                              int* status_out, void* stream) {
+  if (!R || !v || !f) return LRDM_ERR_INVALID_ARG;
+  if (io_dtype != LRDM_DTYPE_F64 && io_dtype != LRDM_DTYPE_F32) return LRDM_ERR_INVALID_ARG;
+  if (K < 1 || K > static_k_max()) return LRDM_ERR_INVALID_ARG;
+  if (n < 1 || !(w > 0.0) || !isfinite(alpha) || !(pinv_rcond >= 0.0)) return LRDM_ERR_INVALID_ARG;
+  return from_cuda(launch_ls_static(R, v, f, io_dtype, K, n, w, alpha, pinv_rcond, rho_inout,
+                                    coeff_out, s_rel_out, status_out,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
 lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
                           double* const* eps_bar, double* const* occ_bar, void* stream) {
   if (!ctx || !f_bar || !v_bar) return LRDM_ERR_INVALID_ARG;

@@ -164,6 +164,13 @@ cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype,
                       double* coef, double* coeff_out, double* s_rel_out, double* partial,
                       double* scal, double* upd_partial, int* status, cudaStream_t st);
 
+// allocation-free least-squares step (k_ls.cu, static device scratch)
+int static_k_max();
+cudaError_t launch_ls_static(const void* R, const void* v, const void* f, int io_dtype, int K,
+                             long long n, double w, double alpha, double rcond, void* rho_inout,
+                             double* coeff_out, double* s_rel_out, int* status_out,
+                             cudaStream_t st);
+
 // ---------------- tensor-core GEMMs (k_tc.cu) ----------------
 cudaError_t launch_gemm1_tc(int prec, const Channel& c, const SysState& S, int s, int K,
                             const float* a, void* Xout, int* status, cudaStream_t st);
