@@ -33,9 +33,9 @@ __global__ void k_copy_rowmajor(const void* __restrict__ src, int io_dtype, int 
   }
 }
 
-// Padded row-major [Ng_pad][ns_pad] and transposed [ns_pad][Ng_pad] copies for
-// the tensor-core paths; split into bf16 hi/lo (x = hi + lo, lo = bf16(x - hi))
-// or kept as fp32.  Tiled transpose through shared memory.
+// Padded row-major [Ng_pad][ns_pad] and transposed (tile-major, see below)
+// copies for the tensor-core paths; split into bf16 hi/lo (x = hi + lo,
+// lo = bf16(x - hi)) or rounded to TF32.  Tiled transpose through shared memory.
 __global__ void k_copy_tc(const void* __restrict__ src, int io_dtype, int ld, long long Ng, int ns,
                           long long Ng_pad, int ns_pad, float* __restrict__ R32,
                           float* __restrict__ T32, __nv_bfloat16* __restrict__ Rhi,
@@ -62,12 +62,16 @@ __global__ void k_copy_tc(const void* __restrict__ src, int io_dtype, int ld, lo
     }
   }
   __syncthreads();
+  // transposed copies are tile-major: [i / 128][r / RB][i % 128][r % RB] with
+  // RB = 64 bytes of the element type, so that one (128 states x 64 bytes)
+  // tensor-core operand tile is a contiguous 8 KB block
   for (int yy = ty; yy < 32; yy += 8) {
     int i = i0 + yy;
     long long r = r0 + tx;
     if (i < ns_pad && r < Ng_pad) {
       float x = tile[tx][yy];
-      long long o = (long long)i * Ng_pad + r;
+      const int RB = T32 ? 16 : 32;
+      long long o = (((long long)(i >> 7) * (Ng_pad / RB) + r / RB) * 128 + (i & 127)) * RB + r % RB;
       if (T32) T32[o] = to_tf32(x);
       if (Thi) {
         __nv_bfloat16 hi = __float2bfloat16_rn(x);

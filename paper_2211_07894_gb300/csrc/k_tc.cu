@@ -4,14 +4,14 @@
 //        tile 128 (i) x 256 (j), i-blocks with i0 < j0 + 256 only (upper part);
 //        the whole grid reduction runs inside one tile; the a_k weighting is
 //        applied to the A tile in shared memory between its TMA load and the
-//        MMAs (one Psi^T tile load per r-chunk, scaled per direction).
+//        MMAs (the weights chunk arrives with the tiles by a bulk copy).
 // GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
 //        tile 128 (r) x 256 (j); for each j-block the i-reduction stops at the
 //        block's end (X'' is zero below the diagonal); two TMEM accumulators so
 //        the row-dot epilogue of one j-block overlaps the MMAs of the next.
 //        Psi X'' only ever lives in tensor memory.
 //
-// Both: A and B K-major in 128-byte-swizzled shared memory, loaded by TMA;
+// Both: A and B K-major in 64-byte-swizzled shared memory, loaded by TMA;
 // one thread issues tcgen05.mma, accumulators (FP32) in tensor memory, read
 // back with tcgen05.ld.  Precisions: split BF16x3 (a = a_hi + a_lo, three
 // bf16 products a_hi b_hi + a_hi b_lo + a_lo b_hi) and TF32.  Persistent
@@ -28,9 +28,10 @@ namespace {
 
 constexpr int BM = 128;                 // MMA M = tensor-memory lanes
 constexpr int BN = 256;                 // MMA N
-constexpr int ROWB = 128;               // bytes per swizzled smem row
-constexpr int TILE_A = BM * ROWB;       // 16 KB per operand part
-constexpr int TILE_B = BN * ROWB;       // 32 KB per operand part
+constexpr int ROWB = 64;                // bytes per swizzled smem row (64-byte swizzle)
+constexpr int KSTEPS = ROWB / 32;       // 32-byte MMA K steps per row
+constexpr int TILE_A = BM * ROWB;       // 8 KB per operand part
+constexpr int TILE_B = BN * ROWB;       // 16 KB per operand part
 constexpr int NTHREADS = 192;           // warp 0 TMA, warp 1 MMA, warps 2-5 math / epilogue
 constexpr uint64_t WAIT_NS = 4000000000ull;
 
@@ -38,23 +39,29 @@ template <int PREC>
 struct Tr;
 template <>
 struct Tr<LRDM_BF16X3> {
-  static constexpr int BK = 64;          // bf16 per 128-byte row
+  static constexpr int BK = 32;          // bf16 per 64-byte row
   static constexpr int PARTS = 2;        // hi, lo
-  static constexpr int STAGES = 2;
+  static constexpr int STAGES = 4;
   static constexpr uint32_t IDESC = ptx::idesc_make(1, BM, BN);
 };
 template <>
 struct Tr<LRDM_TF32> {
-  static constexpr int BK = 32;          // fp32 per 128-byte row
+  static constexpr int BK = 16;          // fp32 per 64-byte row
   static constexpr int PARTS = 1;
-  static constexpr int STAGES = 4;
+  static constexpr int STAGES = 8;
   static constexpr uint32_t IDESC = ptx::idesc_make(2, BM, BN);
 };
 
 template <int PREC>
 __host__ __device__ constexpr int stage_bytes() { return Tr<PREC>::PARTS * (TILE_A + TILE_B); }
+// GEMM1 stages also carry the chunk of direction weights (BK floats), padded
+// so that every stage starts on a 1024-byte boundary.
 template <int PREC>
-__host__ __device__ constexpr int smem_bytes() { return Tr<PREC>::STAGES * stage_bytes<PREC>() + 1024 + 256; }
+__host__ __device__ constexpr int stage_stride_g1() { return stage_bytes<PREC>() + 1024; }
+template <int PREC>
+__host__ __device__ constexpr int smem_bytes() { return Tr<PREC>::STAGES * stage_bytes<PREC>() + 1024 + 512; }
+template <int PREC>
+__host__ __device__ constexpr int smem_bytes_g1() { return Tr<PREC>::STAGES * stage_stride_g1<PREC>() + 1024 + 512; }
 
 struct Bars {
   uint64_t* full;      // [STAGES] TMA landed
@@ -85,10 +92,14 @@ __device__ __forceinline__ Bars carve(uint8_t* tail) {
 __device__ __forceinline__ bool wait1(uint64_t* bar, uint32_t parity, const Bars& B, int* status) {
   return ptx::mbar_wait(bar, parity, B.abort, status, WAIT_NS, STATUS_TIMEOUT);
 }
-// Warp-uniform bounded wait: every lane polls, the decision is unanimous.
+// Warp-uniform bounded wait: lane 0 polls, the warp follows its verdict
+// (__syncwarp orders the other lanes' later shared-memory reads after it).
 __device__ __forceinline__ bool waitw(uint64_t* bar, uint32_t parity, const Bars& B, int* status) {
-  bool ok = ptx::mbar_wait(bar, parity, B.abort, status, WAIT_NS, STATUS_TIMEOUT);
-  return __all_sync(0xffffffffu, ok);
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = ptx::mbar_wait(bar, parity, B.abort, status, WAIT_NS, STATUS_TIMEOUT);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
 // Wait that ignores the abort flag (used to drain in-flight work on exit).
 __device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity) {
@@ -108,15 +119,15 @@ __device__ __forceinline__ void issue_stage_mmas(uint32_t d, uint32_t sa, uint32
   const uint32_t a0 = sa, a1 = sa + TILE_A;
   const uint32_t b0 = sa + PARTS * TILE_A, b1 = b0 + TILE_B;
 #pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {          // 4 x 32-byte K steps per 128-byte row
+  for (int kk = 0; kk < KSTEPS; ++kk) {     // 32-byte K steps along the swizzled row
     const uint32_t off = kk * 32;
     const uint32_t acc = (first && kk == 0) ? 0u : 1u;
     if (PREC == LRDM_BF16X3) {
-      ptx::mma_f16(d, ptx::desc_k_sw128(a0 + off), ptx::desc_k_sw128(b0 + off), Tr<PREC>::IDESC, acc);
-      ptx::mma_f16(d, ptx::desc_k_sw128(a0 + off), ptx::desc_k_sw128(b1 + off), Tr<PREC>::IDESC, 1);
-      ptx::mma_f16(d, ptx::desc_k_sw128(a1 + off), ptx::desc_k_sw128(b0 + off), Tr<PREC>::IDESC, 1);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b1 + off), Tr<PREC>::IDESC, 1);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a1 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, 1);
     } else {
-      ptx::mma_tf32(d, ptx::desc_k_sw128(a0 + off), ptx::desc_k_sw128(b0 + off), Tr<PREC>::IDESC, acc);
+      ptx::mma_tf32(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
     }
   }
 }
@@ -343,7 +354,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                const G1Params P) {
   using T = Tr<PREC>;
   constexpr int STAGES = T::STAGES, PARTS = T::PARTS, BK = T::BK;
-  constexpr int SB = stage_bytes<PREC>();
+  constexpr int SB = stage_stride_g1<PREC>();          // stride between stages
+  constexpr int TX = stage_bytes<PREC>() + BK * 4;     // bytes landing per stage
+  constexpr int SCALE_OFF = stage_bytes<PREC>();       // weights chunk within a stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Bars B = carve<STAGES>(smem + STAGES * SB);
@@ -387,11 +400,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int rc = 0; rc < P.nch; ++rc) {
         if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
         uint8_t* st = smem + s * SB;
-        ptx::mbar_arrive_expect_tx(&B.full[s], SB);
-        ptx::tma_load_2d(st, &mA0, &B.full[s], rc * BK, I * BM);
-        if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, &mA1, &B.full[s], rc * BK, I * BM);
-        ptx::tma_load_2d(st + PARTS * TILE_A, &mB0, &B.full[s], rc * BK, J * BN);
-        if (PARTS == 2) ptx::tma_load_2d(st + PARTS * TILE_A + TILE_B, &mB1, &B.full[s], rc * BK, J * BN);
+        ptx::mbar_arrive_expect_tx(&B.full[s], TX);
+        ptx::tma_load_4d(st, &mA0, &B.full[s], 0, 0, rc, I);
+        if (PARTS == 2) ptx::tma_load_4d(st + TILE_A, &mA1, &B.full[s], 0, 0, rc, I);
+        ptx::tma_load_4d(st + PARTS * TILE_A, &mB0, &B.full[s], 0, 0, rc, J * (BN / 128));
+        if (PARTS == 2)
+          ptx::tma_load_4d(st + PARTS * TILE_A + TILE_B, &mB1, &B.full[s], 0, 0, rc, J * (BN / 128));
+        ptx::bulk_load(st + SCALE_OFF, P.a + (long long)k * P.a_stride + (long long)rc * BK, BK * 4,
+                       &B.full[s]);
         pending[s] = (int)ph;
         if (++s == STAGES) { s = 0; ph ^= 1; }
       }
@@ -429,22 +445,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
       int k, I, J;
       g1_item(P, item, k, I, J);
-      const float* ak = P.a + (long long)k * P.a_stride;
       for (int rc = 0; rc < P.nch; ++rc) {
         if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
         uint8_t* st = smem + s * SB;
         uint8_t* r0 = st + row * ROWB;
-        const float* ar = ak + (long long)rc * BK;
+        const float* ar = reinterpret_cast<const float*>(st + SCALE_OFF);
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int p = (it + row) & 7;         // physical 16-byte chunk of this row
-          const int c = p ^ (row & 7);          // its logical chunk under the 128B swizzle
+        for (int it = 0; it < ROWB / 16; ++it) {
+          // physical 16-byte chunk of this row: rows 2m and 2m+1 share a 128-byte
+          // bank line, so rotating by m makes each group of 8 lanes hit 8
+          // distinct bank quads (no conflicts)
+          const int p = (it + (row >> 1)) & 3;
+          const int c = p ^ ((row >> 1) & 3);    // its logical chunk under the 64-byte swizzle
           if (PREC == LRDM_BF16X3) {
             uint4* hp = reinterpret_cast<uint4*>(r0 + p * 16);
             uint4* lp = reinterpret_cast<uint4*>(r0 + TILE_A + p * 16);
             const uint4 h = *hp, l = *lp;
-            const float4 s0 = __ldg(reinterpret_cast<const float4*>(ar + c * 8));
-            const float4 s1 = __ldg(reinterpret_cast<const float4*>(ar + c * 8 + 4));
+            const float4 s0 = *reinterpret_cast<const float4*>(ar + c * 8);
+            const float4 s1 = *reinterpret_cast<const float4*>(ar + c * 8 + 4);
             const float sc[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
             const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
             uint32_t oh[4], ol[4];
@@ -463,7 +481,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           } else {
             float4* xp = reinterpret_cast<float4*>(r0 + p * 16);
             const float4 x = *xp;
-            const float4 sc = __ldg(reinterpret_cast<const float4*>(ar + c * 4));
+            const float4 sc = *reinterpret_cast<const float4*>(ar + c * 4);
             *xp = make_float4(tf32_round(x.x * sc.x), tf32_round(x.y * sc.y),
                               tf32_round(x.z * sc.z), tf32_round(x.w * sc.w));
           }
@@ -526,14 +544,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D (rank 2) or 3D map over a row-major array; box inner extent = 128 bytes.
+// Map of rank 2-4 over a row-major array; box inner extent = 64 bytes,
+// 64-byte swizzle (matching desc_k_sw64).
 bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int rank, const uint64_t* dims,
               const uint64_t* strides_bytes, const uint32_t* box) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t gd[3];
-  cuuint64_t gs[2];
-  cuuint32_t bx[3], es[3] = {1, 1, 1};
+  cuuint64_t gd[4];
+  cuuint64_t gs[3];
+  cuuint32_t bx[4], es[4] = {1, 1, 1, 1};
   for (int i = 0; i < rank; ++i) {
     gd[i] = dims[i];
     bx[i] = box[i];
@@ -541,7 +560,7 @@ bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int rank, const 
   for (int i = 0; i < rank - 1; ++i) gs[i] = strides_bytes[i];
   CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                   rank, const_cast<void*>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -572,12 +591,15 @@ cudaError_t gemm1(const Channel& c, const SysState& S, int s, int K, const float
   const int eb = PREC == LRDM_BF16X3 ? 2 : 4;
   const void* p0 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_hi : (const void*)c.psiT32;
   const void* p1 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_lo : (const void*)c.psiT32;
+  // Psi^T is tile-major [ns_pad/128][Ng_pad/BK][128][BK]: one A box is one
+  // contiguous 8 KB tile, a B box two of them (consecutive state blocks).
   CUtensorMap mA0, mA1, mB0, mB1;
-  const uint64_t dims[2] = {(uint64_t)S.Ng_pad, (uint64_t)c.ns_pad};
-  const uint64_t strides[1] = {(uint64_t)S.Ng_pad * eb};
-  const uint32_t boxA[2] = {(uint32_t)BK, (uint32_t)BM}, boxB[2] = {(uint32_t)BK, (uint32_t)BN};
-  if (!make_map(&mA0, p0, eb, 2, dims, strides, boxA) || !make_map(&mA1, p1, eb, 2, dims, strides, boxA) ||
-      !make_map(&mB0, p0, eb, 2, dims, strides, boxB) || !make_map(&mB1, p1, eb, 2, dims, strides, boxB))
+  const uint64_t dims[4] = {(uint64_t)BK, 128, (uint64_t)(S.Ng_pad / BK), (uint64_t)(c.ns_pad / 128)};
+  const uint64_t strides[3] = {(uint64_t)BK * eb, (uint64_t)128 * BK * eb,
+                               (uint64_t)128 * S.Ng_pad * eb};
+  const uint32_t boxA[4] = {(uint32_t)BK, 128, 1, 1}, boxB[4] = {(uint32_t)BK, 128, 1, BN / 128};
+  if (!make_map(&mA0, p0, eb, 4, dims, strides, boxA) || !make_map(&mA1, p1, eb, 4, dims, strides, boxA) ||
+      !make_map(&mB0, p0, eb, 4, dims, strides, boxB) || !make_map(&mB1, p1, eb, 4, dims, strides, boxB))
     return cudaErrorInvalidValue;
   G1Params P;
   P.K = K;
@@ -593,7 +615,7 @@ cudaError_t gemm1(const Channel& c, const SysState& S, int s, int K, const float
   P.X = static_cast<float*>(Xout);
   P.status = status;
   static bool attr = false;
-  const int smem = smem_bytes<PREC>();
+  const int smem = smem_bytes_g1<PREC>();
   cudaError_t e = set_smem(k_gemm1_tc<PREC>, smem, attr);
   if (e != cudaSuccess) return e;
   const int items = K * P.items_per_k;

@@ -41,9 +41,9 @@ struct Channel {
   // Psi operand copies (which ones exist depends on the precision)
   double* psi64 = nullptr;           // [Ng][ns]
   float* psi32 = nullptr;            // [Ng][ns]           (FP32 SIMT)
-  float* psiT32 = nullptr;           // [ns_pad][Ng_pad]   (TF32, GEMM1 operand)
+  float* psiT32 = nullptr;           // Psi^T tile-major [ns_pad/128][Ng_pad/16][128][16] (TF32, GEMM1)
   float* psiR32 = nullptr;           // [Ng_pad][ns_pad]   (TF32, GEMM2 operand)
-  __nv_bfloat16* psiT_hi = nullptr;  // [ns_pad][Ng_pad]   (BF16X3, GEMM1)
+  __nv_bfloat16* psiT_hi = nullptr;  // Psi^T tile-major [ns_pad/128][Ng_pad/32][128][32] (BF16X3, GEMM1)
   __nv_bfloat16* psiT_lo = nullptr;
   __nv_bfloat16* psiR_hi = nullptr;  // [Ng_pad][ns_pad]   (BF16X3, GEMM2)
   __nv_bfloat16* psiR_lo = nullptr;
