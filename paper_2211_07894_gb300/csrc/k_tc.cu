@@ -1,10 +1,11 @@
 // Tensor-core (tcgen05) forms of the two contractions on sm_103a.
 //
 // GEMM1  X_k[i, j] = sum_r (a_k[r] Psi[r, i]) Psi[r, j]     (H-breve', §II.C)
-//        tile 128 (i) x 256 (j), i-blocks with i0 < j0 + 256 only (upper part);
-//        the whole grid reduction runs inside one tile; the a_k weighting is
-//        applied to the A tile in shared memory between its TMA load and the
-//        MMAs (the weights chunk arrives with the tiles by a bulk copy).
+//        tile 128 (i) x 256 (j), i-blocks with i0 < j0 + 256 only (upper part),
+//        two directions per tile (two TMEM accumulators); the whole grid
+//        reduction runs inside one tile; the a_k weighting is applied to the
+//        A tile in shared memory between its TMA load and the MMAs (the
+//        weights chunks arrive with the tiles by bulk copies).
 // GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
 //        tile 128 (r) x 256 (j); for each j-block the i-reduction stops at the
 //        block's end (X'' is zero below the diagonal); two TMEM accumulators so
@@ -54,14 +55,9 @@ struct Tr<LRDM_TF32> {
 
 template <int PREC>
 __host__ __device__ constexpr int stage_bytes() { return Tr<PREC>::PARTS * (TILE_A + TILE_B); }
-// GEMM1 stages also carry the chunk of direction weights (BK floats), padded
-// so that every stage starts on a 1024-byte boundary.
-template <int PREC>
-__host__ __device__ constexpr int stage_stride_g1() { return stage_bytes<PREC>() + 1024; }
 template <int PREC>
 __host__ __device__ constexpr int smem_bytes() { return Tr<PREC>::STAGES * stage_bytes<PREC>() + 1024 + 512; }
-template <int PREC>
-__host__ __device__ constexpr int smem_bytes_g1() { return Tr<PREC>::STAGES * stage_stride_g1<PREC>() + 1024 + 512; }
+
 
 struct Bars {
   uint64_t* full;      // [STAGES] TMA landed
@@ -141,6 +137,7 @@ __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 
 
 struct G2Params {
   int K, ns_pad, nR, NJ;
+  int kgroup;              // directions that share one Psi row block side by side
   long long Ng;
   const void* psi0;        // epilogue Psi rows: bf16 hi (BF16X3) or fp32 (TF32), [Ng_pad][ns_pad]
   const void* psi1;        // bf16 lo (BF16X3)
@@ -152,6 +149,18 @@ struct G2Params {
   int out_io, out_is_io;
   int* status;
 };
+
+// Item order: groups of kgroup directions, row block, direction within the
+// group -- the items of one row block run side by side and share its Psi rows
+// through L2, while only kgroup matrices X''_k compete for L2 at a time.
+__device__ __forceinline__ void g2_item(const G2Params& P, int item, int& k, int& R) {
+  const int per = P.nR * P.kgroup;
+  const int kg = item / per;
+  const int rem = item - kg * per;
+  const int g = min(P.kgroup, P.K - kg * P.kgroup);
+  R = rem / g;
+  k = kg * P.kgroup + (rem - R * g);
+}
 
 template <int PREC>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -199,7 +208,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int pending[STAGES];
     for (int i = 0; i < STAGES; ++i) pending[i] = -1;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
-      const int k = item / P.nR, R = item - k * P.nR;
+      int k, R;
+      g2_item(P, item, k, R);
       bool ok = true;
       for (int J = 0; J < P.NJ && ok; ++J) {
         const int nch = min((J + 1) * BN, P.ns_pad) / BK;
@@ -253,7 +263,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t aph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      const int k = item / P.nR, R = item - k * P.nR;
+      int k, R;
+      g2_item(P, item, k, R);
       const long long r = (long long)R * BM + row;
       double acc_row = 0.0;
       for (int J = 0; J < P.NJ; ++J) {
@@ -324,18 +335,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // ===========================================================================
 // GEMM1: projection with the per-direction weights applied in shared memory
 // ===========================================================================
+//
+// One work item = one (I, J) tile for a pair of directions (k0, k0 + 1): the
+// Psi^T tiles of a stage are loaded once, the weighting step writes one scaled
+// copy of the A tile per direction, and the MMAs accumulate into two 256-column
+// TMEM accumulators.  Stage layout: [A for k0 (TMA raw, scaled in place)]
+// [A for k1 (written by the weighting step)] [B] [weights of k0, k1].
+
+template <int PREC>
+struct G1Cfg {
+  static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
+  static constexpr int A_OFF0 = 0;
+  static constexpr int A_OFF1 = PARTS * TILE_A;
+  static constexpr int B_OFF = 2 * PARTS * TILE_A;
+  static constexpr int SC_OFF = B_OFF + PARTS * TILE_B;
+  static constexpr int STRIDE = SC_OFF + 1024;                 // 1024-aligned stages
+  static constexpr int STAGES = PREC == LRDM_BF16X3 ? 3 : 6;
+  static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
+};
 
 struct G1Params {
-  int K, ns, ns_pad, nI, NJ, items_per_k, nch;
+  int K, ns, ns_pad, nI, NJ, ntiles, nkp, nch;
   const float* a;          // weights of this channel, direction stride a_stride
   long long a_stride;
   float* X;                // [K][ns_pad][ns_pad]
   int* status;
 };
 
-__device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k, int& I, int& J) {
-  k = item / P.items_per_k;
-  int idx = item - k * P.items_per_k;
+// Items are ordered with the direction pair fastest: the pairs of one (I, J)
+// tile run side by side on different SMs and stream the same Psi^T tiles
+// through L2 at the same time.
+__device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k0, int& I, int& J) {
+  int idx = item / P.nkp;
+  k0 = 2 * (item - idx * P.nkp);
   int j = 0;
   for (;;) {
     const int cnt = min(2 * (j + 1), P.nI);     // i-blocks of 128 below the end of j-block j
@@ -348,20 +380,90 @@ __device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k, int
 }
 
 template <int PREC>
+__device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t a0, uint32_t b0, uint32_t first) {
+  constexpr int PARTS = Tr<PREC>::PARTS;
+  const uint32_t a1 = a0 + TILE_A, b1 = b0 + TILE_B;
+  (void)PARTS;
+#pragma unroll
+  for (int kk = 0; kk < KSTEPS; ++kk) {
+    const uint32_t off = kk * 32;
+    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+    if (PREC == LRDM_BF16X3) {
+      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b1 + off), Tr<PREC>::IDESC, 1);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a1 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, 1);
+    } else {
+      ptx::mma_tf32(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
+    }
+  }
+}
+
+// Scales one 16-byte chunk (8 bf16 hi + 8 bf16 lo, or 4 fp32) of the raw A row
+// by the weights of both directions: writes k0's copy in place and k1's copy
+// at the same position of the second A buffer.
+template <int PREC>
+__device__ __forceinline__ void scale_chunk(uint32_t raw, uint32_t out1, uint32_t sc0, uint32_t sc1,
+                                            bool two) {
+  if (PREC == LRDM_BF16X3) {
+    const uint4 h = ptx::lds128(raw), l = ptx::lds128(raw + TILE_A);
+    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      x[2 * e] = bf_lo(hw[e]) + bf_lo(lw[e]);
+      x[2 * e + 1] = bf_hi(hw[e]) + bf_hi(lw[e]);
+    }
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (d == 1 && !two) break;
+      const uint32_t sa = d == 0 ? sc0 : sc1;
+      const uint4 s0 = ptx::lds128(sa), s1 = ptx::lds128(sa + 16);
+      const float sc[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
+                           __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
+                           __uint_as_float(s1.z), __uint_as_float(s1.w)};
+      uint32_t oh[4], ol[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float y0 = x[2 * e] * sc[2 * e];
+        const float y1 = x[2 * e + 1] * sc[2 * e + 1];
+        const __nv_bfloat162 hi2 = __floats2bfloat162_rn(y0, y1);
+        const float2 hf = __bfloat1622float2(hi2);
+        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+        oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
+        ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
+      }
+      const uint32_t dst = d == 0 ? raw : out1;
+      ptx::sts128(dst, make_uint4(oh[0], oh[1], oh[2], oh[3]));
+      ptx::sts128(dst + TILE_A, make_uint4(ol[0], ol[1], ol[2], ol[3]));
+    }
+  } else {
+    const uint4 x = ptx::lds128(raw);
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (d == 1 && !two) break;
+      const uint4 sc = ptx::lds128(d == 0 ? sc0 : sc1);
+      ptx::sts128(d == 0 ? raw : out1,
+                  make_uint4(__float_as_uint(tf32_round(__uint_as_float(x.x) * __uint_as_float(sc.x))),
+                             __float_as_uint(tf32_round(__uint_as_float(x.y) * __uint_as_float(sc.y))),
+                             __float_as_uint(tf32_round(__uint_as_float(x.z) * __uint_as_float(sc.z))),
+                             __float_as_uint(tf32_round(__uint_as_float(x.w) * __uint_as_float(sc.w)))));
+    }
+  }
+}
+
+template <int PREC>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm1_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                const G1Params P) {
-  using T = Tr<PREC>;
-  constexpr int STAGES = T::STAGES, PARTS = T::PARTS, BK = T::BK;
-  constexpr int SB = stage_stride_g1<PREC>();          // stride between stages
-  constexpr int TX = stage_bytes<PREC>() + BK * 4;     // bytes landing per stage
-  constexpr int SCALE_OFF = stage_bytes<PREC>();       // weights chunk within a stage
+  using C = G1Cfg<PREC>;
+  constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::STRIDE;
+  constexpr int TILES = PARTS * (TILE_A + TILE_B);       // TMA bytes per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Bars B = carve<STAGES>(smem + STAGES * SB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int items = P.K * P.items_per_k;
+  const int items = P.ntiles * P.nkp;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -377,7 +479,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     ptx::fence_proxy_async_smem();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(B.tmem_slot, BN);
+    ptx::tmem_alloc(B.tmem_slot, 2 * BN);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -395,19 +497,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int i = 0; i < STAGES; ++i) pending[i] = -1;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k, I, J;
-      g1_item(P, item, k, I, J);
+      int k0, I, J;
+      g1_item(P, item, k0, I, J);
+      const bool two = k0 + 1 < P.K;
+      const float* w0 = P.a + (long long)k0 * P.a_stride;
       for (int rc = 0; rc < P.nch; ++rc) {
         if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
         uint8_t* st = smem + s * SB;
-        ptx::mbar_arrive_expect_tx(&B.full[s], TX);
-        ptx::tma_load_4d(st, &mA0, &B.full[s], 0, 0, rc, I);
-        if (PARTS == 2) ptx::tma_load_4d(st + TILE_A, &mA1, &B.full[s], 0, 0, rc, I);
-        ptx::tma_load_4d(st + PARTS * TILE_A, &mB0, &B.full[s], 0, 0, rc, J * (BN / 128));
+        ptx::mbar_arrive_expect_tx(&B.full[s], TILES + (two ? 2 : 1) * BK * 4);
+        ptx::tma_load_4d(st + C::A_OFF0, &mA0, &B.full[s], 0, 0, rc, I);
+        if (PARTS == 2) ptx::tma_load_4d(st + C::A_OFF0 + TILE_A, &mA1, &B.full[s], 0, 0, rc, I);
+        ptx::tma_load_4d(st + C::B_OFF, &mB0, &B.full[s], 0, 0, rc, J * (BN / 128));
         if (PARTS == 2)
-          ptx::tma_load_4d(st + PARTS * TILE_A + TILE_B, &mB1, &B.full[s], 0, 0, rc, J * (BN / 128));
-        ptx::bulk_load(st + SCALE_OFF, P.a + (long long)k * P.a_stride + (long long)rc * BK, BK * 4,
-                       &B.full[s]);
+          ptx::tma_load_4d(st + C::B_OFF + TILE_B, &mB1, &B.full[s], 0, 0, rc, J * (BN / 128));
+        ptx::bulk_load(st + C::SC_OFF, w0 + (long long)rc * BK, BK * 4, &B.full[s]);
+        if (two) ptx::bulk_load(st + C::SC_OFF + BK * 4, w0 + P.a_stride + (long long)rc * BK, BK * 4, &B.full[s]);
         pending[s] = (int)ph;
         if (++s == STAGES) { s = 0; ph ^= 1; }
       }
@@ -420,12 +524,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t ph = 0, aph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      int k0, I, J;
+      g1_item(P, item, k0, I, J);
+      const bool two = k0 + 1 < P.K;
       if (!wait1(&B.acc_empty[0], aph ^ 1, B, P.status)) break;
       ptx::tc_fence_after();
       for (int rc = 0; rc < P.nch; ++rc) {
         if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
-        issue_stage_mmas<PREC>(tmem, ptx::smem_u32(smem + s * SB), rc == 0);
+        const uint32_t st = ptx::smem_u32(smem + s * SB);
+        issue_mmas<PREC>(tmem, st + C::A_OFF0, st + C::B_OFF, rc == 0);
+        if (two) issue_mmas<PREC>(tmem + BN, st + C::A_OFF1, st + C::B_OFF, rc == 0);
         ptx::mma_commit(&B.empty[s]);
         if (++s == STAGES) { s = 0; ph ^= 1; }
       }
@@ -436,55 +545,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     ptx::mma_commit(B.drain);
     wait_drain(B.drain, 0);
   } else if (warp >= 2) {
-    // -------- weighting of the A tile (in place), then the tile epilogue --------
+    // -------- weighting of the A tile for both directions, then the epilogue --------
     const int q = warp & 3;
     const int row = q * 32 + lane;
     int s = 0;
     uint32_t ph = 0, aph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k, I, J;
-      g1_item(P, item, k, I, J);
+      int k0, I, J;
+      g1_item(P, item, k0, I, J);
+      const bool two = k0 + 1 < P.K;
       for (int rc = 0; rc < P.nch; ++rc) {
         if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
-        uint8_t* st = smem + s * SB;
-        uint8_t* r0 = st + row * ROWB;
-        const float* ar = reinterpret_cast<const float*>(st + SCALE_OFF);
+        const uint32_t st = ptx::smem_u32(smem + s * SB);
+        const uint32_t r0 = st + C::A_OFF0 + row * ROWB;
+        const uint32_t r1 = st + C::A_OFF1 + row * ROWB;
+        const uint32_t sc = st + C::SC_OFF;
 #pragma unroll
         for (int it = 0; it < ROWB / 16; ++it) {
           // physical 16-byte chunk of this row: rows 2m and 2m+1 share a 128-byte
-          // bank line, so rotating by m makes each group of 8 lanes hit 8
-          // distinct bank quads (no conflicts)
+          // bank line, so rotating by m spreads each group of 8 lanes over 8
+          // distinct bank quads
           const int p = (it + (row >> 1)) & 3;
           const int c = p ^ ((row >> 1) & 3);    // its logical chunk under the 64-byte swizzle
-          if (PREC == LRDM_BF16X3) {
-            uint4* hp = reinterpret_cast<uint4*>(r0 + p * 16);
-            uint4* lp = reinterpret_cast<uint4*>(r0 + TILE_A + p * 16);
-            const uint4 h = *hp, l = *lp;
-            const float4 s0 = *reinterpret_cast<const float4*>(ar + c * 8);
-            const float4 s1 = *reinterpret_cast<const float4*>(ar + c * 8 + 4);
-            const float sc[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-            const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-            uint32_t oh[4], ol[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float x0 = (bf_lo(hw[e]) + bf_lo(lw[e])) * sc[2 * e];
-              const float x1 = (bf_hi(hw[e]) + bf_hi(lw[e])) * sc[2 * e + 1];
-              const __nv_bfloat162 hi2 = __floats2bfloat162_rn(x0, x1);
-              const float2 hf = __bfloat1622float2(hi2);
-              const __nv_bfloat162 lo2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-              oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
-              ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
-            }
-            *hp = make_uint4(oh[0], oh[1], oh[2], oh[3]);
-            *lp = make_uint4(ol[0], ol[1], ol[2], ol[3]);
-          } else {
-            float4* xp = reinterpret_cast<float4*>(r0 + p * 16);
-            const float4 x = *xp;
-            const float4 sc = *reinterpret_cast<const float4*>(ar + c * 4);
-            *xp = make_float4(tf32_round(x.x * sc.x), tf32_round(x.y * sc.y),
-                              tf32_round(x.z * sc.z), tf32_round(x.w * sc.w));
-          }
+          const uint32_t wofs = (uint32_t)c * 16u * (uint32_t)(BK / (ROWB / 16)) / 4u;  // c * (BK/4) floats
+          scale_chunk<PREC>(r0 + p * 16, r1 + p * 16, sc + wofs, sc + BK * 4 + wofs, two);
         }
         ptx::fence_proxy_async_smem();
         __syncwarp();
@@ -492,23 +577,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (++s == STAGES) { s = 0; ph ^= 1; }
       }
       if (!ok) break;
-      // epilogue: X[i][j] and X[j][i] for i <= j of this tile
+      // epilogue: X[i][j] and X[j][i] for i <= j of this tile, both directions
       if (!waitw(&B.acc_full[0], aph, B, P.status)) break;
       ptx::tc_fence_after();
       const int i = I * BM + row;
-      float* Xk = P.X + (long long)k * P.ns_pad * P.ns_pad;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        float v[32];
-        ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
-        const int j0 = J * BN + c * 32;
-        if (i < P.ns) {
+      for (int d = 0; d < (two ? 2 : 1); ++d) {
+        float* Xk = P.X + (long long)(k0 + d) * P.ns_pad * P.ns_pad;
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+          float v[32];
+          ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * BN + c * 32), v);
+          const int j0 = J * BN + c * 32;
+          if (i < P.ns) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int j = j0 + e;
-            if (j >= i && j < P.ns) {
-              Xk[(long long)i * P.ns_pad + j] = v[e];
-              Xk[(long long)j * P.ns_pad + i] = v[e];
+            for (int e = 0; e < 32; ++e) {
+              const int j = j0 + e;
+              if (j >= i && j < P.ns) {
+                Xk[(long long)i * P.ns_pad + j] = v[e];
+                Xk[(long long)j * P.ns_pad + i] = v[e];
+              }
             }
           }
         }
@@ -523,7 +611,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, BN);
+    ptx::tmem_dealloc(tmem, 2 * BN);
   }
 }
 
@@ -607,18 +695,19 @@ cudaError_t gemm1(const Channel& c, const SysState& S, int s, int K, const float
   P.ns_pad = c.ns_pad;
   P.nI = c.ns_pad / BM;
   P.NJ = (c.ns_pad + BN - 1) / BN;
-  P.items_per_k = 0;
-  for (int j = 0; j < P.NJ; ++j) P.items_per_k += (2 * (j + 1) < P.nI ? 2 * (j + 1) : P.nI);
+  P.ntiles = 0;
+  for (int j = 0; j < P.NJ; ++j) P.ntiles += (2 * (j + 1) < P.nI ? 2 * (j + 1) : P.nI);
+  P.nkp = (K + 1) / 2;
   P.nch = (int)(S.Ng_pad / BK);
   P.a = a;
   P.a_stride = (long long)S.nspin * S.Ng_pad;
   P.X = static_cast<float*>(Xout);
   P.status = status;
   static bool attr = false;
-  const int smem = smem_bytes_g1<PREC>();
+  const int smem = G1Cfg<PREC>::SMEM;
   cudaError_t e = set_smem(k_gemm1_tc<PREC>, smem, attr);
   if (e != cudaSuccess) return e;
-  const int items = K * P.items_per_k;
+  const int items = P.ntiles * P.nkp;
   const int grid = items < num_sms() ? items : num_sms();
   if (grid <= 0) return cudaSuccess;
   k_gemm1_tc<PREC><<<grid, NTHREADS, smem, st>>>(mA0, mA1, mB0, mB1, P);
@@ -649,6 +738,7 @@ cudaError_t gemm2(const Channel& c, const SysState& S, int K, double factor, con
   P.K = K;
   P.ns_pad = c.ns_pad;
   P.nR = (int)(S.Ng_pad / BM);
+  P.kgroup = K < 2 ? K : 2;
   P.NJ = (c.ns_pad + BN - 1) / BN;
   P.Ng = S.Ng;
   P.psi0 = a0;

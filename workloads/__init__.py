@@ -262,9 +262,11 @@ def config5_small(scale):
 
 def random_subspace_torch(n, h, ns, seed, device, dtype=None):
     """Psi = orth(diag(e) G)/sqrt(w) built on the device by two passes of
-    Cholesky-QR (Gram in float32 with TF32 off, Cholesky in float64).  Same
-    recipe as random_subspace() with torch's RNG, for grids too large to
-    generate on the host."""
+    Cholesky-QR (Gram in float32 with TF32 off; the small Cholesky factor and
+    its triangular inverse in float64 on the host).  Same recipe as
+    random_subspace() with torch's RNG, for grids too large to generate on
+    the host."""
+    import scipy.linalg
     import torch
     dtype = dtype or torch.float32
     N = int(np.prod(n))
@@ -278,12 +280,11 @@ def random_subspace_torch(n, h, ns, seed, device, dtype=None):
     torch.backends.cuda.matmul.allow_tf32 = False
     try:
         for _ in range(2):
-            C = (A.T @ A).double()
+            C = (A.T @ A).double().cpu().numpy()
             C = 0.5 * (C + C.T)
-            U = torch.linalg.cholesky(C, upper=True)
-            Uinv = torch.linalg.solve_triangular(
-                U, torch.eye(ns, device=device, dtype=torch.float64), upper=True)
-            A = A @ Uinv.float()
+            U = np.linalg.cholesky(C).T
+            Uinv = scipy.linalg.solve_triangular(U, np.eye(ns), lower=False)
+            A = A @ torch.as_tensor(Uinv, dtype=torch.float32, device=device)
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
     A.mul_(1.0 / np.sqrt(w))
