@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--grid", type=int, default=96, help="grid edge (96 = the benchmark workload)")
     p.add_argument("--ns", type=int, default=NS)
+    p.add_argument("--compare-fp64", action="store_true",
+                   help="time the plain FP64 GPU form (torch, Psi X' materialised) and the "
+                        "library's FP64 path on a 48^3 slice instead of the benchmark step")
     return p.parse_args()
 
 
@@ -234,8 +237,66 @@ def build_problem(torch, rank, prec, edge, ns):
     return ctx, V, R, ng
 
 
+def compare_fp64(args):
+    """The plain FP64 GPU form: per direction, X = Psi^T (a o Psi) and
+    drho = rowsum((Psi X') o Psi) with dense torch FP64 matmuls (Psi X'
+    materialised), next to this library's FP64 path, both for one direction on
+    a 48^3 grid with N_s = 4096 (1/8 of the 96^3 rows; both forms are linear in
+    the rows, so GD/s at 96^3 = 1 / (8 t)).  The two dense products are > 99 %
+    of the plain form's work; its element-wise steps are not timed."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_2211_07894_gb300 import Context
+    torch.cuda.set_device(0)
+    n = (48, 48, 48)
+    ng = int(np.prod(n))
+    scale = float(np.prod(GRID)) / ng
+    psi32 = workloads.random_subspace_torch(n, H, NS, seed=2211078940 + 60, device="cuda")
+    psi = psi32.double()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    a = torch.randn(ng, dtype=torch.float64, device="cuda", generator=g)
+    Xp = torch.randn(NS, NS, dtype=torch.float64, device="cuda", generator=g)
+    Xp = Xp + Xp.T
+
+    def plain():
+        X = psi.T @ (a[:, None] * psi)
+        d = ((psi @ Xp) * psi).sum(dim=1)
+        return X, d
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    t_plain = timed(plain)
+    eps = torch.as_tensor(workloads.random_eigenvalues(NS, workloads.rng_for(5, 60)), device="cuda")
+    V = torch.as_tensor(workloads.smooth_directions(n, H, 1, 1, workloads.rng_for(5, 61)),
+                        dtype=torch.float64, device="cuda")
+    ctx = Context([dict(n=n, h=H, psi=[psi], eps=[eps], n_electrons=NE, kT=KT, g=2.0,
+                        rho_floor=1e-3, k_max=1)], prec="fp64", io_dtype=torch.float64, k_max=1)
+    F = torch.empty_like(V)
+    t_ours = timed(lambda: ctx.gateaux([V], out=[F]))
+    for impl, t in (("plain-fp64-gpu", t_plain), ("library-fp64", t_ours)):
+        print(json.dumps({"impl": impl, "metric": METRIC, "value": 1.0 / (t * scale),
+                          "unit": "GD/s", "dtype": "f64",
+                          "sample": "1 direction, 48^3 grid, N_s=4096; GD/s scaled by the 8x row ratio",
+                          "seconds_per_direction_at_96^3": t * scale}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.compare_fp64:
+        return compare_fp64(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -1,0 +1,102 @@
+"""Parity at the benchmark size (96^3 grid, N_s = 4096, K = 16, FP32 Psi,
+split-BF16x3 contractions -- the launch configuration bench.py times).
+
+The oracle cannot evaluate the whole path at this size in seconds, so it
+checks (a) sampled entries of the projected perturbation X_k, each computed
+one by one in FP64 from its definition sum_r Psi_ri w dV_k(r) Psi_rj, with
+dV_k from the oracle's own density, xc kernel and Hartree solve, and (b)
+properties of the response that hold at any size: int drho_k = 0 (electron
+count), <dV_a, drho_b> = <dV_b, drho_a> (self-adjoint chi_0), <dV_a, drho_a>
+<= 0 (negative semidefinite chi_0), and f_k + v_k = drho_k consistency with
+g-scaling.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+N = (96, 96, 96)
+H = (0.5, 0.5, 0.5)
+NS, K, NE, KT = 4096, 16, 3700.0, 0.005
+
+
+@pytest.fixture(scope="module")
+def full():
+    from paper_2211_07894_gb300 import Context, build
+    build.build()
+    ng = int(np.prod(N))
+    psi = workloads.random_subspace_torch(N, H, NS, seed=2211078940 + 50, device="cuda")
+    eps = workloads.random_eigenvalues(NS, workloads.rng_for(5, 0))
+    V = workloads.smooth_directions(N, H, K, 1, workloads.rng_for(5, 1))
+    ctx = Context([dict(n=N, h=H, psi=[psi], eps=[torch.as_tensor(eps, device="cuda")],
+                        n_electrons=NE, kT=KT, g=2.0, rho_floor=1e-3, k_max=K)],
+                  prec="bf16x3", io_dtype=torch.float32, k_max=K)
+    Vd = torch.as_tensor(V, dtype=torch.float32, device="cuda")
+    (F,), dmu = ctx.gateaux([Vd])
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    psi_h = psi.cpu().numpy()
+    # oracle side: occupations, density (row blocks of the same per-row formula),
+    # xc kernel and dV_k from the FP32 Psi values the device was given
+    mu = oracle.solve_mu([eps], NE, KT, 2.0)
+    occ = oracle.fermi(eps, mu, KT)
+    rho = np.empty(ng)
+    for r0 in range(0, ng, 65536):
+        rho[r0:r0 + 65536] = oracle.density(psi_h[r0:r0 + 65536].astype(np.float64), occ, 2.0, 1e-3)
+    fx = oracle.lda_fx(rho)
+    dV = np.stack([oracle.perturbation_potential([V[k, 0]], [fx], N, H)[0] for k in range(K)])
+    return dict(ctx=ctx, psi=psi_h, V=V, F=F.double().cpu().numpy()[:, 0], dV=dV, mu=mu,
+                w=float(np.prod(H)), dmu=dmu.cpu().numpy())
+
+
+def test_chemical_potential(full):
+    assert abs(full["ctx"].mu() - full["mu"]) < 1e-12
+
+
+def test_sampled_projection_entries(full):
+    rng = np.random.default_rng(11)
+    w = full["w"]
+    worst = 0.0
+    for k in (0, 7, 15):
+        X = full["ctx"].projection(k).cpu().numpy()
+        idx = [(i, i) for i in rng.integers(0, NS, 4)] + [tuple(sorted(rng.integers(0, NS, 2))) for _ in range(8)]
+        ref = []
+        for i, j in idx:
+            pi = full["psi"][:, i].astype(np.float64)
+            pj = full["psi"][:, j].astype(np.float64)
+            ref.append(float(np.dot(pi * (w * full["dV"][k]), pj)))
+        ref = np.array(ref)
+        got = np.array([X[i, j] for i, j in idx])
+        scale = np.sqrt(np.mean(ref ** 2))
+        worst = max(worst, float(np.max(np.abs(got - ref)) / scale))
+        # symmetric by construction
+        i, j = idx[-1]
+        assert X[i, j] == X[j, i]
+    print(f"full-size X samples: max |err| / rms = {worst:.3e}")
+    assert worst < 1e-4
+
+
+def test_response_properties(full):
+    w = full["w"]
+    drho = full["F"] + full["V"][:, 0]          # f = drho - v
+    dV = full["dV"]
+    for k in range(K):
+        nrm = np.sqrt(w * np.sum(drho[k] ** 2))
+        vol = np.sqrt(w * drho.shape[1])
+        assert abs(w * drho[k].sum()) <= 1e-4 * nrm * vol
+    worst = 0.0
+    for a, b in [(0, 1), (2, 9), (5, 15), (3, 4)]:
+        lhs = w * np.dot(dV[a], drho[b])
+        rhs = w * np.dot(dV[b], drho[a])
+        scale = np.sqrt(abs(w * np.dot(dV[a], drho[a]) * w * np.dot(dV[b], drho[b])))
+        worst = max(worst, abs(lhs - rhs) / scale)
+    print(f"full-size self-adjointness: max rel asymmetry {worst:.3e}")
+    assert worst < 1e-4
+    for k in range(K):
+        assert w * np.dot(dV[k], drho[k]) < 0.0

@@ -1,0 +1,48 @@
+"""Precision study at the 72^3 / N_s = 2048 / K = 12 size with 5 % of the
+eigenvalues in near-degenerate pairs (gap 1e-9 Ha, a third of them next to the
+Fermi level): every contraction precision against the FP64 oracle.
+
+The GPU runs all 12 directions in one call (its launch configuration); the
+oracle evaluates three of them in full.  The Loewner entries of the 1e-9 Ha
+pairs, mu and mu' stay FP64 in every mode, so the FP64 run must meet 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import oracle_system, rel_err
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 5e-3, "bf16x3": 1e-5}
+CHECK = [0, 5, 11]
+
+
+@pytest.fixture(scope="module")
+def study():
+    from paper_2211_07894_gb300 import build
+    build.build()
+    cfg = workloads.config4()
+    osys = oracle_system(cfg)
+    ref = oracle.gateaux(osys, cfg["V"][CHECK])
+    return cfg, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
+def test_precision(study, prec):
+    from gpu_helpers import directions, make_context
+    cfg, ref = study
+    io = torch.float64 if prec == "fp64" else torch.float32
+    ctx, _ = make_context([cfg], prec, io)
+    V = directions(cfg, io)
+    (F,), dmu = ctx.gateaux([V])
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    Fh = F.double().cpu().numpy()
+    errs = [rel_err(Fh[k], ref["F"][n]) for n, k in enumerate(CHECK)]
+    print(f"precision study {prec}: f rel err per direction {['%.2e' % e for e in errs]}")
+    assert max(errs) < TOL[prec]
