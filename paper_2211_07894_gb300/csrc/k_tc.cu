@@ -1,11 +1,11 @@
 // Tensor-core (tcgen05) forms of the two contractions on sm_103a.
 //
 // GEMM1  X_k[i, j] = sum_r (a_k[r] Psi[r, i]) Psi[r, j]     (H-breve', §II.C)
-//        tile 128 (i) x 256 (j), i-blocks with i0 < j0 + 256 only (upper part),
-//        two directions per tile (two TMEM accumulators); the whole grid
-//        reduction runs inside one tile; the a_k weighting is applied to the
-//        A tile in shared memory between its TMA load and the MMAs (the
-//        weights chunks arrive with the tiles by bulk copies).
+//        tile 128 (i) x 256 (j), i-blocks with i0 < j0 + 256 only (upper part);
+//        the whole grid reduction runs inside one tile, in segments of 512
+//        rows whose TMEM results are summed in FP32 registers; the a_k
+//        weighting is applied to the A tile in shared memory between its TMA
+//        load and the MMAs (the weights chunk arrives with the tiles).
 // GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
 //        tile 128 (r) x 256 (j); for each j-block the i-reduction stops at the
 //        block's end (X'' is zero below the diagonal); two TMEM accumulators so
@@ -23,6 +23,8 @@
 #include "tc_ptx.cuh"
 
 #include <cudaTypedefs.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 namespace lrdm {
 namespace {
@@ -336,38 +338,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // GEMM1: projection with the per-direction weights applied in shared memory
 // ===========================================================================
 //
-// One work item = one (I, J) tile for a pair of directions (k0, k0 + 1): the
-// Psi^T tiles of a stage are loaded once, the weighting step writes one scaled
-// copy of the A tile per direction, and the MMAs accumulate into two 256-column
-// TMEM accumulators.  Stage layout: [A for k0 (TMA raw, scaled in place)]
-// [A for k1 (written by the weighting step)] [B] [weights of k0, k1].
+// One work item = one (I, J) tile of one direction, reduced over the whole
+// grid.  The tensor cores' FP32 accumulation truncates, and over a reduction
+// of 10^5-10^6 rows that bias reaches ~1e-3 of the result; so the reduction is
+// segmented: each segment of SEG stages (SEG * BK rows) accumulates in one of
+// two TMEM buffers, after which eight warps add it into FP32 running sums held
+// in registers (round-to-nearest) while the MMAs fill the other buffer.  The
+// same eight warps apply the direction weights to the A tile of every stage
+// (in shared memory, between its TMA load and the MMAs).
+
+constexpr int G1_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 weighting + accumulation
+constexpr int G1_SEG = 16;          // stages per TMEM accumulation segment
+constexpr int G1_LAG = 2;           // stages the weighting runs ahead before flushing a segment
 
 template <int PREC>
 struct G1Cfg {
   static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
-  static constexpr int A_OFF0 = 0;
-  static constexpr int A_OFF1 = PARTS * TILE_A;
-  static constexpr int B_OFF = 2 * PARTS * TILE_A;
+  static constexpr int B_OFF = PARTS * TILE_A;
   static constexpr int SC_OFF = B_OFF + PARTS * TILE_B;
   static constexpr int STRIDE = SC_OFF + 1024;                 // 1024-aligned stages
-  static constexpr int STAGES = PREC == LRDM_BF16X3 ? 3 : 6;
+  static constexpr int STAGES = PREC == LRDM_BF16X3 ? 4 : 8;
   static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
 };
 
 struct G1Params {
-  int K, ns, ns_pad, nI, NJ, ntiles, nkp, nch;
+  int K, ns, ns_pad, nI, NJ, ntiles, nch;
   const float* a;          // weights of this channel, direction stride a_stride
   long long a_stride;
   float* X;                // [K][ns_pad][ns_pad]
   int* status;
 };
 
-// Items are ordered with the direction pair fastest: the pairs of one (I, J)
+// Items are ordered with the direction fastest: the K items of one (I, J)
 // tile run side by side on different SMs and stream the same Psi^T tiles
 // through L2 at the same time.
-__device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k0, int& I, int& J) {
-  int idx = item / P.nkp;
-  k0 = 2 * (item - idx * P.nkp);
+__device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k, int& I, int& J) {
+  int idx = item / P.K;
+  k = item - idx * P.K;
   int j = 0;
   for (;;) {
     const int cnt = min(2 * (j + 1), P.nI);     // i-blocks of 128 below the end of j-block j
@@ -379,100 +386,65 @@ __device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k0, in
   I = idx;
 }
 
+// Scales one 16-byte chunk (8 bf16 hi + 8 bf16 lo, or 4 fp32) of the A row in
+// place by the direction weights at shared address sc.
 template <int PREC>
-__device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t a0, uint32_t b0, uint32_t first) {
-  constexpr int PARTS = Tr<PREC>::PARTS;
-  const uint32_t a1 = a0 + TILE_A, b1 = b0 + TILE_B;
-  (void)PARTS;
-#pragma unroll
-  for (int kk = 0; kk < KSTEPS; ++kk) {
-    const uint32_t off = kk * 32;
-    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-    if (PREC == LRDM_BF16X3) {
-      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
-      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b1 + off), Tr<PREC>::IDESC, 1);
-      ptx::mma_f16(d, ptx::desc_k_sw64(a1 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, 1);
-    } else {
-      ptx::mma_tf32(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
-    }
-  }
-}
-
-// Scales one 16-byte chunk (8 bf16 hi + 8 bf16 lo, or 4 fp32) of the raw A row
-// by the weights of both directions: writes k0's copy in place and k1's copy
-// at the same position of the second A buffer.
-template <int PREC>
-__device__ __forceinline__ void scale_chunk(uint32_t raw, uint32_t out1, uint32_t sc0, uint32_t sc1,
-                                            bool two) {
+__device__ __forceinline__ void scale_chunk(uint32_t raw, uint32_t sc) {
   if (PREC == LRDM_BF16X3) {
     const uint4 h = ptx::lds128(raw), l = ptx::lds128(raw + TILE_A);
+    const uint4 s0 = ptx::lds128(sc), s1 = ptx::lds128(sc + 16);
     const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-    float x[8];
+    const float w8[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
+                         __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
+                         __uint_as_float(s1.z), __uint_as_float(s1.w)};
+    uint32_t oh[4], ol[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      x[2 * e] = bf_lo(hw[e]) + bf_lo(lw[e]);
-      x[2 * e + 1] = bf_hi(hw[e]) + bf_hi(lw[e]);
+      const float y0 = (bf_lo(hw[e]) + bf_lo(lw[e])) * w8[2 * e];
+      const float y1 = (bf_hi(hw[e]) + bf_hi(lw[e])) * w8[2 * e + 1];
+      const __nv_bfloat162 hi2 = __floats2bfloat162_rn(y0, y1);
+      const float2 hf = __bfloat1622float2(hi2);
+      const __nv_bfloat162 lo2 = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+      oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
+      ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
     }
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      if (d == 1 && !two) break;
-      const uint32_t sa = d == 0 ? sc0 : sc1;
-      const uint4 s0 = ptx::lds128(sa), s1 = ptx::lds128(sa + 16);
-      const float sc[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
-                           __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
-                           __uint_as_float(s1.z), __uint_as_float(s1.w)};
-      uint32_t oh[4], ol[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float y0 = x[2 * e] * sc[2 * e];
-        const float y1 = x[2 * e + 1] * sc[2 * e + 1];
-        const __nv_bfloat162 hi2 = __floats2bfloat162_rn(y0, y1);
-        const float2 hf = __bfloat1622float2(hi2);
-        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
-        oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
-        ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
-      }
-      const uint32_t dst = d == 0 ? raw : out1;
-      ptx::sts128(dst, make_uint4(oh[0], oh[1], oh[2], oh[3]));
-      ptx::sts128(dst + TILE_A, make_uint4(ol[0], ol[1], ol[2], ol[3]));
-    }
+    ptx::sts128(raw, make_uint4(oh[0], oh[1], oh[2], oh[3]));
+    ptx::sts128(raw + TILE_A, make_uint4(ol[0], ol[1], ol[2], ol[3]));
   } else {
     const uint4 x = ptx::lds128(raw);
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      if (d == 1 && !two) break;
-      const uint4 sc = ptx::lds128(d == 0 ? sc0 : sc1);
-      ptx::sts128(d == 0 ? raw : out1,
-                  make_uint4(__float_as_uint(tf32_round(__uint_as_float(x.x) * __uint_as_float(sc.x))),
-                             __float_as_uint(tf32_round(__uint_as_float(x.y) * __uint_as_float(sc.y))),
-                             __float_as_uint(tf32_round(__uint_as_float(x.z) * __uint_as_float(sc.z))),
-                             __float_as_uint(tf32_round(__uint_as_float(x.w) * __uint_as_float(sc.w)))));
-    }
+    const uint4 w = ptx::lds128(sc);
+    ptx::sts128(raw, make_uint4(__float_as_uint(tf32_round(__uint_as_float(x.x) * __uint_as_float(w.x))),
+                                __float_as_uint(tf32_round(__uint_as_float(x.y) * __uint_as_float(w.y))),
+                                __float_as_uint(tf32_round(__uint_as_float(x.z) * __uint_as_float(w.z))),
+                                __float_as_uint(tf32_round(__uint_as_float(x.w) * __uint_as_float(w.w)))));
   }
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(G1_THREADS, 1)
     k_gemm1_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                const G1Params P) {
   using C = G1Cfg<PREC>;
   constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::STRIDE;
-  constexpr int TILES = PARTS * (TILE_A + TILE_B);       // TMA bytes per stage
+  constexpr int TX = PARTS * (TILE_A + TILE_B) + BK * 4;   // bytes landing per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Bars B = carve<STAGES>(smem + STAGES * SB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int items = P.ntiles * P.nkp;
+  const int items = P.K * P.ntiles;
+  const int nseg = (P.nch + G1_SEG - 1) / G1_SEG;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       ptx::mbar_init(&B.full[s], 1);
       ptx::mbar_init(&B.empty[s], 1);
-      ptx::mbar_init(&B.ready[s], 4);
+      ptx::mbar_init(&B.ready[s], 8);
     }
-    ptx::mbar_init(&B.acc_full[0], 1);
-    ptx::mbar_init(&B.acc_empty[0], 4);
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&B.acc_full[b], 1);      // segment b accumulated
+      ptx::mbar_init(&B.acc_empty[b], 8);     // segment b added to the running sums
+    }
     ptx::mbar_init(B.drain, 1);
     *B.abort = 0;
     ptx::fence_barrier_init();
@@ -497,21 +469,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int i = 0; i < STAGES; ++i) pending[i] = -1;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k0, I, J;
-      g1_item(P, item, k0, I, J);
-      const bool two = k0 + 1 < P.K;
-      const float* w0 = P.a + (long long)k0 * P.a_stride;
+      int k, I, J;
+      g1_item(P, item, k, I, J);
+      const float* wk = P.a + (long long)k * P.a_stride;
       for (int rc = 0; rc < P.nch; ++rc) {
         if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
         uint8_t* st = smem + s * SB;
-        ptx::mbar_arrive_expect_tx(&B.full[s], TILES + (two ? 2 : 1) * BK * 4);
-        ptx::tma_load_4d(st + C::A_OFF0, &mA0, &B.full[s], 0, 0, rc, I);
-        if (PARTS == 2) ptx::tma_load_4d(st + C::A_OFF0 + TILE_A, &mA1, &B.full[s], 0, 0, rc, I);
+        ptx::mbar_arrive_expect_tx(&B.full[s], TX);
+        ptx::tma_load_4d(st, &mA0, &B.full[s], 0, 0, rc, I);
+        if (PARTS == 2) ptx::tma_load_4d(st + TILE_A, &mA1, &B.full[s], 0, 0, rc, I);
         ptx::tma_load_4d(st + C::B_OFF, &mB0, &B.full[s], 0, 0, rc, J * (BN / 128));
         if (PARTS == 2)
           ptx::tma_load_4d(st + C::B_OFF + TILE_B, &mB1, &B.full[s], 0, 0, rc, J * (BN / 128));
-        ptx::bulk_load(st + C::SC_OFF, w0 + (long long)rc * BK, BK * 4, &B.full[s]);
-        if (two) ptx::bulk_load(st + C::SC_OFF + BK * 4, w0 + P.a_stride + (long long)rc * BK, BK * 4, &B.full[s]);
+        ptx::bulk_load(st + C::SC_OFF, wk + (long long)rc * BK, BK * 4, &B.full[s]);
         pending[s] = (int)ph;
         if (++s == STAGES) { s = 0; ph ^= 1; }
       }
@@ -519,92 +489,101 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int i = 0; i < STAGES; ++i)
       if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    int s = 0;
-    uint32_t ph = 0, aph = 0;
+    // ---------------- MMA issuer: segments alternate between two TMEM buffers ----------------
+    int s = 0, b = 0;
+    uint32_t ph = 0, bph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k0, I, J;
-      g1_item(P, item, k0, I, J);
-      const bool two = k0 + 1 < P.K;
-      if (!wait1(&B.acc_empty[0], aph ^ 1, B, P.status)) break;
-      ptx::tc_fence_after();
-      for (int rc = 0; rc < P.nch; ++rc) {
-        if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
+      for (int sg = 0; sg < nseg && ok; ++sg) {
+        if (!wait1(&B.acc_empty[b], bph ^ 1, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
-        const uint32_t st = ptx::smem_u32(smem + s * SB);
-        issue_mmas<PREC>(tmem, st + C::A_OFF0, st + C::B_OFF, rc == 0);
-        if (two) issue_mmas<PREC>(tmem + BN, st + C::A_OFF1, st + C::B_OFF, rc == 0);
-        ptx::mma_commit(&B.empty[s]);
-        if (++s == STAGES) { s = 0; ph ^= 1; }
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+        const int r0 = sg * G1_SEG, r1 = min(P.nch, r0 + G1_SEG);
+        for (int rc = r0; rc < r1; ++rc) {
+          if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
+          ptx::tc_fence_after();
+          issue_stage_mmas<PREC>(d, ptx::smem_u32(smem + s * SB), rc == r0);
+          ptx::mma_commit(&B.empty[s]);
+          if (++s == STAGES) { s = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&B.acc_full[b]);
+        if (++b == 2) { b = 0; bph ^= 1; }
       }
-      if (!ok) break;
-      ptx::mma_commit(&B.acc_full[0]);
-      aph ^= 1;
     }
     ptx::mma_commit(B.drain);
     wait_drain(B.drain, 0);
   } else if (warp >= 2) {
-    // -------- weighting of the A tile for both directions, then the epilogue --------
-    const int q = warp & 3;
+    // ---- weighting of the A tiles, segment accumulation, tile epilogue ----
+    const int q = warp & 3;                 // TMEM lane quarter
+    const int half = (warp - 2) >> 2;       // columns [128 half, 128 half + 128) of the tile
     const int row = q * 32 + lane;
-    int s = 0;
-    uint32_t ph = 0, aph = 0;
+    int s = 0, b = 0;
+    uint32_t ph = 0, bph = 0;
     bool ok = true;
+    float sum[128];
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k0, I, J;
-      g1_item(P, item, k0, I, J);
-      const bool two = k0 + 1 < P.K;
+      int k, I, J;
+      g1_item(P, item, k, I, J);
+#pragma unroll
+      for (int c = 0; c < 128; ++c) sum[c] = 0.f;
+      int flushed = 0;                      // segments already added into sum[]
       for (int rc = 0; rc < P.nch; ++rc) {
         if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
         const uint32_t st = ptx::smem_u32(smem + s * SB);
-        const uint32_t r0 = st + C::A_OFF0 + row * ROWB;
-        const uint32_t r1 = st + C::A_OFF1 + row * ROWB;
+        const uint32_t r0 = st + row * ROWB;
         const uint32_t sc = st + C::SC_OFF;
 #pragma unroll
-        for (int it = 0; it < ROWB / 16; ++it) {
-          // physical 16-byte chunk of this row: rows 2m and 2m+1 share a 128-byte
-          // bank line, so rotating by m spreads each group of 8 lanes over 8
-          // distinct bank quads
+        for (int u = 0; u < 2; ++u) {
+          const int it = 2 * half + u;
+          // physical 16-byte chunk: rotating by row/2 keeps each group of 8 lanes
+          // on 8 distinct bank quads
           const int p = (it + (row >> 1)) & 3;
-          const int c = p ^ ((row >> 1) & 3);    // its logical chunk under the 64-byte swizzle
-          const uint32_t wofs = (uint32_t)c * 16u * (uint32_t)(BK / (ROWB / 16)) / 4u;  // c * (BK/4) floats
-          scale_chunk<PREC>(r0 + p * 16, r1 + p * 16, sc + wofs, sc + BK * 4 + wofs, two);
+          const int c = p ^ ((row >> 1) & 3);      // logical chunk under the 64-byte swizzle
+          scale_chunk<PREC>(r0 + p * 16, sc + c * (BK / 4) * 4);
         }
         ptx::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&B.ready[s]);
         if (++s == STAGES) { s = 0; ph ^= 1; }
+        // add a finished segment into the running sums once the weighting is
+        // G1_LAG stages ahead of its end (so the MMAs keep being fed)
+        const int ready_seg = (rc + 1 - G1_LAG) / G1_SEG;   // segments whose end is >= G1_LAG behind
+        const bool last = rc + 1 == P.nch;
+        while (flushed < nseg && (flushed < ready_seg || last)) {
+          if (!waitw(&B.acc_full[b], bph, B, P.status)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * 128);
+#pragma unroll
+          for (int c8 = 0; c8 < 8; ++c8) {
+            float v[16];
+            ptx::tmem_ld16(ta + c8 * 16, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sum[c8 * 16 + e] += v[e];
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&B.acc_empty[b]);
+          if (++b == 2) { b = 0; bph ^= 1; }
+          ++flushed;
+        }
+        if (!ok) break;
       }
       if (!ok) break;
-      // epilogue: X[i][j] and X[j][i] for i <= j of this tile, both directions
-      if (!waitw(&B.acc_full[0], aph, B, P.status)) break;
-      ptx::tc_fence_after();
+      // epilogue: X[i][j] and X[j][i] for i <= j of this tile
       const int i = I * BM + row;
-#pragma unroll 1
-      for (int d = 0; d < (two ? 2 : 1); ++d) {
-        float* Xk = P.X + (long long)(k0 + d) * P.ns_pad * P.ns_pad;
-#pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-          float v[32];
-          ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * BN + c * 32), v);
-          const int j0 = J * BN + c * 32;
-          if (i < P.ns) {
+      if (i < P.ns) {
+        float* Xk = P.X + (long long)k * P.ns_pad * P.ns_pad;
+        const int j0 = J * BN + half * 128;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const int j = j0 + e;
-              if (j >= i && j < P.ns) {
-                Xk[(long long)i * P.ns_pad + j] = v[e];
-                Xk[(long long)j * P.ns_pad + i] = v[e];
-              }
-            }
+        for (int c = 0; c < 128; ++c) {
+          const int j = j0 + c;
+          if (j >= i && j < P.ns) {
+            Xk[(long long)i * P.ns_pad + j] = sum[c];
+            Xk[(long long)j * P.ns_pad + i] = sum[c];
           }
         }
       }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&B.acc_empty[0]);
-      aph ^= 1;
     }
   }
   ptx::tc_fence_before();
@@ -697,7 +676,6 @@ cudaError_t gemm1(const Channel& c, const SysState& S, int s, int K, const float
   P.NJ = (c.ns_pad + BN - 1) / BN;
   P.ntiles = 0;
   for (int j = 0; j < P.NJ; ++j) P.ntiles += (2 * (j + 1) < P.nI ? 2 * (j + 1) : P.nI);
-  P.nkp = (K + 1) / 2;
   P.nch = (int)(S.Ng_pad / BK);
   P.a = a;
   P.a_stride = (long long)S.nspin * S.Ng_pad;
@@ -707,10 +685,18 @@ cudaError_t gemm1(const Channel& c, const SysState& S, int s, int K, const float
   const int smem = G1Cfg<PREC>::SMEM;
   cudaError_t e = set_smem(k_gemm1_tc<PREC>, smem, attr);
   if (e != cudaSuccess) return e;
-  const int items = P.ntiles * P.nkp;
+  const int items = P.ntiles * K;
   const int grid = items < num_sms() ? items : num_sms();
   if (grid <= 0) return cudaSuccess;
-  k_gemm1_tc<PREC><<<grid, NTHREADS, smem, st>>>(mA0, mA1, mB0, mB1, P);
+  if (getenv("LRDM_DEBUG")) {
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, k_gemm1_tc<PREC>);
+    int nb = -1;
+    cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm1_tc<PREC>, G1_THREADS, smem);
+    fprintf(stderr, "gemm1: regs %d local %zu maxthreads %d smem %d occupancy %d (%s)\n", fa.numRegs,
+            fa.localSizeBytes, fa.maxThreadsPerBlock, smem, nb, cudaGetErrorString(oe));
+  }
+  k_gemm1_tc<PREC><<<grid, G1_THREADS, smem, st>>>(mA0, mA1, mB0, mB1, P);
   return cudaGetLastError();
 }
 

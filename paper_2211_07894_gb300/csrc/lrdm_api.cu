@@ -5,6 +5,8 @@
 #include "lrdm_internal.h"
 
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -16,6 +18,10 @@ namespace {
 
 lrdm_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return LRDM_OK;
+  // LRDM_DEBUG=1 in the environment prints the CUDA error behind a failure
+  static const bool debug = getenv("LRDM_DEBUG") != nullptr;
+  if (debug) fprintf(stderr, "liblrdm: CUDA error %d (%s): %s\n", (int)e, cudaGetErrorName(e),
+                     cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? LRDM_ERR_OOM : LRDM_ERR_CUDA;
 }
 lrdm_status from_cufft(cufftResult r) {
