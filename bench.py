@@ -5,8 +5,12 @@ Metric: Gateaux derivatives per second at a 96^3 grid (884,736 points),
 N_s = 4096, K = 16 directions (one derivative = one (system, direction) f_k).
 One step = one pass of the whole path over one batch of K directions:
 Hartree + LDA kernel, projection GEMM, mu' and Loewner scaling, response GEMM
-with the f = drho - v epilogue (lrdm_gateaux_batch), then the K x K
-least-squares step and update (lrdm_apply).
+with the f = drho - v epilogue (lrdm_gateaux_batch), the K x K least-squares
+step and update (lrdm_apply), and the hand-written adjoint of the response
+map and of the eigenvalue / occupation inputs for one cotangent per direction
+(lrdm_backward).  The forward call alone (one CUDA-graph replay of
+lrdm_gateaux_batch) is timed separately and reported under "forward_only",
+with and without the Poisson (cuFFT) step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|tf32|fp32|fp64]
   python bench.py --impl reference ...     (the FP64 CPU oracle, timed on the host)
@@ -32,7 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "Gateaux derivatives/sec at 96^3 grid, N_s=4096, K=16"
+METRIC = "Gateaux derivatives/sec at 96^3 grid, N_s=4096, K=16; tensor-pipe % vs FP64 plain form"
 GRID = (96, 96, 96)
 H = (0.5, 0.5, 0.5)
 NS = 4096
@@ -51,8 +55,12 @@ def parse():
     p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "tf32", "fp32", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64-plain", action="store_true",
+                   help="skip timing the plain FP64 GPU form")
     p.add_argument("--grid", type=int, default=96, help="grid edge (96 = the benchmark workload)")
     p.add_argument("--ns", type=int, default=NS)
+    p.add_argument("--fwd-reps", type=int, default=10,
+                   help="graph replays of the forward call timed for forward_only")
     p.add_argument("--compare-fp64", action="store_true",
                    help="time the plain FP64 GPU form (torch, Psi X' materialised) and the "
                         "library's FP64 path on a 48^3 slice instead of the benchmark step")
@@ -156,6 +164,7 @@ def oracle_step(sysm, V, R):
     import oracle
     res = oracle.gateaux(sysm, V)
     oracle.lrdm_apply(R, V, res["F"], sysm.w, 0.5, rho=sysm.rho[0][None, :])
+    oracle.backward(sysm, res["F"], res)
 
 
 def cpu_cores():
@@ -177,7 +186,7 @@ def time_oracle(steps, warmup):
         oracle_step(sysm, V, R)
     dt = (time.perf_counter() - t0) / max(steps, 1)
     gds = 1.0 / (dt * scale)     # one direction per step, scaled to 96^3 rows
-    sample = (f"oracle.gateaux + lrdm_apply, K=1, N_s={NS}, grid {ORACLE_SAMPLE_GRID[0]}^3 "
+    sample = (f"oracle.gateaux + lrdm_apply + backward, K=1, N_s={NS}, grid {ORACLE_SAMPLE_GRID[0]}^3 "
               f"(1/{int(scale)} of the 96^3 rows), {steps} step(s); GD/s scaled by the row ratio")
     return gds, dt, sample
 
@@ -231,29 +240,32 @@ def build_problem(torch, rank, prec, edge, ns):
     if io == torch.float64:
         system["psi"] = [psi.double()]
         V, R = V.double(), R.double()
-    ctx = Context([system], prec=prec, io_dtype=io, k_max=KDIR)
+    ctx = Context([system], prec=prec, io_dtype=io, k_max=KDIR, use_graph=True)
     del psi, system
     torch.cuda.empty_cache()
     return ctx, V, R, ng
 
 
-def compare_fp64(args):
+FP64_SAMPLE_GRID = (48, 48, 48)
+
+
+def time_fp64_plain(torch, reps=1, with_library=False):
     """The plain FP64 GPU form: per direction, X = Psi^T (a o Psi) and
     drho = rowsum((Psi X') o Psi) with dense torch FP64 matmuls (Psi X'
-    materialised), next to this library's FP64 path, both for one direction on
-    a 48^3 grid with N_s = 4096 (1/8 of the 96^3 rows; both forms are linear in
-    the rows, so GD/s at 96^3 = 1 / (8 t)).  The two dense products are > 99 %
-    of the plain form's work; its element-wise steps are not timed."""
+    materialised), for one direction on a 48^3 grid with N_s = 4096 (1/8 of
+    the 96^3 rows; both products are linear in the rows, so GD/s at 96^3 =
+    1 / (8 t)).  The two dense products are > 99 % of the plain form's work;
+    its element-wise steps are not timed.  with_library also times this
+    library's FP64 path on the same slice."""
     import numpy as np
-    import torch
     import workloads
     from paper_2211_07894_gb300 import Context
-    torch.cuda.set_device(0)
-    n = (48, 48, 48)
+    n = FP64_SAMPLE_GRID
     ng = int(np.prod(n))
     scale = float(np.prod(GRID)) / ng
     psi32 = workloads.random_subspace_torch(n, H, NS, seed=2211078940 + 60, device="cuda")
     psi = psi32.double()
+    del psi32
     g = torch.Generator(device="cuda")
     g.manual_seed(5)
     a = torch.randn(ng, dtype=torch.float64, device="cuda", generator=g)
@@ -265,7 +277,7 @@ def compare_fp64(args):
         d = ((psi @ Xp) * psi).sum(dim=1)
         return X, d
 
-    def timed(fn, reps=2):
+    def timed(fn):
         fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -277,19 +289,33 @@ def compare_fp64(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3 / reps
 
+    out = {}
     t_plain = timed(plain)
-    eps = torch.as_tensor(workloads.random_eigenvalues(NS, workloads.rng_for(5, 60)), device="cuda")
-    V = torch.as_tensor(workloads.smooth_directions(n, H, 1, 1, workloads.rng_for(5, 61)),
-                        dtype=torch.float64, device="cuda")
-    ctx = Context([dict(n=n, h=H, psi=[psi], eps=[eps], n_electrons=NE, kT=KT, g=2.0,
-                        rho_floor=1e-3, k_max=1)], prec="fp64", io_dtype=torch.float64, k_max=1)
-    F = torch.empty_like(V)
-    t_ours = timed(lambda: ctx.gateaux([V], out=[F]))
-    for impl, t in (("plain-fp64-gpu", t_plain), ("library-fp64", t_ours)):
-        print(json.dumps({"impl": impl, "metric": METRIC, "value": 1.0 / (t * scale),
-                          "unit": "GD/s", "dtype": "f64",
-                          "sample": "1 direction, 48^3 grid, N_s=4096; GD/s scaled by the 8x row ratio",
-                          "seconds_per_direction_at_96^3": t * scale}), flush=True)
+    out["plain-fp64-gpu"] = t_plain
+    if with_library:
+        eps = torch.as_tensor(workloads.random_eigenvalues(NS, workloads.rng_for(5, 60)), device="cuda")
+        V = torch.as_tensor(workloads.smooth_directions(n, H, 1, 1, workloads.rng_for(5, 61)),
+                            dtype=torch.float64, device="cuda")
+        ctx = Context([dict(n=n, h=H, psi=[psi], eps=[eps], n_electrons=NE, kT=KT, g=2.0,
+                            rho_floor=1e-3, k_max=1)], prec="fp64", io_dtype=torch.float64, k_max=1)
+        F = torch.empty_like(V)
+        out["library-fp64"] = timed(lambda: ctx.gateaux([V], out=[F]))
+        ctx.close()
+    del psi, a, Xp
+    torch.cuda.empty_cache()
+    sample = (f"1 direction, {n[0]}^3 grid, N_s={NS}, {reps} timed rep(s); GD/s scaled by the "
+              f"{int(scale)}x row ratio")
+    return {k: (1.0 / (t * scale), t * scale) for k, t in out.items()}, sample
+
+
+def compare_fp64(args):
+    import torch
+    torch.cuda.set_device(0)
+    res, sample = time_fp64_plain(torch, reps=2, with_library=True)
+    for impl, (gds, sec) in res.items():
+        print(json.dumps({"impl": impl, "metric": METRIC, "value": gds, "unit": "GD/s",
+                          "dtype": "f64", "sample": sample,
+                          "seconds_per_direction_at_96^3": sec}), flush=True)
     return 0
 
 
@@ -319,14 +345,20 @@ def main():
     coeff = torch.empty(KDIR, dtype=torch.float64, device="cuda")
     srel = torch.empty(1, dtype=torch.float64, device="cuda")
     dmu = torch.empty(KDIR, dtype=torch.float64, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2211078940 + 70 + rank)
+    fbar = torch.randn(V.shape, dtype=V.dtype, device="cuda", generator=gen)
+    bwd_out = None
     stream = torch.cuda.current_stream()
 
-    def step():
-        ctx.gateaux([V], out=[F], dmu=dmu)
-        ctx.apply(0, R, V, F, 0.0, rho=rho_out, coeff=coeff, s_rel=srel)
+    def step(Vs, Rs, Fb):
+        nonlocal bwd_out
+        ctx.gateaux([Vs], out=[F], dmu=dmu)
+        ctx.apply(0, Rs, Vs, F, 0.0, rho=rho_out, coeff=coeff, s_rel=srel)
+        bwd_out = ctx.backward([Fb], out=bwd_out)
 
     for _ in range(max(args.warmup, 0)):
-        step()
+        step(V, R, fbar)
     torch.cuda.synchronize()
     if ctx.status() != 0:
         raise RuntimeError("device status not ok after warm-up")
@@ -341,7 +373,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        step(V, R, fbar)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -362,25 +394,56 @@ def main():
     if ctx.status() != 0:
         raise RuntimeError("device status not ok after the timed region")
 
+    # the forward call alone: CUDA-graph replays of lrdm_gateaux_batch
+    ctx.gateaux([V], out=[F], dmu=dmu)          # captures the graph
+    torch.cuda.synchronize()
+    reps = max(args.fwd_reps, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for a0, a1 in ev:
+        a0.record(stream)
+        ctx.gateaux([V], out=[F], dmu=dmu)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = sorted(a0.elapsed_time(a1) for a0, a1 in ev)
+    fwd_med = statistics.median(fwd_ms)
+    # Poisson per forward call (one solve per call; the backward makes one more)
+    poisson_fwd = prof["poisson_ms"] / max(prof["poisson_calls"], 1)
+    forward_only = {"value": KDIR * world / (fwd_med / 1e3), "unit": "GD/s",
+                    "ms_median": fwd_med, "ms_min": fwd_ms[0], "replays": reps,
+                    "graph": True, "poisson_ms": poisson_fwd,
+                    "value_without_poisson": KDIR * world / ((fwd_med - poisson_fwd) / 1e3)}
+    if ctx.status() != 0:
+        raise RuntimeError("device status not ok after the forward-only replays")
+
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
         Vh = V.cpu().pin_memory()
         Rh = R.cpu().pin_memory()
+        Fbh = fbar.cpu().pin_memory()
         out_h = torch.empty_like(rho_out, device="cpu").pin_memory()
         coef_h = torch.empty(KDIR, dtype=torch.float64).pin_memory()
         srel_h = torch.empty(1, dtype=torch.float64).pin_memory()
+        vbar_h = torch.empty_like(V, device="cpu").pin_memory()
+        ebar_h = torch.empty(ns, dtype=torch.float64).pin_memory()
+        obar_h = torch.empty(ns, dtype=torch.float64).pin_memory()
         Vd = torch.empty_like(V)
         Rd = torch.empty_like(R)
+        Fbd = torch.empty_like(fbar)
 
         def e2e_step():
             Vd.copy_(Vh, non_blocking=True)
             Rd.copy_(Rh, non_blocking=True)
-            ctx.gateaux([Vd], out=[F], dmu=dmu)
-            ctx.apply(0, Rd, Vd, F, 0.0, rho=rho_out, coeff=coeff, s_rel=srel)
+            Fbd.copy_(Fbh, non_blocking=True)
+            step(Vd, Rd, Fbd)
+            vbar, eb, ob = bwd_out
             out_h.copy_(rho_out, non_blocking=True)
             coef_h.copy_(coeff, non_blocking=True)
             srel_h.copy_(srel, non_blocking=True)
+            vbar_h.copy_(vbar[0], non_blocking=True)
+            ebar_h.copy_(eb[0], non_blocking=True)
+            obar_h.copy_(ob[0], non_blocking=True)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -398,10 +461,13 @@ def main():
             t = torch.tensor([ems], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
-        h2d = Vh.numel() * Vh.element_size() + Rh.numel() * Rh.element_size()
-        d2h = (out_h.numel() * out_h.element_size() + coef_h.numel() * 8 + 8)
+        nb = lambda x: x.numel() * x.element_size()
+        h2d = nb(Vh) + nb(Rh) + nb(Fbh)
+        d2h = nb(out_h) + nb(coef_h) + nb(srel_h) + nb(vbar_h) + nb(ebar_h) + nb(obar_h)
         e2e = {"value": total_gd / (ems / 1e3), "unit": "GD/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+        if ctx.status() != 0:
+            raise RuntimeError("device status not ok after the end-to-end steps")
 
     # roofline of the dominant contraction
     peaks, peak_src = load_peaks()
@@ -433,6 +499,18 @@ def main():
                 "kernel": name, "avg_launch_ms": avg_s * 1e3, "launches": nl,
                 "alg_flop_per_launch": alg_flops, "peak_source": f"{peak_src}; {note}"}
 
+    fp64_plain = None
+    if not args.no_fp64_plain:
+        ctx.close()
+        del F, fbar, bwd_out
+        torch.cuda.empty_cache()
+        res, sample = time_fp64_plain(torch)
+        gds, sec = res["plain-fp64-gpu"]
+        fp64_plain = {"value": gds * world, "unit": "GD/s", "seconds_per_direction": sec,
+                      "sample": sample,
+                      "speedup_forward_only": forward_only["value"] / (gds * world),
+                      "speedup_step": value / (gds * world)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gds, dt, sample = time_oracle(1, 0)
@@ -452,8 +530,12 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],
+                "forward_only": forward_only, "fp64_plain": fp64_plain,
                 "breakdown_ms": {"gemm1_per_step": prof["gemm1_ms"] / steps,
-                                 "gemm2_per_step": prof["gemm2_ms"] / steps}}
+                                 "gemm2_per_step": prof["gemm2_ms"] / steps,
+                                 "poisson_per_step": prof["poisson_ms"] / steps,
+                                 "gemm1_launches_per_step": prof["gemm1_launches"] / steps,
+                                 "gemm2_launches_per_step": prof["gemm2_launches"] / steps}}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -193,17 +193,20 @@ lrdm_status lrdm_get_mu(lrdm_ctx* ctx, int sys, double* mu_host);
  * into out ([N_g], io dtype, device).  Asynchronous. */
 lrdm_status lrdm_get_density(lrdm_ctx* ctx, int sys, int spin, void* out, void* stream);
 
-/* Benchmark instrumentation.  While enabled, each contraction launch is
- * bracketed by CUDA events recorded on its launching stream (at most 4096
- * launches are kept), and the library counts the kernels it launches itself
- * (cuFFT's own kernels are not counted).  lrdm_profile_read synchronises
- * those events and returns the summed device times (ms) and counts of the
- * projection GEMM (X_k) and the response GEMM (drho_k) launches, and the total
- * number of library kernel launches; reset != 0 clears the record. */
+/* Benchmark instrumentation.  While enabled, each contraction launch and each
+ * Poisson solve (cuFFT forward, symbol kernel, cuFFT inverse) is bracketed by
+ * CUDA events recorded on its launching stream (at most 4096 records are
+ * kept), the library counts the kernels it launches itself (cuFFT's own
+ * kernels are not counted), and lrdm_gateaux_batch does not use its CUDA
+ * graph.  lrdm_profile_read synchronises those events and returns the summed
+ * device times (ms) and counts of the projection GEMM (X_k, forward and
+ * backward) launches, the response GEMM (drho_k, forward and backward)
+ * launches and the Poisson solves, and the total number of library kernel
+ * launches; any output pointer may be NULL; reset != 0 clears the record. */
 lrdm_status lrdm_profile_enable(lrdm_ctx* ctx, int on);
 lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_launches,
-                              double* gemm2_ms, long long* gemm2_launches,
-                              long long* kernel_launches, int reset);
+                              double* gemm2_ms, long long* gemm2_launches, double* poisson_ms,
+                              long long* poisson_calls, long long* kernel_launches, int reset);
 
 /* Copies the projected perturbation X_k = Psi^T diag(w dV_k) Psi of direction
  * k, channel `spin`, of system `sys` from the most recent lrdm_gateaux_batch

@@ -93,6 +93,7 @@ def load(path: Optional[str] = None):
     lib.lrdm_profile_enable.restype = c_int
     lib.lrdm_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(ctypes.c_longlong),
                                       POINTER(c_double), POINTER(ctypes.c_longlong),
+                                      POINTER(c_double), POINTER(ctypes.c_longlong),
                                       POINTER(ctypes.c_longlong), c_int]
     lib.lrdm_profile_read.restype = c_int
     lib.lrdm_destroy.argtypes = [c_void_p]
@@ -184,13 +185,16 @@ def lrdm_profile_enable(ctx, on: int) -> int:
 
 
 def lrdm_profile_read(ctx, reset: int = 1):
-    t1, t2 = c_double(), c_double()
-    n1, n2, nk = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    t1, t2, t3 = c_double(), c_double(), c_double()
+    n1, n2, n3, nk = (ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong(),
+                      ctypes.c_longlong())
     _check("lrdm_profile_read", load().lrdm_profile_read(ctx, ctypes.byref(t1), ctypes.byref(n1),
                                                          ctypes.byref(t2), ctypes.byref(n2),
+                                                         ctypes.byref(t3), ctypes.byref(n3),
                                                          ctypes.byref(nk), reset))
     return dict(gemm1_ms=t1.value, gemm1_launches=n1.value, gemm2_ms=t2.value,
-                gemm2_launches=n2.value, kernel_launches=nk.value)
+                gemm2_launches=n2.value, poisson_ms=t3.value, poisson_calls=n3.value,
+                kernel_launches=nk.value)
 
 
 def lrdm_destroy(ctx) -> None:
@@ -327,8 +331,19 @@ class Context:
         _check("lrdm_apply", code)
         return coeff, s_rel
 
-    def backward(self, fbar: List, want_eps=True, stream=None):
+    def backward(self, fbar: List, want_eps=True, stream=None, out=None):
+        """Adjoint of the most recent gateaux call.  ``out`` = (vbar, eps_bar,
+        occ_bar) from an earlier call may be passed back to reuse its buffers."""
         torch = self.torch
+        if out is not None:
+            vbar, eb, ob = out
+            code = lrdm_backward(self.handle, [f.data_ptr() if f is not None else 0 for f in fbar],
+                                 [v.data_ptr() if v is not None else 0 for v in vbar],
+                                 [e.data_ptr() if e is not None else 0 for e in eb] if want_eps else None,
+                                 [o.data_ptr() if o is not None else 0 for o in ob] if want_eps else None,
+                                 self._stream(stream))
+            _check("lrdm_backward", code)
+            return vbar, eb, ob
         vbar = [torch.empty_like(f) if f is not None else None for f in fbar]
         eb, ob = [], []
         ebp, obp = [], []

@@ -20,9 +20,11 @@
 // which the kernel raises the timeout status bit, drains its own copies and
 // MMAs, frees its tensor memory and returns.
 #include "lrdm_internal.h"
+#include "tc_problem.h"
 #include "tc_ptx.cuh"
 
 #include <cudaTypedefs.h>
+#include <string.h>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -137,38 +139,53 @@ __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 
 // GEMM2: response contraction with the row-dot epilogue
 // ===========================================================================
 
+// One grouped launch covers several problems (systems / spin channels); slot
+// q of the launch is problem pid[q] with K[q] directions, items
+// [begin[q], begin[q + 1]).  Slots are ordered by decreasing item cost.
 struct G2Params {
-  int K, ns_pad, nR, NJ;
-  int kgroup;              // directions that share one Psi row block side by side
-  long long Ng;
-  const void* psi0;        // epilogue Psi rows: bf16 hi (BF16X3) or fp32 (TF32), [Ng_pad][ns_pad]
-  const void* psi1;        // bf16 lo (BF16X3)
-  double factor;
-  const void* v;
-  long long v_stride;
-  void* out;
-  long long out_stride;
+  const TcProblem* probs;
+  int nslot;
+  int begin[TC_MAX_SLOTS + 1];
+  int pid[TC_MAX_SLOTS];
+  int K[TC_MAX_SLOTS];
+  int kgroup[TC_MAX_SLOTS];         // directions that share one Psi row block side by side
+  double factor[TC_MAX_SLOTS];
+  const void* v[TC_MAX_SLOTS];
+  long long v_stride[TC_MAX_SLOTS];
+  void* out[TC_MAX_SLOTS];
+  long long out_stride[TC_MAX_SLOTS];
   int out_io, out_is_io;
   int* status;
 };
 
-// Item order: groups of kgroup directions, row block, direction within the
-// group -- the items of one row block run side by side and share its Psi rows
-// through L2, while only kgroup matrices X''_k compete for L2 at a time.
-__device__ __forceinline__ void g2_item(const G2Params& P, int item, int& k, int& R) {
-  const int per = P.nR * P.kgroup;
-  const int kg = item / per;
-  const int rem = item - kg * per;
-  const int g = min(P.kgroup, P.K - kg * P.kgroup);
+__device__ __forceinline__ int find_slot(const int* begin, int nslot, int item) {
+  int q = 0;
+  while (q + 1 < nslot && item >= begin[q + 1]) ++q;
+  return q;
+}
+
+// Item order within a problem: groups of kgroup directions, row block,
+// direction within the group -- the items of one row block run side by side
+// and share its Psi rows through L2, while only kgroup matrices X''_k compete
+// for L2 at a time.
+__device__ __forceinline__ const TcProblem* g2_item(const G2Params& P, int item, int& q, int& k,
+                                                    int& R) {
+  q = find_slot(P.begin, P.nslot, item);
+  const TcProblem* pr = P.probs + P.pid[q];
+  const int local = item - P.begin[q];
+  const int G = P.kgroup[q], K = P.K[q];
+  const int per = pr->nR * G;
+  const int kg = local / per;
+  const int rem = local - kg * per;
+  const int g = min(G, K - kg * G);
   R = rem / g;
-  k = kg * P.kgroup + (rem - R * g);
+  k = kg * G + (rem - R * g);
+  return pr;
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_gemm2_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-               const G2Params P) {
+    k_gemm2_tc(const __grid_constant__ G2Params P) {
   using T = Tr<PREC>;
   constexpr int STAGES = T::STAGES, PARTS = T::PARTS, BK = T::BK;
   constexpr int SB = stage_bytes<PREC>();
@@ -176,7 +193,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Bars B = carve<STAGES>(smem + STAGES * SB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int items = P.K * P.nR;
+  const int items = P.begin[P.nslot];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -203,27 +220,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    ptx::prefetch_tmap(&mA0);
-    ptx::prefetch_tmap(&mB0);
+    for (int q = 0; q < P.nslot; ++q) {
+      const TcProblem* pr = P.probs + P.pid[q];
+      ptx::tmap_acquire(&pr->g2a0);
+      ptx::tmap_acquire(&pr->g2b0);
+      if (PARTS == 2) {
+        ptx::tmap_acquire(&pr->g2a1);
+        ptx::tmap_acquire(&pr->g2b1);
+      }
+    }
     int s = 0;
     uint32_t ph = 0;
     int pending[STAGES];
     for (int i = 0; i < STAGES; ++i) pending[i] = -1;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
-      int k, R;
-      g2_item(P, item, k, R);
+      int q, k, R;
+      const TcProblem* pr = g2_item(P, item, q, k, R);
+      const int NJ = pr->NJ, ns_pad = pr->ns_pad;
+      const CUtensorMap *mA0 = &pr->g2a0, *mA1 = &pr->g2a1, *mB0 = &pr->g2b0, *mB1 = &pr->g2b1;
       bool ok = true;
-      for (int J = 0; J < P.NJ && ok; ++J) {
-        const int nch = min((J + 1) * BN, P.ns_pad) / BK;
+      for (int J = 0; J < NJ && ok; ++J) {
+        const int nch = min((J + 1) * BN, ns_pad) / BK;
         for (int ic = 0; ic < nch; ++ic) {
           if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
           uint8_t* st = smem + s * SB;
           ptx::mbar_arrive_expect_tx(&B.full[s], SB);
-          ptx::tma_load_2d(st, &mA0, &B.full[s], ic * BK, R * BM);
-          if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, &mA1, &B.full[s], ic * BK, R * BM);
-          ptx::tma_load_3d(st + PARTS * TILE_A, &mB0, &B.full[s], ic * BK, J * BN, k);
+          ptx::tma_load_2d(st, mA0, &B.full[s], ic * BK, R * BM);
+          if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, mA1, &B.full[s], ic * BK, R * BM);
+          ptx::tma_load_3d(st + PARTS * TILE_A, mB0, &B.full[s], ic * BK, J * BN, k);
           if (PARTS == 2)
-            ptx::tma_load_3d(st + PARTS * TILE_A + TILE_B, &mB1, &B.full[s], ic * BK, J * BN, k);
+            ptx::tma_load_3d(st + PARTS * TILE_A + TILE_B, mB1, &B.full[s], ic * BK, J * BN, k);
           pending[s] = (int)ph;
           if (++s == STAGES) { s = 0; ph ^= 1; }
         }
@@ -238,11 +264,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t ph = 0, aph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      for (int J = 0; J < P.NJ && ok; ++J) {
+      int q, k, R;
+      const TcProblem* pr = g2_item(P, item, q, k, R);
+      const int NJ = pr->NJ, ns_pad = pr->ns_pad;
+      for (int J = 0; J < NJ && ok; ++J) {
         if (!wait1(&B.acc_empty[a], aph ^ 1, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(a * BN);
-        const int nch = min((J + 1) * BN, P.ns_pad) / BK;
+        const int nch = min((J + 1) * BN, ns_pad) / BK;
         for (int ic = 0; ic < nch; ++ic) {
           if (!wait1(&B.full[s], ph, B, P.status)) { ok = false; break; }
           ptx::tc_fence_after();
@@ -259,31 +288,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     wait_drain(B.drain, 0);
   } else if (warp >= 2) {
     // ---------------- row-dot epilogue (TMEM lane quarter = warp % 4) ----------------
-    const int q = warp & 3;
-    const int row = q * 32 + lane;
+    const int lq = warp & 3;
+    const int row = lq * 32 + lane;
     int a = 0;
     uint32_t aph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k, R;
-      g2_item(P, item, k, R);
+      int q, k, R;
+      const TcProblem* pr = g2_item(P, item, q, k, R);
+      const int NJ = pr->NJ, ns_pad = pr->ns_pad;
+      const long long Ng = pr->Ng;
+      const void* psi0 = pr->psi0;
+      const void* psi1 = pr->psi1;
       const long long r = (long long)R * BM + row;
       double acc_row = 0.0;
-      for (int J = 0; J < P.NJ; ++J) {
+      for (int J = 0; J < NJ; ++J) {
         if (!waitw(&B.acc_full[a], aph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
         float part = 0.f;
-        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+        const uint32_t tb = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * BN);
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
           float v[32];
           ptx::tmem_ld32(tb + c * 32, v);
           const int j0 = J * BN + c * 32;
-          if (r < P.Ng && j0 < P.ns_pad) {
-            const long long o = r * P.ns_pad + j0;
+          if (r < Ng && j0 < ns_pad) {
+            const long long o = r * ns_pad + j0;
             if (PREC == LRDM_BF16X3) {
-              const uint4* ph = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(P.psi0) + o);
-              const uint4* pl = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(P.psi1) + o);
+              const uint4* ph = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(psi0) + o);
+              const uint4* pl = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(psi1) + o);
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const uint4 h = __ldg(ph + u), l = __ldg(pl + u);
@@ -295,7 +328,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
               }
             } else {
-              const float4* pf = reinterpret_cast<const float4*>(static_cast<const float*>(P.psi0) + o);
+              const float4* pf = reinterpret_cast<const float4*>(static_cast<const float*>(psi0) + o);
 #pragma unroll
               for (int u = 0; u < 8; ++u) {
                 const float4 x = __ldg(pf + u);
@@ -311,17 +344,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (++a == 2) { a = 0; aph ^= 1; }
       }
       if (!ok) break;
-      if (r < P.Ng) {
-        const double d = P.factor * acc_row;
-        const long long o = (long long)k * P.out_stride + r;
+      if (r < Ng) {
+        const double d = P.factor[q] * acc_row;
+        const long long o = (long long)k * P.out_stride[q] + r;
         if (P.out_is_io) {
-          const long long ov = (long long)k * P.v_stride + r;
+          const long long ov = (long long)k * P.v_stride[q] + r;
           if (P.out_io == LRDM_DTYPE_F64)
-            static_cast<double*>(P.out)[o] = d - static_cast<const double*>(P.v)[ov];
+            static_cast<double*>(P.out[q])[o] = d - static_cast<const double*>(P.v[q])[ov];
           else
-            static_cast<float*>(P.out)[o] = (float)(d - (double)static_cast<const float*>(P.v)[ov]);
+            static_cast<float*>(P.out[q])[o] = (float)(d - (double)static_cast<const float*>(P.v[q])[ov]);
         } else {
-          static_cast<float*>(P.out)[o] = (float)d;
+          static_cast<float*>(P.out[q])[o] = (float)d;
         }
       }
     }
@@ -362,28 +395,38 @@ struct G1Cfg {
 };
 
 struct G1Params {
-  int K, ns, ns_pad, nI, NJ, ntiles, nch;
-  const float* a;          // weights of this channel, direction stride a_stride
-  long long a_stride;
-  float* X;                // [K][ns_pad][ns_pad]
+  const TcProblem* probs;
+  int nslot;
+  int begin[TC_MAX_SLOTS + 1];
+  int pid[TC_MAX_SLOTS];
+  int K[TC_MAX_SLOTS];
+  float* X[TC_MAX_SLOTS];           // [K][ns_pad][ns_pad] per slot
   int* status;
 };
 
-// Items are ordered with the direction fastest: the K items of one (I, J)
-// tile run side by side on different SMs and stream the same Psi^T tiles
-// through L2 at the same time.
-__device__ __forceinline__ void g1_item(const G1Params& P, int item, int& k, int& I, int& J) {
-  int idx = item / P.K;
-  k = item - idx * P.K;
+// Items of a problem are ordered with the direction fastest: the K items of
+// one (I, J) tile run side by side on different SMs and stream the same Psi^T
+// tiles through L2 at the same time.
+__device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item, int& q, int& k,
+                                                    int& I, int& J) {
+  q = find_slot(P.begin, P.nslot, item);
+  const TcProblem* pr = P.probs + P.pid[q];
+  int idx = item - P.begin[q];
+  const int K = P.K[q];
+  const int t = idx / K;
+  k = idx - t * K;
+  idx = t;
+  const int nI = pr->nI;
   int j = 0;
   for (;;) {
-    const int cnt = min(2 * (j + 1), P.nI);     // i-blocks of 128 below the end of j-block j
+    const int cnt = min(2 * (j + 1), nI);     // i-blocks of 128 below the end of j-block j
     if (idx < cnt) break;
     idx -= cnt;
     ++j;
   }
   J = j;
   I = idx;
+  return pr;
 }
 
 // Scales one 16-byte chunk (8 bf16 hi + 8 bf16 lo, or 4 fp32) of the A row in
@@ -422,9 +465,7 @@ __device__ __forceinline__ void scale_chunk(uint32_t raw, uint32_t sc) {
 
 template <int PREC>
 __global__ void __launch_bounds__(G1_THREADS, 1)
-    k_gemm1_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-               const G1Params P) {
+    k_gemm1_tc(const __grid_constant__ G1Params P) {
   using C = G1Cfg<PREC>;
   constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::STRIDE;
   constexpr int TX = PARTS * (TILE_A + TILE_B) + BK * 4;   // bytes landing per stage
@@ -432,8 +473,7 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Bars B = carve<STAGES>(smem + STAGES * SB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int items = P.K * P.ntiles;
-  const int nseg = (P.nch + G1_SEG - 1) / G1_SEG;
+  const int items = P.begin[P.nslot];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -461,26 +501,35 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    ptx::prefetch_tmap(&mA0);
-    ptx::prefetch_tmap(&mB0);
+    for (int q = 0; q < P.nslot; ++q) {
+      const TcProblem* pr = P.probs + P.pid[q];
+      ptx::tmap_acquire(&pr->g1a0);
+      ptx::tmap_acquire(&pr->g1b0);
+      if (PARTS == 2) {
+        ptx::tmap_acquire(&pr->g1a1);
+        ptx::tmap_acquire(&pr->g1b1);
+      }
+    }
     int s = 0;
     uint32_t ph = 0;
     int pending[STAGES];
     for (int i = 0; i < STAGES; ++i) pending[i] = -1;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k, I, J;
-      g1_item(P, item, k, I, J);
-      const float* wk = P.a + (long long)k * P.a_stride;
-      for (int rc = 0; rc < P.nch; ++rc) {
+      int q, k, I, J;
+      const TcProblem* pr = g1_item(P, item, q, k, I, J);
+      const float* wk = pr->a + (long long)k * pr->a_stride;
+      const int nch = pr->nch;
+      const CUtensorMap *mA0 = &pr->g1a0, *mA1 = &pr->g1a1, *mB0 = &pr->g1b0, *mB1 = &pr->g1b1;
+      for (int rc = 0; rc < nch; ++rc) {
         if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
         uint8_t* st = smem + s * SB;
         ptx::mbar_arrive_expect_tx(&B.full[s], TX);
-        ptx::tma_load_4d(st, &mA0, &B.full[s], 0, 0, rc, I);
-        if (PARTS == 2) ptx::tma_load_4d(st + TILE_A, &mA1, &B.full[s], 0, 0, rc, I);
-        ptx::tma_load_4d(st + C::B_OFF, &mB0, &B.full[s], 0, 0, rc, J * (BN / 128));
+        ptx::tma_load_4d(st, mA0, &B.full[s], 0, 0, rc, I);
+        if (PARTS == 2) ptx::tma_load_4d(st + TILE_A, mA1, &B.full[s], 0, 0, rc, I);
+        ptx::tma_load_4d(st + C::B_OFF, mB0, &B.full[s], 0, 0, rc, J * (BN / 128));
         if (PARTS == 2)
-          ptx::tma_load_4d(st + C::B_OFF + TILE_B, &mB1, &B.full[s], 0, 0, rc, J * (BN / 128));
+          ptx::tma_load_4d(st + C::B_OFF + TILE_B, mB1, &B.full[s], 0, 0, rc, J * (BN / 128));
         ptx::bulk_load(st + C::SC_OFF, wk + (long long)rc * BK, BK * 4, &B.full[s]);
         pending[s] = (int)ph;
         if (++s == STAGES) { s = 0; ph ^= 1; }
@@ -494,11 +543,15 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
     uint32_t ph = 0, bph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      int q, k, I, J;
+      const TcProblem* pr = g1_item(P, item, q, k, I, J);
+      const int nch = pr->nch;
+      const int nseg = (nch + G1_SEG - 1) / G1_SEG;
       for (int sg = 0; sg < nseg && ok; ++sg) {
         if (!wait1(&B.acc_empty[b], bph ^ 1, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(b * BN);
-        const int r0 = sg * G1_SEG, r1 = min(P.nch, r0 + G1_SEG);
+        const int r0 = sg * G1_SEG, r1 = min(nch, r0 + G1_SEG);
         for (int rc = r0; rc < r1; ++rc) {
           if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
           ptx::tc_fence_after();
@@ -515,20 +568,22 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
     wait_drain(B.drain, 0);
   } else if (warp >= 2) {
     // ---- weighting of the A tiles, segment accumulation, tile epilogue ----
-    const int q = warp & 3;                 // TMEM lane quarter
+    const int lq = warp & 3;                // TMEM lane quarter
     const int half = (warp - 2) >> 2;       // columns [128 half, 128 half + 128) of the tile
-    const int row = q * 32 + lane;
+    const int row = lq * 32 + lane;
     int s = 0, b = 0;
     uint32_t ph = 0, bph = 0;
     bool ok = true;
     float sum[128];
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int k, I, J;
-      g1_item(P, item, k, I, J);
+      int q, k, I, J;
+      const TcProblem* pr = g1_item(P, item, q, k, I, J);
+      const int nch = pr->nch, ns = pr->ns, ns_pad = pr->ns_pad;
+      const int nseg = (nch + G1_SEG - 1) / G1_SEG;
 #pragma unroll
       for (int c = 0; c < 128; ++c) sum[c] = 0.f;
       int flushed = 0;                      // segments already added into sum[]
-      for (int rc = 0; rc < P.nch; ++rc) {
+      for (int rc = 0; rc < nch; ++rc) {
         if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
         const uint32_t st = ptx::smem_u32(smem + s * SB);
         const uint32_t r0 = st + row * ROWB;
@@ -549,11 +604,11 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
         // add a finished segment into the running sums once the weighting is
         // G1_LAG stages ahead of its end (so the MMAs keep being fed)
         const int ready_seg = (rc + 1 - G1_LAG) / G1_SEG;   // segments whose end is >= G1_LAG behind
-        const bool last = rc + 1 == P.nch;
+        const bool last = rc + 1 == nch;
         while (flushed < nseg && (flushed < ready_seg || last)) {
           if (!waitw(&B.acc_full[b], bph, B, P.status)) { ok = false; break; }
           ptx::tc_fence_after();
-          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * 128);
+          const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * BN + half * 128);
 #pragma unroll
           for (int c8 = 0; c8 < 8; ++c8) {
             float v[16];
@@ -572,15 +627,15 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
       if (!ok) break;
       // epilogue: X[i][j] and X[j][i] for i <= j of this tile
       const int i = I * BM + row;
-      if (i < P.ns) {
-        float* Xk = P.X + (long long)k * P.ns_pad * P.ns_pad;
+      if (i < ns) {
+        float* Xk = P.X[q] + (long long)k * ns_pad * ns_pad;
         const int j0 = J * BN + half * 128;
 #pragma unroll
         for (int c = 0; c < 128; ++c) {
           const int j = j0 + c;
-          if (j >= i && j < P.ns) {
-            Xk[(long long)i * P.ns_pad + j] = sum[c];
-            Xk[(long long)j * P.ns_pad + i] = sum[c];
+          if (j >= i && j < ns) {
+            Xk[(long long)i * ns_pad + j] = sum[c];
+            Xk[(long long)j * ns_pad + i] = sum[c];
           }
         }
       }
@@ -651,101 +706,146 @@ cudaError_t set_smem(Kern k, int bytes, bool& done) {
   return e;
 }
 
+// Builds the descriptor of one (system, channel) for the tensor-core kernels.
 template <int PREC>
-cudaError_t gemm1(const Channel& c, const SysState& S, int s, int K, const float* a, void* Xout,
-                  int* status, cudaStream_t st) {
+bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   constexpr int BK = Tr<PREC>::BK;
   const int eb = PREC == LRDM_BF16X3 ? 2 : 4;
-  const void* p0 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_hi : (const void*)c.psiT32;
-  const void* p1 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_lo : (const void*)c.psiT32;
-  // Psi^T is tile-major [ns_pad/128][Ng_pad/BK][128][BK]: one A box is one
+  memset(&pr, 0, sizeof(pr));
+  // GEMM1: Psi^T tile-major [ns_pad/128][Ng_pad/BK][128][BK]: an A box is one
   // contiguous 8 KB tile, a B box two of them (consecutive state blocks).
-  CUtensorMap mA0, mA1, mB0, mB1;
-  const uint64_t dims[4] = {(uint64_t)BK, 128, (uint64_t)(S.Ng_pad / BK), (uint64_t)(c.ns_pad / 128)};
-  const uint64_t strides[3] = {(uint64_t)BK * eb, (uint64_t)128 * BK * eb,
-                               (uint64_t)128 * S.Ng_pad * eb};
-  const uint32_t boxA[4] = {(uint32_t)BK, 128, 1, 1}, boxB[4] = {(uint32_t)BK, 128, 1, BN / 128};
-  if (!make_map(&mA0, p0, eb, 4, dims, strides, boxA) || !make_map(&mA1, p1, eb, 4, dims, strides, boxA) ||
-      !make_map(&mB0, p0, eb, 4, dims, strides, boxB) || !make_map(&mB1, p1, eb, 4, dims, strides, boxB))
-    return cudaErrorInvalidValue;
-  G1Params P;
-  P.K = K;
-  P.ns = c.ns;
-  P.ns_pad = c.ns_pad;
-  P.nI = c.ns_pad / BM;
-  P.NJ = (c.ns_pad + BN - 1) / BN;
-  P.ntiles = 0;
-  for (int j = 0; j < P.NJ; ++j) P.ntiles += (2 * (j + 1) < P.nI ? 2 * (j + 1) : P.nI);
-  P.nch = (int)(S.Ng_pad / BK);
-  P.a = a;
-  P.a_stride = (long long)S.nspin * S.Ng_pad;
-  P.X = static_cast<float*>(Xout);
-  P.status = status;
-  static bool attr = false;
-  const int smem = G1Cfg<PREC>::SMEM;
-  cudaError_t e = set_smem(k_gemm1_tc<PREC>, smem, attr);
-  if (e != cudaSuccess) return e;
-  const int items = P.ntiles * K;
-  const int grid = items < num_sms() ? items : num_sms();
-  if (grid <= 0) return cudaSuccess;
-  if (getenv("LRDM_DEBUG")) {
-    cudaFuncAttributes fa;
-    cudaFuncGetAttributes(&fa, k_gemm1_tc<PREC>);
-    int nb = -1;
-    cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gemm1_tc<PREC>, G1_THREADS, smem);
-    fprintf(stderr, "gemm1: regs %d local %zu maxthreads %d smem %d occupancy %d (%s)\n", fa.numRegs,
-            fa.localSizeBytes, fa.maxThreadsPerBlock, smem, nb, cudaGetErrorString(oe));
+  const void* t0 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_hi : (const void*)c.psiT32;
+  const void* t1 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_lo : (const void*)c.psiT32;
+  const uint64_t d1[4] = {(uint64_t)BK, 128, (uint64_t)(S.Ng_pad / BK), (uint64_t)(c.ns_pad / 128)};
+  const uint64_t s1[3] = {(uint64_t)BK * eb, (uint64_t)128 * BK * eb, (uint64_t)128 * S.Ng_pad * eb};
+  const uint32_t bA1[4] = {(uint32_t)BK, 128, 1, 1}, bB1[4] = {(uint32_t)BK, 128, 1, BN / 128};
+  // GEMM2: Psi rows [Ng_pad][ns_pad] (A) and X'' [k_max][j][i] (B).
+  const void* r0 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_hi : (const void*)c.psiR32;
+  const void* r1 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_lo : (const void*)c.psiR32;
+  const void* x0 = c.Xpp;
+  const void* x1 = PREC == LRDM_BF16X3 ? c.Xpp_lo : c.Xpp;
+  const uint64_t dA2[2] = {(uint64_t)c.ns_pad, (uint64_t)S.Ng_pad};
+  const uint64_t sA2[1] = {(uint64_t)c.ns_pad * eb};
+  const uint32_t bA2[2] = {(uint32_t)BK, (uint32_t)BM};
+  const uint64_t dB2[3] = {(uint64_t)c.ns_pad, (uint64_t)c.ns_pad, (uint64_t)S.kmax};
+  const uint64_t sB2[2] = {(uint64_t)c.ns_pad * eb, (uint64_t)c.ns_pad * c.ns_pad * eb};
+  const uint32_t bB2[3] = {(uint32_t)BK, (uint32_t)BN, 1};
+  if (!make_map(&pr.g1a0, t0, eb, 4, d1, s1, bA1) || !make_map(&pr.g1a1, t1, eb, 4, d1, s1, bA1) ||
+      !make_map(&pr.g1b0, t0, eb, 4, d1, s1, bB1) || !make_map(&pr.g1b1, t1, eb, 4, d1, s1, bB1) ||
+      !make_map(&pr.g2a0, r0, eb, 2, dA2, sA2, bA2) || !make_map(&pr.g2a1, r1, eb, 2, dA2, sA2, bA2) ||
+      !make_map(&pr.g2b0, x0, eb, 3, dB2, sB2, bB2) || !make_map(&pr.g2b1, x1, eb, 3, dB2, sB2, bB2))
+    return false;
+  pr.Ng = S.Ng;
+  pr.a_stride = (long long)S.nspin * S.Ng_pad;
+  pr.a = static_cast<const float*>(S.a) + (size_t)ch * S.Ng_pad;
+  pr.psi0 = r0;
+  pr.psi1 = r1;
+  pr.ns = c.ns;
+  pr.ns_pad = c.ns_pad;
+  pr.nI = c.ns_pad / BM;
+  pr.NJ = (c.ns_pad + BN - 1) / BN;
+  pr.ntiles = 0;
+  for (int j = 0; j < pr.NJ; ++j) pr.ntiles += (2 * (j + 1) < pr.nI ? 2 * (j + 1) : pr.nI);
+  pr.nch = (int)(S.Ng_pad / BK);
+  pr.nR = (int)(S.Ng_pad / BM);
+  pr.kmax = S.kmax;
+  return true;
+}
+
+// Slots in decreasing order of per-item cost (longest items first, so that a
+// persistent grid's round-robin assignment ends evenly).
+void order_slots(const TcEntry* e, int n, int gemm, int* order) {
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 1; i < n; ++i) {
+    int t = order[i], j = i;
+    auto cost = [&](int x) {
+      const TcProblem& p = *e[x].host;
+      return gemm == 1 ? (double)p.nch : (double)p.ns_pad * p.ns_pad;
+    };
+    while (j > 0 && cost(order[j - 1]) < cost(t)) {
+      order[j] = order[j - 1];
+      --j;
+    }
+    order[j] = t;
   }
-  k_gemm1_tc<PREC><<<grid, G1_THREADS, smem, st>>>(mA0, mA1, mB0, mB1, P);
-  return cudaGetLastError();
 }
 
 template <int PREC>
-cudaError_t gemm2(const Channel& c, const SysState& S, int K, double factor, const void* v,
-                  long long v_stride, void* out, long long out_stride, int out_io, int out_is_io,
-                  int* status, cudaStream_t st) {
-  constexpr int BK = Tr<PREC>::BK;
-  const int eb = PREC == LRDM_BF16X3 ? 2 : 4;
-  const void* a0 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_hi : (const void*)c.psiR32;
-  const void* a1 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_lo : (const void*)c.psiR32;
-  const void* b0 = c.Xpp;
-  const void* b1 = PREC == LRDM_BF16X3 ? c.Xpp_lo : c.Xpp;
-  CUtensorMap mA0, mA1, mB0, mB1;
-  const uint64_t dA[2] = {(uint64_t)c.ns_pad, (uint64_t)S.Ng_pad};
-  const uint64_t sA[1] = {(uint64_t)c.ns_pad * eb};
-  const uint32_t boxA[2] = {(uint32_t)BK, (uint32_t)BM};
-  const uint64_t dB[3] = {(uint64_t)c.ns_pad, (uint64_t)c.ns_pad, (uint64_t)K};
-  const uint64_t sB[2] = {(uint64_t)c.ns_pad * eb, (uint64_t)c.ns_pad * c.ns_pad * eb};
-  const uint32_t boxB[3] = {(uint32_t)BK, (uint32_t)BN, 1};
-  if (!make_map(&mA0, a0, eb, 2, dA, sA, boxA) || !make_map(&mA1, a1, eb, 2, dA, sA, boxA) ||
-      !make_map(&mB0, b0, eb, 3, dB, sB, boxB) || !make_map(&mB1, b1, eb, 3, dB, sB, boxB))
-    return cudaErrorInvalidValue;
-  G2Params P;
-  P.K = K;
-  P.ns_pad = c.ns_pad;
-  P.nR = (int)(S.Ng_pad / BM);
-  P.kgroup = K < 2 ? K : 2;
-  P.NJ = (c.ns_pad + BN - 1) / BN;
-  P.Ng = S.Ng;
-  P.psi0 = a0;
-  P.psi1 = a1;
-  P.factor = factor;
-  P.v = v;
-  P.v_stride = v_stride;
-  P.out = out;
-  P.out_stride = out_stride;
-  P.out_io = out_io;
-  P.out_is_io = out_is_io;
-  P.status = status;
+cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st) {
+  static bool attr = false;
+  const int smem = G1Cfg<PREC>::SMEM;
+  cudaError_t err = set_smem(k_gemm1_tc<PREC>, smem, attr);
+  if (err != cudaSuccess) return err;
+  for (int base = 0; base < n; base += TC_MAX_SLOTS) {
+    const int m = n - base < TC_MAX_SLOTS ? n - base : TC_MAX_SLOTS;
+    int order[TC_MAX_SLOTS];
+    order_slots(e + base, m, 1, order);
+    G1Params P;
+    memset(&P, 0, sizeof(P));
+    P.status = status;
+    int items = 0, q = 0;
+    for (int t = 0; t < m; ++t) {
+      const TcEntry& x = e[base + order[t]];
+      if (x.K <= 0) continue;
+      P.probs = x.dev_base;
+      P.pid[q] = x.pid;
+      P.K[q] = x.K;
+      P.X[q] = static_cast<float*>(x.X);
+      P.begin[q] = items;
+      items += x.host->ntiles * x.K;
+      ++q;
+    }
+    P.nslot = q;
+    P.begin[q] = items;
+    if (items == 0) continue;
+    const int grid = items < num_sms() ? items : num_sms();
+    k_gemm1_tc<PREC><<<grid, G1_THREADS, smem, st>>>(P);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+template <int PREC>
+cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int* status,
+                        cudaStream_t st) {
   static bool attr = false;
   const int smem = smem_bytes<PREC>();
-  cudaError_t e = set_smem(k_gemm2_tc<PREC>, smem, attr);
-  if (e != cudaSuccess) return e;
-  const int items = K * P.nR;
-  const int grid = items < num_sms() ? items : num_sms();
-  if (grid <= 0) return cudaSuccess;
-  k_gemm2_tc<PREC><<<grid, NTHREADS, smem, st>>>(mA0, mA1, mB0, mB1, P);
-  return cudaGetLastError();
+  cudaError_t err = set_smem(k_gemm2_tc<PREC>, smem, attr);
+  if (err != cudaSuccess) return err;
+  for (int base = 0; base < n; base += TC_MAX_SLOTS) {
+    const int m = n - base < TC_MAX_SLOTS ? n - base : TC_MAX_SLOTS;
+    int order[TC_MAX_SLOTS];
+    order_slots(e + base, m, 2, order);
+    G2Params P;
+    memset(&P, 0, sizeof(P));
+    P.out_io = out_io;
+    P.out_is_io = out_is_io;
+    P.status = status;
+    int items = 0, q = 0;
+    for (int t = 0; t < m; ++t) {
+      const TcEntry& x = e[base + order[t]];
+      if (x.K <= 0) continue;
+      P.probs = x.dev_base;
+      P.pid[q] = x.pid;
+      P.K[q] = x.K;
+      P.kgroup[q] = x.K < 2 ? x.K : 2;
+      P.factor[q] = x.factor;
+      P.v[q] = x.v;
+      P.v_stride[q] = x.v_stride;
+      P.out[q] = x.out;
+      P.out_stride[q] = x.out_stride;
+      P.begin[q] = items;
+      items += x.host->nR * x.K;
+      ++q;
+    }
+    P.nslot = q;
+    P.begin[q] = items;
+    if (items == 0) continue;
+    const int grid = items < num_sms() ? items : num_sms();
+    k_gemm2_tc<PREC><<<grid, NTHREADS, smem, st>>>(P);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -759,22 +859,20 @@ bool tc_supported() {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-cudaError_t launch_gemm1_tc(int prec, const Channel& c, const SysState& S, int s, int K,
-                            const float* a, void* Xout, int* status, cudaStream_t st) {
-  if (K == 0) return cudaSuccess;
-  if (prec == LRDM_BF16X3) return gemm1<LRDM_BF16X3>(c, S, s, K, a, Xout, status, st);
-  return gemm1<LRDM_TF32>(c, S, s, K, a, Xout, status, st);
+bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcProblem& pr) {
+  if (prec == LRDM_BF16X3) return build_problem<LRDM_BF16X3>(c, S, ch, pr);
+  return build_problem<LRDM_TF32>(c, S, ch, pr);
 }
 
-cudaError_t launch_gemm2_tc(int prec, const Channel& c, const SysState& S, int K, double factor,
-                            const void* v, long long v_stride, void* out, long long out_stride,
-                            int out_io_dtype, int out_is_io, int* status, cudaStream_t st) {
-  if (K == 0) return cudaSuccess;
-  if (prec == LRDM_BF16X3)
-    return gemm2<LRDM_BF16X3>(c, S, K, factor, v, v_stride, out, out_stride, out_io_dtype,
-                              out_is_io, status, st);
-  return gemm2<LRDM_TF32>(c, S, K, factor, v, v_stride, out, out_stride, out_io_dtype, out_is_io,
-                          status, st);
+cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st) {
+  if (prec == LRDM_BF16X3) return gemm1_group<LRDM_BF16X3>(e, n, status, st);
+  return gemm1_group<LRDM_TF32>(e, n, status, st);
+}
+
+cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
+                                  int* status, cudaStream_t st) {
+  if (prec == LRDM_BF16X3) return gemm2_group<LRDM_BF16X3>(e, n, out_io, out_is_io, status, st);
+  return gemm2_group<LRDM_TF32>(e, n, out_io, out_is_io, status, st);
 }
 
 }  // namespace lrdm

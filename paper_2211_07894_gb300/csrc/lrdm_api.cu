@@ -265,7 +265,7 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
 }
 
 // V_H = F^-1[4 pi F[fft_real] / |G|^2] in place in S.fft_real (all k_max slots).
-lrdm_status hartree(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
+lrdm_status hartree_body(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
   const int fp64 = ctx->opt.prec == LRDM_FP64;
   LRDM_FFT(cufftSetStream(S.plan_r2c, st));
   LRDM_FFT(cufftSetStream(S.plan_c2r, st));
@@ -287,75 +287,142 @@ lrdm_status hartree(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
   return LRDM_OK;
 }
 
+lrdm_status hartree(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
+  int pi = prof_begin(ctx, 3, st);
+  lrdm_status rc = hartree_body(ctx, S, K, st);
+  prof_end(ctx, pi, st);
+  return rc;
+}
+
 size_t io_size(int io) { return io == LRDM_DTYPE_F64 ? 8 : 4; }
 
-// GEMM1 of channel c with weights S.a -> Xdst (split partials or full matrix)
-lrdm_status gemm1(lrdm_ctx* ctx, SysState& S, int c, int K, void* Xdst, cudaStream_t st) {
+// CUDA-core GEMM1 of channel c with weights S.a -> Xdst (split partials)
+lrdm_status gemm1_simt(lrdm_ctx* ctx, SysState& S, int c, int K, void* Xdst, cudaStream_t st) {
   const int prec = ctx->opt.prec;
   Channel& ch = S.ch[c];
   const size_t csz = prec == LRDM_FP64 ? 8 : 4;
   const char* a = static_cast<const char*>(S.a) + (size_t)c * S.Ng_pad * csz;
   int pi = prof_begin(ctx, 1, st);
   count(ctx, 1);
-  cudaError_t e;
-  if (is_tc(prec)) {
-    e = launch_gemm1_tc(prec, ch, S, c, K, reinterpret_cast<const float*>(a), Xdst, ctx->d_status,
-                        st);
-  } else {
-    const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
-                                        : static_cast<const void*>(ch.psi32);
-    e = launch_gemm1_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, a, (long long)S.nspin * S.Ng_pad,
-                          K, Xdst, S.nsplit, st);
-  }
+  const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
+                                      : static_cast<const void*>(ch.psi32);
+  cudaError_t e = launch_gemm1_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, a,
+                                    (long long)S.nspin * S.Ng_pad, K, Xdst, S.nsplit, st);
   prof_end(ctx, pi, st);
   return from_cuda(e);
 }
 
-// GEMM2 of channel c: out = factor * diag(Psi X'' Psi^T) (- v)
-lrdm_status gemm2(lrdm_ctx* ctx, SysState& S, int c, int K, double factor, const void* v,
-                  long long v_stride, void* out, long long out_stride, int out_is_io,
-                  cudaStream_t st) {
+// CUDA-core GEMM2 of channel c: out = factor * diag(Psi X'' Psi^T) (- v)
+lrdm_status gemm2_simt(lrdm_ctx* ctx, SysState& S, int c, int K, double factor, const void* v,
+                       long long v_stride, void* out, long long out_stride, int out_is_io,
+                       cudaStream_t st) {
   const int prec = ctx->opt.prec;
   Channel& ch = S.ch[c];
   int pi = prof_begin(ctx, 2, st);
   count(ctx, 1);
-  cudaError_t e;
-  if (is_tc(prec)) {
-    e = launch_gemm2_tc(prec, ch, S, K, factor, v, v_stride, out, out_stride, ctx->opt.io_dtype,
-                        out_is_io, ctx->d_status, st);
-  } else {
-    const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
-                                        : static_cast<const void*>(ch.psi32);
-    e = launch_gemm2_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, ch.Xpp, K, factor, v, v_stride,
-                          out, out_stride, ctx->opt.io_dtype, out_is_io, st);
-  }
+  const void* psi = prec == LRDM_FP64 ? static_cast<const void*>(ch.psi64)
+                                      : static_cast<const void*>(ch.psi32);
+  cudaError_t e = launch_gemm2_simt(prec == LRDM_FP64, psi, ch.ns, S.Ng, ch.Xpp, K, factor, v,
+                                    v_stride, out, out_stride, ctx->opt.io_dtype, out_is_io, st);
   prof_end(ctx, pi, st);
   return from_cuda(e);
 }
 
-lrdm_status forward_system(lrdm_ctx* ctx, int s, const void* v, int K, void* f, double* dmu_out,
-                           cudaStream_t st) {
-  SysState& S = ctx->sys[s];
+// One grouped tensor-core launch over the entries collected in ctx->tc_entries.
+lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
+  const int n = (int)ctx->tc_entries.size();
+  if (n == 0) return LRDM_OK;
+  int pi = prof_begin(ctx, gemm, st);
+  count(ctx, (n + TC_MAX_SLOTS - 1) / TC_MAX_SLOTS);
+  cudaError_t e = gemm == 1
+                      ? launch_gemm1_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
+                                              ctx->d_status, st)
+                      : launch_gemm2_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
+                                              ctx->opt.io_dtype, out_is_io, ctx->d_status, st);
+  prof_end(ctx, pi, st);
+  return from_cuda(e);
+}
+
+TcEntry tc_entry(lrdm_ctx* ctx, int s, int c, int K) {
+  TcEntry x;
+  const int pid = ctx->tc_pid[2 * s + c];
+  x.dev_base = ctx->tc_dev;
+  x.host = &ctx->tc_host[pid];
+  x.pid = pid;
+  x.K = K;
+  return x;
+}
+
+// The forward path of all systems: potentials and weights per system, then
+// one projection contraction over every (system, channel), mu' and the
+// Loewner scaling, then one response contraction over every (system, channel).
+lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void* const* f,
+                        double* dmu_out, cudaStream_t st) {
   const int prec = ctx->opt.prec;
   const int fp64 = prec == LRDM_FP64;
   const int io = ctx->opt.io_dtype;
-  S.last_K = K;
-  if (K == 0) return LRDM_OK;
-  LRDM_CU(launch_spin_sum(v, io, K, S.nspin, S.Ng, S.fft_real, fp64, st));
-  LRDM_CK(hartree(ctx, S, K, st));
-  LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, K, S.nspin, S.Ng,
-                            S.Ng_pad, S.w, S.a, fp64, st));
-  count(ctx, 4 + S.nspin);   // spin sum, symbol, weights, mu', Loewner scale per channel
-  for (int c = 0; c < S.nspin; ++c) LRDM_CK(gemm1(ctx, S, c, K, S.ch[c].Xpart, st));
-  const void* X[2] = {S.ch[0].Xpart, S.ch[S.nspin - 1].Xpart};
-  LRDM_CU(launch_dmu(S, X, K, fp64, S.dmu, dmu_out, ctx->d_status, st));
   const size_t isz = io_size(io);
-  for (int c = 0; c < S.nspin; ++c) {
-    LRDM_CU(launch_loewner_scale(S, c, S.ch[c].Xpart, K, fp64, S.dmu, 0, 0.0, prec, st));
-    LRDM_CK(gemm2(ctx, S, c, K, S.g, static_cast<const char*>(v) + (size_t)c * S.Ng * isz,
-                  (long long)S.nspin * S.Ng, static_cast<char*>(f) + (size_t)c * S.Ng * isz,
-                  (long long)S.nspin * S.Ng, 1, st));
+  const bool tc = is_tc(prec);
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    S.last_K = K[s];
+    if (K[s] == 0) continue;
+    LRDM_CU(launch_spin_sum(v[s], io, K[s], S.nspin, S.Ng, S.fft_real, fp64, st));
+    LRDM_CK(hartree(ctx, S, K[s], st));
+    LRDM_CU(launch_dv_weights(v[s], io, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, K[s], S.nspin,
+                              S.Ng, S.Ng_pad, S.w, S.a, fp64, st));
+    count(ctx, 3);
   }
+  // projection X_k = Psi^T diag(w dV_k) Psi
+  if (tc) {
+    ctx->tc_entries.clear();
+    for (int s = 0; s < ctx->nsys; ++s)
+      for (int c = 0; c < ctx->sys[s].nspin && K[s] > 0; ++c) {
+        TcEntry x = tc_entry(ctx, s, c, K[s]);
+        x.X = ctx->sys[s].ch[c].Xpart;
+        ctx->tc_entries.push_back(x);
+      }
+    LRDM_CK(tc_group(ctx, 1, 0, st));
+  } else {
+    for (int s = 0; s < ctx->nsys; ++s)
+      for (int c = 0; c < ctx->sys[s].nspin && K[s] > 0; ++c)
+        LRDM_CK(gemm1_simt(ctx, ctx->sys[s], c, K[s], ctx->sys[s].ch[c].Xpart, st));
+  }
+  // mu' and the Loewner scaling
+  int off = 0;
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    if (K[s] > 0) {
+      const void* X[2] = {S.ch[0].Xpart, S.ch[S.nspin - 1].Xpart};
+      LRDM_CU(launch_dmu(S, X, K[s], fp64, S.dmu, dmu_out ? dmu_out + off : nullptr, ctx->d_status, st));
+      for (int c = 0; c < S.nspin; ++c)
+        LRDM_CU(launch_loewner_scale(S, c, S.ch[c].Xpart, K[s], fp64, S.dmu, 0, 0.0, prec, st));
+      count(ctx, 1 + S.nspin);
+    }
+    off += K[s];
+  }
+  // response drho_k and f_k = drho_k - v_k
+  if (tc) ctx->tc_entries.clear();
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    for (int c = 0; c < S.nspin && K[s] > 0; ++c) {
+      const void* vc = static_cast<const char*>(v[s]) + (size_t)c * S.Ng * isz;
+      void* fc = static_cast<char*>(f[s]) + (size_t)c * S.Ng * isz;
+      const long long stride = (long long)S.nspin * S.Ng;
+      if (tc) {
+        TcEntry x = tc_entry(ctx, s, c, K[s]);
+        x.factor = S.g;
+        x.v = vc;
+        x.v_stride = stride;
+        x.out = fc;
+        x.out_stride = stride;
+        ctx->tc_entries.push_back(x);
+      } else {
+        LRDM_CK(gemm2_simt(ctx, S, c, K[s], S.g, vc, stride, fc, stride, 1, st));
+      }
+    }
+  }
+  if (tc) LRDM_CK(tc_group(ctx, 2, 1, st));
   return LRDM_OK;
 }
 
@@ -372,6 +439,7 @@ void free_ctx(lrdm_ctx* ctx) {
     if (S.plan_r2c) cufftDestroy(S.plan_r2c);
     if (S.plan_c2r) cufftDestroy(S.plan_c2r);
   }
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
   delete[] ctx->sys;
@@ -467,6 +535,29 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
       ctx->inv_trace[s] = tr != 0.0 ? 1.0 / tr : 0.0;
     }
     if (rc != LRDM_OK) break;
+    if (is_tc(o.prec)) {
+      ctx->tc_pid.assign(2 * nsys, -1);
+      for (int s = 0; s < nsys && rc == LRDM_OK; ++s)
+        for (int c = 0; c < ctx->sys[s].nspin; ++c) {
+          TcProblem pr;
+          if (!build_tc_problem(o.prec, ctx->sys[s].ch[c], ctx->sys[s], c, pr)) {
+            rc = LRDM_ERR_CUDA;
+            break;
+          }
+          ctx->tc_pid[2 * s + c] = (int)ctx->tc_host.size();
+          ctx->tc_host.push_back(pr);
+        }
+      if (rc != LRDM_OK) break;
+      if ((rc = dalloc(ctx, reinterpret_cast<char**>(&ctx->tc_dev),
+                       ctx->tc_host.size() * sizeof(TcProblem), false)) != LRDM_OK)
+        break;
+      if (cudaMemcpy(ctx->tc_dev, ctx->tc_host.data(), ctx->tc_host.size() * sizeof(TcProblem),
+                     cudaMemcpyHostToDevice) != cudaSuccess) {
+        rc = LRDM_ERR_CUDA;
+        break;
+      }
+      ctx->tc_entries.reserve(2 * nsys);
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = LRDM_ERR_CUDA;
     if (cudaGetLastError() != cudaSuccess) rc = LRDM_ERR_CUDA;
   } while (0);
@@ -486,12 +577,43 @@ lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K
     if (K[s] > 0 && (!v[s] || !f_out[s])) return LRDM_ERR_INVALID_ARG;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int off = 0;
-  for (int s = 0; s < ctx->nsys; ++s) {
-    LRDM_CK(forward_system(ctx, s, v[s], K[s], f_out[s], dmu_out ? dmu_out + off : nullptr, st));
-    off += K[s];
+  // CUDA graph: captured on the first call with a given set of buffers and K's
+  // (and stream), replayed afterwards.  Not used on the legacy default stream
+  // or while profiling.
+  if (ctx->opt.use_graph && st != nullptr && !ctx->prof_on) {
+    std::vector<const void*> key;
+    key.reserve(3 * ctx->nsys + 2);
+    for (int s = 0; s < ctx->nsys; ++s) {
+      key.push_back(v[s]);
+      key.push_back(f_out[s]);
+      key.push_back(reinterpret_cast<const void*>((intptr_t)K[s]));
+    }
+    key.push_back(dmu_out);
+    key.push_back(st);
+    if (ctx->graph_exec && key == ctx->graph_key) {
+      for (int s = 0; s < ctx->nsys; ++s) ctx->sys[s].last_K = K[s];
+      return from_cuda(cudaGraphLaunch(ctx->graph_exec, st));
+    }
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+    }
+    LRDM_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    lrdm_status rc = forward_all(ctx, v, K, f_out, dmu_out, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc != LRDM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    LRDM_CU(e);
+    e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    LRDM_CU(e);
+    ctx->graph_key = key;
+    return from_cuda(cudaGraphLaunch(ctx->graph_exec, st));
   }
-  return LRDM_OK;
+  return forward_all(ctx, v, K, f_out, dmu_out, st);
 }
 
 lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, const void* f, int K,
@@ -534,29 +656,67 @@ lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* 
     if (S.last_K < 0) return LRDM_ERR_INVALID_ARG;   // no forward call yet
     if (S.last_K > 0 && (!f_bar[s] || !v_bar[s])) return LRDM_ERR_INVALID_ARG;
   }
+  const bool tc = is_tc(prec);
+  const size_t csz = fp64 ? 8 : 4;
+  // Gbar_k = g Psi^T diag(fbar_k) Psi
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    if (S.last_K > 0) {
+      LRDM_CU(launch_scale_weights(f_bar[s], io, S.last_K, S.nspin, S.Ng, S.Ng_pad, S.g, S.a, fp64, st));
+      count(ctx, 1);
+    }
+  }
+  if (tc) {
+    ctx->tc_entries.clear();
+    for (int s = 0; s < ctx->nsys; ++s)
+      for (int c = 0; c < ctx->sys[s].nspin && ctx->sys[s].last_K > 0; ++c) {
+        TcEntry x = tc_entry(ctx, s, c, ctx->sys[s].last_K);
+        x.X = ctx->sys[s].ch[c].Gpart;
+        ctx->tc_entries.push_back(x);
+      }
+    LRDM_CK(tc_group(ctx, 1, 0, st));
+  } else {
+    for (int s = 0; s < ctx->nsys; ++s)
+      for (int c = 0; c < ctx->sys[s].nspin && ctx->sys[s].last_K > 0; ++c)
+        LRDM_CK(gemm1_simt(ctx, ctx->sys[s], c, ctx->sys[s].last_K, ctx->sys[s].ch[c].Gpart, st));
+  }
+  // Ybar = L o Gbar - diag(L) T / sum L;  dVbar = w diag(Psi Ybar Psi^T) into S.a
+  if (tc) ctx->tc_entries.clear();
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    const int K = S.last_K;
+    if (K == 0) continue;
+    const double inv_tr = ctx->inv_trace[s];
+    const void* G[2] = {S.ch[0].Gpart, S.ch[S.nspin - 1].Gpart};
+    LRDM_CU(launch_trace_bar(S, G, K, fp64, S.tbar, st));
+    count(ctx, 1 + S.nspin);
+    for (int c = 0; c < S.nspin; ++c) {
+      LRDM_CU(launch_loewner_scale(S, c, S.ch[c].Gpart, K, fp64, S.tbar, 1, inv_tr, prec, st));
+      void* out = static_cast<char*>(S.a) + (size_t)c * S.Ng_pad * csz;
+      const long long stride = (long long)S.nspin * S.Ng_pad;
+      if (tc) {
+        TcEntry x = tc_entry(ctx, s, c, K);
+        x.factor = S.w;
+        x.out = out;
+        x.out_stride = stride;
+        ctx->tc_entries.push_back(x);
+      } else {
+        LRDM_CK(gemm2_simt(ctx, S, c, K, S.w, nullptr, 0, out, stride, 0, st));
+      }
+    }
+  }
+  if (tc) LRDM_CK(tc_group(ctx, 2, 0, st));
+  // vbar = V_H[sum_s dVbar] + f_x dVbar - fbar;  eps_bar, occ_bar
   for (int s = 0; s < ctx->nsys; ++s) {
     SysState& S = ctx->sys[s];
     const int K = S.last_K;
     const double inv_tr = ctx->inv_trace[s];
     if (K > 0) {
-      // Gbar_k = g Psi^T diag(fbar_k) Psi
-      LRDM_CU(launch_scale_weights(f_bar[s], io, K, S.nspin, S.Ng, S.Ng_pad, S.g, S.a, fp64, st));
-      for (int c = 0; c < S.nspin; ++c) LRDM_CK(gemm1(ctx, S, c, K, S.ch[c].Gpart, st));
-      const void* G[2] = {S.ch[0].Gpart, S.ch[S.nspin - 1].Gpart};
-      LRDM_CU(launch_trace_bar(S, G, K, fp64, S.tbar, st));
-      // Ybar = L o Gbar - diag(L) T / sum L;  dVbar = w diag(Psi Ybar Psi^T)
-      const size_t csz = fp64 ? 8 : 4;
-      for (int c = 0; c < S.nspin; ++c) {
-        LRDM_CU(launch_loewner_scale(S, c, S.ch[c].Gpart, K, fp64, S.tbar, 1, inv_tr, prec, st));
-        LRDM_CK(gemm2(ctx, S, c, K, S.w, nullptr, 0,
-                      static_cast<char*>(S.a) + (size_t)c * S.Ng_pad * csz,
-                      (long long)S.nspin * S.Ng_pad, 0, st));
-      }
-      // vbar = V_H[sum_s dVbar] + f_x dVbar - fbar
       LRDM_CU(launch_spin_sum_padded(S.a, K, S.nspin, S.Ng, S.Ng_pad, S.fft_real, fp64, st));
       LRDM_CK(hartree(ctx, S, K, st));
       LRDM_CU(launch_adjoint_potential(S.a, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, f_bar[s],
                                        io, K, S.nspin, S.Ng, S.Ng_pad, v_bar[s], fp64, st));
+      count(ctx, 3);
     }
     for (int c = 0; c < S.nspin; ++c) {
       double* eb = eps_bar ? eps_bar[2 * s + c] : nullptr;
@@ -568,6 +728,7 @@ lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* 
         continue;
       }
       LRDM_CU(launch_eps_occ_bar(S, c, K, fp64, inv_tr, ctx->opt.degen_tol, eb, ob, st));
+      count(ctx, 1);
     }
   }
   return LRDM_OK;
@@ -622,11 +783,11 @@ lrdm_status lrdm_profile_enable(lrdm_ctx* ctx, int on) {
 }
 
 lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_launches,
-                              double* gemm2_ms, long long* gemm2_launches,
-                              long long* kernel_launches, int reset) {
+                              double* gemm2_ms, long long* gemm2_launches, double* poisson_ms,
+                              long long* poisson_calls, long long* kernel_launches, int reset) {
   if (!ctx) return LRDM_ERR_INVALID_ARG;
-  double t[3] = {0, 0, 0};
-  long long n[3] = {0, 0, 0};
+  double t[4] = {0, 0, 0, 0};
+  long long n[4] = {0, 0, 0, 0};
   for (int i = 0; i < ctx->prof_n; ++i) {
     if (cudaEventSynchronize(ctx->prof_ev[2 * i + 1]) != cudaSuccess) return LRDM_ERR_CUDA;
     float ms = 0.f;
@@ -639,6 +800,8 @@ lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_
   if (gemm1_launches) *gemm1_launches = n[1];
   if (gemm2_ms) *gemm2_ms = t[2];
   if (gemm2_launches) *gemm2_launches = n[2];
+  if (poisson_ms) *poisson_ms = t[3];
+  if (poisson_calls) *poisson_calls = n[3];
   if (kernel_launches) *kernel_launches = ctx->launches;
   if (reset) {
     ctx->prof_n = 0;

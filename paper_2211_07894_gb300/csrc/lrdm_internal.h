@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/lrdm.h"
+#include "tc_problem.h"
 
 namespace lrdm {
 
@@ -89,6 +90,14 @@ struct lrdm_ctx {
   double* ls_scal = nullptr;         // [4]: r2, s_rel scratch
   double* upd_partial = nullptr;     // [UPD_BLOCKS]
   std::vector<void*> allocs;         // every device allocation, freed by lrdm_destroy
+  // tensor-core problem table: one entry per (system, channel)
+  std::vector<lrdm::TcProblem> tc_host;
+  lrdm::TcProblem* tc_dev = nullptr;
+  std::vector<int> tc_pid;           // [2 * sys + channel] -> index, -1 if absent
+  std::vector<lrdm::TcEntry> tc_entries;   // scratch list for one grouped launch
+  // CUDA graph of lrdm_gateaux_batch (use_graph)
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<const void*> graph_key;
   std::vector<double> inv_trace;     // per system 1 / sum_s sum_i L_ii
   // profiling (lrdm_profile_enable / lrdm_profile_read)
   bool prof_on = false;
@@ -172,11 +181,13 @@ cudaError_t launch_ls_static(const void* R, const void* v, const void* f, int io
                              cudaStream_t st);
 
 // ---------------- tensor-core GEMMs (k_tc.cu) ----------------
-cudaError_t launch_gemm1_tc(int prec, const Channel& c, const SysState& S, int s, int K,
-                            const float* a, void* Xout, int* status, cudaStream_t st);
-cudaError_t launch_gemm2_tc(int prec, const Channel& c, const SysState& S, int K, double factor,
-                            const void* v, long long v_stride, void* out, long long out_stride,
-                            int out_io_dtype, int out_is_io, int* status, cudaStream_t st);
+// Descriptor of channel ch of system S for the tensor-core kernels (false if a
+// tensor map cannot be encoded).
+bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcProblem& pr);
+// Grouped launches over n problems (each with its own K; K = 0 entries skipped).
+cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st);
+cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
+                                  int* status, cudaStream_t st);
 bool tc_supported();
 
 }  // namespace lrdm

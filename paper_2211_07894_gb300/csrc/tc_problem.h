@@ -1,0 +1,42 @@
+// Per-(system, channel) descriptor of the tensor-core contractions, built once
+// by lrdm_create and kept in device memory: the TMA tensor maps of both
+// contractions (which only reference context-owned buffers) and the sizes.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+namespace lrdm {
+
+struct TcProblem {
+  CUtensorMap g1a0, g1a1, g1b0, g1b1;   // GEMM1: Psi^T tile-major (A box 128 rows, B box 256)
+  CUtensorMap g2a0, g2a1, g2b0, g2b1;   // GEMM2: Psi rows (A), X'' [k_max][j][i] (B)
+  long long Ng;                          // grid points
+  long long a_stride;                    // direction stride of the GEMM1 weights
+  const float* a;                        // GEMM1 weights of this channel (direction 0)
+  const void* psi0;                      // GEMM2 epilogue rows: bf16 hi / fp32
+  const void* psi1;                      // bf16 lo
+  int ns, ns_pad, nI, NJ, ntiles, nch, nR, kmax;
+};
+
+constexpr int TC_MAX_SLOTS = 16;        // problems per grouped launch
+
+}  // namespace lrdm
+
+namespace lrdm {
+
+// One problem's share of a grouped launch (host side).
+struct TcEntry {
+  const TcProblem* dev_base = nullptr;   // device array of all problems of the context
+  const TcProblem* host = nullptr;       // host copy of this problem
+  int pid = 0;                           // index into the device array
+  int K = 0;                             // directions this call
+  void* X = nullptr;                     // GEMM1 output [K][ns_pad][ns_pad] FP32
+  double factor = 0.0;                   // GEMM2: out = factor * drho (- v)
+  const void* v = nullptr;
+  long long v_stride = 0;
+  void* out = nullptr;
+  long long out_stride = 0;
+};
+
+}  // namespace lrdm
