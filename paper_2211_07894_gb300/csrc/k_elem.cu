@@ -50,16 +50,21 @@ __global__ void k_spin_sum(const void* __restrict__ v, int io, int K, int nspin,
 // Multiplies the half-spectrum (R2C layout [K][n0][n1][n2/2+1]) by
 // 4 pi / |G|^2 / N_g (G = 0 -> 0); kind 1 replaces |G|^2 by the second-order
 // finite-difference symbol sum_d (4/h_d^2) sin^2(G_d h_d / 2).
-__global__ void k_poisson(void* __restrict__ cplx, int K, int n0, int n1, int n2, double h0,
-                          double h1, double h2, int kind, int fp64) {
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+  return __uint_as_float(t);
+}
+
+__global__ void k_poisson_table(int n0, int n1, int n2, double h0, double h1, double h2, int kind,
+                                double* __restrict__ sym) {
   const int m2n = n2 / 2 + 1;
   const long long per = (long long)n0 * n1 * m2n;
   const double inv_ng = 1.0 / ((double)n0 * n1 * n2);
   const double two_pi = 6.283185307179586;
-  GRID_STRIDE(e, (long long)K * per) {
-    long long rem = e % per;
-    int m2 = (int)(rem % m2n);
-    long long t = rem / m2n;
+  GRID_STRIDE(e, per) {
+    int m2 = (int)(e % m2n);
+    long long t = e / m2n;
     int m1 = (int)(t % n1);
     int m0 = (int)(t / n1);
     int f0 = m0 <= n0 / 2 ? m0 : m0 - n0;
@@ -73,15 +78,32 @@ __global__ void k_poisson(void* __restrict__ cplx, int K, int n0, int n1, int n2
     } else {
       q = g0 * g0 + g1 * g1 + g2 * g2;
     }
-    double sym = (f0 == 0 && f1 == 0 && f2 == 0) || q <= 0.0 ? 0.0 : 12.566370614359172 / q * inv_ng;
+    sym[e] = (f0 == 0 && f1 == 0 && f2 == 0) || q <= 0.0 ? 0.0 : 12.566370614359172 / q * inv_ng;
+  }
+}
+
+// Applies the symbol table to all K transformed fields: one thread per
+// half-complex point, looping over the fields (the symbol is read once).
+__global__ void k_poisson(void* __restrict__ cplx, int K, long long per,
+                          const double* __restrict__ sym, int fp64) {
+  GRID_STRIDE(m, per) {
+    const double sm = sym[m];
     if (fp64) {
       double2* z = static_cast<double2*>(cplx);
-      z[e].x *= sym;
-      z[e].y *= sym;
+      for (int k = 0; k < K; ++k) {
+        double2 v = z[(long long)k * per + m];
+        v.x *= sm;
+        v.y *= sm;
+        z[(long long)k * per + m] = v;
+      }
     } else {
       float2* z = static_cast<float2*>(cplx);
-      z[e].x = (float)(z[e].x * sym);
-      z[e].y = (float)(z[e].y * sym);
+      for (int k = 0; k < K; ++k) {
+        float2 v = z[(long long)k * per + m];
+        v.x = (float)(v.x * sm);
+        v.y = (float)(v.y * sm);
+        z[(long long)k * per + m] = v;
+      }
     }
   }
 }
@@ -231,6 +253,63 @@ __global__ void k_loewner_scale(const void* __restrict__ X, int acc64, int nspli
   }
 }
 
+// X'' for the tensor-core response GEMM: entry (k, row = j, col = i) =
+// c_ij L_ij (X_ij - delta_ij shift_k) (adjoint: c_ij (L_ij X_ij - delta_ij
+// L_ii shift_k inv_trace)), c = 2 / 1 / 0 for i < j / i = j / i > j, rounded to
+// TF32 (layout 1) or split into bf16 hi / lo (layout 2).  Off-diagonal products
+// in FP32 with the FP32 copy of L (the result is stored with at most 16
+// significant bits); the diagonal (mu' shift) in FP64.  One thread per four
+// consecutive columns: grid (column quads, rows, directions).
+__global__ void k_loewner_scale_tc(const float* __restrict__ X, int ns, int ld,
+                                   const float* __restrict__ Lf, const double* __restrict__ L,
+                                   const double* __restrict__ shift, int adjoint,
+                                   double inv_trace, int layout, void* __restrict__ out,
+                                   __nv_bfloat16* __restrict__ out_lo) {
+  const int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int row = blockIdx.y;
+  const int k = blockIdx.z;
+  if (c0 >= ld) return;
+  const long long o = ((long long)k * ld + row) * ld + c0;
+  const float4 x4 = *reinterpret_cast<const float4*>(X + o);
+  const float4 l4 = *reinterpret_cast<const float4*>(Lf + (long long)row * ld + c0);
+  const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, ls[4] = {l4.x, l4.y, l4.z, l4.w};
+  float v[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int i = c0 + e, j = row;
+    if (i < j && j < ns) {
+      v[e] = 2.f * ls[e] * xs[e];
+    } else if (i == j && j < ns) {
+      const double l = L[(long long)i * ns + i];
+      v[e] = (float)(adjoint ? l * (double)xs[e] - l * shift[k] * inv_trace
+                             : l * ((double)xs[e] - shift[k]));
+    } else {
+      v[e] = 0.f;
+    }
+  }
+  if (layout == 1) {
+    float4 t;
+    t.x = tf32_rna(v[0]);
+    t.y = tf32_rna(v[1]);
+    t.z = tf32_rna(v[2]);
+    t.w = tf32_rna(v[3]);
+    *reinterpret_cast<float4*>(static_cast<float*>(out) + o) = t;
+  } else {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[2], v[3]);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[0] - f01.x, v[1] - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[2] - f23.x, v[3] - f23.y);
+    uint2 hw, lw;
+    hw.x = *reinterpret_cast<const uint32_t*>(&h01);
+    hw.y = *reinterpret_cast<const uint32_t*>(&h23);
+    lw.x = *reinterpret_cast<const uint32_t*>(&l01);
+    lw.y = *reinterpret_cast<const uint32_t*>(&l23);
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out) + o) = hw;
+    *reinterpret_cast<uint2*>(out_lo + o) = lw;
+  }
+}
+
 // Backward trace terms T_k = sum_s sum_m L_mm Gbar_k,mm (the adjoint of the
 // mu' constraint) -- same reduction as k_dmu without the division.
 __global__ void k_trace_bar(DmuArgs A, int acc64, double* __restrict__ tbar) {
@@ -272,22 +351,40 @@ __global__ void k_eps_occ_bar(const void* __restrict__ X, const void* __restrict
   double eb = 0.0, ob = 0.0;
   for (int j = threadIdx.x; j < ns; j += blockDim.x) {
     double lb = 0.0;
-    for (int k = 0; k < K; ++k) {
-      double x = 0.0, gg = 0.0;
-      for (int p = 0; p < nsplit; ++p) {
-        long long o = ((long long)p * K + k) * mat + (long long)i * ldx + j;
-        x += ld_c(X, acc64, o);
-        gg += ld_c(G, acc64, o);
+    if (acc64 || i == j) {
+      for (int k = 0; k < K; ++k) {
+        double x = 0.0, gg = 0.0;
+        for (int p = 0; p < nsplit; ++p) {
+          long long o = ((long long)p * K + k) * mat + (long long)i * ldx + j;
+          x += ld_c(X, acc64, o);
+          gg += ld_c(G, acc64, o);
+        }
+        if (i == j) lb += gg * (x - dmu[k]) - tbar[k] * inv_trace * (x - dmu[k]);
+        else lb += gg * x;
       }
-      if (i == j) lb += gg * (x - dmu[k]) - tbar[k] * inv_trace * (x - dmu[k]);
-      else lb += gg * x;
+    } else {
+      // FP32 partials: the off-diagonal sum over directions in FP32
+      const float* Xf = static_cast<const float*>(X);
+      const float* Gf = static_cast<const float*>(G);
+      float acc = 0.f;
+      for (int k = 0; k < K; ++k) {
+        float x = 0.f, gg = 0.f;
+        for (int p = 0; p < nsplit; ++p) {
+          long long o = ((long long)p * K + k) * mat + (long long)i * ldx + j;
+          x += Xf[o];
+          gg += Gf[o];
+        }
+        acc = fmaf(gg, x, acc);
+      }
+      lb = (double)acc;
     }
     double de = eps[i] - eps[j];
     if (i == j) {
       ob += lb * (-(1.0 - 2.0 * occ[i]) / kT);
     } else if (fabs(de) > tau) {
-      eb += 2.0 * lb * (-L[(long long)i * ns + j] / de);
-      ob += 2.0 * lb / de;
+      const double rde = 1.0 / de;
+      eb += 2.0 * lb * (-L[(long long)i * ns + j] * rde);
+      ob += 2.0 * lb * rde;
     } else {
       double fb = 0.5 * (occ[i] + occ[j]);
       ob += 2.0 * lb * (-(1.0 - 2.0 * fb) / (2.0 * kT));
@@ -338,11 +435,17 @@ cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long 
   return cudaGetLastError();
 }
 
-cudaError_t launch_poisson_symbol(void* cplx, int K, const int* n, const double* h, int kind,
-                                  int fp64, cudaStream_t st) {
-  long long tot = (long long)K * n[0] * n[1] * (n[2] / 2 + 1);
-  k_poisson<<<grid_for(tot, 256), 256, 0, st>>>(cplx, K, n[0], n[1], n[2], h[0], h[1], h[2], kind,
-                                                 fp64);
+cudaError_t launch_poisson_table(const int* n, const double* h, int kind, double* sym,
+                                 cudaStream_t st) {
+  const long long per = (long long)n[0] * n[1] * (n[2] / 2 + 1);
+  k_poisson_table<<<grid_for(per, 256), 256, 0, st>>>(n[0], n[1], n[2], h[0], h[1], h[2], kind, sym);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_symbol(void* cplx, int K, long long per, const double* sym, int fp64,
+                                  cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  k_poisson<<<grid_for(per, 256), 256, 0, st>>>(cplx, K, per, sym, fp64);
   return cudaGetLastError();
 }
 
@@ -412,8 +515,17 @@ cudaError_t launch_loewner_scale(const SysState& S, int s, const void* Xpart, in
                                  cudaStream_t st) {
   const Channel& c = S.ch[s];
   int layout = prec == LRDM_BF16X3 ? 2 : (prec == LRDM_TF32 ? 1 : 0);
-  int ldx = layout == 0 ? c.ns : c.ns_pad;
-  int ldo = layout == 0 ? c.ns : c.ns_pad;
+  if (K == 0) return cudaSuccess;
+  if (layout != 0) {
+    const int ld = c.ns_pad;                     // multiple of 128, nsplit = 1
+    dim3 grid((ld / 4 + 127) / 128, ld, K);
+    k_loewner_scale_tc<<<grid, 128, 0, st>>>(static_cast<const float*>(Xpart), c.ns, ld, c.Lf, c.L,
+                                              shift, adjoint, inv_trace_L, layout, c.Xpp,
+                                              static_cast<__nv_bfloat16*>(c.Xpp_lo));
+    return cudaGetLastError();
+  }
+  int ldx = c.ns;
+  int ldo = c.ns;
   long long tot = (long long)K * ldo * ldo;
   k_loewner_scale<<<grid_for(tot, 256), 256, 0, st>>>(
       Xpart, acc_fp64, S.nsplit, K, c.ns, ldx, c.L, shift, adjoint, inv_trace_L, layout, ldo,

@@ -140,6 +140,16 @@ __device__ __forceinline__ double log_sinhc(double u) {
 // cancellation for near-degenerate pairs.  Log domain where a factor could overflow.
 // occ_mode: divided differences of the given occupations, midpoint derivative
 // for |eps_i - eps_j| <= degen_tol kT.
+__global__ void k_loewner_f32(const double* __restrict__ L, int ns, int ns_pad,
+                              float* __restrict__ Lf) {
+  const long long total = (long long)ns_pad * ns_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ns_pad), j = (int)(e - (long long)i * ns_pad);
+    Lf[e] = (i < ns && j < ns) ? (float)L[(long long)i * ns + j] : 0.f;
+  }
+}
+
 __global__ void k_loewner(const double* __restrict__ eps, const double* __restrict__ occ, int ns,
                           double mu, double kT, int occ_mode, double degen_tol,
                           double* __restrict__ L) {
@@ -227,6 +237,11 @@ cudaError_t launch_loewner(const double* eps, const double* occ, int ns, double 
                            int occ_mode, double degen_tol, double* L, cudaStream_t st) {
   k_loewner<<<grid_for((long long)ns * ns, 256), 256, 0, st>>>(eps, occ, ns, mu, kT, occ_mode,
                                                                 degen_tol, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loewner_f32(const double* L, int ns, int ns_pad, float* Lf, cudaStream_t st) {
+  k_loewner_f32<<<grid_for((long long)ns_pad * ns_pad, 256), 256, 0, st>>>(L, ns, ns_pad, Lf);
   return cudaGetLastError();
 }
 

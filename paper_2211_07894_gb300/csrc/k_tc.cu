@@ -1,18 +1,18 @@
 // Tensor-core (tcgen05) forms of the two contractions on sm_103a.
 //
 // GEMM1  X_k[i, j] = sum_r (a_k[r] Psi[r, i]) Psi[r, j]     (H-breve', §II.C)
-//        tile 128 (i) x 256 (j), i-blocks with i0 < j0 + 256 only (upper part);
-//        the whole grid reduction runs inside one tile, in segments of 512
-//        rows whose TMEM results are summed in FP32 registers; the a_k
-//        weighting is applied to the A tile in shared memory between its TMA
-//        load and the MMAs (the weights chunk arrives with the tiles).
+//        tile 128 (i) x 128 (j), blocks I <= J only (upper part), two
+//        directions per tile; the whole grid reduction runs inside one tile,
+//        in segments of 1024 rows whose TMEM results are summed in FP32
+//        registers; the a_k weighting is applied to the A rows between their
+//        TMA load and the MMAs, which read the weighted A from tensor memory.
 // GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
 //        tile 128 (r) x 256 (j); for each j-block the i-reduction stops at the
 //        block's end (X'' is zero below the diagonal); two TMEM accumulators so
 //        the row-dot epilogue of one j-block overlaps the MMAs of the next.
 //        Psi X'' only ever lives in tensor memory.
 //
-// Both: A and B K-major in 64-byte-swizzled shared memory, loaded by TMA;
+// Both: operands K-major in 64-byte-swizzled shared memory, loaded by TMA;
 // one thread issues tcgen05.mma, accumulators (FP32) in tensor memory, read
 // back with tcgen05.ld.  Precisions: split BF16x3 (a = a_hi + a_lo, three
 // bf16 products a_hi b_hi + a_hi b_lo + a_lo b_hi) and TF32.  Persistent
@@ -368,31 +368,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ===========================================================================
-// GEMM1: projection with the per-direction weights applied in shared memory
+// GEMM1: projection, direction weights applied on the way into tensor memory
 // ===========================================================================
 //
-// One work item = one (I, J) tile of one direction, reduced over the whole
-// grid.  The tensor cores' FP32 accumulation truncates, and over a reduction
-// of 10^5-10^6 rows that bias reaches ~1e-3 of the result; so the reduction is
-// segmented: each segment of SEG stages (SEG * BK rows) accumulates in one of
-// two TMEM buffers, after which eight warps add it into FP32 running sums held
-// in registers (round-to-nearest) while the MMAs fill the other buffer.  The
-// same eight warps apply the direction weights to the A tile of every stage
-// (in shared memory, between its TMA load and the MMAs).
+// One work item = one 128 x 128 tile (I <= J) of X for a pair of directions
+// (k0, k0 + 1), reduced over the whole grid.  Per stage the TMA brings the
+// raw Psi^T rows of block I (A) and block J (B) and both directions' weights;
+// eight warps form a_k o A for the two directions, split it into bf16 hi / lo
+// (or round it to TF32) and store it in tensor memory, from where the MMAs
+// read their A operand (B stays in shared memory).  One A / B load thus
+// serves two directions, and shared memory sees no write-back of the
+// weighted tile.
+//
+// The tensor cores' FP32 accumulation truncates, and over a reduction of
+// 10^5-10^6 rows that bias reaches ~1e-3 of the result; so the reduction is
+// segmented: each segment of SEG stages (1024 rows) accumulates from zero in
+// TMEM, after which the same eight warps add it into FP32 running sums held
+// in registers (round-to-nearest) before the next segment starts.
+//
+// TMEM columns: [0, 256) the accumulators of the two directions (128 each);
+// [256, 512) the weighted-A ring, one slot of 2 x ACOLS columns per stage.
 
-constexpr int G1_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 weighting + accumulation
-constexpr int G1_SEG = 16;          // stages per TMEM accumulation segment
-constexpr int G1_LAG = 2;           // stages the weighting runs ahead before flushing a segment
+// Warps 0-7 (warpgroups 0, 1): weighting + accumulation, 224 registers each
+// after reallocation; warpgroup 2: warp 8 TMA, warp 9 MMA and TMEM owner,
+// warps 10-11 idle, 56 registers each.  Launch: 384 x 168 = 64512 registers =
+// 256 x 224 + 128 x 56; per SM sub-partition (warps w, w + 4, w + 8):
+// 2 x 32 x 224 + 32 x 56 = 16128 <= 16384.
+constexpr int G1_THREADS = 384;
+constexpr int G1_REG_MATH = 224, G1_REG_CTRL = 56;
+static_assert(256 * G1_REG_MATH + 128 * G1_REG_CTRL == G1_THREADS * 168, "register split");
+constexpr int G1_BN = 128;              // tile width (j) = tile height (i)
+constexpr int G1_TILE = G1_BN * ROWB;   // 8 KB per operand part (128 rows x 64 bytes)
+constexpr int G1_ACOL = 256;            // first TMEM column of the weighted-A ring
 
 template <int PREC>
 struct G1Cfg {
   static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
-  static constexpr int B_OFF = PARTS * TILE_A;
-  static constexpr int SC_OFF = B_OFF + PARTS * TILE_B;
-  static constexpr int STRIDE = SC_OFF + 1024;                 // 1024-aligned stages
   static constexpr int STAGES = PREC == LRDM_BF16X3 ? 4 : 8;
+  // TMEM columns of one direction's weighted A per stage: bf16 packs two
+  // elements per column and has two parts (hi, lo); tf32 one element per column
+  static constexpr int ACOLS = BK;
+  static constexpr int SLOT = 2 * ACOLS;
+  static constexpr int B_OFF = PARTS * G1_TILE;
+  static constexpr int SC_OFF = 2 * PARTS * G1_TILE;
+  static constexpr int STRIDE = SC_OFF + 1024;                  // 1024-aligned stages
   static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
+  static constexpr int SEG = 1024 / BK;                          // stages per accumulation segment
+  static constexpr int LAG = STAGES - 1;                         // stages weighted ahead of a flush
+  static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, G1_BN);
 };
+static_assert(G1_ACOL + G1Cfg<LRDM_BF16X3>::STAGES * G1Cfg<LRDM_BF16X3>::SLOT <= 512, "TMEM budget");
+static_assert(G1_ACOL + G1Cfg<LRDM_TF32>::STAGES * G1Cfg<LRDM_TF32>::SLOT <= 512, "TMEM budget");
+static_assert(G1Cfg<LRDM_BF16X3>::LAG <= G1Cfg<LRDM_BF16X3>::STAGES, "flush lag");
 
 struct G1Params {
   const TcProblem* probs;
@@ -404,62 +431,279 @@ struct G1Params {
   int* status;
 };
 
-// Items of a problem are ordered with the direction fastest: the K items of
-// one (I, J) tile run side by side on different SMs and stream the same Psi^T
-// tiles through L2 at the same time.
-__device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item, int& q, int& k,
-                                                    int& I, int& J) {
+// Item -> slot q, first direction k0, directions nd (1 or 2), tile I <= J.
+// Direction pairs run fastest: the pairs of one tile run side by side on
+// different SMs and stream the same Psi^T rows through L2; tiles go column by
+// column, so neighbouring tiles share their B rows.
+__device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item, int& q, int& k0,
+                                                    int& nd, int& I, int& J) {
   q = find_slot(P.begin, P.nslot, item);
   const TcProblem* pr = P.probs + P.pid[q];
-  int idx = item - P.begin[q];
+  const int idx = item - P.begin[q];
   const int K = P.K[q];
-  const int t = idx / K;
-  k = idx - t * K;
-  idx = t;
-  const int nI = pr->nI;
+  const int npair = (K + 1) >> 1;
+  int t = idx / npair;
+  const int pp = idx - t * npair;
+  k0 = 2 * pp;
+  nd = min(2, K - k0);
   int j = 0;
-  for (;;) {
-    const int cnt = min(2 * (j + 1), nI);     // i-blocks of 128 below the end of j-block j
-    if (idx < cnt) break;
-    idx -= cnt;
+  while (t > j) {                   // column j holds tiles I = 0..j
+    t -= j + 1;
     ++j;
   }
   J = j;
-  I = idx;
+  I = t;
   return pr;
 }
 
-// Scales one 16-byte chunk (8 bf16 hi + 8 bf16 lo, or 4 fp32) of the A row in
-// place by the direction weights at shared address sc.
+// The weighted A operand of one stage for this thread's row: 16-byte chunks
+// 2h and 2h + 1 of the row (elements [16 h, 16 h + 16) of bf16 hi / lo input,
+// [8 h, 8 h + 8) of fp32 input) times each direction's weights, stored at TMEM
+// address ta (this warp's lane quarter, first column of the stage's slot).
 template <int PREC>
-__device__ __forceinline__ void scale_chunk(uint32_t raw, uint32_t sc) {
+__device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd, uint32_t ta) {
+  using C = G1Cfg<PREC>;
+  const uint32_t ra = st + row * ROWB;
+  const int sw = (row >> 1) & 3;                 // 64-byte swizzle of this row
   if (PREC == LRDM_BF16X3) {
-    const uint4 h = ptx::lds128(raw), l = ptx::lds128(raw + TILE_A);
-    const uint4 s0 = ptx::lds128(sc), s1 = ptx::lds128(sc + 16);
-    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-    const float w8[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
-                         __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
-                         __uint_as_float(s1.z), __uint_as_float(s1.w)};
-    uint32_t oh[4], ol[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float y0 = (bf_lo(hw[e]) + bf_lo(lw[e])) * w8[2 * e];
-      const float y1 = (bf_hi(hw[e]) + bf_hi(lw[e])) * w8[2 * e + 1];
-      const __nv_bfloat162 hi2 = __floats2bfloat162_rn(y0, y1);
-      const float2 hf = __bfloat1622float2(hi2);
-      const __nv_bfloat162 lo2 = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
-      oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
-      ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
+    for (int u = 0; u < 2; ++u) {               // one 16-byte chunk (8 elements) at a time
+      const int c = 2 * h + u;
+      const int p = c ^ sw;
+      const uint4 hv = ptx::lds128(ra + p * 16), lv = ptx::lds128(ra + G1_TILE + p * 16);
+      const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
+      float x[8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        x[2 * e] = bf_lo(hw[e]) + bf_lo(lw[e]);
+        x[2 * e + 1] = bf_hi(hw[e]) + bf_hi(lw[e]);
+      }
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        if (d >= nd) break;
+        const uint32_t sc = st + C::SC_OFF + d * C::BK * 4 + c * 8 * 4;
+        const uint4 s0 = ptx::lds128(sc), s1 = ptx::lds128(sc + 16);
+        const float w[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
+                            __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
+                            __uint_as_float(s1.z), __uint_as_float(s1.w)};
+        uint32_t oh[4], ol[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float y0 = x[2 * e] * w[2 * e], y1 = x[2 * e + 1] * w[2 * e + 1];
+          const __nv_bfloat162 hi2 = __floats2bfloat162_rn(y0, y1);
+          const float2 hf = __bfloat1622float2(hi2);
+          const __nv_bfloat162 lo2 = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
+          oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
+          ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
+        }
+        ptx::tmem_st4(ta + d * C::ACOLS + c * 4, oh);          // hi: columns [0, 16) of the direction
+        ptx::tmem_st4(ta + d * C::ACOLS + 16 + c * 4, ol);     // lo: columns [16, 32)
+      }
     }
-    ptx::sts128(raw, make_uint4(oh[0], oh[1], oh[2], oh[3]));
-    ptx::sts128(raw + TILE_A, make_uint4(ol[0], ol[1], ol[2], ol[3]));
   } else {
-    const uint4 x = ptx::lds128(raw);
-    const uint4 w = ptx::lds128(sc);
-    ptx::sts128(raw, make_uint4(__float_as_uint(tf32_round(__uint_as_float(x.x) * __uint_as_float(w.x))),
-                                __float_as_uint(tf32_round(__uint_as_float(x.y) * __uint_as_float(w.y))),
-                                __float_as_uint(tf32_round(__uint_as_float(x.z) * __uint_as_float(w.z))),
-                                __float_as_uint(tf32_round(__uint_as_float(x.w) * __uint_as_float(w.w)))));
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int p = (2 * h + u) ^ sw;
+      const uint4 v = ptx::lds128(ra + p * 16);
+      x[4 * u] = __uint_as_float(v.x);
+      x[4 * u + 1] = __uint_as_float(v.y);
+      x[4 * u + 2] = __uint_as_float(v.z);
+      x[4 * u + 3] = __uint_as_float(v.w);
+    }
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (d >= nd) break;
+      const uint32_t sc = st + C::SC_OFF + d * C::BK * 4 + h * 8 * 4;
+      const uint4 s0 = ptx::lds128(sc), s1 = ptx::lds128(sc + 16);
+      const float w[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
+                          __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
+                          __uint_as_float(s1.z), __uint_as_float(s1.w)};
+      uint32_t o[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) o[e] = __float_as_uint(tf32_round(x[e] * w[e]));
+      ptx::tmem_st8(ta + d * C::ACOLS + h * 8, o);
+    }
+  }
+}
+
+// The MMAs of one stage: for each direction d, D_d (+)= A'_d B^T over the
+// stage's BK grid rows (three bf16 products for the split form).
+template <int PREC>
+__device__ __forceinline__ void issue_g1_mmas(uint32_t tmem, uint32_t aslot, uint32_t sb, int nd,
+                                              bool first) {
+  using C = G1Cfg<PREC>;
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    if (d >= nd) break;
+    const uint32_t dt = tmem + d * G1_BN;
+    const uint32_t at = tmem + aslot + d * C::ACOLS;
+#pragma unroll
+    for (int kk = 0; kk < KSTEPS; ++kk) {     // 32-byte K steps along the swizzled B row
+      const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+      const uint64_t b0 = ptx::desc_k_sw64(sb + kk * 32);
+      if (PREC == LRDM_BF16X3) {
+        const uint64_t b1 = ptx::desc_k_sw64(sb + G1_TILE + kk * 32);
+        ptx::mma_f16_ta(dt, at + kk * 8, b0, C::IDESC, acc);        // hi x hi
+        ptx::mma_f16_ta(dt, at + kk * 8, b1, C::IDESC, 1);          // hi x lo
+        ptx::mma_f16_ta(dt, at + 16 + kk * 8, b0, C::IDESC, 1);     // lo x hi
+      } else {
+        ptx::mma_tf32_ta(dt, at + kk * 8, b0, C::IDESC, acc);
+      }
+    }
+  }
+}
+
+// ---- the roles of k_gemm1_tc ----
+
+template <int PREC>
+__device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, const Bars& B, int items) {
+  using C = G1Cfg<PREC>;
+  constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::STRIDE;
+  for (int q = 0; q < P.nslot; ++q) {
+    const TcProblem* pr = P.probs + P.pid[q];
+    ptx::tmap_acquire(&pr->g1a0);
+    if (PARTS == 2) ptx::tmap_acquire(&pr->g1a1);
+  }
+  int s = 0;
+  uint32_t ph = 0;
+  int pending[STAGES];
+  for (int i = 0; i < STAGES; ++i) pending[i] = -1;
+  bool ok = true;
+  for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    int q, k0, nd, I, J;
+    const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
+    const float* w0 = pr->a + (long long)k0 * pr->a_stride;
+    const long long wstride = pr->a_stride;
+    const int nch = pr->nch;
+    const CUtensorMap *m0 = &pr->g1a0, *m1 = &pr->g1a1;
+    const uint32_t tx = 2 * PARTS * G1_TILE + nd * BK * 4;
+    for (int rc = 0; rc < nch; ++rc) {
+      if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
+      uint8_t* st = smem + s * SB;
+      ptx::mbar_arrive_expect_tx(&B.full[s], tx);
+      ptx::tma_load_4d(st, m0, &B.full[s], 0, 0, rc, I);
+      if (PARTS == 2) ptx::tma_load_4d(st + G1_TILE, m1, &B.full[s], 0, 0, rc, I);
+      ptx::tma_load_4d(st + C::B_OFF, m0, &B.full[s], 0, 0, rc, J);
+      if (PARTS == 2) ptx::tma_load_4d(st + C::B_OFF + G1_TILE, m1, &B.full[s], 0, 0, rc, J);
+      for (int d = 0; d < nd; ++d)
+        ptx::bulk_load(st + C::SC_OFF + d * BK * 4, w0 + d * wstride + (long long)rc * BK, BK * 4,
+                       &B.full[s]);
+      pending[s] = (int)ph;
+      if (++s == STAGES) { s = 0; ph ^= 1; }
+    }
+  }
+  for (int i = 0; i < STAGES; ++i)
+    if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
+}
+
+template <int PREC>
+__device__ __forceinline__ void g1_mma(const G1Params& P, uint8_t* smem, const Bars& B, int items,
+                                       uint32_t tmem) {
+  using C = G1Cfg<PREC>;
+  constexpr int STAGES = C::STAGES, SB = C::STRIDE, SEG = C::SEG;
+  int s = 0;
+  uint32_t ph = 0, aph = 0;
+  bool ok = true;
+  for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    int q, k0, nd, I, J;
+    const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
+    const int nch = pr->nch;
+    const int nseg = (nch + SEG - 1) / SEG;
+    for (int sg = 0; sg < nseg && ok; ++sg) {
+      if (!wait1(&B.acc_empty[0], aph ^ 1, B, P.status)) { ok = false; break; }
+      ptx::tc_fence_after();
+      const int r0 = sg * SEG, r1 = min(nch, r0 + SEG);
+      for (int rc = r0; rc < r1; ++rc) {
+        if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        issue_g1_mmas<PREC>(tmem, (uint32_t)(G1_ACOL + s * C::SLOT),
+                            ptx::smem_u32(smem + s * SB) + C::B_OFF, nd, rc == r0);
+        ptx::mma_commit(&B.empty[s]);
+        if (++s == STAGES) { s = 0; ph ^= 1; }
+      }
+      if (!ok) break;
+      ptx::mma_commit(&B.acc_full[0]);
+      aph ^= 1;
+    }
+  }
+  ptx::mma_commit(B.drain);
+  wait_drain(B.drain, 0);
+}
+
+// Weighting into tensor memory, segment accumulation and the tile epilogue
+// (warps 0-7; warp w serves TMEM lane quarter w % 4 and element half /
+// direction w / 4).
+template <int PREC>
+__device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const Bars& B, int items,
+                                        uint32_t tmem, int warp, int lane) {
+  using C = G1Cfg<PREC>;
+  constexpr int STAGES = C::STAGES, SB = C::STRIDE, SEG = C::SEG, LAG = C::LAG;
+  const int lq = warp & 3;
+  const int h = warp >> 2;
+  const int row = lq * 32 + lane;
+  const uint32_t tq = tmem + ((uint32_t)(lq * 32) << 16);
+  int s = 0;
+  uint32_t ph = 0, aph = 0;
+  bool ok = true;
+  float sum[128];
+  for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    int q, k0, nd, I, J;
+    const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
+    const int nch = pr->nch, ns = pr->ns, ns_pad = pr->ns_pad;
+    const int nseg = (nch + SEG - 1) / SEG;
+#pragma unroll
+    for (int c = 0; c < 128; ++c) sum[c] = 0.f;
+    int flushed = 0;                      // segments already added into sum[]
+    for (int rc = 0; rc < nch; ++rc) {
+      if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
+      weight_stage<PREC>(ptx::smem_u32(smem + s * SB), row, h, nd,
+                         tq + (uint32_t)(G1_ACOL + s * C::SLOT));
+      ptx::tmem_wait_st();
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&B.ready[s]);
+      if (++s == STAGES) { s = 0; ph ^= 1; }
+      // add a finished segment into the running sums once the weighting is
+      // LAG stages past its end (those stages are ready when the MMAs resume)
+      const int ready_seg = (rc + 1 - LAG) / SEG;
+      const bool last = rc + 1 == nch;
+      while (flushed < nseg && (flushed < ready_seg || last)) {
+        if (!waitw(&B.acc_full[0], aph, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        if (h < nd) {
+          const uint32_t ta = tq + (uint32_t)(h * G1_BN);
+#pragma unroll
+          for (int c8 = 0; c8 < 8; ++c8) {
+            float v[16];
+            ptx::tmem_ld16(ta + c8 * 16, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sum[c8 * 16 + e] += v[e];
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&B.acc_empty[0]);
+        aph ^= 1;
+        ++flushed;
+      }
+      if (!ok) break;
+    }
+    if (!ok) break;
+    // epilogue: X[i][j] and X[j][i] for i <= j of this tile, direction k0 + h
+    const int i = I * G1_BN + row;
+    if (h < nd && i < ns) {
+      float* Xk = P.X[q] + (long long)(k0 + h) * ns_pad * ns_pad;
+      const int j0 = J * G1_BN;
+#pragma unroll
+      for (int c = 0; c < 128; ++c) {
+        const int j = j0 + c;
+        if (j >= i && j < ns) {
+          Xk[(long long)i * ns_pad + j] = sum[c];
+          Xk[(long long)j * ns_pad + i] = sum[c];
+        }
+      }
+    }
   }
 }
 
@@ -467,8 +711,7 @@ template <int PREC>
 __global__ void __launch_bounds__(G1_THREADS, 1)
     k_gemm1_tc(const __grid_constant__ G1Params P) {
   using C = G1Cfg<PREC>;
-  constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::STRIDE;
-  constexpr int TX = PARTS * (TILE_A + TILE_B) + BK * 4;   // bytes landing per stage
+  constexpr int STAGES = C::STAGES, SB = C::STRIDE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Bars B = carve<STAGES>(smem + STAGES * SB);
@@ -481,171 +724,34 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
       ptx::mbar_init(&B.empty[s], 1);
       ptx::mbar_init(&B.ready[s], 8);
     }
-    for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(&B.acc_full[b], 1);      // segment b accumulated
-      ptx::mbar_init(&B.acc_empty[b], 8);     // segment b added to the running sums
-    }
+    ptx::mbar_init(&B.acc_full[0], 1);       // segment accumulated
+    ptx::mbar_init(&B.acc_empty[0], 8);      // segment added to the running sums
     ptx::mbar_init(B.drain, 1);
     *B.abort = 0;
     ptx::fence_barrier_init();
     ptx::fence_proxy_async_smem();
   }
-  if (warp == 1) {
-    ptx::tmem_alloc(B.tmem_slot, 2 * BN);
+  if (warp == 9) {
+    ptx::tmem_alloc(B.tmem_slot, 512);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *B.tmem_slot;
-
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    for (int q = 0; q < P.nslot; ++q) {
-      const TcProblem* pr = P.probs + P.pid[q];
-      ptx::tmap_acquire(&pr->g1a0);
-      ptx::tmap_acquire(&pr->g1b0);
-      if (PARTS == 2) {
-        ptx::tmap_acquire(&pr->g1a1);
-        ptx::tmap_acquire(&pr->g1b1);
-      }
-    }
-    int s = 0;
-    uint32_t ph = 0;
-    int pending[STAGES];
-    for (int i = 0; i < STAGES; ++i) pending[i] = -1;
-    bool ok = true;
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int q, k, I, J;
-      const TcProblem* pr = g1_item(P, item, q, k, I, J);
-      const float* wk = pr->a + (long long)k * pr->a_stride;
-      const int nch = pr->nch;
-      const CUtensorMap *mA0 = &pr->g1a0, *mA1 = &pr->g1a1, *mB0 = &pr->g1b0, *mB1 = &pr->g1b1;
-      for (int rc = 0; rc < nch; ++rc) {
-        if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
-        uint8_t* st = smem + s * SB;
-        ptx::mbar_arrive_expect_tx(&B.full[s], TX);
-        ptx::tma_load_4d(st, mA0, &B.full[s], 0, 0, rc, I);
-        if (PARTS == 2) ptx::tma_load_4d(st + TILE_A, mA1, &B.full[s], 0, 0, rc, I);
-        ptx::tma_load_4d(st + C::B_OFF, mB0, &B.full[s], 0, 0, rc, J * (BN / 128));
-        if (PARTS == 2)
-          ptx::tma_load_4d(st + C::B_OFF + TILE_B, mB1, &B.full[s], 0, 0, rc, J * (BN / 128));
-        ptx::bulk_load(st + C::SC_OFF, wk + (long long)rc * BK, BK * 4, &B.full[s]);
-        pending[s] = (int)ph;
-        if (++s == STAGES) { s = 0; ph ^= 1; }
-      }
-    }
-    for (int i = 0; i < STAGES; ++i)
-      if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer: segments alternate between two TMEM buffers ----------------
-    int s = 0, b = 0;
-    uint32_t ph = 0, bph = 0;
-    bool ok = true;
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int q, k, I, J;
-      const TcProblem* pr = g1_item(P, item, q, k, I, J);
-      const int nch = pr->nch;
-      const int nseg = (nch + G1_SEG - 1) / G1_SEG;
-      for (int sg = 0; sg < nseg && ok; ++sg) {
-        if (!wait1(&B.acc_empty[b], bph ^ 1, B, P.status)) { ok = false; break; }
-        ptx::tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(b * BN);
-        const int r0 = sg * G1_SEG, r1 = min(nch, r0 + G1_SEG);
-        for (int rc = r0; rc < r1; ++rc) {
-          if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
-          ptx::tc_fence_after();
-          issue_stage_mmas<PREC>(d, ptx::smem_u32(smem + s * SB), rc == r0);
-          ptx::mma_commit(&B.empty[s]);
-          if (++s == STAGES) { s = 0; ph ^= 1; }
-        }
-        if (!ok) break;
-        ptx::mma_commit(&B.acc_full[b]);
-        if (++b == 2) { b = 0; bph ^= 1; }
-      }
-    }
-    ptx::mma_commit(B.drain);
-    wait_drain(B.drain, 0);
-  } else if (warp >= 2) {
-    // ---- weighting of the A tiles, segment accumulation, tile epilogue ----
-    const int lq = warp & 3;                // TMEM lane quarter
-    const int half = (warp - 2) >> 2;       // columns [128 half, 128 half + 128) of the tile
-    const int row = lq * 32 + lane;
-    int s = 0, b = 0;
-    uint32_t ph = 0, bph = 0;
-    bool ok = true;
-    float sum[128];
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int q, k, I, J;
-      const TcProblem* pr = g1_item(P, item, q, k, I, J);
-      const int nch = pr->nch, ns = pr->ns, ns_pad = pr->ns_pad;
-      const int nseg = (nch + G1_SEG - 1) / G1_SEG;
-#pragma unroll
-      for (int c = 0; c < 128; ++c) sum[c] = 0.f;
-      int flushed = 0;                      // segments already added into sum[]
-      for (int rc = 0; rc < nch; ++rc) {
-        if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
-        const uint32_t st = ptx::smem_u32(smem + s * SB);
-        const uint32_t r0 = st + row * ROWB;
-        const uint32_t sc = st + C::SC_OFF;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = 2 * half + u;
-          // physical 16-byte chunk: rotating by row/2 keeps each group of 8 lanes
-          // on 8 distinct bank quads
-          const int p = (it + (row >> 1)) & 3;
-          const int c = p ^ ((row >> 1) & 3);      // logical chunk under the 64-byte swizzle
-          scale_chunk<PREC>(r0 + p * 16, sc + c * (BK / 4) * 4);
-        }
-        ptx::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&B.ready[s]);
-        if (++s == STAGES) { s = 0; ph ^= 1; }
-        // add a finished segment into the running sums once the weighting is
-        // G1_LAG stages ahead of its end (so the MMAs keep being fed)
-        const int ready_seg = (rc + 1 - G1_LAG) / G1_SEG;   // segments whose end is >= G1_LAG behind
-        const bool last = rc + 1 == nch;
-        while (flushed < nseg && (flushed < ready_seg || last)) {
-          if (!waitw(&B.acc_full[b], bph, B, P.status)) { ok = false; break; }
-          ptx::tc_fence_after();
-          const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * BN + half * 128);
-#pragma unroll
-          for (int c8 = 0; c8 < 8; ++c8) {
-            float v[16];
-            ptx::tmem_ld16(ta + c8 * 16, v);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) sum[c8 * 16 + e] += v[e];
-          }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&B.acc_empty[b]);
-          if (++b == 2) { b = 0; bph ^= 1; }
-          ++flushed;
-        }
-        if (!ok) break;
-      }
-      if (!ok) break;
-      // epilogue: X[i][j] and X[j][i] for i <= j of this tile
-      const int i = I * BM + row;
-      if (i < ns) {
-        float* Xk = P.X[q] + (long long)k * ns_pad * ns_pad;
-        const int j0 = J * BN + half * 128;
-#pragma unroll
-        for (int c = 0; c < 128; ++c) {
-          const int j = j0 + c;
-          if (j >= i && j < ns) {
-            Xk[(long long)i * ns_pad + j] = sum[c];
-            Xk[(long long)j * ns_pad + i] = sum[c];
-          }
-        }
-      }
-    }
+  if (warp >= 8) {
+    ptx::setmaxnreg_dec<G1_REG_CTRL>();
+    if (warp == 8 && lane == 0) g1_producer<PREC>(P, smem, B, items);
+    else if (warp == 9 && lane == 0) g1_mma<PREC>(P, smem, B, items, tmem);
+  } else {
+    ptx::setmaxnreg_inc<G1_REG_MATH>();
+    g1_math<PREC>(P, smem, B, items, tmem, warp, lane);
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
+  if (warp == 9) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, 2 * BN);
+    ptx::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -712,13 +818,13 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   constexpr int BK = Tr<PREC>::BK;
   const int eb = PREC == LRDM_BF16X3 ? 2 : 4;
   memset(&pr, 0, sizeof(pr));
-  // GEMM1: Psi^T tile-major [ns_pad/128][Ng_pad/BK][128][BK]: an A box is one
-  // contiguous 8 KB tile, a B box two of them (consecutive state blocks).
+  // GEMM1: Psi^T tile-major [ns_pad/128][Ng_pad/BK][128][BK]: a box (A or B
+  // operand of one stage) is one contiguous 8 KB tile.
   const void* t0 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_hi : (const void*)c.psiT32;
   const void* t1 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_lo : (const void*)c.psiT32;
   const uint64_t d1[4] = {(uint64_t)BK, 128, (uint64_t)(S.Ng_pad / BK), (uint64_t)(c.ns_pad / 128)};
   const uint64_t s1[3] = {(uint64_t)BK * eb, (uint64_t)128 * BK * eb, (uint64_t)128 * S.Ng_pad * eb};
-  const uint32_t bA1[4] = {(uint32_t)BK, 128, 1, 1}, bB1[4] = {(uint32_t)BK, 128, 1, BN / 128};
+  const uint32_t bA1[4] = {(uint32_t)BK, 128, 1, 1};
   // GEMM2: Psi rows [Ng_pad][ns_pad] (A) and X'' [k_max][j][i] (B).
   const void* r0 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_hi : (const void*)c.psiR32;
   const void* r1 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_lo : (const void*)c.psiR32;
@@ -731,7 +837,6 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   const uint64_t sB2[2] = {(uint64_t)c.ns_pad * eb, (uint64_t)c.ns_pad * c.ns_pad * eb};
   const uint32_t bB2[3] = {(uint32_t)BK, (uint32_t)BN, 1};
   if (!make_map(&pr.g1a0, t0, eb, 4, d1, s1, bA1) || !make_map(&pr.g1a1, t1, eb, 4, d1, s1, bA1) ||
-      !make_map(&pr.g1b0, t0, eb, 4, d1, s1, bB1) || !make_map(&pr.g1b1, t1, eb, 4, d1, s1, bB1) ||
       !make_map(&pr.g2a0, r0, eb, 2, dA2, sA2, bA2) || !make_map(&pr.g2a1, r1, eb, 2, dA2, sA2, bA2) ||
       !make_map(&pr.g2b0, x0, eb, 3, dB2, sB2, bB2) || !make_map(&pr.g2b1, x1, eb, 3, dB2, sB2, bB2))
     return false;
@@ -744,8 +849,7 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   pr.ns_pad = c.ns_pad;
   pr.nI = c.ns_pad / BM;
   pr.NJ = (c.ns_pad + BN - 1) / BN;
-  pr.ntiles = 0;
-  for (int j = 0; j < pr.NJ; ++j) pr.ntiles += (2 * (j + 1) < pr.nI ? 2 * (j + 1) : pr.nI);
+  pr.ntiles = pr.nI * (pr.nI + 1) / 2;    // GEMM1 128 x 128 tiles with I <= J
   pr.nch = (int)(S.Ng_pad / BK);
   pr.nR = (int)(S.Ng_pad / BM);
   pr.kmax = S.kmax;
@@ -792,7 +896,7 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st) {
       P.K[q] = x.K;
       P.X[q] = static_cast<float*>(x.X);
       P.begin[q] = items;
-      items += x.host->ntiles * x.K;
+      items += x.host->ntiles * ((x.K + 1) / 2);
       ++q;
     }
     P.nslot = q;

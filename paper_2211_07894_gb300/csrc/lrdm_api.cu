@@ -186,6 +186,10 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
     LRDM_CU(cudaMemcpyAsync(ch.occ, occ[c].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
     LRDM_CK(dalloc(ctx, &ch.L, (size_t)ns * ns, false));
     LRDM_CU(launch_loewner(ch.eps, ch.occ, ns, S.mu, S.kT, S.occ_given ? 1 : 0, o.degen_tol, ch.L, st));
+    if (is_tc(prec)) {
+      LRDM_CK(dalloc(ctx, &ch.Lf, (size_t)ch.ns_pad * ch.ns_pad, false));
+      LRDM_CU(launch_loewner_f32(ch.L, ns, ch.ns_pad, ch.Lf, st));
+    }
     // density and xc kernel
     LRDM_CK(dalloc(ctx, &ch.rho, S.Ng, false));
     if (in.rho[c]) {
@@ -261,6 +265,8 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
   S.plans = true;
   LRDM_FFT(cufftPlanMany(&S.plan_c2r, 3, nn, nullptr, 1, (int)nc, nullptr, 1, (int)S.Ng,
                          fp64 ? CUFFT_Z2D : CUFFT_C2R, S.kmax));
+  LRDM_CK(dalloc(ctx, &S.sym, (size_t)nc, false));
+  LRDM_CU(launch_poisson_table(S.n, S.h, o.poisson_symbol, S.sym, st));
   return LRDM_OK;
 }
 
@@ -276,7 +282,8 @@ lrdm_status hartree_body(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
     LRDM_FFT(cufftExecR2C(S.plan_r2c, static_cast<cufftReal*>(S.fft_real),
                           static_cast<cufftComplex*>(S.fft_cplx)));
   }
-  LRDM_CU(launch_poisson_symbol(S.fft_cplx, K, S.n, S.h, ctx->opt.poisson_symbol, fp64, st));
+  LRDM_CU(launch_poisson_symbol(S.fft_cplx, K, (long long)S.n[0] * S.n[1] * (S.n[2] / 2 + 1),
+                                S.sym, fp64, st));
   if (fp64) {
     LRDM_FFT(cufftExecZ2D(S.plan_c2r, static_cast<cufftDoubleComplex*>(S.fft_cplx),
                           static_cast<cufftDoubleReal*>(S.fft_real)));

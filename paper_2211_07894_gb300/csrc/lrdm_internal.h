@@ -37,6 +37,7 @@ struct Channel {
   double* eps = nullptr;             // [ns]
   double* occ = nullptr;             // [ns]
   double* L = nullptr;               // [ns][ns] Loewner matrix
+  float* Lf = nullptr;               // [ns_pad][ns_pad] FP32 copy, zero padded (tensor-core modes)
   double* fx = nullptr;              // [Ng] xc kernel
   double* rho = nullptr;             // [Ng] density used for fx
   // Psi operand copies (which ones exist depends on the precision)
@@ -71,6 +72,7 @@ struct SysState {
   bool plans = false;
   void* fft_real = nullptr;          // [kmax][Ng] compute type
   void* fft_cplx = nullptr;          // [kmax][n0][n1][n2/2+1]
+  double* sym = nullptr;             // [n0][n1][n2/2+1] Poisson symbol / N_g
   void* a = nullptr;                 // [kmax][nspin][Ng_pad] GEMM1 weights (compute type)
   double* dmu = nullptr;             // [kmax]
   double* tbar = nullptr;            // [kmax] backward trace terms
@@ -119,13 +121,20 @@ cudaError_t launch_fx(const double* rho, long long Ng, int spin_polarized, doubl
 cudaError_t launch_loewner(const double* eps, const double* occ, int ns, double mu, double kT,
                            int occ_mode, double degen_tol, double* L, cudaStream_t st);
 cudaError_t launch_to_io(const double* src, long long n, void* dst, int io_dtype, cudaStream_t st);
+// Lf[i][j] = (float) L[i][j] for i, j < ns, 0 in the padding
+cudaError_t launch_loewner_f32(const double* L, int ns, int ns_pad, float* Lf, cudaStream_t st);
 
 // ---------------- element-wise / reduction kernels (k_elem.cu) ----------------
 // fft_real[k][r] = sum_s v[k][s][r]  (compute type = double if fp64 else float)
 cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long long Ng,
                             void* fft_real, int fp64, cudaStream_t st);
-cudaError_t launch_poisson_symbol(void* cplx, int K, const int* n, const double* h, int kind,
-                                  int fp64, cudaStream_t st);
+// sym[m] = 4 pi / |G_m|^2 / N_g on the half-complex grid (G = 0 -> 0); kind 1
+// uses the second-order finite-difference symbol (once per system)
+cudaError_t launch_poisson_table(const int* n, const double* h, int kind, double* sym,
+                                 cudaStream_t st);
+// cplx[k][m] *= sym[m] for k < K
+cudaError_t launch_poisson_symbol(void* cplx, int K, long long per, const double* sym, int fp64,
+                                  cudaStream_t st);
 // a[k][s][r] = scale * (VH[k][r] + fx_s[r] * v[k][s][r]);  mode 1 (adjoint):
 // out[k][s][r] = VH[k][r] + fx_s[r] * dvbar[k][s][r] - fbar[k][s][r] (io dtype)
 cudaError_t launch_dv_weights(const void* v, int io_dtype, const void* VH, const double* fx0,

@@ -9,14 +9,14 @@
 namespace lrdm {
 
 struct TcProblem {
-  CUtensorMap g1a0, g1a1, g1b0, g1b1;   // GEMM1: Psi^T tile-major (A box 128 rows, B box 256)
+  CUtensorMap g1a0, g1a1;               // GEMM1: Psi^T tile-major, box 128 rows (A and B)
   CUtensorMap g2a0, g2a1, g2b0, g2b1;   // GEMM2: Psi rows (A), X'' [k_max][j][i] (B)
   long long Ng;                          // grid points
   long long a_stride;                    // direction stride of the GEMM1 weights
   const float* a;                        // GEMM1 weights of this channel (direction 0)
   const void* psi0;                      // GEMM2 epilogue rows: bf16 hi / fp32
   const void* psi1;                      // bf16 lo
-  int ns, ns_pad, nI, NJ, ntiles, nch, nR, kmax;
+  int ns, ns_pad, nI, NJ, ntiles, nch, nR, kmax;   // GEMM1: nI blocks, ntiles tiles; GEMM2: NJ, nR
 };
 
 constexpr int TC_MAX_SLOTS = 16;        // problems per grouped launch
