@@ -105,8 +105,27 @@ typedef struct lrdm_options {
                             degenerate in occupation mode; 1e-5                 */
   int poisson_symbol;    /* 0: 4 pi/|G|^2 (spectral); 1: second-order FD symbol  */
   int use_graph;         /* replay lrdm_gateaux_batch from a captured CUDA graph  */
-  int autotune;          /* reserved: tile choice by measurement at create        */
+  int autotune;          /* tensor-core precisions: 0 -> default launch shape (two
+                            directions per projection tile, response j-tile 256,
+                            direction group 2); 1 -> lrdm_create times the
+                            candidates (1 or 2 directions per projection tile;
+                            j-tile 128 or 256 x group 1, 2, 4) on the context's
+                            own problems and keeps the fastest; with the
+                            environment variable LRDM_TUNE_CACHE naming a file,
+                            results are read from / appended to it (one JSON
+                            object per line, keyed by device and problem sizes) */
   int debug_flags;       /* test-only host-side fault injection; 0 in production */
+  int fermi_T;           /* 0: the response uses the Loewner (divided-difference)
+                            matrix of Fermi-Dirac; T >= 1: the first-order
+                            response of the depth-T recursive Fermi-operator
+                            expansion (Eq. recursiveFermiOperator), i.e. the
+                            Loewner matrix of f_T(e) = 1/(1 + exp(2^(T+1)
+                            artanh(2^-(T+1) (e - mu)/kT))); mu and the
+                            occupations stay Fermi-Dirac.  Requires every
+                            |eps - mu| < kT 2^(T+1) (else LRDM_ERR_INVALID_ARG at
+                            create), no occupations given, and T <= 30;
+                            lrdm_backward then returns v_bar only
+                            (eps_bar / occ_bar -> LRDM_ERR_UNSUPPORTED)         */
 } lrdm_options;
 
 typedef struct lrdm_ctx lrdm_ctx;
@@ -207,6 +226,33 @@ lrdm_status lrdm_profile_enable(lrdm_ctx* ctx, int on);
 lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_launches,
                               double* gemm2_ms, long long* gemm2_launches, double* poisson_ms,
                               long long* poisson_calls, long long* kernel_launches, int reset);
+
+/* Launch shape of the tensor-core contractions chosen at create (defaults
+ * or the autotuner's choice): directions per projection tile, response
+ * j-tile width, response direction group.  Any pointer may be NULL. */
+lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_dpt, int* g2_bn, int* g2_kgroup);
+
+/* One LRDM preconditioning step of system `sys` with adaptively chosen rank
+ * (§II.B, Eqs. jlowrank, krylovOrtho, plowrank, relativeError, quasinewton):
+ * u_1 = R/||R||; for i = 1..r_max: t_i = Gateaux derivative along u_i (one
+ * direction through the forward path), a = S^+ c over u_1..u_i, s_rel; stop
+ * when s_rel < s_tol; else u_{i+1} = t_i Gram-Schmidt-orthonormalised against
+ * u_1..u_i.  Then rho_inout <- rho_inout - alpha sum_k a_k u_k when rho_inout
+ * is not NULL; alpha < 0 selects the paper's schedule (0.1 while ||R|| >= 2,
+ * else 0.5).
+ *   R          [nspin][N_g] io dtype, device; ||R|| > 0 (else INVALID_ARG)
+ *   U, T       [r_max][nspin][N_g] io dtype, device, caller-owned: the
+ *              directions and their Gateaux derivatives (outputs; rows
+ *              beyond the final rank are unspecified)
+ *   coeff_out  device [r_max] or NULL: a (first `rank` entries)
+ *   s_rel_out  HOST double [r_max] or NULL: s_rel after each rank
+ *   rank_out   HOST int or NULL;  r_norm_out  HOST double or NULL: ||R||
+ * 1 <= r_max <= 64.  Synchronises the stream once per rank (to read s_rel);
+ * the forward state of every system of the context is replaced (a following
+ * lrdm_backward differentiates the last direction of `sys` only). */
+lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol, int r_max,
+                             double alpha, void* rho_inout, void* U, void* T, double* coeff_out,
+                             double* s_rel_out, int* rank_out, double* r_norm_out, void* stream);
 
 /* Copies the projected perturbation X_k = Psi^T diag(w dV_k) Psi of direction
  * k, channel `spin`, of system `sys` from the most recent lrdm_gateaux_batch

@@ -19,6 +19,7 @@ from .lrdm_oracle import (  # noqa: F401
     solve_mu,
     loewner,
     loewner_from_occ,
+    loewner_recursive,
     lda_vx,
     lda_fx,
     poisson_symbol,
@@ -31,6 +32,8 @@ from .lrdm_oracle import (  # noqa: F401
     density_response,
     gateaux,
     lrdm_apply,
+    alpha_schedule,
+    lrdm_krylov_step,
     backward,
     total_eps_grad,
     fermi_recursive,

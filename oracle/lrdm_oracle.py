@@ -30,7 +30,7 @@ __all__ = [
     "lda_vx", "lda_fx", "poisson_symbol", "hartree", "density",
     "perturbation_potential", "project", "dmu_shift", "subspace_response",
     "density_response", "gateaux", "lrdm_apply", "backward", "total_eps_grad",
-    "fermi_recursive",
+    "fermi_recursive", "loewner_recursive", "alpha_schedule", "lrdm_krylov_step",
 ]
 
 
@@ -47,6 +47,11 @@ class System:
     rho[s]  : (N_g,) density entering the xc kernel; for nspin = 1 the total
               density, for nspin = 2 the channel densities      (Eq. kseqcont)
     occ[s]  : optional occupations; None -> Fermi-Dirac(eps, mu, kT)
+    fermi_T : 0 -> the response uses the Loewner matrix of Fermi-Dirac; T > 0
+              -> the first-order response of the paper's depth-T recursive
+              Fermi-operator expansion (mu and the occupations stay
+              Fermi-Dirac: they describe the SCF state the response is taken
+              about)
     """
 
     n: Sequence[int]
@@ -60,6 +65,7 @@ class System:
     occ: Optional[List[np.ndarray]] = None
     poisson: str = "spectral"
     degen_tol: float = 1e-5
+    fermi_T: int = 0
 
     @property
     def nspin(self) -> int:
@@ -197,6 +203,36 @@ def fermi_recursive(eps, mu, kT, T):
     return X
 
 
+def loewner_recursive(eps, mu, kT, T):
+    """First-order response of the paper's recursive Fermi-operator expansion
+    at the diagonal projected Hamiltonian D = diag(eps) (Eq.
+    recursiveFermiOperator, canonical density-matrix perturbation theory):
+    d/dlam X_T(D + lam E) = L_T o E (mu fixed; the mu' shift enters as E - mu' I).
+
+    The recursion's steps, perturbed in the paper's order:
+      X_0 = 1/2 - 2^-(T+2) (D - mu)/kT            X_0^(1) = -2^-(T+2) E / kT
+      X_n = P(X_{n-1}),  P(x) = x^2 / (x^2 + (1-x)^2)
+    With X_{n-1} = diag(x) diagonal, the first-order change of P(X_{n-1}) along
+    a symmetric X_{n-1}^(1) is [P](x_i, x_j) X_{n-1,ij}^(1), where [P] is the
+    divided difference of P: P(a) - P(b) = (a - b)(a + b - 2ab) / (q(a) q(b)),
+    q(x) = x^2 + (1-x)^2, so [P](a, b) = (a (1-b) + b (1-a)) / (q(a) q(b))
+    exactly (at a = b it is P'(a)).  Hence L_T is -2^-(T+2)/kT times the
+    elementwise product of the T matrices [P](x_{n-1,i}, x_{n-1,j}).  The
+    recursion is carried on both X and I - X (the two matrices P is built
+    from: x_n = x^2 / q, 1 - x_n = (1-x)^2 / q), so that states far below or
+    above mu, where x_n rounds to 1 or 0, keep their relative accuracy."""
+    z = 2.0 ** (-(T + 2)) * (np.asarray(eps, dtype=np.float64) - mu) / kT
+    x, xb = 0.5 - z, 0.5 + z                  # X_0 and I - X_0
+    n = x.shape[0]
+    L = np.full((n, n), -(2.0 ** (-(T + 2))) / kT)
+    for _ in range(T):
+        q = x * x + xb * xb
+        num = x[:, None] * xb[None, :] + xb[:, None] * x[None, :]
+        L = L * (num / (q[:, None] * q[None, :]))
+        x, xb = x * x / q, xb * xb / q
+    return L
+
+
 # ---------------------------------------------------------------------------
 # Kernel K = K_xc + K_c (Eq. jacobian)
 # ---------------------------------------------------------------------------
@@ -296,6 +332,10 @@ def _occupations(system: System, mu: float):
 
 
 def _loewner_channels(system: System, mu: float):
+    if system.fermi_T:
+        if system.occ is not None:
+            raise ValueError("fermi_T with given occupations is not defined")
+        return [loewner_recursive(e, mu, system.kT, system.fermi_T) for e in system.eps]
     if system.occ is not None:
         return [loewner_from_occ(e, o, system.kT, system.degen_tol)
                 for e, o in zip(system.eps, system.occ)]
@@ -380,6 +420,55 @@ def lrdm_apply(R, V, F, w, alpha, rho=None, rcond=1e-12):
            "r_norm": np.sqrt(r2)}
     if rho is not None:
         out["rho_new"] = np.asarray(rho, dtype=np.float64) - alpha * delta
+    return out
+
+
+def alpha_schedule(r_norm, threshold=2.0):
+    """The paper's damping: alpha = 0.1 while ||R|| is above a threshold of
+    order one, 0.5 below it (§II.B; the threshold 2.0 of its setup, §III)."""
+    return 0.5 if r_norm < threshold else 0.1
+
+
+def lrdm_krylov_step(system: System, R, s_tol=0.3, r_max=8, alpha=None, rho=None, rcond=1e-12):
+    """One LRDM preconditioning step with adaptively chosen rank (§II.B):
+
+      u_1 = R / ||R||;  for i = 1, 2, ...:
+        t_i = d/dlam R[rho + lam u_i]            (gateaux, one direction)
+        a = S^+ c, S_kl = <t_k, t_l>, c_k = <t_k, R>,
+        s_rel = ||sum_k a_k t_k - R|| / ||R||    (Eqs. plowrank, relativeError)
+        stop when s_rel < s_tol or i = r_max;
+        u_{i+1} = t_i - sum_{k<=i} <t_i, u_k> u_k,  u_{i+1} /= ||u_{i+1}||
+                                                 (Eq. krylovOrtho, classical
+                                                  Gram-Schmidt as printed)
+      Delta = sum_k a_k u_k,  rho_new = rho - alpha Delta (Eq. quasinewton);
+      alpha None -> alpha_schedule(||R||).
+
+    Directions and residuals have the shape (nspin, N_g); for a spin pair the
+    inner product sums the two channels (Eq. innerproductDirectsumHilbertspace).
+    Returns the directions U (r, nspin, N_g), their derivatives T, the
+    coefficients a, the rank r, s_rel after each rank, ||R||, alpha, Delta and
+    rho_new when rho is given."""
+    w = system.w
+    Rm = np.asarray(R, dtype=np.float64)
+    r_norm = float(np.sqrt(w * np.sum(Rm * Rm)))
+    U = [Rm / r_norm]
+    T = []
+    s_hist = []
+    while True:
+        T.append(gateaux(system, U[-1][None])["F"][0])
+        ls = lrdm_apply(Rm, np.stack(U), np.stack(T), w, 0.0, rcond=rcond)
+        s_hist.append(ls["s_rel"])
+        if ls["s_rel"] < s_tol or len(U) == r_max:
+            break
+        t = T[-1]
+        u = t - sum(w * float(np.sum(t * uk)) * uk for uk in U)
+        U.append(u / np.sqrt(w * np.sum(u * u)))
+    if alpha is None:
+        alpha = alpha_schedule(r_norm)
+    out = {"U": np.stack(U), "T": np.stack(T), "a": ls["a"], "rank": len(U), "s_rel": s_hist,
+           "r_norm": r_norm, "alpha": alpha, "delta": ls["delta"]}
+    if rho is not None:
+        out["rho_new"] = np.asarray(rho, dtype=np.float64) - alpha * ls["delta"]
     return out
 
 

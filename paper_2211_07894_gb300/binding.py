@@ -43,7 +43,8 @@ class lrdm_system(ctypes.Structure):
 class lrdm_options(ctypes.Structure):
     _fields_ = [("prec", c_int), ("io_dtype", c_int), ("k_max", c_int),
                 ("pinv_rcond", c_double), ("degen_tol", c_double), ("poisson_symbol", c_int),
-                ("use_graph", c_int), ("autotune", c_int), ("debug_flags", c_int)]
+                ("use_graph", c_int), ("autotune", c_int), ("debug_flags", c_int),
+                ("fermi_T", c_int)]
 
 
 _lib = None
@@ -51,7 +52,8 @@ _lib = None
 EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_apply",
            "lrdm_apply_static",
            "lrdm_backward", "lrdm_status_query", "lrdm_get_mu", "lrdm_get_density",
-           "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string"]
+           "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string",
+           "lrdm_get_tuning", "lrdm_krylov_step"]
 
 
 def load(path: Optional[str] = None):
@@ -96,6 +98,12 @@ def load(path: Optional[str] = None):
                                       POINTER(c_double), POINTER(ctypes.c_longlong),
                                       POINTER(ctypes.c_longlong), c_int]
     lib.lrdm_profile_read.restype = c_int
+    lib.lrdm_krylov_step.argtypes = [c_void_p, c_int, c_void_p, c_double, c_int, c_double, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, POINTER(c_double), POINTER(c_int),
+                                     POINTER(c_double), c_void_p]
+    lib.lrdm_krylov_step.restype = c_int
+    lib.lrdm_get_tuning.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]
+    lib.lrdm_get_tuning.restype = c_int
     lib.lrdm_destroy.argtypes = [c_void_p]
     lib.lrdm_destroy.restype = None
     lib.lrdm_status_string.argtypes = [c_int]
@@ -197,6 +205,25 @@ def lrdm_profile_read(ctx, reset: int = 1):
                 kernel_launches=nk.value)
 
 
+def lrdm_krylov_step(ctx, sys, R_ptr, s_tol, r_max, alpha, rho_ptr, U_ptr, T_ptr, coeff_ptr,
+                     stream: int = 0):
+    """Returns (status, rank, s_rel list, ||R||)."""
+    s_rel = (c_double * max(1, r_max))()
+    rank = c_int(0)
+    rn = c_double(0.0)
+    code = load().lrdm_krylov_step(ctx, sys, c_void_p(R_ptr), float(s_tol), int(r_max), float(alpha),
+                                   c_void_p(rho_ptr), c_void_p(U_ptr), c_void_p(T_ptr),
+                                   c_void_p(coeff_ptr), s_rel, ctypes.byref(rank), ctypes.byref(rn),
+                                   c_void_p(stream))
+    return code, rank.value, [s_rel[i] for i in range(rank.value)], rn.value
+
+
+def lrdm_get_tuning(ctx):
+    a, b, c = c_int(), c_int(), c_int()
+    _check("lrdm_get_tuning", load().lrdm_get_tuning(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(g1_dpt=a.value, g2_bn=b.value, g2_kgroup=c.value)
+
+
 def lrdm_destroy(ctx) -> None:
     load().lrdm_destroy(ctx)
 
@@ -220,7 +247,8 @@ class Context:
     """
 
     def __init__(self, systems, prec="bf16x3", io_dtype=None, k_max=16, pinv_rcond=1e-12,
-                 degen_tol=1e-5, poisson="spectral", use_graph=False, stream=None):
+                 degen_tol=1e-5, poisson="spectral", use_graph=False, stream=None, fermi_T=0,
+                 autotune=False):
         import torch
         self.torch = torch
         self.io_dtype = io_dtype or torch.float32
@@ -233,6 +261,8 @@ class Context:
         o.degen_tol = float(degen_tol)
         o.poisson_symbol = 1 if poisson == "fd" else 0
         o.use_graph = 1 if use_graph else 0
+        o.fermi_T = int(fermi_T)
+        o.autotune = 1 if autotune else 0
         self.options = o
         keep = []
         cs = []
@@ -375,6 +405,27 @@ class Context:
         _check("lrdm_get_projection", lrdm_get_projection(self.handle, sys, spin, k,
                                                           out.data_ptr(), self._stream(stream)))
         return out
+
+    def krylov_step(self, R, s_tol=0.3, r_max=8, alpha=-1.0, rho=None, sys=0, stream=None):
+        """One LRDM step with adaptive rank (lrdm_krylov_step).  R: (nspin, N_g)
+        in the io dtype; rho (same shape) is updated in place when given;
+        alpha < 0 selects the paper's schedule.  Returns dict(U, T, a, rank,
+        s_rel, r_norm) with U, T (rank, nspin, N_g)."""
+        torch = self.torch
+        assert R.is_contiguous() and R.dtype == self.io_dtype
+        U = torch.empty((r_max,) + tuple(R.shape), dtype=self.io_dtype, device="cuda")
+        T = torch.empty_like(U)
+        a = torch.zeros(r_max, dtype=torch.float64, device="cuda")
+        code, rank, s_rel, rn = lrdm_krylov_step(self.handle, sys, R.data_ptr(), s_tol, r_max, alpha,
+                                                 rho.data_ptr() if rho is not None else 0,
+                                                 U.data_ptr(), T.data_ptr(), a.data_ptr(),
+                                                 self._stream(stream))
+        _check("lrdm_krylov_step", code)
+        return dict(U=U[:rank], T=T[:rank], a=a[:rank], rank=rank, s_rel=s_rel, r_norm=rn)
+
+    def tuning(self):
+        """Launch shape of the tensor-core contractions (defaults or autotuned)."""
+        return lrdm_get_tuning(self.handle)
 
     def profile(self, on=True):
         _check("lrdm_profile_enable", lrdm_profile_enable(self.handle, 1 if on else 0))

@@ -40,7 +40,7 @@ __global__ void k_copy_tc(const void* __restrict__ src, int io_dtype, int ld, lo
                           long long Ng_pad, int ns_pad, float* __restrict__ R32,
                           float* __restrict__ T32, __nv_bfloat16* __restrict__ Rhi,
                           __nv_bfloat16* __restrict__ Rlo, __nv_bfloat16* __restrict__ Thi,
-                          __nv_bfloat16* __restrict__ Tlo) {
+                          __nv_bfloat16* __restrict__ Tlo, float* __restrict__ Tf) {
   __shared__ float tile[32][33];
   long long r0 = (long long)blockIdx.x * 32;
   int i0 = blockIdx.y * 32;
@@ -63,8 +63,9 @@ __global__ void k_copy_tc(const void* __restrict__ src, int io_dtype, int ld, lo
   }
   __syncthreads();
   // transposed copies are tile-major: [i / 128][r / RB][i % 128][r % RB] with
-  // RB = 64 bytes of the element type, so that one (128 states x 64 bytes)
-  // tensor-core operand tile is a contiguous 8 KB block
+  // RB = 64 bytes of the operand type (16 TF32, 32 bf16; the exact FP32 copy
+  // of the split mode shares the bf16 RB = 32), so that one (128 states x RB
+  // rows) tensor-core operand tile is a contiguous block
   for (int yy = ty; yy < 32; yy += 8) {
     int i = i0 + yy;
     long long r = r0 + tx;
@@ -78,6 +79,7 @@ __global__ void k_copy_tc(const void* __restrict__ src, int io_dtype, int ld, lo
         Thi[o] = hi;
         Tlo[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
       }
+      if (Tf) Tf[o] = x;
     }
   }
 }
@@ -150,15 +152,47 @@ __global__ void k_loewner_f32(const double* __restrict__ L, int ns, int ns_pad,
   }
 }
 
+// artanh(w) / w, even in w, |w| < 1
+__device__ __forceinline__ double artanhc(double w) {
+  const double a = fabs(w);
+  if (a < 1e-4) return 1.0 + a * a / 3.0;
+  return atanh(a) / a;
+}
+
+// Loewner matrix of f_T(e) = 1 / (1 + exp(g(e))), g = c artanh(u), c = 2^(T+1),
+// u = (e - mu) / (c kT), |u| < 1: with
+//   f_i - f_j = -sinh((g_i - g_j)/2) / (2 cosh(g_i/2) cosh(g_j/2)) and
+//   g_i - g_j = c artanh(w), w = (u_i - u_j) / (1 - u_i u_j),  u_i - u_j = (e_i - e_j)/(c kT),
+//   L_ij = -sinhc((g_i - g_j)/2) artanhc(w) / (4 kT (1 - u_i u_j) cosh(g_i/2) cosh(g_j/2)),
+// free of cancellation for close e_i, e_j; in the log domain where a factor
+// would overflow.  The diagonal (w = 0) is f_T'.
+__device__ double loewner_T(double ei, double ej, double mu, double kT, int T) {
+  const double c = ldexp(1.0, T + 1);
+  const double ui = (ei - mu) / (c * kT), uj = (ej - mu) / (c * kT);
+  const double gi = c * atanh(ui), gj = c * atanh(uj);
+  const double den = 1.0 - ui * uj;
+  const double w = (ui - uj) / den;
+  const double hd = 0.5 * (gi - gj);
+  if (fabs(gi) < 1400.0 && fabs(gj) < 1400.0 && fabs(hd) < 700.0) {
+    const double sc = hd == 0.0 ? 1.0 : sinh(hd) / hd;
+    return -sc * artanhc(w) / (4.0 * kT * den * cosh(0.5 * gi) * cosh(0.5 * gj));
+  }
+  const double lm = log_sinhc(hd) + log(artanhc(w)) - log(4.0 * kT * den) - log_cosh(0.5 * gi) -
+                    log_cosh(0.5 * gj);
+  return -exp(lm);
+}
+
 __global__ void k_loewner(const double* __restrict__ eps, const double* __restrict__ occ, int ns,
-                          double mu, double kT, int occ_mode, double degen_tol,
+                          double mu, double kT, int occ_mode, double degen_tol, int fermi_T,
                           double* __restrict__ L) {
   long long total = (long long)ns * ns;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int i = (int)(e / ns), j = (int)(e - (long long)i * ns);
     double val;
-    if (occ_mode) {
+    if (fermi_T > 0) {
+      val = loewner_T(eps[i], eps[j], mu, kT, fermi_T);
+    } else if (occ_mode) {
       double de = eps[i] - eps[j];
       if (fabs(de) <= degen_tol * kT) {
         double fb = 0.5 * (occ[i] + occ[j]);
@@ -209,7 +243,7 @@ cudaError_t launch_convert_psi(const void* src, int io_dtype, int ld, long long 
   dim3 blk(32, 8);
   dim3 grd((unsigned)((Ng_pad + 31) / 32), (unsigned)((c.ns_pad + 31) / 32));
   k_copy_tc<<<grd, blk, 0, st>>>(src, io_dtype, ld, Ng, ns, Ng_pad, c.ns_pad, c.psiR32, c.psiT32,
-                                 c.psiR_hi, c.psiR_lo, c.psiT_hi, c.psiT_lo);
+                                 c.psiR_hi, c.psiR_lo, c.psiT_hi, c.psiT_lo, c.psiTf);
   return cudaGetLastError();
 }
 
@@ -234,9 +268,10 @@ cudaError_t launch_fx(const double* rho, long long Ng, int spin_polarized, doubl
 }
 
 cudaError_t launch_loewner(const double* eps, const double* occ, int ns, double mu, double kT,
-                           int occ_mode, double degen_tol, double* L, cudaStream_t st) {
+                           int occ_mode, double degen_tol, int fermi_T, double* L,
+                           cudaStream_t st) {
   k_loewner<<<grid_for((long long)ns * ns, 256), 256, 0, st>>>(eps, occ, ns, mu, kT, occ_mode,
-                                                                degen_tol, L);
+                                                                degen_tol, fermi_T, L);
   return cudaGetLastError();
 }
 

@@ -32,11 +32,9 @@ namespace lrdm {
 namespace {
 
 constexpr int BM = 128;                 // MMA M = tensor-memory lanes
-constexpr int BN = 256;                 // MMA N
 constexpr int ROWB = 64;                // bytes per swizzled smem row (64-byte swizzle)
 constexpr int KSTEPS = ROWB / 32;       // 32-byte MMA K steps per row
 constexpr int TILE_A = BM * ROWB;       // 8 KB per operand part
-constexpr int TILE_B = BN * ROWB;       // 16 KB per operand part
 constexpr int NTHREADS = 192;           // warp 0 TMA, warp 1 MMA, warps 2-5 math / epilogue
 constexpr uint64_t WAIT_NS = 4000000000ull;
 
@@ -46,21 +44,24 @@ template <>
 struct Tr<LRDM_BF16X3> {
   static constexpr int BK = 32;          // bf16 per 64-byte row
   static constexpr int PARTS = 2;        // hi, lo
-  static constexpr int STAGES = 4;
-  static constexpr uint32_t IDESC = ptx::idesc_make(1, BM, BN);
 };
 template <>
 struct Tr<LRDM_TF32> {
   static constexpr int BK = 16;          // fp32 per 64-byte row
   static constexpr int PARTS = 1;
-  static constexpr int STAGES = 8;
-  static constexpr uint32_t IDESC = ptx::idesc_make(2, BM, BN);
 };
 
-template <int PREC>
-__host__ __device__ constexpr int stage_bytes() { return Tr<PREC>::PARTS * (TILE_A + TILE_B); }
-template <int PREC>
-__host__ __device__ constexpr int smem_bytes() { return Tr<PREC>::STAGES * stage_bytes<PREC>() + 1024 + 512; }
+// GEMM2 configuration for j-tile width BN2 (128 or 256): the B operand is
+// loaded as BN2 / 128 boxes of 128 rows; deeper pipelines for the narrow tile.
+template <int PREC, int BN2>
+struct G2Cfg {
+  static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
+  static constexpr int TILE_B2 = BN2 * ROWB;
+  static constexpr int SB = PARTS * (TILE_A + TILE_B2);
+  static constexpr int STAGES = PREC == LRDM_BF16X3 ? (BN2 == 256 ? 4 : 6) : (BN2 == 256 ? 8 : 12);
+  static constexpr int SMEM = STAGES * SB + 1024 + 512;
+  static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, BN2);
+};
 
 
 struct Bars {
@@ -113,21 +114,22 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-template <int PREC>
+template <int PREC, int BN2>
 __device__ __forceinline__ void issue_stage_mmas(uint32_t d, uint32_t sa, uint32_t first) {
+  using C = G2Cfg<PREC, BN2>;
   constexpr int PARTS = Tr<PREC>::PARTS;
   const uint32_t a0 = sa, a1 = sa + TILE_A;
-  const uint32_t b0 = sa + PARTS * TILE_A, b1 = b0 + TILE_B;
+  const uint32_t b0 = sa + PARTS * TILE_A, b1 = b0 + C::TILE_B2;
 #pragma unroll
   for (int kk = 0; kk < KSTEPS; ++kk) {     // 32-byte K steps along the swizzled row
     const uint32_t off = kk * 32;
     const uint32_t acc = (first && kk == 0) ? 0u : 1u;
     if (PREC == LRDM_BF16X3) {
-      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
-      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b1 + off), Tr<PREC>::IDESC, 1);
-      ptx::mma_f16(d, ptx::desc_k_sw64(a1 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, 1);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), C::IDESC, acc);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b1 + off), C::IDESC, 1);
+      ptx::mma_f16(d, ptx::desc_k_sw64(a1 + off), ptx::desc_k_sw64(b0 + off), C::IDESC, 1);
     } else {
-      ptx::mma_tf32(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), Tr<PREC>::IDESC, acc);
+      ptx::mma_tf32(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), C::IDESC, acc);
     }
   }
 }
@@ -154,6 +156,7 @@ struct G2Params {
   long long v_stride[TC_MAX_SLOTS];
   void* out[TC_MAX_SLOTS];
   long long out_stride[TC_MAX_SLOTS];
+  int nR[TC_MAX_SLOTS];             // row blocks processed (the problem's nR; fewer when tuning)
   int out_io, out_is_io;
   int* status;
 };
@@ -174,7 +177,7 @@ __device__ __forceinline__ const TcProblem* g2_item(const G2Params& P, int item,
   const TcProblem* pr = P.probs + P.pid[q];
   const int local = item - P.begin[q];
   const int G = P.kgroup[q], K = P.K[q];
-  const int per = pr->nR * G;
+  const int per = P.nR[q] * G;
   const int kg = local / per;
   const int rem = local - kg * per;
   const int g = min(G, K - kg * G);
@@ -183,12 +186,12 @@ __device__ __forceinline__ const TcProblem* g2_item(const G2Params& P, int item,
   return pr;
 }
 
-template <int PREC>
+template <int PREC, int BN2>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm2_tc(const __grid_constant__ G2Params P) {
-  using T = Tr<PREC>;
-  constexpr int STAGES = T::STAGES, PARTS = T::PARTS, BK = T::BK;
-  constexpr int SB = stage_bytes<PREC>();
+  using C = G2Cfg<PREC, BN2>;
+  constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK;
+  constexpr int SB = C::SB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const Bars B = carve<STAGES>(smem + STAGES * SB);
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     ptx::fence_proxy_async_smem();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(B.tmem_slot, 2 * BN);
+    ptx::tmem_alloc(B.tmem_slot, 2 * BN2);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -236,20 +239,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
       int q, k, R;
       const TcProblem* pr = g2_item(P, item, q, k, R);
-      const int NJ = pr->NJ, ns_pad = pr->ns_pad;
+      const int ns_pad = pr->ns_pad;
+      const int NJ = (ns_pad + BN2 - 1) / BN2;
       const CUtensorMap *mA0 = &pr->g2a0, *mA1 = &pr->g2a1, *mB0 = &pr->g2b0, *mB1 = &pr->g2b1;
       bool ok = true;
       for (int J = 0; J < NJ && ok; ++J) {
-        const int nch = min((J + 1) * BN, ns_pad) / BK;
+        const int nch = min((J + 1) * BN2, ns_pad) / BK;
+        const int nbox = min(BN2, ns_pad - J * BN2) / 128;      // 128-row boxes of B in this j-tile
         for (int ic = 0; ic < nch; ++ic) {
           if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
           uint8_t* st = smem + s * SB;
-          ptx::mbar_arrive_expect_tx(&B.full[s], SB);
+          ptx::mbar_arrive_expect_tx(&B.full[s], PARTS * (TILE_A + nbox * 128 * ROWB));
           ptx::tma_load_2d(st, mA0, &B.full[s], ic * BK, R * BM);
           if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, mA1, &B.full[s], ic * BK, R * BM);
-          ptx::tma_load_3d(st + PARTS * TILE_A, mB0, &B.full[s], ic * BK, J * BN, k);
-          if (PARTS == 2)
-            ptx::tma_load_3d(st + PARTS * TILE_A + TILE_B, mB1, &B.full[s], ic * BK, J * BN, k);
+          for (int hb = 0; hb < nbox; ++hb) {
+            ptx::tma_load_3d(st + PARTS * TILE_A + hb * 128 * ROWB, mB0, &B.full[s], ic * BK,
+                             J * BN2 + hb * 128, k);
+            if (PARTS == 2)
+              ptx::tma_load_3d(st + PARTS * TILE_A + C::TILE_B2 + hb * 128 * ROWB, mB1, &B.full[s],
+                               ic * BK, J * BN2 + hb * 128, k);
+          }
           pending[s] = (int)ph;
           if (++s == STAGES) { s = 0; ph ^= 1; }
         }
@@ -266,16 +275,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
       int q, k, R;
       const TcProblem* pr = g2_item(P, item, q, k, R);
-      const int NJ = pr->NJ, ns_pad = pr->ns_pad;
+      const int ns_pad = pr->ns_pad;
+      const int NJ = (ns_pad + BN2 - 1) / BN2;
       for (int J = 0; J < NJ && ok; ++J) {
         if (!wait1(&B.acc_empty[a], aph ^ 1, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(a * BN);
-        const int nch = min((J + 1) * BN, ns_pad) / BK;
+        const uint32_t d = tmem + (uint32_t)(a * BN2);
+        const int nch = min((J + 1) * BN2, ns_pad) / BK;
         for (int ic = 0; ic < nch; ++ic) {
           if (!wait1(&B.full[s], ph, B, P.status)) { ok = false; break; }
           ptx::tc_fence_after();
-          issue_stage_mmas<PREC>(d, ptx::smem_u32(smem + s * SB), ic == 0);
+          issue_stage_mmas<PREC, BN2>(d, ptx::smem_u32(smem + s * SB), ic == 0);
           ptx::mma_commit(&B.empty[s]);
           if (++s == STAGES) { s = 0; ph ^= 1; }
         }
@@ -296,7 +306,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
       int q, k, R;
       const TcProblem* pr = g2_item(P, item, q, k, R);
-      const int NJ = pr->NJ, ns_pad = pr->ns_pad;
+      const int ns_pad = pr->ns_pad;
+      const int NJ = (ns_pad + BN2 - 1) / BN2;
       const long long Ng = pr->Ng;
       const void* psi0 = pr->psi0;
       const void* psi1 = pr->psi1;
@@ -306,12 +317,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!waitw(&B.acc_full[a], aph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
         float part = 0.f;
-        const uint32_t tb = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * BN);
+        const uint32_t tb = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * BN2);
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int c = 0; c < BN2 / 32; ++c) {
           float v[32];
           ptx::tmem_ld32(tb + c * 32, v);
-          const int j0 = J * BN + c * 32;
+          const int j0 = J * BN2 + c * 32;
           if (r < Ng && j0 < ns_pad) {
             const long long o = r * ns_pad + j0;
             if (PREC == LRDM_BF16X3) {
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, 2 * BN);
+    ptx::tmem_dealloc(tmem, 2 * BN2);
   }
 }
 
@@ -409,8 +420,9 @@ struct G1Cfg {
   // elements per column and has two parts (hi, lo); tf32 one element per column
   static constexpr int ACOLS = BK;
   static constexpr int SLOT = 2 * ACOLS;
-  static constexpr int B_OFF = PARTS * G1_TILE;
-  static constexpr int SC_OFF = 2 * PARTS * G1_TILE;
+  static constexpr int A_BYTES = BM * BK * 4;                   // FP32 A rows (128-byte rows for bf16 mode)
+  static constexpr int B_OFF = A_BYTES;
+  static constexpr int SC_OFF = B_OFF + PARTS * G1_TILE;
   static constexpr int STRIDE = SC_OFF + 1024;                  // 1024-aligned stages
   static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
   static constexpr int SEG = 1024 / BK;                          // stages per accumulation segment
@@ -428,8 +440,14 @@ struct G1Params {
   int pid[TC_MAX_SLOTS];
   int K[TC_MAX_SLOTS];
   float* X[TC_MAX_SLOTS];           // [K][ns_pad][ns_pad] per slot
+  int dpt;                          // directions per tile (1 or 2)
+  int nch_lim;                      // > 0: reduce over the first nch_lim stages only (tuning)
   int* status;
 };
+
+__device__ __forceinline__ int g1_nch(const G1Params& P, const TcProblem* pr) {
+  return P.nch_lim > 0 ? min(P.nch_lim, pr->nch) : pr->nch;
+}
 
 // Item -> slot q, first direction k0, directions nd (1 or 2), tile I <= J.
 // Direction pairs run fastest: the pairs of one tile run side by side on
@@ -440,12 +458,12 @@ __device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item,
   q = find_slot(P.begin, P.nslot, item);
   const TcProblem* pr = P.probs + P.pid[q];
   const int idx = item - P.begin[q];
-  const int K = P.K[q];
-  const int npair = (K + 1) >> 1;
+  const int K = P.K[q], dpt = P.dpt;
+  const int npair = (K + dpt - 1) / dpt;
   int t = idx / npair;
   const int pp = idx - t * npair;
-  k0 = 2 * pp;
-  nd = min(2, K - k0);
+  k0 = dpt * pp;
+  nd = min(dpt, K - k0);
   int j = 0;
   while (t > j) {                   // column j holds tiles I = 0..j
     t -= j + 1;
@@ -456,72 +474,70 @@ __device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item,
   return pr;
 }
 
-// The weighted A operand of one stage for this thread's row: 16-byte chunks
-// 2h and 2h + 1 of the row (elements [16 h, 16 h + 16) of bf16 hi / lo input,
-// [8 h, 8 h + 8) of fp32 input) times each direction's weights, stored at TMEM
-// address ta (this warp's lane quarter, first column of the stage's slot).
+// The weighted A operand of one stage for this thread's row: elements
+// [BK/2 h, BK/2 h + BK/2) of the FP32 row times each direction's weights,
+// split into bf16 hi / lo (or rounded to TF32) and stored at TMEM address ta
+// (this warp's lane quarter, first column of the stage's slot).  Packed FP32
+// pair arithmetic (two elements per instruction).
 template <int PREC>
 __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd, uint32_t ta) {
   using C = G1Cfg<PREC>;
-  const uint32_t ra = st + row * ROWB;
-  const int sw = (row >> 1) & 3;                 // 64-byte swizzle of this row
   if (PREC == LRDM_BF16X3) {
+    // A rows of 32 FP32 = 128 bytes, 128-byte swizzle: chunk c sits at c ^ (row % 8)
+    const uint32_t ra = st + row * 128;
+    const int sw = row & 7;
+    uint64_t xp[8];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {               // one 16-byte chunk (8 elements) at a time
-      const int c = 2 * h + u;
-      const int p = c ^ sw;
-      const uint4 hv = ptx::lds128(ra + p * 16), lv = ptx::lds128(ra + G1_TILE + p * 16);
-      const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {lv.x, lv.y, lv.z, lv.w};
-      float x[8];
+    for (int u = 0; u < 4; ++u) {
+      const uint4 v = ptx::lds128(ra + (((4 * h + u) ^ sw) << 4));
+      xp[2 * u] = ptx::f2_pack(v.x, v.y);
+      xp[2 * u + 1] = ptx::f2_pack(v.z, v.w);
+    }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        x[2 * e] = bf_lo(hw[e]) + bf_lo(lw[e]);
-        x[2 * e + 1] = bf_hi(hw[e]) + bf_hi(lw[e]);
+    for (int d = 0; d < 2; ++d) {
+      if (d >= nd) break;
+      const uint32_t sc = st + C::SC_OFF + d * C::BK * 4 + h * 16 * 4;
+      uint32_t oh[8], ol[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint4 w = ptx::lds128(sc + u * 16);
+        const uint64_t y0 = ptx::f2_mul(xp[2 * u], ptx::f2_pack(w.x, w.y));
+        const uint64_t y1 = ptx::f2_mul(xp[2 * u + 1], ptx::f2_pack(w.z, w.w));
+        const uint32_t h0 = ptx::bf2_from_f2(y0), h1 = ptx::bf2_from_f2(y1);
+        oh[2 * u] = h0;
+        oh[2 * u + 1] = h1;
+        ol[2 * u] = ptx::bf2_from_f2(ptx::f2_sub(y0, ptx::f2_from_bf2(h0)));
+        ol[2 * u + 1] = ptx::bf2_from_f2(ptx::f2_sub(y1, ptx::f2_from_bf2(h1)));
       }
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        if (d >= nd) break;
-        const uint32_t sc = st + C::SC_OFF + d * C::BK * 4 + c * 8 * 4;
-        const uint4 s0 = ptx::lds128(sc), s1 = ptx::lds128(sc + 16);
-        const float w[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
-                            __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
-                            __uint_as_float(s1.z), __uint_as_float(s1.w)};
-        uint32_t oh[4], ol[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float y0 = x[2 * e] * w[2 * e], y1 = x[2 * e + 1] * w[2 * e + 1];
-          const __nv_bfloat162 hi2 = __floats2bfloat162_rn(y0, y1);
-          const float2 hf = __bfloat1622float2(hi2);
-          const __nv_bfloat162 lo2 = __floats2bfloat162_rn(y0 - hf.x, y1 - hf.y);
-          oh[e] = *reinterpret_cast<const uint32_t*>(&hi2);
-          ol[e] = *reinterpret_cast<const uint32_t*>(&lo2);
-        }
-        ptx::tmem_st4(ta + d * C::ACOLS + c * 4, oh);          // hi: columns [0, 16) of the direction
-        ptx::tmem_st4(ta + d * C::ACOLS + 16 + c * 4, ol);     // lo: columns [16, 32)
-      }
+      ptx::tmem_st8(ta + d * C::ACOLS + h * 8, oh);          // hi: columns [0, 16) of the direction
+      ptx::tmem_st8(ta + d * C::ACOLS + 16 + h * 8, ol);     // lo: columns [16, 32)
     }
   } else {
-    float x[8];
+    // A rows of 16 FP32 = 64 bytes, 64-byte swizzle: chunk c sits at c ^ ((row / 2) % 4)
+    const uint32_t ra = st + row * ROWB;
+    const int sw = (row >> 1) & 3;
+    uint64_t xp[4];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int p = (2 * h + u) ^ sw;
-      const uint4 v = ptx::lds128(ra + p * 16);
-      x[4 * u] = __uint_as_float(v.x);
-      x[4 * u + 1] = __uint_as_float(v.y);
-      x[4 * u + 2] = __uint_as_float(v.z);
-      x[4 * u + 3] = __uint_as_float(v.w);
+      const uint4 v = ptx::lds128(ra + (((2 * h + u) ^ sw) << 4));
+      xp[2 * u] = ptx::f2_pack(v.x, v.y);
+      xp[2 * u + 1] = ptx::f2_pack(v.z, v.w);
     }
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       if (d >= nd) break;
       const uint32_t sc = st + C::SC_OFF + d * C::BK * 4 + h * 8 * 4;
-      const uint4 s0 = ptx::lds128(sc), s1 = ptx::lds128(sc + 16);
-      const float w[8] = {__uint_as_float(s0.x), __uint_as_float(s0.y), __uint_as_float(s0.z),
-                          __uint_as_float(s0.w), __uint_as_float(s1.x), __uint_as_float(s1.y),
-                          __uint_as_float(s1.z), __uint_as_float(s1.w)};
       uint32_t o[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) o[e] = __float_as_uint(tf32_round(x[e] * w[e]));
+      for (int u = 0; u < 2; ++u) {
+        const uint4 w = ptx::lds128(sc + u * 16);
+        const uint64_t y0 = ptx::f2_mul(xp[2 * u], ptx::f2_pack(w.x, w.y));
+        const uint64_t y1 = ptx::f2_mul(xp[2 * u + 1], ptx::f2_pack(w.z, w.w));
+        o[4 * u] = __float_as_uint(tf32_round(__uint_as_float((uint32_t)y0)));
+        o[4 * u + 1] = __float_as_uint(tf32_round(__uint_as_float((uint32_t)(y0 >> 32))));
+        o[4 * u + 2] = __float_as_uint(tf32_round(__uint_as_float((uint32_t)y1)));
+        o[4 * u + 3] = __float_as_uint(tf32_round(__uint_as_float((uint32_t)(y1 >> 32))));
+      }
       ptx::tmem_st8(ta + d * C::ACOLS + h * 8, o);
     }
   }
@@ -562,8 +578,9 @@ __device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, co
   constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::STRIDE;
   for (int q = 0; q < P.nslot; ++q) {
     const TcProblem* pr = P.probs + P.pid[q];
-    ptx::tmap_acquire(&pr->g1a0);
-    if (PARTS == 2) ptx::tmap_acquire(&pr->g1a1);
+    ptx::tmap_acquire(&pr->g1a);
+    ptx::tmap_acquire(&pr->g1b0);
+    if (PARTS == 2) ptx::tmap_acquire(&pr->g1b1);
   }
   int s = 0;
   uint32_t ph = 0;
@@ -575,17 +592,16 @@ __device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, co
     const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
     const float* w0 = pr->a + (long long)k0 * pr->a_stride;
     const long long wstride = pr->a_stride;
-    const int nch = pr->nch;
-    const CUtensorMap *m0 = &pr->g1a0, *m1 = &pr->g1a1;
-    const uint32_t tx = 2 * PARTS * G1_TILE + nd * BK * 4;
+    const int nch = g1_nch(P, pr);
+    const CUtensorMap *ma = &pr->g1a, *mb0 = &pr->g1b0, *mb1 = &pr->g1b1;
+    const uint32_t tx = C::A_BYTES + PARTS * G1_TILE + nd * BK * 4;
     for (int rc = 0; rc < nch; ++rc) {
       if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
       uint8_t* st = smem + s * SB;
       ptx::mbar_arrive_expect_tx(&B.full[s], tx);
-      ptx::tma_load_4d(st, m0, &B.full[s], 0, 0, rc, I);
-      if (PARTS == 2) ptx::tma_load_4d(st + G1_TILE, m1, &B.full[s], 0, 0, rc, I);
-      ptx::tma_load_4d(st + C::B_OFF, m0, &B.full[s], 0, 0, rc, J);
-      if (PARTS == 2) ptx::tma_load_4d(st + C::B_OFF + G1_TILE, m1, &B.full[s], 0, 0, rc, J);
+      ptx::tma_load_4d(st, ma, &B.full[s], 0, 0, rc, I);
+      ptx::tma_load_4d(st + C::B_OFF, mb0, &B.full[s], 0, 0, rc, J);
+      if (PARTS == 2) ptx::tma_load_4d(st + C::B_OFF + G1_TILE, mb1, &B.full[s], 0, 0, rc, J);
       for (int d = 0; d < nd; ++d)
         ptx::bulk_load(st + C::SC_OFF + d * BK * 4, w0 + d * wstride + (long long)rc * BK, BK * 4,
                        &B.full[s]);
@@ -608,7 +624,7 @@ __device__ __forceinline__ void g1_mma(const G1Params& P, uint8_t* smem, const B
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
     int q, k0, nd, I, J;
     const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
-    const int nch = pr->nch;
+    const int nch = g1_nch(P, pr);
     const int nseg = (nch + SEG - 1) / SEG;
     for (int sg = 0; sg < nseg && ok; ++sg) {
       if (!wait1(&B.acc_empty[0], aph ^ 1, B, P.status)) { ok = false; break; }
@@ -650,7 +666,7 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
     int q, k0, nd, I, J;
     const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
-    const int nch = pr->nch, ns = pr->ns, ns_pad = pr->ns_pad;
+    const int nch = g1_nch(P, pr), ns = pr->ns, ns_pad = pr->ns_pad;
     const int nseg = (nch + SEG - 1) / SEG;
 #pragma unroll
     for (int c = 0; c < 128; ++c) sum[c] = 0.f;
@@ -775,7 +791,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // Map of rank 2-4 over a row-major array; box inner extent = 64 bytes,
 // 64-byte swizzle (matching desc_k_sw64).
 bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int rank, const uint64_t* dims,
-              const uint64_t* strides_bytes, const uint32_t* box) {
+              const uint64_t* strides_bytes, const uint32_t* box,
+              CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_64B) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t gd[4];
@@ -788,7 +805,7 @@ bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int rank, const 
   for (int i = 0; i < rank - 1; ++i) gs[i] = strides_bytes[i];
   CUresult r = fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                   rank, const_cast<void*>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -822,9 +839,13 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   // operand of one stage) is one contiguous 8 KB tile.
   const void* t0 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_hi : (const void*)c.psiT32;
   const void* t1 = PREC == LRDM_BF16X3 ? (const void*)c.psiT_lo : (const void*)c.psiT32;
+  const void* ta = PREC == LRDM_BF16X3 ? (const void*)c.psiTf : (const void*)c.psiT32;
   const uint64_t d1[4] = {(uint64_t)BK, 128, (uint64_t)(S.Ng_pad / BK), (uint64_t)(c.ns_pad / 128)};
   const uint64_t s1[3] = {(uint64_t)BK * eb, (uint64_t)128 * BK * eb, (uint64_t)128 * S.Ng_pad * eb};
+  const uint64_t sa[3] = {(uint64_t)BK * 4, (uint64_t)128 * BK * 4, (uint64_t)128 * S.Ng_pad * 4};
   const uint32_t bA1[4] = {(uint32_t)BK, 128, 1, 1};
+  // FP32 A rows: BK * 4 bytes (128 for bf16 mode -> 128-byte swizzle, 64 for TF32)
+  const CUtensorMapSwizzle swa = BK * 4 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   // GEMM2: Psi rows [Ng_pad][ns_pad] (A) and X'' [k_max][j][i] (B).
   const void* r0 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_hi : (const void*)c.psiR32;
   const void* r1 = PREC == LRDM_BF16X3 ? (const void*)c.psiR_lo : (const void*)c.psiR32;
@@ -835,8 +856,9 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   const uint32_t bA2[2] = {(uint32_t)BK, (uint32_t)BM};
   const uint64_t dB2[3] = {(uint64_t)c.ns_pad, (uint64_t)c.ns_pad, (uint64_t)S.kmax};
   const uint64_t sB2[2] = {(uint64_t)c.ns_pad * eb, (uint64_t)c.ns_pad * c.ns_pad * eb};
-  const uint32_t bB2[3] = {(uint32_t)BK, (uint32_t)BN, 1};
-  if (!make_map(&pr.g1a0, t0, eb, 4, d1, s1, bA1) || !make_map(&pr.g1a1, t1, eb, 4, d1, s1, bA1) ||
+  const uint32_t bB2[3] = {(uint32_t)BK, 128, 1};            // GEMM2 B: 128-row boxes
+  if (!make_map(&pr.g1a, ta, 4, 4, d1, sa, bA1, swa) || !make_map(&pr.g1b0, t0, eb, 4, d1, s1, bA1) ||
+      !make_map(&pr.g1b1, t1, eb, 4, d1, s1, bA1) ||
       !make_map(&pr.g2a0, r0, eb, 2, dA2, sA2, bA2) || !make_map(&pr.g2a1, r1, eb, 2, dA2, sA2, bA2) ||
       !make_map(&pr.g2b0, x0, eb, 3, dB2, sB2, bB2) || !make_map(&pr.g2b1, x1, eb, 3, dB2, sB2, bB2))
     return false;
@@ -848,7 +870,7 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   pr.ns = c.ns;
   pr.ns_pad = c.ns_pad;
   pr.nI = c.ns_pad / BM;
-  pr.NJ = (c.ns_pad + BN - 1) / BN;
+  pr.NJ = (c.ns_pad + 255) / 256;        // GEMM2 j-tiles at the default width
   pr.ntiles = pr.nI * (pr.nI + 1) / 2;    // GEMM1 128 x 128 tiles with I <= J
   pr.nch = (int)(S.Ng_pad / BK);
   pr.nR = (int)(S.Ng_pad / BM);
@@ -875,11 +897,13 @@ void order_slots(const TcEntry* e, int n, int gemm, int* order) {
 }
 
 template <int PREC>
-cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st) {
+cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, const TcTune& t,
+                        int nch_lim) {
   static bool attr = false;
   const int smem = G1Cfg<PREC>::SMEM;
   cudaError_t err = set_smem(k_gemm1_tc<PREC>, smem, attr);
   if (err != cudaSuccess) return err;
+  const int dpt = t.g1_dpt == 1 ? 1 : 2;
   for (int base = 0; base < n; base += TC_MAX_SLOTS) {
     const int m = n - base < TC_MAX_SLOTS ? n - base : TC_MAX_SLOTS;
     int order[TC_MAX_SLOTS];
@@ -887,16 +911,18 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st) {
     G1Params P;
     memset(&P, 0, sizeof(P));
     P.status = status;
+    P.dpt = dpt;
+    P.nch_lim = nch_lim;
     int items = 0, q = 0;
-    for (int t = 0; t < m; ++t) {
-      const TcEntry& x = e[base + order[t]];
+    for (int u = 0; u < m; ++u) {
+      const TcEntry& x = e[base + order[u]];
       if (x.K <= 0) continue;
       P.probs = x.dev_base;
       P.pid[q] = x.pid;
       P.K[q] = x.K;
       P.X[q] = static_cast<float*>(x.X);
       P.begin[q] = items;
-      items += x.host->ntiles * ((x.K + 1) / 2);
+      items += x.host->ntiles * ((x.K + dpt - 1) / dpt);
       ++q;
     }
     P.nslot = q;
@@ -909,13 +935,14 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st) {
   return cudaSuccess;
 }
 
-template <int PREC>
+template <int PREC, int BN2>
 cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int* status,
-                        cudaStream_t st) {
+                        cudaStream_t st, const TcTune& t, int nR_lim) {
   static bool attr = false;
-  const int smem = smem_bytes<PREC>();
-  cudaError_t err = set_smem(k_gemm2_tc<PREC>, smem, attr);
+  const int smem = G2Cfg<PREC, BN2>::SMEM;
+  cudaError_t err = set_smem(k_gemm2_tc<PREC, BN2>, smem, attr);
   if (err != cudaSuccess) return err;
+  const int kg = t.g2_kgroup == 1 || t.g2_kgroup == 4 ? t.g2_kgroup : 2;
   for (int base = 0; base < n; base += TC_MAX_SLOTS) {
     const int m = n - base < TC_MAX_SLOTS ? n - base : TC_MAX_SLOTS;
     int order[TC_MAX_SLOTS];
@@ -926,27 +953,28 @@ cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int*
     P.out_is_io = out_is_io;
     P.status = status;
     int items = 0, q = 0;
-    for (int t = 0; t < m; ++t) {
-      const TcEntry& x = e[base + order[t]];
+    for (int u = 0; u < m; ++u) {
+      const TcEntry& x = e[base + order[u]];
       if (x.K <= 0) continue;
       P.probs = x.dev_base;
       P.pid[q] = x.pid;
       P.K[q] = x.K;
-      P.kgroup[q] = x.K < 2 ? x.K : 2;
+      P.kgroup[q] = x.K < kg ? x.K : kg;
       P.factor[q] = x.factor;
       P.v[q] = x.v;
       P.v_stride[q] = x.v_stride;
       P.out[q] = x.out;
       P.out_stride[q] = x.out_stride;
+      P.nR[q] = nR_lim > 0 && nR_lim < x.host->nR ? nR_lim : x.host->nR;
       P.begin[q] = items;
-      items += x.host->nR * x.K;
+      items += P.nR[q] * x.K;
       ++q;
     }
     P.nslot = q;
     P.begin[q] = items;
     if (items == 0) continue;
     const int grid = items < num_sms() ? items : num_sms();
-    k_gemm2_tc<PREC><<<grid, NTHREADS, smem, st>>>(P);
+    k_gemm2_tc<PREC, BN2><<<grid, NTHREADS, smem, st>>>(P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   return cudaSuccess;
@@ -968,15 +996,20 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
   return build_problem<LRDM_TF32>(c, S, ch, pr);
 }
 
-cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st) {
-  if (prec == LRDM_BF16X3) return gemm1_group<LRDM_BF16X3>(e, n, status, st);
-  return gemm1_group<LRDM_TF32>(e, n, status, st);
+cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
+                                  const TcTune& t, int nch_lim) {
+  if (prec == LRDM_BF16X3) return gemm1_group<LRDM_BF16X3>(e, n, status, st, t, nch_lim);
+  return gemm1_group<LRDM_TF32>(e, n, status, st, t, nch_lim);
 }
 
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
-                                  int* status, cudaStream_t st) {
-  if (prec == LRDM_BF16X3) return gemm2_group<LRDM_BF16X3>(e, n, out_io, out_is_io, status, st);
-  return gemm2_group<LRDM_TF32>(e, n, out_io, out_is_io, status, st);
+                                  int* status, cudaStream_t st, const TcTune& t, int nR_lim) {
+  const bool narrow = t.g2_bn == 128;
+  if (prec == LRDM_BF16X3)
+    return narrow ? gemm2_group<LRDM_BF16X3, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim)
+                  : gemm2_group<LRDM_BF16X3, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim);
+  return narrow ? gemm2_group<LRDM_TF32, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim)
+                : gemm2_group<LRDM_TF32, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim);
 }
 
 }  // namespace lrdm

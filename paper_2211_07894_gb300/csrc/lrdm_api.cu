@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <new>
+#include <string>
 #include <vector>
 
 using namespace lrdm;
@@ -185,7 +186,12 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
     LRDM_CU(cudaMemcpyAsync(ch.eps, eps[c].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
     LRDM_CU(cudaMemcpyAsync(ch.occ, occ[c].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
     LRDM_CK(dalloc(ctx, &ch.L, (size_t)ns * ns, false));
-    LRDM_CU(launch_loewner(ch.eps, ch.occ, ns, S.mu, S.kT, S.occ_given ? 1 : 0, o.degen_tol, ch.L, st));
+    if (o.fermi_T > 0)
+      for (int i = 0; i < ns; ++i)
+        if (!(fabs(eps[c][i] - S.mu) < S.kT * std::ldexp(1.0, o.fermi_T + 1)))
+          return LRDM_ERR_INVALID_ARG;     // outside the recursion's monotone window
+    LRDM_CU(launch_loewner(ch.eps, ch.occ, ns, S.mu, S.kT, S.occ_given ? 1 : 0, o.degen_tol,
+                           o.fermi_T, ch.L, st));
     if (is_tc(prec)) {
       LRDM_CK(dalloc(ctx, &ch.Lf, (size_t)ch.ns_pad * ch.ns_pad, false));
       LRDM_CU(launch_loewner_f32(ch.L, ns, ch.ns_pad, ch.Lf, st));
@@ -216,6 +222,7 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
         LRDM_CK(dalloc(ctx, &ch.psiR_lo, npad, false));
         LRDM_CK(dalloc(ctx, &ch.psiT_hi, npad, false));
         LRDM_CK(dalloc(ctx, &ch.psiT_lo, npad, false));
+        LRDM_CK(dalloc(ctx, &ch.psiTf, npad, false));
       }
     }
     LRDM_CU(launch_convert_psi(in.psi[c], o.io_dtype, in.ld_psi[c], S.Ng, ns, ch, prec, S.Ng_pad, st));
@@ -343,9 +350,10 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
   count(ctx, (n + TC_MAX_SLOTS - 1) / TC_MAX_SLOTS);
   cudaError_t e = gemm == 1
                       ? launch_gemm1_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
-                                              ctx->d_status, st)
+                                              ctx->d_status, st, ctx->tune)
                       : launch_gemm2_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
-                                              ctx->opt.io_dtype, out_is_io, ctx->d_status, st);
+                                              ctx->opt.io_dtype, out_is_io, ctx->d_status, st,
+                                              ctx->tune);
   prof_end(ctx, pi, st);
   return from_cuda(e);
 }
@@ -358,6 +366,136 @@ TcEntry tc_entry(lrdm_ctx* ctx, int s, int c, int K) {
   x.pid = pid;
   x.K = K;
   return x;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: launch shape of the tensor-core contractions
+// ---------------------------------------------------------------------------
+
+// Identifies the problem set (device, precision, every (N_g, N_s padded, k_max)).
+std::string tune_key(lrdm_ctx* ctx) {
+  int dev = 0, sms = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  std::string k = "sm" + std::to_string(major) + std::to_string(minor) + "x" + std::to_string(sms) +
+                  ";prec" + std::to_string(ctx->opt.prec);
+  for (int s = 0; s < ctx->nsys; ++s)
+    for (int c = 0; c < ctx->sys[s].nspin; ++c)
+      k += ";" + std::to_string(ctx->sys[s].Ng) + "," + std::to_string(ctx->sys[s].ch[c].ns_pad) +
+           "," + std::to_string(ctx->sys[s].kmax);
+  return k;
+}
+
+// Cache file: one JSON object per line,
+//   {"key": "...", "g1_dpt": 2, "g2_bn": 256, "g2_kgroup": 2}
+bool tune_cache_read(const char* path, const std::string& key, TcTune& t) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[4096];
+  const std::string want = "\"key\": \"" + key + "\"";
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    if (!strstr(line, want.c_str())) continue;
+    const char* a = strstr(line, "\"g1_dpt\":");
+    const char* b = strstr(line, "\"g2_bn\":");
+    const char* c = strstr(line, "\"g2_kgroup\":");
+    TcTune u;
+    if (a && b && c && sscanf(a, "\"g1_dpt\": %d", &u.g1_dpt) == 1 &&
+        sscanf(b, "\"g2_bn\": %d", &u.g2_bn) == 1 &&
+        sscanf(c, "\"g2_kgroup\": %d", &u.g2_kgroup) == 1 && (u.g1_dpt == 1 || u.g1_dpt == 2) &&
+        (u.g2_bn == 128 || u.g2_bn == 256) &&
+        (u.g2_kgroup == 1 || u.g2_kgroup == 2 || u.g2_kgroup == 4)) {
+      t = u;
+      found = true;                  // the last matching line wins
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_append(const char* path, const std::string& key, const TcTune& t) {
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"g1_dpt\": %d, \"g2_bn\": %d, \"g2_kgroup\": %d}\n",
+          key.c_str(), t.g1_dpt, t.g2_bn, t.g2_kgroup);
+  fclose(f);
+}
+
+// Minimum over `reps` timed launches (after one untimed) of a launch function.
+template <typename F>
+float time_launch(F&& launch, cudaStream_t st, int reps, cudaError_t& err) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  err = launch();
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    cudaEventRecord(e0, st);
+    err = launch();
+    cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+// Times the candidate launch shapes on this context's own problems (K = each
+// system's k_max, reductions capped so that the whole search takes about a
+// second at the largest sizes) and keeps the fastest.  The buffers written
+// (X, the GEMM1 weights scratch) are overwritten by every later call.
+lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
+  constexpr int G1_NCH_CAP = 256, G2_NR_CAP = 608, REPS = 3;
+  const char* cache = getenv("LRDM_TUNE_CACHE");
+  const std::string key = tune_key(ctx);
+  if (cache && *cache && tune_cache_read(cache, key, ctx->tune)) return LRDM_OK;
+  std::vector<TcEntry> g1, g2;
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    for (int c = 0; c < S.nspin; ++c) {
+      TcEntry x = tc_entry(ctx, s, c, S.kmax);
+      x.X = S.ch[c].Xpart;
+      g1.push_back(x);
+      TcEntry y = tc_entry(ctx, s, c, S.kmax);
+      y.factor = 1.0;
+      y.out = static_cast<float*>(S.a) + (size_t)c * S.Ng_pad;
+      y.out_stride = (long long)S.nspin * S.Ng_pad;
+      g2.push_back(y);
+    }
+  }
+  cudaError_t err = cudaSuccess;
+  TcTune best = ctx->tune;
+  float tbest = 1e30f;
+  for (int dpt = 1; dpt <= 2; ++dpt) {
+    TcTune t = ctx->tune;
+    t.g1_dpt = dpt;
+    const float ms = time_launch([&] { return launch_gemm1_tc_group(ctx->opt.prec, g1.data(), (int)g1.size(),
+                                                                    ctx->d_status, st, t, G1_NCH_CAP); },
+                                 st, REPS, err);
+    if (err != cudaSuccess) return from_cuda(err);
+    if (ms < tbest) { tbest = ms; best.g1_dpt = dpt; }
+  }
+  tbest = 1e30f;
+  for (int bn = 128; bn <= 256; bn *= 2)
+    for (int kg = 1; kg <= 4; kg *= 2) {
+      TcTune t = ctx->tune;
+      t.g2_bn = bn;
+      t.g2_kgroup = kg;
+      const float ms = time_launch([&] { return launch_gemm2_tc_group(ctx->opt.prec, g2.data(), (int)g2.size(),
+                                                                      LRDM_DTYPE_F32, 0, ctx->d_status, st, t,
+                                                                      G2_NR_CAP); },
+                                   st, REPS, err);
+      if (err != cudaSuccess) return from_cuda(err);
+      if (ms < tbest) { tbest = ms; best.g2_bn = bn; best.g2_kgroup = kg; }
+    }
+  ctx->tune = best;
+  if (cache && *cache) tune_cache_append(cache, key, best);
+  return LRDM_OK;
 }
 
 // The forward path of all systems: potentials and weights per system, then
@@ -500,6 +638,10 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
   if (!(o.pinv_rcond >= 0.0)) return LRDM_ERR_INVALID_ARG;
   if (!(o.degen_tol >= 0.0)) return LRDM_ERR_INVALID_ARG;
   if (o.poisson_symbol != 0 && o.poisson_symbol != 1) return LRDM_ERR_INVALID_ARG;
+  if (o.fermi_T < 0 || o.fermi_T > 30) return LRDM_ERR_INVALID_ARG;
+  if (o.fermi_T > 0)
+    for (int s = 0; s < nsys; ++s)
+      if (sys[s].occ[0]) return LRDM_ERR_INVALID_ARG;
   for (int s = 0; s < nsys; ++s) LRDM_CK(validate_system(sys[s], o));
   if (is_tc(o.prec) && !tc_supported()) return LRDM_ERR_UNSUPPORTED;
 
@@ -522,6 +664,8 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
     if ((rc = dalloc(ctx, &ctx->ls_coef, KMAX_LIMIT)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->ls_scal, 4)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->upd_partial, UPD_BLOCKS)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->gs_scratch, gram_schmidt_scratch())) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->gs_norm, 1)) != LRDM_OK) break;
     ctx->inv_trace.resize(nsys);
     for (int s = 0; s < nsys && rc == LRDM_OK; ++s) {
       rc = setup_system(ctx, s, sys[s], st);
@@ -529,15 +673,18 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
       // 1 / sum_s sum_i L_ii with L_ii = -f_i (1 - f_i)/kT
       double tr = 0.0;
       SysState& S = ctx->sys[s];
+      // sum of the diagonal of L as the device holds it (the same entries the
+      // forward's mu' uses), whichever Fermi operator L describes
       for (int c = 0; c < S.nspin; ++c) {
-        std::vector<double> occ(S.ch[c].ns);
-        if (cudaMemcpyAsync(occ.data(), S.ch[c].occ, occ.size() * 8, cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
+        const int ns = S.ch[c].ns;
+        std::vector<double> diag(ns);
+        if (cudaMemcpy2DAsync(diag.data(), sizeof(double), S.ch[c].L, (size_t)(ns + 1) * sizeof(double),
+                              sizeof(double), ns, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
           rc = LRDM_ERR_CUDA;
           break;
         }
-        for (double f : occ) tr += -f * (1.0 - f) / S.kT;
+        for (double l : diag) tr += l;
       }
       ctx->inv_trace[s] = tr != 0.0 ? 1.0 / tr : 0.0;
     }
@@ -564,6 +711,7 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
         break;
       }
       ctx->tc_entries.reserve(2 * nsys);
+      if (o.autotune && (rc = autotune(ctx, st)) != LRDM_OK) break;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = LRDM_ERR_CUDA;
     if (cudaGetLastError() != cudaSuccess) rc = LRDM_ERR_CUDA;
@@ -638,6 +786,61 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
                              static_cast<cudaStream_t>(stream)));
 }
 
+lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol, int r_max,
+                             double alpha, void* rho_inout, void* U, void* T, double* coeff_out,
+                             double* s_rel_out, int* rank_out, double* r_norm_out, void* stream) {
+  if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !U || !T) return LRDM_ERR_INVALID_ARG;
+  if (r_max < 1 || r_max > KMAX_LIMIT || !(s_tol >= 0.0) || !isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SysState& S = ctx->sys[sys];
+  const int io = ctx->opt.io_dtype;
+  const long long n = (long long)S.nspin * S.Ng;
+  const size_t vb = (size_t)n * io_size(io);
+  // u_1 = R / ||R||
+  LRDM_CU(launch_gram_schmidt(nullptr, 0, R, io, n, S.w, U, ctx->gs_scratch, ctx->gs_norm, st));
+  count(ctx, 2);
+  double r_norm = 0.0;
+  LRDM_CU(cudaMemcpyAsync(&r_norm, ctx->gs_norm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  LRDM_CU(cudaStreamSynchronize(st));
+  if (!(r_norm > 0.0) || !isfinite(r_norm)) return LRDM_ERR_INVALID_ARG;
+  if (r_norm_out) *r_norm_out = r_norm;
+  std::vector<const void*> v(ctx->nsys, nullptr);
+  std::vector<void*> f(ctx->nsys, nullptr);
+  std::vector<int> K(ctx->nsys, 0);
+  int rank = 0;
+  for (int i = 0; i < r_max; ++i) {
+    // t_i = d/dlam R[rho + lam u_i]
+    v[sys] = static_cast<const char*>(U) + i * vb;
+    f[sys] = static_cast<char*>(T) + i * vb;
+    K[sys] = 1;
+    LRDM_CK(forward_all(ctx, v.data(), K.data(), f.data(), nullptr, st));
+    rank = i + 1;
+    // least squares on the first i + 1 directions (no update yet) -> s_rel
+    LRDM_CU(launch_ls(R, U, T, io, rank, n, S.w, 0.0, ctx->opt.pinv_rcond, nullptr, ctx->ls_coef,
+                      coeff_out, nullptr, ctx->ls_partial, ctx->ls_scal, ctx->upd_partial,
+                      ctx->d_status, st));
+    count(ctx, 4);
+    double s_rel = 0.0;
+    LRDM_CU(cudaMemcpyAsync(&s_rel, ctx->ls_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LRDM_CU(cudaStreamSynchronize(st));
+    if (s_rel_out) s_rel_out[i] = s_rel;
+    if (s_rel < s_tol || rank == r_max) break;
+    // u_{i+1} = t_i - sum_k <t_i, u_k> u_k, normalised
+    LRDM_CU(launch_gram_schmidt(U, rank, static_cast<const char*>(T) + i * vb, io, n, S.w,
+                                static_cast<char*>(U) + rank * vb, ctx->gs_scratch, ctx->gs_norm, st));
+    count(ctx, 3);
+  }
+  if (rank_out) *rank_out = rank;
+  if (rho_inout) {
+    const double a = alpha < 0.0 ? (r_norm < 2.0 ? 0.5 : 0.1) : alpha;
+    LRDM_CU(launch_ls(R, U, T, io, rank, n, S.w, a, ctx->opt.pinv_rcond, rho_inout, ctx->ls_coef,
+                      coeff_out, nullptr, ctx->ls_partial, ctx->ls_scal, ctx->upd_partial,
+                      ctx->d_status, st));
+    count(ctx, 4);
+  }
+  return LRDM_OK;
+}
+
 lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int io_dtype, int K,
                               long long n, double w, double alpha, double pinv_rcond,
                               void* rho_inout, double* coeff_out, double* s_rel_out,
@@ -662,6 +865,10 @@ lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* 
     SysState& S = ctx->sys[s];
     if (S.last_K < 0) return LRDM_ERR_INVALID_ARG;   // no forward call yet
     if (S.last_K > 0 && (!f_bar[s] || !v_bar[s])) return LRDM_ERR_INVALID_ARG;
+    if (ctx->opt.fermi_T > 0)
+      for (int c = 0; c < S.nspin; ++c)
+        if ((eps_bar && eps_bar[2 * s + c]) || (occ_bar && occ_bar[2 * s + c]))
+          return LRDM_ERR_UNSUPPORTED;
   }
   const bool tc = is_tc(prec);
   const size_t csz = fp64 ? 8 : 4;
@@ -775,6 +982,14 @@ lrdm_status lrdm_get_projection(lrdm_ctx* ctx, int sys, int spin, int k, double*
   if (spin < 0 || spin >= S.nspin || k < 0 || k >= S.last_K) return LRDM_ERR_INVALID_ARG;
   return from_cuda(launch_get_projection(S, spin, k, ctx->opt.prec == LRDM_FP64, out,
                                          static_cast<cudaStream_t>(stream)));
+}
+
+lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_dpt, int* g2_bn, int* g2_kgroup) {
+  if (!ctx) return LRDM_ERR_INVALID_ARG;
+  if (g1_dpt) *g1_dpt = ctx->tune.g1_dpt;
+  if (g2_bn) *g2_bn = ctx->tune.g2_bn;
+  if (g2_kgroup) *g2_kgroup = ctx->tune.g2_kgroup;
+  return LRDM_OK;
 }
 
 lrdm_status lrdm_profile_enable(lrdm_ctx* ctx, int on) {

@@ -47,6 +47,7 @@ struct Channel {
   float* psiR32 = nullptr;           // [Ng_pad][ns_pad]   (TF32, GEMM2 operand)
   __nv_bfloat16* psiT_hi = nullptr;  // Psi^T tile-major [ns_pad/128][Ng_pad/32][128][32] (BF16X3, GEMM1)
   __nv_bfloat16* psiT_lo = nullptr;
+  float* psiTf = nullptr;            // Psi^T tile-major FP32 [ns_pad/128][Ng_pad/32][128][32] (BF16X3, GEMM1 A)
   __nv_bfloat16* psiR_hi = nullptr;  // [Ng_pad][ns_pad]   (BF16X3, GEMM2)
   __nv_bfloat16* psiR_lo = nullptr;
   // workspaces
@@ -91,6 +92,8 @@ struct lrdm_ctx {
   double* ls_coef = nullptr;         // [KMAX_LIMIT]
   double* ls_scal = nullptr;         // [4]: r2, s_rel scratch
   double* upd_partial = nullptr;     // [UPD_BLOCKS]
+  double* gs_scratch = nullptr;      // Gram-Schmidt partial sums (Krylov step)
+  double* gs_norm = nullptr;         // [1] norm of the last normalised direction
   std::vector<void*> allocs;         // every device allocation, freed by lrdm_destroy
   // tensor-core problem table: one entry per (system, channel)
   std::vector<lrdm::TcProblem> tc_host;
@@ -100,6 +103,7 @@ struct lrdm_ctx {
   // CUDA graph of lrdm_gateaux_batch (use_graph)
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key;
+  lrdm::TcTune tune;                 // launch shape of the tensor-core contractions
   std::vector<double> inv_trace;     // per system 1 / sum_s sum_i L_ii
   // profiling (lrdm_profile_enable / lrdm_profile_read)
   bool prof_on = false;
@@ -119,7 +123,8 @@ cudaError_t launch_density(const void* psi_src, int io_dtype, int ld, long long 
 cudaError_t launch_copy_rho(const void* src, int io_dtype, long long Ng, double* rho, cudaStream_t st);
 cudaError_t launch_fx(const double* rho, long long Ng, int spin_polarized, double* fx, cudaStream_t st);
 cudaError_t launch_loewner(const double* eps, const double* occ, int ns, double mu, double kT,
-                           int occ_mode, double degen_tol, double* L, cudaStream_t st);
+                           int occ_mode, double degen_tol, int fermi_T, double* L,
+                           cudaStream_t st);
 cudaError_t launch_to_io(const double* src, long long n, void* dst, int io_dtype, cudaStream_t st);
 // Lf[i][j] = (float) L[i][j] for i, j < ns, 0 in the padding
 cudaError_t launch_loewner_f32(const double* L, int ns, int ns_pad, float* Lf, cudaStream_t st);
@@ -177,6 +182,11 @@ cudaError_t launch_gemm2_simt(int fp64, const void* psi, int ns, long long Ng, c
                               cudaStream_t st);
 
 // ---------------- least squares (k_ls.cu) ----------------
+// out = (t - sum_{k<K} <t, u_k> u_k) / ||.||_w (Krylov step, k_krylov.cu);
+// norm_out[0] = the norm before scaling.  scratch: gram_schmidt_scratch() doubles.
+cudaError_t launch_gram_schmidt(const void* U, int K, const void* t, int io, long long n, double w,
+                                void* out, double* scratch, double* norm_out, cudaStream_t st);
+size_t gram_schmidt_scratch();
 cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype, int K,
                       long long n, double w, double alpha, double rcond, void* rho_inout,
                       double* coef, double* coeff_out, double* s_rel_out, double* partial,
@@ -194,9 +204,12 @@ cudaError_t launch_ls_static(const void* R, const void* v, const void* f, int io
 // tensor map cannot be encoded).
 bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcProblem& pr);
 // Grouped launches over n problems (each with its own K; K = 0 entries skipped).
-cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st);
+// nch_lim / nR_lim > 0 cap the grid reduction (GEMM1) or the row blocks
+// (GEMM2) per problem: partial work with the same item structure (tuning).
+cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
+                                  const TcTune& t, int nch_lim = 0);
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
-                                  int* status, cudaStream_t st);
+                                  int* status, cudaStream_t st, const TcTune& t, int nR_lim = 0);
 bool tc_supported();
 
 }  // namespace lrdm

@@ -9,7 +9,8 @@
 namespace lrdm {
 
 struct TcProblem {
-  CUtensorMap g1a0, g1a1;               // GEMM1: Psi^T tile-major, box 128 rows (A and B)
+  CUtensorMap g1a;                      // GEMM1 A: Psi^T tile-major FP32 (TF32: rounded), box 128 rows
+  CUtensorMap g1b0, g1b1;               // GEMM1 B: Psi^T tile-major bf16 hi / lo (TF32: = A)
   CUtensorMap g2a0, g2a1, g2b0, g2b1;   // GEMM2: Psi rows (A), X'' [k_max][j][i] (B)
   long long Ng;                          // grid points
   long long a_stride;                    // direction stride of the GEMM1 weights
@@ -20,6 +21,15 @@ struct TcProblem {
 };
 
 constexpr int TC_MAX_SLOTS = 16;        // problems per grouped launch
+
+// Launch shape of the tensor-core contractions (chosen by the autotuner or
+// the defaults): directions per GEMM1 tile (1, 2), GEMM2 j-tile width (128,
+// 256) and GEMM2 direction group (directions sharing one Psi row block: 1, 2, 4).
+struct TcTune {
+  int g1_dpt = 2;
+  int g2_bn = 256;
+  int g2_kgroup = 2;
+};
 
 }  // namespace lrdm
 

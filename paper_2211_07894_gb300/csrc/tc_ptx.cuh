@@ -83,6 +83,31 @@ __device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
                : "memory");
 }
 
+// ---------------- packed FP32 pairs ----------------
+__device__ __forceinline__ uint64_t f2_pack(uint32_t lo, uint32_t hi) {
+  return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// Rounds the two FP32 halves of p to bf16 and packs them (low half -> low 16 bits).
+__device__ __forceinline__ uint32_t bf2_from_f2(uint64_t p) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)(p >> 32)), "r"((uint32_t)p));
+  return r;
+}
+// The two bf16 of b widened to an FP32 pair.
+__device__ __forceinline__ uint64_t f2_from_bf2(uint32_t b) {
+  return f2_pack(b << 16, b & 0xffff0000u);
+}
+
 // ---------------- TMA ----------------
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {

@@ -169,6 +169,78 @@ def test_batched_uneven_equals_separate(lib, prec):
         assert err < TOL[prec]
 
 
+def _tune_key(cfgs, prec_code):
+    """The autotuner's cache key of a problem set (device, precision, every
+    (N_g, N_s padded to 128, k_max)); each system's k_max is its K."""
+    props = torch.cuda.get_device_properties(0)
+    major, minor = torch.cuda.get_device_capability(0)
+    k = f"sm{major}{minor}x{props.multi_processor_count};prec{prec_code}"
+    for c in cfgs:
+        ng = int(np.prod(c["n"]))
+        for p in c["psi"]:
+            k += f";{ng},{(p.shape[1] + 127) // 128 * 128},{c['V'].shape[0]}"
+    return k
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_forced_launch_shapes(lib, prec, tmp_path, monkeypatch):
+    """Every non-default launch shape (one direction per projection tile,
+    128-wide response j-tiles, direction groups 1 and 4), forced through the
+    tuning cache: the per-direction projection is unchanged bit for bit, and
+    the response meets the oracle tolerance."""
+    from gpu_helpers import directions, make_context
+    cfgs = workloads.config3(scale=8)[:3]
+    io = IO[prec]
+    base, _ = make_context(cfgs, prec, io)
+    V = [directions(c, io) for c in cfgs]
+    F0, _ = base.gateaux(V)
+    X0 = base.projection(1, sys=1)
+    code = {"tf32": 2, "bf16x3": 3}[prec]
+    for dpt, bn, kg in [(1, 128, 1), (2, 128, 4), (1, 256, 4)]:
+        cache = tmp_path / f"tune_{dpt}_{bn}_{kg}.jsonl"
+        cache.write_text('{"key": "%s", "g1_dpt": %d, "g2_bn": %d, "g2_kgroup": %d}\n'
+                         % (_tune_key(cfgs, code), dpt, bn, kg))
+        monkeypatch.setenv("LRDM_TUNE_CACHE", str(cache))
+        ctx, _ = make_context(cfgs, prec, io, autotune=True)
+        assert ctx.tuning() == {"g1_dpt": dpt, "g2_bn": bn, "g2_kgroup": kg}
+        F, _ = ctx.gateaux(V)
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        assert torch.equal(ctx.projection(1, sys=1), X0)
+        for i, c in enumerate(cfgs):
+            ref = oracle.gateaux(oracle_system(c), c["V"])
+            err = per_direction_rel_err(F[i].double().cpu().numpy(), ref["F"])
+            assert err < TOL[prec]
+            if bn == 256:
+                assert torch.equal(F[i], F0[i])
+        assert len(cache.read_text().splitlines()) == 1     # read, not re-tuned
+
+
+def test_autotune_batched(lib, tmp_path, monkeypatch):
+    """The autotuner on the uneven batch: a valid choice, results within the
+    oracle tolerance, and the choice cached and reused."""
+    from gpu_helpers import directions, make_context
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("LRDM_TUNE_CACHE", str(cache))
+    cfgs = workloads.config3(scale=8)
+    ctx, _ = make_context(cfgs, "bf16x3", torch.float32, autotune=True)
+    t = ctx.tuning()
+    print("autotuned launch shape (uneven batch):", t)
+    assert t["g1_dpt"] in (1, 2) and t["g2_bn"] in (128, 256) and t["g2_kgroup"] in (1, 2, 4)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and '"key": "sm' in lines[0]
+    V = [directions(c, torch.float32) for c in cfgs]
+    F, _ = ctx.gateaux(V)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    for i, c in enumerate(cfgs):
+        ref = oracle.gateaux(oracle_system(c), c["V"])
+        assert per_direction_rel_err(F[i].double().cpu().numpy(), ref["F"]) < TOL["bf16x3"]
+    again, _ = make_context(cfgs, "bf16x3", torch.float32, autotune=True)
+    assert again.tuning() == t
+    assert len(cache.read_text().splitlines()) == 1
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_graph_replay(lib, cfg1, prec):
     """use_graph: the first call on a stream captures the forward path, later
@@ -283,6 +355,75 @@ def test_backward_vs_oracle(lib, prec):
     assert per_direction_rel_err(vbar[0].double().cpu().numpy(), ref["vbar"]) < tol
     assert rel_err(eb[0].cpu().numpy(), ref["eps_bar"][0]) < tol * 10
     assert rel_err(ob[0].cpu().numpy(), ref["occ_bar"][0]) < tol * 10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_recursive_fermi_response(lib, prec):
+    """fermi_T = 8: the device's closed-form Loewner matrix of f_T against the
+    oracle's perturbed recursion (Eq. recursiveFermiOperator), forward and the
+    v-adjoint; eigenvalue / occupation gradients are refused in this mode."""
+    from gpu_helpers import directions, make_context
+    from paper_2211_07894_gb300 import LrdmError
+    cfg = _ragged(cfg_id=23, n=(16, 18, 14), ns=150, K=4, ne=110, kT=0.01)
+    io = IO[prec]
+    ctx, _ = make_context([cfg], prec, io, fermi_T=8)
+    V = directions(cfg, io)
+    (F,), dmu = ctx.gateaux([V])
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    osys = oracle_system(cfg)
+    osys.fermi_T = 8
+    ref = oracle.gateaux(osys, cfg["V"])
+    err = per_direction_rel_err(F.double().cpu().numpy(), ref["F"])
+    print(f"fermi_T=8 {prec}: f rel err {err:.2e}")
+    assert err < TOL[prec]
+    # the recursion at depth 8 differs from Fermi-Dirac by far more than the tolerance
+    full = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    assert per_direction_rel_err(ref["F"], full["F"]) > 100 * TOL["fp64"]
+    fbar = workloads.rng_for(23, 9).standard_normal(cfg["V"].shape)
+    vbar, _, _ = ctx.backward([torch.as_tensor(fbar, dtype=io, device="cuda")], want_eps=False)
+    torch.cuda.synchronize()
+    bref = oracle.backward(osys, fbar, ref)
+    assert per_direction_rel_err(vbar[0].double().cpu().numpy(), bref["vbar"]) < TOL[prec]
+    with pytest.raises(LrdmError) as e:
+        ctx.backward([torch.as_tensor(fbar, dtype=io, device="cuda")], want_eps=True)
+    assert e.value.code == 9          # LRDM_ERR_UNSUPPORTED
+    # eigenvalues outside the recursion's window |eps - mu| < kT 2^(T+1) are refused
+    with pytest.raises(LrdmError) as e:
+        make_context([cfg], prec, io, fermi_T=3)
+    assert e.value.code == 1
+
+
+@pytest.mark.parametrize("prec,spin", [("fp64", False), ("fp64", True), ("bf16x3", False)])
+def test_krylov_step(lib, cfg1, prec, spin):
+    """lrdm_krylov_step against the oracle's LRDM step (§II.B): same rank,
+    directions, derivatives, coefficients and updated density."""
+    from gpu_helpers import make_context
+    io = IO[prec]
+    if spin:
+        cfg = workloads.spin_pair_system(98, (10, 9, 8), 40, 36, 60.0, 0.01, 1)
+    else:
+        cfg = cfg1
+    osys = oracle_system(cfg)
+    R = np.asarray(cfg["R"], dtype=np.float64)
+    ref = oracle.lrdm_krylov_step(osys, R, s_tol=1e-12, r_max=4)
+    # a tolerance between the s_rel of ranks 2 and 3 makes the adaptive stop at 3
+    s_tol = 0.5 * (ref["s_rel"][1] + ref["s_rel"][2])
+    ref = oracle.lrdm_krylov_step(osys, R, s_tol=s_tol, r_max=4, rho=np.stack(osys.rho))
+    ctx, _ = make_context([cfg], prec, io, k_max=1)
+    rho = torch.as_tensor(np.stack(osys.rho), dtype=io, device="cuda")
+    out = ctx.krylov_step(torch.as_tensor(R, dtype=io, device="cuda"), s_tol=s_tol, r_max=4, rho=rho)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert out["rank"] == ref["rank"] == 3
+    tol = TOL[prec]
+    assert abs(out["r_norm"] - ref["r_norm"]) <= 1e-12 * ref["r_norm"]
+    assert np.allclose(out["s_rel"], ref["s_rel"], rtol=10 * tol, atol=0)
+    assert per_direction_rel_err(out["U"].double().cpu().numpy(), ref["U"]) < 10 * tol
+    assert per_direction_rel_err(out["T"].double().cpu().numpy(), ref["T"]) < 10 * tol
+    assert np.allclose(out["a"].cpu().numpy(), ref["a"], rtol=100 * tol, atol=0)
+    assert rel_err(rho.double().cpu().numpy() - np.stack(osys.rho),
+                   ref["rho_new"] - np.stack(osys.rho)) < 100 * tol
 
 
 def test_autograd_function_dot_product(lib, cfg1):

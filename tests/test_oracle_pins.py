@@ -339,6 +339,139 @@ def test_recursive_fermi_closed_form():
     assert np.max(np.abs(oracle.fermi_recursive(eps, mu, kT, 10) - oracle.fermi(eps, mu, kT))) < 1e-6
 
 
+def _matrix_recursion(H, mu, kT, T):
+    """The paper's recursion applied to a dense symmetric matrix (brute force)."""
+    n = H.shape[0]
+    I = np.eye(n)
+    X = 0.5 * I - 2.0 ** (-(T + 2)) * (H - mu * I) / kT
+    for _ in range(T):
+        X2 = X @ X
+        X = np.linalg.solve(X2 + (I - X) @ (I - X), X2)   # X2 (X2 + (I-X)^2)^-1, commuting
+        X = 0.5 * (X + X.T)
+    return X
+
+
+@pytest.mark.parametrize("T", [4, 8, 10])
+def test_recursive_response_is_derivative_of_matrix_recursion(T):
+    """L_T o E equals the central difference of the literal matrix recursion
+    X_T(D + lam E) (one Richardson step), with a 1e-9 Ha pair in D."""
+    rng = workloads.rng_for(97, T)
+    eps = np.sort(rng.uniform(-0.3, 0.3, 9))
+    eps[4] = eps[3] + 1e-9
+    mu, kT = 0.02, 0.01
+    E = rng.standard_normal((9, 9))
+    E = 0.5 * (E + E.T)
+    D = np.diag(eps)
+
+    def d(eta):
+        return (_matrix_recursion(D + eta * E, mu, kT, T) -
+                _matrix_recursion(D - eta * E, mu, kT, T)) / (2 * eta)
+
+    eta = 1e-4 * kT
+    fd = (4 * d(eta / 2) - d(eta)) / 3
+    LT = oracle.loewner_recursive(eps, mu, kT, T)
+    assert np.max(np.abs(LT * E - fd)) < 1e-7 * np.max(np.abs(LT * E))
+
+
+def test_recursive_response_matches_mpmath_closed_form():
+    """Entries of L_T against divided differences of the closed form
+    f_T(e) = 1 / (1 + exp(2^(T+1) artanh(2^-(T+1) (e - mu) / kT))) at 160 digits
+    (deep states have 1 - f_T ~ e^-180, whose differences must not cancel in the
+    reference), gaps down to 1e-12 Ha; the diagonal is f_T'."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 160
+    T, mu, kT = 8, 0.01, 0.005
+    base = np.array([-0.8, -0.05, -0.003, 0.0, 0.004, 0.02, 0.3, 0.9])
+    eps = np.unique(np.concatenate([base + g for g in (0.0, 1e-12, 1e-9, 1e-6, 1e-3)]))
+    LT = oracle.loewner_recursive(eps, mu, kT, T)
+    c = mp.mpf(2) ** (T + 1)
+
+    def fT(e):
+        y = (mp.mpf(e) - mp.mpf(mu)) / mp.mpf(kT)
+        return 1 / (1 + mp.e ** (c * mp.atanh(y / c)))
+
+    worst = 0.0
+    for i in range(len(eps)):
+        for j in range(len(eps)):
+            if i == j:
+                ref = mp.diff(fT, mp.mpf(float(eps[i])))
+            else:
+                ref = (fT(float(eps[i])) - fT(float(eps[j]))) / (mp.mpf(float(eps[i])) - mp.mpf(float(eps[j])))
+            err = float(abs((mp.mpf(float(LT[i, j])) - ref) / ref))
+            # conditioning of x_0 = 1/2 - 2^-(T+2) y: rounding x_0 loses ~2^(T+2)|y| ulp...
+            xi, xj = abs(eps[i] - mu) / kT, abs(eps[j] - mu) / kT
+            bound = 2e-14 + 2.0 ** (T + 2) * 2.2e-16 * (1 + xi + xj) / 8
+            worst = max(worst, err / bound)
+    assert worst < 1.0
+
+
+def test_recursive_response_converges_to_fermi_dirac():
+    """L_T -> the Fermi-Dirac Loewner matrix with error ~ 4^-T."""
+    eps = np.linspace(-1.0, 1.0, 41)
+    mu, kT = 0.1, 0.05
+    L = oracle.loewner(eps, mu, kT)
+    errs = [np.abs(oracle.loewner_recursive(eps, mu, kT, T) - L).max() / np.abs(L).max()
+            for T in (6, 7, 8, 9, 10)]
+    ratios = [errs[t] / errs[t + 1] for t in range(4)]
+    assert all(3.5 < r < 4.5 for r in ratios)
+    assert errs[-1] < 1e-6
+
+
+@pytest.mark.parametrize("spin", [False, True])
+def test_krylov_step_matches_brute_force_krylov_least_squares(cfg1, spin):
+    """The LRDM step (Eqs. jlowrank, krylovOrtho, plowrank, relativeError)
+    against an independent construction: the Krylov space span{R, JR, ...,
+    J^(r-1) R} built by applying J (the Gateaux map) repeatedly, and the
+    least-squares solution min ||J Delta - R||_w over it by lstsq.  Also: the
+    directions are w-orthonormal and s_rel does not increase with the rank."""
+    if spin:
+        sysm_cfg = workloads.spin_pair_system(98, (10, 9, 8), 40, 36, 60.0, 0.01, 1)
+        sysm = oracle_system(sysm_cfg)
+        R = sysm_cfg["R"]
+    else:
+        sysm = oracle_system(cfg1)
+        R = cfg1["R"]
+    w = sysm.w
+    out = oracle.lrdm_krylov_step(sysm, R, s_tol=1e-6, r_max=4)
+    r = out["rank"]
+    assert r == 4
+    U = out["U"].reshape(r, -1)
+    assert np.max(np.abs(w * U @ U.T - np.eye(r))) < 1e-12
+    assert all(b <= a + 1e-12 for a, b in zip(out["s_rel"], out["s_rel"][1:]))
+
+    def J(v):
+        return oracle.gateaux(sysm, v.reshape((1,) + R.shape))["F"][0]
+
+    Kr = [np.asarray(R, dtype=np.float64)]
+    for _ in range(r):
+        Kr.append(J(Kr[-1]))
+    B = np.stack([k.ravel() for k in Kr[:r]], axis=1)          # R, JR, ..., J^(r-1) R
+    JB = np.stack([k.ravel() for k in Kr[1:]], axis=1)         # J of each
+    b, *_ = np.linalg.lstsq(np.sqrt(w) * JB, np.sqrt(w) * np.ravel(R), rcond=None)
+    ref = (B @ b).reshape(R.shape)
+    assert rel_err(out["delta"], ref) < 1e-8
+    # and the residual of the low-rank model equals the last s_rel
+    res = (JB @ b) - np.ravel(R)
+    s_ref = np.sqrt(np.sum(res * res) / np.sum(np.ravel(R) ** 2))
+    assert abs(out["s_rel"][-1] - s_ref) < 1e-8 * max(s_ref, 1e-3)
+
+
+def test_krylov_step_rank_control_and_alpha_schedule(cfg1):
+    sysm = oracle_system(cfg1)
+    R = cfg1["R"]
+    full = oracle.lrdm_krylov_step(sysm, R, s_tol=1e-9, r_max=5)
+    # the rank is the first one whose s_rel is below the tolerance
+    tol = 0.5 * (full["s_rel"][1] + full["s_rel"][2])
+    out = oracle.lrdm_krylov_step(sysm, R, s_tol=tol, r_max=5)
+    assert out["rank"] == 3
+    assert np.allclose(out["U"], full["U"][:3], atol=1e-13)
+    assert oracle.alpha_schedule(2.5) == 0.1 and oracle.alpha_schedule(1.0) == 0.5
+    assert out["alpha"] == (0.5 if out["r_norm"] < 2.0 else 0.1)
+    rho = sysm.rho[0][None, :]
+    out = oracle.lrdm_krylov_step(sysm, R, s_tol=tol, r_max=5, alpha=0.3, rho=rho)
+    assert np.allclose(out["rho_new"], rho - 0.3 * out["delta"], atol=1e-15)
+
+
 def test_mu_bisection():
     eps = np.array([-1.0, -0.5, 0.0, 0.5])
     # half filling of a spectrum symmetric about -0.25: mu = -0.25 exactly
