@@ -77,6 +77,41 @@ def load_peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
+TC_SOURCES = ("paper_2211_07894_gb300/csrc/k_tc.cu", "paper_2211_07894_gb300/csrc/tc_ptx.cuh",
+              "paper_2211_07894_gb300/csrc/tc_problem.h")
+
+
+def tc_source_hash():
+    """SHA-256 of the tensor-core kernel sources (the DRAM counters recorded
+    under profiles/ are valid only for the sources they were taken with)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the ncu summaries
+    under profiles/ (lines 'traffic-record: kernel=... workload=...
+    source_sha256=... dram_bytes_per_launch=...'), or None when no record
+    matches the current kernel sources."""
+    import glob
+    want = tc_source_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                line = line.strip().strip("`")
+                if not line.startswith("traffic-record:"):
+                    continue
+                f = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)
+                if (f.get("kernel") == kernel and f.get("workload") == workload
+                        and f.get("source_sha256") == want):
+                    return float(f["dram_bytes_per_launch"])
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -475,6 +510,7 @@ def main():
     g2 = (prof["gemm2_ms"], prof["gemm2_launches"])
     name, (tms, nl) = max((("projection GEMM (X_k)", g1), ("response GEMM (drho_k)", g2)),
                           key=lambda x: x[1][0])
+    kname = "k_gemm1_tc" if name.startswith("projection") else "k_gemm2_tc"
     avg_s = tms / max(nl, 1) / 1e3
     alg_flops = KDIR * ng * ns * ns           # one launch: K directions, symmetric half
     if args.prec == "bf16x3":
@@ -495,7 +531,8 @@ def main():
         bound, note = "alu", "FP64 peak = measured torch FP64 matmul (1.10 TF/s)"
     achieved = issued / avg_s / 1e12 if avg_s > 0 else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None,
+                "traffic": recorded_traffic(kname, f"{args.grid}^3/{ns}/K{KDIR}/{args.prec}"),
                 "kernel": name, "avg_launch_ms": avg_s * 1e3, "launches": nl,
                 "alg_flop_per_launch": alg_flops, "peak_source": f"{peak_src}; {note}"}
 

@@ -254,6 +254,65 @@ lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol
                              double alpha, void* rho_inout, void* U, void* T, double* coeff_out,
                              double* s_rel_out, int* rank_out, double* r_norm_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Accumulated LRDM (LRDMA, §II.B.1): a low-rank approximation of the Jacobian
+ * kept across SCF steps.  The object holds the history (direction functions
+ * u_k and their Gateaux derivatives t_k, grid functions of n = nspin * N_g
+ * values in the io dtype) independently of any context, since every SCF step
+ * brings a new subspace (a new lrdm_ctx); each step computes new derivatives
+ * with the context it is given.
+ * ------------------------------------------------------------------------- */
+typedef struct lrdm_lrdma lrdm_lrdma;
+
+typedef struct lrdm_lrdma_params {
+  double s_tol;          /* rank tolerance on s_rel (0.3)                         */
+  double beta_tol;       /* linearity-indicator threshold for clearing (0.1)      */
+  double r_norm_clear;   /* clear instead of accumulating when ||R|| > this (1.0) */
+  double alpha;          /* damping; < 0 -> 0.1 while ||R|| >= 2, else 0.5 (-1)   */
+  int r_max_iter;        /* new directions per accumulating step (5)             */
+  int r_max;             /* maximum kept rank, <= the capacity (capacity)         */
+} lrdm_lrdma_params;
+
+typedef enum {
+  LRDMA_FRESH = 0,            /* no history: rank built afresh                    */
+  LRDMA_REUSE = 1,            /* history s_rel < s_tol: used without new ranks     */
+  LRDMA_ACCUMULATE = 2,       /* history extended by new directions                */
+  LRDMA_CLEAR_LINEARITY = 3,  /* beta > beta_tol: cleared, rebuilt (CL)           */
+  LRDMA_CLEAR_RESIDUAL = 4,   /* ||R|| > r_norm_clear: cleared, rebuilt (CR)      */
+  LRDMA_CLEAR_TRUNCATED = 5   /* previous accumulation missed s_tol: cleared (CT) */
+} lrdm_lrdma_event;
+
+typedef struct lrdm_lrdma_report {
+  int event;             /* lrdm_lrdma_event                                     */
+  int rank;              /* directions kept after the step                       */
+  int rank_new;          /* Gateaux derivatives computed in the step             */
+  double s_rel;          /* s_rel of the final low-rank model on R               */
+  double beta;           /* linearity indicator (-1 when not evaluated)          */
+  double r_norm;         /* ||R||                                                */
+  double alpha;          /* damping used                                         */
+} lrdm_lrdma_report;
+
+/* Fills the paper's settings (capacity is set by lrdm_lrdma_create). */
+void lrdm_lrdma_default_params(lrdm_lrdma_params* p);
+/* n = nspin * N_g values per grid function, io dtype, quadrature weight w,
+ * history capacity 1..64 directions (2 * capacity * n values of device memory). */
+lrdm_status lrdm_lrdma_create(lrdm_lrdma** out, long long n, int io_dtype, double w, int capacity);
+/* One step: the decisions of §II.B.1 in the paper's order (CT pending ->
+ * clear; with a history: beta > beta_tol -> clear (CL); history s_rel < s_tol
+ * -> reuse; ||R|| > r_norm_clear -> clear (CR); else accumulate up to
+ * r_max_iter new directions orthogonal to the history, scheduling CT when
+ * s_tol is not reached), then rho_inout <- rho_inout - alpha sum a_k u_k
+ * (rho_inout may be NULL) and the prediction R_lin = R - alpha sum a_k t_k for
+ * the next step's beta.  ctx's io dtype and system `sys` (nspin * N_g = n,
+ * quadrature weight w) must match the object.  R: [nspin][N_g] device.
+ * Synchronises the stream (decisions are taken on the host).  The forward
+ * state of the context is replaced. */
+lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R, void* rho_inout,
+                            const lrdm_lrdma_params* p, lrdm_lrdma_report* report, void* stream);
+/* Drops the history (e.g. at a restart). */
+lrdm_status lrdm_lrdma_clear(lrdm_lrdma* a);
+void lrdm_lrdma_destroy(lrdm_lrdma* a);
+
 /* Copies the projected perturbation X_k = Psi^T diag(w dV_k) Psi of direction
  * k, channel `spin`, of system `sys` from the most recent lrdm_gateaux_batch
  * into out ([N_s][N_s] FP64, device), for inspection and testing.

@@ -34,6 +34,8 @@ from .lrdm_oracle import (  # noqa: F401
     lrdm_apply,
     alpha_schedule,
     lrdm_krylov_step,
+    LrdmaState,
+    lrdma_step,
     backward,
     total_eps_grad,
     fermi_recursive,

@@ -31,6 +31,7 @@ __all__ = [
     "perturbation_potential", "project", "dmu_shift", "subspace_response",
     "density_response", "gateaux", "lrdm_apply", "backward", "total_eps_grad",
     "fermi_recursive", "loewner_recursive", "alpha_schedule", "lrdm_krylov_step",
+    "LrdmaState", "lrdma_step",
 ]
 
 
@@ -469,6 +470,97 @@ def lrdm_krylov_step(system: System, R, s_tol=0.3, r_max=8, alpha=None, rho=None
            "r_norm": r_norm, "alpha": alpha, "delta": ls["delta"]}
     if rho is not None:
         out["rho_new"] = np.asarray(rho, dtype=np.float64) - alpha * ls["delta"]
+    return out
+
+
+@dataclasses.dataclass
+class LrdmaState:
+    """History of the accumulated low-rank approximation (LRDMA, §II.B.1):
+    the direction functions U and their Gateaux derivatives T kept since the
+    last clearing, the linear prediction of the next residual (Eq.
+    linearapprox) and a pending clearing (CT event)."""
+    U: list = dataclasses.field(default_factory=list)
+    T: list = dataclasses.field(default_factory=list)
+    R_lin: Optional[np.ndarray] = None
+    clear_next: bool = False
+
+
+def _orthonormalise(x, U, w):
+    """x - sum_k <x, u_k> u_k, normalised (classical Gram-Schmidt, Eq. krylovOrtho)."""
+    u = x - sum(w * float(np.sum(x * uk)) * uk for uk in U)
+    return u / np.sqrt(w * np.sum(u * u))
+
+
+def lrdma_step(system: System, state: LrdmaState, R, rho=None, s_tol=0.3, beta_tol=0.1,
+               r_norm_clear=1.0, r_max_iter=5, r_max=20, alpha=None, rcond=1e-12):
+    """One SCF preconditioning step of the accumulated LRDM (LRDMA, §II.B.1),
+    in the order the paper states its decisions:
+
+    1. If a clearing is pending (CT) the history is cleared.  Otherwise, with a
+       history, the linearity indicator beta = | ||R_lin|| / ||R|| - 1 | (Eq.
+       linearityIndicator; R_lin = R_prev - alpha sum_k a_k t_k, Eq.
+       linearapprox) decides: beta > beta_tol clears (CL); else the history's
+       own s_rel on R is computed: below s_tol the history is used as it is
+       (reuse); else ||R|| > r_norm_clear clears (CR); else the history is
+       extended (accumulate).
+    2. Without a history (first step or cleared) the rank is built afresh as in
+       lrdm_krylov_step (up to r_max).  When accumulating, the first new
+       direction is the normalised orthogonal complement of R to the history
+       and each next one the Gram-Schmidt of the previous derivative against
+       all directions (Eq. accum); at most r_max_iter new ones; if s_rel is
+       still >= s_tol the next step clears (CT).
+    3. a = S^+ c over all kept derivatives, Delta = sum_k a_k u_k,
+       rho_new = rho - alpha Delta (alpha None -> alpha_schedule(||R||)) and
+       R_lin = R - alpha sum_k a_k t_k for the next step's beta.
+    Returns event ('fresh', 'reuse', 'accumulate', 'CL', 'CR', 'CT'), the
+    total and new rank, s_rel, beta, ||R||, alpha, Delta (and rho_new)."""
+    w = system.w
+    Rm = np.asarray(R, dtype=np.float64)
+    r_norm = float(np.sqrt(w * np.sum(Rm * Rm)))
+    beta = None
+    if state.clear_next:
+        event = "CT"
+    elif state.U:
+        beta = abs(float(np.sqrt(w * np.sum(state.R_lin * state.R_lin))) / r_norm - 1.0)
+        if beta > beta_tol:
+            event = "CL"
+        else:
+            s_hist = lrdm_apply(Rm, np.stack(state.U), np.stack(state.T), w, 0.0, rcond=rcond)["s_rel"]
+            if s_hist < s_tol:
+                event = "reuse"
+            elif r_norm > r_norm_clear:
+                event = "CR"
+            else:
+                event = "accumulate"
+    else:
+        event = "fresh"
+    if event in ("CT", "CL", "CR"):
+        state.U, state.T = [], []
+    state.clear_next = False
+    n_new = 0
+    if event != "reuse":
+        fresh = not state.U
+        limit = r_max if fresh else max(1, min(r_max_iter, r_max - len(state.U)))
+        u = Rm / r_norm if fresh else _orthonormalise(Rm, state.U, w)
+        while True:
+            state.U.append(u)
+            state.T.append(gateaux(system, u[None])["F"][0])
+            n_new += 1
+            ls = lrdm_apply(Rm, np.stack(state.U), np.stack(state.T), w, 0.0, rcond=rcond)
+            if ls["s_rel"] < s_tol or n_new == limit:
+                break
+            u = _orthonormalise(state.T[-1], state.U, w)
+        if not fresh and ls["s_rel"] >= s_tol:
+            state.clear_next = True
+    if alpha is None:
+        alpha = alpha_schedule(r_norm)
+    ls = lrdm_apply(Rm, np.stack(state.U), np.stack(state.T), w, alpha, rcond=rcond,
+                    rho=rho if rho is not None else None)
+    state.R_lin = Rm - alpha * np.tensordot(ls["a"], np.stack(state.T), axes=1)
+    out = {"event": event, "rank": len(state.U), "rank_new": n_new, "s_rel": ls["s_rel"],
+           "beta": beta, "r_norm": r_norm, "alpha": alpha, "delta": ls["delta"], "a": ls["a"]}
+    if rho is not None:
+        out["rho_new"] = ls["rho_new"]
     return out
 
 

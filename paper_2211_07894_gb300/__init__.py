@@ -8,6 +8,7 @@ The computation lives in the C-ABI library ``lib/liblrdm.so`` (declared in
 
 from .binding import (  # noqa: F401
     Context,
+    Lrdma,
     LrdmError,
     gateaux_function,
     load,
@@ -19,6 +20,9 @@ from .binding import (  # noqa: F401
     lrdm_gateaux_batch,
     lrdm_get_density,
     lrdm_get_mu,
+    lrdm_get_projection,
+    lrdm_get_tuning,
+    lrdm_krylov_step,
     lrdm_profile_enable,
     lrdm_profile_read,
     lrdm_status_query,

@@ -53,7 +53,21 @@ EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_ap
            "lrdm_apply_static",
            "lrdm_backward", "lrdm_status_query", "lrdm_get_mu", "lrdm_get_density",
            "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string",
-           "lrdm_get_tuning", "lrdm_krylov_step"]
+           "lrdm_get_tuning", "lrdm_krylov_step", "lrdm_lrdma_default_params", "lrdm_lrdma_create",
+           "lrdm_lrdma_step", "lrdm_lrdma_clear", "lrdm_lrdma_destroy"]
+
+
+class lrdm_lrdma_params(ctypes.Structure):
+    _fields_ = [("s_tol", c_double), ("beta_tol", c_double), ("r_norm_clear", c_double),
+                ("alpha", c_double), ("r_max_iter", c_int), ("r_max", c_int)]
+
+
+class lrdm_lrdma_report(ctypes.Structure):
+    _fields_ = [("event", c_int), ("rank", c_int), ("rank_new", c_int), ("s_rel", c_double),
+                ("beta", c_double), ("r_norm", c_double), ("alpha", c_double)]
+
+
+LRDMA_EVENTS = {0: "fresh", 1: "reuse", 2: "accumulate", 3: "CL", 4: "CR", 5: "CT"}
 
 
 def load(path: Optional[str] = None):
@@ -102,6 +116,17 @@ def load(path: Optional[str] = None):
                                      c_void_p, c_void_p, c_void_p, POINTER(c_double), POINTER(c_int),
                                      POINTER(c_double), c_void_p]
     lib.lrdm_krylov_step.restype = c_int
+    lib.lrdm_lrdma_default_params.argtypes = [POINTER(lrdm_lrdma_params)]
+    lib.lrdm_lrdma_default_params.restype = None
+    lib.lrdm_lrdma_create.argtypes = [POINTER(c_void_p), ctypes.c_longlong, c_int, c_double, c_int]
+    lib.lrdm_lrdma_create.restype = c_int
+    lib.lrdm_lrdma_step.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                    POINTER(lrdm_lrdma_params), POINTER(lrdm_lrdma_report), c_void_p]
+    lib.lrdm_lrdma_step.restype = c_int
+    lib.lrdm_lrdma_clear.argtypes = [c_void_p]
+    lib.lrdm_lrdma_clear.restype = c_int
+    lib.lrdm_lrdma_destroy.argtypes = [c_void_p]
+    lib.lrdm_lrdma_destroy.restype = None
     lib.lrdm_get_tuning.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]
     lib.lrdm_get_tuning.restype = c_int
     lib.lrdm_destroy.argtypes = [c_void_p]
@@ -435,6 +460,54 @@ class Context:
 
     def status(self, synchronize=True):
         return lrdm_status_query(self.handle, 1 if synchronize else 0)
+
+
+class Lrdma:
+    """The accumulated LRDM driver (lrdm_lrdma_*): a history of directions and
+    Gateaux derivatives kept across SCF steps, for grid functions of
+    n = nspin * N_g values in the io dtype with quadrature weight w."""
+
+    def __init__(self, n, io_dtype, w, capacity=16):
+        import torch
+        self.torch = torch
+        code_io = DTYPE_F64 if io_dtype == torch.float64 else DTYPE_F32
+        h = c_void_p()
+        _check("lrdm_lrdma_create", load().lrdm_lrdma_create(ctypes.byref(h), int(n), code_io,
+                                                              float(w), int(capacity)))
+        self.handle = h
+
+    def step(self, ctx, R, rho=None, sys=0, stream=None, **params):
+        """One LRDMA step with context `ctx` (its current subspace); params
+        override the paper's settings (s_tol, beta_tol, r_norm_clear, alpha,
+        r_max_iter, r_max).  rho is updated in place.  Returns the report."""
+        p = lrdm_lrdma_params()
+        load().lrdm_lrdma_default_params(ctypes.byref(p))
+        for k, v in params.items():
+            setattr(p, k, v)
+        rep = lrdm_lrdma_report()
+        st = ctx._stream(stream)
+        _check("lrdm_lrdma_step", load().lrdm_lrdma_step(self.handle, ctx.handle, sys,
+                                                          c_void_p(R.data_ptr()),
+                                                          c_void_p(rho.data_ptr() if rho is not None else 0),
+                                                          ctypes.byref(p), ctypes.byref(rep),
+                                                          c_void_p(st)))
+        return dict(event=LRDMA_EVENTS[rep.event], rank=rep.rank, rank_new=rep.rank_new,
+                    s_rel=rep.s_rel, beta=rep.beta if rep.beta >= 0 else None, r_norm=rep.r_norm,
+                    alpha=rep.alpha)
+
+    def clear(self):
+        _check("lrdm_lrdma_clear", load().lrdm_lrdma_clear(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().lrdm_lrdma_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gateaux_function():

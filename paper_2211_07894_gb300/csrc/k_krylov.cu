@@ -94,7 +94,26 @@ __global__ void __launch_bounds__(KR_THREADS) k_normalize(void* __restrict__ out
     st_io(out, io, r, ld_io(out, io, r) * inv);
 }
 
+// norm_out[0] = sqrt(w sum_b partial[b])
+__global__ void k_norm_finish(const double* __restrict__ partial, int nblk, double w,
+                              double* __restrict__ norm_out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[b];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) norm_out[0] = sqrt(w * s);
+}
+
 }  // namespace
+
+cudaError_t launch_norm(const void* x, int io, long long n, double w, double* scratch,
+                        double* norm_out, cudaStream_t st) {
+  k_dots<<<KR_BLOCKS, KR_THREADS, 0, st>>>(x, 1, x, io, n, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_norm_finish<<<1, KR_THREADS, 0, st>>>(scratch, KR_BLOCKS, w, norm_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gram_schmidt(const void* U, int K, const void* t, int io, long long n, double w,
                                 void* out, double* scratch, double* norm_out, cudaStream_t st) {

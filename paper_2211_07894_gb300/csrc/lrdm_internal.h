@@ -187,6 +187,9 @@ cudaError_t launch_gemm2_simt(int fp64, const void* psi, int ns, long long Ng, c
 cudaError_t launch_gram_schmidt(const void* U, int K, const void* t, int io, long long n, double w,
                                 void* out, double* scratch, double* norm_out, cudaStream_t st);
 size_t gram_schmidt_scratch();
+// norm_out[0] = ||x||_w (scratch: gram_schmidt_scratch() doubles)
+cudaError_t launch_norm(const void* x, int io, long long n, double w, double* scratch,
+                        double* norm_out, cudaStream_t st);
 cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype, int K,
                       long long n, double w, double alpha, double rcond, void* rho_inout,
                       double* coef, double* coeff_out, double* s_rel_out, double* partial,

@@ -417,7 +417,8 @@ def test_krylov_step(lib, cfg1, prec, spin):
     assert ctx.status() == 0
     assert out["rank"] == ref["rank"] == 3
     tol = TOL[prec]
-    assert abs(out["r_norm"] - ref["r_norm"]) <= 1e-12 * ref["r_norm"]
+    # ||R|| of the io-dtype copy of R (FP32 rounding of R in the mixed modes)
+    assert abs(out["r_norm"] - ref["r_norm"]) <= (1e-12 if io == torch.float64 else 1e-6) * ref["r_norm"]
     assert np.allclose(out["s_rel"], ref["s_rel"], rtol=10 * tol, atol=0)
     assert per_direction_rel_err(out["U"].double().cpu().numpy(), ref["U"]) < 10 * tol
     assert per_direction_rel_err(out["T"].double().cpu().numpy(), ref["T"]) < 10 * tol
