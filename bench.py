@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--prec", default="bf16x3", choices=["bf16x3", "tf32", "fp32", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="use the default launch shape instead of tuning at create")
     p.add_argument("--no-fp64-plain", action="store_true",
                    help="skip timing the plain FP64 GPU form")
     p.add_argument("--grid", type=int, default=96, help="grid edge (96 = the benchmark workload)")
@@ -92,11 +94,12 @@ def tc_source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from the ncu summaries
-    under profiles/ (lines 'traffic-record: kernel=... workload=...
-    source_sha256=... dram_bytes_per_launch=...'), or None when no record
-    matches the current kernel sources."""
+def recorded_traffic(kernel, workload, shape):
+    """DRAM bytes per launch of `kernel` on `workload` in launch shape `shape`
+    (the kernel's own tuning fields, e.g. 'g1_nb=256,g1_dpt=1') from the ncu
+    summaries under profiles/ (lines 'traffic-record: kernel=... workload=...
+    shape=... source_sha256=... dram_bytes_per_launch=...'), or None when no
+    record matches the current kernel sources and shape."""
     import glob
     want = tc_source_hash()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
@@ -107,7 +110,7 @@ def recorded_traffic(kernel, workload):
                     continue
                 f = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)
                 if (f.get("kernel") == kernel and f.get("workload") == workload
-                        and f.get("source_sha256") == want):
+                        and f.get("shape") == shape and f.get("source_sha256") == want):
                     return float(f["dram_bytes_per_launch"])
     return None
 
@@ -249,7 +252,7 @@ def reference_arm(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def build_problem(torch, rank, prec, edge, ns):
+def build_problem(torch, rank, prec, edge, ns, autotune=True):
     import numpy as np
     import workloads
     from paper_2211_07894_gb300 import Context
@@ -275,7 +278,8 @@ def build_problem(torch, rank, prec, edge, ns):
     if io == torch.float64:
         system["psi"] = [psi.double()]
         V, R = V.double(), R.double()
-    ctx = Context([system], prec=prec, io_dtype=io, k_max=KDIR, use_graph=True)
+    ctx = Context([system], prec=prec, io_dtype=io, k_max=KDIR, use_graph=True,
+                  autotune=autotune and prec in ("bf16x3", "tf32"))
     del psi, system
     torch.cuda.empty_cache()
     return ctx, V, R, ng
@@ -373,8 +377,10 @@ def main():
     from paper_2211_07894_gb300 import build as _build
     _build.build()
 
-    ctx, V, R, ng = build_problem(torch, rank, args.prec, args.grid, args.ns)
+    ctx, V, R, ng = build_problem(torch, rank, args.prec, args.grid, args.ns,
+                                  autotune=not args.no_autotune)
     ns = args.ns
+    tuning = ctx.tuning() if args.prec in ("bf16x3", "tf32") else None
     F = torch.empty_like(V)
     rho_out = torch.empty_like(R)
     coeff = torch.empty(KDIR, dtype=torch.float64, device="cuda")
@@ -511,6 +517,8 @@ def main():
     name, (tms, nl) = max((("projection GEMM (X_k)", g1), ("response GEMM (drho_k)", g2)),
                           key=lambda x: x[1][0])
     kname = "k_gemm1_tc" if name.startswith("projection") else "k_gemm2_tc"
+    kshape = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kname == "k_gemm1_tc"
+               else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
     avg_s = tms / max(nl, 1) / 1e3
     alg_flops = KDIR * ng * ns * ns           # one launch: K directions, symmetric half
     if args.prec == "bf16x3":
@@ -532,7 +540,7 @@ def main():
     achieved = issued / avg_s / 1e12 if avg_s > 0 else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": recorded_traffic(kname, f"{args.grid}^3/{ns}/K{KDIR}/{args.prec}"),
+                "traffic": recorded_traffic(kname, f"{args.grid}^3/{ns}/K{KDIR}/{args.prec}", kshape),
                 "kernel": name, "avg_launch_ms": avg_s * 1e3, "launches": nl,
                 "alg_flop_per_launch": alg_flops, "peak_source": f"{peak_src}; {note}"}
 
@@ -567,7 +575,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],
-                "forward_only": forward_only, "fp64_plain": fp64_plain,
+                "forward_only": forward_only, "fp64_plain": fp64_plain, "launch_shape": tuning,
                 "breakdown_ms": {"gemm1_per_step": prof["gemm1_ms"] / steps,
                                  "gemm2_per_step": prof["gemm2_ms"] / steps,
                                  "poisson_per_step": prof["poisson_ms"] / steps,

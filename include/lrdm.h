@@ -105,11 +105,12 @@ typedef struct lrdm_options {
                             degenerate in occupation mode; 1e-5                 */
   int poisson_symbol;    /* 0: 4 pi/|G|^2 (spectral); 1: second-order FD symbol  */
   int use_graph;         /* replay lrdm_gateaux_batch from a captured CUDA graph  */
-  int autotune;          /* tensor-core precisions: 0 -> default launch shape (two
-                            directions per projection tile, response j-tile 256,
-                            direction group 2); 1 -> lrdm_create times the
-                            candidates (1 or 2 directions per projection tile;
-                            j-tile 128 or 256 x group 1, 2, 4) on the context's
+  int autotune;          /* tensor-core precisions: 0 -> default launch shape
+                            (128 x 256 projection tiles, response j-tile 256,
+                            direction group 4); 1 -> lrdm_create times the
+                            candidates (projection: 128 x 256 tiles, or 128 x 128
+                            tiles with 1 or 2 directions; response: j-tile 128
+                            or 256 x group 1, 2, 4) on the context's
                             own problems and keeps the fastest; with the
                             environment variable LRDM_TUNE_CACHE naming a file,
                             results are read from / appended to it (one JSON
@@ -228,9 +229,10 @@ lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_
                               long long* poisson_calls, long long* kernel_launches, int reset);
 
 /* Launch shape of the tensor-core contractions chosen at create (defaults
- * or the autotuner's choice): directions per projection tile, response
- * j-tile width, response direction group.  Any pointer may be NULL. */
-lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_dpt, int* g2_bn, int* g2_kgroup);
+ * or the autotuner's choice): projection MMA width (128: square tiles; 256:
+ * 128 x 256 tiles, one direction), directions per projection square tile,
+ * response j-tile width, response direction group.  Any pointer may be NULL. */
+lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_nb, int* g1_dpt, int* g2_bn, int* g2_kgroup);
 
 /* One LRDM preconditioning step of system `sys` with adaptively chosen rank
  * (§II.B, Eqs. jlowrank, krylovOrtho, plowrank, relativeError, quasinewton):

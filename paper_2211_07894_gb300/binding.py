@@ -127,7 +127,8 @@ def load(path: Optional[str] = None):
     lib.lrdm_lrdma_clear.restype = c_int
     lib.lrdm_lrdma_destroy.argtypes = [c_void_p]
     lib.lrdm_lrdma_destroy.restype = None
-    lib.lrdm_get_tuning.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]
+    lib.lrdm_get_tuning.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                    POINTER(c_int)]
     lib.lrdm_get_tuning.restype = c_int
     lib.lrdm_destroy.argtypes = [c_void_p]
     lib.lrdm_destroy.restype = None
@@ -244,9 +245,10 @@ def lrdm_krylov_step(ctx, sys, R_ptr, s_tol, r_max, alpha, rho_ptr, U_ptr, T_ptr
 
 
 def lrdm_get_tuning(ctx):
-    a, b, c = c_int(), c_int(), c_int()
-    _check("lrdm_get_tuning", load().lrdm_get_tuning(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return dict(g1_dpt=a.value, g2_bn=b.value, g2_kgroup=c.value)
+    z, a, b, c = c_int(), c_int(), c_int(), c_int()
+    _check("lrdm_get_tuning", load().lrdm_get_tuning(ctx, ctypes.byref(z), ctypes.byref(a),
+                                                     ctypes.byref(b), ctypes.byref(c)))
+    return dict(g1_nb=z.value, g1_dpt=a.value, g2_bn=b.value, g2_kgroup=c.value)
 
 
 def lrdm_destroy(ctx) -> None:

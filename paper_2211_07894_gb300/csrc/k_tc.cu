@@ -408,30 +408,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 constexpr int G1_THREADS = 384;
 constexpr int G1_REG_MATH = 224, G1_REG_CTRL = 56;
 static_assert(256 * G1_REG_MATH + 128 * G1_REG_CTRL == G1_THREADS * 168, "register split");
-constexpr int G1_BN = 128;              // tile width (j) = tile height (i)
+constexpr int G1_BN = 128;              // square-tile width (j) = tile height (i)
 constexpr int G1_TILE = G1_BN * ROWB;   // 8 KB per operand part (128 rows x 64 bytes)
 constexpr int G1_ACOL = 256;            // first TMEM column of the weighted-A ring
 
-template <int PREC>
+// NB = MMA N: 128 -> 128 x 128 tiles (I <= J), one or two directions per tile,
+// the accumulators of the two directions side by side; 256 -> 128 x 256
+// tiles (128-row blocks I below the end of 256-wide block J), one direction.
+template <int PREC, int NB>
 struct G1Cfg {
   static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
   static constexpr int STAGES = PREC == LRDM_BF16X3 ? 4 : 8;
+  static constexpr int MAXD = NB == 256 ? 1 : 2;               // directions per tile at most
   // TMEM columns of one direction's weighted A per stage: bf16 packs two
   // elements per column and has two parts (hi, lo); tf32 one element per column
   static constexpr int ACOLS = BK;
-  static constexpr int SLOT = 2 * ACOLS;
+  static constexpr int SLOT = MAXD * ACOLS;
   static constexpr int A_BYTES = BM * BK * 4;                   // FP32 A rows (128-byte rows for bf16 mode)
+  static constexpr int B_TILE = NB * ROWB;                      // one part of the B rows
   static constexpr int B_OFF = A_BYTES;
-  static constexpr int SC_OFF = B_OFF + PARTS * G1_TILE;
+  static constexpr int SC_OFF = B_OFF + PARTS * B_TILE;
   static constexpr int STRIDE = SC_OFF + 1024;                  // 1024-aligned stages
   static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
   static constexpr int SEG = 1024 / BK;                          // stages per accumulation segment
   static constexpr int LAG = STAGES - 1;                         // stages weighted ahead of a flush
-  static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, G1_BN);
+  static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, NB);
+  static_assert(G1_ACOL + STAGES * SLOT <= 512, "TMEM budget");
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(LAG <= STAGES, "flush lag");
 };
-static_assert(G1_ACOL + G1Cfg<LRDM_BF16X3>::STAGES * G1Cfg<LRDM_BF16X3>::SLOT <= 512, "TMEM budget");
-static_assert(G1_ACOL + G1Cfg<LRDM_TF32>::STAGES * G1Cfg<LRDM_TF32>::SLOT <= 512, "TMEM budget");
-static_assert(G1Cfg<LRDM_BF16X3>::LAG <= G1Cfg<LRDM_BF16X3>::STAGES, "flush lag");
 
 struct G1Params {
   const TcProblem* probs;
@@ -449,25 +454,37 @@ __device__ __forceinline__ int g1_nch(const G1Params& P, const TcProblem* pr) {
   return P.nch_lim > 0 ? min(P.nch_lim, pr->nch) : pr->nch;
 }
 
-// Item -> slot q, first direction k0, directions nd (1 or 2), tile I <= J.
-// Direction pairs run fastest: the pairs of one tile run side by side on
-// different SMs and stream the same Psi^T rows through L2; tiles go column by
-// column, so neighbouring tiles share their B rows.
+// Item -> slot q, first direction k0, directions nd, tile (I, J).  Direction
+// groups run fastest: the items of one tile run side by side on different SMs
+// and stream the same Psi^T rows through L2; tiles go column by column, so
+// neighbouring tiles share their B rows.  NB = 128: column J holds I = 0..J;
+// NB = 256: column J (256 wide) holds the 128-row blocks I < min(2 J + 2, nI).
+template <int NB>
 __device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item, int& q, int& k0,
                                                     int& nd, int& I, int& J) {
   q = find_slot(P.begin, P.nslot, item);
   const TcProblem* pr = P.probs + P.pid[q];
   const int idx = item - P.begin[q];
-  const int K = P.K[q], dpt = P.dpt;
+  const int K = P.K[q], dpt = NB == 256 ? 1 : P.dpt;
   const int npair = (K + dpt - 1) / dpt;
   int t = idx / npair;
   const int pp = idx - t * npair;
   k0 = dpt * pp;
   nd = min(dpt, K - k0);
   int j = 0;
-  while (t > j) {                   // column j holds tiles I = 0..j
-    t -= j + 1;
-    ++j;
+  if (NB == 256) {
+    const int nI = pr->nI;
+    for (;;) {
+      const int cnt = min(2 * (j + 1), nI);
+      if (t < cnt) break;
+      t -= cnt;
+      ++j;
+    }
+  } else {
+    while (t > j) {
+      t -= j + 1;
+      ++j;
+    }
   }
   J = j;
   I = t;
@@ -479,9 +496,9 @@ __device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item,
 // split into bf16 hi / lo (or rounded to TF32) and stored at TMEM address ta
 // (this warp's lane quarter, first column of the stage's slot).  Packed FP32
 // pair arithmetic (two elements per instruction).
-template <int PREC>
+template <int PREC, int NB>
 __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd, uint32_t ta) {
-  using C = G1Cfg<PREC>;
+  using C = G1Cfg<PREC, NB>;
   if (PREC == LRDM_BF16X3) {
     // A rows of 32 FP32 = 128 bytes, 128-byte swizzle: chunk c sits at c ^ (row % 8)
     const uint32_t ra = st + row * 128;
@@ -545,12 +562,12 @@ __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd
 
 // The MMAs of one stage: for each direction d, D_d (+)= A'_d B^T over the
 // stage's BK grid rows (three bf16 products for the split form).
-template <int PREC>
+template <int PREC, int NB>
 __device__ __forceinline__ void issue_g1_mmas(uint32_t tmem, uint32_t aslot, uint32_t sb, int nd,
                                               bool first) {
-  using C = G1Cfg<PREC>;
+  using C = G1Cfg<PREC, NB>;
 #pragma unroll
-  for (int d = 0; d < 2; ++d) {
+  for (int d = 0; d < C::MAXD; ++d) {
     if (d >= nd) break;
     const uint32_t dt = tmem + d * G1_BN;
     const uint32_t at = tmem + aslot + d * C::ACOLS;
@@ -559,7 +576,7 @@ __device__ __forceinline__ void issue_g1_mmas(uint32_t tmem, uint32_t aslot, uin
       const uint32_t acc = (first && kk == 0) ? 0u : 1u;
       const uint64_t b0 = ptx::desc_k_sw64(sb + kk * 32);
       if (PREC == LRDM_BF16X3) {
-        const uint64_t b1 = ptx::desc_k_sw64(sb + G1_TILE + kk * 32);
+        const uint64_t b1 = ptx::desc_k_sw64(sb + C::B_TILE + kk * 32);
         ptx::mma_f16_ta(dt, at + kk * 8, b0, C::IDESC, acc);        // hi x hi
         ptx::mma_f16_ta(dt, at + kk * 8, b1, C::IDESC, 1);          // hi x lo
         ptx::mma_f16_ta(dt, at + 16 + kk * 8, b0, C::IDESC, 1);     // lo x hi
@@ -572,9 +589,9 @@ __device__ __forceinline__ void issue_g1_mmas(uint32_t tmem, uint32_t aslot, uin
 
 // ---- the roles of k_gemm1_tc ----
 
-template <int PREC>
+template <int PREC, int NB>
 __device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, const Bars& B, int items) {
-  using C = G1Cfg<PREC>;
+  using C = G1Cfg<PREC, NB>;
   constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::STRIDE;
   for (int q = 0; q < P.nslot; ++q) {
     const TcProblem* pr = P.probs + P.pid[q];
@@ -589,19 +606,26 @@ __device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, co
   bool ok = true;
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
     int q, k0, nd, I, J;
-    const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
+    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J);
     const float* w0 = pr->a + (long long)k0 * pr->a_stride;
     const long long wstride = pr->a_stride;
     const int nch = g1_nch(P, pr);
     const CUtensorMap *ma = &pr->g1a, *mb0 = &pr->g1b0, *mb1 = &pr->g1b1;
-    const uint32_t tx = C::A_BYTES + PARTS * G1_TILE + nd * BK * 4;
+    const uint32_t tx = C::A_BYTES + PARTS * C::B_TILE + nd * BK * 4;
     for (int rc = 0; rc < nch; ++rc) {
       if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
       uint8_t* st = smem + s * SB;
       ptx::mbar_arrive_expect_tx(&B.full[s], tx);
       ptx::tma_load_4d(st, ma, &B.full[s], 0, 0, rc, I);
-      ptx::tma_load_4d(st + C::B_OFF, mb0, &B.full[s], 0, 0, rc, J);
-      if (PARTS == 2) ptx::tma_load_4d(st + C::B_OFF + G1_TILE, mb1, &B.full[s], 0, 0, rc, J);
+      // B rows: NB / 128 consecutive state blocks (a block past the last one
+      // of the matrix reads the zero fill; those columns are never stored)
+#pragma unroll
+      for (int hb = 0; hb < NB / 128; ++hb) {
+        ptx::tma_load_4d(st + C::B_OFF + hb * G1_TILE, mb0, &B.full[s], 0, 0, rc, J * (NB / 128) + hb);
+        if (PARTS == 2)
+          ptx::tma_load_4d(st + C::B_OFF + C::B_TILE + hb * G1_TILE, mb1, &B.full[s], 0, 0, rc,
+                           J * (NB / 128) + hb);
+      }
       for (int d = 0; d < nd; ++d)
         ptx::bulk_load(st + C::SC_OFF + d * BK * 4, w0 + d * wstride + (long long)rc * BK, BK * 4,
                        &B.full[s]);
@@ -613,17 +637,17 @@ __device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, co
     if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
 }
 
-template <int PREC>
+template <int PREC, int NB>
 __device__ __forceinline__ void g1_mma(const G1Params& P, uint8_t* smem, const Bars& B, int items,
                                        uint32_t tmem) {
-  using C = G1Cfg<PREC>;
+  using C = G1Cfg<PREC, NB>;
   constexpr int STAGES = C::STAGES, SB = C::STRIDE, SEG = C::SEG;
   int s = 0;
   uint32_t ph = 0, aph = 0;
   bool ok = true;
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
     int q, k0, nd, I, J;
-    const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
+    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J);
     const int nch = g1_nch(P, pr);
     const int nseg = (nch + SEG - 1) / SEG;
     for (int sg = 0; sg < nseg && ok; ++sg) {
@@ -633,7 +657,7 @@ __device__ __forceinline__ void g1_mma(const G1Params& P, uint8_t* smem, const B
       for (int rc = r0; rc < r1; ++rc) {
         if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
-        issue_g1_mmas<PREC>(tmem, (uint32_t)(G1_ACOL + s * C::SLOT),
+        issue_g1_mmas<PREC, NB>(tmem, (uint32_t)(G1_ACOL + s * C::SLOT),
                             ptx::smem_u32(smem + s * SB) + C::B_OFF, nd, rc == r0);
         ptx::mma_commit(&B.empty[s]);
         if (++s == STAGES) { s = 0; ph ^= 1; }
@@ -650,10 +674,10 @@ __device__ __forceinline__ void g1_mma(const G1Params& P, uint8_t* smem, const B
 // Weighting into tensor memory, segment accumulation and the tile epilogue
 // (warps 0-7; warp w serves TMEM lane quarter w % 4 and element half /
 // direction w / 4).
-template <int PREC>
+template <int PREC, int NB>
 __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const Bars& B, int items,
                                         uint32_t tmem, int warp, int lane) {
-  using C = G1Cfg<PREC>;
+  using C = G1Cfg<PREC, NB>;
   constexpr int STAGES = C::STAGES, SB = C::STRIDE, SEG = C::SEG, LAG = C::LAG;
   const int lq = warp & 3;
   const int h = warp >> 2;
@@ -665,7 +689,7 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
   float sum[128];
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
     int q, k0, nd, I, J;
-    const TcProblem* pr = g1_item(P, item, q, k0, nd, I, J);
+    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J);
     const int nch = g1_nch(P, pr), ns = pr->ns, ns_pad = pr->ns_pad;
     const int nseg = (nch + SEG - 1) / SEG;
 #pragma unroll
@@ -673,7 +697,7 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
     int flushed = 0;                      // segments already added into sum[]
     for (int rc = 0; rc < nch; ++rc) {
       if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
-      weight_stage<PREC>(ptx::smem_u32(smem + s * SB), row, h, nd,
+      weight_stage<PREC, NB>(ptx::smem_u32(smem + s * SB), row, h, nd,
                          tq + (uint32_t)(G1_ACOL + s * C::SLOT));
       ptx::tmem_wait_st();
       ptx::tc_fence_before();
@@ -687,8 +711,8 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
       while (flushed < nseg && (flushed < ready_seg || last)) {
         if (!waitw(&B.acc_full[0], aph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
-        if (h < nd) {
-          const uint32_t ta = tq + (uint32_t)(h * G1_BN);
+        if (NB == 256 || h < nd) {        // columns [128 h, 128 h + 128) of the accumulators
+          const uint32_t ta = tq + (uint32_t)(h * 128);
 #pragma unroll
           for (int c8 = 0; c8 < 8; ++c8) {
             float v[16];
@@ -706,11 +730,12 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
       if (!ok) break;
     }
     if (!ok) break;
-    // epilogue: X[i][j] and X[j][i] for i <= j of this tile, direction k0 + h
+    // epilogue: X[i][j] and X[j][i] for i <= j of this tile; NB = 128: the
+    // columns of direction k0 + h, NB = 256: columns 128 h.. of direction k0
     const int i = I * G1_BN + row;
-    if (h < nd && i < ns) {
-      float* Xk = P.X[q] + (long long)(k0 + h) * ns_pad * ns_pad;
-      const int j0 = J * G1_BN;
+    if ((NB == 256 || h < nd) && i < ns) {
+      float* Xk = P.X[q] + (long long)(k0 + (NB == 256 ? 0 : h)) * ns_pad * ns_pad;
+      const int j0 = J * NB + (NB == 256 ? h * 128 : 0);
 #pragma unroll
       for (int c = 0; c < 128; ++c) {
         const int j = j0 + c;
@@ -723,10 +748,10 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
   }
 }
 
-template <int PREC>
+template <int PREC, int NB>
 __global__ void __launch_bounds__(G1_THREADS, 1)
     k_gemm1_tc(const __grid_constant__ G1Params P) {
-  using C = G1Cfg<PREC>;
+  using C = G1Cfg<PREC, NB>;
   constexpr int STAGES = C::STAGES, SB = C::STRIDE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -757,11 +782,11 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
   const uint32_t tmem = *B.tmem_slot;
   if (warp >= 8) {
     ptx::setmaxnreg_dec<G1_REG_CTRL>();
-    if (warp == 8 && lane == 0) g1_producer<PREC>(P, smem, B, items);
-    else if (warp == 9 && lane == 0) g1_mma<PREC>(P, smem, B, items, tmem);
+    if (warp == 8 && lane == 0) g1_producer<PREC, NB>(P, smem, B, items);
+    else if (warp == 9 && lane == 0) g1_mma<PREC, NB>(P, smem, B, items, tmem);
   } else {
     ptx::setmaxnreg_inc<G1_REG_MATH>();
-    g1_math<PREC>(P, smem, B, items, tmem, warp, lane);
+    g1_math<PREC, NB>(P, smem, B, items, tmem, warp, lane);
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -872,6 +897,8 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   pr.nI = c.ns_pad / BM;
   pr.NJ = (c.ns_pad + 255) / 256;        // GEMM2 j-tiles at the default width
   pr.ntiles = pr.nI * (pr.nI + 1) / 2;    // GEMM1 128 x 128 tiles with I <= J
+  pr.ntiles_w = 0;                          // GEMM1 128 x 256 tiles (I below the end of J)
+  for (int j = 0; 256 * j < c.ns_pad; ++j) pr.ntiles_w += 2 * (j + 1) < pr.nI ? 2 * (j + 1) : pr.nI;
   pr.nch = (int)(S.Ng_pad / BK);
   pr.nR = (int)(S.Ng_pad / BM);
   pr.kmax = S.kmax;
@@ -896,14 +923,14 @@ void order_slots(const TcEntry* e, int n, int gemm, int* order) {
   }
 }
 
-template <int PREC>
+template <int PREC, int NB>
 cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, const TcTune& t,
                         int nch_lim) {
   static bool attr = false;
-  const int smem = G1Cfg<PREC>::SMEM;
-  cudaError_t err = set_smem(k_gemm1_tc<PREC>, smem, attr);
+  const int smem = G1Cfg<PREC, NB>::SMEM;
+  cudaError_t err = set_smem(k_gemm1_tc<PREC, NB>, smem, attr);
   if (err != cudaSuccess) return err;
-  const int dpt = t.g1_dpt == 1 ? 1 : 2;
+  const int dpt = NB == 256 ? 1 : (t.g1_dpt == 1 ? 1 : 2);
   for (int base = 0; base < n; base += TC_MAX_SLOTS) {
     const int m = n - base < TC_MAX_SLOTS ? n - base : TC_MAX_SLOTS;
     int order[TC_MAX_SLOTS];
@@ -922,14 +949,14 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, c
       P.K[q] = x.K;
       P.X[q] = static_cast<float*>(x.X);
       P.begin[q] = items;
-      items += x.host->ntiles * ((x.K + dpt - 1) / dpt);
+      items += (NB == 256 ? x.host->ntiles_w : x.host->ntiles) * ((x.K + dpt - 1) / dpt);
       ++q;
     }
     P.nslot = q;
     P.begin[q] = items;
     if (items == 0) continue;
     const int grid = items < num_sms() ? items : num_sms();
-    k_gemm1_tc<PREC><<<grid, G1_THREADS, smem, st>>>(P);
+    k_gemm1_tc<PREC, NB><<<grid, G1_THREADS, smem, st>>>(P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   return cudaSuccess;
@@ -998,8 +1025,12 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
                                   const TcTune& t, int nch_lim) {
-  if (prec == LRDM_BF16X3) return gemm1_group<LRDM_BF16X3>(e, n, status, st, t, nch_lim);
-  return gemm1_group<LRDM_TF32>(e, n, status, st, t, nch_lim);
+  const bool wide = t.g1_nb == 256;
+  if (prec == LRDM_BF16X3)
+    return wide ? gemm1_group<LRDM_BF16X3, 256>(e, n, status, st, t, nch_lim)
+                : gemm1_group<LRDM_BF16X3, 128>(e, n, status, st, t, nch_lim);
+  return wide ? gemm1_group<LRDM_TF32, 256>(e, n, status, st, t, nch_lim)
+              : gemm1_group<LRDM_TF32, 128>(e, n, status, st, t, nch_lim);
 }
 
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,

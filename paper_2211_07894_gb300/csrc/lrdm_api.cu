@@ -391,7 +391,7 @@ std::string tune_key(lrdm_ctx* ctx) {
 }
 
 // Cache file: one JSON object per line,
-//   {"key": "...", "g1_dpt": 2, "g2_bn": 256, "g2_kgroup": 2}
+//   {"key": "...", "g1_nb": 256, "g1_dpt": 1, "g2_bn": 256, "g2_kgroup": 4}
 bool tune_cache_read(const char* path, const std::string& key, TcTune& t) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
@@ -400,11 +400,13 @@ bool tune_cache_read(const char* path, const std::string& key, TcTune& t) {
   bool found = false;
   while (fgets(line, sizeof(line), f)) {
     if (!strstr(line, want.c_str())) continue;
+    const char* z = strstr(line, "\"g1_nb\":");
     const char* a = strstr(line, "\"g1_dpt\":");
     const char* b = strstr(line, "\"g2_bn\":");
     const char* c = strstr(line, "\"g2_kgroup\":");
     TcTune u;
-    if (a && b && c && sscanf(a, "\"g1_dpt\": %d", &u.g1_dpt) == 1 &&
+    if (z && a && b && c && sscanf(z, "\"g1_nb\": %d", &u.g1_nb) == 1 &&
+        (u.g1_nb == 128 || u.g1_nb == 256) && sscanf(a, "\"g1_dpt\": %d", &u.g1_dpt) == 1 &&
         sscanf(b, "\"g2_bn\": %d", &u.g2_bn) == 1 &&
         sscanf(c, "\"g2_kgroup\": %d", &u.g2_kgroup) == 1 && (u.g1_dpt == 1 || u.g1_dpt == 2) &&
         (u.g2_bn == 128 || u.g2_bn == 256) &&
@@ -420,8 +422,8 @@ bool tune_cache_read(const char* path, const std::string& key, TcTune& t) {
 void tune_cache_append(const char* path, const std::string& key, const TcTune& t) {
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "{\"key\": \"%s\", \"g1_dpt\": %d, \"g2_bn\": %d, \"g2_kgroup\": %d}\n",
-          key.c_str(), t.g1_dpt, t.g2_bn, t.g2_kgroup);
+  fprintf(f, "{\"key\": \"%s\", \"g1_nb\": %d, \"g1_dpt\": %d, \"g2_bn\": %d, \"g2_kgroup\": %d}\n",
+          key.c_str(), t.g1_nb, t.g1_dpt, t.g2_bn, t.g2_kgroup);
   fclose(f);
 }
 
@@ -473,14 +475,16 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
   cudaError_t err = cudaSuccess;
   TcTune best = ctx->tune;
   float tbest = 1e30f;
-  for (int dpt = 1; dpt <= 2; ++dpt) {
+  const int g1_cand[3][2] = {{256, 1}, {128, 1}, {128, 2}};      // (MMA width, directions per tile)
+  for (const auto& c : g1_cand) {
     TcTune t = ctx->tune;
-    t.g1_dpt = dpt;
+    t.g1_nb = c[0];
+    t.g1_dpt = c[1];
     const float ms = time_launch([&] { return launch_gemm1_tc_group(ctx->opt.prec, g1.data(), (int)g1.size(),
                                                                     ctx->d_status, st, t, G1_NCH_CAP); },
                                  st, REPS, err);
     if (err != cudaSuccess) return from_cuda(err);
-    if (ms < tbest) { tbest = ms; best.g1_dpt = dpt; }
+    if (ms < tbest) { tbest = ms; best.g1_nb = c[0]; best.g1_dpt = c[1]; }
   }
   tbest = 1e30f;
   for (int bn = 128; bn <= 256; bn *= 2)
@@ -1205,8 +1209,9 @@ lrdm_status lrdm_get_projection(lrdm_ctx* ctx, int sys, int spin, int k, double*
                                          static_cast<cudaStream_t>(stream)));
 }
 
-lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_dpt, int* g2_bn, int* g2_kgroup) {
+lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_nb, int* g1_dpt, int* g2_bn, int* g2_kgroup) {
   if (!ctx) return LRDM_ERR_INVALID_ARG;
+  if (g1_nb) *g1_nb = ctx->tune.g1_nb;
   if (g1_dpt) *g1_dpt = ctx->tune.g1_dpt;
   if (g2_bn) *g2_bn = ctx->tune.g2_bn;
   if (g2_kgroup) *g2_kgroup = ctx->tune.g2_kgroup;

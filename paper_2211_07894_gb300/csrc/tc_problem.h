@@ -17,18 +17,21 @@ struct TcProblem {
   const float* a;                        // GEMM1 weights of this channel (direction 0)
   const void* psi0;                      // GEMM2 epilogue rows: bf16 hi / fp32
   const void* psi1;                      // bf16 lo
-  int ns, ns_pad, nI, NJ, ntiles, nch, nR, kmax;   // GEMM1: nI blocks, ntiles tiles; GEMM2: NJ, nR
+  int ns, ns_pad, nI, NJ, ntiles, ntiles_w, nch, nR, kmax;   // GEMM1: nI blocks, ntiles tiles; GEMM2: NJ, nR
 };
 
 constexpr int TC_MAX_SLOTS = 16;        // problems per grouped launch
 
 // Launch shape of the tensor-core contractions (chosen by the autotuner or
-// the defaults): directions per GEMM1 tile (1, 2), GEMM2 j-tile width (128,
-// 256) and GEMM2 direction group (directions sharing one Psi row block: 1, 2, 4).
+// the defaults): GEMM1 MMA width (128: square tiles with 1 or 2 directions;
+// 256: 128 x 256 tiles, one direction), directions per GEMM1 square tile,
+// GEMM2 j-tile width (128, 256) and GEMM2 direction group (directions sharing
+// one Psi row block: 1, 2, 4).
 struct TcTune {
-  int g1_dpt = 2;
+  int g1_nb = 256;
+  int g1_dpt = 1;
   int g2_bn = 256;
-  int g2_kgroup = 2;
+  int g2_kgroup = 4;
 };
 
 }  // namespace lrdm

@@ -17,6 +17,7 @@ from scipy.linalg import eigh
 import oracle
 import workloads
 from helpers import oracle_system, rel_err
+from ks_model import scf_map
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
@@ -28,20 +29,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 # Gateaux derivative with Psi = all eigenvectors (so the subspace is exact).
 # ---------------------------------------------------------------------------
 
-def _scf_map(n, h, vext, lap, rho_channels, n_e, kT, g):
-    w = float(np.prod(h))
-    nspin = len(rho_channels)
-    vh = oracle.hartree(sum(rho_channels), n, h)
-    eps, psi = [], []
-    for s in range(nspin):
-        veff = vext + vh + oracle.lda_vx(rho_channels[s], spin_polarized=(nspin == 2))
-        H = -0.5 * lap + np.diag(veff)
-        e, v = eigh(H)
-        eps.append(e)
-        psi.append(v / np.sqrt(w))
-    mu = oracle.solve_mu(eps, n_e, kT, g)
-    out = [oracle.density(p, oracle.fermi(e, mu, kT), g) for p, e in zip(psi, eps)]
-    return out, eps, psi
+_scf_map = scf_map
 
 
 def _fd_gateaux(n, h, vext, lap, rho, n_e, kT, g, v, eta=2e-3):
