@@ -72,6 +72,21 @@ def test_projection_ragged_tiles(lib, prec):
     assert max(errs) < TOL_X[prec]
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_projection_and_forward_odd_block_count(lib, prec):
+    """N_s = 300 pads to 384 states, three 128-blocks: the last 256-wide
+    projection tile and the last response j-tile are half outside the matrix
+    (their missing rows come from the TMA zero fill and are never stored)."""
+    cfg = _ragged(cfg_id=24, n=(18, 16, 20), ns=300, K=3, ne=230)
+    ctx, V, F, dmu = _run([cfg], prec)
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    errs = [rel_err(ctx.projection(k).cpu().numpy(), ref["X"][0][k]) for k in range(3)]
+    err = per_direction_rel_err(F[0], ref["F"])
+    print(f"odd block count {prec}: X err {max(errs):.2e}, f err {err:.2e}")
+    assert max(errs) < TOL_X[prec]
+    assert err < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
 def test_forward_toy16(lib, cfg1, prec):
     ctx, V, F, dmu = _run([cfg1], prec)
