@@ -456,6 +456,23 @@ def main():
                     "value_without_poisson": KDIR * world / ((fwd_med - poisson_fwd) / 1e3)}
     if ctx.status() != 0:
         raise RuntimeError("device status not ok after the forward-only replays")
+    # one direction per call (the unit of the adaptive-rank LRDM / LRDMA steps)
+    V1, F1 = V[:1].contiguous(), torch.empty_like(V[:1])
+    dmu1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    ctx.gateaux([V1], out=[F1], dmu=dmu1)       # captures the K = 1 graph
+    torch.cuda.synchronize()
+    ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for a0, a1 in ev1:
+        a0.record(stream)
+        ctx.gateaux([V1], out=[F1], dmu=dmu1)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    k1_med = statistics.median(a0.elapsed_time(a1) for a0, a1 in ev1)
+    forward_k1 = {"K": 1, "value": world / (k1_med / 1e3), "unit": "GD/s", "ms_median": k1_med,
+                  "graph": True}
+    if ctx.status() != 0:
+        raise RuntimeError("device status not ok after the one-direction replays")
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -575,7 +592,8 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],
-                "forward_only": forward_only, "fp64_plain": fp64_plain, "launch_shape": tuning,
+                "forward_only": forward_only, "forward_k1": forward_k1, "fp64_plain": fp64_plain,
+                "launch_shape": tuning,
                 "breakdown_ms": {"gemm1_per_step": prof["gemm1_ms"] / steps,
                                  "gemm2_per_step": prof["gemm2_ms"] / steps,
                                  "poisson_per_step": prof["poisson_ms"] / steps,

@@ -260,7 +260,7 @@ __global__ void k_loewner_scale(const void* __restrict__ X, int acc64, int nspli
 // in FP32 with the FP32 copy of L (the result is stored with at most 16
 // significant bits); the diagonal (mu' shift) in FP64.  One thread per four
 // consecutive columns: grid (column quads, rows, directions).
-__global__ void k_loewner_scale_tc(const float* __restrict__ X, int ns, int ld,
+__global__ void k_loewner_scale_tc(const float* __restrict__ X, int nsplit, int K, int ns, int ld,
                                    const float* __restrict__ Lf, const double* __restrict__ L,
                                    const double* __restrict__ shift, int adjoint,
                                    double inv_trace, int layout, void* __restrict__ out,
@@ -270,7 +270,15 @@ __global__ void k_loewner_scale_tc(const float* __restrict__ X, int ns, int ld,
   const int k = blockIdx.z;
   if (c0 >= ld) return;
   const long long o = ((long long)k * ld + row) * ld + c0;
-  const float4 x4 = *reinterpret_cast<const float4*>(X + o);
+  // X: [nsplit][K][ld][ld] partial sums over grid-row ranges, added in order
+  float4 x4 = *reinterpret_cast<const float4*>(X + o);
+  for (int p = 1; p < nsplit; ++p) {
+    const float4 y = *reinterpret_cast<const float4*>(X + o + (long long)p * K * ld * ld);
+    x4.x += y.x;
+    x4.y += y.y;
+    x4.z += y.z;
+    x4.w += y.w;
+  }
   const float4 l4 = *reinterpret_cast<const float4*>(Lf + (long long)row * ld + c0);
   const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, ls[4] = {l4.x, l4.y, l4.z, l4.w};
   float v[4];
@@ -517,9 +525,10 @@ cudaError_t launch_loewner_scale(const SysState& S, int s, const void* Xpart, in
   int layout = prec == LRDM_BF16X3 ? 2 : (prec == LRDM_TF32 ? 1 : 0);
   if (K == 0) return cudaSuccess;
   if (layout != 0) {
-    const int ld = c.ns_pad;                     // multiple of 128, nsplit = 1
+    const int ld = c.ns_pad;                     // multiple of 128
     dim3 grid((ld / 4 + 127) / 128, ld, K);
-    k_loewner_scale_tc<<<grid, 128, 0, st>>>(static_cast<const float*>(Xpart), c.ns, ld, c.Lf, c.L,
+    k_loewner_scale_tc<<<grid, 128, 0, st>>>(static_cast<const float*>(Xpart), S.nsplit, K, c.ns, ld,
+                                              c.Lf, c.L,
                                               shift, adjoint, inv_trace_L, layout, c.Xpp,
                                               static_cast<__nv_bfloat16*>(c.Xpp_lo));
     return cudaGetLastError();

@@ -3,7 +3,7 @@
 // GEMM1  X_k[i, j] = sum_r (a_k[r] Psi[r, i]) Psi[r, j]     (H-breve', §II.C)
 //        tile 128 (i) x 128 (j), blocks I <= J only (upper part), two
 //        directions per tile; the whole grid reduction runs inside one tile,
-//        in segments of 1024 rows whose TMEM results are summed in FP32
+//        in segments of 2048 rows whose TMEM results are summed in FP32
 //        registers; the a_k weighting is applied to the A rows between their
 //        TMA load and the MMAs, which read the weighted A from tensor memory.
 // GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 //
 // The tensor cores' FP32 accumulation truncates, and over a reduction of
 // 10^5-10^6 rows that bias reaches ~1e-3 of the result; so the reduction is
-// segmented: each segment of SEG stages (1024 rows) accumulates from zero in
+// segmented: each segment of SEG stages (2048 rows) accumulates from zero in
 // TMEM, after which the same eight warps add it into FP32 running sums held
 // in registers (round-to-nearest) before the next segment starts.
 //
@@ -430,7 +430,7 @@ struct G1Cfg {
   static constexpr int SC_OFF = B_OFF + PARTS * B_TILE;
   static constexpr int STRIDE = SC_OFF + 1024;                  // 1024-aligned stages
   static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
-  static constexpr int SEG = 1024 / BK;                          // stages per accumulation segment
+  static constexpr int SEG = 2048 / BK;                          // stages per accumulation segment
   static constexpr int LAG = STAGES - 1;                         // stages weighted ahead of a flush
   static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, NB);
   static_assert(G1_ACOL + STAGES * SLOT <= 512, "TMEM budget");
@@ -444,7 +444,8 @@ struct G1Params {
   int begin[TC_MAX_SLOTS + 1];
   int pid[TC_MAX_SLOTS];
   int K[TC_MAX_SLOTS];
-  float* X[TC_MAX_SLOTS];           // [K][ns_pad][ns_pad] per slot
+  float* X[TC_MAX_SLOTS];           // [nsplit][K][ns_pad][ns_pad] per slot
+  int nsplit[TC_MAX_SLOTS];         // grid-row ranges per slot (partial X summed by the consumers)
   int dpt;                          // directions per tile (1 or 2)
   int nch_lim;                      // > 0: reduce over the first nch_lim stages only (tuning)
   int* status;
@@ -454,19 +455,32 @@ __device__ __forceinline__ int g1_nch(const G1Params& P, const TcProblem* pr) {
   return P.nch_lim > 0 ? min(P.nch_lim, pr->nch) : pr->nch;
 }
 
-// Item -> slot q, first direction k0, directions nd, tile (I, J).  Direction
+// Stages [rb, re) of row range `split` of slot q.
+__device__ __forceinline__ void g1_range(const G1Params& P, const TcProblem* pr, int q, int split,
+                                         int& rb, int& re) {
+  const long long n = g1_nch(P, pr);
+  rb = (int)(n * split / P.nsplit[q]);
+  re = (int)(n * (split + 1) / P.nsplit[q]);
+}
+
+// Item -> slot q, row range `split`, first direction k0, directions nd, tile
+// (I, J).  Row ranges run slowest (each is a full set of items over its part
+// of the grid; small K is split so that enough items exist); direction
 // groups run fastest: the items of one tile run side by side on different SMs
 // and stream the same Psi^T rows through L2; tiles go column by column, so
 // neighbouring tiles share their B rows.  NB = 128: column J holds I = 0..J;
 // NB = 256: column J (256 wide) holds the 128-row blocks I < min(2 J + 2, nI).
 template <int NB>
 __device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item, int& q, int& k0,
-                                                    int& nd, int& I, int& J) {
+                                                    int& nd, int& I, int& J, int& split) {
   q = find_slot(P.begin, P.nslot, item);
   const TcProblem* pr = P.probs + P.pid[q];
-  const int idx = item - P.begin[q];
+  int idx = item - P.begin[q];
   const int K = P.K[q], dpt = NB == 256 ? 1 : P.dpt;
   const int npair = (K + dpt - 1) / dpt;
+  const int per_split = (NB == 256 ? pr->ntiles_w : pr->ntiles) * npair;
+  split = idx / per_split;                  // row range of the grid reduction (outermost)
+  idx -= split * per_split;
   int t = idx / npair;
   const int pp = idx - t * npair;
   k0 = dpt * pp;
@@ -605,14 +619,15 @@ __device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, co
   for (int i = 0; i < STAGES; ++i) pending[i] = -1;
   bool ok = true;
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-    int q, k0, nd, I, J;
-    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J);
+    int q, k0, nd, I, J, sp;
+    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J, sp);
+    int rb, re;
+    g1_range(P, pr, q, sp, rb, re);
     const float* w0 = pr->a + (long long)k0 * pr->a_stride;
     const long long wstride = pr->a_stride;
-    const int nch = g1_nch(P, pr);
     const CUtensorMap *ma = &pr->g1a, *mb0 = &pr->g1b0, *mb1 = &pr->g1b1;
     const uint32_t tx = C::A_BYTES + PARTS * C::B_TILE + nd * BK * 4;
-    for (int rc = 0; rc < nch; ++rc) {
+    for (int rc = rb; rc < re; ++rc) {
       if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
       uint8_t* st = smem + s * SB;
       ptx::mbar_arrive_expect_tx(&B.full[s], tx);
@@ -646,14 +661,15 @@ __device__ __forceinline__ void g1_mma(const G1Params& P, uint8_t* smem, const B
   uint32_t ph = 0, aph = 0;
   bool ok = true;
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-    int q, k0, nd, I, J;
-    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J);
-    const int nch = g1_nch(P, pr);
-    const int nseg = (nch + SEG - 1) / SEG;
+    int q, k0, nd, I, J, sp;
+    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J, sp);
+    int rb, re;
+    g1_range(P, pr, q, sp, rb, re);
+    const int nseg = (re - rb + SEG - 1) / SEG;
     for (int sg = 0; sg < nseg && ok; ++sg) {
       if (!wait1(&B.acc_empty[0], aph ^ 1, B, P.status)) { ok = false; break; }
       ptx::tc_fence_after();
-      const int r0 = sg * SEG, r1 = min(nch, r0 + SEG);
+      const int r0 = rb + sg * SEG, r1 = min(re, r0 + SEG);
       for (int rc = r0; rc < r1; ++rc) {
         if (!wait1(&B.ready[s], ph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
@@ -688,14 +704,16 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
   bool ok = true;
   float sum[128];
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-    int q, k0, nd, I, J;
-    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J);
-    const int nch = g1_nch(P, pr), ns = pr->ns, ns_pad = pr->ns_pad;
-    const int nseg = (nch + SEG - 1) / SEG;
+    int q, k0, nd, I, J, sp;
+    const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J, sp);
+    int rb, re;
+    g1_range(P, pr, q, sp, rb, re);
+    const int ns = pr->ns, ns_pad = pr->ns_pad;
+    const int nseg = (re - rb + SEG - 1) / SEG;
 #pragma unroll
     for (int c = 0; c < 128; ++c) sum[c] = 0.f;
     int flushed = 0;                      // segments already added into sum[]
-    for (int rc = 0; rc < nch; ++rc) {
+    for (int rc = rb; rc < re; ++rc) {
       if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
       weight_stage<PREC, NB>(ptx::smem_u32(smem + s * SB), row, h, nd,
                          tq + (uint32_t)(G1_ACOL + s * C::SLOT));
@@ -706,8 +724,8 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
       if (++s == STAGES) { s = 0; ph ^= 1; }
       // add a finished segment into the running sums once the weighting is
       // LAG stages past its end (those stages are ready when the MMAs resume)
-      const int ready_seg = (rc + 1 - LAG) / SEG;
-      const bool last = rc + 1 == nch;
+      const int ready_seg = (rc - rb + 1 - LAG) / SEG;
+      const bool last = rc + 1 == re;
       while (flushed < nseg && (flushed < ready_seg || last)) {
         if (!waitw(&B.acc_full[0], aph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
@@ -734,7 +752,7 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
     // columns of direction k0 + h, NB = 256: columns 128 h.. of direction k0
     const int i = I * G1_BN + row;
     if ((NB == 256 || h < nd) && i < ns) {
-      float* Xk = P.X[q] + (long long)(k0 + (NB == 256 ? 0 : h)) * ns_pad * ns_pad;
+      float* Xk = P.X[q] + ((long long)sp * P.K[q] + k0 + (NB == 256 ? 0 : h)) * ns_pad * ns_pad;
       const int j0 = J * NB + (NB == 256 ? h * 128 : 0);
 #pragma unroll
       for (int c = 0; c < 128; ++c) {
@@ -913,7 +931,7 @@ void order_slots(const TcEntry* e, int n, int gemm, int* order) {
     int t = order[i], j = i;
     auto cost = [&](int x) {
       const TcProblem& p = *e[x].host;
-      return gemm == 1 ? (double)p.nch : (double)p.ns_pad * p.ns_pad;
+      return gemm == 1 ? (double)p.nch / (e[x].split > 1 ? e[x].split : 1) : (double)p.ns_pad * p.ns_pad;
     };
     while (j > 0 && cost(order[j - 1]) < cost(t)) {
       order[j] = order[j - 1];
@@ -948,8 +966,9 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, c
       P.pid[q] = x.pid;
       P.K[q] = x.K;
       P.X[q] = static_cast<float*>(x.X);
+      P.nsplit[q] = x.split > 1 ? x.split : 1;
       P.begin[q] = items;
-      items += (NB == 256 ? x.host->ntiles_w : x.host->ntiles) * ((x.K + dpt - 1) / dpt);
+      items += (NB == 256 ? x.host->ntiles_w : x.host->ntiles) * ((x.K + dpt - 1) / dpt) * P.nsplit[q];
       ++q;
     }
     P.nslot = q;

@@ -360,6 +360,26 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
   return from_cuda(e);
 }
 
+// Grid-row ranges of the tensor-core GEMM1 for K directions of system s:
+// enough items for four waves over the SMs, at most 8 ranges, nsplit * K <=
+// k_max (the partial X share the context's X buffer) and at least 64 stages
+// of the reduction per range.  1 at the benchmark's K = 16.
+int choose_split(lrdm_ctx* ctx, int s, int K) {
+  const SysState& S = ctx->sys[s];
+  if (!is_tc(ctx->opt.prec) || K <= 0 || ctx->tc_pid.empty()) return 1;
+  const TcProblem& pr = ctx->tc_host[ctx->tc_pid[2 * s]];
+  const bool wide = ctx->tune.g1_nb == 256;
+  const int dpt = wide ? 1 : ctx->tune.g1_dpt;
+  const long long items = (long long)(wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
+  const long long waves = 4LL * (ctx->sm_count > 0 ? ctx->sm_count : 148);
+  int want = (int)((waves + items - 1) / items);
+  int smax = S.kmax / K;
+  if (smax > 8) smax = 8;
+  if (smax > pr.nch / 64) smax = pr.nch / 64;
+  if (want > smax) want = smax;
+  return want < 1 ? 1 : want;
+}
+
 TcEntry tc_entry(lrdm_ctx* ctx, int s, int c, int K) {
   TcEntry x;
   const int pid = ctx->tc_pid[2 * s + c];
@@ -527,12 +547,15 @@ lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void*
   // projection X_k = Psi^T diag(w dV_k) Psi
   if (tc) {
     ctx->tc_entries.clear();
-    for (int s = 0; s < ctx->nsys; ++s)
+    for (int s = 0; s < ctx->nsys; ++s) {
+      if (K[s] > 0) ctx->sys[s].nsplit = choose_split(ctx, s, K[s]);
       for (int c = 0; c < ctx->sys[s].nspin && K[s] > 0; ++c) {
         TcEntry x = tc_entry(ctx, s, c, K[s]);
         x.X = ctx->sys[s].ch[c].Xpart;
+        x.split = ctx->sys[s].nsplit;
         ctx->tc_entries.push_back(x);
       }
+    }
     LRDM_CK(tc_group(ctx, 1, 0, st));
   } else {
     for (int s = 0; s < ctx->nsys; ++s)
@@ -656,6 +679,7 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
   ctx->nsys = nsys;
   ctx->opt = o;
   cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
   ctx->sys = new (std::nothrow) SysState[nsys];
   if (!ctx->sys) {
     delete ctx;
@@ -1107,12 +1131,16 @@ lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* 
   }
   if (tc) {
     ctx->tc_entries.clear();
-    for (int s = 0; s < ctx->nsys; ++s)
+    for (int s = 0; s < ctx->nsys; ++s) {
+      // the same ranges as the forward call (the adjoint reduction reads X and Gbar together)
+      if (ctx->sys[s].last_K > 0) ctx->sys[s].nsplit = choose_split(ctx, s, ctx->sys[s].last_K);
       for (int c = 0; c < ctx->sys[s].nspin && ctx->sys[s].last_K > 0; ++c) {
         TcEntry x = tc_entry(ctx, s, c, ctx->sys[s].last_K);
         x.X = ctx->sys[s].ch[c].Gpart;
+        x.split = ctx->sys[s].nsplit;
         ctx->tc_entries.push_back(x);
       }
+    }
     LRDM_CK(tc_group(ctx, 1, 0, st));
   } else {
     for (int s = 0; s < ctx->nsys; ++s)

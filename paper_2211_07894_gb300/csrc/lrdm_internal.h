@@ -67,7 +67,8 @@ struct SysState {
   double w = 0, g = 2, kT = 0, ne = 0, mu = 0;
   bool occ_given = false;
   Channel ch[2];
-  int nsplit = 1;                    // grid-row splits of the CUDA-core GEMM1
+  int nsplit = 1;                    // grid-row splits of GEMM1 (CUDA cores: fixed at create;
+                                     // tensor cores: chosen per call from K, nsplit * K <= kmax)
   // Poisson
   cufftHandle plan_r2c = 0, plan_c2r = 0;
   bool plans = false;
@@ -104,6 +105,7 @@ struct lrdm_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key;
   lrdm::TcTune tune;                 // launch shape of the tensor-core contractions
+  int sm_count = 0;
   std::vector<double> inv_trace;     // per system 1 / sum_s sum_i L_ii
   // profiling (lrdm_profile_enable / lrdm_profile_read)
   bool prof_on = false;

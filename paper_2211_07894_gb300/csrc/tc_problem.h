@@ -44,7 +44,8 @@ struct TcEntry {
   const TcProblem* host = nullptr;       // host copy of this problem
   int pid = 0;                           // index into the device array
   int K = 0;                             // directions this call
-  void* X = nullptr;                     // GEMM1 output [K][ns_pad][ns_pad] FP32
+  void* X = nullptr;                     // GEMM1 output [split][K][ns_pad][ns_pad] FP32
+  int split = 1;                         // GEMM1 grid-row ranges (partials summed by the consumers)
   double factor = 0.0;                   // GEMM2: out = factor * drho (- v)
   const void* v = nullptr;
   long long v_stride = 0;

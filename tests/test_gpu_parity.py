@@ -87,6 +87,41 @@ def test_projection_and_forward_odd_block_count(lib, prec):
     assert err < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_small_k_row_range_split(lib, prec):
+    """A one-direction call (the Krylov steps' unit) splits the projection's
+    grid reduction into row ranges (40^3 rows, N_s = 512: 8 ranges); the
+    partial X are summed by every consumer: X, mu', f and the adjoint meet
+    the oracle tolerance, and the direction agrees with the same direction
+    computed unsplit inside an 8-direction call."""
+    from gpu_helpers import directions, make_context
+    cfg = _ragged(cfg_id=25, n=(40, 40, 40), ns=512, K=8, ne=400)
+    io = IO[prec]
+    ctx, _ = make_context([cfg], prec, io)
+    V = directions(cfg, io)
+    F8, _ = ctx.gateaux([V])
+    F8 = F8[0].double().cpu().numpy()
+    one = V[2:3].contiguous()
+    (F1,), dmu1 = ctx.gateaux([one])
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"][2:3])
+    X1 = ctx.projection(0).cpu().numpy()
+    assert rel_err(X1, ref["X"][0][0]) < TOL_X[prec]
+    err = per_direction_rel_err(F1.double().cpu().numpy(), ref["F"])
+    _check_dmu(dmu1.cpu().numpy(), ref, prec)
+    assert err < TOL[prec]
+    assert rel_err(F1.double().cpu().numpy()[0], F8[2]) < TOL[prec]
+    fbar = workloads.rng_for(25, 9).standard_normal((1,) + cfg["V"].shape[1:])
+    vbar, eb, ob = ctx.backward([torch.as_tensor(fbar, dtype=io, device="cuda")])
+    torch.cuda.synchronize()
+    bref = oracle.backward(oracle_system(cfg), fbar, ref)
+    print(f"K=1 split {prec}: f err {err:.2e}, vbar err "
+          f"{per_direction_rel_err(vbar[0].double().cpu().numpy(), bref['vbar']):.2e}")
+    assert per_direction_rel_err(vbar[0].double().cpu().numpy(), bref["vbar"]) < TOL[prec]
+    assert rel_err(eb[0].cpu().numpy(), bref["eps_bar"][0]) < 10 * TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
 def test_forward_toy16(lib, cfg1, prec):
     ctx, V, F, dmu = _run([cfg1], prec)
