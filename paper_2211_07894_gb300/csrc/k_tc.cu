@@ -3,7 +3,7 @@
 // GEMM1  X_k[i, j] = sum_r (a_k[r] Psi[r, i]) Psi[r, j]     (H-breve', §II.C)
 //        tile 128 (i) x 128 (j), blocks I <= J only (upper part), two
 //        directions per tile; the whole grid reduction runs inside one tile,
-//        in segments of 2048 rows whose TMEM results are summed in FP32
+//        in segments of 1024 rows whose TMEM results are summed in FP32
 //        registers; the a_k weighting is applied to the A rows between their
 //        TMA load and the MMAs, which read the weighted A from tensor memory.
 // GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 //
 // The tensor cores' FP32 accumulation truncates, and over a reduction of
 // 10^5-10^6 rows that bias reaches ~1e-3 of the result; so the reduction is
-// segmented: each segment of SEG stages (2048 rows) accumulates from zero in
+// segmented: each segment of SEG stages (1024 rows) accumulates from zero in
 // TMEM, after which the same eight warps add it into FP32 running sums held
 // in registers (round-to-nearest) before the next segment starts.
 //
@@ -430,7 +430,7 @@ struct G1Cfg {
   static constexpr int SC_OFF = B_OFF + PARTS * B_TILE;
   static constexpr int STRIDE = SC_OFF + 1024;                  // 1024-aligned stages
   static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
-  static constexpr int SEG = 2048 / BK;                          // stages per accumulation segment
+  static constexpr int SEG = 1024 / BK;                          // stages per accumulation segment
   static constexpr int LAG = STAGES - 1;                         // stages weighted ahead of a flush
   static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, NB);
   static_assert(G1_ACOL + STAGES * SLOT <= 512, "TMEM budget");
