@@ -39,4 +39,8 @@ from .lrdm_oracle import (  # noqa: F401
     backward,
     total_eps_grad,
     fermi_recursive,
+    KpointSystem,
+    solve_mu_kpoints,
+    density_kpoints,
+    gateaux_kpoints,
 )

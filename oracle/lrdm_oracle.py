@@ -37,7 +37,8 @@ __all__ = [
     "perturbation_potential", "project", "dmu_shift", "subspace_response",
     "density_response", "gateaux", "lrdm_apply", "backward", "total_eps_grad",
     "fermi_recursive", "loewner_recursive", "alpha_schedule", "lrdm_krylov_step",
-    "LrdmaState", "lrdma_step",
+    "LrdmaState", "lrdma_step", "KpointSystem", "solve_mu_kpoints", "density_kpoints",
+    "gateaux_kpoints",
 ]
 
 
@@ -389,6 +390,105 @@ def gateaux(system: System, V):
             Xps[s][k] = Xp
     return {"F": F, "drho": drho, "dmu": dmu, "X": Xs, "Xp": Xps, "dV": dV,
             "mu": mu, "L": L, "fx": fx}
+
+
+# ---------------------------------------------------------------------------
+# Brillouin-zone sampling (§II.C closing paragraphs, Eq. tracelessCondition)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class KpointSystem:
+    """A spin-restricted periodic system sampled at nk points kappa of the
+    first Brillouin zone: per point a complex subspace Psi_kappa (N_g x N_s,
+    Psi^H diag(w) Psi = I; the lattice-periodic parts of the Bloch functions,
+    whose phase factors cancel in every product below) and its projected
+    eigenvalues; BZ weights k_weights (positive, sum 1) stand for the BZ
+    average.  One mu is shared by all points:
+    g sum_kappa w_kappa sum_i f(eps_i,kappa, mu) = N_e."""
+
+    n: Sequence[int]
+    h: Sequence[float]
+    psi: List[np.ndarray]
+    eps: List[np.ndarray]
+    k_weights: Sequence[float]
+    rho: np.ndarray
+    n_electrons: float
+    kT: float
+    g: float = 2.0
+    poisson: str = "spectral"
+
+    @property
+    def w(self) -> float:
+        return float(np.prod(self.h))
+
+
+def solve_mu_kpoints(eps, k_weights, n_electrons, kT, g, max_iter=400):
+    """mu with g sum_kappa w_kappa sum_i f(eps_i,kappa, mu) = N_e (the
+    electron count of Eq. kseqcont averaged over the BZ), by bisection."""
+    def count(mu):
+        return g * sum(wk * float(fermi(e, mu, kT).sum()) for e, wk in zip(eps, k_weights))
+    lo = min(float(np.min(e)) for e in eps) - 800.0 * kT
+    hi = max(float(np.max(e)) for e in eps) + 800.0 * kT
+    if not (count(lo) < n_electrons < count(hi)):
+        raise ValueError("n_electrons outside the range the states can hold")
+    for _ in range(max_iter):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if count(mid) < n_electrons:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def density_kpoints(system: KpointSystem, mu, floor=0.0):
+    """rho(r) = g sum_kappa w_kappa sum_i f_i,kappa |psi_i,kappa(r)|^2 (+ floor)."""
+    rho = np.full(system.psi[0].shape[0], float(floor))
+    for psi, e, wk in zip(system.psi, system.eps, system.k_weights):
+        rho = rho + system.g * wk * ((np.abs(psi) ** 2) @ fermi(e, mu, system.kT))
+    return rho
+
+
+def gateaux_kpoints(system: KpointSystem, V):
+    """Gateaux derivatives of the residual for a BZ-sampled system.
+
+      dV_k = V_H[v_k] + f_x v_k                        (as for one point)
+      X_kappa = Psi_kappa^H diag(w dV_k) Psi_kappa     (Hermitian; H-breve')
+      mu' from the BZ-averaged traceless condition (Eq. tracelessCondition):
+        sum_kappa w_kappa sum_i L_kappa,ii (X_kappa,ii - mu') = 0
+      Gamma_kappa = L_kappa o (X_kappa - mu' I)         (L_kappa real)
+      drho_k = g sum_kappa w_kappa diag(Psi_kappa Gamma_kappa Psi_kappa^H)
+      f_k = drho_k - v_k.
+    V: (K, N_g) real.  Returns dict(F, drho, dmu, X (per kappa (K, N_s, N_s)
+    complex), mu, L, fx).
+    """
+    V = np.asarray(V, dtype=np.float64)
+    K = V.shape[0]
+    g, w = system.g, system.w
+    mu = solve_mu_kpoints(system.eps, system.k_weights, system.n_electrons, system.kT, g)
+    L = [loewner(e, mu, system.kT) for e in system.eps]
+    fx = lda_fx(system.rho)
+    F = np.zeros_like(V)
+    drho = np.zeros_like(V)
+    dmu = np.zeros(K)
+    Xs = [np.zeros((K,) + Lk.shape, dtype=np.complex128) for Lk in L]
+    for k in range(K):
+        dVk = perturbation_potential([V[k]], [fx], system.n, system.h, system.poisson)[0]
+        X = []
+        for psi in system.psi:
+            Xk = psi.conj().T @ ((w * dVk)[:, None] * psi)
+            X.append(0.5 * (Xk + Xk.conj().T))
+        num = sum(wk * float(np.dot(np.diag(Lk), np.diag(Xk).real))
+                  for wk, Lk, Xk in zip(system.k_weights, L, X))
+        den = sum(wk * float(np.sum(np.diag(Lk))) for wk, Lk in zip(system.k_weights, L))
+        dmu[k] = num / den
+        for q, (psi, wk, Lk, Xk) in enumerate(zip(system.psi, system.k_weights, L, X)):
+            G = Lk * (Xk - dmu[k] * np.eye(Xk.shape[0]))
+            drho[k] += g * wk * np.einsum("ri,ri->r", psi @ G, psi.conj()).real
+            Xs[q][k] = Xk
+        F[k] = drho[k] - V[k]
+    return {"F": F, "drho": drho, "dmu": dmu, "X": Xs, "mu": mu, "L": L, "fx": fx}
 
 
 # ---------------------------------------------------------------------------

@@ -92,6 +92,33 @@ def random_subspace(n, h, ns, rng):
     return Q / np.sqrt(w)
 
 
+def random_subspace_complex(n, h, ns, rng):
+    """Complex Psi = QR(diag(envelope) (G + i G')) / sqrt(w), dense, with
+    Psi^H diag(w) Psi = I: the lattice-periodic parts of the Bloch functions
+    at one k-point."""
+    w = float(np.prod(h))
+    N = int(np.prod(n))
+    G = rng.standard_normal((N, ns)) + 1j * rng.standard_normal((N, ns))
+    Q, _ = np.linalg.qr(envelope(n, h)[:, None] * G, mode="reduced")
+    return Q / np.sqrt(w)
+
+
+def kpoint_system(cfg, n, ns, nk, n_electrons, kT, K, h=(0.5, 0.5, 0.5), stream=0, rho_floor=1e-3):
+    """A spin-restricted periodic system at nk Brillouin-zone points with
+    (1, 3, 3, ..., 1)-shaped weights normalised to 1 (the multiplicities of a
+    symmetry-reduced Monkhorst-Pack line), a complex subspace and sorted
+    eigenvalues per point (shifted by 0.02 Ha from point to point), and K
+    smooth real directions."""
+    rng = rng_for(cfg, stream)
+    raw = np.array([1.0 + 2.0 * min(i, nk - 1 - i) for i in range(nk)])
+    kw = raw / raw.sum()
+    psi = [random_subspace_complex(n, h, ns, rng) for _ in range(nk)]
+    eps = [random_eigenvalues(ns, rng) + 0.02 * q for q in range(nk)]
+    dirs = smooth_directions(n, h, K, 1, rng_for(cfg, stream + 1))[:, 0]
+    return dict(name=f"kp{n[0]}_{ns}_{nk}", n=tuple(n), h=tuple(h), psi=psi, eps=eps, k_weights=kw,
+                n_electrons=float(n_electrons), kT=float(kT), g=2.0, rho_floor=rho_floor, V=dirs)
+
+
 def random_eigenvalues(ns, rng, lo=-1.0, hi=1.0):
     return np.sort(rng.uniform(lo, hi, ns))
 
