@@ -315,6 +315,59 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
 lrdm_status lrdm_lrdma_clear(lrdm_lrdma* a);
 void lrdm_lrdma_destroy(lrdm_lrdma* a);
 
+/* ---------------------------------------------------------------------------
+ * Periodic systems sampled at several points of the first Brillouin zone
+ * (§II.C, closing paragraphs, Eq. tracelessCondition).  Each k-point kappa
+ * has its own complex subspace Psi_kappa (the lattice-periodic parts of the
+ * Bloch functions, Psi^H diag(w) Psi = I, given as real and imaginary planes)
+ * and eigenvalues; the density and the response are BZ averages with weights
+ * w_kappa; one chemical potential is shared; mu' comes from the BZ-averaged
+ * traceless condition:
+ *   X_kappa = Psi_kappa^H diag(w dV_k) Psi_kappa,
+ *   sum_kappa w_kappa sum_i L_kappa,ii (X_kappa,ii - mu') = 0,
+ *   drho_k = g sum_kappa w_kappa diag(Psi_kappa L_kappa o (X_kappa - mu' I) Psi_kappa^H).
+ * Spin-restricted; FP64 or FP32 on the CUDA cores (other precisions:
+ * LRDM_ERR_UNSUPPORTED).  A k-point context serves lrdm_kp_gateaux,
+ * lrdm_apply (sys 0, n = N_g), lrdm_get_mu, lrdm_get_density,
+ * lrdm_status_query, lrdm_profile_* and lrdm_destroy; lrdm_gateaux_batch,
+ * lrdm_backward, lrdm_krylov_step, lrdm_get_projection and lrdm_lrdma_step
+ * return LRDM_ERR_UNSUPPORTED for it.
+ * ------------------------------------------------------------------------- */
+typedef struct lrdm_kpoint_system {
+  int n[3];                       /* periodic grid                                 */
+  double h[3];                    /* spacing (bohr)                                */
+  int nk;                         /* k-points, 1..32                               */
+  int ns;                         /* states per k-point                            */
+  int ld_psi;                     /* leading dimension of every Psi plane, >= ns    */
+  const void* const* psi_re;      /* [nk] device [N_g][ld_psi] io dtype: Re Psi     */
+  const void* const* psi_im;      /* [nk] device [N_g][ld_psi] io dtype: Im Psi     */
+  const double* const* eps;       /* [nk] device [ns] FP64                         */
+  const double* k_weights;        /* HOST [nk], positive, summing to 1 (1e-12)     */
+  const void* rho;                /* device [N_g] io dtype, or NULL: g sum_kappa
+                                     w_kappa sum_i f_i |psi_i|^2 + rho_floor       */
+  double n_electrons;             /* N_e = g sum_kappa w_kappa sum_i f_i            */
+  double kT;                      /* Fermi smearing (Ha), > 0                       */
+  double occ_factor;              /* g; <= 0 -> 2                                  */
+  double rho_floor;
+  int k_max;                      /* directions per call; 0 -> options.k_max       */
+} lrdm_kpoint_system;
+
+/* Creates a context for one Brillouin-zone-sampled system: copies each Psi
+ * plane into the compute type (the caller's buffers are not kept), solves mu
+ * over all k-points on the host, builds the Loewner matrices, the density if
+ * not given, f_x and the Poisson plans.  Synchronises the stream.
+ * Errors: INVALID_ARG (null pointers, nk outside 1..32, weights not positive
+ * or not summing to 1, kT <= 0, bad options), MU_NOT_CONVERGED (N_e outside
+ * what the states can hold), UNSUPPORTED (precision other than FP64 / FP32),
+ * OOM, CUDA. */
+lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const lrdm_options* opt,
+                           void* stream);
+/* f_k = drho_k - v_k for K real directions v ([K][N_g] io dtype, device);
+ * f_out has the same layout; dmu_out device [K] FP64 or NULL.  0 <= K <= k_max
+ * (else INVALID_ARG).  Asynchronous on `stream`. */
+lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, double* dmu_out,
+                            void* stream);
+
 /* Copies the projected perturbation X_k = Psi^T diag(w dV_k) Psi of direction
  * k, channel `spin`, of system `sys` from the most recent lrdm_gateaux_batch
  * into out ([N_s][N_s] FP64, device), for inspection and testing.

@@ -8,6 +8,7 @@ The computation lives in the C-ABI library ``lib/liblrdm.so`` (declared in
 
 from .binding import (  # noqa: F401
     Context,
+    KpContext,
     Lrdma,
     LrdmError,
     gateaux_function,
@@ -22,6 +23,8 @@ from .binding import (  # noqa: F401
     lrdm_get_mu,
     lrdm_get_projection,
     lrdm_get_tuning,
+    lrdm_kp_create,
+    lrdm_kp_gateaux,
     lrdm_krylov_step,
     lrdm_profile_enable,
     lrdm_profile_read,

@@ -47,6 +47,14 @@ class lrdm_options(ctypes.Structure):
                 ("fermi_T", c_int)]
 
 
+class lrdm_kpoint_system(ctypes.Structure):
+    _fields_ = [("n", c_int * 3), ("h", c_double * 3), ("nk", c_int), ("ns", c_int),
+                ("ld_psi", c_int), ("psi_re", POINTER(c_void_p)), ("psi_im", POINTER(c_void_p)),
+                ("eps", POINTER(c_void_p)), ("k_weights", POINTER(c_double)), ("rho", c_void_p),
+                ("n_electrons", c_double), ("kT", c_double), ("occ_factor", c_double),
+                ("rho_floor", c_double), ("k_max", c_int)]
+
+
 _lib = None
 
 EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_apply",
@@ -54,7 +62,8 @@ EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_ap
            "lrdm_backward", "lrdm_status_query", "lrdm_get_mu", "lrdm_get_density",
            "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string",
            "lrdm_get_tuning", "lrdm_krylov_step", "lrdm_lrdma_default_params", "lrdm_lrdma_create",
-           "lrdm_lrdma_step", "lrdm_lrdma_clear", "lrdm_lrdma_destroy"]
+           "lrdm_lrdma_step", "lrdm_lrdma_clear", "lrdm_lrdma_destroy", "lrdm_kp_create",
+           "lrdm_kp_gateaux"]
 
 
 class lrdm_lrdma_params(ctypes.Structure):
@@ -130,6 +139,11 @@ def load(path: Optional[str] = None):
     lib.lrdm_get_tuning.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                     POINTER(c_int)]
     lib.lrdm_get_tuning.restype = c_int
+    lib.lrdm_kp_create.argtypes = [POINTER(c_void_p), POINTER(lrdm_kpoint_system),
+                                   POINTER(lrdm_options), c_void_p]
+    lib.lrdm_kp_create.restype = c_int
+    lib.lrdm_kp_gateaux.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    lib.lrdm_kp_gateaux.restype = c_int
     lib.lrdm_destroy.argtypes = [c_void_p]
     lib.lrdm_destroy.restype = None
     lib.lrdm_status_string.argtypes = [c_int]
@@ -249,6 +263,18 @@ def lrdm_get_tuning(ctx):
     _check("lrdm_get_tuning", load().lrdm_get_tuning(ctx, ctypes.byref(z), ctypes.byref(a),
                                                      ctypes.byref(b), ctypes.byref(c)))
     return dict(g1_nb=z.value, g1_dpt=a.value, g2_bn=b.value, g2_kgroup=c.value)
+
+
+def lrdm_kp_create(system: lrdm_kpoint_system, options: lrdm_options, stream: int = 0):
+    h = c_void_p()
+    code = load().lrdm_kp_create(ctypes.byref(h), ctypes.byref(system), ctypes.byref(options),
+                                 c_void_p(stream))
+    return code, h
+
+
+def lrdm_kp_gateaux(ctx, v_ptr, K, f_ptr, dmu_ptr, stream: int = 0) -> int:
+    return load().lrdm_kp_gateaux(ctx, c_void_p(v_ptr), int(K), c_void_p(f_ptr),
+                                  c_void_p(dmu_ptr or 0), c_void_p(stream))
 
 
 def lrdm_destroy(ctx) -> None:
@@ -453,6 +479,125 @@ class Context:
     def tuning(self):
         """Launch shape of the tensor-core contractions (defaults or autotuned)."""
         return lrdm_get_tuning(self.handle)
+
+    def profile(self, on=True):
+        _check("lrdm_profile_enable", lrdm_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        return lrdm_profile_read(self.handle, 1 if reset else 0)
+
+    def status(self, synchronize=True):
+        return lrdm_status_query(self.handle, 1 if synchronize else 0)
+
+
+class KpContext:
+    """Owns one Brillouin-zone-sampled lrdm_ctx (lrdm_kp_create).
+
+    psi_re / psi_im: per k-point (N_g, N_s) device tensors in the io dtype
+    (real and imaginary planes of the lattice-periodic subspace, orthonormal
+    under the grid quadrature); eps: per k-point float64 device tensors;
+    k_weights: floats summing to 1.  Directions and results are (K, N_g) in
+    the io dtype.
+    """
+
+    def __init__(self, n, h, psi_re, psi_im, eps, k_weights, n_electrons, kT, g=2.0,
+                 rho=None, rho_floor=0.0, prec="fp64", io_dtype=None, k_max=16, degen_tol=1e-5,
+                 stream=None):
+        import torch
+        self.torch = torch
+        self.io_dtype = io_dtype or torch.float64
+        o = lrdm_default_options()
+        o.prec = PRECISIONS[prec]
+        o.io_dtype = DTYPE_F64 if self.io_dtype == torch.float64 else DTYPE_F32
+        o.k_max = int(k_max)
+        o.degen_tol = float(degen_tol)
+        nk = len(psi_re)
+        assert len(psi_im) == nk and len(eps) == nk and len(k_weights) == nk
+        s = lrdm_kpoint_system()
+        for i in range(3):
+            s.n[i] = int(n[i])
+            s.h[i] = float(h[i])
+        s.nk = nk
+        ns = int(psi_re[0].shape[1])
+        s.ns = ns
+        s.ld_psi = int(psi_re[0].stride(0))
+        for t in list(psi_re) + list(psi_im):
+            assert t.is_cuda and t.dtype == self.io_dtype and t.dim() == 2
+            assert t.shape[1] == ns and t.stride(1) == 1 and t.stride(0) == s.ld_psi
+        for e in eps:
+            assert e.is_cuda and e.dtype == torch.float64 and e.is_contiguous() and e.numel() == ns
+        pr = (c_void_p * nk)(*[t.data_ptr() for t in psi_re])
+        pi = (c_void_p * nk)(*[t.data_ptr() for t in psi_im])
+        pe = (c_void_p * nk)(*[e.data_ptr() for e in eps])
+        kw = (c_double * nk)(*[float(x) for x in k_weights])
+        s.psi_re = ctypes.cast(pr, POINTER(c_void_p))
+        s.psi_im = ctypes.cast(pi, POINTER(c_void_p))
+        s.eps = ctypes.cast(pe, POINTER(c_void_p))
+        s.k_weights = ctypes.cast(kw, POINTER(c_double))
+        keep = []
+        if rho is not None:
+            rho = rho.to(self.io_dtype).contiguous()
+            s.rho = rho.data_ptr()
+            keep.append(rho)
+        s.n_electrons = float(n_electrons)
+        s.kT = float(kT)
+        s.occ_factor = float(g)
+        s.rho_floor = float(rho_floor)
+        s.k_max = 0
+        self.Ng = int(np.prod(n))
+        self.k_max = int(k_max)
+        code, hd = lrdm_kp_create(s, o, self._stream(stream))
+        _check("lrdm_kp_create", code)
+        self.handle = hd
+        del keep
+
+    def _stream(self, stream):
+        if stream is None:
+            return self.torch.cuda.current_stream().cuda_stream
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lrdm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def mu(self):
+        return lrdm_get_mu(self.handle, 0)
+
+    def density(self, stream=None):
+        out = self.torch.empty(self.Ng, dtype=self.io_dtype, device="cuda")
+        _check("lrdm_get_density", lrdm_get_density(self.handle, 0, 0, out.data_ptr(),
+                                                    self._stream(stream)))
+        return out
+
+    def gateaux(self, V, out=None, dmu=None, stream=None):
+        """f_k = drho_k - v_k for V (K, N_g); returns (F, dmu)."""
+        torch = self.torch
+        assert V.is_contiguous() and V.dtype == self.io_dtype and V.shape[-1] == self.Ng
+        K = int(V.shape[0])
+        F = out if out is not None else torch.empty_like(V)
+        if dmu is None:
+            dmu = torch.empty(max(1, K), dtype=torch.float64, device="cuda")
+        _check("lrdm_kp_gateaux", lrdm_kp_gateaux(self.handle, V.data_ptr(), K, F.data_ptr(),
+                                                  dmu.data_ptr(), self._stream(stream)))
+        return F, dmu[:K]
+
+    def apply(self, R, V, F, alpha, rho=None, stream=None):
+        """The least-squares step on K derivatives (lrdm_apply, sys 0)."""
+        torch = self.torch
+        K = int(V.shape[0])
+        coeff = torch.empty(K, dtype=torch.float64, device="cuda")
+        s_rel = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check("lrdm_apply", lrdm_apply(self.handle, 0, R.data_ptr(), V.data_ptr(), F.data_ptr(), K,
+                                        float(alpha), rho.data_ptr() if rho is not None else 0,
+                                        coeff.data_ptr(), s_rel.data_ptr(), self._stream(stream)))
+        return coeff, s_rel
 
     def profile(self, on=True):
         _check("lrdm_profile_enable", lrdm_profile_enable(self.handle, 1 if on else 0))

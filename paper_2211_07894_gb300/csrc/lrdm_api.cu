@@ -134,6 +134,26 @@ lrdm_status validate_system(const lrdm_system& s, const lrdm_options& o) {
   return LRDM_OK;
 }
 
+// Poisson: batched real <-> half-complex transforms over k_max fields, the
+// symbol table and the transform buffers of system S.
+lrdm_status setup_poisson(lrdm_ctx* ctx, SysState& S, cudaStream_t st) {
+  const lrdm_options& o = ctx->opt;
+  const int fp64 = o.prec == LRDM_FP64;
+  const size_t csz = fp64 ? sizeof(double) : sizeof(float);
+  const long long nc = (long long)S.n[0] * S.n[1] * (S.n[2] / 2 + 1);
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_real), (size_t)S.kmax * S.Ng * csz));
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_cplx), (size_t)S.kmax * nc * 2 * csz));
+  int nn[3] = {S.n[0], S.n[1], S.n[2]};
+  LRDM_FFT(cufftPlanMany(&S.plan_r2c, 3, nn, nullptr, 1, (int)S.Ng, nullptr, 1, (int)nc,
+                         fp64 ? CUFFT_D2Z : CUFFT_R2C, S.kmax));
+  S.plans = true;
+  LRDM_FFT(cufftPlanMany(&S.plan_c2r, 3, nn, nullptr, 1, (int)nc, nullptr, 1, (int)S.Ng,
+                         fp64 ? CUFFT_Z2D : CUFFT_C2R, S.kmax));
+  LRDM_CK(dalloc(ctx, &S.sym, (size_t)nc, false));
+  LRDM_CU(launch_poisson_table(S.n, S.h, o.poisson_symbol, S.sym, st));
+  return LRDM_OK;
+}
+
 lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStream_t st) {
   const lrdm_options& o = ctx->opt;
   SysState& S = ctx->sys[idx];
@@ -264,19 +284,7 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
   LRDM_CK(dalloc(ctx, &S.dmu, S.kmax));
   LRDM_CK(dalloc(ctx, &S.tbar, S.kmax));
 
-  // Poisson: batched real <-> half-complex transforms over k_max fields
-  const long long nc = (long long)S.n[0] * S.n[1] * (S.n[2] / 2 + 1);
-  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_real), (size_t)S.kmax * S.Ng * csz));
-  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_cplx), (size_t)S.kmax * nc * 2 * csz));
-  int nn[3] = {S.n[0], S.n[1], S.n[2]};
-  LRDM_FFT(cufftPlanMany(&S.plan_r2c, 3, nn, nullptr, 1, (int)S.Ng, nullptr, 1, (int)nc,
-                         fp64 ? CUFFT_D2Z : CUFFT_R2C, S.kmax));
-  S.plans = true;
-  LRDM_FFT(cufftPlanMany(&S.plan_c2r, 3, nn, nullptr, 1, (int)nc, nullptr, 1, (int)S.Ng,
-                         fp64 ? CUFFT_Z2D : CUFFT_C2R, S.kmax));
-  LRDM_CK(dalloc(ctx, &S.sym, (size_t)nc, false));
-  LRDM_CU(launch_poisson_table(S.n, S.h, o.poisson_symbol, S.sym, st));
-  return LRDM_OK;
+  return setup_poisson(ctx, S, st);
 }
 
 // V_H = F^-1[4 pi F[fft_real] / |G|^2] in place in S.fft_real (all k_max slots).
@@ -756,6 +764,7 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
 
 lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K,
                                void* const* f_out, double* dmu_out, void* stream) {
+  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!ctx || !v || !K || !f_out) return LRDM_ERR_INVALID_ARG;
   for (int s = 0; s < ctx->nsys; ++s) {
     if (K[s] < 0 || K[s] > ctx->sys[s].kmax) return LRDM_ERR_INVALID_ARG;
@@ -819,6 +828,7 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
 lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol, int r_max,
                              double alpha, void* rho_inout, void* U, void* T, double* coeff_out,
                              double* s_rel_out, int* rank_out, double* r_norm_out, void* stream) {
+  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !U || !T) return LRDM_ERR_INVALID_ARG;
   if (r_max < 1 || r_max > KMAX_LIMIT || !(s_tol >= 0.0) || !isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -998,6 +1008,7 @@ void lrdm_lrdma_destroy(lrdm_lrdma* a) {
 lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R, void* rho_inout,
                             const lrdm_lrdma_params* params, lrdm_lrdma_report* report,
                             void* stream) {
+  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!a || !ctx || sys < 0 || sys >= ctx->nsys || !R) return LRDM_ERR_INVALID_ARG;
   lrdm_lrdma_params p;
   if (params) p = *params;
@@ -1105,6 +1116,7 @@ lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int i
 
 lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
                           double* const* eps_bar, double* const* occ_bar, void* stream) {
+  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!ctx || !f_bar || !v_bar) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int prec = ctx->opt.prec;
@@ -1230,6 +1242,7 @@ lrdm_status lrdm_get_density(lrdm_ctx* ctx, int sys, int spin, void* out, void* 
 
 lrdm_status lrdm_get_projection(lrdm_ctx* ctx, int sys, int spin, int k, double* out,
                                 void* stream) {
+  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!ctx || !out || sys < 0 || sys >= ctx->nsys) return LRDM_ERR_INVALID_ARG;
   SysState& S = ctx->sys[sys];
   if (spin < 0 || spin >= S.nspin || k < 0 || k >= S.last_K) return LRDM_ERR_INVALID_ARG;
@@ -1287,5 +1300,238 @@ lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_
 }
 
 void lrdm_destroy(lrdm_ctx* ctx) { free_ctx(ctx); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Brillouin-zone-sampled systems (lrdm_kp_create / lrdm_kp_gateaux)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// mu with g sum_kappa w_kappa sum_i f((eps_i,kappa - mu)/kT) = N_e, bisection
+lrdm_status solve_mu_kp_host(const std::vector<std::vector<double>>& eps, const std::vector<double>& kw,
+                             double ne, double kT, double g, double* mu) {
+  auto electrons = [&](double m) {
+    double c = 0.0;
+    for (size_t q = 0; q < eps.size(); ++q) {
+      double cq = 0.0;
+      for (double e : eps[q]) cq += fermi_host((e - m) / kT);
+      c += kw[q] * cq;
+    }
+    return g * c;
+  };
+  double lo = 1e300, hi = -1e300;
+  for (const auto& e : eps)
+    for (double x : e) {
+      lo = fmin(lo, x);
+      hi = fmax(hi, x);
+    }
+  lo -= 800.0 * kT;
+  hi += 800.0 * kT;
+  if (!(electrons(lo) < ne && ne < electrons(hi))) return LRDM_ERR_MU_NOT_CONVERGED;
+  for (int it = 0; it < 400; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (electrons(mid) < ne) lo = mid;
+    else hi = mid;
+  }
+  *mu = 0.5 * (lo + hi);
+  return LRDM_OK;
+}
+
+lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t st) {
+  const lrdm_options& o = ctx->opt;
+  const int fp64 = o.prec == LRDM_FP64;
+  const size_t csz = fp64 ? sizeof(double) : sizeof(float);
+  SysState& S = ctx->sys[0];
+  for (int d = 0; d < 3; ++d) {
+    S.n[d] = in.n[d];
+    S.h[d] = in.h[d];
+  }
+  S.Ng = (long long)in.n[0] * in.n[1] * in.n[2];
+  S.Ng_pad = S.Ng;
+  S.nspin = 1;
+  S.kmax = in.k_max > 0 ? in.k_max : o.k_max;
+  S.w = in.h[0] * in.h[1] * in.h[2];
+  S.g = in.occ_factor > 0.0 ? in.occ_factor : 2.0;
+  S.kT = in.kT;
+  S.ne = in.n_electrons;
+  const int nk = in.nk, ns = in.ns;
+  ctx->kp = true;
+  ctx->kp_nk = nk;
+  ctx->kp_ns = ns;
+  ctx->kp_w.assign(in.k_weights, in.k_weights + nk);
+  std::vector<std::vector<double>> eps(nk, std::vector<double>(ns)), occ(nk, std::vector<double>(ns));
+  for (int q = 0; q < nk; ++q)
+    LRDM_CU(cudaMemcpy(eps[q].data(), in.eps[q], ns * sizeof(double), cudaMemcpyDeviceToHost));
+  LRDM_CK(solve_mu_kp_host(eps, ctx->kp_w, S.ne, S.kT, S.g, &S.mu));
+  // row ranges of the projection: about two blocks per SM at k_max directions
+  const int nt = (ns + 63) / 64;
+  const long long blocks = (long long)nt * (nt + 1) / 2 * S.kmax;
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+  long long split = (2LL * sms + blocks - 1) / blocks;
+  if (split > S.Ng / 256) split = S.Ng / 256;
+  if (split > 64) split = 64;
+  ctx->kp_nsplit = (int)(split < 1 ? 1 : split);
+  const size_t npsi = (size_t)S.Ng * ns, mat = (size_t)ns * ns;
+  ctx->kp_pr.assign(nk, nullptr);
+  ctx->kp_pi.assign(nk, nullptr);
+  ctx->kp_eps.assign(nk, nullptr);
+  ctx->kp_occ.assign(nk, nullptr);
+  ctx->kp_L.assign(nk, nullptr);
+  ctx->kp_Xr.assign(nk, nullptr);
+  ctx->kp_Xi.assign(nk, nullptr);
+  ctx->kp_Yr.assign(nk, nullptr);
+  ctx->kp_Yi.assign(nk, nullptr);
+  Channel& ch = S.ch[0];
+  ch.ns = ns;
+  LRDM_CK(dalloc(ctx, &ch.rho, S.Ng, false));
+  const size_t xc = (size_t)ctx->kp_nsplit * S.kmax * mat;
+  for (int q = 0; q < nk; ++q) {
+    for (int i = 0; i < ns; ++i) occ[q][i] = fermi_host((eps[q][i] - S.mu) / S.kT);
+    LRDM_CK(dalloc(ctx, &ctx->kp_eps[q], ns, false));
+    LRDM_CK(dalloc(ctx, &ctx->kp_occ[q], ns, false));
+    LRDM_CU(cudaMemcpyAsync(ctx->kp_eps[q], eps[q].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    LRDM_CU(cudaMemcpyAsync(ctx->kp_occ[q], occ[q].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    LRDM_CK(dalloc(ctx, &ctx->kp_L[q], mat, false));
+    LRDM_CU(launch_loewner(ctx->kp_eps[q], ctx->kp_occ[q], ns, S.mu, S.kT, 0, o.degen_tol, 0,
+                           ctx->kp_L[q], st));
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_pr[q]), npsi * csz, false));
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_pi[q]), npsi * csz, false));
+    LRDM_CU(launch_kp_copy(fp64, in.psi_re[q], o.io_dtype, in.ld_psi, S.Ng, ns, ctx->kp_pr[q], st));
+    LRDM_CU(launch_kp_copy(fp64, in.psi_im[q], o.io_dtype, in.ld_psi, S.Ng, ns, ctx->kp_pi[q], st));
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Xr[q]), xc * csz));
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Xi[q]), xc * csz));
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Yr[q]), (size_t)S.kmax * mat * csz));
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Yi[q]), (size_t)S.kmax * mat * csz));
+    if (!in.rho)
+      LRDM_CU(launch_kp_density(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, ctx->kp_occ[q],
+                                S.g * ctx->kp_w[q], q == 0, in.rho_floor, ch.rho, st));
+  }
+  if (in.rho) LRDM_CU(launch_copy_rho(in.rho, o.io_dtype, S.Ng, ch.rho, st));
+  LRDM_CK(dalloc(ctx, &ch.fx, S.Ng, false));
+  LRDM_CU(launch_fx(ch.rho, S.Ng, 0, ch.fx, st));
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.a), (size_t)S.kmax * S.Ng * csz));
+  LRDM_CK(dalloc(ctx, &S.dmu, S.kmax));
+  LRDM_CK(dalloc(ctx, &ctx->kp_drho, (size_t)S.kmax * S.Ng));
+  LRDM_CK(setup_poisson(ctx, S, st));
+  LRDM_CU(cudaStreamSynchronize(st));   // the host eps / occ vectors end here
+  return LRDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const lrdm_options* opt,
+                           void* stream) {
+  if (!out) return LRDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!sys || sys->nk < 1 || sys->nk > KP_MAX || sys->ns < 1 || sys->ld_psi < sys->ns)
+    return LRDM_ERR_INVALID_ARG;
+  if (!sys->psi_re || !sys->psi_im || !sys->eps || !sys->k_weights) return LRDM_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (sys->n[d] < 2 || !(sys->h[d] > 0.0)) return LRDM_ERR_INVALID_ARG;
+  double wsum = 0.0;
+  for (int q = 0; q < sys->nk; ++q) {
+    if (!sys->psi_re[q] || !sys->psi_im[q] || !sys->eps[q] || !(sys->k_weights[q] > 0.0))
+      return LRDM_ERR_INVALID_ARG;
+    wsum += sys->k_weights[q];
+  }
+  if (!(fabs(wsum - 1.0) <= 1e-12) || !(sys->kT > 0.0) || !(sys->n_electrons > 0.0))
+    return LRDM_ERR_INVALID_ARG;
+  lrdm_options o;
+  if (opt) o = *opt;
+  else lrdm_default_options(&o);
+  if (o.prec != LRDM_FP64 && o.prec != LRDM_FP32) return LRDM_ERR_UNSUPPORTED;
+  if (o.io_dtype != LRDM_DTYPE_F64 && o.io_dtype != LRDM_DTYPE_F32) return LRDM_ERR_INVALID_ARG;
+  if (o.k_max < 1 || o.k_max > KMAX_LIMIT || sys->k_max < 0 || sys->k_max > KMAX_LIMIT)
+    return LRDM_ERR_INVALID_ARG;
+  if (!(o.degen_tol >= 0.0) || (o.poisson_symbol != 0 && o.poisson_symbol != 1)) return LRDM_ERR_INVALID_ARG;
+  lrdm_ctx* ctx = new (std::nothrow) lrdm_ctx();
+  if (!ctx) return LRDM_ERR_OOM;
+  ctx->nsys = 1;
+  ctx->opt = o;
+  cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+  ctx->sys = new (std::nothrow) SysState[1];
+  if (!ctx->sys) {
+    delete ctx;
+    return LRDM_ERR_OOM;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lrdm_status rc = LRDM_OK;
+  do {
+    if ((rc = dalloc(ctx, &ctx->d_status, 1)) != LRDM_OK) break;
+    const int maxval = KMAX_LIMIT * (KMAX_LIMIT + 1) / 2 + KMAX_LIMIT + 1;
+    if ((rc = dalloc(ctx, &ctx->ls_partial, (size_t)LS_BLOCKS * maxval)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->ls_coef, KMAX_LIMIT)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->ls_scal, 4)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->upd_partial, UPD_BLOCKS)) != LRDM_OK) break;
+    if ((rc = kp_setup(ctx, *sys, st)) != LRDM_OK) break;
+    if (cudaGetLastError() != cudaSuccess) rc = LRDM_ERR_CUDA;
+  } while (0);
+  if (rc != LRDM_OK) {
+    free_ctx(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, double* dmu_out,
+                            void* stream) {
+  if (!ctx || !ctx->kp) return LRDM_ERR_INVALID_ARG;
+  SysState& S = ctx->sys[0];
+  if (K < 0 || K > S.kmax) return LRDM_ERR_INVALID_ARG;
+  if (K == 0) {
+    S.last_K = 0;
+    return LRDM_OK;
+  }
+  if (!v || !f_out) return LRDM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int fp64 = ctx->opt.prec == LRDM_FP64;
+  const int io = ctx->opt.io_dtype;
+  const int ns = ctx->kp_ns, nk = ctx->kp_nk;
+  // dV_k = V_H[v_k] + f_x v_k;  a_k = w dV_k
+  LRDM_CU(launch_spin_sum(v, io, K, 1, S.Ng, S.fft_real, fp64, st));
+  LRDM_CK(hartree(ctx, S, K, st));
+  LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[0].fx, K, 1, S.Ng, S.Ng, S.w, S.a,
+                            fp64, st));
+  // X_kappa = Psi_kappa^H diag(a_k) Psi_kappa
+  int pi = prof_begin(ctx, 1, st);
+  for (int q = 0; q < nk; ++q)
+    LRDM_CU(launch_kp_gemm1(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, S.a, S.Ng, K, ctx->kp_Xr[q],
+                            ctx->kp_Xi[q], ctx->kp_nsplit, st));
+  prof_end(ctx, pi, st);
+  // mu' from the BZ-averaged traceless condition
+  KpDmuArgs A{};
+  for (int q = 0; q < nk; ++q) {
+    A.Xr[q] = ctx->kp_Xr[q];
+    A.L[q] = ctx->kp_L[q];
+    A.kw[q] = ctx->kp_w[q];
+  }
+  A.nk = nk;
+  A.ns = ns;
+  A.K = K;
+  A.nsplit = ctx->kp_nsplit;
+  A.fp64 = fp64;
+  LRDM_CU(launch_kp_dmu(A, S.dmu, dmu_out, st));
+  // drho_k = g sum_kappa w_kappa diag(Psi L o (X - mu' I) Psi^H);  f_k = drho_k - v_k
+  LRDM_CU(cudaMemsetAsync(ctx->kp_drho, 0, (size_t)K * S.Ng * sizeof(double), st));
+  for (int q = 0; q < nk; ++q)
+    LRDM_CU(launch_kp_scale(fp64, ctx->kp_Xr[q], ctx->kp_Xi[q], ctx->kp_nsplit, K, ns, ctx->kp_L[q], S.dmu,
+                            ctx->kp_Yr[q], ctx->kp_Yi[q], st));
+  pi = prof_begin(ctx, 2, st);
+  for (int q = 0; q < nk; ++q)
+    LRDM_CU(launch_kp_gemm2(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, ctx->kp_Yr[q], ctx->kp_Yi[q], K,
+                            S.g * ctx->kp_w[q], ctx->kp_drho, st));
+  prof_end(ctx, pi, st);
+  LRDM_CU(launch_kp_finish(ctx->kp_drho, v, io, (long long)K * S.Ng, f_out, st));
+  count(ctx, 5 + 3 * nk);
+  S.last_K = K;
+  return LRDM_OK;
+}
 
 }  // extern "C"

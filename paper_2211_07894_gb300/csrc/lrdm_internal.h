@@ -113,6 +113,16 @@ struct lrdm_ctx {
   std::vector<int> prof_kind;        // 1 = GEMM1, 2 = GEMM2 per pair
   int prof_n = 0;
   long long launches = 0;            // library kernel launches while profiling
+  // Brillouin-zone-sampled system (lrdm_kp_create): one periodic system, nk
+  // complex subspaces sharing mu, the grid and the Poisson plans of sys[0]
+  bool kp = false;
+  int kp_nk = 0, kp_ns = 0, kp_nsplit = 1;
+  std::vector<double> kp_w;          // BZ weights
+  std::vector<void*> kp_pr, kp_pi;   // [nk] Psi planes [N_g][N_s] compute type
+  std::vector<double*> kp_eps, kp_occ, kp_L;
+  std::vector<void*> kp_Xr, kp_Xi;   // [nk] [nsplit][kmax][N_s][N_s]
+  std::vector<void*> kp_Yr, kp_Yi;   // [nk] [kmax][N_s][N_s] Loewner-scaled
+  double* kp_drho = nullptr;         // [kmax][N_g] FP64 accumulator
 };
 
 namespace lrdm {
@@ -130,6 +140,35 @@ cudaError_t launch_loewner(const double* eps, const double* occ, int ns, double 
 cudaError_t launch_to_io(const double* src, long long n, void* dst, int io_dtype, cudaStream_t st);
 // Lf[i][j] = (float) L[i][j] for i, j < ns, 0 in the padding
 cudaError_t launch_loewner_f32(const double* L, int ns, int ns_pad, float* Lf, cudaStream_t st);
+
+// ---------------- Brillouin-zone-sampled response (k_kpoint.cu) ----------------
+constexpr int KP_MAX = 32;           // k-points per context
+struct KpDmuArgs {
+  const void* Xr[KP_MAX];
+  const double* L[KP_MAX];
+  double kw[KP_MAX];
+  int nk, ns, K, nsplit, fp64;
+};
+// X_kappa (re, im) = Psi^H diag(a_k) Psi over nsplit grid-row ranges
+cudaError_t launch_kp_gemm1(int fp64, const void* pr, const void* pi, int ns, long long Ng,
+                            const void* a, long long a_stride, int K, void* Xr, void* Xi, int nsplit,
+                            cudaStream_t st);
+// mu'_k from the BZ-averaged traceless condition
+cudaError_t launch_kp_dmu(const KpDmuArgs& A, double* dmu, double* dmu_out, cudaStream_t st);
+// Y = c L o conj(X - mu' I), upper part
+cudaError_t launch_kp_scale(int fp64, const void* Xr, const void* Xi, int nsplit, int K, int ns,
+                            const double* L, const double* dmu, void* Yr, void* Yi, cudaStream_t st);
+// drho[k] += factor * Re diag-form of Y over Psi
+cudaError_t launch_kp_gemm2(int fp64, const void* pr, const void* pi, int ns, long long Ng,
+                            const void* Yr, const void* Yi, int K, double factor, double* drho,
+                            cudaStream_t st);
+cudaError_t launch_kp_finish(const double* drho, const void* v, int io, long long n, void* f,
+                             cudaStream_t st);
+cudaError_t launch_kp_density(int fp64, const void* pr, const void* pi, int ns, long long Ng,
+                              const double* occ, double gw, int first, double floor, double* rho,
+                              cudaStream_t st);
+cudaError_t launch_kp_copy(int fp64, const void* src, int io, int ld, long long Ng, int ns, void* dst,
+                           cudaStream_t st);
 
 // ---------------- element-wise / reduction kernels (k_elem.cu) ----------------
 // fft_real[k][r] = sum_s v[k][s][r]  (compute type = double if fp64 else float)

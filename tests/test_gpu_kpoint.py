@@ -1,0 +1,151 @@
+"""GPU parity of the Brillouin-zone-sampled response (lrdm_kp_create /
+lrdm_kp_gateaux) against oracle.gateaux_kpoints (§II.C closing paragraphs,
+Eq. tracelessCondition), through the C ABI.
+
+Sizes: N_s = 150 (three 64-wide tiles, the last one ragged), N_g = 12*11*10 =
+1320 (ragged against the 64-row blocks of the density contraction), nk = 3
+k-points with unequal weights, K = 3 of k_max = 4 directions.  FP64 must agree
+to 1e-10 (relative, per direction); FP32 (FP32 accumulation over row ranges of
+N_g products of unit-scale values, error ~ sqrt(N_g) 2^-24 relative per entry,
+with headroom) to 1e-4, the bound of the real FP32 path.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import per_direction_rel_err, rel_err
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+N = (12, 11, 10)
+NS, NK, NE, KT, K = 150, 3, 110.0, 0.01, 3
+TOL = {"fp64": 1e-10, "fp32": 1e-4}
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2211_07894_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def cfg():
+    return workloads.kpoint_system(70, N, NS, NK, NE, KT, K)
+
+
+def _oracle(cfg, psi):
+    ks = oracle.KpointSystem(n=cfg["n"], h=cfg["h"], psi=psi, eps=cfg["eps"], k_weights=cfg["k_weights"],
+                             rho=np.zeros(int(np.prod(cfg["n"]))), n_electrons=cfg["n_electrons"],
+                             kT=cfg["kT"], g=cfg["g"])
+    mu = oracle.solve_mu_kpoints(cfg["eps"], cfg["k_weights"], cfg["n_electrons"], cfg["kT"], cfg["g"])
+    ks.rho = oracle.density_kpoints(ks, mu, cfg["rho_floor"])
+    return ks, mu
+
+
+def _device(cfg, prec, pass_rho=None, k_max=4, nk=None):
+    from paper_2211_07894_gb300 import KpContext
+    dt = DT[prec]
+    nk = nk or len(cfg["psi"])
+    pr = [torch.as_tensor(np.ascontiguousarray(p.real), dtype=dt, device="cuda") for p in cfg["psi"][:nk]]
+    pi = [torch.as_tensor(np.ascontiguousarray(p.imag), dtype=dt, device="cuda") for p in cfg["psi"][:nk]]
+    eps = [torch.as_tensor(e, dtype=torch.float64, device="cuda") for e in cfg["eps"][:nk]]
+    rho = torch.as_tensor(pass_rho, dtype=dt, device="cuda") if pass_rho is not None else None
+    ctx = KpContext(cfg["n"], cfg["h"], pr, pi, eps, cfg["k_weights"][:nk], cfg["n_electrons"], cfg["kT"],
+                    g=cfg["g"], rho=rho, rho_floor=cfg["rho_floor"], prec=prec, io_dtype=dt, k_max=k_max)
+    psi_seen = [(a.double().cpu().numpy() + 1j * b.double().cpu().numpy()) for a, b in zip(pr, pi)]
+    return ctx, psi_seen
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_kpoint_gateaux_matches_oracle(lib, cfg, prec):
+    ctx, psi_seen = _device(cfg, prec)
+    ks, mu = _oracle(cfg, psi_seen)
+    assert abs(ctx.mu() - mu) < 1e-12
+    rho_d = ctx.density().double().cpu().numpy()
+    assert rel_err(rho_d, ks.rho) < (1e-13 if prec == "fp64" else 1e-6)
+    V = torch.as_tensor(cfg["V"], dtype=DT[prec], device="cuda")
+    F, dmu = ctx.gateaux(V)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    # the oracle on the density the device computed (FP32: its rounded copy)
+    ks.rho = rho_d
+    Vh = V.double().cpu().numpy()
+    ref = oracle.gateaux_kpoints(ks, Vh)
+    Fd = F.double().cpu().numpy()
+    err = per_direction_rel_err(Fd, ref["F"])
+    derr = per_direction_rel_err(Fd + Vh, ref["drho"])
+    dmu_d = dmu.cpu().numpy()
+    scale = max(float(np.max(np.abs(np.diagonal(X, axis1=1, axis2=2)))) for X in ref["X"])
+    print(f"k-point {prec}: f err {err:.2e}, drho err {derr:.2e}, "
+          f"dmu err {np.max(np.abs(dmu_d - ref['dmu'])):.2e}")
+    assert err < TOL[prec]
+    assert derr < TOL[prec]
+    assert np.max(np.abs(dmu_d - ref["dmu"])) <= TOL[prec] * scale
+
+
+def test_kpoint_given_density_single_point_and_fewer_directions(lib, cfg):
+    one = dict(cfg)
+    one["psi"] = cfg["psi"][:1]
+    one["eps"] = cfg["eps"][:1]
+    one["k_weights"] = np.array([1.0])
+    ks, mu = _oracle(one, one["psi"])
+    rho = ks.rho * 1.1
+    ctx, _ = _device(one, "fp64", pass_rho=rho)
+    assert rel_err(ctx.density().cpu().numpy(), rho) < 1e-15
+    V = torch.as_tensor(cfg["V"], dtype=torch.float64, device="cuda")
+    F, dmu = ctx.gateaux(V)
+    torch.cuda.synchronize()
+    ks.rho = rho
+    ref = oracle.gateaux_kpoints(ks, cfg["V"])
+    assert per_direction_rel_err(F.cpu().numpy(), ref["F"]) < 1e-10
+    F1, _ = ctx.gateaux(V[1:2].contiguous())
+    torch.cuda.synchronize()
+    assert rel_err(F1.cpu().numpy()[0], ref["F"][1]) < 1e-10
+    F0, _ = ctx.gateaux(V[:0].contiguous())
+    assert F0.shape[0] == 0
+    assert ctx.status() == 0
+
+
+def test_kpoint_least_squares_step(lib, cfg):
+    ctx, psi_seen = _device(cfg, "fp64")
+    ks, _ = _oracle(cfg, psi_seen)
+    V = torch.as_tensor(cfg["V"], dtype=torch.float64, device="cuda")
+    F, _ = ctx.gateaux(V)
+    R = torch.as_tensor(workloads.smooth_directions(N, cfg["h"], 1, 1, workloads.rng_for(70, 9))[0, 0],
+                        device="cuda").contiguous()
+    rho = torch.as_tensor(ks.rho, device="cuda").clone()
+    coef, srel = ctx.apply(R, V, F, 0.5, rho=rho)
+    torch.cuda.synchronize()
+    ref = oracle.gateaux_kpoints(ks, cfg["V"])
+    want = oracle.lrdm_apply(R.cpu().numpy()[None], cfg["V"][:, None], ref["F"][:, None], ks.w, 0.5,
+                             rho=ks.rho[None])
+    assert np.allclose(coef.cpu().numpy(), want["a"], rtol=1e-9, atol=1e-12)
+    assert abs(srel.item() - want["s_rel"]) < 1e-9
+    assert rel_err(rho.cpu().numpy(), want["rho_new"][0]) < 1e-10
+
+
+def test_kpoint_rejections(lib, cfg):
+    from paper_2211_07894_gb300 import LrdmError, binding
+    with pytest.raises(LrdmError) as e:
+        _device(cfg, "fp64", nk=2)                   # weights of 2 of the 3 points do not sum to 1
+    assert e.value.code == 1
+    with pytest.raises(LrdmError) as e:
+        from paper_2211_07894_gb300 import KpContext
+        p = torch.zeros((int(np.prod(N)), NS), dtype=torch.float32, device="cuda")
+        KpContext(N, cfg["h"], [p], [p], [torch.as_tensor(cfg["eps"][0], device="cuda")], [1.0], NE, KT,
+                  prec="bf16x3", io_dtype=torch.float32)
+    assert e.value.code == 9
+    ctx, _ = _device(cfg, "fp64")
+    V = torch.as_tensor(cfg["V"], dtype=torch.float64, device="cuda")
+    F = torch.empty_like(V)
+    # the real-subspace calls are refused for a k-point context
+    assert binding.lrdm_gateaux_batch(ctx.handle, [V.data_ptr()], [K], [F.data_ptr()], 0) == 9
+    assert binding.lrdm_get_projection(ctx.handle, 0, 0, 0, F.data_ptr()) == 9
+    with pytest.raises(LrdmError):
+        ctx.gateaux(torch.zeros((5, V.shape[1]), dtype=torch.float64, device="cuda"))   # K > k_max
+    assert ctx.status() == 0
