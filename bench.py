@@ -10,7 +10,11 @@ step and update (lrdm_apply), and the hand-written adjoint of the response
 map and of the eigenvalue / occupation inputs for one cotangent per direction
 (lrdm_backward).  The forward call alone (one CUDA-graph replay of
 lrdm_gateaux_batch) is timed separately and reported under "forward_only",
-with and without the Poisson (cuFFT) step.
+with and without the Poisson (cuFFT) step.  A periodic workload sampled at
+4 Brillouin-zone points (48^3 grid, N_s = 512 complex states per point, K = 8,
+FP32; lrdm_kp_gateaux) is timed after the main step and reported under
+"kpoint" with its own roofline and oracle baseline (--kpoint-only runs it
+alone).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|tf32|fp32|fp64]
   python bench.py --impl reference ...     (the FP64 CPU oracle, timed on the host)
@@ -63,6 +67,10 @@ def parse():
     p.add_argument("--ns", type=int, default=NS)
     p.add_argument("--fwd-reps", type=int, default=10,
                    help="graph replays of the forward call timed for forward_only")
+    p.add_argument("--no-kpoint", action="store_true",
+                   help="skip the Brillouin-zone-sampled (k-point) leg")
+    p.add_argument("--kpoint-only", action="store_true",
+                   help="run only the k-point leg and print its JSON")
     p.add_argument("--compare-fp64", action="store_true",
                    help="time the plain FP64 GPU form (torch, Psi X' materialised) and the "
                         "library's FP64 path on a 48^3 slice instead of the benchmark step")
@@ -203,6 +211,102 @@ def oracle_step(sysm, V, R):
     res = oracle.gateaux(sysm, V)
     oracle.lrdm_apply(R, V, res["F"], sysm.w, 0.5, rho=sysm.rho[0][None, :])
     oracle.backward(sysm, res["F"], res)
+
+
+# Brillouin-zone-sampled response (lrdm_kp_gateaux): a periodic workload of
+# nk k-points with complex subspaces, timed beside the main step.
+KP_GRID = (48, 48, 48)
+KP_NS, KP_NK, KP_K, KP_NE, KP_KT = 512, 4, 8, 800.0, 0.01
+KP_SAMPLE_GRID = (24, 24, 24)
+
+
+def kp_weights(nk):
+    raw = [1.0 + 2.0 * min(i, nk - 1 - i) for i in range(nk)]
+    return [x / sum(raw) for x in raw]
+
+
+def time_kpoint(torch, rank, reps=5, warmup=2):
+    """K = 8 real directions through lrdm_kp_gateaux (FP32) on a 48^3 grid
+    with 4 k-points of N_s = 512 complex states each; the projection kernel's
+    ALU roofline from the library's own event timing."""
+    import workloads
+    from paper_2211_07894_gb300 import KpContext
+    rng = workloads.rng_for(80, rank)
+    pr, pi = [], []
+    for q in range(KP_NK):
+        a, b = workloads.random_subspace_complex_torch(KP_GRID, H, KP_NS, 2211078940 + 80 + 10 * rank + q,
+                                                       "cuda")
+        pr.append(a)
+        pi.append(b)
+    eps = [torch.as_tensor(workloads.random_eigenvalues(KP_NS, rng) + 0.02 * q, device="cuda")
+           for q in range(KP_NK)]
+    ctx = KpContext(KP_GRID, H, pr, pi, eps, kp_weights(KP_NK), KP_NE, KP_KT, rho_floor=1e-3,
+                    prec="fp32", io_dtype=torch.float32, k_max=KP_K)
+    del pr, pi
+    V = torch.as_tensor(workloads.smooth_directions(KP_GRID, H, KP_K, 1, workloads.rng_for(80, 100 + rank))[:, 0],
+                        dtype=torch.float32, device="cuda").contiguous()
+    F = torch.empty_like(V)
+    dmu = torch.empty(KP_K, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        ctx.gateaux(V, out=F, dmu=dmu)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.gateaux(V, out=F, dmu=dmu)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read(reset=True)
+    ms = e0.elapsed_time(e1) / reps
+    if ctx.status() != 0:
+        raise RuntimeError("device status not ok after the k-point calls")
+    ctx.close()
+    ng = int(KP_GRID[0] * KP_GRID[1] * KP_GRID[2])
+    # one projection launch: one k-point, K directions, 8 real flops per
+    # (row, i <= j) complex product
+    alg = KP_K * 4.0 * ng * KP_NS * (KP_NS + 1)
+    n1 = max(prof["gemm1_launches"], 1) * KP_NK      # events bracket all k-points of a call
+    avg_s = prof["gemm1_ms"] / n1 / 1e3
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = alg / avg_s / 1e12
+    return {"workload": f"{KP_GRID[0]}^3 grid, {KP_NK} k-points x N_s={KP_NS} complex, K={KP_K}, FP32",
+            "value": KP_K / (ms / 1e3), "unit": "GD/s", "ms_per_call": ms, "reps": reps,
+            "gemm1_ms_per_call": prof["gemm1_ms"] / reps, "gemm2_ms_per_call": prof["gemm2_ms"] / reps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_kp_gemm1<float> (complex projection)",
+                         "avg_launch_ms": avg_s * 1e3, "alg_flop_per_launch": alg,
+                         "peak_source": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"}}
+
+
+def time_kpoint_oracle():
+    """The oracle's gateaux_kpoints on a bounded sample of the k-point
+    workload: the same 4 k-points x N_s = 512, one direction, a 24^3 grid (1/8
+    of the rows); both contractions scale linearly with the rows."""
+    import numpy as np
+    import oracle
+    import workloads
+    n = KP_SAMPLE_GRID
+    rng = workloads.rng_for(81, 0)
+    psi = [workloads.random_subspace_complex(n, H, KP_NS, rng) for _ in range(KP_NK)]
+    eps = [workloads.random_eigenvalues(KP_NS, rng) + 0.02 * q for q in range(KP_NK)]
+    kw = kp_weights(KP_NK)
+    ks = oracle.KpointSystem(n=n, h=H, psi=psi, eps=eps, k_weights=kw, rho=np.zeros(int(np.prod(n))),
+                             n_electrons=KP_NE, kT=KP_KT)
+    mu = oracle.solve_mu_kpoints(eps, kw, KP_NE, KP_KT, 2.0)
+    ks.rho = oracle.density_kpoints(ks, mu, 1e-3)
+    V = workloads.smooth_directions(n, H, 1, 1, workloads.rng_for(81, 1))[:, 0]
+    t0 = time.perf_counter()
+    oracle.gateaux_kpoints(ks, V)
+    dt = time.perf_counter() - t0
+    scale = float(np.prod(KP_GRID)) / float(np.prod(n))
+    return {"value": 1.0 / (dt * scale), "unit": "GD/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"oracle.gateaux_kpoints, K=1, {KP_NK} k-points x N_s={KP_NS}, grid {n[0]}^3 "
+                      f"(1/{int(scale)} of the {KP_GRID[0]}^3 rows); GD/s scaled by the row ratio"}
 
 
 def cpu_cores():
@@ -370,6 +474,14 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    if args.kpoint_only:
+        from paper_2211_07894_gb300 import build as _build
+        _build.build()
+        kp = time_kpoint(torch, rank)
+        if rank == 0 and not args.no_cpu_baseline:
+            kp["cpu_baseline"] = time_kpoint_oracle()
+        print(json.dumps(kp), flush=True)
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -561,10 +673,19 @@ def main():
                 "kernel": name, "avg_launch_ms": avg_s * 1e3, "launches": nl,
                 "alg_flop_per_launch": alg_flops, "peak_source": f"{peak_src}; {note}"}
 
+    kpoint = None
+    if not args.no_kpoint:
+        ctx.close()
+        F = fbar = bwd_out = None
+        torch.cuda.empty_cache()
+        kpoint = time_kpoint(torch, rank)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            kpoint["cpu_baseline"] = time_kpoint_oracle()
+
     fp64_plain = None
     if not args.no_fp64_plain:
         ctx.close()
-        del F, fbar, bwd_out
+        F = fbar = bwd_out = None
         torch.cuda.empty_cache()
         res, sample = time_fp64_plain(torch)
         gds, sec = res["plain-fp64-gpu"]
@@ -593,6 +714,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],
                 "forward_only": forward_only, "forward_k1": forward_k1, "fp64_plain": fp64_plain,
+                "kpoint": kpoint,
                 "launch_shape": tuning,
                 "breakdown_ms": {"gemm1_per_step": prof["gemm1_ms"] / steps,
                                  "gemm2_per_step": prof["gemm2_ms"] / steps,

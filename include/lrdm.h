@@ -326,8 +326,11 @@ void lrdm_lrdma_destroy(lrdm_lrdma* a);
  *   X_kappa = Psi_kappa^H diag(w dV_k) Psi_kappa,
  *   sum_kappa w_kappa sum_i L_kappa,ii (X_kappa,ii - mu') = 0,
  *   drho_k = g sum_kappa w_kappa diag(Psi_kappa L_kappa o (X_kappa - mu' I) Psi_kappa^H).
- * Spin-restricted; FP64 or FP32 on the CUDA cores (other precisions:
- * LRDM_ERR_UNSUPPORTED).  A k-point context serves lrdm_kp_gateaux,
+ * Spin-restricted.  FP64 / FP32 run complex contractions on the CUDA cores;
+ * TF32 / BF16X3 run the real tensor-core contractions on the stacked operand
+ * C = [Re Psi, Im Psi] (N_g x 2 N_s): C^T diag(a) C holds Re X and Im X, and
+ * the density is diag(C M C^T) with M = [[Re G, Im G], [-Im G, Re G]],
+ * G = L o (X - mu' I).  A k-point context serves lrdm_kp_gateaux,
  * lrdm_apply (sys 0, n = N_g), lrdm_get_mu, lrdm_get_density,
  * lrdm_status_query, lrdm_profile_* and lrdm_destroy; lrdm_gateaux_batch,
  * lrdm_backward, lrdm_krylov_step, lrdm_get_projection and lrdm_lrdma_step
@@ -358,8 +361,8 @@ typedef struct lrdm_kpoint_system {
  * not given, f_x and the Poisson plans.  Synchronises the stream.
  * Errors: INVALID_ARG (null pointers, nk outside 1..32, weights not positive
  * or not summing to 1, kT <= 0, bad options), MU_NOT_CONVERGED (N_e outside
- * what the states can hold), UNSUPPORTED (precision other than FP64 / FP32),
- * OOM, CUDA. */
+ * what the states can hold), UNSUPPORTED (tensor-core precision on a device
+ * without sm_103a tensor cores), OOM, CUDA. */
 lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const lrdm_options* opt,
                            void* stream);
 /* f_k = drho_k - v_k for K real directions v ([K][N_g] io dtype, device);

@@ -15,6 +15,15 @@
 //   twice the real part of one term);
 //   drho_k(r) += g w_kappa Re sum_j T_j(r) psi_j(r), T_j = sum_i conj(psi_i) X''_ij
 //   (T never leaves registers), accumulated over k-points in FP64.
+//
+// Tensor-core modes reuse the real contractions on the stacked operand
+// C = [A B] (N_g x 2 N_s): P = C^T diag(a) C holds Re X = P11 + P22 and
+// Im X = P12 - P21, and the density diag(Psi Gamma Psi^H) equals
+// diag(C M C^T) with the symmetric M = [[Re G, Im G], [-Im G, Re G]]
+// (G = Gamma), whose c-weighted upper triangle k_kp_scale_tc writes in the
+// layout of the real GEMM2's X'' operand.
+#include <cuda_bf16.h>
+
 #include "lrdm_internal.h"
 
 namespace lrdm {
@@ -22,6 +31,13 @@ namespace {
 
 constexpr int T = 64;
 constexpr int BK = 16;
+
+// round to the TF32 grid (nearest, ties away), as the TF32 GEMM2 operand expects
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+  return __uint_as_float(t);
+}
 
 // upper-triangular tile p -> (I, J), I <= J, column-major over J
 __device__ __forceinline__ void kp_tri(int p, int& I, int& J) {
@@ -125,14 +141,19 @@ __global__ void __launch_bounds__(256) k_kp_dmu(KpDmuArgs A, double* __restrict_
                                                 double* __restrict__ dmu_out) {
   const int k = blockIdx.x;
   double num = 0.0, den = 0.0;
-  const long long mat = (long long)A.ns * A.ns;
+  const long long mat = (long long)A.ld * A.ld;
   for (int kp = 0; kp < A.nk; ++kp) {
     const double wk = A.kw[kp];
     for (int i = threadIdx.x; i < A.ns; i += blockDim.x) {
       double x = 0.0;
       for (int p = 0; p < A.nsplit; ++p) {
-        const long long o = ((long long)p * A.K + k) * mat + (long long)i * A.ns + i;
+        const long long o = ((long long)p * A.K + k) * mat + (long long)i * A.ld + i;
         x += A.fp64 ? static_cast<const double*>(A.Xr[kp])[o] : (double)static_cast<const float*>(A.Xr[kp])[o];
+        if (A.stacked) {
+          const long long o2 = o + (long long)A.ns * A.ld + A.ns;
+          x += A.fp64 ? static_cast<const double*>(A.Xr[kp])[o2]
+                      : (double)static_cast<const float*>(A.Xr[kp])[o2];
+        }
       }
       const double l = A.L[kp][(long long)i * A.ns + i];
       num += wk * l * x;
@@ -295,9 +316,10 @@ __global__ void k_kp_finish(const double* __restrict__ drho, const void* __restr
   }
 }
 
-// rho = (first ? floor : rho) + g w sum_i f_i (A_i^2 + B_i^2), one warp per grid point
+// rho = (first ? floor : rho) + g w sum_i f_i (A_i^2 + B_i^2), one warp per grid
+// point; A, B rows of leading dimension ld
 template <typename Tc>
-__global__ void k_kp_density(const Tc* __restrict__ pr, const Tc* __restrict__ pi, int ns,
+__global__ void k_kp_density(const Tc* __restrict__ pr, const Tc* __restrict__ pi, int ns, int ld,
                              long long Ng, const double* __restrict__ occ, double gw, int first,
                              double floor, double* __restrict__ rho) {
   const int lane = threadIdx.x & 31;
@@ -306,7 +328,7 @@ __global__ void k_kp_density(const Tc* __restrict__ pr, const Tc* __restrict__ p
   for (long long r = warp; r < Ng; r += nwarps) {
     double acc = 0.0;
     for (int i = lane; i < ns; i += 32) {
-      const double a = pr[r * ns + i], b = pi[r * ns + i];
+      const double a = pr[r * ld + i], b = pi[r * ld + i];
       acc += occ[i] * (a * a + b * b);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -318,7 +340,7 @@ __global__ void k_kp_density(const Tc* __restrict__ pr, const Tc* __restrict__ p
 // compute type, [N_g][N_s]
 template <typename Tc>
 __global__ void k_kp_copy(const void* __restrict__ src, int io, int ld, long long Ng, int ns,
-                          Tc* __restrict__ dst) {
+                          Tc* __restrict__ dst, int ldd, int col0) {
   const long long tot = Ng * ns;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
@@ -326,7 +348,82 @@ __global__ void k_kp_copy(const void* __restrict__ src, int io, int ld, long lon
     const int i = (int)(e - r * ns);
     const double x = io == LRDM_DTYPE_F64 ? static_cast<const double*>(src)[r * ld + i]
                                           : (double)static_cast<const float*>(src)[r * ld + i];
-    dst[e] = (Tc)x;
+    dst[r * ldd + col0 + i] = (Tc)x;
+  }
+}
+
+// M'' at [k][j][i] (i fastest) for i <= j < 2 ns: c_ij M_ij with c = 2 off the
+// diagonal; zero elsewhere (padding included).  One thread per four columns.
+__global__ void k_kp_scale_tc(const float* __restrict__ P, int nsplit, int K, int ns, int ld,
+                              const double* __restrict__ L, const double* __restrict__ dmu, int layout,
+                              void* __restrict__ out, __nv_bfloat16* __restrict__ out_lo) {
+  const int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y;
+  const int k = blockIdx.z;
+  if (c0 >= ld) return;
+  const long long mat = (long long)ld * ld;
+  const long long tot = (long long)K * mat;
+  const float* Pk = P + (long long)k * mat;
+  auto Pat = [&](int r, int c) {               // P[r][c] summed over the row ranges
+    double x = 0.0;
+    for (int p = 0; p < nsplit; ++p) x += (double)Pk[(long long)p * tot + (long long)r * ld + c];
+    return x;
+  };
+  const int n2 = 2 * ns;
+  float v[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int i = c0 + e;
+    double m = 0.0;
+    if (i <= j && j < n2) {
+      const int a = i < ns ? i : i - ns, b = j < ns ? j : j - ns;
+      const double l = L[(long long)a * ns + b];
+      if ((i < ns) == (j < ns)) {              // diagonal blocks: Re Gamma
+        const double xr = Pat(a, b) + Pat(ns + a, ns + b);
+        m = l * (xr - (a == b ? dmu[k] : 0.0));
+      } else {                                 // i in block 0, j in block 1: Im Gamma_ab
+        const double xi = Pat(a, ns + b) - Pat(ns + a, b);
+        m = l * xi;
+      }
+      if (i < j) m *= 2.0;
+    }
+    v[e] = (float)m;
+  }
+  const long long o = ((long long)k * ld + j) * ld + c0;
+  if (layout == 1) {
+    float4 t;
+    t.x = tf32_rna(v[0]);
+    t.y = tf32_rna(v[1]);
+    t.z = tf32_rna(v[2]);
+    t.w = tf32_rna(v[3]);
+    *reinterpret_cast<float4*>(static_cast<float*>(out) + o) = t;
+  } else {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[2], v[3]);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[0] - f01.x, v[1] - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[2] - f23.x, v[3] - f23.y);
+    uint2 hw, lw;
+    hw.x = *reinterpret_cast<const uint32_t*>(&h01);
+    hw.y = *reinterpret_cast<const uint32_t*>(&h23);
+    lw.x = *reinterpret_cast<const uint32_t*>(&l01);
+    lw.y = *reinterpret_cast<const uint32_t*>(&l23);
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out) + o) = hw;
+    *reinterpret_cast<uint2*>(out_lo + o) = lw;
+  }
+}
+
+// f = sum_kappa part_kappa - v, FP64 sum of the FP32 contributions
+__global__ void k_kp_sum(KpSumArgs A, const void* __restrict__ v, int io, long long n,
+                         void* __restrict__ f) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int q = 0; q < A.nk; ++q) d += (double)A.part[q][e];
+    if (io == LRDM_DTYPE_F64)
+      static_cast<double*>(f)[e] = d - static_cast<const double*>(v)[e];
+    else
+      static_cast<float*>(f)[e] = (float)(d - (double)static_cast<const float*>(v)[e]);
   }
 }
 
@@ -401,24 +498,40 @@ cudaError_t launch_kp_finish(const double* drho, const void* v, int io, long lon
   return cudaGetLastError();
 }
 
-cudaError_t launch_kp_density(int fp64, const void* pr, const void* pi, int ns, long long Ng,
+cudaError_t launch_kp_density(int fp64, const void* pr, const void* pi, int ns, int ld, long long Ng,
                               const double* occ, double gw, int first, double floor, double* rho,
                               cudaStream_t st) {
   const unsigned g = kp_grid(Ng * 32, 256);
   if (fp64)
     k_kp_density<double><<<g, 256, 0, st>>>(static_cast<const double*>(pr), static_cast<const double*>(pi),
-                                            ns, Ng, occ, gw, first, floor, rho);
+                                            ns, ld, Ng, occ, gw, first, floor, rho);
   else
     k_kp_density<float><<<g, 256, 0, st>>>(static_cast<const float*>(pr), static_cast<const float*>(pi),
-                                           ns, Ng, occ, gw, first, floor, rho);
+                                           ns, ld, Ng, occ, gw, first, floor, rho);
   return cudaGetLastError();
 }
 
 cudaError_t launch_kp_copy(int fp64, const void* src, int io, int ld, long long Ng, int ns, void* dst,
-                           cudaStream_t st) {
+                           int ldd, int col0, cudaStream_t st) {
   const unsigned g = kp_grid(Ng * ns, 256);
-  if (fp64) k_kp_copy<double><<<g, 256, 0, st>>>(src, io, ld, Ng, ns, static_cast<double*>(dst));
-  else k_kp_copy<float><<<g, 256, 0, st>>>(src, io, ld, Ng, ns, static_cast<float*>(dst));
+  if (fp64) k_kp_copy<double><<<g, 256, 0, st>>>(src, io, ld, Ng, ns, static_cast<double*>(dst), ldd, col0);
+  else k_kp_copy<float><<<g, 256, 0, st>>>(src, io, ld, Ng, ns, static_cast<float*>(dst), ldd, col0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kp_scale_tc(const float* P, int nsplit, int K, int ns, int ld, const double* L,
+                               const double* dmu, int layout, void* out, void* out_lo, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  dim3 grid((unsigned)((ld / 4 + 127) / 128), (unsigned)ld, (unsigned)K);
+  k_kp_scale_tc<<<grid, 128, 0, st>>>(P, nsplit, K, ns, ld, L, dmu, layout, out,
+                                      static_cast<__nv_bfloat16*>(out_lo));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kp_sum(const KpSumArgs& A, const void* v, int io, long long n, void* f,
+                          cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_kp_sum<<<kp_grid(n, 256), 256, 0, st>>>(A, v, io, n, f);
   return cudaGetLastError();
 }
 

@@ -1342,7 +1342,9 @@ lrdm_status solve_mu_kp_host(const std::vector<std::vector<double>>& eps, const 
 
 lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t st) {
   const lrdm_options& o = ctx->opt;
-  const int fp64 = o.prec == LRDM_FP64;
+  const int prec = o.prec;
+  const int fp64 = prec == LRDM_FP64;
+  const bool tc = is_tc(prec);
   const size_t csz = fp64 ? sizeof(double) : sizeof(float);
   SysState& S = ctx->sys[0];
   for (int d = 0; d < 3; ++d) {
@@ -1350,7 +1352,7 @@ lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t s
     S.h[d] = in.h[d];
   }
   S.Ng = (long long)in.n[0] * in.n[1] * in.n[2];
-  S.Ng_pad = S.Ng;
+  S.Ng_pad = tc ? (S.Ng + TC_PAD_GRID - 1) / TC_PAD_GRID * TC_PAD_GRID : S.Ng;
   S.nspin = 1;
   S.kmax = in.k_max > 0 ? in.k_max : o.k_max;
   S.w = in.h[0] * in.h[1] * in.h[2];
@@ -1366,14 +1368,18 @@ lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t s
   for (int q = 0; q < nk; ++q)
     LRDM_CU(cudaMemcpy(eps[q].data(), in.eps[q], ns * sizeof(double), cudaMemcpyDeviceToHost));
   LRDM_CK(solve_mu_kp_host(eps, ctx->kp_w, S.ne, S.kT, S.g, &S.mu));
-  // row ranges of the projection: about two blocks per SM at k_max directions
-  const int nt = (ns + 63) / 64;
-  const long long blocks = (long long)nt * (nt + 1) / 2 * S.kmax;
-  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
-  long long split = (2LL * sms + blocks - 1) / blocks;
-  if (split > S.Ng / 256) split = S.Ng / 256;
-  if (split > 64) split = 64;
-  ctx->kp_nsplit = (int)(split < 1 ? 1 : split);
+  // CUDA cores: row ranges of the projection, about two blocks per SM at
+  // k_max directions; tensor cores: the whole grid per tile
+  ctx->kp_nsplit = 1;
+  if (!tc) {
+    const int nt = (ns + 63) / 64;
+    const long long blocks = (long long)nt * (nt + 1) / 2 * S.kmax;
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+    long long split = (2LL * sms + blocks - 1) / blocks;
+    if (split > S.Ng / 256) split = S.Ng / 256;
+    if (split > 64) split = 64;
+    ctx->kp_nsplit = (int)(split < 1 ? 1 : split);
+  }
   const size_t npsi = (size_t)S.Ng * ns, mat = (size_t)ns * ns;
   ctx->kp_pr.assign(nk, nullptr);
   ctx->kp_pi.assign(nk, nullptr);
@@ -1384,38 +1390,97 @@ lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t s
   ctx->kp_Xi.assign(nk, nullptr);
   ctx->kp_Yr.assign(nk, nullptr);
   ctx->kp_Yi.assign(nk, nullptr);
+  if (tc) {
+    ctx->kp_ch.assign(nk, Channel());
+    ctx->kp_pid.assign(nk, -1);
+    ctx->kp_out.assign(nk, nullptr);
+  }
   Channel& ch = S.ch[0];
   ch.ns = ns;
   LRDM_CK(dalloc(ctx, &ch.rho, S.Ng, false));
   const size_t xc = (size_t)ctx->kp_nsplit * S.kmax * mat;
-  for (int q = 0; q < nk; ++q) {
-    for (int i = 0; i < ns; ++i) occ[q][i] = fermi_host((eps[q][i] - S.mu) / S.kT);
-    LRDM_CK(dalloc(ctx, &ctx->kp_eps[q], ns, false));
-    LRDM_CK(dalloc(ctx, &ctx->kp_occ[q], ns, false));
-    LRDM_CU(cudaMemcpyAsync(ctx->kp_eps[q], eps[q].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
-    LRDM_CU(cudaMemcpyAsync(ctx->kp_occ[q], occ[q].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
-    LRDM_CK(dalloc(ctx, &ctx->kp_L[q], mat, false));
-    LRDM_CU(launch_loewner(ctx->kp_eps[q], ctx->kp_occ[q], ns, S.mu, S.kT, 0, o.degen_tol, 0,
-                           ctx->kp_L[q], st));
-    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_pr[q]), npsi * csz, false));
-    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_pi[q]), npsi * csz, false));
-    LRDM_CU(launch_kp_copy(fp64, in.psi_re[q], o.io_dtype, in.ld_psi, S.Ng, ns, ctx->kp_pr[q], st));
-    LRDM_CU(launch_kp_copy(fp64, in.psi_im[q], o.io_dtype, in.ld_psi, S.Ng, ns, ctx->kp_pi[q], st));
-    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Xr[q]), xc * csz));
-    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Xi[q]), xc * csz));
-    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Yr[q]), (size_t)S.kmax * mat * csz));
-    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Yi[q]), (size_t)S.kmax * mat * csz));
-    if (!in.rho)
-      LRDM_CU(launch_kp_density(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, ctx->kp_occ[q],
-                                S.g * ctx->kp_w[q], q == 0, in.rho_floor, ch.rho, st));
+  const int io = o.io_dtype;
+  const size_t isz = io == LRDM_DTYPE_F64 ? sizeof(double) : sizeof(float);
+  void* stack = nullptr;                       // tensor cores: [N_g][2 N_s] io dtype, set-up only
+  if (tc && cudaMalloc(&stack, npsi * 2 * isz) != cudaSuccess) return LRDM_ERR_OOM;
+  lrdm_status rc = LRDM_OK;
+  for (int q = 0; q < nk && rc == LRDM_OK; ++q) {
+    rc = [&]() -> lrdm_status {
+      for (int i = 0; i < ns; ++i) occ[q][i] = fermi_host((eps[q][i] - S.mu) / S.kT);
+      LRDM_CK(dalloc(ctx, &ctx->kp_eps[q], ns, false));
+      LRDM_CK(dalloc(ctx, &ctx->kp_occ[q], ns, false));
+      LRDM_CU(cudaMemcpyAsync(ctx->kp_eps[q], eps[q].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+      LRDM_CU(cudaMemcpyAsync(ctx->kp_occ[q], occ[q].data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+      LRDM_CK(dalloc(ctx, &ctx->kp_L[q], mat, false));
+      LRDM_CU(launch_loewner(ctx->kp_eps[q], ctx->kp_occ[q], ns, S.mu, S.kT, 0, o.degen_tol, 0,
+                             ctx->kp_L[q], st));
+      if (!tc) {
+        LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_pr[q]), npsi * csz, false));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_pi[q]), npsi * csz, false));
+        LRDM_CU(launch_kp_copy(fp64, in.psi_re[q], io, in.ld_psi, S.Ng, ns, ctx->kp_pr[q], ns, 0, st));
+        LRDM_CU(launch_kp_copy(fp64, in.psi_im[q], io, in.ld_psi, S.Ng, ns, ctx->kp_pi[q], ns, 0, st));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Xr[q]), xc * csz));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Xi[q]), xc * csz));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Yr[q]), (size_t)S.kmax * mat * csz));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->kp_Yi[q]), (size_t)S.kmax * mat * csz));
+        if (!in.rho)
+          LRDM_CU(launch_kp_density(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, ns, S.Ng, ctx->kp_occ[q],
+                                    S.g * ctx->kp_w[q], q == 0, in.rho_floor, ch.rho, st));
+        return LRDM_OK;
+      }
+      // stacked operand C = [Re Psi, Im Psi] in the layouts of the real contractions
+      Channel& c = ctx->kp_ch[q];
+      c.ns = 2 * ns;
+      c.ns_pad = (2 * ns + TC_PAD_STATES - 1) / TC_PAD_STATES * TC_PAD_STATES;
+      const int dio = io == LRDM_DTYPE_F64;
+      LRDM_CU(launch_kp_copy(dio, in.psi_re[q], io, in.ld_psi, S.Ng, ns, stack, 2 * ns, 0, st));
+      LRDM_CU(launch_kp_copy(dio, in.psi_im[q], io, in.ld_psi, S.Ng, ns, stack, 2 * ns, ns, st));
+      if (!in.rho)
+        LRDM_CU(launch_kp_density(dio, stack, static_cast<const char*>(stack) + ns * isz, ns, 2 * ns, S.Ng,
+                                  ctx->kp_occ[q], S.g * ctx->kp_w[q], q == 0, in.rho_floor, ch.rho, st));
+      const size_t npad = (size_t)S.Ng_pad * c.ns_pad;
+      const size_t ld2 = (size_t)c.ns_pad * c.ns_pad;
+      if (prec == LRDM_TF32) {
+        LRDM_CK(dalloc(ctx, &c.psiR32, npad, false));
+        LRDM_CK(dalloc(ctx, &c.psiT32, npad, false));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&c.Xpp), (size_t)S.kmax * ld2 * sizeof(float)));
+      } else {
+        LRDM_CK(dalloc(ctx, &c.psiR_hi, npad, false));
+        LRDM_CK(dalloc(ctx, &c.psiR_lo, npad, false));
+        LRDM_CK(dalloc(ctx, &c.psiT_hi, npad, false));
+        LRDM_CK(dalloc(ctx, &c.psiT_lo, npad, false));
+        LRDM_CK(dalloc(ctx, &c.psiTf, npad, false));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<__nv_bfloat16**>(&c.Xpp), (size_t)S.kmax * ld2));
+        LRDM_CK(dalloc(ctx, reinterpret_cast<__nv_bfloat16**>(&c.Xpp_lo), (size_t)S.kmax * ld2));
+      }
+      LRDM_CU(launch_convert_psi(stack, io, 2 * ns, S.Ng, 2 * ns, c, prec, S.Ng_pad, st));
+      LRDM_CU(cudaStreamSynchronize(st));      // the stacked copy is reused for the next point
+      LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&c.Xpart), (size_t)S.kmax * ld2 * sizeof(float)));
+      LRDM_CK(dalloc(ctx, &ctx->kp_out[q], (size_t)S.kmax * S.Ng));
+      return LRDM_OK;
+    }();
   }
-  if (in.rho) LRDM_CU(launch_copy_rho(in.rho, o.io_dtype, S.Ng, ch.rho, st));
+  if (stack) cudaFree(stack);
+  LRDM_CK(rc);
+  if (in.rho) LRDM_CU(launch_copy_rho(in.rho, io, S.Ng, ch.rho, st));
   LRDM_CK(dalloc(ctx, &ch.fx, S.Ng, false));
   LRDM_CU(launch_fx(ch.rho, S.Ng, 0, ch.fx, st));
-  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.a), (size_t)S.kmax * S.Ng * csz));
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.a), (size_t)S.kmax * S.Ng_pad * csz));
   LRDM_CK(dalloc(ctx, &S.dmu, S.kmax));
-  LRDM_CK(dalloc(ctx, &ctx->kp_drho, (size_t)S.kmax * S.Ng));
+  if (!tc) LRDM_CK(dalloc(ctx, &ctx->kp_drho, (size_t)S.kmax * S.Ng));
   LRDM_CK(setup_poisson(ctx, S, st));
+  if (tc) {
+    for (int q = 0; q < nk; ++q) {
+      TcProblem pr;
+      if (!build_tc_problem(prec, ctx->kp_ch[q], S, 0, pr)) return LRDM_ERR_CUDA;
+      ctx->kp_pid[q] = (int)ctx->tc_host.size();
+      ctx->tc_host.push_back(pr);
+    }
+    LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ctx->tc_dev), ctx->tc_host.size() * sizeof(TcProblem), false));
+    LRDM_CU(cudaMemcpy(ctx->tc_dev, ctx->tc_host.data(), ctx->tc_host.size() * sizeof(TcProblem),
+                       cudaMemcpyHostToDevice));
+    ctx->tc_entries.reserve(nk);
+  }
   LRDM_CU(cudaStreamSynchronize(st));   // the host eps / occ vectors end here
   return LRDM_OK;
 }
@@ -1444,10 +1509,11 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
   lrdm_options o;
   if (opt) o = *opt;
   else lrdm_default_options(&o);
-  if (o.prec != LRDM_FP64 && o.prec != LRDM_FP32) return LRDM_ERR_UNSUPPORTED;
+  if (o.prec < LRDM_FP64 || o.prec > LRDM_BF16X3) return LRDM_ERR_INVALID_ARG;
   if (o.io_dtype != LRDM_DTYPE_F64 && o.io_dtype != LRDM_DTYPE_F32) return LRDM_ERR_INVALID_ARG;
   if (o.k_max < 1 || o.k_max > KMAX_LIMIT || sys->k_max < 0 || sys->k_max > KMAX_LIMIT)
     return LRDM_ERR_INVALID_ARG;
+  if (is_tc(o.prec) && !tc_supported()) return LRDM_ERR_UNSUPPORTED;
   if (!(o.degen_tol >= 0.0) || (o.poisson_symbol != 0 && o.poisson_symbol != 1)) return LRDM_ERR_INVALID_ARG;
   lrdm_ctx* ctx = new (std::nothrow) lrdm_ctx();
   if (!ctx) return LRDM_ERR_OOM;
@@ -1491,24 +1557,41 @@ lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, do
   }
   if (!v || !f_out) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int fp64 = ctx->opt.prec == LRDM_FP64;
+  const int prec = ctx->opt.prec;
+  const int fp64 = prec == LRDM_FP64;
+  const bool tc = is_tc(prec);
   const int io = ctx->opt.io_dtype;
   const int ns = ctx->kp_ns, nk = ctx->kp_nk;
-  // dV_k = V_H[v_k] + f_x v_k;  a_k = w dV_k
+  // dV_k = V_H[v_k] + f_x v_k;  a_k = w dV_k (zero in the grid padding)
   LRDM_CU(launch_spin_sum(v, io, K, 1, S.Ng, S.fft_real, fp64, st));
   LRDM_CK(hartree(ctx, S, K, st));
-  LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[0].fx, K, 1, S.Ng, S.Ng, S.w, S.a,
+  LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[0].fx, K, 1, S.Ng, S.Ng_pad, S.w, S.a,
                             fp64, st));
-  // X_kappa = Psi_kappa^H diag(a_k) Psi_kappa
-  int pi = prof_begin(ctx, 1, st);
-  for (int q = 0; q < nk; ++q)
-    LRDM_CU(launch_kp_gemm1(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, S.a, S.Ng, K, ctx->kp_Xr[q],
-                            ctx->kp_Xi[q], ctx->kp_nsplit, st));
-  prof_end(ctx, pi, st);
+  // X_kappa = Psi_kappa^H diag(a_k) Psi_kappa (tensor cores: the stacked Gram P_kappa)
+  if (tc) {
+    ctx->tc_entries.clear();
+    for (int q = 0; q < nk; ++q) {
+      TcEntry x;
+      x.dev_base = ctx->tc_dev;
+      x.pid = ctx->kp_pid[q];
+      x.host = &ctx->tc_host[x.pid];
+      x.K = K;
+      x.X = ctx->kp_ch[q].Xpart;
+      ctx->tc_entries.push_back(x);
+    }
+    LRDM_CK(tc_group(ctx, 1, 0, st));
+  } else {
+    int pi = prof_begin(ctx, 1, st);
+    for (int q = 0; q < nk; ++q)
+      LRDM_CU(launch_kp_gemm1(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, S.a, S.Ng, K, ctx->kp_Xr[q],
+                              ctx->kp_Xi[q], ctx->kp_nsplit, st));
+    prof_end(ctx, pi, st);
+    count(ctx, nk);
+  }
   // mu' from the BZ-averaged traceless condition
   KpDmuArgs A{};
   for (int q = 0; q < nk; ++q) {
-    A.Xr[q] = ctx->kp_Xr[q];
+    A.Xr[q] = tc ? ctx->kp_ch[q].Xpart : ctx->kp_Xr[q];
     A.L[q] = ctx->kp_L[q];
     A.kw[q] = ctx->kp_w[q];
   }
@@ -1517,19 +1600,49 @@ lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, do
   A.K = K;
   A.nsplit = ctx->kp_nsplit;
   A.fp64 = fp64;
+  A.ld = tc ? ctx->kp_ch[0].ns_pad : ns;
+  A.stacked = tc ? 1 : 0;
   LRDM_CU(launch_kp_dmu(A, S.dmu, dmu_out, st));
+  count(ctx, 1);
   // drho_k = g sum_kappa w_kappa diag(Psi L o (X - mu' I) Psi^H);  f_k = drho_k - v_k
-  LRDM_CU(cudaMemsetAsync(ctx->kp_drho, 0, (size_t)K * S.Ng * sizeof(double), st));
-  for (int q = 0; q < nk; ++q)
-    LRDM_CU(launch_kp_scale(fp64, ctx->kp_Xr[q], ctx->kp_Xi[q], ctx->kp_nsplit, K, ns, ctx->kp_L[q], S.dmu,
-                            ctx->kp_Yr[q], ctx->kp_Yi[q], st));
-  pi = prof_begin(ctx, 2, st);
-  for (int q = 0; q < nk; ++q)
-    LRDM_CU(launch_kp_gemm2(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, ctx->kp_Yr[q], ctx->kp_Yi[q], K,
-                            S.g * ctx->kp_w[q], ctx->kp_drho, st));
-  prof_end(ctx, pi, st);
-  LRDM_CU(launch_kp_finish(ctx->kp_drho, v, io, (long long)K * S.Ng, f_out, st));
-  count(ctx, 5 + 3 * nk);
+  if (tc) {
+    const int layout = prec == LRDM_BF16X3 ? 2 : 1;
+    ctx->tc_entries.clear();
+    for (int q = 0; q < nk; ++q) {
+      const Channel& c = ctx->kp_ch[q];
+      LRDM_CU(launch_kp_scale_tc(static_cast<const float*>(c.Xpart), 1, K, ns, c.ns_pad, ctx->kp_L[q], S.dmu,
+                                 layout, c.Xpp, c.Xpp_lo, st));
+      TcEntry x;
+      x.dev_base = ctx->tc_dev;
+      x.pid = ctx->kp_pid[q];
+      x.host = &ctx->tc_host[x.pid];
+      x.K = K;
+      x.factor = S.g * ctx->kp_w[q];
+      x.out = ctx->kp_out[q];
+      x.out_stride = S.Ng;
+      ctx->tc_entries.push_back(x);
+    }
+    count(ctx, nk);
+    LRDM_CK(tc_group(ctx, 2, 0, st));
+    KpSumArgs B{};
+    for (int q = 0; q < nk; ++q) B.part[q] = ctx->kp_out[q];
+    B.nk = nk;
+    LRDM_CU(launch_kp_sum(B, v, io, (long long)K * S.Ng, f_out, st));
+    count(ctx, 1);
+  } else {
+    LRDM_CU(cudaMemsetAsync(ctx->kp_drho, 0, (size_t)K * S.Ng * sizeof(double), st));
+    for (int q = 0; q < nk; ++q)
+      LRDM_CU(launch_kp_scale(fp64, ctx->kp_Xr[q], ctx->kp_Xi[q], ctx->kp_nsplit, K, ns, ctx->kp_L[q], S.dmu,
+                              ctx->kp_Yr[q], ctx->kp_Yi[q], st));
+    int pi = prof_begin(ctx, 2, st);
+    for (int q = 0; q < nk; ++q)
+      LRDM_CU(launch_kp_gemm2(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, ctx->kp_Yr[q], ctx->kp_Yi[q], K,
+                              S.g * ctx->kp_w[q], ctx->kp_drho, st));
+    prof_end(ctx, pi, st);
+    LRDM_CU(launch_kp_finish(ctx->kp_drho, v, io, (long long)K * S.Ng, f_out, st));
+    count(ctx, 2 * nk + 1);
+  }
+  count(ctx, 3);
   S.last_K = K;
   return LRDM_OK;
 }

@@ -123,6 +123,12 @@ struct lrdm_ctx {
   std::vector<void*> kp_Xr, kp_Xi;   // [nk] [nsplit][kmax][N_s][N_s]
   std::vector<void*> kp_Yr, kp_Yi;   // [nk] [kmax][N_s][N_s] Loewner-scaled
   double* kp_drho = nullptr;         // [kmax][N_g] FP64 accumulator
+  // tensor-core modes: per k-point the stacked real operand C = [Re Psi, Im Psi]
+  // (N_g x 2 N_s) as one channel of the real contractions, its problem index
+  // and its FP32 density contribution [kmax][N_g]
+  std::vector<lrdm::Channel> kp_ch;
+  std::vector<int> kp_pid;
+  std::vector<float*> kp_out;
 };
 
 namespace lrdm {
@@ -144,10 +150,16 @@ cudaError_t launch_loewner_f32(const double* L, int ns, int ns_pad, float* Lf, c
 // ---------------- Brillouin-zone-sampled response (k_kpoint.cu) ----------------
 constexpr int KP_MAX = 32;           // k-points per context
 struct KpDmuArgs {
-  const void* Xr[KP_MAX];
+  const void* Xr[KP_MAX];            // Re X (CUDA cores) or the stacked Gram P (tensor cores)
   const double* L[KP_MAX];
   double kw[KP_MAX];
   int nk, ns, K, nsplit, fp64;
+  int ld;                            // leading dimension of the X planes
+  int stacked;                       // 1: Re X_ii = P_ii + P_(ns+i)(ns+i)
+};
+struct KpSumArgs {
+  const float* part[KP_MAX];         // [K][N_g] per k-point, factor included
+  int nk;
 };
 // X_kappa (re, im) = Psi^H diag(a_k) Psi over nsplit grid-row ranges
 cudaError_t launch_kp_gemm1(int fp64, const void* pr, const void* pi, int ns, long long Ng,
@@ -164,11 +176,19 @@ cudaError_t launch_kp_gemm2(int fp64, const void* pr, const void* pi, int ns, lo
                             cudaStream_t st);
 cudaError_t launch_kp_finish(const double* drho, const void* v, int io, long long n, void* f,
                              cudaStream_t st);
-cudaError_t launch_kp_density(int fp64, const void* pr, const void* pi, int ns, long long Ng,
+cudaError_t launch_kp_density(int fp64, const void* pr, const void* pi, int ns, int ld, long long Ng,
                               const double* occ, double gw, int first, double floor, double* rho,
                               cudaStream_t st);
+// dst[r][col0 + i] = src[r][i] (compute type, leading dimension ldd)
 cudaError_t launch_kp_copy(int fp64, const void* src, int io, int ld, long long Ng, int ns, void* dst,
-                           cudaStream_t st);
+                           int ldd, int col0, cudaStream_t st);
+// tensor-core modes: M'' for the real GEMM2 from the stacked Gram P, layout 1
+// (TF32) or 2 (BF16 hi/lo), [K][ld][ld]
+cudaError_t launch_kp_scale_tc(const float* P, int nsplit, int K, int ns, int ld, const double* L,
+                               const double* dmu, int layout, void* out, void* out_lo, cudaStream_t st);
+// f = sum_kappa part_kappa - v (io dtype)
+cudaError_t launch_kp_sum(const KpSumArgs& A, const void* v, int io, long long n, void* f,
+                          cudaStream_t st);
 
 // ---------------- element-wise / reduction kernels (k_elem.cu) ----------------
 // fft_real[k][r] = sum_s v[k][s][r]  (compute type = double if fp64 else float)

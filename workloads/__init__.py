@@ -316,3 +316,36 @@ def random_subspace_torch(n, h, ns, seed, device, dtype=None):
         torch.backends.cuda.matmul.allow_tf32 = prev
     A.mul_(1.0 / np.sqrt(w))
     return A.to(dtype)
+
+
+def random_subspace_complex_torch(n, h, ns, seed, device):
+    """Complex Psi = orth(diag(e) (G + i G'))/sqrt(w) on the device (two
+    passes of Cholesky-QR: complex64 Gram with TF32 off, the small Cholesky
+    factor and its inverse in complex128 on the host), returned as its real
+    and imaginary float32 planes (N_g, N_s).  Same recipe as
+    random_subspace_complex() with torch's RNG."""
+    import scipy.linalg
+    import torch
+    N = int(np.prod(n))
+    w = float(np.prod(h))
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    re = torch.randn(N, ns, generator=gen, device=device, dtype=torch.float32)
+    im = torch.randn(N, ns, generator=gen, device=device, dtype=torch.float32)
+    A = torch.complex(re, im)
+    del re, im
+    env = torch.from_numpy(envelope(n, h)).to(device=device, dtype=torch.float32)
+    A.mul_(env[:, None])
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for _ in range(2):
+            C = (A.conj().T @ A).cpu().numpy().astype(np.complex128)
+            C = 0.5 * (C + C.conj().T)
+            U = np.linalg.cholesky(C).conj().T
+            Uinv = scipy.linalg.solve_triangular(U, np.eye(ns), lower=False)
+            A = A @ torch.as_tensor(Uinv, dtype=torch.complex64, device=device)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    A.mul_(1.0 / np.sqrt(w))
+    return A.real.contiguous(), A.imag.contiguous()
