@@ -12,7 +12,7 @@ map and of the eigenvalue / occupation inputs for one cotangent per direction
 lrdm_gateaux_batch) is timed separately and reported under "forward_only",
 with and without the Poisson (cuFFT) step.  A periodic workload sampled at
 4 Brillouin-zone points (48^3 grid, N_s = 512 complex states per point, K = 8,
-FP32; lrdm_kp_gateaux) is timed after the main step and reported under
+same precision; lrdm_kp_gateaux) is timed after the main step and reported under
 "kpoint" with its own roofline and oracle baseline (--kpoint-only runs it
 alone).
 
@@ -225,10 +225,11 @@ def kp_weights(nk):
     return [x / sum(raw) for x in raw]
 
 
-def time_kpoint(torch, rank, reps=5, warmup=2):
-    """K = 8 real directions through lrdm_kp_gateaux (FP32) on a 48^3 grid
-    with 4 k-points of N_s = 512 complex states each; the projection kernel's
-    ALU roofline from the library's own event timing."""
+def time_kpoint(torch, rank, prec, autotune=True, reps=5, warmup=2):
+    """K = 8 real directions through lrdm_kp_gateaux on a 48^3 grid with 4
+    k-points of N_s = 512 complex states each (tensor-core precisions: the
+    real contractions on the stacked 2 N_s = 1024-column operand); the
+    projection kernel's roofline from the library's own event timing."""
     import workloads
     from paper_2211_07894_gb300 import KpContext
     rng = workloads.rng_for(80, rank)
@@ -241,7 +242,8 @@ def time_kpoint(torch, rank, reps=5, warmup=2):
     eps = [torch.as_tensor(workloads.random_eigenvalues(KP_NS, rng) + 0.02 * q, device="cuda")
            for q in range(KP_NK)]
     ctx = KpContext(KP_GRID, H, pr, pi, eps, kp_weights(KP_NK), KP_NE, KP_KT, rho_floor=1e-3,
-                    prec="fp32", io_dtype=torch.float32, k_max=KP_K)
+                    prec=prec, io_dtype=torch.float32, k_max=KP_K, autotune=autotune)
+    tuning = ctx.tuning() if prec in ("bf16x3", "tf32") else None
     del pr, pi
     V = torch.as_tensor(workloads.smooth_directions(KP_GRID, H, KP_K, 1, workloads.rng_for(80, 100 + rank))[:, 0],
                         dtype=torch.float32, device="cuda").contiguous()
@@ -266,21 +268,35 @@ def time_kpoint(torch, rank, reps=5, warmup=2):
         raise RuntimeError("device status not ok after the k-point calls")
     ctx.close()
     ng = int(KP_GRID[0] * KP_GRID[1] * KP_GRID[2])
-    # one projection launch: one k-point, K directions, 8 real flops per
-    # (row, i <= j) complex product
-    alg = KP_K * 4.0 * ng * KP_NS * (KP_NS + 1)
-    n1 = max(prof["gemm1_launches"], 1) * KP_NK      # events bracket all k-points of a call
-    avg_s = prof["gemm1_ms"] / n1 / 1e3
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    achieved = alg / avg_s / 1e12
-    return {"workload": f"{KP_GRID[0]}^3 grid, {KP_NK} k-points x N_s={KP_NS} complex, K={KP_K}, FP32",
+    # the projection work of one call (all k-points): per k-point and
+    # direction the upper triangle of the complex N_s x N_s product, 8 real
+    # flops per (row, i <= j), = the symmetric half of the stacked real
+    # (2 N_s)^2 Gram, 2 flops per (row, i, j) / 2
+    alg = KP_NK * KP_K * 4.0 * ng * KP_NS * KP_NS
+    per_call = prof["gemm1_ms"] / max(prof["gemm1_launches"], 1) / 1e3   # one event per call
+    peaks, src = load_peaks()
+    sus = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    if prec == "bf16x3":
+        issued, peak, bound = 3.0 * alg, sus, "tensor"
+        note, kname = "bf16x3 issues 3 bf16 MMAs per product; achieved = issued bf16 rate", "k_gemm1_tc"
+    elif prec == "tf32":
+        issued, peak, bound = alg, 0.5 * sus, "tensor"
+        note, kname = "tf32 peak = bf16 sustained x 1/2 (nominal ratio)", "k_gemm1_tc"
+    elif prec == "fp32":
+        issued, peak, bound = alg, 152 * 128 * 2 * 2.07e9 / 1e12, "alu"
+        note, kname = "FP32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz", "k_kp_gemm1<float>"
+    else:
+        issued, peak, bound = alg, 1.10, "alu"
+        note, kname = "FP64 peak = measured torch FP64 matmul (1.10 TF/s)", "k_kp_gemm1<double>"
+    achieved = issued / per_call / 1e12
+    return {"workload": f"{KP_GRID[0]}^3 grid, {KP_NK} k-points x N_s={KP_NS} complex, K={KP_K}, {prec}",
             "value": KP_K / (ms / 1e3), "unit": "GD/s", "ms_per_call": ms, "reps": reps,
+            "launch_shape": tuning,
             "gemm1_ms_per_call": prof["gemm1_ms"] / reps, "gemm2_ms_per_call": prof["gemm2_ms"] / reps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_kp_gemm1<float> (complex projection)",
-                         "avg_launch_ms": avg_s * 1e3, "alg_flop_per_launch": alg,
-                         "peak_source": "FP32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"}}
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": kname,
+                         "gemm1_ms_per_call": per_call * 1e3, "alg_flop_per_call": alg,
+                         "peak_source": f"{src}; {note}"}}
 
 
 def time_kpoint_oracle():
@@ -477,7 +493,7 @@ def main():
     if args.kpoint_only:
         from paper_2211_07894_gb300 import build as _build
         _build.build()
-        kp = time_kpoint(torch, rank)
+        kp = time_kpoint(torch, rank, args.prec, autotune=not args.no_autotune)
         if rank == 0 and not args.no_cpu_baseline:
             kp["cpu_baseline"] = time_kpoint_oracle()
         print(json.dumps(kp), flush=True)
@@ -678,7 +694,7 @@ def main():
         ctx.close()
         F = fbar = bwd_out = None
         torch.cuda.empty_cache()
-        kpoint = time_kpoint(torch, rank)
+        kpoint = time_kpoint(torch, rank, args.prec, autotune=not args.no_autotune)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             kpoint["cpu_baseline"] = time_kpoint_oracle()
 

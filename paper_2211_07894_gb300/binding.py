@@ -502,7 +502,7 @@ class KpContext:
 
     def __init__(self, n, h, psi_re, psi_im, eps, k_weights, n_electrons, kT, g=2.0,
                  rho=None, rho_floor=0.0, prec="fp64", io_dtype=None, k_max=16, degen_tol=1e-5,
-                 stream=None):
+                 autotune=False, stream=None):
         import torch
         self.torch = torch
         self.io_dtype = io_dtype or torch.float64
@@ -511,6 +511,7 @@ class KpContext:
         o.io_dtype = DTYPE_F64 if self.io_dtype == torch.float64 else DTYPE_F32
         o.k_max = int(k_max)
         o.degen_tol = float(degen_tol)
+        o.autotune = 1 if autotune else 0
         nk = len(psi_re)
         assert len(psi_im) == nk and len(eps) == nk and len(k_weights) == nk
         s = lrdm_kpoint_system()
@@ -604,6 +605,10 @@ class KpContext:
 
     def profile_read(self, reset=True):
         return lrdm_profile_read(self.handle, 1 if reset else 0)
+
+    def tuning(self):
+        """Launch shape of the tensor-core contractions (defaults or autotuned)."""
+        return lrdm_get_tuning(self.handle)
 
     def status(self, synchronize=True):
         return lrdm_status_query(self.handle, 1 if synchronize else 0)

@@ -411,6 +411,12 @@ std::string tune_key(lrdm_ctx* ctx) {
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   std::string k = "sm" + std::to_string(major) + std::to_string(minor) + "x" + std::to_string(sms) +
                   ";prec" + std::to_string(ctx->opt.prec);
+  if (ctx->kp) {                      // one stacked problem per k-point
+    for (const Channel& c : ctx->kp_ch)
+      k += ";kp" + std::to_string(ctx->sys[0].Ng) + "," + std::to_string(c.ns_pad) + "," +
+           std::to_string(ctx->sys[0].kmax);
+    return k;
+  }
   for (int s = 0; s < ctx->nsys; ++s)
     for (int c = 0; c < ctx->sys[s].nspin; ++c)
       k += ";" + std::to_string(ctx->sys[s].Ng) + "," + std::to_string(ctx->sys[s].ch[c].ns_pad) +
@@ -487,7 +493,22 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
   const std::string key = tune_key(ctx);
   if (cache && *cache && tune_cache_read(cache, key, ctx->tune)) return LRDM_OK;
   std::vector<TcEntry> g1, g2;
-  for (int s = 0; s < ctx->nsys; ++s) {
+  for (size_t q = 0; q < ctx->kp_ch.size(); ++q) {     // k-point context: the stacked problems
+    SysState& S = ctx->sys[0];
+    TcEntry x;
+    x.dev_base = ctx->tc_dev;
+    x.pid = ctx->kp_pid[q];
+    x.host = &ctx->tc_host[x.pid];
+    x.K = S.kmax;
+    x.X = ctx->kp_ch[q].Xpart;
+    g1.push_back(x);
+    x.X = nullptr;
+    x.factor = 1.0;
+    x.out = ctx->kp_out[q];
+    x.out_stride = S.Ng;
+    g2.push_back(x);
+  }
+  for (int s = 0; s < ctx->nsys && !ctx->kp; ++s) {
     SysState& S = ctx->sys[s];
     for (int c = 0; c < S.nspin; ++c) {
       TcEntry x = tc_entry(ctx, s, c, S.kmax);
@@ -1536,6 +1557,7 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
     if ((rc = dalloc(ctx, &ctx->ls_scal, 4)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->upd_partial, UPD_BLOCKS)) != LRDM_OK) break;
     if ((rc = kp_setup(ctx, *sys, st)) != LRDM_OK) break;
+    if (is_tc(o.prec) && o.autotune && (rc = autotune(ctx, st)) != LRDM_OK) break;
     if (cudaGetLastError() != cudaSuccess) rc = LRDM_ERR_CUDA;
   } while (0);
   if (rc != LRDM_OK) {

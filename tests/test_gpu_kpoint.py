@@ -157,3 +157,24 @@ def test_kpoint_rejections(lib, cfg):
     with pytest.raises(LrdmError):
         ctx.gateaux(torch.zeros((5, V.shape[1]), dtype=torch.float64, device="cuda"))   # K > k_max
     assert ctx.status() == 0
+
+
+def test_kpoint_autotuned_shape_matches_default(lib, cfg):
+    # the tuner picks among launch shapes of the same contractions: results agree
+    ctx0, _ = _device(cfg, "bf16x3")
+    from paper_2211_07894_gb300 import KpContext
+    pr = [torch.as_tensor(np.ascontiguousarray(p.real), dtype=torch.float32, device="cuda") for p in cfg["psi"]]
+    pi = [torch.as_tensor(np.ascontiguousarray(p.imag), dtype=torch.float32, device="cuda") for p in cfg["psi"]]
+    eps = [torch.as_tensor(e, dtype=torch.float64, device="cuda") for e in cfg["eps"]]
+    ctx1 = KpContext(cfg["n"], cfg["h"], pr, pi, eps, cfg["k_weights"], cfg["n_electrons"], cfg["kT"],
+                     g=cfg["g"], rho_floor=cfg["rho_floor"], prec="bf16x3", io_dtype=torch.float32, k_max=4,
+                     autotune=True)
+    t = ctx1.tuning()
+    assert t["g1_nb"] in (128, 256) and t["g2_bn"] in (128, 256) and t["g2_kgroup"] in (1, 2, 4)
+    V = torch.as_tensor(cfg["V"], dtype=torch.float32, device="cuda")
+    F0, d0 = ctx0.gateaux(V)
+    F1, d1 = ctx1.gateaux(V)
+    torch.cuda.synchronize()
+    assert ctx1.status() == 0
+    assert per_direction_rel_err(F1.double().cpu().numpy(), F0.double().cpu().numpy()) < 1e-5
+    assert np.max(np.abs(d1.cpu().numpy() - d0.cpu().numpy())) < 1e-6
