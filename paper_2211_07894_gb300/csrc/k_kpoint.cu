@@ -354,6 +354,9 @@ __global__ void k_kp_copy(const void* __restrict__ src, int io, int ld, long lon
 
 // M'' at [k][j][i] (i fastest) for i <= j < 2 ns: c_ij M_ij with c = 2 off the
 // diagonal; zero elsewhere (padding included).  One thread per four columns.
+// P (both triangles written by GEMM1) and L are symmetric, so every read
+// takes the entry whose column follows i: consecutive threads read
+// consecutive addresses.
 __global__ void k_kp_scale_tc(const float* __restrict__ P, int nsplit, int K, int ns, int ld,
                               const double* __restrict__ L, const double* __restrict__ dmu, int layout,
                               void* __restrict__ out, __nv_bfloat16* __restrict__ out_lo) {
@@ -377,12 +380,12 @@ __global__ void k_kp_scale_tc(const float* __restrict__ P, int nsplit, int K, in
     double m = 0.0;
     if (i <= j && j < n2) {
       const int a = i < ns ? i : i - ns, b = j < ns ? j : j - ns;
-      const double l = L[(long long)a * ns + b];
-      if ((i < ns) == (j < ns)) {              // diagonal blocks: Re Gamma
-        const double xr = Pat(a, b) + Pat(ns + a, ns + b);
+      const double l = L[(long long)b * ns + a];
+      if ((i < ns) == (j < ns)) {              // diagonal blocks: Re Gamma_ab = L_ab (P11 + P22 - mu')
+        const double xr = Pat(b, a) + Pat(ns + b, ns + a);
         m = l * (xr - (a == b ? dmu[k] : 0.0));
-      } else {                                 // i in block 0, j in block 1: Im Gamma_ab
-        const double xi = Pat(a, ns + b) - Pat(ns + a, b);
+      } else {                                 // i in block 0, j in block 1: Im Gamma_ab = L_ab (P12 - P21)
+        const double xi = Pat(ns + b, a) - Pat(b, ns + a);
         m = l * xi;
       }
       if (i < j) m *= 2.0;
