@@ -289,12 +289,16 @@ def time_kpoint(torch, rank, prec, autotune=True, reps=5, warmup=2):
         issued, peak, bound = alg, 1.10, "alu"
         note, kname = "FP64 peak = measured torch FP64 matmul (1.10 TF/s)", "k_kp_gemm1<double>"
     achieved = issued / per_call / 1e12
+    traffic = None
+    if tuning:
+        traffic = recorded_traffic(kname, f"{KP_GRID[0]}^3/kp{KP_NK}x{KP_NS}/K{KP_K}/{prec}",
+                                   f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}")
     return {"workload": f"{KP_GRID[0]}^3 grid, {KP_NK} k-points x N_s={KP_NS} complex, K={KP_K}, {prec}",
             "value": KP_K / (ms / 1e3), "unit": "GD/s", "ms_per_call": ms, "reps": reps,
             "launch_shape": tuning,
             "gemm1_ms_per_call": prof["gemm1_ms"] / reps, "gemm2_ms_per_call": prof["gemm2_ms"] / reps,
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": kname,
+                         "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                          "gemm1_ms_per_call": per_call * 1e3, "alg_flop_per_call": alg,
                          "peak_source": f"{src}; {note}"}}
 

@@ -178,3 +178,37 @@ def test_kpoint_autotuned_shape_matches_default(lib, cfg):
     assert ctx1.status() == 0
     assert per_direction_rel_err(F1.double().cpu().numpy(), F0.double().cpu().numpy()) < 1e-5
     assert np.max(np.abs(d1.cpu().numpy() - d0.cpu().numpy())) < 1e-6
+
+
+@pytest.mark.parametrize("prec,io", [("bf16x3", torch.float64), ("tf32", torch.float32)])
+def test_kpoint_tensor_cores_edge_cases(lib, cfg, prec, io):
+    """Tensor-core k-point path with FP64 io or TF32, one point with weight 1
+    and a given density, K = 1 and K = 2 < k_max after a K = 3 call."""
+    from paper_2211_07894_gb300 import KpContext
+    one = dict(cfg)
+    one["psi"] = cfg["psi"][1:2]
+    one["eps"] = cfg["eps"][1:2]
+    one["k_weights"] = np.array([1.0])
+    ks, mu = _oracle(one, one["psi"])
+    rho = ks.rho * 0.9
+    pr = [torch.as_tensor(np.ascontiguousarray(p.real), dtype=io, device="cuda") for p in one["psi"]]
+    pi = [torch.as_tensor(np.ascontiguousarray(p.imag), dtype=io, device="cuda") for p in one["psi"]]
+    eps = [torch.as_tensor(e, dtype=torch.float64, device="cuda") for e in one["eps"]]
+    ctx = KpContext(cfg["n"], cfg["h"], pr, pi, eps, [1.0], cfg["n_electrons"], cfg["kT"], g=cfg["g"],
+                    rho=torch.as_tensor(rho, dtype=io, device="cuda"), prec=prec, io_dtype=io, k_max=4)
+    psi_seen = [a.double().cpu().numpy() + 1j * b.double().cpu().numpy() for a, b in zip(pr, pi)]
+    ks.psi = psi_seen
+    ks.rho = ctx.density().double().cpu().numpy()
+    V = torch.as_tensor(cfg["V"], dtype=io, device="cuda")
+    ref = oracle.gateaux_kpoints(ks, V.double().cpu().numpy())
+    tol = TOL[prec]
+    F3, _ = ctx.gateaux(V)
+    F1, d1 = ctx.gateaux(V[2:3].contiguous())
+    F2, _ = ctx.gateaux(V[:2].contiguous())
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert per_direction_rel_err(F3.double().cpu().numpy(), ref["F"]) < tol
+    assert rel_err(F1.double().cpu().numpy()[0], ref["F"][2]) < tol
+    assert per_direction_rel_err(F2.double().cpu().numpy(), ref["F"][:2]) < tol
+    # the same direction gives the same result in a batch of 3 or alone
+    assert torch.equal(F1[0], F3[2]) or rel_err(F1.double().cpu().numpy()[0], F3.double().cpu().numpy()[2]) < 1e-6
