@@ -115,7 +115,16 @@ typedef struct lrdm_options {
                             environment variable LRDM_TUNE_CACHE naming a file,
                             results are read from / appended to it (one JSON
                             object per line, keyed by device and problem sizes) */
-  int debug_flags;       /* test-only host-side fault injection; 0 in production */
+  int debug_flags;       /* test-only fault injection, 0 in production:
+                            LRDM_DEBUG_STALL_PROJECTION makes the next
+                            tensor-core projection launch (once) leave one
+                            weighted stage of CTA 0 unpublished, so that its
+                            MMA thread's bounded wait (4 s) expires: the kernel
+                            sets LRDM_ERR_TIMEOUT in the status word, waits for
+                            its own copies and MMAs, frees its tensor memory
+                            and returns (no trap, no hang); that call's results
+                            are undefined, later calls are unaffected.  Not for
+                            use with use_graph. */
   int fermi_T;           /* 0: the response uses the Loewner (divided-difference)
                             matrix of Fermi-Dirac; T >= 1: the first-order
                             response of the depth-T recursive Fermi-operator
@@ -130,6 +139,9 @@ typedef struct lrdm_options {
 } lrdm_options;
 
 typedef struct lrdm_ctx lrdm_ctx;
+
+/* lrdm_options.debug_flags bits (tests only) */
+#define LRDM_DEBUG_STALL_PROJECTION 1
 
 /* Fills *opt with the defaults above (BF16X3, F32 io, k_max 16). */
 void lrdm_default_options(lrdm_options* opt);

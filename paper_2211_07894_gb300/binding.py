@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "shape", 3: "out of memory", 
                 9: "unsupported"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
 DTYPE_F64, DTYPE_F32 = 0, 1
+DEBUG_STALL_PROJECTION = 1      # lrdm_options.debug_flags bit (tests only)
 
 
 class LrdmError(RuntimeError):
@@ -301,7 +302,7 @@ class Context:
 
     def __init__(self, systems, prec="bf16x3", io_dtype=None, k_max=16, pinv_rcond=1e-12,
                  degen_tol=1e-5, poisson="spectral", use_graph=False, stream=None, fermi_T=0,
-                 autotune=False):
+                 autotune=False, debug_flags=0):
         import torch
         self.torch = torch
         self.io_dtype = io_dtype or torch.float32
@@ -316,6 +317,7 @@ class Context:
         o.use_graph = 1 if use_graph else 0
         o.fermi_T = int(fermi_T)
         o.autotune = 1 if autotune else 0
+        o.debug_flags = int(debug_flags)
         self.options = o
         keep = []
         cs = []

@@ -448,6 +448,7 @@ struct G1Params {
   int nsplit[TC_MAX_SLOTS];         // grid-row ranges per slot (partial X summed by the consumers)
   int dpt;                          // directions per tile (1 or 2)
   int nch_lim;                      // > 0: reduce over the first nch_lim stages only (tuning)
+  int stall;                        // test only: CTA 0 never publishes its first weighted stage
   int* status;
 };
 
@@ -703,6 +704,9 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
   uint32_t ph = 0, aph = 0;
   bool ok = true;
   float sum[128];
+  // test only: the MMA thread of CTA 0 then waits for a stage that is never
+  // published, and its bounded wait ends the launch with a timeout status
+  bool stall = P.stall != 0 && blockIdx.x == 0;
   for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
     int q, k0, nd, I, J, sp;
     const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J, sp);
@@ -720,7 +724,8 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
       ptx::tmem_wait_st();
       ptx::tc_fence_before();
       __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&B.ready[s]);
+      if (lane == 0 && !stall) ptx::mbar_arrive(&B.ready[s]);
+      stall = false;
       if (++s == STAGES) { s = 0; ph ^= 1; }
       // add a finished segment into the running sums once the weighting is
       // LAG stages past its end (those stages are ready when the MMAs resume)
@@ -943,7 +948,7 @@ void order_slots(const TcEntry* e, int n, int gemm, int* order) {
 
 template <int PREC, int NB>
 cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, const TcTune& t,
-                        int nch_lim) {
+                        int nch_lim, int stall) {
   static bool attr = false;
   const int smem = G1Cfg<PREC, NB>::SMEM;
   cudaError_t err = set_smem(k_gemm1_tc<PREC, NB>, smem, attr);
@@ -958,6 +963,7 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, c
     P.status = status;
     P.dpt = dpt;
     P.nch_lim = nch_lim;
+    P.stall = base == 0 ? stall : 0;
     int items = 0, q = 0;
     for (int u = 0; u < m; ++u) {
       const TcEntry& x = e[base + order[u]];
@@ -1043,13 +1049,13 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 }
 
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
-                                  const TcTune& t, int nch_lim) {
+                                  const TcTune& t, int nch_lim, int stall) {
   const bool wide = t.g1_nb == 256;
   if (prec == LRDM_BF16X3)
-    return wide ? gemm1_group<LRDM_BF16X3, 256>(e, n, status, st, t, nch_lim)
-                : gemm1_group<LRDM_BF16X3, 128>(e, n, status, st, t, nch_lim);
-  return wide ? gemm1_group<LRDM_TF32, 256>(e, n, status, st, t, nch_lim)
-              : gemm1_group<LRDM_TF32, 128>(e, n, status, st, t, nch_lim);
+    return wide ? gemm1_group<LRDM_BF16X3, 256>(e, n, status, st, t, nch_lim, stall)
+                : gemm1_group<LRDM_BF16X3, 128>(e, n, status, st, t, nch_lim, stall);
+  return wide ? gemm1_group<LRDM_TF32, 256>(e, n, status, st, t, nch_lim, stall)
+              : gemm1_group<LRDM_TF32, 128>(e, n, status, st, t, nch_lim, stall);
 }
 
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,

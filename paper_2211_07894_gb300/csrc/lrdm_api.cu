@@ -358,9 +358,12 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
   if (n == 0) return LRDM_OK;
   int pi = prof_begin(ctx, gemm, st);
   count(ctx, (n + TC_MAX_SLOTS - 1) / TC_MAX_SLOTS);
+  // test-only fault injection, once: the next projection launch times out
+  const int stall = gemm == 1 && (ctx->opt.debug_flags & LRDM_DEBUG_STALL_PROJECTION) ? 1 : 0;
+  if (stall) ctx->opt.debug_flags &= ~LRDM_DEBUG_STALL_PROJECTION;
   cudaError_t e = gemm == 1
                       ? launch_gemm1_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
-                                              ctx->d_status, st, ctx->tune)
+                                              ctx->d_status, st, ctx->tune, 0, stall)
                       : launch_gemm2_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
                                               ctx->opt.io_dtype, out_is_io, ctx->d_status, st,
                                               ctx->tune);

@@ -270,8 +270,10 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 // Grouped launches over n problems (each with its own K; K = 0 entries skipped).
 // nch_lim / nR_lim > 0 cap the grid reduction (GEMM1) or the row blocks
 // (GEMM2) per problem: partial work with the same item structure (tuning).
+// stall != 0 (test only): CTA 0 of the first launch never publishes its
+// first weighted stage, so its bounded wait expires (timeout status).
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
-                                  const TcTune& t, int nch_lim = 0);
+                                  const TcTune& t, int nch_lim = 0, int stall = 0);
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
                                   int* status, cudaStream_t st, const TcTune& t, int nR_lim = 0);
 bool tc_supported();
