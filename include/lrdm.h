@@ -343,10 +343,10 @@ void lrdm_lrdma_destroy(lrdm_lrdma* a);
  * C = [Re Psi, Im Psi] (N_g x 2 N_s): C^T diag(a) C holds Re X and Im X, and
  * the density is diag(C M C^T) with M = [[Re G, Im G], [-Im G, Re G]],
  * G = L o (X - mu' I).  A k-point context serves lrdm_kp_gateaux,
- * lrdm_apply (sys 0, n = N_g), lrdm_get_mu, lrdm_get_density,
+ * lrdm_apply, lrdm_krylov_step and lrdm_lrdma_step (sys 0, grid functions of
+ * n = N_g values), lrdm_get_mu, lrdm_get_density, lrdm_get_tuning,
  * lrdm_status_query, lrdm_profile_* and lrdm_destroy; lrdm_gateaux_batch,
- * lrdm_backward, lrdm_krylov_step, lrdm_get_projection and lrdm_lrdma_step
- * return LRDM_ERR_UNSUPPORTED for it.
+ * lrdm_backward and lrdm_get_projection return LRDM_ERR_UNSUPPORTED for it.
  * ------------------------------------------------------------------------- */
 typedef struct lrdm_kpoint_system {
   int n[3];                       /* periodic grid                                 */

@@ -536,6 +536,15 @@ def alpha_schedule(r_norm, threshold=2.0):
     return 0.5 if r_norm < threshold else 0.1
 
 
+def _derivative(system, u):
+    """t = d/dlam R[rho + lam u] for one direction u: the single-point response
+    (u of shape (nspin, N_g)) or the Brillouin-zone-sampled one (u of shape
+    (N_g,), a KpointSystem)."""
+    if isinstance(system, KpointSystem):
+        return gateaux_kpoints(system, u[None])["F"][0]
+    return gateaux(system, u[None])["F"][0]
+
+
 def lrdm_krylov_step(system: System, R, s_tol=0.3, r_max=8, alpha=None, rho=None, rcond=1e-12):
     """One LRDM preconditioning step with adaptively chosen rank (§II.B):
 
@@ -550,8 +559,9 @@ def lrdm_krylov_step(system: System, R, s_tol=0.3, r_max=8, alpha=None, rho=None
       Delta = sum_k a_k u_k,  rho_new = rho - alpha Delta (Eq. quasinewton);
       alpha None -> alpha_schedule(||R||).
 
-    Directions and residuals have the shape (nspin, N_g); for a spin pair the
-    inner product sums the two channels (Eq. innerproductDirectsumHilbertspace).
+    Directions and residuals have the shape (nspin, N_g) (a KpointSystem: (N_g,),
+    the derivatives by gateaux_kpoints); for a spin pair the inner product sums
+    the two channels (Eq. innerproductDirectsumHilbertspace).
     Returns the directions U (r, nspin, N_g), their derivatives T, the
     coefficients a, the rank r, s_rel after each rank, ||R||, alpha, Delta and
     rho_new when rho is given."""
@@ -562,7 +572,7 @@ def lrdm_krylov_step(system: System, R, s_tol=0.3, r_max=8, alpha=None, rho=None
     T = []
     s_hist = []
     while True:
-        T.append(gateaux(system, U[-1][None])["F"][0])
+        T.append(_derivative(system, U[-1]))
         ls = lrdm_apply(Rm, np.stack(U), np.stack(T), w, 0.0, rcond=rcond)
         s_hist.append(ls["s_rel"])
         if ls["s_rel"] < s_tol or len(U) == r_max:
@@ -652,7 +662,7 @@ def lrdma_step(system: System, state: LrdmaState, R, rho=None, s_tol=0.3, beta_t
         u = Rm / r_norm if fresh else _orthonormalise(Rm, state.U, w)
         while True:
             state.U.append(u)
-            state.T.append(gateaux(system, u[None])["F"][0])
+            state.T.append(_derivative(system, u))
             n_new += 1
             ls = lrdm_apply(Rm, np.stack(state.U), np.stack(state.T), w, 0.0, rcond=rcond)
             if ls["s_rel"] < s_tol or n_new == limit:

@@ -612,6 +612,22 @@ class KpContext:
         """Launch shape of the tensor-core contractions (defaults or autotuned)."""
         return lrdm_get_tuning(self.handle)
 
+    def krylov_step(self, R, s_tol=0.3, r_max=8, alpha=-1.0, rho=None, stream=None):
+        """The paper's adaptive-rank LRDM step (lrdm_krylov_step) on this
+        BZ-sampled system.  R: (N_g,) in the io dtype; rho (same shape) is
+        updated in place when given.  Returns dict(U, T, a, rank, s_rel, r_norm)."""
+        torch = self.torch
+        assert R.is_contiguous() and R.dtype == self.io_dtype and R.numel() == self.Ng
+        U = torch.empty((r_max, self.Ng), dtype=self.io_dtype, device="cuda")
+        T = torch.empty_like(U)
+        a = torch.zeros(r_max, dtype=torch.float64, device="cuda")
+        code, rank, s_rel, rn = lrdm_krylov_step(self.handle, 0, R.data_ptr(), s_tol, r_max, alpha,
+                                                 rho.data_ptr() if rho is not None else 0,
+                                                 U.data_ptr(), T.data_ptr(), a.data_ptr(),
+                                                 self._stream(stream))
+        _check("lrdm_krylov_step", code)
+        return dict(U=U[:rank], T=T[:rank], a=a[:rank], rank=rank, s_rel=s_rel, r_norm=rn)
+
     def status(self, synchronize=True):
         return lrdm_status_query(self.handle, 1 if synchronize else 0)
 

@@ -632,6 +632,15 @@ lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void*
   return LRDM_OK;
 }
 
+// One forward call of the direction drivers (Krylov step, LRDMA): system sys
+// gets K[sys] directions, the others none; a Brillouin-zone-sampled context
+// runs its own forward (one system, one channel).
+lrdm_status forward_one(lrdm_ctx* ctx, int sys, const void* const* v, const int* K, void* const* f,
+                        cudaStream_t st) {
+  if (ctx->kp) return lrdm_kp_gateaux(ctx, v[sys], K[sys], f[sys], nullptr, st);
+  return forward_all(ctx, v, K, f, nullptr, st);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -852,7 +861,6 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
 lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol, int r_max,
                              double alpha, void* rho_inout, void* U, void* T, double* coeff_out,
                              double* s_rel_out, int* rank_out, double* r_norm_out, void* stream) {
-  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !U || !T) return LRDM_ERR_INVALID_ARG;
   if (r_max < 1 || r_max > KMAX_LIMIT || !(s_tol >= 0.0) || !isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -877,7 +885,7 @@ lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol
     v[sys] = static_cast<const char*>(U) + i * vb;
     f[sys] = static_cast<char*>(T) + i * vb;
     K[sys] = 1;
-    LRDM_CK(forward_all(ctx, v.data(), K.data(), f.data(), nullptr, st));
+    LRDM_CK(forward_one(ctx, sys, v.data(), K.data(), f.data(), st));
     rank = i + 1;
     // least squares on the first i + 1 directions (no update yet) -> s_rel
     LRDM_CU(launch_ls(R, U, T, io, rank, n, S.w, 0.0, ctx->opt.pinv_rcond, nullptr, ctx->ls_coef,
@@ -1032,7 +1040,6 @@ void lrdm_lrdma_destroy(lrdm_lrdma* a) {
 lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R, void* rho_inout,
                             const lrdm_lrdma_params* params, lrdm_lrdma_report* report,
                             void* stream) {
-  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!a || !ctx || sys < 0 || sys >= ctx->nsys || !R) return LRDM_ERR_INVALID_ARG;
   lrdm_lrdma_params p;
   if (params) p = *params;
@@ -1097,7 +1104,7 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
       v[sys] = U + a->m * vb;
       f[sys] = T + a->m * vb;
       K[sys] = 1;
-      LRDM_CK(forward_all(ctx, v.data(), K.data(), f.data(), nullptr, st));
+      LRDM_CK(forward_one(ctx, sys, v.data(), K.data(), f.data(), st));
       ++a->m;
       ++n_new;
       LRDM_CK(lrdma_ls(a, R, U, a->m, 0.0, nullptr, rcond, &s_rel, st));
@@ -1559,6 +1566,8 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
     if ((rc = dalloc(ctx, &ctx->ls_coef, KMAX_LIMIT)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->ls_scal, 4)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->upd_partial, UPD_BLOCKS)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->gs_scratch, gram_schmidt_scratch())) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->gs_norm, 1)) != LRDM_OK) break;
     if ((rc = kp_setup(ctx, *sys, st)) != LRDM_OK) break;
     if (is_tc(o.prec) && o.autotune && (rc = autotune(ctx, st)) != LRDM_OK) break;
     if (cudaGetLastError() != cudaSuccess) rc = LRDM_ERR_CUDA;

@@ -212,3 +212,62 @@ def test_kpoint_tensor_cores_edge_cases(lib, cfg, prec, io):
     assert per_direction_rel_err(F2.double().cpu().numpy(), ref["F"][:2]) < tol
     # the same direction gives the same result in a batch of 3 or alone
     assert torch.equal(F1[0], F3[2]) or rel_err(F1.double().cpu().numpy()[0], F3.double().cpu().numpy()[2]) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_kpoint_krylov_step(lib, cfg, prec):
+    """lrdm_krylov_step on a k-point context against the oracle's LRDM step
+    with the k-point derivative: same rank, directions, derivatives,
+    coefficients and density update."""
+    ctx, psi_seen = _device(cfg, prec, k_max=1)
+    ks, _ = _oracle(cfg, psi_seen)
+    ks.rho = ctx.density().double().cpu().numpy()
+    io = DT[prec]
+    R = workloads.smooth_field(cfg["n"], cfg["h"], 0.1, workloads.rng_for(70, 11))
+    R = torch.as_tensor(R, dtype=io).double().numpy()           # the values the device sees
+    ref = oracle.lrdm_krylov_step(ks, R, s_tol=1e-12, r_max=4)
+    s_tol = 0.5 * (ref["s_rel"][1] + ref["s_rel"][2])           # stop at rank 3
+    ref = oracle.lrdm_krylov_step(ks, R, s_tol=s_tol, r_max=4, rho=ks.rho)
+    rho = torch.as_tensor(ks.rho, dtype=io, device="cuda")
+    out = ctx.krylov_step(torch.as_tensor(R, dtype=io, device="cuda"), s_tol=s_tol, r_max=4, rho=rho)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    assert out["rank"] == ref["rank"] == 3
+    tol = TOL[prec]
+    assert np.allclose(out["s_rel"], ref["s_rel"], rtol=10 * tol, atol=0)
+    assert per_direction_rel_err(out["U"].double().cpu().numpy(), ref["U"]) < 10 * tol
+    assert per_direction_rel_err(out["T"].double().cpu().numpy(), ref["T"]) < 10 * tol
+    assert np.allclose(out["a"].cpu().numpy(), ref["a"], rtol=100 * tol, atol=0)
+    assert rel_err(rho.double().cpu().numpy() - ks.rho, ref["rho_new"] - ks.rho) < 100 * tol
+
+
+def test_kpoint_lrdma_steps_follow_oracle(lib, cfg):
+    """Three accumulated-LRDM steps (lrdm_lrdma_step) on one k-point context
+    along a residual sequence R_{n+1} = R_lin,n + a small smooth change: the
+    same event, kept and new rank, s_rel and density update as the oracle."""
+    from paper_2211_07894_gb300 import Lrdma
+    ctx, psi_seen = _device(cfg, "fp64", k_max=1)
+    ks, _ = _oracle(cfg, psi_seen)
+    ks.rho = ctx.density().cpu().numpy()
+    gpu = Lrdma(int(np.prod(N)), torch.float64, ks.w, capacity=8)
+    state = oracle.LrdmaState()
+    rng = workloads.rng_for(70, 12)
+    R = workloads.smooth_field(N, cfg["h"], 0.1, rng)
+    rho = ks.rho.copy()
+    events = []
+    for it in range(3):
+        ref = oracle.lrdma_step(ks, state, R, rho=rho, r_max=8)
+        rho_d = torch.as_tensor(rho, device="cuda").clone()
+        rep = gpu.step(ctx, torch.as_tensor(R, device="cuda").contiguous(), rho_d, r_max=8)
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        assert rep["event"] == ref["event"], (it, rep, ref["event"])
+        assert (rep["rank"], rep["rank_new"]) == (ref["rank"], ref["rank_new"])
+        assert abs(rep["s_rel"] - ref["s_rel"]) <= 1e-9 * max(ref["s_rel"], 1e-3)
+        d_ref = ref["rho_new"] - rho
+        assert rel_err(rho_d.cpu().numpy() - rho, d_ref) < 1e-9
+        events.append(rep["event"])
+        rho = ref["rho_new"]
+        R = state.R_lin + workloads.smooth_field(N, cfg["h"], 0.002, rng)
+    print(f"k-point LRDMA events {events}")
+    gpu.close()

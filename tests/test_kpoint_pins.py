@@ -13,6 +13,9 @@
   <dV_b, drho_a> (self-adjoint chi_0), and invariance under a phase per state
   (Psi_kappa -> Psi_kappa diag(e^{i phi})) and under complex conjugation of
   every Psi (the time-reversed points -kappa).
+* The adaptive-rank LRDM step on a BZ-sampled system (oracle.lrdm_krylov_step
+  with the k-point derivative) against the Krylov space of the k-point
+  Gateaux map and an lstsq solve over it.
 """
 
 import numpy as np
@@ -124,3 +127,28 @@ def test_phase_and_conjugation_invariance(kp):
     b = oracle.gateaux_kpoints(_system(kp, [p.conj() for p in kp["psi"]]), kp["V"])
     assert rel_err(b["F"], ref["F"]) < 1e-12
     assert np.abs(b["dmu"] - ref["dmu"]).max() < 1e-12
+
+
+def test_krylov_step_on_kpoints_matches_krylov_least_squares(kp):
+    """The adaptive-rank LRDM step on a BZ-sampled system against an
+    independent construction: span{R, JR, ..., J^(r-1) R} with J the pinned
+    k-point Gateaux map, and min ||J Delta - R||_w over it by lstsq."""
+    ks = _system(kp)
+    w = ks.w
+    R = workloads.smooth_field(ks.n, ks.h, 0.1, workloads.rng_for(60, 7))
+    out = oracle.lrdm_krylov_step(ks, R, s_tol=1e-6, r_max=4)
+    r = out["rank"]
+    assert r == 4
+    U = out["U"].reshape(r, -1)
+    assert np.max(np.abs(w * U @ U.T - np.eye(r))) < 1e-12
+
+    def J(v):
+        return oracle.gateaux_kpoints(ks, v[None])["F"][0]
+
+    Kr = [np.asarray(R, dtype=np.float64)]
+    for _ in range(r):
+        Kr.append(J(Kr[-1]))
+    B = np.stack(Kr[:r], axis=1)
+    JB = np.stack(Kr[1:], axis=1)
+    b, *_ = np.linalg.lstsq(np.sqrt(w) * JB, np.sqrt(w) * R, rcond=None)
+    assert rel_err(out["delta"], B @ b) < 1e-8
