@@ -43,4 +43,5 @@ from .lrdm_oracle import (  # noqa: F401
     solve_mu_kpoints,
     density_kpoints,
     gateaux_kpoints,
+    backward_kpoints,
 )

@@ -38,7 +38,7 @@ __all__ = [
     "density_response", "gateaux", "lrdm_apply", "backward", "total_eps_grad",
     "fermi_recursive", "loewner_recursive", "alpha_schedule", "lrdm_krylov_step",
     "LrdmaState", "lrdma_step", "KpointSystem", "solve_mu_kpoints", "density_kpoints",
-    "gateaux_kpoints",
+    "gateaux_kpoints", "backward_kpoints",
 ]
 
 
@@ -489,6 +489,40 @@ def gateaux_kpoints(system: KpointSystem, V):
             Xs[q][k] = Xk
         F[k] = drho[k] - V[k]
     return {"F": F, "drho": drho, "dmu": dmu, "X": Xs, "mu": mu, "L": L, "fx": fx}
+
+
+def backward_kpoints(system: KpointSystem, Fbar):
+    """Adjoint of gateaux_kpoints with respect to the directions (Euclidean
+    inner product over array entries): v_bar = J^T f_bar for f = J v.
+
+    <f_bar, drho> = g sum_kappa w_kappa tr(Gamma_kappa B_kappa) with
+    B_kappa = Psi^H diag(f_bar) Psi; moving L and the mu' constraint across
+    gives Y_kappa = L_kappa o B_kappa - (T / D) diag(L_kappa), T = sum_kappa
+    w_kappa sum_i L_ii B_ii, D = sum_kappa w_kappa sum_i L_ii (the same
+    traceless projection as the forward: the map is self-adjoint), then
+      dV_bar = w g sum_kappa w_kappa diag(Psi_kappa Y_kappa Psi_kappa^H),
+      v_bar = V_H[dV_bar] + f_x dV_bar - f_bar.
+    Fbar: (K, N_g).  Returns v_bar (K, N_g)."""
+    Fbar = np.asarray(Fbar, dtype=np.float64)
+    g, w = system.g, system.w
+    mu = solve_mu_kpoints(system.eps, system.k_weights, system.n_electrons, system.kT, g)
+    L = [loewner(e, mu, system.kT) for e in system.eps]
+    fx = lda_fx(system.rho)
+    den = sum(wk * float(np.sum(np.diag(Lk))) for wk, Lk in zip(system.k_weights, L))
+    vbar = np.zeros_like(Fbar)
+    for k in range(Fbar.shape[0]):
+        B = []
+        for psi in system.psi:
+            Bk = psi.conj().T @ (Fbar[k][:, None] * psi)
+            B.append(0.5 * (Bk + Bk.conj().T))
+        T = sum(wk * float(np.dot(np.diag(Lk), np.diag(Bk).real))
+                for wk, Lk, Bk in zip(system.k_weights, L, B))
+        dvbar = np.zeros(Fbar.shape[1])
+        for psi, wk, Lk, Bk in zip(system.psi, system.k_weights, L, B):
+            Y = Lk * Bk - (T / den) * np.diag(np.diag(Lk))
+            dvbar += w * g * wk * np.einsum("ri,ri->r", psi @ Y, psi.conj()).real
+        vbar[k] = hartree(dvbar, system.n, system.h, system.poisson) + fx * dvbar - Fbar[k]
+    return vbar
 
 
 # ---------------------------------------------------------------------------

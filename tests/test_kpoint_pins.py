@@ -13,6 +13,9 @@
   <dV_b, drho_a> (self-adjoint chi_0), and invariance under a phase per state
   (Psi_kappa -> Psi_kappa diag(e^{i phi})) and under complex conjugation of
   every Psi (the time-reversed points -kappa).
+* Adjoint (oracle.backward_kpoints): dot-product test <f_bar, J v> =
+  <J^T f_bar, v> with J from gateaux_kpoints, and one real point with weight
+  1 against the pinned real adjoint (oracle.backward).
 * The adaptive-rank LRDM step on a BZ-sampled system (oracle.lrdm_krylov_step
   with the k-point derivative) against the Krylov space of the k-point
   Gateaux map and an lstsq solve over it.
@@ -152,3 +155,30 @@ def test_krylov_step_on_kpoints_matches_krylov_least_squares(kp):
     JB = np.stack(Kr[1:], axis=1)
     b, *_ = np.linalg.lstsq(np.sqrt(w) * JB, np.sqrt(w) * R, rcond=None)
     assert rel_err(out["delta"], B @ b) < 1e-8
+
+
+def test_adjoint_dot_product(kp):
+    ks = _system(kp)
+    rng = workloads.rng_for(60, 9)
+    V = kp["V"]
+    Fbar = rng.standard_normal(V.shape)
+    F = oracle.gateaux_kpoints(ks, V)["F"]
+    vbar = oracle.backward_kpoints(ks, Fbar)
+    lhs = float(np.sum(Fbar * F))
+    rhs = float(np.sum(vbar * V))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1e-30)
+
+
+def test_adjoint_single_real_point_equals_real_adjoint():
+    cfg = workloads.random_system(62, (8, 7, 6), 24, 26.0, 0.02, 3)
+    mu = oracle.solve_mu(cfg["eps"], cfg["n_electrons"], cfg["kT"], 2.0)
+    ks = oracle.KpointSystem(n=cfg["n"], h=cfg["h"], psi=[cfg["psi"][0].astype(np.complex128)],
+                             eps=cfg["eps"], k_weights=[1.0], rho=np.zeros(336),
+                             n_electrons=cfg["n_electrons"], kT=cfg["kT"], g=2.0)
+    ks.rho = oracle.density_kpoints(ks, mu, cfg["rho_floor"])
+    real = oracle.System(n=cfg["n"], h=cfg["h"], psi=cfg["psi"], eps=cfg["eps"], rho=[ks.rho],
+                         n_electrons=cfg["n_electrons"], kT=cfg["kT"], g=2.0)
+    Fbar = workloads.rng_for(62, 1).standard_normal(cfg["V"].shape)
+    a = oracle.backward_kpoints(ks, Fbar[:, 0])
+    b = oracle.backward(real, Fbar, V=cfg["V"])["vbar"]
+    assert rel_err(a, b[:, 0]) < 1e-12
