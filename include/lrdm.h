@@ -344,9 +344,11 @@ void lrdm_lrdma_destroy(lrdm_lrdma* a);
  * the density is diag(C M C^T) with M = [[Re G, Im G], [-Im G, Re G]],
  * G = L o (X - mu' I).  A k-point context serves lrdm_kp_gateaux,
  * lrdm_apply, lrdm_krylov_step and lrdm_lrdma_step (sys 0, grid functions of
- * n = N_g values), lrdm_get_mu, lrdm_get_density, lrdm_get_tuning,
- * lrdm_status_query, lrdm_profile_* and lrdm_destroy; lrdm_gateaux_batch,
- * lrdm_backward and lrdm_get_projection return LRDM_ERR_UNSUPPORTED for it.
+ * n = N_g values), lrdm_backward (v_bar of the last lrdm_kp_gateaux call,
+ * f_bar / v_bar [K][N_g]; eps_bar / occ_bar must be NULL, else
+ * LRDM_ERR_UNSUPPORTED), lrdm_get_mu, lrdm_get_density, lrdm_get_tuning,
+ * lrdm_status_query, lrdm_profile_* and lrdm_destroy; lrdm_gateaux_batch and
+ * lrdm_get_projection return LRDM_ERR_UNSUPPORTED for it.
  * ------------------------------------------------------------------------- */
 typedef struct lrdm_kpoint_system {
   int n[3];                       /* periodic grid                                 */

@@ -612,6 +612,15 @@ class KpContext:
         """Launch shape of the tensor-core contractions (defaults or autotuned)."""
         return lrdm_get_tuning(self.handle)
 
+    def backward(self, fbar, out=None, stream=None):
+        """v_bar = J^T f_bar for the most recent gateaux call (lrdm_backward);
+        fbar, v_bar: (K, N_g) in the io dtype."""
+        assert fbar.is_contiguous() and fbar.dtype == self.io_dtype
+        vbar = out if out is not None else self.torch.empty_like(fbar)
+        _check("lrdm_backward", lrdm_backward(self.handle, [fbar.data_ptr()], [vbar.data_ptr()],
+                                              None, None, self._stream(stream)))
+        return vbar
+
     def krylov_step(self, R, s_tol=0.3, r_max=8, alpha=-1.0, rho=None, stream=None):
         """The paper's adaptive-rank LRDM step (lrdm_krylov_step) on this
         BZ-sampled system.  R: (N_g,) in the io dtype; rho (same shape) is

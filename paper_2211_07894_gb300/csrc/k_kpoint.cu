@@ -430,6 +430,27 @@ __global__ void k_kp_sum(KpSumArgs A, const void* __restrict__ v, int io, long l
   }
 }
 
+// out[k][r] (compute type, row stride ld) = sum_kappa part_kappa[k][r]
+// (A given: FP32 contributions) or drho[k][r] (FP64 accumulator); zero for
+// N_g <= r < ld.
+__global__ void k_kp_collect(KpSumArgs A, int use_parts, const double* __restrict__ drho, long long Ng,
+                             long long ld, long long tot, void* __restrict__ out, int fp64) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / ld, r = e - k * ld;
+    double d = 0.0;
+    if (r < Ng) {
+      const long long o = k * Ng + r;
+      if (use_parts)
+        for (int q = 0; q < A.nk; ++q) d += (double)A.part[q][o];
+      else
+        d = drho[o];
+    }
+    if (fp64) static_cast<double*>(out)[e] = d;
+    else static_cast<float*>(out)[e] = (float)d;
+  }
+}
+
 inline unsigned kp_grid(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152LL * 32) b = 152LL * 32;
@@ -528,6 +549,16 @@ cudaError_t launch_kp_scale_tc(const float* P, int nsplit, int K, int ns, int ld
   dim3 grid((unsigned)((ld / 4 + 127) / 128), (unsigned)ld, (unsigned)K);
   k_kp_scale_tc<<<grid, 128, 0, st>>>(P, nsplit, K, ns, ld, L, dmu, layout, out,
                                       static_cast<__nv_bfloat16*>(out_lo));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kp_collect(const KpSumArgs* A, const double* drho, int K, long long Ng, long long ld,
+                              void* out, int fp64, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  const long long tot = (long long)K * ld;
+  KpSumArgs a{};
+  if (A) a = *A;
+  k_kp_collect<<<kp_grid(tot, 256), 256, 0, st>>>(a, A ? 1 : 0, drho, Ng, ld, tot, out, fp64);
   return cudaGetLastError();
 }
 

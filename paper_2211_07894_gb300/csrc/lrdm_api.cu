@@ -136,6 +136,9 @@ lrdm_status validate_system(const lrdm_system& s, const lrdm_options& o) {
 
 // Poisson: batched real <-> half-complex transforms over k_max fields, the
 // symbol table and the transform buffers of system S.
+lrdm_status kp_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
+                        double* const* eps_bar, double* const* occ_bar, cudaStream_t st);
+
 lrdm_status setup_poisson(lrdm_ctx* ctx, SysState& S, cudaStream_t st) {
   const lrdm_options& o = ctx->opt;
   const int fp64 = o.prec == LRDM_FP64;
@@ -1147,8 +1150,8 @@ lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int i
 
 lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
                           double* const* eps_bar, double* const* occ_bar, void* stream) {
-  if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!ctx || !f_bar || !v_bar) return LRDM_ERR_INVALID_ARG;
+  if (ctx->kp) return kp_backward(ctx, f_bar, v_bar, eps_bar, occ_bar, static_cast<cudaStream_t>(stream));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int prec = ctx->opt.prec;
   const int fp64 = prec == LRDM_FP64;
@@ -1368,6 +1371,120 @@ lrdm_status solve_mu_kp_host(const std::vector<std::vector<double>>& eps, const 
     else hi = mid;
   }
   *mu = 0.5 * (lo + hi);
+  return LRDM_OK;
+}
+
+// The k-point response of the weights in S.a ([K][N_g,pad], compute type):
+// per point P = Psi^H diag(a_k) Psi, mu'_k from the BZ-averaged traceless
+// condition (into S.dmu, and dmu_out when given), Gamma = L o (P - mu' I),
+// and factor * w_kappa diag(Psi Gamma Psi^H) into the per-point FP32
+// contributions (tensor cores) or the FP64 accumulator (CUDA cores).  The
+// forward passes a = w dV and factor g; the adjoint a = fbar and factor w g
+// (the map is self-adjoint, the same traceless projection applies).
+lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cudaStream_t st) {
+  SysState& S = ctx->sys[0];
+  const int prec = ctx->opt.prec;
+  const int fp64 = prec == LRDM_FP64;
+  const bool tc = is_tc(prec);
+  const int ns = ctx->kp_ns, nk = ctx->kp_nk;
+  if (tc) {
+    ctx->tc_entries.clear();
+    for (int q = 0; q < nk; ++q) {
+      TcEntry x;
+      x.dev_base = ctx->tc_dev;
+      x.pid = ctx->kp_pid[q];
+      x.host = &ctx->tc_host[x.pid];
+      x.K = K;
+      x.X = ctx->kp_ch[q].Xpart;
+      ctx->tc_entries.push_back(x);
+    }
+    LRDM_CK(tc_group(ctx, 1, 0, st));
+  } else {
+    int pi = prof_begin(ctx, 1, st);
+    for (int q = 0; q < nk; ++q)
+      LRDM_CU(launch_kp_gemm1(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, S.a, S.Ng_pad, K, ctx->kp_Xr[q],
+                              ctx->kp_Xi[q], ctx->kp_nsplit, st));
+    prof_end(ctx, pi, st);
+    count(ctx, nk);
+  }
+  KpDmuArgs A{};
+  for (int q = 0; q < nk; ++q) {
+    A.Xr[q] = tc ? ctx->kp_ch[q].Xpart : ctx->kp_Xr[q];
+    A.L[q] = ctx->kp_L[q];
+    A.kw[q] = ctx->kp_w[q];
+  }
+  A.nk = nk;
+  A.ns = ns;
+  A.K = K;
+  A.nsplit = ctx->kp_nsplit;
+  A.fp64 = fp64;
+  A.ld = tc ? ctx->kp_ch[0].ns_pad : ns;
+  A.stacked = tc ? 1 : 0;
+  LRDM_CU(launch_kp_dmu(A, S.dmu, dmu_out, st));
+  count(ctx, 1);
+  if (tc) {
+    const int layout = prec == LRDM_BF16X3 ? 2 : 1;
+    ctx->tc_entries.clear();
+    for (int q = 0; q < nk; ++q) {
+      const Channel& c = ctx->kp_ch[q];
+      LRDM_CU(launch_kp_scale_tc(static_cast<const float*>(c.Xpart), 1, K, ns, c.ns_pad, ctx->kp_L[q], S.dmu,
+                                 layout, c.Xpp, c.Xpp_lo, st));
+      TcEntry x;
+      x.dev_base = ctx->tc_dev;
+      x.pid = ctx->kp_pid[q];
+      x.host = &ctx->tc_host[x.pid];
+      x.K = K;
+      x.factor = factor * ctx->kp_w[q];
+      x.out = ctx->kp_out[q];
+      x.out_stride = S.Ng;
+      ctx->tc_entries.push_back(x);
+    }
+    count(ctx, nk);
+    LRDM_CK(tc_group(ctx, 2, 0, st));
+  } else {
+    LRDM_CU(cudaMemsetAsync(ctx->kp_drho, 0, (size_t)K * S.Ng * sizeof(double), st));
+    for (int q = 0; q < nk; ++q)
+      LRDM_CU(launch_kp_scale(fp64, ctx->kp_Xr[q], ctx->kp_Xi[q], ctx->kp_nsplit, K, ns, ctx->kp_L[q], S.dmu,
+                              ctx->kp_Yr[q], ctx->kp_Yi[q], st));
+    int pi = prof_begin(ctx, 2, st);
+    for (int q = 0; q < nk; ++q)
+      LRDM_CU(launch_kp_gemm2(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, ctx->kp_Yr[q], ctx->kp_Yi[q], K,
+                              factor * ctx->kp_w[q], ctx->kp_drho, st));
+    prof_end(ctx, pi, st);
+    count(ctx, 2 * nk);
+  }
+  return LRDM_OK;
+}
+
+// Adjoint of lrdm_kp_gateaux with respect to the directions: the response of
+// the weights fbar with factor w g, then vbar = V_H[dVbar] + f_x dVbar - fbar.
+// Eigenvalue / occupation gradients are not defined for k-point contexts.
+lrdm_status kp_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
+                        double* const* eps_bar, double* const* occ_bar, cudaStream_t st) {
+  if ((eps_bar && (eps_bar[0] || eps_bar[1])) || (occ_bar && (occ_bar[0] || occ_bar[1])))
+    return LRDM_ERR_UNSUPPORTED;
+  SysState& S = ctx->sys[0];
+  const int K = S.last_K;
+  if (K < 0) return LRDM_ERR_INVALID_ARG;      // no forward call yet
+  if (K == 0) return LRDM_OK;
+  if (!f_bar[0] || !v_bar[0]) return LRDM_ERR_INVALID_ARG;
+  const int fp64 = ctx->opt.prec == LRDM_FP64;
+  const int io = ctx->opt.io_dtype;
+  LRDM_CU(launch_scale_weights(f_bar[0], io, K, 1, S.Ng, S.Ng_pad, 1.0, S.a, fp64, st));
+  LRDM_CK(kp_response(ctx, K, S.w * S.g, nullptr, st));
+  if (is_tc(ctx->opt.prec)) {
+    KpSumArgs B{};
+    for (int q = 0; q < ctx->kp_nk; ++q) B.part[q] = ctx->kp_out[q];
+    B.nk = ctx->kp_nk;
+    LRDM_CU(launch_kp_collect(&B, nullptr, K, S.Ng, S.Ng_pad, S.a, fp64, st));
+  } else {
+    LRDM_CU(launch_kp_collect(nullptr, ctx->kp_drho, K, S.Ng, S.Ng_pad, S.a, fp64, st));
+  }
+  LRDM_CU(launch_spin_sum_padded(S.a, K, 1, S.Ng, S.Ng_pad, S.fft_real, fp64, st));
+  LRDM_CK(hartree(ctx, S, K, st));
+  LRDM_CU(launch_adjoint_potential(S.a, S.fft_real, S.ch[0].fx, S.ch[0].fx, f_bar[0], io, K, 1, S.Ng,
+                                   S.Ng_pad, v_bar[0], fp64, st));
+  count(ctx, 5);
   return LRDM_OK;
 }
 
@@ -1591,92 +1708,25 @@ lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, do
   }
   if (!v || !f_out) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int prec = ctx->opt.prec;
-  const int fp64 = prec == LRDM_FP64;
-  const bool tc = is_tc(prec);
+  const int fp64 = ctx->opt.prec == LRDM_FP64;
   const int io = ctx->opt.io_dtype;
-  const int ns = ctx->kp_ns, nk = ctx->kp_nk;
   // dV_k = V_H[v_k] + f_x v_k;  a_k = w dV_k (zero in the grid padding)
   LRDM_CU(launch_spin_sum(v, io, K, 1, S.Ng, S.fft_real, fp64, st));
   LRDM_CK(hartree(ctx, S, K, st));
   LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[0].fx, K, 1, S.Ng, S.Ng_pad, S.w, S.a,
                             fp64, st));
-  // X_kappa = Psi_kappa^H diag(a_k) Psi_kappa (tensor cores: the stacked Gram P_kappa)
-  if (tc) {
-    ctx->tc_entries.clear();
-    for (int q = 0; q < nk; ++q) {
-      TcEntry x;
-      x.dev_base = ctx->tc_dev;
-      x.pid = ctx->kp_pid[q];
-      x.host = &ctx->tc_host[x.pid];
-      x.K = K;
-      x.X = ctx->kp_ch[q].Xpart;
-      ctx->tc_entries.push_back(x);
-    }
-    LRDM_CK(tc_group(ctx, 1, 0, st));
-  } else {
-    int pi = prof_begin(ctx, 1, st);
-    for (int q = 0; q < nk; ++q)
-      LRDM_CU(launch_kp_gemm1(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, S.a, S.Ng, K, ctx->kp_Xr[q],
-                              ctx->kp_Xi[q], ctx->kp_nsplit, st));
-    prof_end(ctx, pi, st);
-    count(ctx, nk);
-  }
-  // mu' from the BZ-averaged traceless condition
-  KpDmuArgs A{};
-  for (int q = 0; q < nk; ++q) {
-    A.Xr[q] = tc ? ctx->kp_ch[q].Xpart : ctx->kp_Xr[q];
-    A.L[q] = ctx->kp_L[q];
-    A.kw[q] = ctx->kp_w[q];
-  }
-  A.nk = nk;
-  A.ns = ns;
-  A.K = K;
-  A.nsplit = ctx->kp_nsplit;
-  A.fp64 = fp64;
-  A.ld = tc ? ctx->kp_ch[0].ns_pad : ns;
-  A.stacked = tc ? 1 : 0;
-  LRDM_CU(launch_kp_dmu(A, S.dmu, dmu_out, st));
-  count(ctx, 1);
-  // drho_k = g sum_kappa w_kappa diag(Psi L o (X - mu' I) Psi^H);  f_k = drho_k - v_k
-  if (tc) {
-    const int layout = prec == LRDM_BF16X3 ? 2 : 1;
-    ctx->tc_entries.clear();
-    for (int q = 0; q < nk; ++q) {
-      const Channel& c = ctx->kp_ch[q];
-      LRDM_CU(launch_kp_scale_tc(static_cast<const float*>(c.Xpart), 1, K, ns, c.ns_pad, ctx->kp_L[q], S.dmu,
-                                 layout, c.Xpp, c.Xpp_lo, st));
-      TcEntry x;
-      x.dev_base = ctx->tc_dev;
-      x.pid = ctx->kp_pid[q];
-      x.host = &ctx->tc_host[x.pid];
-      x.K = K;
-      x.factor = S.g * ctx->kp_w[q];
-      x.out = ctx->kp_out[q];
-      x.out_stride = S.Ng;
-      ctx->tc_entries.push_back(x);
-    }
-    count(ctx, nk);
-    LRDM_CK(tc_group(ctx, 2, 0, st));
-    KpSumArgs B{};
-    for (int q = 0; q < nk; ++q) B.part[q] = ctx->kp_out[q];
-    B.nk = nk;
-    LRDM_CU(launch_kp_sum(B, v, io, (long long)K * S.Ng, f_out, st));
-    count(ctx, 1);
-  } else {
-    LRDM_CU(cudaMemsetAsync(ctx->kp_drho, 0, (size_t)K * S.Ng * sizeof(double), st));
-    for (int q = 0; q < nk; ++q)
-      LRDM_CU(launch_kp_scale(fp64, ctx->kp_Xr[q], ctx->kp_Xi[q], ctx->kp_nsplit, K, ns, ctx->kp_L[q], S.dmu,
-                              ctx->kp_Yr[q], ctx->kp_Yi[q], st));
-    int pi = prof_begin(ctx, 2, st);
-    for (int q = 0; q < nk; ++q)
-      LRDM_CU(launch_kp_gemm2(fp64, ctx->kp_pr[q], ctx->kp_pi[q], ns, S.Ng, ctx->kp_Yr[q], ctx->kp_Yi[q], K,
-                              S.g * ctx->kp_w[q], ctx->kp_drho, st));
-    prof_end(ctx, pi, st);
-    LRDM_CU(launch_kp_finish(ctx->kp_drho, v, io, (long long)K * S.Ng, f_out, st));
-    count(ctx, 2 * nk + 1);
-  }
   count(ctx, 3);
+  // drho_k = g sum_kappa w_kappa diag(Psi L o (X - mu' I) Psi^H);  f_k = drho_k - v_k
+  LRDM_CK(kp_response(ctx, K, S.g, dmu_out, st));
+  if (is_tc(ctx->opt.prec)) {
+    KpSumArgs B{};
+    for (int q = 0; q < ctx->kp_nk; ++q) B.part[q] = ctx->kp_out[q];
+    B.nk = ctx->kp_nk;
+    LRDM_CU(launch_kp_sum(B, v, io, (long long)K * S.Ng, f_out, st));
+  } else {
+    LRDM_CU(launch_kp_finish(ctx->kp_drho, v, io, (long long)K * S.Ng, f_out, st));
+  }
+  count(ctx, 1);
   S.last_K = K;
   return LRDM_OK;
 }

@@ -186,6 +186,10 @@ cudaError_t launch_kp_copy(int fp64, const void* src, int io, int ld, long long 
 // (TF32) or 2 (BF16 hi/lo), [K][ld][ld]
 cudaError_t launch_kp_scale_tc(const float* P, int nsplit, int K, int ns, int ld, const double* L,
                                const double* dmu, int layout, void* out, void* out_lo, cudaStream_t st);
+// out[k][r] (compute type, row stride ld, zero padding) = sum_kappa
+// A->part[kappa][k][r] (A given) or drho[k][r]
+cudaError_t launch_kp_collect(const KpSumArgs* A, const double* drho, int K, long long Ng, long long ld,
+                              void* out, int fp64, cudaStream_t st);
 // f = sum_kappa part_kappa - v (io dtype)
 cudaError_t launch_kp_sum(const KpSumArgs& A, const void* v, int io, long long n, void* f,
                           cudaStream_t st);

@@ -271,3 +271,59 @@ def test_kpoint_lrdma_steps_follow_oracle(lib, cfg):
         R = state.R_lin + workloads.smooth_field(N, cfg["h"], 0.002, rng)
     print(f"k-point LRDMA events {events}")
     gpu.close()
+
+
+def test_kpoint_many_points_split_launches(lib):
+    """20 k-points (more than the 16 problems of one grouped tensor-core
+    launch: two launches per contraction) and the 32-point maximum, small
+    sizes; 33 points are refused."""
+    from paper_2211_07894_gb300 import KpContext, LrdmError
+    for nk, prec in ((20, "bf16x3"), (32, "fp64")):
+        c = workloads.kpoint_system(71, (8, 7, 6), 20, nk, 22.0, 0.02, 2)
+        ctx, psi_seen = _device(c, prec, k_max=2)
+        ks, mu = _oracle(c, psi_seen)
+        assert abs(ctx.mu() - mu) < 1e-12
+        ks.rho = ctx.density().double().cpu().numpy()
+        V = torch.as_tensor(c["V"], dtype=DT[prec], device="cuda")
+        F, _ = ctx.gateaux(V)
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        ref = oracle.gateaux_kpoints(ks, V.double().cpu().numpy())
+        err = per_direction_rel_err(F.double().cpu().numpy(), ref["F"])
+        print(f"{nk} k-points {prec}: f err {err:.2e}")
+        assert err < TOL[prec]
+        ctx.close()
+    c = workloads.kpoint_system(72, (6, 6, 6), 8, 33, 8.0, 0.02, 1)
+    p = [torch.as_tensor(np.ascontiguousarray(x.real), device="cuda") for x in c["psi"]]
+    e = [torch.as_tensor(x, device="cuda") for x in c["eps"]]
+    with pytest.raises(LrdmError) as ex:
+        KpContext(c["n"], c["h"], p, p, e, c["k_weights"], 8.0, 0.02)
+    assert ex.value.code == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+def test_kpoint_backward_matches_oracle(lib, cfg, prec):
+    """lrdm_backward on a k-point context (v_bar of the last forward call)
+    against oracle.backward_kpoints, and the dot-product identity on the
+    device's own forward and adjoint."""
+    ctx, psi_seen = _device(cfg, prec)
+    ks, _ = _oracle(cfg, psi_seen)
+    ks.rho = ctx.density().double().cpu().numpy()
+    io = DT[prec]
+    V = torch.as_tensor(cfg["V"], dtype=io, device="cuda")
+    fbar = torch.as_tensor(workloads.rng_for(70, 13).standard_normal(cfg["V"].shape), dtype=io, device="cuda")
+    F, _ = ctx.gateaux(V)
+    vbar = ctx.backward(fbar)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    ref = oracle.backward_kpoints(ks, fbar.double().cpu().numpy())
+    err = per_direction_rel_err(vbar.double().cpu().numpy(), ref)
+    lhs = float((fbar.double() * F.double()).sum())
+    rhs = float((vbar.double() * V.double()).sum())
+    print(f"k-point adjoint {prec}: v_bar err {err:.2e}, dot-product rel {abs(lhs - rhs) / abs(lhs):.2e}")
+    assert err < TOL[prec]
+    assert abs(lhs - rhs) <= 10 * TOL[prec] * abs(lhs)
+    from paper_2211_07894_gb300 import binding
+    e = torch.empty(NS, dtype=torch.float64, device="cuda")
+    assert binding.lrdm_backward(ctx.handle, [fbar.data_ptr()], [vbar.data_ptr()], [e.data_ptr(), 0],
+                                 None) == 9       # no eigenvalue gradients for k-point contexts
