@@ -71,6 +71,8 @@ def parse():
                    help="skip the Brillouin-zone-sampled (k-point) leg")
     p.add_argument("--kpoint-only", action="store_true",
                    help="run only the k-point leg and print its JSON")
+    p.add_argument("--jsonl", default=None,
+                   help="also append the result line (with a UTC timestamp and the host) to this JSONL file")
     p.add_argument("--compare-fp64", action="store_true",
                    help="time the plain FP64 GPU form (torch, Psi X' materialised) and the "
                         "library's FP64 path on a 48^3 slice instead of the benchmark step")
@@ -327,6 +329,16 @@ def time_kpoint_oracle():
     return {"value": 1.0 / (dt * scale), "unit": "GD/s", "cores": cpu_cores(), "kind": "oracle",
             "sample": f"oracle.gateaux_kpoints, K=1, {KP_NK} k-points x N_s={KP_NS}, grid {n[0]}^3 "
                       f"(1/{int(scale)} of the {KP_GRID[0]}^3 rows); GD/s scaled by the row ratio"}
+
+
+def append_jsonl(path, line):
+    """One run record per line: the bench line plus when and where it ran."""
+    import platform
+    rec = dict(line)
+    rec["time_utc"] = time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
+    rec["host"] = {"machine": platform.machine(), "cores": os.cpu_count(), "python": platform.python_version()}
+    with open(path, "a") as fh:
+        fh.write(json.dumps(rec) + "\n")
 
 
 def cpu_cores():
@@ -742,6 +754,8 @@ def main():
                                  "gemm1_launches_per_step": prof["gemm1_launches"] / steps,
                                  "gemm2_launches_per_step": prof["gemm2_launches"] / steps}}
         print(json.dumps(line), flush=True)
+        if args.jsonl:
+            append_jsonl(args.jsonl, line)
     ctx.close()
     if dist:
         dist.destroy_process_group()

@@ -691,18 +691,24 @@ class Lrdma:
 
 def gateaux_function():
     """torch.autograd.Function whose forward is lrdm_gateaux_batch on one system
+    (a Context; V (K, nspin, N_g)) or lrdm_kp_gateaux (a KpContext; V (K, N_g))
     and whose backward is lrdm_backward (the hand-written adjoint)."""
     import torch
 
     class LrdmResponse(torch.autograd.Function):
         @staticmethod
         def forward(fctx, lctx, V):
-            (F,), _ = lctx.gateaux([V.detach().contiguous()])
             fctx.lctx = lctx
+            if isinstance(lctx, KpContext):
+                F, _ = lctx.gateaux(V.detach().contiguous())
+                return F
+            (F,), _ = lctx.gateaux([V.detach().contiguous()])
             return F
 
         @staticmethod
         def backward(fctx, gF):
+            if isinstance(fctx.lctx, KpContext):
+                return None, fctx.lctx.backward(gF.contiguous())
             vbar, _, _ = fctx.lctx.backward([gF.contiguous()], want_eps=False)
             return None, vbar[0]
 

@@ -73,7 +73,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", LIB] + objs + [
-            "-L" + libdir, "-lcufft", "-Xlinker", "-rpath=" + libdir]
+            "-L" + libdir, "-lcufft", "-ldl", "-Xlinker", "-rpath=" + libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

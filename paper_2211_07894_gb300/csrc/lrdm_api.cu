@@ -315,6 +315,7 @@ lrdm_status hartree_body(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
 }
 
 lrdm_status hartree(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st) {
+  NvtxRange nvtx_("poisson");
   int pi = prof_begin(ctx, 3, st);
   lrdm_status rc = hartree_body(ctx, S, K, st);
   prof_end(ctx, pi, st);
@@ -357,6 +358,7 @@ lrdm_status gemm2_simt(lrdm_ctx* ctx, SysState& S, int c, int K, double factor, 
 
 // One grouped tensor-core launch over the entries collected in ctx->tc_entries.
 lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
+  NvtxRange nvtx_("contraction (tensor cores)");
   const int n = (int)ctx->tc_entries.size();
   if (n == 0) return LRDM_OK;
   int pi = prof_begin(ctx, gemm, st);
@@ -699,6 +701,7 @@ const char* lrdm_status_string(lrdm_status s) {
 
 lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
                         const lrdm_options* opt, void* stream) {
+  NvtxRange nvtx_("lrdm_create");
   if (!out) return LRDM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!sys || nsys < 1) return LRDM_ERR_INVALID_ARG;
@@ -800,6 +803,7 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
 
 lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K,
                                void* const* f_out, double* dmu_out, void* stream) {
+  NvtxRange nvtx_("lrdm_gateaux_batch");
   if (ctx && ctx->kp) return LRDM_ERR_UNSUPPORTED;
   if (!ctx || !v || !K || !f_out) return LRDM_ERR_INVALID_ARG;
   for (int s = 0; s < ctx->nsys; ++s) {
@@ -849,6 +853,7 @@ lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K
 lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, const void* f, int K,
                        double alpha, void* rho_inout, double* coeff_out, double* s_rel_out,
                        void* stream) {
+  NvtxRange nvtx_("lrdm_apply");
   if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !v || !f) return LRDM_ERR_INVALID_ARG;
   if (K < 1 || K > KMAX_LIMIT) return LRDM_ERR_INVALID_ARG;
   if (!isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
@@ -864,6 +869,7 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
 lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol, int r_max,
                              double alpha, void* rho_inout, void* U, void* T, double* coeff_out,
                              double* s_rel_out, int* rank_out, double* r_norm_out, void* stream) {
+  NvtxRange nvtx_("lrdm_krylov_step");
   if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !U || !T) return LRDM_ERR_INVALID_ARG;
   if (r_max < 1 || r_max > KMAX_LIMIT || !(s_tol >= 0.0) || !isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1043,6 +1049,7 @@ void lrdm_lrdma_destroy(lrdm_lrdma* a) {
 lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R, void* rho_inout,
                             const lrdm_lrdma_params* params, lrdm_lrdma_report* report,
                             void* stream) {
+  NvtxRange nvtx_("lrdm_lrdma_step");
   if (!a || !ctx || sys < 0 || sys >= ctx->nsys || !R) return LRDM_ERR_INVALID_ARG;
   lrdm_lrdma_params p;
   if (params) p = *params;
@@ -1150,6 +1157,7 @@ lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int i
 
 lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
                           double* const* eps_bar, double* const* occ_bar, void* stream) {
+  NvtxRange nvtx_("lrdm_backward");
   if (!ctx || !f_bar || !v_bar) return LRDM_ERR_INVALID_ARG;
   if (ctx->kp) return kp_backward(ctx, f_bar, v_bar, eps_bar, occ_bar, static_cast<cudaStream_t>(stream));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1382,6 +1390,7 @@ lrdm_status solve_mu_kp_host(const std::vector<std::vector<double>>& eps, const 
 // forward passes a = w dV and factor g; the adjoint a = fbar and factor w g
 // (the map is self-adjoint, the same traceless projection applies).
 lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cudaStream_t st) {
+  NvtxRange nvtx_("k-point response");
   SysState& S = ctx->sys[0];
   const int prec = ctx->opt.prec;
   const int fp64 = prec == LRDM_FP64;
@@ -1639,6 +1648,7 @@ extern "C" {
 
 lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const lrdm_options* opt,
                            void* stream) {
+  NvtxRange nvtx_("lrdm_kp_create");
   if (!out) return LRDM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!sys || sys->nk < 1 || sys->nk > KP_MAX || sys->ns < 1 || sys->ld_psi < sys->ns)
@@ -1699,6 +1709,7 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
 
 lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, double* dmu_out,
                             void* stream) {
+  NvtxRange nvtx_("lrdm_kp_gateaux");
   if (!ctx || !ctx->kp) return LRDM_ERR_INVALID_ARG;
   SysState& S = ctx->sys[0];
   if (K < 0 || K > S.kmax) return LRDM_ERR_INVALID_ARG;

@@ -9,10 +9,21 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lrdm.h"
 #include "tc_problem.h"
 
 namespace lrdm {
+
+// NVTX range for the profilers' timelines (one per API call and per phase of
+// the forward / adjoint); no cost beyond a call when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Bits of the sticky device status word.
 enum : int {

@@ -327,3 +327,17 @@ def test_kpoint_backward_matches_oracle(lib, cfg, prec):
     e = torch.empty(NS, dtype=torch.float64, device="cuda")
     assert binding.lrdm_backward(ctx.handle, [fbar.data_ptr()], [vbar.data_ptr()], [e.data_ptr(), 0],
                                  None) == 9       # no eigenvalue gradients for k-point contexts
+
+
+def test_kpoint_autograd_function(lib, cfg):
+    """gateaux_function on a k-point context: torch autograd through the
+    hand-written adjoint satisfies <fbar, F> = <V.grad, V> (F linear in V)."""
+    from paper_2211_07894_gb300 import gateaux_function
+    ctx, _ = _device(cfg, "fp64")
+    V = torch.as_tensor(cfg["V"], dtype=torch.float64, device="cuda").requires_grad_(True)
+    fbar = torch.as_tensor(workloads.rng_for(70, 14).standard_normal(cfg["V"].shape), device="cuda")
+    F = gateaux_function().apply(ctx, V)
+    (F * fbar).sum().backward()
+    lhs = float((fbar * F.detach()).sum())
+    rhs = float((V.grad * V.detach()).sum())
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
