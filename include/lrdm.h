@@ -325,6 +325,20 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
                             const lrdm_lrdma_params* p, lrdm_lrdma_report* report, void* stream);
 /* Drops the history (e.g. at a restart). */
 lrdm_status lrdm_lrdma_clear(lrdm_lrdma* a);
+
+/* Checkpoint / resume of the history (no counterpart in the paper, which
+ * keeps no state across runs).  get_state returns the kept rank m and the
+ * flags (LRDM_LRDMA_CLEAR_NEXT: a CT clearing is pending; LRDM_LRDMA_HAVE_LIN:
+ * R_lin holds the previous step's linear prediction).  export copies the m
+ * kept directions U ([m][n]), their derivatives T ([m][n]) and R_lin ([n]),
+ * io dtype, into the caller's buffers (host or device); import restores them
+ * (m <= capacity) together with the flags.  Both synchronise the stream. */
+#define LRDM_LRDMA_CLEAR_NEXT 1
+#define LRDM_LRDMA_HAVE_LIN 2
+lrdm_status lrdm_lrdma_get_state(const lrdm_lrdma* a, int* m, int* flags);
+lrdm_status lrdm_lrdma_export(const lrdm_lrdma* a, void* U, void* T, void* R_lin, void* stream);
+lrdm_status lrdm_lrdma_import(lrdm_lrdma* a, int m, int flags, const void* U, const void* T,
+                              const void* R_lin, void* stream);
 void lrdm_lrdma_destroy(lrdm_lrdma* a);
 
 /* ---------------------------------------------------------------------------

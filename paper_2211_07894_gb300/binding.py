@@ -64,7 +64,7 @@ EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_ap
            "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string",
            "lrdm_get_tuning", "lrdm_krylov_step", "lrdm_lrdma_default_params", "lrdm_lrdma_create",
            "lrdm_lrdma_step", "lrdm_lrdma_clear", "lrdm_lrdma_destroy", "lrdm_kp_create",
-           "lrdm_kp_gateaux"]
+           "lrdm_kp_gateaux", "lrdm_lrdma_get_state", "lrdm_lrdma_export", "lrdm_lrdma_import"]
 
 
 class lrdm_lrdma_params(ctypes.Structure):
@@ -135,6 +135,12 @@ def load(path: Optional[str] = None):
     lib.lrdm_lrdma_step.restype = c_int
     lib.lrdm_lrdma_clear.argtypes = [c_void_p]
     lib.lrdm_lrdma_clear.restype = c_int
+    lib.lrdm_lrdma_get_state.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int)]
+    lib.lrdm_lrdma_get_state.restype = c_int
+    lib.lrdm_lrdma_export.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.lrdm_lrdma_export.restype = c_int
+    lib.lrdm_lrdma_import.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.lrdm_lrdma_import.restype = c_int
     lib.lrdm_lrdma_destroy.argtypes = [c_void_p]
     lib.lrdm_lrdma_destroy.restype = None
     lib.lrdm_get_tuning.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
@@ -650,6 +656,7 @@ class Lrdma:
         import torch
         self.torch = torch
         code_io = DTYPE_F64 if io_dtype == torch.float64 else DTYPE_F32
+        self.n, self.io_dtype, self.w = int(n), io_dtype, float(w)
         h = c_void_p()
         _check("lrdm_lrdma_create", load().lrdm_lrdma_create(ctypes.byref(h), int(n), code_io,
                                                               float(w), int(capacity)))
@@ -676,6 +683,38 @@ class Lrdma:
 
     def clear(self):
         _check("lrdm_lrdma_clear", load().lrdm_lrdma_clear(self.handle))
+
+    def save(self, path):
+        """Writes the history (U, T, R_lin, rank and flags) to an .npz file."""
+        m, fl = c_int(), c_int()
+        _check("lrdm_lrdma_get_state", load().lrdm_lrdma_get_state(self.handle, ctypes.byref(m),
+                                                                    ctypes.byref(fl)))
+        dt = np.float64 if self.io_dtype == self.torch.float64 else np.float32
+        U = np.zeros((max(m.value, 1), self.n), dtype=dt)
+        T = np.zeros_like(U)
+        R = np.zeros(self.n, dtype=dt)
+        _check("lrdm_lrdma_export", load().lrdm_lrdma_export(self.handle, c_void_p(U.ctypes.data),
+                                                              c_void_p(T.ctypes.data),
+                                                              c_void_p(R.ctypes.data), c_void_p(0)))
+        np.savez(path, U=U[:m.value], T=T[:m.value], R_lin=R, m=m.value, flags=fl.value,
+                 n=self.n, w=self.w)
+
+    def load(self, path):
+        """Restores a history written by save() (same n and io dtype)."""
+        d = np.load(path)
+        dt = np.float64 if self.io_dtype == self.torch.float64 else np.float32
+        if int(d["n"]) != self.n:
+            raise ValueError("history of another grid size")
+        m = int(d["m"])
+        if m:
+            U = np.ascontiguousarray(d["U"], dtype=dt)
+            T = np.ascontiguousarray(d["T"], dtype=dt)
+        else:
+            U = T = np.zeros((1, self.n), dtype=dt)
+        R = np.ascontiguousarray(d["R_lin"], dtype=dt)
+        _check("lrdm_lrdma_import", load().lrdm_lrdma_import(self.handle, m, int(d["flags"]),
+                                                              c_void_p(U.ctypes.data), c_void_p(T.ctypes.data),
+                                                              c_void_p(R.ctypes.data), c_void_p(0)))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1032,6 +1032,43 @@ lrdm_status lrdm_lrdma_create(lrdm_lrdma** out, long long n, int io_dtype, doubl
   return LRDM_OK;
 }
 
+lrdm_status lrdm_lrdma_get_state(const lrdm_lrdma* a, int* m, int* flags) {
+  if (!a || !m || !flags) return LRDM_ERR_INVALID_ARG;
+  *m = a->m;
+  *flags = (a->clear_next ? LRDM_LRDMA_CLEAR_NEXT : 0) | (a->have_lin ? LRDM_LRDMA_HAVE_LIN : 0);
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_lrdma_export(const lrdm_lrdma* a, void* U, void* T, void* R_lin, void* stream) {
+  if (!a || !U || !T || !R_lin) return LRDM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vb = (size_t)a->n * io_size(a->io);
+  if (a->m > 0) {
+    LRDM_CU(cudaMemcpyAsync(U, a->U, a->m * vb, cudaMemcpyDefault, st));
+    LRDM_CU(cudaMemcpyAsync(T, a->T, a->m * vb, cudaMemcpyDefault, st));
+  }
+  LRDM_CU(cudaMemcpyAsync(R_lin, a->R_lin, vb, cudaMemcpyDefault, st));
+  return from_cuda(cudaStreamSynchronize(st));
+}
+
+lrdm_status lrdm_lrdma_import(lrdm_lrdma* a, int m, int flags, const void* U, const void* T,
+                              const void* R_lin, void* stream) {
+  if (!a || m < 0 || m > a->cap || (m > 0 && (!U || !T)) || !R_lin) return LRDM_ERR_INVALID_ARG;
+  if (flags & ~(LRDM_LRDMA_CLEAR_NEXT | LRDM_LRDMA_HAVE_LIN)) return LRDM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vb = (size_t)a->n * io_size(a->io);
+  if (m > 0) {
+    LRDM_CU(cudaMemcpyAsync(a->U, U, m * vb, cudaMemcpyDefault, st));
+    LRDM_CU(cudaMemcpyAsync(a->T, T, m * vb, cudaMemcpyDefault, st));
+  }
+  LRDM_CU(cudaMemcpyAsync(a->R_lin, R_lin, vb, cudaMemcpyDefault, st));
+  LRDM_CU(cudaStreamSynchronize(st));
+  a->m = m;
+  a->clear_next = (flags & LRDM_LRDMA_CLEAR_NEXT) != 0;
+  a->have_lin = (flags & LRDM_LRDMA_HAVE_LIN) != 0;
+  return LRDM_OK;
+}
+
 lrdm_status lrdm_lrdma_clear(lrdm_lrdma* a) {
   if (!a) return LRDM_ERR_INVALID_ARG;
   a->m = 0;
