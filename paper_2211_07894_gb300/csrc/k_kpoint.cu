@@ -61,7 +61,10 @@ __global__ void __launch_bounds__(256) k_kp_gemm1(const Tc* __restrict__ pr, con
   const Tc* aq = a + (long long)q * a_stride;
   const long long rb = (long long)split * rows_per;
   const long long re = min(Ng, rb + rows_per);
-  __shared__ Tc Ar[BK][T], Ai[BK][T], Br[BK][T], Bi[BK][T];
+  __shared__ __align__(16) Tc Ar[BK][T];
+  __shared__ __align__(16) Tc Ai[BK][T];
+  __shared__ __align__(16) Tc Br[BK][T];
+  __shared__ __align__(16) Tc Bi[BK][T];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   Tc sr[4][4], si[4][4];
 #pragma unroll
@@ -93,16 +96,10 @@ __global__ void __launch_bounds__(256) k_kp_gemm1(const Tc* __restrict__ pr, con
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       Tc xr[4], xi[4], yr[4], yi[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        xr[m] = Ar[kk][ty + 16 * m];
-        xi[m] = Ai[kk][ty + 16 * m];
-      }
-#pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        yr[n] = Br[kk][tx + 16 * n];
-        yi[n] = Bi[kk][tx + 16 * n];
-      }
+      ld4(&Ar[kk][4 * ty], xr);              // rows 4 ty .. 4 ty + 3
+      ld4(&Ai[kk][4 * ty], xi);
+      ld4(&Br[kk][4 * tx], yr);              // columns 4 tx .. 4 tx + 3
+      ld4(&Bi[kk][4 * tx], yi);
 #pragma unroll
       for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -119,10 +116,10 @@ __global__ void __launch_bounds__(256) k_kp_gemm1(const Tc* __restrict__ pr, con
   Tc* Xiq = Xi + ((long long)split * K + q) * mat;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    const int i = i0 + ty + 16 * m;
+    const int i = i0 + 4 * ty + m;
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
-      const int j = j0 + tx + 16 * n;
+      const int j = j0 + 4 * tx + n;
       if (i < ns && j < ns) {
         Xrq[(long long)i * ns + j] = sr[m][n];
         Xiq[(long long)i * ns + j] = si[m][n];

@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(256) k_gemm1(const Tc* __restrict__ psi, int n
   const Tc* aq = a + (long long)q * a_stride;
   const long long rb = (long long)split * rows_per;
   const long long re = min(Ng, rb + rows_per);
-  __shared__ Tc As[BK][T];
-  __shared__ Tc Bs[BK][T];
+  __shared__ __align__(16) Tc As[BK][T];
+  __shared__ __align__(16) Tc Bs[BK][T];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   Tc acc[4][4];
 #pragma unroll
@@ -60,10 +60,8 @@ __global__ void __launch_bounds__(256) k_gemm1(const Tc* __restrict__ psi, int n
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       Tc ar[4], br[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) ar[m] = As[kk][ty + 16 * m];
-#pragma unroll
-      for (int n = 0; n < 4; ++n) br[n] = Bs[kk][tx + 16 * n];
+      ld4(&As[kk][4 * ty], ar);              // rows 4 ty .. 4 ty + 3
+      ld4(&Bs[kk][4 * tx], br);              // columns 4 tx .. 4 tx + 3
 #pragma unroll
       for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -74,10 +72,10 @@ __global__ void __launch_bounds__(256) k_gemm1(const Tc* __restrict__ psi, int n
   Tc* Xq = Xpart + ((long long)split * nq + q) * (long long)ns * ns;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    int i = i0 + ty + 16 * m;
+    int i = i0 + 4 * ty + m;
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
-      int j = j0 + tx + 16 * n;
+      int j = j0 + 4 * tx + n;
       if (i < ns && j < ns) {
         Xq[(long long)i * ns + j] = acc[m][n];
         if (I != J) Xq[(long long)j * ns + i] = acc[m][n];

@@ -16,6 +16,24 @@
 
 namespace lrdm {
 
+// Four consecutive shared-memory values (16-byte aligned) with 128-bit loads:
+// the register tiles of the CUDA-core contractions.
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
 // NVTX range for the profilers' timelines (one per API call and per phase of
 // the forward / adjoint); no cost beyond a call when no tool is attached.
 struct NvtxRange {
