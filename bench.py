@@ -254,6 +254,7 @@ def time_kpoint(torch, rank, prec, autotune=True, reps=5, warmup=2):
     ctx = KpContext(KP_GRID, H, pr, pi, eps, kp_weights(KP_NK), KP_NE, KP_KT, rho_floor=1e-3,
                     prec=prec, io_dtype=torch.float32, k_max=KP_K, autotune=autotune)
     tuning = ctx.tuning() if prec in ("bf16x3", "tf32") else None
+    split = ctx.split(KP_K)
     del pr, pi
     V = torch.as_tensor(workloads.smooth_directions(KP_GRID, H, KP_K, 1, workloads.rng_for(80, 100 + rank))[:, 0],
                         dtype=torch.float32, device="cuda").contiguous()
@@ -302,10 +303,10 @@ def time_kpoint(torch, rank, prec, autotune=True, reps=5, warmup=2):
     traffic = None
     if tuning:
         traffic = recorded_traffic(kname, f"{KP_GRID[0]}^3/kp{KP_NK}x{KP_NS}/K{KP_K}/{prec}",
-                                   f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}")
+                                   f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']},split={split}")
     return {"workload": f"{KP_GRID[0]}^3 grid, {KP_NK} k-points x N_s={KP_NS} complex, K={KP_K}, {prec}",
             "value": KP_K / (ms / 1e3), "unit": "GD/s", "ms_per_call": ms, "reps": reps,
-            "launch_shape": tuning,
+            "launch_shape": tuning, "projection_row_ranges": split,
             "gemm1_ms_per_call": prof["gemm1_ms"] / reps, "gemm2_ms_per_call": prof["gemm2_ms"] / reps,
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kname,

@@ -398,6 +398,10 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
  * (else INVALID_ARG).  Asynchronous on `stream`. */
 lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, double* dmu_out,
                             void* stream);
+/* The number of grid-row ranges the projection of a K-direction call is
+ * split into (tensor cores: chosen per call to fill the persistent grid's
+ * waves, at most 4; CUDA cores: fixed at create).  For measurement. */
+lrdm_status lrdm_kp_get_split(lrdm_ctx* ctx, int K, int* split);
 
 /* Copies the projected perturbation X_k = Psi^T diag(w dV_k) Psi of direction
  * k, channel `spin`, of system `sys` from the most recent lrdm_gateaux_batch

@@ -64,7 +64,8 @@ EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_ap
            "lrdm_get_projection", "lrdm_profile_enable", "lrdm_profile_read", "lrdm_destroy", "lrdm_status_string",
            "lrdm_get_tuning", "lrdm_krylov_step", "lrdm_lrdma_default_params", "lrdm_lrdma_create",
            "lrdm_lrdma_step", "lrdm_lrdma_clear", "lrdm_lrdma_destroy", "lrdm_kp_create",
-           "lrdm_kp_gateaux", "lrdm_lrdma_get_state", "lrdm_lrdma_export", "lrdm_lrdma_import"]
+           "lrdm_kp_gateaux", "lrdm_lrdma_get_state", "lrdm_lrdma_export", "lrdm_lrdma_import",
+           "lrdm_kp_get_split"]
 
 
 class lrdm_lrdma_params(ctypes.Structure):
@@ -151,6 +152,8 @@ def load(path: Optional[str] = None):
     lib.lrdm_kp_create.restype = c_int
     lib.lrdm_kp_gateaux.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     lib.lrdm_kp_gateaux.restype = c_int
+    lib.lrdm_kp_get_split.argtypes = [c_void_p, c_int, POINTER(c_int)]
+    lib.lrdm_kp_get_split.restype = c_int
     lib.lrdm_destroy.argtypes = [c_void_p]
     lib.lrdm_destroy.restype = None
     lib.lrdm_status_string.argtypes = [c_int]
@@ -617,6 +620,12 @@ class KpContext:
     def tuning(self):
         """Launch shape of the tensor-core contractions (defaults or autotuned)."""
         return lrdm_get_tuning(self.handle)
+
+    def split(self, K):
+        """Grid-row ranges of the projection for a K-direction call."""
+        v = c_int()
+        _check("lrdm_kp_get_split", load().lrdm_kp_get_split(self.handle, int(K), ctypes.byref(v)))
+        return v.value
 
     def backward(self, fbar, out=None, stream=None):
         """v_bar = J^T f_bar for the most recent gateaux call (lrdm_backward);

@@ -1426,6 +1426,36 @@ lrdm_status solve_mu_kp_host(const std::vector<std::vector<double>>& eps, const 
 // contributions (tensor cores) or the FP64 accumulator (CUDA cores).  The
 // forward passes a = w dV and factor g; the adjoint a = fbar and factor w g
 // (the map is self-adjoint, the same traceless projection applies).
+// Grid-row ranges of the tensor-core projection for K directions over all
+// k-points: the fewest ranges (up to the P buffers' capacity, at least 64
+// stages each) whose work items fill the persistent grid's waves to 90 %,
+// else the best fill.
+int kp_choose_split(lrdm_ctx* ctx, int K) {
+  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+  long long per = 0;                                // items of one range over all points
+  int nch = 1 << 30;
+  for (int q = 0; q < ctx->kp_nk; ++q) {
+    const TcProblem& pr = ctx->tc_host[ctx->kp_pid[q]];
+    const bool wide = ctx->tune.g1_nb == 256;
+    const int dpt = wide ? 1 : ctx->tune.g1_dpt;
+    per += (long long)(wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
+    nch = std::min(nch, pr.nch);
+  }
+  int best = 1;
+  double best_fill = 0.0;
+  for (int s = 1; s <= ctx->kp_split_cap && nch / s >= 64; ++s) {
+    const long long items = per * s;
+    const long long waves = (items + sms - 1) / sms;
+    const double fill = (double)items / (double)(waves * sms);
+    if (fill > best_fill + 1e-9) {
+      best_fill = fill;
+      best = s;
+    }
+    if (fill >= 0.9) break;
+  }
+  return best;
+}
+
 lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cudaStream_t st) {
   NvtxRange nvtx_("k-point response");
   SysState& S = ctx->sys[0];
@@ -1433,6 +1463,7 @@ lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cu
   const int fp64 = prec == LRDM_FP64;
   const bool tc = is_tc(prec);
   const int ns = ctx->kp_ns, nk = ctx->kp_nk;
+  const int split = tc ? kp_choose_split(ctx, K) : ctx->kp_nsplit;
   if (tc) {
     ctx->tc_entries.clear();
     for (int q = 0; q < nk; ++q) {
@@ -1442,6 +1473,7 @@ lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cu
       x.host = &ctx->tc_host[x.pid];
       x.K = K;
       x.X = ctx->kp_ch[q].Xpart;
+      x.split = split;
       ctx->tc_entries.push_back(x);
     }
     LRDM_CK(tc_group(ctx, 1, 0, st));
@@ -1462,7 +1494,7 @@ lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cu
   A.nk = nk;
   A.ns = ns;
   A.K = K;
-  A.nsplit = ctx->kp_nsplit;
+  A.nsplit = split;
   A.fp64 = fp64;
   A.ld = tc ? ctx->kp_ch[0].ns_pad : ns;
   A.stacked = tc ? 1 : 0;
@@ -1473,8 +1505,8 @@ lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cu
     ctx->tc_entries.clear();
     for (int q = 0; q < nk; ++q) {
       const Channel& c = ctx->kp_ch[q];
-      LRDM_CU(launch_kp_scale_tc(static_cast<const float*>(c.Xpart), 1, K, ns, c.ns_pad, ctx->kp_L[q], S.dmu,
-                                 layout, c.Xpp, c.Xpp_lo, st));
+      LRDM_CU(launch_kp_scale_tc(static_cast<const float*>(c.Xpart), split, K, ns, c.ns_pad, ctx->kp_L[q],
+                                 S.dmu, layout, c.Xpp, c.Xpp_lo, st));
       TcEntry x;
       x.dev_base = ctx->tc_dev;
       x.pid = ctx->kp_pid[q];
@@ -1649,7 +1681,12 @@ lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t s
       }
       LRDM_CU(launch_convert_psi(stack, io, 2 * ns, S.Ng, 2 * ns, c, prec, S.Ng_pad, st));
       LRDM_CU(cudaStreamSynchronize(st));      // the stacked copy is reused for the next point
-      LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&c.Xpart), (size_t)S.kmax * ld2 * sizeof(float)));
+      // room for up to 4 grid-row ranges of the projection (kp_choose_split),
+      // fewer where that would exceed 1 GB per point
+      int cap = 4;
+      while (cap > 1 && (size_t)cap * S.kmax * ld2 * sizeof(float) > ((size_t)1 << 30)) --cap;
+      ctx->kp_split_cap = cap;
+      LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&c.Xpart), (size_t)cap * S.kmax * ld2 * sizeof(float)));
       LRDM_CK(dalloc(ctx, &ctx->kp_out[q], (size_t)S.kmax * S.Ng));
       return LRDM_OK;
     }();
@@ -1741,6 +1778,12 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
     return rc;
   }
   *out = ctx;
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_kp_get_split(lrdm_ctx* ctx, int K, int* split) {
+  if (!ctx || !ctx->kp || !split || K < 1 || K > ctx->sys[0].kmax) return LRDM_ERR_INVALID_ARG;
+  *split = is_tc(ctx->opt.prec) ? kp_choose_split(ctx, K) : ctx->kp_nsplit;
   return LRDM_OK;
 }
 

@@ -158,6 +158,7 @@ struct lrdm_ctx {
   std::vector<lrdm::Channel> kp_ch;
   std::vector<int> kp_pid;
   std::vector<float*> kp_out;
+  int kp_split_cap = 1;              // tensor cores: grid-row ranges the P buffers hold
 };
 
 namespace lrdm {

@@ -341,3 +341,23 @@ def test_kpoint_autograd_function(lib, cfg):
     lhs = float((fbar * F.detach()).sum())
     rhs = float((V.grad * V.detach()).sum())
     assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+def test_kpoint_split_row_ranges(lib):
+    """A 24^3 grid (432 reduction stages) where the tensor-core projection
+    splits the grid into row ranges (3 for 45 items per range on 152 SMs):
+    the summed partials give the oracle's response."""
+    c = workloads.kpoint_system(73, (24, 24, 24), NS, NK, NE, KT, K)
+    for prec in ("bf16x3", "fp64"):
+        ctx, psi_seen = _device(c, prec)
+        ks, _ = _oracle(c, psi_seen)
+        ks.rho = ctx.density().double().cpu().numpy()
+        V = torch.as_tensor(c["V"], dtype=DT[prec], device="cuda")
+        F, dmu = ctx.gateaux(V)
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        ref = oracle.gateaux_kpoints(ks, V.double().cpu().numpy())
+        err = per_direction_rel_err(F.double().cpu().numpy(), ref["F"])
+        print(f"k-point 24^3 {prec}: f err {err:.2e}")
+        assert err < TOL[prec]
+        ctx.close()
