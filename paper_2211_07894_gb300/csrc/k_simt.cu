@@ -35,39 +35,62 @@ __global__ void __launch_bounds__(256) k_gemm1(const Tc* __restrict__ psi, int n
   const Tc* aq = a + (long long)q * a_stride;
   const long long rb = (long long)split * rows_per;
   const long long re = min(Ng, rb + rows_per);
-  __shared__ __align__(16) Tc As[BK][T];
-  __shared__ __align__(16) Tc Bs[BK][T];
+  // two stages in shared memory; the next stage's global values are loaded
+  // into registers while the current one is multiplied (one barrier a stage)
+  __shared__ __align__(16) Tc As[2][BK][T];
+  __shared__ __align__(16) Tc Bs[2][BK][T];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  static_assert(BK * T == 4 * 256, "four elements of each operand per thread and stage");
+  const int cc = threadIdx.x & (T - 1), rr0 = threadIdx.x / T;   // rows rr0 + 4 u of a stage
   Tc acc[4][4];
 #pragma unroll
   for (int m = 0; m < 4; ++m)
 #pragma unroll
     for (int n = 0; n < 4; ++n) acc[m][n] = Tc(0);
-  for (long long r0 = rb; r0 < re; r0 += BK) {
-    for (int e = threadIdx.x; e < BK * T; e += 256) {
-      int rr = e / T, cc = e % T;
-      long long r = r0 + rr;
+  Tc pa[4], pb[4];
+  auto fetch = [&](long long r0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long r = r0 + rr0 + 4 * u;
       Tc av = Tc(0), bv = Tc(0);
       if (r < re) {
-        Tc sc = aq[r];
+        const Tc sc = aq[r];
         if (i0 + cc < ns) av = psi[r * ns + i0 + cc] * sc;
         if (j0 + cc < ns) bv = psi[r * ns + j0 + cc];
       }
-      As[rr][cc] = av;
-      Bs[rr][cc] = bv;
+      pa[u] = av;
+      pb[u] = bv;
     }
-    __syncthreads();
+  };
+  auto stash = [&](int b) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      As[b][rr0 + 4 * u][cc] = pa[u];
+      Bs[b][rr0 + 4 * u][cc] = pb[u];
+    }
+  };
+  if (rb < re) {
+    fetch(rb);
+    stash(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (long long r0 = rb; r0 < re; r0 += BK) {
+    const bool more = r0 + BK < re;
+    if (more) fetch(r0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       Tc ar[4], br[4];
-      ld4(&As[kk][4 * ty], ar);              // rows 4 ty .. 4 ty + 3
-      ld4(&Bs[kk][4 * tx], br);              // columns 4 tx .. 4 tx + 3
+      ld4(&As[buf][kk][4 * ty], ar);         // rows 4 ty .. 4 ty + 3
+      ld4(&Bs[buf][kk][4 * tx], br);         // columns 4 tx .. 4 tx + 3
 #pragma unroll
       for (int m = 0; m < 4; ++m)
 #pragma unroll
         for (int n = 0; n < 4; ++n) acc[m][n] += ar[m] * br[n];
     }
+    if (more) stash(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
   Tc* Xq = Xpart + ((long long)split * nq + q) * (long long)ns * ns;
 #pragma unroll
