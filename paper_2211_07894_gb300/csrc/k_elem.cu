@@ -50,12 +50,6 @@ __global__ void k_spin_sum(const void* __restrict__ v, int io, int K, int nspin,
 // Multiplies the half-spectrum (R2C layout [K][n0][n1][n2/2+1]) by
 // 4 pi / |G|^2 / N_g (G = 0 -> 0); kind 1 replaces |G|^2 by the second-order
 // finite-difference symbol sum_d (4/h_d^2) sin^2(G_d h_d / 2).
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t t;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-  return __uint_as_float(t);
-}
-
 __global__ void k_poisson_table(int n0, int n1, int n2, double h0, double h1, double h2, int kind,
                                 double* __restrict__ sym) {
   const int m2n = n2 / 2 + 1;

@@ -32,12 +32,6 @@ namespace {
 constexpr int T = 64;
 constexpr int BK = 16;
 
-// round to the TF32 grid (nearest, ties away), as the TF32 GEMM2 operand expects
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t t;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-  return __uint_as_float(t);
-}
 
 // upper-triangular tile p -> (I, J), I <= J, column-major over J
 __device__ __forceinline__ void kp_tri(int p, int& I, int& J) {

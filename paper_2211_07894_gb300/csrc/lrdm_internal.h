@@ -16,6 +16,14 @@
 
 namespace lrdm {
 
+// Rounds to the TF32 grid (nearest, ties away from zero): the values the TF32
+// response GEMM reads as its X'' operand.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+  return __uint_as_float(t);
+}
+
 // Four consecutive shared-memory values (16-byte aligned) with 128-bit loads:
 // the register tiles of the CUDA-core contractions.
 __device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
