@@ -27,9 +27,13 @@
  *  - All array pointers are DEVICE pointers unless stated otherwise.  The
  *    caller owns every input and output buffer; the library only borrows
  *    them for the duration of the stream work it enqueues.
- *  - lrdm_create allocates everything the context needs (workspaces sized
- *    for k_max, the operand copies of Psi, cuFFT plans).  The other calls
- *    allocate nothing and do not synchronise the host with the device.
+ *  - lrdm_create / lrdm_kp_create allocate everything a context needs
+ *    (workspaces sized for k_max, the operand copies of Psi, cuFFT plans) and
+ *    lrdm_lrdma_create the history buffers; no other call allocates device
+ *    memory (lrdm_apply_static uses a fixed device array).  Calls that take
+ *    decisions on the host synchronise their stream: lrdm_krylov_step,
+ *    lrdm_lrdma_step, lrdm_lrdma_export / _import, lrdm_status_query with
+ *    synchronize = 1 and the create calls; the others only enqueue work.
  *  - Argument errors are returned synchronously, before anything is
  *    enqueued.  Errors found on the device (non-finite values, an expired
  *    bounded wait, a singular least-squares matrix) set a sticky status word
