@@ -399,7 +399,9 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
                            void* stream);
 /* f_k = drho_k - v_k for K real directions v ([K][N_g] io dtype, device);
  * f_out has the same layout; dmu_out device [K] FP64 or NULL.  0 <= K <= k_max
- * (else INVALID_ARG).  Asynchronous on `stream`. */
+ * (else INVALID_ARG).  Asynchronous on `stream`; with options.use_graph the
+ * call is captured into a CUDA graph on its first use with a given set of
+ * buffers, K and stream and replayed afterwards (as lrdm_gateaux_batch). */
 lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, double* dmu_out,
                             void* stream);
 /* The number of grid-row ranges the projection of a K-direction call is

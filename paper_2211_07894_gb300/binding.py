@@ -513,7 +513,7 @@ class KpContext:
 
     def __init__(self, n, h, psi_re, psi_im, eps, k_weights, n_electrons, kT, g=2.0,
                  rho=None, rho_floor=0.0, prec="fp64", io_dtype=None, k_max=16, degen_tol=1e-5,
-                 autotune=False, stream=None):
+                 autotune=False, use_graph=False, stream=None):
         import torch
         self.torch = torch
         self.io_dtype = io_dtype or torch.float64
@@ -523,6 +523,7 @@ class KpContext:
         o.k_max = int(k_max)
         o.degen_tol = float(degen_tol)
         o.autotune = 1 if autotune else 0
+        o.use_graph = 1 if use_graph else 0
         nk = len(psi_re)
         assert len(psi_im) == nk and len(eps) == nk and len(k_weights) == nk
         s = lrdm_kpoint_system()

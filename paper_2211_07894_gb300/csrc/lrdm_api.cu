@@ -138,6 +138,7 @@ lrdm_status validate_system(const lrdm_system& s, const lrdm_options& o) {
 // symbol table and the transform buffers of system S.
 lrdm_status kp_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_bar,
                         double* const* eps_bar, double* const* occ_bar, cudaStream_t st);
+lrdm_status kp_forward(lrdm_ctx* ctx, const void* v, int K, void* f_out, double* dmu_out, cudaStream_t st);
 
 lrdm_status setup_poisson(lrdm_ctx* ctx, SysState& S, cudaStream_t st) {
   const lrdm_options& o = ctx->opt;
@@ -637,12 +638,45 @@ lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void*
   return LRDM_OK;
 }
 
+// CUDA graph of a forward call: captured on the first call with a given key
+// (buffers, K's, stream), replayed afterwards.  Not used on the legacy
+// default stream or while profiling.
+bool use_graph(const lrdm_ctx* ctx, cudaStream_t st) {
+  return ctx->opt.use_graph && st != nullptr && !ctx->prof_on;
+}
+
+template <typename Body>
+lrdm_status graph_call(lrdm_ctx* ctx, const std::vector<const void*>& key, cudaStream_t st, Body body) {
+  if (ctx->graph_exec && key == ctx->graph_key) return from_cuda(cudaGraphLaunch(ctx->graph_exec, st));
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  LRDM_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  lrdm_status rc = body();
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != LRDM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  LRDM_CU(e);
+  e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  LRDM_CU(e);
+  ctx->graph_key = key;
+  return from_cuda(cudaGraphLaunch(ctx->graph_exec, st));
+}
+
 // One forward call of the direction drivers (Krylov step, LRDMA): system sys
 // gets K[sys] directions, the others none; a Brillouin-zone-sampled context
 // runs its own forward (one system, one channel).
 lrdm_status forward_one(lrdm_ctx* ctx, int sys, const void* const* v, const int* K, void* const* f,
                         cudaStream_t st) {
-  if (ctx->kp) return lrdm_kp_gateaux(ctx, v[sys], K[sys], f[sys], nullptr, st);
+  if (ctx->kp) {
+    ctx->sys[0].last_K = K[sys];
+    return K[sys] > 0 ? kp_forward(ctx, v[sys], K[sys], f[sys], nullptr, st) : LRDM_OK;
+  }
   return forward_all(ctx, v, K, f, nullptr, st);
 }
 
@@ -811,41 +845,18 @@ lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K
     if (K[s] > 0 && (!v[s] || !f_out[s])) return LRDM_ERR_INVALID_ARG;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // CUDA graph: captured on the first call with a given set of buffers and K's
-  // (and stream), replayed afterwards.  Not used on the legacy default stream
-  // or while profiling.
-  if (ctx->opt.use_graph && st != nullptr && !ctx->prof_on) {
+  if (use_graph(ctx, st)) {
     std::vector<const void*> key;
     key.reserve(3 * ctx->nsys + 2);
     for (int s = 0; s < ctx->nsys; ++s) {
       key.push_back(v[s]);
       key.push_back(f_out[s]);
       key.push_back(reinterpret_cast<const void*>((intptr_t)K[s]));
+      ctx->sys[s].last_K = K[s];
     }
     key.push_back(dmu_out);
     key.push_back(st);
-    if (ctx->graph_exec && key == ctx->graph_key) {
-      for (int s = 0; s < ctx->nsys; ++s) ctx->sys[s].last_K = K[s];
-      return from_cuda(cudaGraphLaunch(ctx->graph_exec, st));
-    }
-    if (ctx->graph_exec) {
-      cudaGraphExecDestroy(ctx->graph_exec);
-      ctx->graph_exec = nullptr;
-    }
-    LRDM_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    lrdm_status rc = forward_all(ctx, v, K, f_out, dmu_out, st);
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(st, &g);
-    if (rc != LRDM_OK) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    LRDM_CU(e);
-    e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
-    cudaGraphDestroy(g);
-    LRDM_CU(e);
-    ctx->graph_key = key;
-    return from_cuda(cudaGraphLaunch(ctx->graph_exec, st));
+    return graph_call(ctx, key, st, [&] { return forward_all(ctx, v, K, f_out, dmu_out, st); });
   }
   return forward_all(ctx, v, K, f_out, dmu_out, st);
 }
@@ -1534,6 +1545,30 @@ lrdm_status kp_response(lrdm_ctx* ctx, int K, double factor, double* dmu_out, cu
   return LRDM_OK;
 }
 
+// The k-point forward: dV_k = V_H[v_k] + f_x v_k, a_k = w dV_k (zero in the
+// grid padding), the response with factor g, f_k = drho_k - v_k.
+lrdm_status kp_forward(lrdm_ctx* ctx, const void* v, int K, void* f_out, double* dmu_out, cudaStream_t st) {
+  SysState& S = ctx->sys[0];
+  const int fp64 = ctx->opt.prec == LRDM_FP64;
+  const int io = ctx->opt.io_dtype;
+  LRDM_CU(launch_spin_sum(v, io, K, 1, S.Ng, S.fft_real, fp64, st));
+  LRDM_CK(hartree(ctx, S, K, st));
+  LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[0].fx, K, 1, S.Ng, S.Ng_pad, S.w, S.a,
+                            fp64, st));
+  count(ctx, 3);
+  LRDM_CK(kp_response(ctx, K, S.g, dmu_out, st));
+  if (is_tc(ctx->opt.prec)) {
+    KpSumArgs B{};
+    for (int q = 0; q < ctx->kp_nk; ++q) B.part[q] = ctx->kp_out[q];
+    B.nk = ctx->kp_nk;
+    LRDM_CU(launch_kp_sum(B, v, io, (long long)K * S.Ng, f_out, st));
+  } else {
+    LRDM_CU(launch_kp_finish(ctx->kp_drho, v, io, (long long)K * S.Ng, f_out, st));
+  }
+  count(ctx, 1);
+  return LRDM_OK;
+}
+
 // Adjoint of lrdm_kp_gateaux with respect to the directions: the response of
 // the weights fbar with factor w g, then vbar = V_H[dVbar] + f_x dVbar - fbar.
 // Eigenvalue / occupation gradients are not defined for k-point contexts.
@@ -1799,27 +1834,12 @@ lrdm_status lrdm_kp_gateaux(lrdm_ctx* ctx, const void* v, int K, void* f_out, do
   }
   if (!v || !f_out) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int fp64 = ctx->opt.prec == LRDM_FP64;
-  const int io = ctx->opt.io_dtype;
-  // dV_k = V_H[v_k] + f_x v_k;  a_k = w dV_k (zero in the grid padding)
-  LRDM_CU(launch_spin_sum(v, io, K, 1, S.Ng, S.fft_real, fp64, st));
-  LRDM_CK(hartree(ctx, S, K, st));
-  LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[0].fx, K, 1, S.Ng, S.Ng_pad, S.w, S.a,
-                            fp64, st));
-  count(ctx, 3);
-  // drho_k = g sum_kappa w_kappa diag(Psi L o (X - mu' I) Psi^H);  f_k = drho_k - v_k
-  LRDM_CK(kp_response(ctx, K, S.g, dmu_out, st));
-  if (is_tc(ctx->opt.prec)) {
-    KpSumArgs B{};
-    for (int q = 0; q < ctx->kp_nk; ++q) B.part[q] = ctx->kp_out[q];
-    B.nk = ctx->kp_nk;
-    LRDM_CU(launch_kp_sum(B, v, io, (long long)K * S.Ng, f_out, st));
-  } else {
-    LRDM_CU(launch_kp_finish(ctx->kp_drho, v, io, (long long)K * S.Ng, f_out, st));
-  }
-  count(ctx, 1);
   S.last_K = K;
-  return LRDM_OK;
+  if (use_graph(ctx, st)) {
+    const std::vector<const void*> key = {v, f_out, reinterpret_cast<const void*>((intptr_t)K), dmu_out, st};
+    return graph_call(ctx, key, st, [&] { return kp_forward(ctx, v, K, f_out, dmu_out, st); });
+  }
+  return kp_forward(ctx, v, K, f_out, dmu_out, st);
 }
 
 }  // extern "C"
