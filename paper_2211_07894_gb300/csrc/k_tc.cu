@@ -418,19 +418,24 @@ constexpr int G1_ACOL = 256;            // first TMEM column of the weighted-A r
 template <int PREC, int NB>
 struct G1Cfg {
   static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
-  static constexpr int STAGES = PREC == LRDM_BF16X3 ? 4 : 8;
+  // grid-row chunks of BK rows per stage: TF32 takes two 16-row chunks (the
+  // operand layouts' box), so that a stage holds four MMAs as BF16x3's holds six
+  static constexpr int SUB = PREC == LRDM_TF32 ? 2 : 1;
+  static constexpr int STAGES = 4;
   static constexpr int MAXD = NB == 256 ? 1 : 2;               // directions per tile at most
   // TMEM columns of one direction's weighted A per stage: bf16 packs two
   // elements per column and has two parts (hi, lo); tf32 one element per column
-  static constexpr int ACOLS = BK;
+  static constexpr int ACOLS = BK * SUB;
   static constexpr int SLOT = MAXD * ACOLS;
-  static constexpr int A_BYTES = BM * BK * 4;                   // FP32 A rows (128-byte rows for bf16 mode)
-  static constexpr int B_TILE = NB * ROWB;                      // one part of the B rows
+  static constexpr int A_CHUNK = BM * BK * 4;                   // FP32 A rows of one chunk
+  static constexpr int A_BYTES = A_CHUNK * SUB;
+  static constexpr int B_TILE = NB * ROWB;                      // one part of the B rows of one chunk
+  static constexpr int B_CHUNK = PARTS * B_TILE;
   static constexpr int B_OFF = A_BYTES;
-  static constexpr int SC_OFF = B_OFF + PARTS * B_TILE;
+  static constexpr int SC_OFF = B_OFF + SUB * B_CHUNK;
   static constexpr int STRIDE = SC_OFF + 1024;                  // 1024-aligned stages
   static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
-  static constexpr int SEG = 1024 / BK;                          // stages per accumulation segment
+  static constexpr int SEG = 1024 / (BK * SUB);                  // stages per accumulation segment
   static constexpr int LAG = STAGES - 1;                         // stages weighted ahead of a flush
   static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, NB);
   static_assert(G1_ACOL + STAGES * SLOT <= 512, "TMEM budget");
@@ -452,14 +457,18 @@ struct G1Params {
   int* status;
 };
 
+// Stages of the grid reduction: chunks of BK rows (nch_lim caps them for
+// tuning), SUB chunks per stage.
+template <int SUB>
 __device__ __forceinline__ int g1_nch(const G1Params& P, const TcProblem* pr) {
-  return P.nch_lim > 0 ? min(P.nch_lim, pr->nch) : pr->nch;
+  return (P.nch_lim > 0 ? min(P.nch_lim, pr->nch) : pr->nch) / SUB;
 }
 
 // Stages [rb, re) of row range `split` of slot q.
+template <int SUB>
 __device__ __forceinline__ void g1_range(const G1Params& P, const TcProblem* pr, int q, int split,
                                          int& rb, int& re) {
-  const long long n = g1_nch(P, pr);
+  const long long n = g1_nch<SUB>(P, pr);
   rb = (int)(n * split / P.nsplit[q]);
   re = (int)(n * (split + 1) / P.nsplit[q]);
 }
@@ -528,7 +537,7 @@ __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       if (d >= nd) break;
-      const uint32_t sc = st + C::SC_OFF + d * C::BK * 4 + h * 16 * 4;
+      const uint32_t sc = st + C::SC_OFF + d * C::BK * C::SUB * 4 + h * 16 * 4;
       uint32_t oh[8], ol[8];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -545,8 +554,11 @@ __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd
       ptx::tmem_st8(ta + d * C::ACOLS + 16 + h * 8, ol);     // lo: columns [16, 32)
     }
   } else {
-    // A rows of 16 FP32 = 64 bytes, 64-byte swizzle: chunk c sits at c ^ ((row / 2) % 4)
-    const uint32_t ra = st + row * ROWB;
+    // per chunk c of 16 grid rows: A rows of 16 FP32 = 64 bytes, 64-byte
+    // swizzle: 16-byte unit u sits at u ^ ((row / 2) % 4)
+#pragma unroll
+    for (int c = 0; c < C::SUB; ++c) {
+    const uint32_t ra = st + c * C::A_CHUNK + row * ROWB;
     const int sw = (row >> 1) & 3;
     uint64_t xp[4];
 #pragma unroll
@@ -558,7 +570,7 @@ __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       if (d >= nd) break;
-      const uint32_t sc = st + C::SC_OFF + d * C::BK * 4 + h * 8 * 4;
+      const uint32_t sc = st + C::SC_OFF + d * C::BK * C::SUB * 4 + c * C::BK * 4 + h * 8 * 4;
       uint32_t o[8];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -570,7 +582,8 @@ __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd
         o[4 * u + 2] = __float_as_uint(tf32_round(__uint_as_float((uint32_t)y1)));
         o[4 * u + 3] = __float_as_uint(tf32_round(__uint_as_float((uint32_t)(y1 >> 32))));
       }
-      ptx::tmem_st8(ta + d * C::ACOLS + h * 8, o);
+      ptx::tmem_st8(ta + d * C::ACOLS + c * C::BK + h * 8, o);
+    }
     }
   }
 }
@@ -587,16 +600,20 @@ __device__ __forceinline__ void issue_g1_mmas(uint32_t tmem, uint32_t aslot, uin
     const uint32_t dt = tmem + d * G1_BN;
     const uint32_t at = tmem + aslot + d * C::ACOLS;
 #pragma unroll
-    for (int kk = 0; kk < KSTEPS; ++kk) {     // 32-byte K steps along the swizzled B row
-      const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-      const uint64_t b0 = ptx::desc_k_sw64(sb + kk * 32);
-      if (PREC == LRDM_BF16X3) {
-        const uint64_t b1 = ptx::desc_k_sw64(sb + C::B_TILE + kk * 32);
-        ptx::mma_f16_ta(dt, at + kk * 8, b0, C::IDESC, acc);        // hi x hi
-        ptx::mma_f16_ta(dt, at + kk * 8, b1, C::IDESC, 1);          // hi x lo
-        ptx::mma_f16_ta(dt, at + 16 + kk * 8, b0, C::IDESC, 1);     // lo x hi
-      } else {
-        ptx::mma_tf32_ta(dt, at + kk * 8, b0, C::IDESC, acc);
+    for (int c = 0; c < C::SUB; ++c) {        // chunks of BK grid rows
+      const uint32_t bc = sb + c * C::B_CHUNK;
+#pragma unroll
+      for (int kk = 0; kk < KSTEPS; ++kk) {   // 32-byte K steps along the swizzled B row
+        const uint32_t acc = (first && c == 0 && kk == 0) ? 0u : 1u;
+        const uint64_t b0 = ptx::desc_k_sw64(bc + kk * 32);
+        if (PREC == LRDM_BF16X3) {
+          const uint64_t b1 = ptx::desc_k_sw64(bc + C::B_TILE + kk * 32);
+          ptx::mma_f16_ta(dt, at + kk * 8, b0, C::IDESC, acc);        // hi x hi
+          ptx::mma_f16_ta(dt, at + kk * 8, b1, C::IDESC, 1);          // hi x lo
+          ptx::mma_f16_ta(dt, at + 16 + kk * 8, b0, C::IDESC, 1);     // lo x hi
+        } else {
+          ptx::mma_tf32_ta(dt, at + c * C::BK + kk * 8, b0, C::IDESC, acc);
+        }
       }
     }
   }
@@ -623,28 +640,32 @@ __device__ __forceinline__ void g1_producer(const G1Params& P, uint8_t* smem, co
     int q, k0, nd, I, J, sp;
     const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J, sp);
     int rb, re;
-    g1_range(P, pr, q, sp, rb, re);
+    g1_range<C::SUB>(P, pr, q, sp, rb, re);
     const float* w0 = pr->a + (long long)k0 * pr->a_stride;
     const long long wstride = pr->a_stride;
     const CUtensorMap *ma = &pr->g1a, *mb0 = &pr->g1b0, *mb1 = &pr->g1b1;
-    const uint32_t tx = C::A_BYTES + PARTS * C::B_TILE + nd * BK * 4;
+    constexpr int SUB = C::SUB;
+    const uint32_t tx = C::A_BYTES + SUB * C::B_CHUNK + nd * BK * SUB * 4;
     for (int rc = rb; rc < re; ++rc) {
       if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
       uint8_t* st = smem + s * SB;
       ptx::mbar_arrive_expect_tx(&B.full[s], tx);
-      ptx::tma_load_4d(st, ma, &B.full[s], 0, 0, rc, I);
-      // B rows: NB / 128 consecutive state blocks (a block past the last one
-      // of the matrix reads the zero fill; those columns are never stored)
 #pragma unroll
-      for (int hb = 0; hb < NB / 128; ++hb) {
-        ptx::tma_load_4d(st + C::B_OFF + hb * G1_TILE, mb0, &B.full[s], 0, 0, rc, J * (NB / 128) + hb);
-        if (PARTS == 2)
-          ptx::tma_load_4d(st + C::B_OFF + C::B_TILE + hb * G1_TILE, mb1, &B.full[s], 0, 0, rc,
-                           J * (NB / 128) + hb);
+      for (int c = 0; c < SUB; ++c) {
+        const int ch = rc * SUB + c;           // chunk of BK grid rows
+        ptx::tma_load_4d(st + c * C::A_CHUNK, ma, &B.full[s], 0, 0, ch, I);
+        // B rows: NB / 128 consecutive state blocks (a block past the last one
+        // of the matrix reads the zero fill; those columns are never stored)
+#pragma unroll
+        for (int hb = 0; hb < NB / 128; ++hb) {
+          uint8_t* bd = st + C::B_OFF + c * C::B_CHUNK + hb * G1_TILE;
+          ptx::tma_load_4d(bd, mb0, &B.full[s], 0, 0, ch, J * (NB / 128) + hb);
+          if (PARTS == 2) ptx::tma_load_4d(bd + C::B_TILE, mb1, &B.full[s], 0, 0, ch, J * (NB / 128) + hb);
+        }
       }
       for (int d = 0; d < nd; ++d)
-        ptx::bulk_load(st + C::SC_OFF + d * BK * 4, w0 + d * wstride + (long long)rc * BK, BK * 4,
-                       &B.full[s]);
+        ptx::bulk_load(st + C::SC_OFF + d * BK * SUB * 4, w0 + d * wstride + (long long)rc * BK * SUB,
+                       BK * SUB * 4, &B.full[s]);
       pending[s] = (int)ph;
       if (++s == STAGES) { s = 0; ph ^= 1; }
     }
@@ -665,7 +686,7 @@ __device__ __forceinline__ void g1_mma(const G1Params& P, uint8_t* smem, const B
     int q, k0, nd, I, J, sp;
     const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J, sp);
     int rb, re;
-    g1_range(P, pr, q, sp, rb, re);
+    g1_range<C::SUB>(P, pr, q, sp, rb, re);
     const int nseg = (re - rb + SEG - 1) / SEG;
     for (int sg = 0; sg < nseg && ok; ++sg) {
       if (!wait1(&B.acc_empty[0], aph ^ 1, B, P.status)) { ok = false; break; }
@@ -711,7 +732,7 @@ __device__ __forceinline__ void g1_math(const G1Params& P, uint8_t* smem, const 
     int q, k0, nd, I, J, sp;
     const TcProblem* pr = g1_item<NB>(P, item, q, k0, nd, I, J, sp);
     int rb, re;
-    g1_range(P, pr, q, sp, rb, re);
+    g1_range<C::SUB>(P, pr, q, sp, rb, re);
     const int ns = pr->ns, ns_pad = pr->ns_pad;
     const int nseg = (re - rb + SEG - 1) / SEG;
 #pragma unroll
