@@ -56,9 +56,13 @@ struct Tr<LRDM_TF32> {
 template <int PREC, int BN2>
 struct G2Cfg {
   static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
+  // state chunks of BK per stage: TF32 takes two 16-state chunks (the
+  // operand boxes), so that a stage holds four MMAs as BF16x3's holds six
+  static constexpr int SUB = PREC == LRDM_TF32 ? 2 : 1;
   static constexpr int TILE_B2 = BN2 * ROWB;
-  static constexpr int SB = PARTS * (TILE_A + TILE_B2);
-  static constexpr int STAGES = PREC == LRDM_BF16X3 ? (BN2 == 256 ? 4 : 6) : (BN2 == 256 ? 8 : 12);
+  static constexpr int CHUNK = PARTS * (TILE_A + TILE_B2);      // A and B parts of one chunk
+  static constexpr int SB = SUB * CHUNK;
+  static constexpr int STAGES = BN2 == 256 ? 4 : 6;
   static constexpr int SMEM = STAGES * SB + 1024 + 512;
   static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, BM, BN2);
 };
@@ -244,20 +248,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const CUtensorMap *mA0 = &pr->g2a0, *mA1 = &pr->g2a1, *mB0 = &pr->g2b0, *mB1 = &pr->g2b1;
       bool ok = true;
       for (int J = 0; J < NJ && ok; ++J) {
-        const int nch = min((J + 1) * BN2, ns_pad) / BK;
+        const int nch = min((J + 1) * BN2, ns_pad) / (BK * C::SUB);     // stages
         const int nbox = min(BN2, ns_pad - J * BN2) / 128;      // 128-row boxes of B in this j-tile
         for (int ic = 0; ic < nch; ++ic) {
           if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
-          uint8_t* st = smem + s * SB;
-          ptx::mbar_arrive_expect_tx(&B.full[s], PARTS * (TILE_A + nbox * 128 * ROWB));
-          ptx::tma_load_2d(st, mA0, &B.full[s], ic * BK, R * BM);
-          if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, mA1, &B.full[s], ic * BK, R * BM);
-          for (int hb = 0; hb < nbox; ++hb) {
-            ptx::tma_load_3d(st + PARTS * TILE_A + hb * 128 * ROWB, mB0, &B.full[s], ic * BK,
-                             J * BN2 + hb * 128, k);
-            if (PARTS == 2)
-              ptx::tma_load_3d(st + PARTS * TILE_A + C::TILE_B2 + hb * 128 * ROWB, mB1, &B.full[s],
-                               ic * BK, J * BN2 + hb * 128, k);
+          ptx::mbar_arrive_expect_tx(&B.full[s], C::SUB * PARTS * (TILE_A + nbox * 128 * ROWB));
+#pragma unroll
+          for (int c = 0; c < C::SUB; ++c) {
+            uint8_t* st = smem + s * SB + c * C::CHUNK;
+            const int i0 = (ic * C::SUB + c) * BK;              // first state of the chunk
+            ptx::tma_load_2d(st, mA0, &B.full[s], i0, R * BM);
+            if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, mA1, &B.full[s], i0, R * BM);
+            for (int hb = 0; hb < nbox; ++hb) {
+              ptx::tma_load_3d(st + PARTS * TILE_A + hb * 128 * ROWB, mB0, &B.full[s], i0,
+                               J * BN2 + hb * 128, k);
+              if (PARTS == 2)
+                ptx::tma_load_3d(st + PARTS * TILE_A + C::TILE_B2 + hb * 128 * ROWB, mB1, &B.full[s],
+                                 i0, J * BN2 + hb * 128, k);
+            }
           }
           pending[s] = (int)ph;
           if (++s == STAGES) { s = 0; ph ^= 1; }
@@ -281,11 +289,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!wait1(&B.acc_empty[a], aph ^ 1, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(a * BN2);
-        const int nch = min((J + 1) * BN2, ns_pad) / BK;
+        const int nch = min((J + 1) * BN2, ns_pad) / (BK * C::SUB);     // stages
         for (int ic = 0; ic < nch; ++ic) {
           if (!wait1(&B.full[s], ph, B, P.status)) { ok = false; break; }
           ptx::tc_fence_after();
-          issue_stage_mmas<PREC, BN2>(d, ptx::smem_u32(smem + s * SB), ic == 0);
+#pragma unroll
+          for (int c = 0; c < C::SUB; ++c)
+            issue_stage_mmas<PREC, BN2>(d, ptx::smem_u32(smem + s * SB + c * C::CHUNK), ic == 0 && c == 0);
           ptx::mma_commit(&B.empty[s]);
           if (++s == STAGES) { s = 0; ph ^= 1; }
         }
