@@ -97,7 +97,7 @@ __device__ __forceinline__ Bars carve(uint8_t* tail) {
 __device__ __forceinline__ bool wait1(uint64_t* bar, uint32_t parity, const Bars& B, int* status) {
   return ptx::mbar_wait(bar, parity, B.abort, status, WAIT_NS, STATUS_TIMEOUT);
 }
-// Warp-uniform bounded wait: lane 0 polls, the warp follows its verdict
+// Warp-uniform bounded wait: lane 0 polls, and the whole warp takes its result
 // (__syncwarp orders the other lanes' later shared-memory reads after it).
 __device__ __forceinline__ bool waitw(uint64_t* bar, uint32_t parity, const Bars& B, int* status) {
   int ok = 1;
