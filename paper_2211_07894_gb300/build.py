@@ -19,7 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "liblrdm.so")
-SOURCES = ["lrdm_api.cu", "k_setup.cu", "k_elem.cu", "k_simt.cu", "k_ls.cu", "k_tc.cu", "k_krylov.cu", "k_kpoint.cu"]
+SOURCES = ["lrdm_api.cu", "lrdm_lrdma.cu", "lrdm_kpoint_api.cu", "k_setup.cu", "k_elem.cu", "k_simt.cu",
+           "k_ls.cu", "k_tc.cu", "k_krylov.cu", "k_kpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
