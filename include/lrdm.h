@@ -49,6 +49,12 @@
 extern "C" {
 #endif
 
+/* The library is built with hidden visibility; what this header declares is
+ * its whole exported interface. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 typedef enum lrdm_status {
   LRDM_OK = 0,
   LRDM_ERR_INVALID_ARG = 1,      /* null pointer, bad enum, K > k_max, ...   */
@@ -420,6 +426,10 @@ lrdm_status lrdm_get_projection(lrdm_ctx* ctx, int sys, int spin, int k, double*
 void lrdm_destroy(lrdm_ctx* ctx);
 
 const char* lrdm_status_string(lrdm_status s);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

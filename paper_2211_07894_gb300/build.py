@@ -35,7 +35,9 @@ def _cuda_home() -> str:
 
 
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
+    # hidden visibility: the library exports only what include/lrdm.h declares
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler",
+                   "-fPIC,-O3,-fvisibility=hidden,-fvisibility-inlines-hidden",
                    "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
 
@@ -45,6 +47,11 @@ def build(verbose: bool = False, force: bool = False) -> str:
     obj_dir = os.path.join(HERE, "_build")
     os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(OUT_DIR, exist_ok=True)
+    # objects made with other compiler flags are rebuilt
+    stamp = os.path.join(obj_dir, "flags.txt")
+    flags = " ".join(_flags())
+    if not os.path.exists(stamp) or open(stamp).read() != flags:
+        force = True
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "lrdm.h"))
     hdr_time = max(os.path.getmtime(h) for h in headers)
@@ -78,6 +85,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    with open(stamp, "w") as fh:
+        fh.write(flags)
     return LIB
 
 

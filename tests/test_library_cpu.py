@@ -87,3 +87,18 @@ def test_degenerate_pairs_recipe():
     for i in d["pairs"]:
         assert abs(gaps[i] - 1e-9) < 1e-15
     assert np.all(gaps > 0)
+
+
+def test_library_exports_nothing_else(lib):
+    """The library is built with hidden visibility: its exported functions are
+    exactly those of include/*.h (std:: template instantiations aside)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    from paper_2211_07894_gb300 import build
+    out = subprocess.run([nm, "-D", "--defined-only", build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if len(ln.split()) == 3 and ln.split()[1] == "T"}
+    assert exported == set(_declared_functions())
