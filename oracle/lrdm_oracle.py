@@ -17,10 +17,10 @@ Functions are direct evaluations in the order of the paper's equations.  No
 blocking or fusion beyond what each docstring states.
 
 Pins: every function is checked against brute force, closed forms, mpmath or
-invariants (tests/test_oracle_pins.py, tests/test_scf_lrdm.py) except the
-branch logic of lrdma_step (reuse / accumulate / residual clearing), which is
-parity unpinned beyond its special case (always clearing = lrdm_krylov_step)
-and its invariants: the paper prints no worked example of those decisions.
+invariants (tests/test_oracle_pins.py, tests/test_kpoint_pins.py,
+tests/test_scf_lrdm.py); the decisions of lrdma_step, of which the paper
+prints no worked example, against closed forms on an exactly linear residual
+map (tests/test_lrdma_pins.py).
 """
 
 from __future__ import annotations
@@ -664,8 +664,10 @@ def lrdma_step(system: System, state: LrdmaState, R, rho=None, s_tol=0.3, beta_t
        R_lin = R - alpha sum_k a_k t_k for the next step's beta.
     Returns event ('fresh', 'reuse', 'accumulate', 'CL', 'CR', 'CT'), the
     total and new rank, s_rel, beta, ||R||, alpha, Delta (and rho_new).
-    Parity unpinned for the branch logic beyond the always-clearing special
-    case (which equals lrdm_krylov_step) and the history invariants."""
+    Pinned on an exactly linear residual map (tests/test_lrdma_pins.py): the
+    closed forms of beta and of the reused fit, each clearing followed by a
+    build equal to lrdm_krylov_step, and the span / orthogonality of the
+    accumulated directions, with the CT flag."""
     w = system.w
     Rm = np.asarray(R, dtype=np.float64)
     r_norm = float(np.sqrt(w * np.sum(Rm * Rm)))
