@@ -499,3 +499,36 @@ def test_autograd_function_dot_product(lib, cfg1):
     lhs = float((fbar * F.detach()).sum())
     rhs = float((V.grad * V.detach()).sum())
     assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16x3"])
+def test_maximum_directions(lib, prec):
+    """K = k_max = 64 (the largest batch a call takes) on a ragged system:
+    forward, the least-squares step over all 64 derivatives and the adjoint
+    against the oracle."""
+    cfg = _ragged(cfg_id=23, n=(12, 10, 14), ns=70, K=64, ne=50)
+    io = IO[prec]
+    ctx, V, F, dmu = _run([cfg], prec)
+    osys = oracle_system(cfg)
+    ref = oracle.gateaux(osys, cfg["V"])
+    err = per_direction_rel_err(F[0], ref["F"])
+    print(f"K = 64 {prec}: f err {err:.3e}")
+    assert err < TOL[prec]
+    _check_dmu(dmu, ref, prec)
+    Fd = torch.as_tensor(ref["F"], dtype=io, device="cuda")
+    R = torch.as_tensor(cfg["R"], dtype=io, device="cuda")
+    coef, srel = ctx.apply(0, R, V[0], Fd, 0.5)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    want = oracle.lrdm_apply(cfg["R"], cfg["V"], ref["F"], osys.w, 0.5)
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    # a = S^+ c with cond(S) ~ 1e4: the coefficients carry the io rounding times cond(S)
+    assert rel_err(coef.cpu().numpy(), want["a"]) < (1e-8 if prec == "fp64" else 1e-2)
+    assert abs(srel.item() - want["s_rel"]) < tol * 10
+    if prec != "tf32":
+        fbar = workloads.rng_for(23, 9).standard_normal(cfg["V"].shape)
+        vbar, _, _ = ctx.backward([torch.as_tensor(fbar, dtype=io, device="cuda")])
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        vref = oracle.backward(osys, fbar, V=cfg["V"])["vbar"]
+        assert per_direction_rel_err(vbar[0].double().cpu().numpy(), vref) < TOL[prec]
