@@ -112,25 +112,36 @@ def tc_source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(kernel, workload, shape):
-    """DRAM bytes per launch of `kernel` on `workload` in launch shape `shape`
-    (the kernel's own tuning fields, e.g. 'g1_nb=256,g1_dpt=1') from the ncu
-    summaries under profiles/ (lines 'traffic-record: kernel=... workload=...
-    shape=... source_sha256=... dram_bytes_per_launch=...'), or None when no
-    record matches the current kernel sources and shape."""
+def recorded_value(record, field, kernel, workload, shape):
+    """A per-launch ncu figure of `kernel` on `workload` in launch shape
+    `shape` (the kernel's own tuning fields, e.g. 'g1_nb=256,g1_dpt=1') from
+    the summaries under profiles/ (lines '<record>: kernel=... workload=...
+    shape=... source_sha256=... <field>=...'), or None when no record matches
+    the current kernel sources and shape."""
     import glob
     want = tc_source_hash()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as fh:
             for line in fh:
                 line = line.strip().strip("`")
-                if not line.startswith("traffic-record:"):
+                if not line.startswith(record + ":"):
                     continue
                 f = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)
                 if (f.get("kernel") == kernel and f.get("workload") == workload
-                        and f.get("shape") == shape and f.get("source_sha256") == want):
-                    return float(f["dram_bytes_per_launch"])
+                        and f.get("shape") == shape and f.get("source_sha256") == want
+                        and field in f):
+                    return float(f[field])
     return None
+
+
+def recorded_traffic(kernel, workload, shape):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return recorded_value("traffic-record", "dram_bytes_per_launch", kernel, workload, shape)
+
+
+def recorded_tensor_pipe(kernel, workload, shape):
+    """sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed, %."""
+    return recorded_value("tensor-pipe-record", "pct_of_elapsed", kernel, workload, shape)
 
 
 class ClockSampler:
@@ -714,6 +725,22 @@ def main():
                 "kernel": name, "avg_launch_ms": avg_s * 1e3, "launches": nl,
                 "alg_flop_per_launch": alg_flops, "peak_source": f"{peak_src}; {note}"}
 
+    # tensor-pipe use of both contractions: the issued rate against the
+    # measured peak (live) and ncu's pipe-active share (recorded full-size capture)
+    tensor_pipe = None
+    if args.prec in ("bf16x3", "tf32"):
+        tensor_pipe = {"source": "rate_frac: issued MMA rate / peak (as roofline); ncu_pct_of_elapsed: "
+                                 "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed "
+                                 "from a one-pass capture of this workload under profiles/ (null "
+                                 "when none matches the current sources and shape)"}
+        for key, kn, (ms, n) in (("projection", "k_gemm1_tc", g1), ("response", "k_gemm2_tc", g2)):
+            sh = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kn == "k_gemm1_tc"
+                   else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
+            sec = ms / max(n, 1) / 1e3
+            tensor_pipe[key] = {
+                "rate_frac": issued / sec / 1e12 / peak if sec > 0 else None,
+                "ncu_pct_of_elapsed": recorded_tensor_pipe(kn, f"{args.grid}^3/{ns}/K{KDIR}/{args.prec}", sh)}
+
     kpoint = None
     if not args.no_kpoint:
         ctx.close()
@@ -752,7 +779,8 @@ def main():
                            "precision": args.prec,
                            "l2": "inputs larger than L2 (Psi operand copies > 14 GB)",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "tensor_pipe": tensor_pipe, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],
                 "forward_only": forward_only, "forward_k1": forward_k1, "fp64_plain": fp64_plain,
                 "kpoint": kpoint,

@@ -45,13 +45,18 @@ def test_recorded_traffic_parser(tmp_path, monkeypatch):
         "text\n`traffic-record: kernel=k_gemm1_tc workload=96^3/4096/K16/bf16x3 shape=g1_nb=256,g1_dpt=1 "
         f"source_sha256={h} dram_bytes_per_launch=123.0`\n"
         "`traffic-record: kernel=k_gemm1_tc workload=96^3/4096/K16/bf16x3 shape=g1_nb=128,g1_dpt=2 "
-        "source_sha256=0000 dram_bytes_per_launch=5`\n")
+        "source_sha256=0000 dram_bytes_per_launch=5`\n"
+        "`tensor-pipe-record: kernel=k_gemm2_tc workload=96^3/4096/K16/bf16x3 shape=g2_bn=256,g2_kgroup=4 "
+        f"source_sha256={h} pct_of_elapsed=81.5`\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "tc_source_hash", lambda: h)
     assert bench.recorded_traffic("k_gemm1_tc", "96^3/4096/K16/bf16x3", "g1_nb=256,g1_dpt=1") == 123.0
     # a record taken with other kernel sources, or another shape, is not used
     assert bench.recorded_traffic("k_gemm1_tc", "96^3/4096/K16/bf16x3", "g1_nb=128,g1_dpt=2") is None
     assert bench.recorded_traffic("k_gemm2_tc", "96^3/4096/K16/bf16x3", "g1_nb=256,g1_dpt=1") is None
+    assert bench.recorded_tensor_pipe("k_gemm2_tc", "96^3/4096/K16/bf16x3", "g2_bn=256,g2_kgroup=4") == 81.5
+    assert bench.recorded_tensor_pipe("k_gemm1_tc", "96^3/4096/K16/bf16x3", "g1_nb=256,g1_dpt=1") is None
+    assert bench.recorded_traffic("k_gemm2_tc", "96^3/4096/K16/bf16x3", "g2_bn=256,g2_kgroup=4") is None
 
 
 def test_run_log_and_context(tmp_path):
