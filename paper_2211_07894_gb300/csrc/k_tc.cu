@@ -10,7 +10,9 @@
 //        tile 128 (r) x 256 (j); for each j-block the i-reduction stops at the
 //        block's end (X'' is zero below the diagonal); two TMEM accumulators so
 //        the row-dot epilogue of one j-block overlaps the MMAs of the next.
-//        Psi X'' only ever lives in tensor memory.
+//        Psi X'' only ever lives in tensor memory.  With one direction at
+//        N_s >= 2048 an item's j-blocks are split into parts run by
+//        neighbouring CTAs (FP64 part sums, added by k_g2_combine).
 //
 // Both: operands K-major in 64-byte-swizzled shared memory, loaded by TMA;
 // one thread issues tcgen05.mma, accumulators (FP32) in tensor memory, read
@@ -25,6 +27,8 @@
 
 #include <cudaTypedefs.h>
 #include <string.h>
+
+#include <algorithm>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -161,6 +165,12 @@ struct G2Params {
   void* out[TC_MAX_SLOTS];
   long long out_stride[TC_MAX_SLOTS];
   int nR[TC_MAX_SLOTS];             // row blocks processed (the problem's nR; fewer when tuning)
+  // j-tile parts: with nsplit > 1 a (row block, direction) item becomes nsplit
+  // items, part p taking the j-tiles jl[jb[p] .. jb[p + 1]) and writing its
+  // FP64 sum to the problem's part buffer (summed by k_g2_combine)
+  int nsplit[TC_MAX_SLOTS];
+  int jb[TC_MAX_SLOTS][G2_MAX_SPLIT + 1];
+  unsigned char jl[TC_MAX_SLOTS][G2_MAX_NJ];
   int out_io, out_is_io;
   int* status;
 };
@@ -172,22 +182,37 @@ __device__ __forceinline__ int find_slot(const int* begin, int nslot, int item) 
 }
 
 // Item order within a problem: groups of kgroup directions, row block,
-// direction within the group -- the items of one row block run side by side
-// and share its Psi rows through L2, while only kgroup matrices X''_k compete
-// for L2 at a time.
+// direction within the group, j-tile part -- the items of one row block run
+// side by side and share its Psi rows through L2, while only kgroup matrices
+// X''_k compete for L2 at a time.  [j0, j1) indexes the item's j-tiles
+// (through jl when the problem's items are split into parts).
+template <int BN2>
 __device__ __forceinline__ const TcProblem* g2_item(const G2Params& P, int item, int& q, int& k,
-                                                    int& R) {
+                                                    int& R, int& jp, int& j0, int& j1) {
   q = find_slot(P.begin, P.nslot, item);
   const TcProblem* pr = P.probs + P.pid[q];
   const int local = item - P.begin[q];
-  const int G = P.kgroup[q], K = P.K[q];
-  const int per = P.nR[q] * G;
+  const int G = P.kgroup[q], K = P.K[q], S = P.nsplit[q];
+  const int per = P.nR[q] * G * S;
   const int kg = local / per;
   const int rem = local - kg * per;
   const int g = min(G, K - kg * G);
-  R = rem / g;
-  k = kg * G + (rem - R * g);
+  R = rem / (g * S);
+  const int t = rem - R * g * S;
+  k = kg * G + t / S;
+  jp = t - (t / S) * S;
+  if (S > 1) {
+    j0 = P.jb[q][jp];
+    j1 = P.jb[q][jp + 1];
+  } else {
+    j0 = 0;
+    j1 = (pr->ns_pad + BN2 - 1) / BN2;
+  }
   return pr;
+}
+
+__device__ __forceinline__ int g2_tile(const G2Params& P, int q, int jj) {
+  return P.nsplit[q] > 1 ? (int)P.jl[q][jj] : jj;
 }
 
 template <int PREC, int BN2>
@@ -241,13 +266,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int pending[STAGES];
     for (int i = 0; i < STAGES; ++i) pending[i] = -1;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
-      int q, k, R;
-      const TcProblem* pr = g2_item(P, item, q, k, R);
+      int q, k, R, jp, j0, j1;
+      const TcProblem* pr = g2_item<BN2>(P, item, q, k, R, jp, j0, j1);
       const int ns_pad = pr->ns_pad;
-      const int NJ = (ns_pad + BN2 - 1) / BN2;
       const CUtensorMap *mA0 = &pr->g2a0, *mA1 = &pr->g2a1, *mB0 = &pr->g2b0, *mB1 = &pr->g2b1;
       bool ok = true;
-      for (int J = 0; J < NJ && ok; ++J) {
+      for (int jj = j0; jj < j1 && ok; ++jj) {
+        const int J = g2_tile(P, q, jj);
         const int nch = min((J + 1) * BN2, ns_pad) / (BK * C::SUB);     // stages
         const int nbox = min(BN2, ns_pad - J * BN2) / 128;      // 128-row boxes of B in this j-tile
         for (int ic = 0; ic < nch; ++ic) {
@@ -281,11 +306,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t ph = 0, aph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int q, k, R;
-      const TcProblem* pr = g2_item(P, item, q, k, R);
+      int q, k, R, jp, j0, j1;
+      const TcProblem* pr = g2_item<BN2>(P, item, q, k, R, jp, j0, j1);
       const int ns_pad = pr->ns_pad;
-      const int NJ = (ns_pad + BN2 - 1) / BN2;
-      for (int J = 0; J < NJ && ok; ++J) {
+      for (int jj = j0; jj < j1 && ok; ++jj) {
+        const int J = g2_tile(P, q, jj);
         if (!wait1(&B.acc_empty[a], aph ^ 1, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(a * BN2);
@@ -314,16 +339,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t aph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int q, k, R;
-      const TcProblem* pr = g2_item(P, item, q, k, R);
+      int q, k, R, jp, j0, j1;
+      const TcProblem* pr = g2_item<BN2>(P, item, q, k, R, jp, j0, j1);
       const int ns_pad = pr->ns_pad;
-      const int NJ = (ns_pad + BN2 - 1) / BN2;
       const long long Ng = pr->Ng;
       const void* psi0 = pr->psi0;
       const void* psi1 = pr->psi1;
       const long long r = (long long)R * BM + row;
       double acc_row = 0.0;
-      for (int J = 0; J < NJ; ++J) {
+      for (int jj = j0; jj < j1; ++jj) {
+        const int J = g2_tile(P, q, jj);
         if (!waitw(&B.acc_full[a], aph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
         float part = 0.f;
@@ -365,7 +390,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (++a == 2) { a = 0; aph ^= 1; }
       }
       if (!ok) break;
-      if (r < Ng) {
+      if (r < Ng && P.nsplit[q] > 1) {
+        pr->part[((long long)jp * P.K[q] + k) * Ng + r] = P.factor[q] * acc_row;
+      } else if (r < Ng) {
         const double d = P.factor[q] * acc_row;
         const long long o = (long long)k * P.out_stride[q] + r;
         if (P.out_is_io) {
@@ -1018,9 +1045,77 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, c
   return cudaSuccess;
 }
 
+// Sum of a split GEMM2's part sums in part order, then as the unsplit
+// epilogue: out = sum - v in the io dtype (out_is_io) or FP32 sum.
+__global__ void k_g2_combine(const double* __restrict__ part, int nsplit, int K, long long Ng,
+                             const void* __restrict__ v, long long v_stride, void* __restrict__ out,
+                             long long out_stride, int out_io, int out_is_io) {
+  const long long n = (long long)K * Ng;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / Ng);
+    const long long r = i - (long long)k * Ng;
+    double d = 0.0;
+    for (int p = 0; p < nsplit; ++p) d += part[((long long)p * K + k) * Ng + r];
+    const long long o = (long long)k * out_stride + r;
+    if (out_is_io) {
+      const long long ov = (long long)k * v_stride + r;
+      if (out_io == LRDM_DTYPE_F64)
+        static_cast<double*>(out)[o] = d - static_cast<const double*>(v)[ov];
+      else
+        static_cast<float*>(out)[o] = (float)(d - (double)static_cast<const float*>(v)[ov]);
+    } else {
+      static_cast<float*>(out)[o] = (float)d;
+    }
+  }
+}
+
+// j-tile parts of a GEMM2 problem with K directions.  Every CTA streams its
+// row block's Psi rows once per j-tile; with one direction at N_s >= 2048 the
+// row blocks of one wave (2 MB each in bf16 hi / lo) outgrow L2, where a
+// group of directions would share each row block side by side.  Splitting
+// each (row block, direction) item into parts over its j-tiles puts the parts
+// of one row block side by side instead: 4 parts (2 when 4 do not balance).
+// The tiles are dealt largest first to the part with the least work (tile J
+// holds min((J + 1) BN2, ns_pad) states); since the round-robin item order
+// gives each CTA the same part throughout, a split whose largest part exceeds
+// the mean by more than 5 % is not used.  At two directions a split measured
+// no faster than the pair sharing the row block.
+int g2_partition(const TcProblem& pr, int K, int BN2, int* jb, unsigned char* jl) {
+  const int NJ = (pr.ns_pad + BN2 - 1) / BN2;
+  if (K != 1 || pr.ns_pad < 2048 || NJ > G2_MAX_NJ || pr.part == nullptr) return 1;
+  for (int S = 4; S >= 2; S /= 2) {
+    if (S > NJ || S * K > G2_MAX_SPLIT) continue;
+    long long load[G2_MAX_SPLIT] = {0, 0, 0, 0};
+    int owner[G2_MAX_NJ];
+    for (int J = NJ - 1; J >= 0; --J) {
+      int best = 0;
+      for (int p = 1; p < S; ++p)
+        if (load[p] < load[best]) best = p;
+      owner[J] = best;
+      load[best] += (long long)std::min((J + 1) * BN2, pr.ns_pad) + 64;   // + epilogue
+    }
+    long long mx = 0, tot = 0;
+    for (int p = 0; p < S; ++p) {
+      mx = std::max(mx, load[p]);
+      tot += load[p];
+    }
+    if (20 * mx * S > 21 * tot) continue;              // max > 1.05 x mean
+    int m = 0;
+    for (int p = 0; p < S; ++p) {
+      jb[p] = m;
+      for (int J = 0; J < NJ; ++J)
+        if (owner[J] == p) jl[m++] = (unsigned char)J;
+    }
+    jb[S] = m;
+    return S;
+  }
+  return 1;
+}
+
 template <int PREC, int BN2>
 cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int* status,
-                        cudaStream_t st, const TcTune& t, int nR_lim) {
+                        cudaStream_t st, const TcTune& t, int nR_lim, int* launches) {
   static bool attr = false;
   const int smem = G2Cfg<PREC, BN2>::SMEM;
   cudaError_t err = set_smem(k_gemm2_tc<PREC, BN2>, smem, attr);
@@ -1032,6 +1127,7 @@ cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int*
     order_slots(e + base, m, 2, order);
     G2Params P;
     memset(&P, 0, sizeof(P));
+    const TcProblem* hp[TC_MAX_SLOTS] = {};
     P.out_io = out_io;
     P.out_is_io = out_is_io;
     P.status = status;
@@ -1049,8 +1145,10 @@ cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int*
       P.out[q] = x.out;
       P.out_stride[q] = x.out_stride;
       P.nR[q] = nR_lim > 0 && nR_lim < x.host->nR ? nR_lim : x.host->nR;
+      P.nsplit[q] = g2_partition(*x.host, x.K, BN2, P.jb[q], P.jl[q]);
+      hp[q] = x.host;
       P.begin[q] = items;
-      items += P.nR[q] * x.K;
+      items += P.nR[q] * x.K * P.nsplit[q];
       ++q;
     }
     P.nslot = q;
@@ -1059,6 +1157,16 @@ cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int*
     const int grid = items < num_sms() ? items : num_sms();
     k_gemm2_tc<PREC, BN2><<<grid, NTHREADS, smem, st>>>(P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (launches) ++*launches;
+    for (int u = 0; u < q; ++u) {
+      if (P.nsplit[u] <= 1) continue;
+      const long long nk = (long long)P.K[u] * hp[u]->Ng;
+      const int blocks = (int)std::min<long long>((nk + 255) / 256, 4LL * num_sms());
+      k_g2_combine<<<blocks, 256, 0, st>>>(hp[u]->part, P.nsplit[u], P.K[u], hp[u]->Ng, P.v[u],
+                                           P.v_stride[u], P.out[u], P.out_stride[u], out_io, out_is_io);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      if (launches) ++*launches;
+    }
   }
   return cudaSuccess;
 }
@@ -1090,13 +1198,14 @@ cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status
 }
 
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
-                                  int* status, cudaStream_t st, const TcTune& t, int nR_lim) {
+                                  int* status, cudaStream_t st, const TcTune& t, int nR_lim,
+                                  int* launches) {
   const bool narrow = t.g2_bn == 128;
   if (prec == LRDM_BF16X3)
-    return narrow ? gemm2_group<LRDM_BF16X3, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim)
-                  : gemm2_group<LRDM_BF16X3, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim);
-  return narrow ? gemm2_group<LRDM_TF32, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim)
-                : gemm2_group<LRDM_TF32, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim);
+    return narrow ? gemm2_group<LRDM_BF16X3, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches)
+                  : gemm2_group<LRDM_BF16X3, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches);
+  return narrow ? gemm2_group<LRDM_TF32, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches)
+                : gemm2_group<LRDM_TF32, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches);
 }
 
 }  // namespace lrdm

@@ -337,24 +337,32 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
   const int n = (int)ctx->tc_entries.size();
   if (n == 0) return LRDM_OK;
   int pi = prof_begin(ctx, gemm, st);
-  count(ctx, (n + TC_MAX_SLOTS - 1) / TC_MAX_SLOTS);
   // test-only fault injection, once: the next projection launch times out
   const int stall = gemm == 1 && (ctx->opt.debug_flags & LRDM_DEBUG_STALL_PROJECTION) ? 1 : 0;
   if (stall) ctx->opt.debug_flags &= ~LRDM_DEBUG_STALL_PROJECTION;
-  cudaError_t e = gemm == 1
-                      ? launch_gemm1_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
-                                              ctx->d_status, st, ctx->tune, 0, stall)
-                      : launch_gemm2_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n,
-                                              ctx->opt.io_dtype, out_is_io, ctx->d_status, st,
-                                              ctx->tune);
+  int launches = (n + TC_MAX_SLOTS - 1) / TC_MAX_SLOTS;
+  cudaError_t e;
+  if (gemm == 1) {
+    e = launch_gemm1_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n, ctx->d_status, st, ctx->tune,
+                              0, stall);
+  } else {
+    launches = 0;
+    e = launch_gemm2_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n, ctx->opt.io_dtype, out_is_io,
+                              ctx->d_status, st, ctx->tune, 0, &launches);
+  }
+  count(ctx, launches);
   prof_end(ctx, pi, st);
   return from_cuda(e);
 }
 
-// Grid-row ranges of the tensor-core GEMM1 for K directions of system s:
-// enough items for four waves over the SMs, at most 8 ranges, nsplit * K <=
-// k_max (the partial X share the context's X buffer) and at least 64 stages
-// of the reduction per range.  1 at the benchmark's K = 16.
+// Grid-row ranges of the tensor-core GEMM1 for K directions of system s.
+// The work items (tiles x directions x ranges) are of equal size, so the
+// launch time follows the number of waves over the SMs: the count that fills
+// the last wave best (by more than half a percent over a smaller count), with
+// at most 8 ranges, nsplit * K <= k_max (the partial X share the context's X
+// buffer) and at least 64 stages of the reduction per range.  1 at the
+// benchmark's K = 16 (4352 items, 0.987 of 29 waves); 5 at K = 1 there
+// (1360 items, 0.994 of 9 waves, against 0.895 for 1-4 ranges).
 int choose_split(lrdm_ctx* ctx, int s, int K) {
   const SysState& S = ctx->sys[s];
   if (!is_tc(ctx->opt.prec) || K <= 0 || ctx->tc_pid.empty()) return 1;
@@ -362,13 +370,21 @@ int choose_split(lrdm_ctx* ctx, int s, int K) {
   const bool wide = ctx->tune.g1_nb == 256;
   const int dpt = wide ? 1 : ctx->tune.g1_dpt;
   const long long items = (long long)(wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
-  const long long waves = 4LL * (ctx->sm_count > 0 ? ctx->sm_count : 148);
-  int want = (int)((waves + items - 1) / items);
+  const long long sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
   int smax = S.kmax / K;
   if (smax > 8) smax = 8;
   if (smax > pr.nch / 64) smax = pr.nch / 64;
-  if (want > smax) want = smax;
-  return want < 1 ? 1 : want;
+  int best = 1;
+  double best_fill = 0.0;
+  for (int sp = 1; sp <= smax; ++sp) {
+    const long long n = items * sp;
+    const double fill = (double)n / (double)(((n + sms - 1) / sms) * sms);
+    if (fill > best_fill + 0.005) {
+      best_fill = fill;
+      best = sp;
+    }
+  }
+  return best;
 }
 
 TcEntry tc_entry(lrdm_ctx* ctx, int s, int c, int K) {
@@ -757,6 +773,7 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
             rc = LRDM_ERR_CUDA;
             break;
           }
+          if ((rc = dalloc(ctx, &pr.part, (size_t)G2_MAX_SPLIT * ctx->sys[s].Ng)) != LRDM_OK) break;
           ctx->tc_pid[2 * s + c] = (int)ctx->tc_host.size();
           ctx->tc_host.push_back(pr);
         }

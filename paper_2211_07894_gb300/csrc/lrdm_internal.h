@@ -316,8 +316,11 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 // first weighted stage, so its bounded wait expires (timeout status).
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
                                   const TcTune& t, int nch_lim = 0, int stall = 0);
+// launches (may be null) counts the kernels enqueued: one per 16 problems, plus
+// one part-sum kernel per problem whose items were split (K = 1)
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
-                                  int* status, cudaStream_t st, const TcTune& t, int nR_lim = 0);
+                                  int* status, cudaStream_t st, const TcTune& t, int nR_lim = 0,
+                                  int* launches = nullptr);
 bool tc_supported();
 
 }  // namespace lrdm

@@ -370,6 +370,7 @@ lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t s
     for (int q = 0; q < nk; ++q) {
       TcProblem pr;
       if (!build_tc_problem(prec, ctx->kp_ch[q], S, 0, pr)) return LRDM_ERR_CUDA;
+      LRDM_CK(dalloc(ctx, &pr.part, (size_t)G2_MAX_SPLIT * S.Ng));
       ctx->kp_pid[q] = (int)ctx->tc_host.size();
       ctx->tc_host.push_back(pr);
     }

@@ -17,10 +17,16 @@ struct TcProblem {
   const float* a;                        // GEMM1 weights of this channel (direction 0)
   const void* psi0;                      // GEMM2 epilogue rows: bf16 hi / fp32
   const void* psi1;                      // bf16 lo
+  double* part;                          // GEMM2 j-tile part sums [G2_MAX_SPLIT][Ng] (small K)
   int ns, ns_pad, nI, NJ, ntiles, ntiles_w, nch, nR, kmax;   // GEMM1: nI blocks, ntiles tiles; GEMM2: NJ, nR
 };
 
 constexpr int TC_MAX_SLOTS = 16;        // problems per grouped launch
+// GEMM2 at small K: a (row block, direction) item split into up to
+// G2_MAX_SPLIT parts over its j-tiles (at most G2_MAX_NJ tiles), parts * K <=
+// G2_MAX_SPLIT so that the part sums fit the problem's part buffer
+constexpr int G2_MAX_SPLIT = 4;
+constexpr int G2_MAX_NJ = 64;
 
 // Launch shape of the tensor-core contractions (chosen by the autotuner or
 // the defaults): GEMM1 MMA width (128: square tiles with 1 or 2 directions;

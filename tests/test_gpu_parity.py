@@ -532,3 +532,36 @@ def test_maximum_directions(lib, prec):
         assert ctx.status() == 0
         vref = oracle.backward(osys, fbar, V=cfg["V"])["vbar"]
         assert per_direction_rel_err(vbar[0].double().cpu().numpy(), vref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec,bn", [("bf16x3", 256), ("bf16x3", 128), ("tf32", 256)])
+def test_response_split_over_j_tiles(lib, prec, bn, tmp_path, monkeypatch):
+    """N_s = 2048 on a ragged grid (2464 rows): with K = 1 the response
+    items are split into 4 parts over their j-tiles, whose FP64 part sums a
+    second kernel adds in order; K = 2 and 4 run unsplit.  All three against
+    the oracle, and K = 1 and 2 against the same directions of K = 4."""
+    from gpu_helpers import directions, make_context
+    cfg = _ragged(cfg_id=24, n=(16, 14, 11), ns=2048, K=4, ne=1800)
+    io = IO[prec]
+    code = {"tf32": 2, "bf16x3": 3}[prec]
+    cache = tmp_path / "tune.jsonl"
+    cache.write_text('{"key": "%s", "g1_nb": 256, "g1_dpt": 1, "g2_bn": %d, "g2_kgroup": 4}\n'
+                     % (_tune_key([cfg], code), bn))
+    monkeypatch.setenv("LRDM_TUNE_CACHE", str(cache))
+    ctx, _ = make_context([cfg], prec, io, autotune=True)
+    assert ctx.tuning()["g2_bn"] == bn
+    V = directions(cfg, io)
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    out = {}
+    for K in (1, 2, 4):
+        F, _ = ctx.gateaux([V[:K].contiguous()])
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        out[K] = F[0].double().cpu().numpy()
+        err = per_direction_rel_err(out[K], ref["F"][:K])
+        print(f"N_s 2048 {prec} bn {bn} K = {K}: f err {err:.3e}")
+        assert err < TOL[prec]
+    # same projections up to FP32 rounding of the grid reduction: the split
+    # response agrees with the unsplit one far inside the tolerance
+    for K in (1, 2):
+        assert per_direction_rel_err(out[K], out[4][:K]) < 0.1 * TOL[prec]
