@@ -234,6 +234,69 @@ def oracle_step(sysm, V, R):
     oracle.backward(sysm, res["F"], res)
 
 
+# the same oracle step on one host core: a 16^3 sample (the smallest grid that
+# holds N_s = 4096 orthonormal states; 1/216 of the 96^3 rows)
+ORACLE_1T_GRID = (16, 16, 16)
+
+
+def one_thread_child(path):
+    """Runs in a child process whose BLAS pools have one thread: loads the
+    sample written by time_oracle_one_thread, times one oracle step, prints
+    the seconds."""
+    import numpy as np
+    import oracle
+    d = np.load(path)
+    n = tuple(int(x) for x in d["n"])
+    sysm = oracle.System(n=n, h=H, psi=[d["psi"]], eps=[d["eps"]], rho=[d["rho"]], n_electrons=NE,
+                         kT=KT, g=2.0)
+    t0 = time.perf_counter()
+    oracle_step(sysm, d["V"], d["R"])
+    print(time.perf_counter() - t0)
+
+
+def time_oracle_one_thread():
+    """The oracle step on one core, beside the all-cores figure: the sample
+    is built here with every core, the step is timed in a child process with
+    OPENBLAS / OMP / MKL threads = 1.  GD/s scaled by the row ratio; None
+    when the child fails."""
+    import tempfile
+    import numpy as np
+    global ORACLE_SAMPLE_GRID
+    saved = ORACLE_SAMPLE_GRID
+    ORACLE_SAMPLE_GRID = ORACLE_1T_GRID
+    try:
+        sysm, V, R, scale = oracle_sample_system()
+    finally:
+        ORACLE_SAMPLE_GRID = saved
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "sample.npz")
+        np.savez(path, n=np.asarray(ORACLE_1T_GRID), psi=sysm.psi[0], eps=sysm.eps[0], rho=sysm.rho[0],
+                 V=V, R=R)
+        try:
+            r = subprocess.run([sys.executable, "-c", f"import bench; bench.one_thread_child({path!r})"],
+                               cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+            sec = float(r.stdout.strip().splitlines()[-1])
+        except Exception:
+            return None
+    return {"value": 1.0 / (sec * scale), "unit": "GD/s", "cores": 1, "seconds": sec,
+            "sample": f"oracle.gateaux + lrdm_apply + backward, K=1, N_s={NS}, grid {ORACLE_1T_GRID[0]}^3 "
+                      f"(1/{int(scale)} of the 96^3 rows), one BLAS thread; GD/s scaled by the row ratio"}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), else what platform reports."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
 # Brillouin-zone-sampled response (lrdm_kp_gateaux): a periodic workload of
 # nk k-points with complex subspaces, timed beside the main step.
 KP_GRID = (48, 48, 48)
@@ -397,7 +460,8 @@ def reference_arm(args, rank, world):
             "config": {"workload": f"96^3 grid, N_s={NS}, K={KDIR} (oracle on a bounded sample)",
                        "grid": list(GRID), "n_s": NS, "K": KDIR},
             "cpu_baseline": {"value": gds, "unit": "GD/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model(),
+                             "one_thread": time_oracle_one_thread()},
             "e2e": {"value": gds, "unit": "GD/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -766,7 +830,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gds, dt, sample = time_oracle(1, 0)
         cpu = {"value": gds, "unit": "GD/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "cpu_model": cpu_model(), "one_thread": time_oracle_one_thread()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GD/s", "n_gpus": world,

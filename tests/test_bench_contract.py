@@ -33,6 +33,8 @@ def test_reference_arm_line():
     assert d["higher_is_better"] is True and d["value"] > 0 and d["vs_baseline"] is None
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    one = d["cpu_baseline"]["one_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and d["cpu_baseline"]["cpu_model"]
     assert d["e2e"] == {"value": d["value"], "unit": "GD/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
