@@ -102,3 +102,29 @@ def test_library_exports_nothing_else(lib):
                          check=True).stdout
     exported = {ln.split()[-1] for ln in out.splitlines() if len(ln.split()) == 3 and ln.split()[1] == "T"}
     assert exported == set(_declared_functions())
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    """Without a CUDA device the library refuses a valid system in every
+    precision (no host fallback exists), and a missing library is an error."""
+    import torch
+    from paper_2211_07894_gb300 import binding
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    psi = np.zeros((64, 8), dtype=np.float32)
+    eps = np.linspace(-1.0, 1.0, 8)
+    for prec in binding.PRECISIONS.values():
+        o = binding.lrdm_default_options()
+        o.prec = prec
+        s = binding.lrdm_system()
+        s.n[0] = s.n[1] = s.n[2] = 4
+        s.h[0] = s.h[1] = s.h[2] = 0.5
+        s.nspin = 1
+        s.ns[0] = s.ld_psi[0] = 8
+        s.psi[0] = psi.ctypes.data
+        s.eps[0] = eps.ctypes.data
+        s.n_electrons, s.kT = 4.0, 0.01
+        code, h = binding.lrdm_create([s], o)
+        assert code != 0 and not h.value, prec
+    with pytest.raises(OSError):
+        binding.load(os.path.join(ROOT, "no_such_dir", "liblrdm.so"))
