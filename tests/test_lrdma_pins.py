@@ -1,5 +1,6 @@
 """Pins of the accumulated LRDM step's decisions (oracle.lrdma_step, §II.B.1,
-Eqs. linearapprox, linearityIndicator, accum), CPU only.
+Eqs. linearapprox, linearityIndicator, accum), CPU only, on a real system and
+on a Brillouin-zone-sampled one (§II.C closing paragraphs).
 
 The paper prints no worked example of the decisions, so they are pinned on a
 residual map that is exactly linear: one fixed system (so the Jacobian J, and
@@ -32,12 +33,28 @@ import workloads
 from helpers import oracle_system, rel_err
 
 
-@pytest.fixture(scope="module")
-def lin():
-    cfg = workloads.random_system(71, (8, 7, 6), 24, 26.0, 0.02, 3)
-    sysm = oracle_system(cfg)
-    R0 = workloads.smooth_field(cfg["n"], cfg["h"], 0.1, workloads.rng_for(71, 1))[None]
-    return sysm, R0
+def _kpoint_system(cfg):
+    mu = oracle.solve_mu_kpoints(cfg["eps"], cfg["k_weights"], cfg["n_electrons"], cfg["kT"], cfg["g"])
+    ks = oracle.KpointSystem(n=cfg["n"], h=cfg["h"], psi=cfg["psi"], eps=cfg["eps"], k_weights=cfg["k_weights"],
+                             rho=np.zeros(int(np.prod(cfg["n"]))), n_electrons=cfg["n_electrons"],
+                             kT=cfg["kT"], g=cfg["g"])
+    ks.rho = oracle.density_kpoints(ks, mu, cfg["rho_floor"])
+    return ks
+
+
+@pytest.fixture(scope="module", params=["real", "kpoint"])
+def lin(request):
+    """A fixed system (real, or sampled at 4 k-points with complex
+    subspaces), a residual R0 and the Gateaux map J of that system."""
+    if request.param == "real":
+        cfg = workloads.random_system(71, (8, 7, 6), 24, 26.0, 0.02, 3)
+        sysm = oracle_system(cfg)
+        R0 = workloads.smooth_field(cfg["n"], cfg["h"], 0.1, workloads.rng_for(71, 1))[None]
+        return sysm, R0, lambda u: oracle.gateaux(sysm, u[None])["F"][0]
+    cfg = workloads.kpoint_system(72, (8, 7, 6), 24, 4, 26.0, 0.02, 3)
+    sysm = _kpoint_system(cfg)
+    R0 = workloads.smooth_field(cfg["n"], cfg["h"], 0.1, workloads.rng_for(72, 1))
+    return sysm, R0, lambda u: oracle.gateaux_kpoints(sysm, u[None])["F"][0]
 
 
 def _first(sysm, R0, alpha, s_tol=0.3, r_max=20):
@@ -62,7 +79,7 @@ def _krylov_equal(out, ref, R):
 
 @pytest.mark.parametrize("c", [2.0, 0.7, 1.05])
 def test_beta_closed_form_and_CL(lin, c):
-    sysm, R0 = lin
+    sysm, R0, _ = lin
     state, _ = _first(sysm, R0, alpha=0.5)
     R1 = c * state.R_lin
     out = oracle.lrdma_step(sysm, state, R1, alpha=0.5, r_norm_clear=1e9)
@@ -76,7 +93,7 @@ def test_beta_closed_form_and_CL(lin, c):
 
 @pytest.mark.parametrize("alpha", [0.5, 0.3])
 def test_reuse_closed_form(lin, alpha):
-    sysm, R0 = lin
+    sysm, R0, _ = lin
     state, first = _first(sysm, R0, alpha=alpha, s_tol=0.02)
     s = first["s_rel"]
     r0 = first["rank"]
@@ -97,7 +114,7 @@ def test_reuse_closed_form(lin, alpha):
 
 
 def test_CR_rebuilds_like_lrdm(lin):
-    sysm, R0 = lin
+    sysm, R0, _ = lin
     state, _ = _first(sysm, R0, alpha=1.0)
     R1 = state.R_lin.copy()
     rn = float(np.sqrt(sysm.w * np.sum(R1 * R1)))
@@ -108,7 +125,7 @@ def test_CR_rebuilds_like_lrdm(lin):
 
 @pytest.mark.parametrize("r_max_iter", [1, 3, 5])
 def test_accumulate_directions_and_CT(lin, r_max_iter):
-    sysm, R0 = lin
+    sysm, R0, J = lin
     w = sysm.w
     state, first = _first(sysm, R0, alpha=1.0, r_max=2, s_tol=1e-9)
     r0 = first["rank"]
@@ -117,7 +134,7 @@ def test_accumulate_directions_and_CT(lin, r_max_iter):
     # R_lin itself lies in span(U_old, t_last) after a Krylov build; a small
     # part outside it (beta stays below beta_tol) tells R's complement from t's
     R_lin = state.R_lin.copy()
-    z = workloads.smooth_field(sysm.n, sysm.h, 1.0, workloads.rng_for(71, 2))[None]
+    z = workloads.smooth_field(sysm.n, sysm.h, 1.0, workloads.rng_for(71, 2)).reshape(R_lin.shape)
     R1 = R_lin + 0.05 * np.sqrt(w * np.sum(R_lin * R_lin)) * z
     beta = abs(np.sqrt(np.sum(R_lin * R_lin) / np.sum(R1 * R1)) - 1.0)
     s_tol = 1e-9
@@ -136,7 +153,7 @@ def test_accumulate_directions_and_CT(lin, r_max_iter):
     assert rel_err(U[r0], comp / np.sqrt(w * np.sum(comp * comp))) < 1e-12
     # each next one comes from the previous derivative, orthogonalised against all directions
     for j in range(1, m):
-        t_prev = oracle.gateaux(sysm, U[r0 + j - 1][None])["F"][0]
+        t_prev = J(U[r0 + j - 1])
         assert rel_err(state.T[r0 + j - 1], t_prev) < 1e-14
         assert _span_residual(U[r0 + j], U[:r0 + j] + [t_prev], w) < 1e-10
     # the fit uses every kept derivative
@@ -152,7 +169,7 @@ def test_accumulate_directions_and_CT(lin, r_max_iter):
 
 
 def test_accumulate_stops_at_s_tol_without_CT(lin):
-    sysm, R0 = lin
+    sysm, R0, _ = lin
     state, _ = _first(sysm, R0, alpha=1.0, r_max=2, s_tol=1e-9)
     R1 = state.R_lin.copy()
     out = oracle.lrdma_step(sysm, state, R1, alpha=0.5, s_tol=0.3, r_max_iter=5, r_norm_clear=1e9)
