@@ -73,7 +73,7 @@ def parse():
                    help="skip timing the plain FP64 GPU form")
     p.add_argument("--grid", type=int, default=96, help="grid edge (96 = the benchmark workload)")
     p.add_argument("--ns", type=int, default=NS)
-    p.add_argument("--fwd-reps", type=int, default=10,
+    p.add_argument("--fwd-reps", type=int, default=20,
                    help="graph replays of the forward call timed for forward_only")
     p.add_argument("--no-kpoint", action="store_true",
                    help="skip the Brillouin-zone-sampled (k-point) leg")
