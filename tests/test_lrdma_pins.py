@@ -1,6 +1,7 @@
 """Pins of the accumulated LRDM step's decisions (oracle.lrdma_step, §II.B.1,
-Eqs. linearapprox, linearityIndicator, accum), CPU only, on a real system and
-on a Brillouin-zone-sampled one (§II.C closing paragraphs).
+Eqs. linearapprox, linearityIndicator, accum), CPU only, on a restricted
+system, a spin pair (§II.D) and a Brillouin-zone-sampled system (§II.C
+closing paragraphs).
 
 The paper prints no worked example of the decisions, so they are pinned on a
 residual map that is exactly linear: one fixed system (so the Jacobian J, and
@@ -42,15 +43,20 @@ def _kpoint_system(cfg):
     return ks
 
 
-@pytest.fixture(scope="module", params=["real", "kpoint"])
+@pytest.fixture(scope="module", params=["real", "spin", "kpoint"])
 def lin(request):
-    """A fixed system (real, or sampled at 4 k-points with complex
-    subspaces), a residual R0 and the Gateaux map J of that system."""
+    """A fixed system (restricted, a spin pair with a shared mu, or sampled at
+    4 k-points with complex subspaces), a residual R0 and the Gateaux map J
+    of that system."""
     if request.param == "real":
         cfg = workloads.random_system(71, (8, 7, 6), 24, 26.0, 0.02, 3)
         sysm = oracle_system(cfg)
         R0 = workloads.smooth_field(cfg["n"], cfg["h"], 0.1, workloads.rng_for(71, 1))[None]
         return sysm, R0, lambda u: oracle.gateaux(sysm, u[None])["F"][0]
+    if request.param == "spin":
+        cfg = workloads.spin_pair_system(73, (8, 7, 6), 24, 20, 22.0, 0.02, 3)
+        sysm = oracle_system(cfg)
+        return sysm, cfg["R"], lambda u: oracle.gateaux(sysm, u[None])["F"][0]
     cfg = workloads.kpoint_system(72, (8, 7, 6), 24, 4, 26.0, 0.02, 3)
     sysm = _kpoint_system(cfg)
     R0 = workloads.smooth_field(cfg["n"], cfg["h"], 0.1, workloads.rng_for(72, 1))
@@ -134,7 +140,10 @@ def test_accumulate_directions_and_CT(lin, r_max_iter):
     # R_lin itself lies in span(U_old, t_last) after a Krylov build; a small
     # part outside it (beta stays below beta_tol) tells R's complement from t's
     R_lin = state.R_lin.copy()
-    z = workloads.smooth_field(sysm.n, sysm.h, 1.0, workloads.rng_for(71, 2)).reshape(R_lin.shape)
+    rz = workloads.rng_for(71, 2)
+    ng = int(np.prod(sysm.n))
+    z = np.stack([workloads.smooth_field(sysm.n, sysm.h, 1.0, rz) for _ in range(R_lin.size // ng)])
+    z = z.reshape(R_lin.shape) / np.sqrt(w * np.sum(z * z))
     R1 = R_lin + 0.05 * np.sqrt(w * np.sum(R_lin * R_lin)) * z
     beta = abs(np.sqrt(np.sum(R_lin * R_lin) / np.sum(R1 * R1)) - 1.0)
     s_tol = 1e-9
