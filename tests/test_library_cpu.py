@@ -128,3 +128,43 @@ def test_no_cpu_fallback_without_a_gpu(lib):
         assert code != 0 and not h.value, prec
     with pytest.raises(OSError):
         binding.load(os.path.join(ROOT, "no_such_dir", "liblrdm.so"))
+
+
+STRUCTS = ["lrdm_system", "lrdm_options", "lrdm_kpoint_system", "lrdm_lrdma_params", "lrdm_lrdma_report"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct of include/lrdm.h as the binding declares it with ctypes:
+    same size and the same offset for each field, checked against a C
+    program compiled from the header (a drifted field would pass garbage
+    through the boundary without any error)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2211_07894_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lrdm.h"', "int main(void) {"]
+    for name in STRUCTS:
+        st = getattr(binding, name)
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {}
+    for ln in out:
+        parts = ln.split()
+        if len(parts) == 3:
+            c_layout[(parts[0], parts[1])] = int(parts[2])
+    for name in STRUCTS:
+        st = getattr(binding, name)
+        assert c_layout[(name, "size")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert c_layout[(name, field)] == getattr(st, field).offset, (name, field)
