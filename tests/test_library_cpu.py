@@ -168,3 +168,26 @@ def test_binding_structs_match_the_header(tmp_path):
         assert c_layout[(name, "size")] == ctypes.sizeof(st), name
         for field, _ in st._fields_:
             assert c_layout[(name, field)] == getattr(st, field).offset, (name, field)
+
+
+def test_binding_argtypes_match_header_prototypes(lib):
+    """Each prototype of include/lrdm.h has ctypes argtypes in the binding
+    (without them ctypes would pass doubles and 64-bit pointers by guess),
+    with the same number of parameters."""
+    text = ""
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            text += open(os.path.join(inc, fn)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"\b(lrdm_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S)
+    assert len(protos) >= 20
+    checked = 0
+    for name, params in protos:
+        params = " ".join(params.split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        argtypes = getattr(getattr(lib, name), "argtypes", None)
+        assert argtypes is not None, f"{name} has no argtypes"
+        assert len(argtypes) == n, (name, n, len(argtypes))
+        checked += 1
+    assert checked == len(protos)
