@@ -135,9 +135,10 @@ STRUCTS = ["lrdm_system", "lrdm_options", "lrdm_kpoint_system", "lrdm_lrdma_para
 
 def test_binding_structs_match_the_header(tmp_path):
     """Every struct of include/lrdm.h as the binding declares it with ctypes:
-    same size and the same offset for each field, checked against a C
-    program compiled from the header (a drifted field would pass garbage
-    through the boundary without any error)."""
+    same size and the same offset for each field, and the enum values the
+    binding hardcodes, checked against a C program compiled from the header
+    (a drifted field or code would pass garbage through the boundary without
+    any error)."""
     import ctypes
     import shutil
     import subprocess
@@ -151,6 +152,14 @@ def test_binding_structs_match_the_header(tmp_path):
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
         for field, _ in st._fields_:
             lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    consts = {"LRDM_FP64": binding.PRECISIONS["fp64"], "LRDM_FP32": binding.PRECISIONS["fp32"],
+              "LRDM_TF32": binding.PRECISIONS["tf32"], "LRDM_BF16X3": binding.PRECISIONS["bf16x3"],
+              "LRDM_DTYPE_F64": binding.DTYPE_F64, "LRDM_DTYPE_F32": binding.DTYPE_F32,
+              "LRDM_DEBUG_STALL_PROJECTION": binding.DEBUG_STALL_PROJECTION}
+    events = ["LRDMA_FRESH", "LRDMA_REUSE", "LRDMA_ACCUMULATE", "LRDMA_CLEAR_LINEARITY",
+              "LRDMA_CLEAR_RESIDUAL", "LRDMA_CLEAR_TRUNCATED"]
+    for c in list(consts) + events:
+        lines.append(f'  printf("const {c} %d\\n", (int)({c}));')
     lines += ["  return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
@@ -168,6 +177,10 @@ def test_binding_structs_match_the_header(tmp_path):
         assert c_layout[(name, "size")] == ctypes.sizeof(st), name
         for field, _ in st._fields_:
             assert c_layout[(name, field)] == getattr(st, field).offset, (name, field)
+    for c, v in consts.items():
+        assert c_layout[("const", c)] == v, c
+    # the binding's event names in the header's order (fresh, reuse, accumulate, CL, CR, CT)
+    assert [c_layout[("const", e)] for e in events] == sorted(binding.LRDMA_EVENTS)
 
 
 def test_binding_argtypes_match_header_prototypes(lib):
