@@ -451,6 +451,14 @@ def time_oracle(steps, warmup):
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
+    if (world > 1 and "numpy" not in sys.modules and os.environ.get("OMP_NUM_THREADS") == "1"
+            and not os.environ.get("OPENBLAS_NUM_THREADS")):
+        # torchrun starts every rank with one OpenMP thread; rank 0 is the only
+        # rank working here, so its BLAS gets the host's cores (an explicit
+        # OPENBLAS_NUM_THREADS is left as set)
+        n = str(os.cpu_count() or 1)
+        os.environ["OMP_NUM_THREADS"] = n
+        os.environ["OPENBLAS_NUM_THREADS"] = n
     steps = max(1, args.steps)
     gds, dt, sample = time_oracle(steps, max(0, min(args.warmup, 1)))
     line = {"impl": "reference", "metric": METRIC, "value": gds, "unit": "GD/s",

@@ -70,3 +70,20 @@ def test_run_log_and_context(tmp_path):
     assert all("time_utc" in r and r["host"]["cores"] >= 1 for r in recs)
     assert abs(sum(bench.kp_weights(bench.KP_NK)) - 1.0) < 1e-15
     assert "3.4x" in bench.PAPER_CONTEXT["scf_cost_reduction_vs_kerker"]
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """Launched as the multi-GPU runs are (torchrun, 2 ranks, 127.0.0.1): rank
+    0 alone times the oracle and prints the one JSON line, the other rank
+    exits 0 without work."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", "29517", os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    # torchrun's one OpenMP thread per rank does not throttle the only working rank
+    assert d["cpu_baseline"]["cores"] == os.cpu_count()
