@@ -598,6 +598,10 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    # every library call runs on a dedicated stream: the forward call's CUDA
+    # graph is captured and replayed only on a stream other than the legacy
+    # default one
+    torch.cuda.set_stream(torch.cuda.Stream())
     if args.kpoint_only:
         from paper_2211_07894_gb300 import build as _build
         _build.build()

@@ -116,10 +116,11 @@ typedef struct lrdm_options {
   int poisson_symbol;    /* 0: 4 pi/|G|^2 (spectral); 1: second-order FD symbol  */
   int use_graph;         /* replay lrdm_gateaux_batch from a captured CUDA graph  */
   int autotune;          /* tensor-core precisions: 0 -> default launch shape
-                            (128 x 256 projection tiles, response j-tile 256,
-                            direction group 4); 1 -> lrdm_create times the
-                            candidates (projection: 128 x 256 tiles, or 128 x 128
-                            tiles with 1 or 2 directions; response: j-tile 128
+                            (256 x 256 projection tiles on CTA pairs, response
+                            j-tile 256, direction group 4); 1 -> lrdm_create
+                            times the candidates (projection: pair tiles,
+                            128 x 256 tiles, or 128 x 128 tiles with 1 or 2
+                            directions; response: j-tile 128
                             or 256 x group 1, 2, 4) on the context's
                             own problems and keeps the fastest; with the
                             environment variable LRDM_TUNE_CACHE naming a file,
@@ -205,7 +206,9 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
  * K is limited to 16: larger K returns LRDM_ERR_INVALID_ARG before anything is
  * enqueued.  The first call on each device looks the array's device address
  * up (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array: calls that
+ * before any stream capture.  The address belongs to the device's primary
+ * context: after cudaDeviceReset the library must be loaded again before
+ * this entry point is used.  Every call shares the array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Asynchronous. */
 lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int io_dtype, int K,
@@ -252,9 +255,21 @@ lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_
 
 /* Launch shape of the tensor-core contractions chosen at create (defaults
  * or the autotuner's choice): projection MMA width (128: square tiles; 256:
- * 128 x 256 tiles, one direction), directions per projection square tile,
- * response j-tile width, response direction group.  Any pointer may be NULL. */
+ * 128 x 256 tiles, one direction; 512: 256 x 256 tiles, one direction, each
+ * computed by a pair of CTAs on neighbouring SMs with M = 256 pair MMAs),
+ * directions per projection square tile, response j-tile width, response
+ * direction group.  Any pointer may be NULL. */
 lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_nb, int* g1_dpt, int* g2_bn, int* g2_kgroup);
+
+/* Sets the launch shape used by the following calls on ctx (values as
+ * returned by lrdm_get_tuning: g1_nb 128, 256 or 512; g1_dpt 1, or 2 with
+ * g1_nb = 128; g2_bn 128 or 256; g2_kgroup 1, 2 or 4).  Results depend on the
+ * shape only through the blocking of the reductions.  A captured forward
+ * graph is dropped and captured again by the next call.  Must not be called
+ * while another host thread uses ctx.  Errors: INVALID_ARG (null ctx or a
+ * value outside the sets above), UNSUPPORTED (a CUDA-core precision, which
+ * has no such shape).  No device work. */
+lrdm_status lrdm_set_tuning(lrdm_ctx* ctx, int g1_nb, int g1_dpt, int g2_bn, int g2_kgroup);
 
 /* One LRDM preconditioning step of system `sys` with adaptively chosen rank
  * (§II.B, Eqs. jlowrank, krylovOrtho, plowrank, relativeError, quasinewton):

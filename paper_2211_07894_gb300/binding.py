@@ -65,7 +65,7 @@ EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_ap
            "lrdm_get_tuning", "lrdm_krylov_step", "lrdm_lrdma_default_params", "lrdm_lrdma_create",
            "lrdm_lrdma_step", "lrdm_lrdma_clear", "lrdm_lrdma_destroy", "lrdm_kp_create",
            "lrdm_kp_gateaux", "lrdm_lrdma_get_state", "lrdm_lrdma_export", "lrdm_lrdma_import",
-           "lrdm_kp_get_split"]
+           "lrdm_kp_get_split", "lrdm_set_tuning"]
 
 
 class lrdm_lrdma_params(ctypes.Structure):
@@ -147,6 +147,8 @@ def load(path: Optional[str] = None):
     lib.lrdm_get_tuning.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                     POINTER(c_int)]
     lib.lrdm_get_tuning.restype = c_int
+    lib.lrdm_set_tuning.argtypes = [c_void_p, c_int, c_int, c_int, c_int]
+    lib.lrdm_set_tuning.restype = c_int
     lib.lrdm_kp_create.argtypes = [POINTER(c_void_p), POINTER(lrdm_kpoint_system),
                                    POINTER(lrdm_options), c_void_p]
     lib.lrdm_kp_create.restype = c_int
@@ -273,6 +275,10 @@ def lrdm_get_tuning(ctx):
     _check("lrdm_get_tuning", load().lrdm_get_tuning(ctx, ctypes.byref(z), ctypes.byref(a),
                                                      ctypes.byref(b), ctypes.byref(c)))
     return dict(g1_nb=z.value, g1_dpt=a.value, g2_bn=b.value, g2_kgroup=c.value)
+
+
+def lrdm_set_tuning(ctx, g1_nb, g1_dpt, g2_bn, g2_kgroup) -> int:
+    return load().lrdm_set_tuning(ctx, g1_nb, g1_dpt, g2_bn, g2_kgroup)
 
 
 def lrdm_kp_create(system: lrdm_kpoint_system, options: lrdm_options, stream: int = 0):
@@ -491,6 +497,13 @@ class Context:
         """Launch shape of the tensor-core contractions (defaults or autotuned)."""
         return lrdm_get_tuning(self.handle)
 
+    def set_tuning(self, g1_nb=None, g1_dpt=None, g2_bn=None, g2_kgroup=None):
+        """Pins the launch shape (unset fields keep their current value)."""
+        t = self.tuning()
+        _check("lrdm_set_tuning", lrdm_set_tuning(
+            self.handle, t["g1_nb"] if g1_nb is None else g1_nb, t["g1_dpt"] if g1_dpt is None else g1_dpt,
+            t["g2_bn"] if g2_bn is None else g2_bn, t["g2_kgroup"] if g2_kgroup is None else g2_kgroup))
+
     def profile(self, on=True):
         _check("lrdm_profile_enable", lrdm_profile_enable(self.handle, 1 if on else 0))
 
@@ -621,6 +634,13 @@ class KpContext:
     def tuning(self):
         """Launch shape of the tensor-core contractions (defaults or autotuned)."""
         return lrdm_get_tuning(self.handle)
+
+    def set_tuning(self, g1_nb=None, g1_dpt=None, g2_bn=None, g2_kgroup=None):
+        """Pins the launch shape (unset fields keep their current value)."""
+        t = self.tuning()
+        _check("lrdm_set_tuning", lrdm_set_tuning(
+            self.handle, t["g1_nb"] if g1_nb is None else g1_nb, t["g1_dpt"] if g1_dpt is None else g1_dpt,
+            t["g2_bn"] if g2_bn is None else g2_bn, t["g2_kgroup"] if g2_kgroup is None else g2_kgroup))
 
     def split(self, K):
         """Grid-row ranges of the projection for a K-direction call."""

@@ -7,6 +7,8 @@
 
 #include <math.h>
 
+#include <atomic>
+
 namespace lrdm {
 namespace {
 
@@ -273,12 +275,18 @@ cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = 2 * (size_t)K * (K + 1) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the shared-memory limit is a per-device function attribute: one bit per
+  // device ordinal records that it was raised (a racing first call from
+  // another host thread sets the same value again)
+  static std::atomic<unsigned long long> attr_set{0};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
     e = cudaFuncSetAttribute(k_ls_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              2 * KMAX_LIMIT * (KMAX_LIMIT + 1) * (int)sizeof(double));
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   k_ls_solve<<<1, KMAX_LIMIT, smem, st>>>(partial, LS_BLOCKS, K, w, rcond, coef, coeff_out, scal,
                                           status);
@@ -318,22 +326,30 @@ constexpr int SC_TOTAL = SC_STATUS + 1;
 static __device__ __align__(256) double g_ls_scratch[SC_TOTAL];
 
 constexpr int MAX_DEVICES = 64;
-double* g_scratch_addr[MAX_DEVICES] = {nullptr};
+// Device address of g_ls_scratch per device ordinal.  Host threads that race
+// on a device's first call each look the address up and store the same value;
+// the atomics make that race well defined.  The address belongs to the
+// device's primary context: after cudaDeviceReset the process must reload
+// the library before calling lrdm_apply_static again.
+std::atomic<double*> g_scratch_addr[MAX_DEVICES];
 
 // Device address of g_ls_scratch on the current device (looked up once per
-// device; the host-side symbol is not a device address).
+// device with that device current; the host-side symbol is not a device
+// address).
 cudaError_t static_scratch(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  if (!g_scratch_addr[dev]) {
+  double* a = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_ls_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    a = static_cast<double*>(p);
+    g_scratch_addr[dev].store(a, std::memory_order_release);
   }
-  *out = g_scratch_addr[dev];
+  *out = a;
   return cudaSuccess;
 }
 

@@ -1,11 +1,14 @@
 // Tensor-core (tcgen05) forms of the two contractions on sm_103a.
 //
 // GEMM1  X_k[i, j] = sum_r (a_k[r] Psi[r, i]) Psi[r, j]     (H-breve', §II.C)
-//        tile 128 (i) x 128 (j), blocks I <= J only (upper part), two
-//        directions per tile; the whole grid reduction runs inside one tile,
-//        in segments of 1024 rows whose TMEM results are summed in FP32
+//        upper-part tiles only; the whole grid reduction runs inside one
+//        tile, in segments of 1024 rows whose TMEM results are summed in FP32
 //        registers; the a_k weighting is applied to the A rows between their
 //        TMA load and the MMAs, which read the weighted A from tensor memory.
+//        Three forms: 256 x 256 tiles on a CTA pair (cta_group::2, M = 256
+//        MMAs, each CTA holding half of the A and B rows; the default),
+//        128 x 256 tiles on one CTA, and 128 x 128 tiles with one or two
+//        directions.
 // GEMM2  drho_k(r) = factor * sum_j Psi[r, j] (sum_{i <= j} Psi[r, i] X''_k[i, j])
 //        tile 128 (r) x 256 (j); for each j-block the i-reduction stops at the
 //        block's end (X'' is zero below the diagonal); two TMEM accumulators so
@@ -29,6 +32,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -557,9 +561,8 @@ __device__ __forceinline__ const TcProblem* g1_item(const G1Params& P, int item,
 // split into bf16 hi / lo (or rounded to TF32) and stored at TMEM address ta
 // (this warp's lane quarter, first column of the stage's slot).  Packed FP32
 // pair arithmetic (two elements per instruction).
-template <int PREC, int NB>
-__device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd, uint32_t ta) {
-  using C = G1Cfg<PREC, NB>;
+template <int PREC, class C>
+__device__ __forceinline__ void weight_stage_c(uint32_t st, int row, int h, int nd, uint32_t ta) {
   if (PREC == LRDM_BF16X3) {
     // A rows of 32 FP32 = 128 bytes, 128-byte swizzle: chunk c sits at c ^ (row % 8)
     const uint32_t ra = st + row * 128;
@@ -623,6 +626,11 @@ __device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd
     }
     }
   }
+}
+
+template <int PREC, int NB>
+__device__ __forceinline__ void weight_stage(uint32_t st, int row, int h, int nd, uint32_t ta) {
+  weight_stage_c<PREC, G1Cfg<PREC, NB>>(st, row, h, nd, ta);
 }
 
 // The MMAs of one stage: for each direction d, D_d (+)= A'_d B^T over the
@@ -878,19 +886,330 @@ __global__ void __launch_bounds__(G1_THREADS, 1)
 }
 
 // ===========================================================================
+// GEMM1 on CTA pairs (cta_group::2): 256 x 256 tiles, one direction
+// ===========================================================================
+//
+// A cluster of two CTAs on neighbouring SMs computes one 256 x 256 tile
+// (I2, J) of X_k, I2 <= J in 256-state blocks, with M = 256 pair MMAs: CTA r
+// of the pair loads (by TMA) and weights the FP32 Psi^T rows of the 128-state
+// block 2 I2 + r into its own tensor memory (the A rows of the MMA), and loads
+// the bf16 hi / lo (or TF32) Psi^T rows of the 128-state block 2 J + r (its
+// half of the B rows).  One thread of the even CTA issues the MMAs; each CTA's
+// tensor memory receives its 128 rows x 256 columns of the accumulator.  Per
+// SM that halves the B rows loaded and read per MMA, against the 128 x 256
+// single-CTA tile, for the same MMA work.
+//
+// Barriers: full[s] (each CTA, its own TMA bytes); ready[s] and acc_empty
+// (even CTA, 16 arrivals: the 8 math warps of both CTAs); empty[s] and
+// acc_full (both CTAs, one arrival each from the multicast MMA commit); drain
+// (even CTA).  The reduction is segmented as in k_gemm1_tc.
+
+template <int PREC>
+struct G1PCfg {
+  static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
+  static constexpr int SUB = PREC == LRDM_TF32 ? 2 : 1;
+  static constexpr int STAGES = 6;
+  static constexpr int ACOLS = BK * SUB;
+  static constexpr int SLOT = ACOLS;
+  static constexpr int A_CHUNK = BM * BK * 4;
+  static constexpr int A_BYTES = A_CHUNK * SUB;
+  static constexpr int B_TILE = 128 * ROWB;                     // this CTA's 128 B rows, one part
+  static constexpr int B_CHUNK = PARTS * B_TILE;
+  static constexpr int B_OFF = A_BYTES;
+  static constexpr int SC_OFF = B_OFF + SUB * B_CHUNK;
+  static constexpr int STRIDE = SC_OFF + 1024;
+  static constexpr int SMEM = STAGES * STRIDE + 1024 + 512;
+  static constexpr int SEG = 1024 / (BK * SUB);
+  static constexpr int LAG = STAGES - 1;
+  static constexpr int TX = A_BYTES + SUB * B_CHUNK + BK * SUB * 4;   // TMA bytes per stage and CTA
+  static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, 256, 256);
+  static_assert(G1_ACOL + STAGES * SLOT <= 512, "TMEM budget");
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+};
+
+constexpr uint16_t PAIR_MASK = 0x3;
+
+// Pair item -> slot q, row range `split`, direction k, tile (I2, J): row
+// ranges outermost, then tiles column by column (column J holds I2 = 0..J),
+// directions fastest (the pairs working on one tile stream the same Psi^T
+// rows through L2).
+__device__ __forceinline__ const TcProblem* g1p_item(const G1Params& P, int item, int& q, int& k,
+                                                     int& I2, int& J, int& split) {
+  q = find_slot(P.begin, P.nslot, item);
+  const TcProblem* pr = P.probs + P.pid[q];
+  int idx = item - P.begin[q];
+  const int K = P.K[q];
+  const int per_split = pr->ntiles_p * K;
+  split = idx / per_split;
+  idx -= split * per_split;
+  int t = idx / K;
+  k = idx - t * K;
+  int j = 0;
+  while (t > j) {
+    t -= j + 1;
+    ++j;
+  }
+  J = j;
+  I2 = t;
+  return pr;
+}
+
+template <int PREC>
+__device__ __forceinline__ void issue_g1p_mmas(uint32_t tmem, uint32_t aslot, uint32_t sb, bool first) {
+  using C = G1PCfg<PREC>;
+  const uint32_t at = tmem + aslot;
+#pragma unroll
+  for (int c = 0; c < C::SUB; ++c) {
+    const uint32_t bc = sb + c * C::B_CHUNK;
+#pragma unroll
+    for (int kk = 0; kk < KSTEPS; ++kk) {
+      const uint32_t acc = (first && c == 0 && kk == 0) ? 0u : 1u;
+      const uint64_t b0 = ptx::desc_k_sw64(bc + kk * 32);
+      if (PREC == LRDM_BF16X3) {
+        const uint64_t b1 = ptx::desc_k_sw64(bc + C::B_TILE + kk * 32);
+        ptx::mma_f16_ta_pair(tmem, at + kk * 8, b0, C::IDESC, acc);        // hi x hi
+        ptx::mma_f16_ta_pair(tmem, at + kk * 8, b1, C::IDESC, 1);          // hi x lo
+        ptx::mma_f16_ta_pair(tmem, at + 16 + kk * 8, b0, C::IDESC, 1);     // lo x hi
+      } else {
+        ptx::mma_tf32_ta_pair(tmem, at + c * C::BK + kk * 8, b0, C::IDESC, acc);
+      }
+    }
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void g1p_producer(const G1Params& P, uint8_t* smem, const Bars& B, int items,
+                                             int rank, int pair, int npairs) {
+  using C = G1PCfg<PREC>;
+  constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SUB = C::SUB;
+  for (int q = 0; q < P.nslot; ++q) {
+    const TcProblem* pr = P.probs + P.pid[q];
+    ptx::tmap_acquire(&pr->g1a);
+    ptx::tmap_acquire(&pr->g1b0);
+    if (PARTS == 2) ptx::tmap_acquire(&pr->g1b1);
+  }
+  int s = 0;
+  uint32_t ph = 0;
+  int pending[STAGES];
+  for (int i = 0; i < STAGES; ++i) pending[i] = -1;
+  bool ok = true;
+  for (int item = pair; item < items && ok; item += npairs) {
+    int q, k, I2, J, sp;
+    const TcProblem* pr = g1p_item(P, item, q, k, I2, J, sp);
+    int rb, re;
+    g1_range<SUB>(P, pr, q, sp, rb, re);
+    const float* w0 = pr->a + (long long)k * pr->a_stride;
+    const int ia = 2 * I2 + rank, ib = 2 * J + rank;   // 128-state blocks (past the end: zero fill)
+    for (int rc = rb; rc < re; ++rc) {
+      if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
+      uint8_t* st = smem + s * C::STRIDE;
+      ptx::mbar_arrive_expect_tx(&B.full[s], C::TX);
+#pragma unroll
+      for (int c = 0; c < SUB; ++c) {
+        const int ch = rc * SUB + c;
+        ptx::tma_load_4d(st + c * C::A_CHUNK, &pr->g1a, &B.full[s], 0, 0, ch, ia);
+        uint8_t* bd = st + C::B_OFF + c * C::B_CHUNK;
+        ptx::tma_load_4d(bd, &pr->g1b0, &B.full[s], 0, 0, ch, ib);
+        if (PARTS == 2) ptx::tma_load_4d(bd + C::B_TILE, &pr->g1b1, &B.full[s], 0, 0, ch, ib);
+      }
+      ptx::bulk_load(st + C::SC_OFF, w0 + (long long)rc * BK * SUB, BK * SUB * 4, &B.full[s]);
+      pending[s] = (int)ph;
+      if (++s == STAGES) { s = 0; ph ^= 1; }
+    }
+  }
+  for (int i = 0; i < STAGES; ++i)
+    if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
+}
+
+// The MMA thread's waits on barriers that both CTAs' math warps arrive on:
+// the CTA-scope try_wait (which suspends the thread between polls; the
+// cluster-scope form spins and takes issue slots from the math warps that
+// share its sub-partition), paired with the default-semantics remote arrive.
+__device__ __forceinline__ bool wait_cl(uint64_t* bar, uint32_t parity, const Bars& B, int* status) {
+  return ptx::mbar_wait(bar, parity, B.abort, status, WAIT_NS, STATUS_TIMEOUT);
+}
+
+// MMA issue (even CTA of the pair only).
+template <int PREC>
+__device__ __forceinline__ void g1p_mma(const G1Params& P, uint8_t* smem, const Bars& B, int items,
+                                        uint32_t tmem, int pair, int npairs) {
+  using C = G1PCfg<PREC>;
+  constexpr int STAGES = C::STAGES, SEG = C::SEG;
+  int s = 0;
+  uint32_t ph = 0, aph = 0;
+  bool ok = true;
+  for (int item = pair; item < items && ok; item += npairs) {
+    int q, k, I2, J, sp;
+    const TcProblem* pr = g1p_item(P, item, q, k, I2, J, sp);
+    int rb, re;
+    g1_range<C::SUB>(P, pr, q, sp, rb, re);
+    const int nseg = (re - rb + SEG - 1) / SEG;
+    for (int sg = 0; sg < nseg && ok; ++sg) {
+      if (!wait_cl(&B.acc_empty[0], aph ^ 1, B, P.status)) { ok = false; break; }
+      ptx::tc_fence_after();
+      const int r0 = rb + sg * SEG, r1 = min(re, r0 + SEG);
+      for (int rc = r0; rc < r1; ++rc) {
+        if (!wait_cl(&B.ready[s], ph, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        issue_g1p_mmas<PREC>(tmem, (uint32_t)(G1_ACOL + s * C::SLOT),
+                             ptx::smem_u32(smem + s * C::STRIDE) + C::B_OFF, rc == r0);
+        ptx::mma_commit_pair_mc(&B.empty[s], PAIR_MASK);
+        if (++s == STAGES) { s = 0; ph ^= 1; }
+      }
+      if (!ok) break;
+      ptx::mma_commit_pair_mc(&B.acc_full[0], PAIR_MASK);
+      aph ^= 1;
+    }
+  }
+  ptx::mma_commit_pair(B.drain);
+  wait_drain(B.drain, 0);
+}
+
+// Weighting into this CTA's tensor memory, segment accumulation and the tile
+// epilogue (warps 0-7 of both CTAs; warp w serves TMEM lane quarter w % 4 and
+// element half / accumulator column half w / 4).
+template <int PREC>
+__device__ __forceinline__ void g1p_math(const G1Params& P, uint8_t* smem, const Bars& B, int items,
+                                         uint32_t tmem, int warp, int lane, int rank, int pair,
+                                         int npairs) {
+  using C = G1PCfg<PREC>;
+  constexpr int STAGES = C::STAGES, SEG = C::SEG, LAG = C::LAG;
+  const int lq = warp & 3;
+  const int h = warp >> 2;
+  const int row = lq * 32 + lane;
+  const uint32_t tq = tmem + ((uint32_t)(lq * 32) << 16);
+  int s = 0;
+  uint32_t ph = 0, aph = 0;
+  bool ok = true;
+  float sum[128];
+  bool stall = P.stall != 0 && blockIdx.x == 0;
+  for (int item = pair; item < items && ok; item += npairs) {
+    int q, k, I2, J, sp;
+    const TcProblem* pr = g1p_item(P, item, q, k, I2, J, sp);
+    int rb, re;
+    g1_range<C::SUB>(P, pr, q, sp, rb, re);
+    const int ns = pr->ns, ns_pad = pr->ns_pad;
+    const int nseg = (re - rb + SEG - 1) / SEG;
+#pragma unroll
+    for (int c = 0; c < 128; ++c) sum[c] = 0.f;
+    int flushed = 0;
+    for (int rc = rb; rc < re; ++rc) {
+      if (!waitw(&B.full[s], ph, B, P.status)) { ok = false; break; }
+      weight_stage_c<PREC, C>(ptx::smem_u32(smem + s * C::STRIDE), row, h, 1,
+                              tq + (uint32_t)(G1_ACOL + s * C::SLOT));
+      ptx::tmem_wait_st();
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0 && !stall) ptx::mbar_arrive_cluster(&B.ready[s], 0);
+      stall = false;
+      if (++s == STAGES) { s = 0; ph ^= 1; }
+      const int ready_seg = (rc - rb + 1 - LAG) / SEG;
+      const bool last = rc + 1 == re;
+      while (flushed < nseg && (flushed < ready_seg || last)) {
+        if (!waitw(&B.acc_full[0], aph, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t ta = tq + (uint32_t)(h * 128);
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+          float v[16];
+          ptx::tmem_ld16(ta + c8 * 16, v);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) sum[c8 * 16 + e] += v[e];
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive_cluster(&B.acc_empty[0], 0);
+        aph ^= 1;
+        ++flushed;
+      }
+      if (!ok) break;
+    }
+    if (!ok) break;
+    const int i = (2 * I2 + rank) * BM + row;
+    if (i < ns) {
+      float* Xk = P.X[q] + ((long long)sp * P.K[q] + k) * ns_pad * ns_pad;
+      const int j0 = J * 256 + h * 128;
+#pragma unroll
+      for (int c = 0; c < 128; ++c) {
+        const int j = j0 + c;
+        if (j >= i && j < ns) {
+          Xk[(long long)i * ns_pad + j] = sum[c];
+          Xk[(long long)j * ns_pad + i] = sum[c];
+        }
+      }
+    }
+  }
+}
+
+// Launched in clusters of two CTAs (an even number of CTAs, one per SM).
+template <int PREC>
+__global__ void __launch_bounds__(G1_THREADS, 1)
+    k_gemm1_pair(const __grid_constant__ G1Params P) {
+  using C = G1PCfg<PREC>;
+  constexpr int STAGES = C::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const Bars B = carve<STAGES>(smem + STAGES * C::STRIDE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = P.begin[P.nslot];
+  const int rank = (int)ptx::cluster_ctarank();
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&B.full[s], 1);
+      ptx::mbar_init(&B.empty[s], 1);
+      ptx::mbar_init(&B.ready[s], 16);
+    }
+    ptx::mbar_init(&B.acc_full[0], 1);
+    ptx::mbar_init(&B.acc_empty[0], 16);
+    ptx::mbar_init(B.drain, 1);
+    *B.abort = 0;
+    ptx::fence_barrier_init();
+    ptx::fence_proxy_async_smem();
+  }
+  if (warp == 9) {
+    ptx::tmem_alloc_pair(B.tmem_slot, 512);
+    ptx::tmem_relinquish_pair();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::cluster_sync();          // both CTAs' barriers initialised before any remote arrive
+  ptx::tc_fence_after();
+  const uint32_t tmem = *B.tmem_slot;
+  if (warp >= 8) {
+    ptx::setmaxnreg_dec<G1_REG_CTRL>();
+    if (warp == 8 && lane == 0) g1p_producer<PREC>(P, smem, B, items, rank, pair, npairs);
+    else if (warp == 9 && lane == 0 && rank == 0) g1p_mma<PREC>(P, smem, B, items, tmem, pair, npairs);
+  } else {
+    ptx::setmaxnreg_inc<G1_REG_MATH>();
+    g1p_math<PREC>(P, smem, B, items, tmem, warp, lane, rank, pair, npairs);
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::cluster_sync();          // the even CTA's MMAs into this CTA's memory are complete
+  if (warp == 9) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc_pair(tmem, 512);
+  }
+}
+
+// ===========================================================================
 // host side
 // ===========================================================================
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // the driver entry point is the same for every device; initialised once
+  // (thread-safe static initialisation)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -916,22 +1235,40 @@ bool make_map(CUtensorMap* m, const void* base, int elem_bytes, int rank, const 
   return r == CUDA_SUCCESS;
 }
 
+// Function attributes and device properties are per device: the records
+// below are kept per device ordinal (cached values are plain queries, so two
+// host threads that race on a first call store the same value).
+constexpr int MAX_DEV = 64;
+
+int cur_dev() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
+  static std::atomic<int> cache[MAX_DEV];
+  const int dev = cur_dev();
+  int n = dev >= 0 && dev < MAX_DEV ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (n > 0) return n;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (n <= 0) n = 148;
+  if (dev >= 0 && dev < MAX_DEV) cache[dev].store(n, std::memory_order_relaxed);
   return n;
 }
 
+// One bit per device: the kernel's dynamic shared-memory limit has been raised.
+struct DevMask {
+  std::atomic<unsigned long long> bits{0};
+};
+
 template <typename Kern>
-cudaError_t set_smem(Kern k, int bytes, bool& done) {
-  if (done) return cudaSuccess;
+cudaError_t set_smem(Kern k, int bytes, DevMask& done) {
+  const int dev = cur_dev();
+  const unsigned long long bit = dev >= 0 && dev < MAX_DEV ? 1ull << dev : 0ull;
+  if (bit && (done.bits.load(std::memory_order_acquire) & bit)) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done = true;
+  if (e == cudaSuccess && bit) done.bits.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
 
@@ -980,6 +1317,7 @@ bool build_problem(const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   pr.ntiles = pr.nI * (pr.nI + 1) / 2;    // GEMM1 128 x 128 tiles with I <= J
   pr.ntiles_w = 0;                          // GEMM1 128 x 256 tiles (I below the end of J)
   for (int j = 0; 256 * j < c.ns_pad; ++j) pr.ntiles_w += 2 * (j + 1) < pr.nI ? 2 * (j + 1) : pr.nI;
+  pr.ntiles_p = pr.NJ * (pr.NJ + 1) / 2;    // GEMM1 256 x 256 pair tiles with I <= J
   pr.nch = (int)(S.Ng_pad / BK);
   pr.nR = (int)(S.Ng_pad / BM);
   pr.kmax = S.kmax;
@@ -1007,7 +1345,7 @@ void order_slots(const TcEntry* e, int n, int gemm, int* order) {
 template <int PREC, int NB>
 cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, const TcTune& t,
                         int nch_lim, int stall) {
-  static bool attr = false;
+  static DevMask attr;
   const int smem = G1Cfg<PREC, NB>::SMEM;
   cudaError_t err = set_smem(k_gemm1_tc<PREC, NB>, smem, attr);
   if (err != cudaSuccess) return err;
@@ -1041,6 +1379,99 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, c
     const int grid = items < num_sms() ? items : num_sms();
     k_gemm1_tc<PREC, NB><<<grid, G1_THREADS, smem, st>>>(P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+// Clusters of two that fit on the device at once with the pair kernel's
+// shared memory (one CTA per SM), per device.
+template <int PREC>
+cudaError_t pair_attr() {
+  static DevMask attr;
+  return set_smem(k_gemm1_pair<PREC>, G1PCfg<PREC>::SMEM, attr);
+}
+
+template <int PREC>
+int pair_clusters() {
+  static std::atomic<int> cache[MAX_DEV];
+  const int dev = cur_dev();
+  int n = dev >= 0 && dev < MAX_DEV ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (n > 0) return n;
+  if (pair_attr<PREC>() != cudaSuccess) {   // the occupancy query needs the shared-memory limit
+    cudaGetLastError();
+    return num_sms() / 2 - 2;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * (num_sms() / 2), 1, 1);
+  cfg.blockDim = dim3(G1_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = G1PCfg<PREC>::SMEM;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaOccupancyMaxActiveClusters(&n, k_gemm1_pair<PREC>, &cfg) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = num_sms() / 2 - 2;
+  }
+  if (n > num_sms() / 2) n = num_sms() / 2;
+  if (dev >= 0 && dev < MAX_DEV) cache[dev].store(n, std::memory_order_relaxed);
+  // LRDM_DEBUG=1 in the environment reports the persistent grid of the pair kernel
+  if (getenv("LRDM_DEBUG"))
+    fprintf(stderr, "liblrdm: device %d: pair projection grid of %d CTA pairs (%d SMs)\n", dev, n,
+            num_sms());
+  return n;
+}
+
+template <int PREC>
+cudaError_t gemm1_pair_group(const TcEntry* e, int n, int* status, cudaStream_t st, int nch_lim,
+                             int stall) {
+  const int smem = G1PCfg<PREC>::SMEM;
+  cudaError_t err = pair_attr<PREC>();
+  if (err != cudaSuccess) return err;
+  for (int base = 0; base < n; base += TC_MAX_SLOTS) {
+    const int m = n - base < TC_MAX_SLOTS ? n - base : TC_MAX_SLOTS;
+    int order[TC_MAX_SLOTS];
+    order_slots(e + base, m, 1, order);
+    G1Params P;
+    memset(&P, 0, sizeof(P));
+    P.status = status;
+    P.dpt = 1;
+    P.nch_lim = nch_lim;
+    P.stall = base == 0 ? stall : 0;
+    int items = 0, q = 0;
+    for (int u = 0; u < m; ++u) {
+      const TcEntry& x = e[base + order[u]];
+      if (x.K <= 0) continue;
+      P.probs = x.dev_base;
+      P.pid[q] = x.pid;
+      P.K[q] = x.K;
+      P.X[q] = static_cast<float*>(x.X);
+      P.nsplit[q] = x.split > 1 ? x.split : 1;
+      P.begin[q] = items;
+      items += x.host->ntiles_p * x.K * P.nsplit[q];
+      ++q;
+    }
+    P.nslot = q;
+    P.begin[q] = items;
+    if (items == 0) continue;
+    const int clusters = pair_clusters<PREC>();
+    const int pairs = items < clusters ? items : clusters;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * pairs, 1, 1);
+    cfg.blockDim = dim3(G1_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((err = cudaLaunchKernelEx(&cfg, k_gemm1_pair<PREC>, P)) != cudaSuccess) return err;
   }
   return cudaSuccess;
 }
@@ -1116,7 +1547,7 @@ int g2_partition(const TcProblem& pr, int K, int BN2, int* jb, unsigned char* jl
 template <int PREC, int BN2>
 cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int* status,
                         cudaStream_t st, const TcTune& t, int nR_lim, int* launches) {
-  static bool attr = false;
+  static DevMask attr;
   const int smem = G2Cfg<PREC, BN2>::SMEM;
   cudaError_t err = set_smem(k_gemm2_tc<PREC, BN2>, smem, attr);
   if (err != cudaSuccess) return err;
@@ -1182,6 +1613,10 @@ bool tc_supported() {
   return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
+int tc_pair_units(int prec) {
+  return prec == LRDM_BF16X3 ? pair_clusters<LRDM_BF16X3>() : pair_clusters<LRDM_TF32>();
+}
+
 bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcProblem& pr) {
   if (prec == LRDM_BF16X3) return build_problem<LRDM_BF16X3>(c, S, ch, pr);
   return build_problem<LRDM_TF32>(c, S, ch, pr);
@@ -1189,6 +1624,9 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
                                   const TcTune& t, int nch_lim, int stall) {
+  if (t.g1_nb == G1_PAIR)
+    return prec == LRDM_BF16X3 ? gemm1_pair_group<LRDM_BF16X3>(e, n, status, st, nch_lim, stall)
+                               : gemm1_pair_group<LRDM_TF32>(e, n, status, st, nch_lim, stall);
   const bool wide = t.g1_nb == 256;
   if (prec == LRDM_BF16X3)
     return wide ? gemm1_group<LRDM_BF16X3, 256>(e, n, status, st, t, nch_lim, stall)

@@ -367,10 +367,13 @@ int choose_split(lrdm_ctx* ctx, int s, int K) {
   const SysState& S = ctx->sys[s];
   if (!is_tc(ctx->opt.prec) || K <= 0 || ctx->tc_pid.empty()) return 1;
   const TcProblem& pr = ctx->tc_host[ctx->tc_pid[2 * s]];
+  const bool pair = ctx->tune.g1_nb == G1_PAIR;
   const bool wide = ctx->tune.g1_nb == 256;
-  const int dpt = wide ? 1 : ctx->tune.g1_dpt;
-  const long long items = (long long)(wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
-  const long long sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+  const int dpt = wide || pair ? 1 : ctx->tune.g1_dpt;
+  const long long items =
+      (long long)(pair ? pr.ntiles_p : wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
+  // work units of the persistent grid: SMs, or CTA pairs for the pair tiles
+  const long long sms = pair ? tc_pair_units(ctx->opt.prec) : ctx->sm_count > 0 ? ctx->sm_count : 148;
   int smax = S.kmax / K;
   if (smax > 8) smax = 8;
   if (smax > pr.nch / 64) smax = pr.nch / 64;
@@ -439,7 +442,8 @@ bool tune_cache_read(const char* path, const std::string& key, TcTune& t) {
     const char* c = strstr(line, "\"g2_kgroup\":");
     TcTune u;
     if (z && a && b && c && sscanf(z, "\"g1_nb\": %d", &u.g1_nb) == 1 &&
-        (u.g1_nb == 128 || u.g1_nb == 256) && sscanf(a, "\"g1_dpt\": %d", &u.g1_dpt) == 1 &&
+        (u.g1_nb == 128 || u.g1_nb == 256 || u.g1_nb == G1_PAIR) &&
+        sscanf(a, "\"g1_dpt\": %d", &u.g1_dpt) == 1 &&
         sscanf(b, "\"g2_bn\": %d", &u.g2_bn) == 1 &&
         sscanf(c, "\"g2_kgroup\": %d", &u.g2_kgroup) == 1 && (u.g1_dpt == 1 || u.g1_dpt == 2) &&
         (u.g2_bn == 128 || u.g2_bn == 256) &&
@@ -523,7 +527,7 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
   cudaError_t err = cudaSuccess;
   TcTune best = ctx->tune;
   float tbest = 1e30f;
-  const int g1_cand[3][2] = {{256, 1}, {128, 1}, {128, 2}};      // (MMA width, directions per tile)
+  const int g1_cand[4][2] = {{G1_PAIR, 1}, {256, 1}, {128, 1}, {128, 2}};   // (MMA width, directions per tile)
   for (const auto& c : g1_cand) {
     TcTune t = ctx->tune;
     t.g1_nb = c[0];
@@ -1054,6 +1058,26 @@ lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_nb, int* g1_dpt, int* g2_bn, 
   if (g1_dpt) *g1_dpt = ctx->tune.g1_dpt;
   if (g2_bn) *g2_bn = ctx->tune.g2_bn;
   if (g2_kgroup) *g2_kgroup = ctx->tune.g2_kgroup;
+  return LRDM_OK;
+}
+
+lrdm_status lrdm_set_tuning(lrdm_ctx* ctx, int g1_nb, int g1_dpt, int g2_bn, int g2_kgroup) {
+  if (!ctx) return LRDM_ERR_INVALID_ARG;
+  if (!is_tc(ctx->opt.prec)) return LRDM_ERR_UNSUPPORTED;
+  const bool nb_ok = g1_nb == 128 || g1_nb == 256 || g1_nb == G1_PAIR;
+  const bool dpt_ok = g1_dpt == 1 || (g1_dpt == 2 && g1_nb == 128);
+  const bool bn_ok = g2_bn == 128 || g2_bn == 256;
+  const bool kg_ok = g2_kgroup == 1 || g2_kgroup == 2 || g2_kgroup == 4;
+  if (!nb_ok || !dpt_ok || !bn_ok || !kg_ok) return LRDM_ERR_INVALID_ARG;
+  ctx->tune.g1_nb = g1_nb;
+  ctx->tune.g1_dpt = g1_dpt;
+  ctx->tune.g2_bn = g2_bn;
+  ctx->tune.g2_kgroup = g2_kgroup;
+  if (ctx->graph_exec) {            // captured with the old shape (freed once it has run)
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    ctx->graph_key.clear();
+  }
   return LRDM_OK;
 }
 

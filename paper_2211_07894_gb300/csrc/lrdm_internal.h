@@ -322,5 +322,8 @@ cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io,
                                   int* status, cudaStream_t st, const TcTune& t, int nR_lim = 0,
                                   int* launches = nullptr);
 bool tc_supported();
+// CTA pairs the pair-tile projection kernel keeps resident on the current
+// device (its persistent grid is twice this many CTAs).
+int tc_pair_units(int prec);
 
 }  // namespace lrdm

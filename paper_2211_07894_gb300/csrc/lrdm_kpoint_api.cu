@@ -63,14 +63,16 @@ lrdm_status solve_mu_kp_host(const std::vector<std::vector<double>>& eps, const 
 // stages each) whose work items fill the persistent grid's waves to 90 %,
 // else the best fill.
 int kp_choose_split(lrdm_ctx* ctx, int K) {
-  const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+  const bool pair = ctx->tune.g1_nb == G1_PAIR;
+  // work units of the persistent grid: SMs, or CTA pairs for the pair tiles
+  const int sms = pair ? tc_pair_units(ctx->opt.prec) : ctx->sm_count > 0 ? ctx->sm_count : 152;
   long long per = 0;                                // items of one range over all points
   int nch = 1 << 30;
   for (int q = 0; q < ctx->kp_nk; ++q) {
     const TcProblem& pr = ctx->tc_host[ctx->kp_pid[q]];
     const bool wide = ctx->tune.g1_nb == 256;
-    const int dpt = wide ? 1 : ctx->tune.g1_dpt;
-    per += (long long)(wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
+    const int dpt = wide || pair ? 1 : ctx->tune.g1_dpt;
+    per += (long long)(pair ? pr.ntiles_p : wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
     nch = std::min(nch, pr.nch);
   }
   int best = 1;

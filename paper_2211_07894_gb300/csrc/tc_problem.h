@@ -19,6 +19,7 @@ struct TcProblem {
   const void* psi1;                      // bf16 lo
   double* part;                          // GEMM2 j-tile part sums [G2_MAX_SPLIT][Ng] (small K)
   int ns, ns_pad, nI, NJ, ntiles, ntiles_w, nch, nR, kmax;   // GEMM1: nI blocks, ntiles tiles; GEMM2: NJ, nR
+  int ntiles_p;                          // GEMM1 on CTA pairs: 256 x 256 tiles with I <= J
 };
 
 constexpr int TC_MAX_SLOTS = 16;        // problems per grouped launch
@@ -30,11 +31,14 @@ constexpr int G2_MAX_NJ = 64;
 
 // Launch shape of the tensor-core contractions (chosen by the autotuner or
 // the defaults): GEMM1 MMA width (128: square tiles with 1 or 2 directions;
-// 256: 128 x 256 tiles, one direction), directions per GEMM1 square tile,
+// 256: 128 x 256 tiles, one direction; G1_PAIR: 256 x 256 tiles, one
+// direction, on a CTA pair), directions per GEMM1 square tile,
 // GEMM2 j-tile width (128, 256) and GEMM2 direction group (directions sharing
 // one Psi row block: 1, 2, 4).
+constexpr int G1_PAIR = 512;
+
 struct TcTune {
-  int g1_nb = 256;
+  int g1_nb = G1_PAIR;
   int g1_dpt = 1;
   int g2_bn = 256;
   int g2_kgroup = 4;

@@ -4,10 +4,15 @@ split-BF16x3 contractions -- the launch configuration bench.py times).
 The oracle cannot evaluate the whole path at this size in seconds, so it
 checks (a) sampled entries of the projected perturbation X_k, each computed
 one by one in FP64 from its definition sum_r Psi_ri w dV_k(r) Psi_rj, with
-dV_k from the oracle's own density, xc kernel and Hartree solve, and (b)
-properties of the response that hold at any size: int drho_k = 0 (electron
-count), <dV_a, drho_b> = <dV_b, drho_a> (self-adjoint chi_0), <dV_a, drho_a>
-<= 0 (negative semidefinite chi_0), and f_k + v_k = drho_k consistency with
+dV_k from the oracle's own density, xc kernel and Hartree solve; (b) the
+result f_k itself, element by element on 4096 seeded grid rows, for two of
+the 16 directions: the oracle forms the whole FP64 X_k (its projection summed
+over row blocks of the grid, the sum over r that defines X_k), mu'_k, the
+subspace response L o (X_k - mu'_k I) and drho_k at the sampled rows (the
+response at a row needs only that row of Psi); and (c) properties of the
+response that hold at any size: int drho_k = 0 (electron count),
+<dV_a, drho_b> = <dV_b, drho_a> (self-adjoint chi_0), <dV_a, drho_a> <= 0
+(negative semidefinite chi_0), and f_k + v_k = drho_k consistency with
 g-scaling.
 """
 
@@ -52,7 +57,7 @@ def full():
     fx = oracle.lda_fx(rho)
     dV = np.stack([oracle.perturbation_potential([V[k, 0]], [fx], N, H)[0] for k in range(K)])
     return dict(ctx=ctx, psi=psi_h, V=V, F=F.double().cpu().numpy()[:, 0], dV=dV, mu=mu,
-                w=float(np.prod(H)), dmu=dmu.cpu().numpy())
+                w=float(np.prod(H)), dmu=dmu.cpu().numpy(), eps=eps)
 
 
 def test_chemical_potential(full):
@@ -80,6 +85,41 @@ def test_sampled_projection_entries(full):
         assert X[i, j] == X[j, i]
     print(f"full-size X samples: max |err| / rms = {worst:.3e}")
     assert worst < 1e-4
+
+
+ROWS_CHECKED = 4096
+DIRS_CHECKED = (0, 15)
+
+
+def test_sampled_response_rows(full):
+    """f_k on 4096 seeded rows against the oracle's FP64 response (split-BF16x3
+    gate 1e-5 relative, as at the small sizes)."""
+    w = full["w"]
+    psi = full["psi"]
+    ng = psi.shape[0]
+    eps = full["eps"]
+    L = oracle.loewner(eps, full["mu"], KT)
+    X = {k: np.zeros((NS, NS)) for k in DIRS_CHECKED}
+    for r0 in range(0, ng, 49152):
+        blk = psi[r0:r0 + 49152].astype(np.float64)
+        for k in DIRS_CHECKED:
+            X[k] += oracle.project(blk, w * full["dV"][k][r0:r0 + 49152])
+        del blk
+    rows = np.sort(np.random.default_rng(2211078940 + 51).choice(ng, ROWS_CHECKED, replace=False))
+    prow = psi[rows].astype(np.float64)
+    worst = 0.0
+    for k in DIRS_CHECKED:
+        dmu = oracle.dmu_shift([L], [X[k]])
+        Xp = oracle.subspace_response(L, X[k], dmu)
+        f_ref = oracle.density_response(prow, Xp, 2.0) - full["V"][k, 0, rows]
+        got = full["F"][k, rows]
+        err = float(np.linalg.norm(got - f_ref) / np.linalg.norm(f_ref))
+        peak = float(np.max(np.abs(got - f_ref)) / np.sqrt(np.mean(f_ref ** 2)))
+        print(f"full-size f, direction {k}: rel err on {ROWS_CHECKED} rows {err:.2e} "
+              f"(max |err| / rms {peak:.2e}); dmu {full['dmu'][k]:.6e} vs {dmu:.6e}")
+        worst = max(worst, err)
+        assert abs(full["dmu"][k] - dmu) <= 1e-4 * np.max(np.abs(np.diag(X[k])))
+    assert worst < 1e-5
 
 
 def test_response_properties(full):

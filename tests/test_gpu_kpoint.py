@@ -19,6 +19,7 @@ import pytest
 
 import oracle
 import workloads
+from gates import check, gate
 from helpers import per_direction_rel_err, rel_err
 
 torch = pytest.importorskip("torch")
@@ -27,8 +28,6 @@ pytestmark = pytest.mark.gpu
 
 N = (12, 11, 10)
 NS, NK, NE, KT, K = 150, 3, 110.0, 0.01, 3
-TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 5e-3, "bf16x3": 1e-5}
-TOL_DMU = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 5e-3, "bf16x3": 1e-4}
 DT = {"fp64": torch.float64, "fp32": torch.float32, "tf32": torch.float32, "bf16x3": torch.float32}
 
 
@@ -91,9 +90,9 @@ def test_kpoint_gateaux_matches_oracle(lib, cfg, prec):
     scale = max(float(np.max(np.abs(np.diagonal(X, axis1=1, axis2=2)))) for X in ref["X"])
     print(f"k-point {prec}: f err {err:.2e}, drho err {derr:.2e}, "
           f"dmu err {np.max(np.abs(dmu_d - ref['dmu'])):.2e}")
-    assert err < TOL[prec]
-    assert derr < TOL[prec]
-    assert np.max(np.abs(dmu_d - ref["dmu"])) <= TOL_DMU[prec] * scale
+    check(prec, "kpoint_gateaux_matches_oracle", err)
+    check(prec, "kpoint_gateaux_matches_oracle", derr)
+    check(prec, "kpoint_gateaux_matches_oracle", float(np.max(np.abs(dmu_d - ref["dmu"]))) / scale, "dmu")
 
 
 def test_kpoint_given_density_single_point_and_fewer_directions(lib, cfg):
@@ -201,15 +200,15 @@ def test_kpoint_tensor_cores_edge_cases(lib, cfg, prec, io):
     ks.rho = ctx.density().double().cpu().numpy()
     V = torch.as_tensor(cfg["V"], dtype=io, device="cuda")
     ref = oracle.gateaux_kpoints(ks, V.double().cpu().numpy())
-    tol = TOL[prec]
+    case = "kpoint_tensor_cores_edge_cases"
     F3, _ = ctx.gateaux(V)
     F1, d1 = ctx.gateaux(V[2:3].contiguous())
     F2, _ = ctx.gateaux(V[:2].contiguous())
     torch.cuda.synchronize()
     assert ctx.status() == 0
-    assert per_direction_rel_err(F3.double().cpu().numpy(), ref["F"]) < tol
-    assert rel_err(F1.double().cpu().numpy()[0], ref["F"][2]) < tol
-    assert per_direction_rel_err(F2.double().cpu().numpy(), ref["F"][:2]) < tol
+    check(prec, case, per_direction_rel_err(F3.double().cpu().numpy(), ref["F"]))
+    check(prec, case, rel_err(F1.double().cpu().numpy()[0], ref["F"][2]))
+    check(prec, case, per_direction_rel_err(F2.double().cpu().numpy(), ref["F"][:2]))
     # the same direction gives the same result in a batch of 3 or alone
     assert torch.equal(F1[0], F3[2]) or rel_err(F1.double().cpu().numpy()[0], F3.double().cpu().numpy()[2]) < 1e-6
 
@@ -233,7 +232,7 @@ def test_kpoint_krylov_step(lib, cfg, prec):
     torch.cuda.synchronize()
     assert ctx.status() == 0
     assert out["rank"] == ref["rank"] == 3
-    tol = TOL[prec]
+    tol = gate(prec, "kpoint_krylov_step")
     assert np.allclose(out["s_rel"], ref["s_rel"], rtol=10 * tol, atol=0)
     assert per_direction_rel_err(out["U"].double().cpu().numpy(), ref["U"]) < 10 * tol
     assert per_direction_rel_err(out["T"].double().cpu().numpy(), ref["T"]) < 10 * tol
@@ -291,7 +290,7 @@ def test_kpoint_many_points_split_launches(lib):
         ref = oracle.gateaux_kpoints(ks, V.double().cpu().numpy())
         err = per_direction_rel_err(F.double().cpu().numpy(), ref["F"])
         print(f"{nk} k-points {prec}: f err {err:.2e}")
-        assert err < TOL[prec]
+        check(prec, "kpoint_many_points_split_launches", err)
         ctx.close()
     c = workloads.kpoint_system(72, (6, 6, 6), 8, 33, 8.0, 0.02, 1)
     p = [torch.as_tensor(np.ascontiguousarray(x.real), device="cuda") for x in c["psi"]]
@@ -321,8 +320,8 @@ def test_kpoint_backward_matches_oracle(lib, cfg, prec):
     lhs = float((fbar.double() * F.double()).sum())
     rhs = float((vbar.double() * V.double()).sum())
     print(f"k-point adjoint {prec}: v_bar err {err:.2e}, dot-product rel {abs(lhs - rhs) / abs(lhs):.2e}")
-    assert err < TOL[prec]
-    assert abs(lhs - rhs) <= 10 * TOL[prec] * abs(lhs)
+    check(prec, "kpoint_backward_matches_oracle", err)
+    assert abs(lhs - rhs) <= 10 * gate(prec, "kpoint_backward_matches_oracle") * abs(lhs)
     from paper_2211_07894_gb300 import binding
     e = torch.empty(NS, dtype=torch.float64, device="cuda")
     assert binding.lrdm_backward(ctx.handle, [fbar.data_ptr()], [vbar.data_ptr()], [e.data_ptr(), 0],
@@ -359,7 +358,7 @@ def test_kpoint_split_row_ranges(lib):
         ref = oracle.gateaux_kpoints(ks, V.double().cpu().numpy())
         err = per_direction_rel_err(F.double().cpu().numpy(), ref["F"])
         print(f"k-point 24^3 {prec}: f err {err:.2e}")
-        assert err < TOL[prec]
+        check(prec, "kpoint_split_row_ranges", err)
         ctx.close()
 
 

@@ -12,13 +12,13 @@ import pytest
 
 import oracle
 import workloads
+from gates import check
 from helpers import oracle_system, rel_err
 
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-4, "tf32": 5e-3, "bf16x3": 1e-5}
 CHECK = [0, 5, 11]
 
 
@@ -45,4 +45,4 @@ def test_precision(study, prec):
     Fh = F.double().cpu().numpy()
     errs = [rel_err(Fh[k], ref["F"][n]) for n, k in enumerate(CHECK)]
     print(f"precision study {prec}: f rel err per direction {['%.2e' % e for e in errs]}")
-    assert max(errs) < TOL[prec]
+    check(prec, "precision_72cube", max(errs))

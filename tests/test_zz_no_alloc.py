@@ -77,3 +77,66 @@ def test_static_apply_rejects_oversized_k(lib):
                                      17, n, 1.0, 0.5, 1e-12, 0, 0, 0, 0,
                                      torch.cuda.current_stream().cuda_stream)
     assert code == 1      # LRDM_ERR_INVALID_ARG: K above the static limit of 16
+
+
+def _call_static(R, V, F, K, w, alpha, rho, coef, srel, status, io):
+    from paper_2211_07894_gb300 import binding
+    dtype_code = binding.DTYPE_F64 if io == torch.float64 else binding.DTYPE_F32
+    return binding.lrdm_apply_static(R.data_ptr(), V.data_ptr(), F.data_ptr(), dtype_code, K, R.numel(), w,
+                                     alpha, 1e-12, rho.data_ptr(), coef.data_ptr(), srel.data_ptr(),
+                                     status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+
+
+def test_static_apply_status_bits(lib, cfg1):
+    """The status word the call reports: a singular S (two equal derivatives)
+    sets the singular bit and gives lrdm_apply's minimum-norm coefficients; a
+    non-finite residual sets the non-finite bit; the next clean call reports
+    0, since the word is cleared at the start of every call."""
+    from gpu_helpers import make_context
+    io = torch.float64
+    ctx, _ = make_context([cfg1], "fp64", io)
+    w = float(np.prod(cfg1["h"]))
+    R, V, F = _inputs(cfg1, 3, io)
+    F2 = F.clone()
+    F2[1] = F2[0]
+    rho = torch.zeros_like(R)
+    coef = torch.empty(3, dtype=torch.float64, device="cuda")
+    srel = torch.empty(1, dtype=torch.float64, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    assert _call_static(R, V, F2, 3, w, 0.0, rho, coef, srel, status, io) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 4
+    coef_ref, _ = ctx.apply(0, R, V, F2, 0.0, rho=torch.zeros_like(R))
+    torch.cuda.synchronize()
+    assert torch.allclose(coef, coef_ref, rtol=1e-10, atol=1e-14)
+    Rn = R.clone()
+    Rn[0, 5] = float("nan")
+    assert _call_static(Rn, V, F, 3, w, 0.0, rho, coef, srel, status, io) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 2
+    assert _call_static(R, V, F, 3, w, 0.0, rho, coef, srel, status, io) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+
+def test_static_apply_allocates_nothing(lib, cfg1):
+    """After a first call on the device (which looks the scratch array up),
+    further calls leave torch's allocator and the device's free memory as
+    they were."""
+    io = torch.float32
+    w = float(np.prod(cfg1["h"]))
+    R, V, F = _inputs(cfg1, 4, io)
+    rho = torch.zeros_like(R)
+    coef = torch.empty(4, dtype=torch.float64, device="cuda")
+    srel = torch.empty(1, dtype=torch.float64, device="cuda")
+    status = torch.empty(1, dtype=torch.int32, device="cuda")
+    assert _call_static(R, V, F, 4, w, 0.5, rho, coef, srel, status, io) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert _call_static(R, V, F, 4, w, 0.5, rho, coef, srel, status, io) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert int(status.item()) == 0
