@@ -81,6 +81,15 @@ def parse():
                    help="run only the k-point leg and print its JSON")
     p.add_argument("--jsonl", default=None,
                    help="also append the result line (with a UTC timestamp and the host) to this JSONL file")
+    p.add_argument("--config", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                   help="instead of the benchmark step, time the forward call of another workload "
+                        "(1: 16^3 toy model, 2: 48^3 / 512, 3: the uneven batch with its spin pair, "
+                        "4: 72^3 / 2048 with near-degenerate pairs) in its precisions, with the FP64 "
+                        "oracle timed on the host cores in full and the error of every precision")
+    p.add_argument("--prec-list", default="",
+                   help="with --config: comma-separated precisions instead of the config's own")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip timing the uneven batch (64 derivatives per call) after the main step")
     p.add_argument("--compare-fp64", action="store_true",
                    help="time the plain FP64 GPU form (torch, Psi X' materialised) and the "
                         "library's FP64 path on a 48^3 slice instead of the benchmark step")
@@ -360,19 +369,12 @@ def time_kpoint(torch, rank, prec, autotune=True, reps=5, warmup=2):
     alg = KP_NK * KP_K * 4.0 * ng * KP_NS * KP_NS
     per_call = prof["gemm1_ms"] / max(prof["gemm1_launches"], 1) / 1e3   # one event per call
     peaks, src = load_peaks()
-    sus = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
-    if prec == "bf16x3":
-        issued, peak, bound = 3.0 * alg, sus, "tensor"
-        note, kname = "bf16x3 issues 3 bf16 MMAs per product; achieved = issued bf16 rate", "k_gemm1_tc"
-    elif prec == "tf32":
-        issued, peak, bound = alg, 0.5 * sus, "tensor"
-        note, kname = "tf32 peak = bf16 sustained x 1/2 (nominal ratio)", "k_gemm1_tc"
-    elif prec == "fp32":
-        issued, peak, bound = alg, 152 * 128 * 2 * 2.07e9 / 1e12, "alu"
-        note, kname = "FP32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz", "k_kp_gemm1<float>"
+    peak, bound, issue, note = dtype_peak(prec, peaks)
+    issued = issue * alg
+    if prec in ("bf16x3", "tf32"):
+        kname = "k_gemm1_pair" if tuning and tuning["g1_nb"] == 512 else "k_gemm1_tc"
     else:
-        issued, peak, bound = alg, 1.10, "alu"
-        note, kname = "FP64 peak = measured torch FP64 matmul (1.10 TF/s)", "k_kp_gemm1<double>"
+        kname = "k_kp_gemm1<float>" if prec == "fp32" else "k_kp_gemm1<double>"
     achieved = issued / per_call / 1e12
     traffic = None
     if tuning:
@@ -479,6 +481,174 @@ def reference_arm(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+# Peaks that MEASURED_PEAKS does not carry, measured on the GB300s
+# with the same method (torch.matmul, CUDA events; best of 10 for the burst
+# figure, back to back for 4 s for the sustained one): TF32 8192^3 1022 TF/s
+# burst, 909 sustained; FP64 4096^3 1.10 (burst = sustained); FP32 without
+# tensor cores 69.8 (the roofline below uses the FMA peak instead).
+PEAK_TF32_SUSTAINED = 908.7
+PEAK_FP64 = 1.10
+
+
+def dtype_peak(prec, peaks):
+    """(peak TF/s, bound, issued products per algorithmic product, note)
+    of a contraction in precision prec."""
+    bf = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    if prec == "bf16x3":
+        return bf, "tensor", 3.0, "bf16x3 issues 3 bf16 MMAs per product; achieved = issued bf16 rate"
+    if prec == "tf32":
+        if PEAK_TF32_SUSTAINED:
+            return (PEAK_TF32_SUSTAINED, "tensor", 1.0,
+                    "tf32 peak = measured torch TF32 matmul, sustained (8192^3, 4 s)")
+        return 0.5 * bf, "tensor", 1.0, "tf32 peak = bf16 sustained x 1/2 (nominal ratio)"
+    if prec == "fp32":
+        return 152 * 128 * 2 * 2.07e9 / 1e12, "alu", 1.0, "FP32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    return PEAK_FP64, "alu", 1.0, f"FP64 peak = measured torch FP64 matmul ({PEAK_FP64} TF/s)"
+
+
+def oracle_system_for(cfg):
+    """oracle.System of a workloads config: occupations, mu and the density
+    g sum f psi^2 + floor from the oracle itself."""
+    import numpy as np
+    import oracle
+    g = cfg["g"]
+    mu = oracle.solve_mu(cfg["eps"], cfg["n_electrons"], cfg["kT"], g)
+    occ = [oracle.fermi(e, mu, cfg["kT"]) for e in cfg["eps"]]
+    rho = [oracle.density(p, o, g, cfg["rho_floor"]) for p, o in zip(cfg["psi"], occ)]
+    return oracle.System(n=cfg["n"], h=cfg["h"], psi=[np.asarray(p, dtype=np.float64) for p in cfg["psi"]],
+                         eps=[np.asarray(e, dtype=np.float64) for e in cfg["eps"]], rho=rho,
+                         n_electrons=cfg["n_electrons"], kT=cfg["kT"], g=g)
+
+
+CONFIG_LEGS = {
+    1: ("16^3 FD toy model (8 Gaussian wells, dense eigenpairs), N_s=32, N_e=24, kT=0.01, K=4",
+        ["fp64"]),
+    2: ("48^3 grid, N_s=512, N_e=460, kT=0.005, K=8 (random subspace under a smooth envelope)",
+        ["fp64", "fp32", "tf32", "bf16x3"]),
+    3: ("6 uneven systems (32^3/256/K4 .. 64^3/1024/K16) + spin pair (64^3, 768/704, K8): "
+        "64 derivatives per call, FP32 storage", ["bf16x3", "tf32", "fp32"]),
+    4: ("72^3 grid, N_s=2048, N_e=1800, kT=0.002, K=12, 5% near-degenerate pairs (gap 1e-9 Ha)",
+        ["fp64", "fp32", "tf32", "bf16x3"]),
+}
+
+
+def config_inputs(n):
+    import workloads
+    if n == 1:
+        return [workloads.config1()]
+    if n == 2:
+        return [workloads.config2()]
+    if n == 3:
+        return workloads.config3()
+    return [workloads.config4()]
+
+
+def time_forward(torch, ctx, V, reps_max=20, budget_s=10.0):
+    """Median of CUDA-event timed forward calls (graph replays: the context
+    is created with use_graph and the calls run on a non-default stream)."""
+    stream = torch.cuda.current_stream()
+    F = [torch.empty_like(v) for v in V]
+    ctx.gateaux(V, out=F)              # captures the graph
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    ctx.gateaux(V, out=F)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    first = a0.elapsed_time(a1)
+    reps = int(max(3, min(reps_max, budget_s * 1e3 / max(first, 1e-3))))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for b0, b1 in ev:
+        b0.record(stream)
+        ctx.gateaux(V, out=F)
+        b1.record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(b0.elapsed_time(b1) for b0, b1 in ev)
+    return statistics.median(ms), reps, F
+
+
+def gpu_config_run(torch, cfgs, prec, refs, peaks, autotune=True):
+    """One precision of a config leg: forward GD/s (graph replays), the
+    contractions' rates from one profiled (eager) call, the error of every
+    direction against the oracle's results."""
+    import numpy as np
+    from paper_2211_07894_gb300 import Context
+    io = torch.float64 if prec == "fp64" else torch.float32
+    systems, V = [], []
+    for c in cfgs:
+        d = dict(n=c["n"], h=c["h"], n_electrons=c["n_electrons"], kT=c["kT"], g=c["g"],
+                 rho_floor=c["rho_floor"], k_max=c["V"].shape[0])
+        d["psi"] = [torch.as_tensor(np.ascontiguousarray(p), dtype=io, device="cuda") for p in c["psi"]]
+        d["eps"] = [torch.as_tensor(np.ascontiguousarray(e), dtype=torch.float64, device="cuda")
+                    for e in c["eps"]]
+        systems.append(d)
+        V.append(torch.as_tensor(np.ascontiguousarray(c["V"]), dtype=io, device="cuda"))
+    tc = prec in ("bf16x3", "tf32")
+    ctx = Context(systems, prec=prec, io_dtype=io, k_max=max(c["V"].shape[0] for c in cfgs),
+                  use_graph=True, autotune=autotune and tc)
+    del systems
+    ms, reps, F = time_forward(torch, ctx, V)
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    ctx.gateaux(V, out=F)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    if ctx.status() != 0:
+        raise RuntimeError(f"device status not ok ({prec})")
+    errs = []
+    for f, ref in zip(F, refs or []):
+        fh = f.double().cpu().numpy()
+        for k in range(fh.shape[0]):
+            b = ref["F"][k]
+            errs.append(float(np.sqrt(np.sum((fh[k] - b) ** 2) / np.sum(b * b))))
+    ktot = sum(c["V"].shape[0] for c in cfgs)
+    alg = sum(c["V"].shape[0] * int(np.prod(c["n"])) * sum(p.shape[1] ** 2 for p in c["psi"]) for c in cfgs)
+    peak, bound, issue, note = dtype_peak(prec, peaks)
+    rates = {}
+    for key, t, n in (("projection", prof["gemm1_ms"], prof["gemm1_launches"]),
+                      ("response", prof["gemm2_ms"], prof["gemm2_launches"])):
+        r = issue * alg / (t / 1e3) / 1e12 if t > 0 else None
+        rates[key] = {"ms": t, "launches": n, "achieved_tflops": r, "peak": peak,
+                      "frac": r / peak if r else None}
+    out = {"gd_s": ktot / (ms / 1e3), "ms_median": ms, "replays": reps, "graph": True,
+           "err_f_max": max(errs) if errs else None,
+           "err_f_median": statistics.median(errs) if errs else None,
+           "bound": bound, "peak_source": note, "contractions": rates,
+           "gpu_launches_per_call": prof["kernel_launches"],
+           "launch_shape": ctx.tuning() if tc else None}
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def config_leg(args, torch):
+    import numpy as np
+    import oracle
+    n = args.config
+    desc, precs = CONFIG_LEGS[n]
+    if args.prec_list:
+        precs = [p for p in args.prec_list.split(",") if p]
+    cfgs = config_inputs(n)
+    ktot = sum(c["V"].shape[0] for c in cfgs)
+    t0 = time.perf_counter()
+    refs = [oracle.gateaux(oracle_system_for(c), c["V"]) for c in cfgs]
+    t_or = time.perf_counter() - t0
+    peaks, peak_src = load_peaks()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    gpu = {p: gpu_config_run(torch, cfgs, p, refs, peaks, autotune=not args.no_autotune) for p in precs}
+    clocks = sampler.stop()
+    line = {"leg": "config", "config_id": n, "workload": desc, "derivatives_per_call": ktot,
+            "unit": "GD/s", "data": "synthetic",
+            "oracle": {"gd_s": ktot / t_or, "seconds": t_or, "cores": cpu_cores(), "cpu_model": cpu_model(),
+                       "kind": "oracle", "sample": "full run: oracle.gateaux over every direction"},
+            "gpu": gpu, "clocks": clocks, "peaks_source": peak_src}
+    print(json.dumps(line), flush=True)
+    if args.jsonl:
+        append_jsonl(args.jsonl, line)
+    return 0
 
 def build_problem(torch, rank, prec, edge, ns, autotune=True):
     import numpy as np
@@ -602,6 +772,10 @@ def main():
     # graph is captured and replayed only on a stream other than the legacy
     # default one
     torch.cuda.set_stream(torch.cuda.Stream())
+    if args.config:
+        from paper_2211_07894_gb300 import build as _build
+        _build.build()
+        return config_leg(args, torch) if rank == 0 else 0
     if args.kpoint_only:
         from paper_2211_07894_gb300 import build as _build
         _build.build()
@@ -773,27 +947,14 @@ def main():
     g2 = (prof["gemm2_ms"], prof["gemm2_launches"])
     name, (tms, nl) = max((("projection GEMM (X_k)", g1), ("response GEMM (drho_k)", g2)),
                           key=lambda x: x[1][0])
-    kname = "k_gemm1_tc" if name.startswith("projection") else "k_gemm2_tc"
-    kshape = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kname == "k_gemm1_tc"
+    g1_kernel = "k_gemm1_pair" if tuning and tuning["g1_nb"] == 512 else "k_gemm1_tc"
+    kname = g1_kernel if name.startswith("projection") else "k_gemm2_tc"
+    kshape = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kname != "k_gemm2_tc"
                else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
     avg_s = tms / max(nl, 1) / 1e3
     alg_flops = KDIR * ng * ns * ns           # one launch: K directions, symmetric half
-    if args.prec == "bf16x3":
-        issued = 3.0 * alg_flops
-        peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
-        bound, note = "tensor", "bf16x3 issues 3 bf16 MMAs per product; achieved = issued bf16 rate"
-    elif args.prec == "tf32":
-        issued = alg_flops
-        peak = 0.5 * peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
-        bound, note = "tensor", "tf32 peak = bf16 sustained x 1/2 (nominal ratio)"
-    elif args.prec == "fp32":
-        issued = alg_flops
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        bound, note = "alu", "FP32 FMA peak = 152 SMs x 128 lanes x 2 x 2.07 GHz"
-    else:
-        issued = alg_flops
-        peak = 1.10
-        bound, note = "alu", "FP64 peak = measured torch FP64 matmul (1.10 TF/s)"
+    peak, bound, issue, note = dtype_peak(args.prec, peaks)
+    issued = issue * alg_flops
     achieved = issued / avg_s / 1e12 if avg_s > 0 else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
@@ -809,13 +970,29 @@ def main():
                                  "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed "
                                  "from a one-pass capture of this workload under profiles/ (null "
                                  "when none matches the current sources and shape)"}
-        for key, kn, (ms, n) in (("projection", "k_gemm1_tc", g1), ("response", "k_gemm2_tc", g2)):
-            sh = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kn == "k_gemm1_tc"
+        for key, kn, (ms, n) in (("projection", g1_kernel, g1), ("response", "k_gemm2_tc", g2)):
+            sh = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kn != "k_gemm2_tc"
                    else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
             sec = ms / max(n, 1) / 1e3
             tensor_pipe[key] = {
                 "rate_frac": issued / sec / 1e12 / peak if sec > 0 else None,
                 "ncu_pct_of_elapsed": recorded_tensor_pipe(kn, f"{args.grid}^3/{ns}/K{KDIR}/{args.prec}", sh)}
+
+    # the uneven batch with its spin pair: 64 derivatives per call (one
+    # grouped launch per contraction, graph replay), same precision
+    batched = None
+    if not args.no_batched and args.prec in ("bf16x3", "tf32", "fp32"):
+        ctx.close()
+        F = fbar = bwd_out = None
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        cfgs3 = config_inputs(3)
+        gen_s = time.perf_counter() - t0
+        batched = gpu_config_run(torch, cfgs3, args.prec, None, load_peaks()[0],
+                                 autotune=not args.no_autotune)
+        batched.update({"workload": CONFIG_LEGS[3][0], "derivatives_per_call": 64,
+                        "value": batched["gd_s"] * world, "host_generation_s": gen_s})
+        del cfgs3
 
     kpoint = None
     if not args.no_kpoint:
@@ -859,7 +1036,7 @@ def main():
                 "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],
                 "forward_only": forward_only, "forward_k1": forward_k1, "fp64_plain": fp64_plain,
-                "kpoint": kpoint,
+                "kpoint": kpoint, "batched_uneven": batched,
                 "paper_context": PAPER_CONTEXT,
                 "launch_shape": tuning,
                 "breakdown_ms": {"gemm1_per_step": prof["gemm1_ms"] / steps,

@@ -244,10 +244,21 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
 
   // workspaces
   const int accsz = fp64 ? 8 : 4;
+  // tensor cores: the X / G buffers hold up to 8 grid-row partials of a
+  // k_max-direction call while they stay within 512 MB per channel, so that
+  // small subspaces (few tiles) can split their grid reduction at any K
+  S.xslots = S.kmax;
+  if (is_tc(prec)) {
+    size_t ldmax = 0;
+    for (int c = 0; c < in.nspin; ++c) ldmax = std::max(ldmax, (size_t)S.ch[c].ns_pad);
+    const size_t per = (size_t)S.kmax * ldmax * ldmax * accsz;
+    const size_t cap = std::min<size_t>(8, std::max<size_t>(1, (512ull << 20) / per));
+    S.xslots = (int)(cap * S.kmax);
+  }
   for (int c = 0; c < in.nspin; ++c) {
     Channel& ch = S.ch[c];
     const size_t ldx = is_tc(prec) ? ch.ns_pad : ch.ns;
-    const size_t xcount = (size_t)S.nsplit * S.kmax * ldx * ldx;
+    const size_t xcount = (size_t)S.nsplit * (is_tc(prec) ? S.xslots : S.kmax) * ldx * ldx;
     LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ch.Xpart), xcount * accsz));
     LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&ch.Gpart), xcount * accsz));
     const size_t pcount = (size_t)S.kmax * ldx * ldx;
@@ -359,8 +370,9 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
 // The work items (tiles x directions x ranges) are of equal size, so the
 // launch time follows the number of waves over the SMs: the count that fills
 // the last wave best (by more than half a percent over a smaller count), with
-// at most 8 ranges, nsplit * K <= k_max (the partial X share the context's X
-// buffer) and at least 64 stages of the reduction per range.  1 at the
+// at most 8 ranges, nsplit * K <= the X buffer's direction slots (k_max, or
+// up to 8 k_max for small subspaces) and at least 64 stages of the reduction
+// per range.  1 at the
 // benchmark's K = 16 (4352 items, 0.987 of 29 waves); 5 at K = 1 there
 // (1360 items, 0.994 of 9 waves, against 0.895 for 1-4 ranges).
 int choose_split(lrdm_ctx* ctx, int s, int K) {
@@ -374,7 +386,7 @@ int choose_split(lrdm_ctx* ctx, int s, int K) {
       (long long)(pair ? pr.ntiles_p : wide ? pr.ntiles_w : pr.ntiles) * ((K + dpt - 1) / dpt);
   // work units of the persistent grid: SMs, or CTA pairs for the pair tiles
   const long long sms = pair ? tc_pair_units(ctx->opt.prec) : ctx->sm_count > 0 ? ctx->sm_count : 148;
-  int smax = S.kmax / K;
+  int smax = S.xslots / K;
   if (smax > 8) smax = 8;
   if (smax > pr.nch / 64) smax = pr.nch / 64;
   int best = 1;

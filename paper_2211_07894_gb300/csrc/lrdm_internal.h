@@ -104,8 +104,10 @@ struct SysState {
   double w = 0, g = 2, kT = 0, ne = 0, mu = 0;
   bool occ_given = false;
   Channel ch[2];
+  int xslots = 0;                    // tensor cores: direction slots of the X / G buffers (>= kmax;
+                                     // grid-row partials of a K-direction call use nsplit * K of them)
   int nsplit = 1;                    // grid-row splits of GEMM1 (CUDA cores: fixed at create;
-                                     // tensor cores: chosen per call from K, nsplit * K <= kmax)
+                                     // tensor cores: chosen per call from K, nsplit * K <= xslots)
   // Poisson
   cufftHandle plan_r2c = 0, plan_c2r = 0;
   bool plans = false;
