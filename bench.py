@@ -88,6 +88,10 @@ def parse():
                         "oracle timed on the host cores in full and the error of every precision")
     p.add_argument("--prec-list", default="",
                    help="with --config: comma-separated precisions instead of the config's own")
+    p.add_argument("--shard", default="replicas", choices=["replicas", "directions"],
+                   help="N > 1: an independent system per rank (weak scaling), or one system whose "
+                        "K directions are split over the ranks, f all-gathered before the "
+                        "least-squares step on every rank (strong scaling)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip timing the uneven batch (64 derivatives per call) after the main step")
     p.add_argument("--compare-fp64", action="store_true",
@@ -756,100 +760,10 @@ def compare_fp64(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.compare_fp64:
-        return compare_fp64(args)
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        return reference_arm(args, rank, world)
-
-    import torch
-    torch.cuda.set_device(local)
-    # every library call runs on a dedicated stream: the forward call's CUDA
-    # graph is captured and replayed only on a stream other than the legacy
-    # default one
-    torch.cuda.set_stream(torch.cuda.Stream())
-    if args.config:
-        from paper_2211_07894_gb300 import build as _build
-        _build.build()
-        return config_leg(args, torch) if rank == 0 else 0
-    if args.kpoint_only:
-        from paper_2211_07894_gb300 import build as _build
-        _build.build()
-        kp = time_kpoint(torch, rank, args.prec, autotune=not args.no_autotune)
-        if rank == 0 and not args.no_cpu_baseline:
-            kp["cpu_baseline"] = time_kpoint_oracle()
-        print(json.dumps(kp), flush=True)
-        return 0
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    from paper_2211_07894_gb300 import build as _build
-    _build.build()
-
-    ctx, V, R, ng = build_problem(torch, rank, args.prec, args.grid, args.ns,
-                                  autotune=not args.no_autotune)
-    ns = args.ns
-    tuning = ctx.tuning() if args.prec in ("bf16x3", "tf32") else None
-    F = torch.empty_like(V)
-    rho_out = torch.empty_like(R)
-    coeff = torch.empty(KDIR, dtype=torch.float64, device="cuda")
-    srel = torch.empty(1, dtype=torch.float64, device="cuda")
-    dmu = torch.empty(KDIR, dtype=torch.float64, device="cuda")
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(2211078940 + 70 + rank)
-    fbar = torch.randn(V.shape, dtype=V.dtype, device="cuda", generator=gen)
-    bwd_out = None
+def time_forward_calls(torch, ctx, V, F, dmu, prof, args, world):
+    """The forward call alone (CUDA-graph replays of lrdm_gateaux_batch, K
+    directions and one direction)."""
     stream = torch.cuda.current_stream()
-
-    def step(Vs, Rs, Fb):
-        nonlocal bwd_out
-        ctx.gateaux([Vs], out=[F], dmu=dmu)
-        ctx.apply(0, Rs, Vs, F, 0.0, rho=rho_out, coeff=coeff, s_rel=srel)
-        bwd_out = ctx.backward([Fb], out=bwd_out)
-
-    for _ in range(max(args.warmup, 0)):
-        step(V, R, fbar)
-    torch.cuda.synchronize()
-    if ctx.status() != 0:
-        raise RuntimeError("device status not ok after warm-up")
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ctx.profile(True)
-    ctx.profile_read(reset=True)
-    sampler = ClockSampler(local)
-    sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(V, R, fbar)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    prof = ctx.profile_read(reset=True)
-    ctx.profile(False)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    steps = max(args.steps, 1)
-    ms_step = ms / steps
-    total_gd = KDIR * steps * world
-    value = total_gd / (ms / 1e3)
-    if ctx.status() != 0:
-        raise RuntimeError("device status not ok after the timed region")
-
-    # the forward call alone: CUDA-graph replays of lrdm_gateaux_batch
     ctx.gateaux([V], out=[F], dmu=dmu)          # captures the graph
     torch.cuda.synchronize()
     reps = max(args.fwd_reps, 1)
@@ -888,58 +802,177 @@ def main():
     if ctx.status() != 0:
         raise RuntimeError("device status not ok after the one-direction replays")
 
+    return forward_only, forward_k1
+
+
+def time_e2e(torch, ctx, step, bwd, V, R, fbar, rho_out, coeff, srel, ns, k_local, steps, total_gd, dist):
+    """The timed step through the public API with the inputs copied from
+    pinned host buffers and the results read back inside the timed region."""
+    stream = torch.cuda.current_stream()
+    Vh = V.cpu().pin_memory()
+    Rh = R.cpu().pin_memory()
+    Fbh = fbar.cpu().pin_memory()
+    out_h = torch.empty_like(rho_out, device="cpu").pin_memory()
+    coef_h = torch.empty(KDIR, dtype=torch.float64).pin_memory()
+    srel_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    vbar_h = torch.empty((k_local,) + tuple(V.shape[1:]), dtype=V.dtype).pin_memory()
+    ebar_h = torch.empty(ns, dtype=torch.float64).pin_memory()
+    obar_h = torch.empty(ns, dtype=torch.float64).pin_memory()
+    Vd = torch.empty_like(V)
+    Rd = torch.empty_like(R)
+    Fbd = torch.empty_like(fbar)
+
+    def e2e_step():
+        Vd.copy_(Vh, non_blocking=True)
+        Rd.copy_(Rh, non_blocking=True)
+        Fbd.copy_(Fbh, non_blocking=True)
+        step(Vd, Rd, Fbd)
+        vbar, eb, ob = bwd()
+        out_h.copy_(rho_out, non_blocking=True)
+        coef_h.copy_(coeff, non_blocking=True)
+        srel_h.copy_(srel, non_blocking=True)
+        vbar_h.copy_(vbar[0], non_blocking=True)
+        ebar_h.copy_(eb[0], non_blocking=True)
+        obar_h.copy_(ob[0], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(steps):
+        e2e_step()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ems = a0.elapsed_time(a1)
+    if dist:
+        t = torch.tensor([ems], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    nb = lambda x: x.numel() * x.element_size()
+    h2d = nb(Vh) + nb(Rh) + nb(Fbh)
+    d2h = nb(out_h) + nb(coef_h) + nb(srel_h) + nb(vbar_h) + nb(ebar_h) + nb(obar_h)
+    e2e = {"value": total_gd / (ems / 1e3), "unit": "GD/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+    if ctx.status() != 0:
+        raise RuntimeError("device status not ok after the end-to-end steps")
+    return e2e
+
+
+def main():
+    args = parse()
+    if args.compare_fp64:
+        return compare_fp64(args)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    # every library call runs on a dedicated stream: the forward call's CUDA
+    # graph is captured and replayed only on a stream other than the legacy
+    # default one
+    torch.cuda.set_stream(torch.cuda.Stream())
+    if args.config:
+        from paper_2211_07894_gb300 import build as _build
+        _build.build()
+        return config_leg(args, torch) if rank == 0 else 0
+    if args.kpoint_only:
+        from paper_2211_07894_gb300 import build as _build
+        _build.build()
+        kp = time_kpoint(torch, rank, args.prec, autotune=not args.no_autotune)
+        if rank == 0 and not args.no_cpu_baseline:
+            kp["cpu_baseline"] = time_kpoint_oracle()
+        print(json.dumps(kp), flush=True)
+        return 0
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2211_07894_gb300 import build as _build
+    _build.build()
+
+    directions = args.shard == "directions"
+    seed_rank = 0 if directions else rank          # one shared system when the directions are split
+    ctx, V, R, ng = build_problem(torch, seed_rank, args.prec, args.grid, args.ns,
+                                  autotune=not args.no_autotune)
+    ns = args.ns
+    tuning = ctx.tuning() if args.prec in ("bf16x3", "tf32") else None
+    F = torch.empty_like(V)
+    rho_out = torch.empty_like(R)
+    coeff = torch.empty(KDIR, dtype=torch.float64, device="cuda")
+    srel = torch.empty(1, dtype=torch.float64, device="cuda")
+    dmu = torch.empty(KDIR, dtype=torch.float64, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2211078940 + 70 + seed_rank)
+    fbar = torch.randn(V.shape, dtype=V.dtype, device="cuda", generator=gen)
+    bwd_out = None
+    stream = torch.cuda.current_stream()
+    k_lo, k_hi = 0, KDIR                       # the directions this rank evaluates
+    if directions:
+        from paper_2211_07894_gb300.sharding import shard_bounds, sharded_step
+        k_lo, k_hi = shard_bounds(KDIR, world, rank)
+
+    def step(Vs, Rs, Fb):
+        nonlocal bwd_out
+        if directions:
+            # this rank's slice forward, all-gather of f, the K x K step on every rank
+            sharded_step(ctx, Vs, Rs, 0.0, rho=rho_out, coeff=coeff, s_rel=srel)
+            bwd_out = ctx.backward([Fb[k_lo:k_hi]], out=bwd_out)
+            return
+        ctx.gateaux([Vs], out=[F], dmu=dmu)
+        ctx.apply(0, Rs, Vs, F, 0.0, rho=rho_out, coeff=coeff, s_rel=srel)
+        bwd_out = ctx.backward([Fb], out=bwd_out)
+
+    for _ in range(max(args.warmup, 0)):
+        step(V, R, fbar)
+    torch.cuda.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("device status not ok after warm-up")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(V, R, fbar)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    steps = max(args.steps, 1)
+    ms_step = ms / steps
+    total_gd = KDIR * steps * (1 if directions else world)
+    value = total_gd / (ms / 1e3)
+    if ctx.status() != 0:
+        raise RuntimeError("device status not ok after the timed region")
+    forward_only = forward_k1 = None
+    if not directions:
+        forward_only, forward_k1 = time_forward_calls(torch, ctx, V, F, dmu, prof, args, world)
+
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        Vh = V.cpu().pin_memory()
-        Rh = R.cpu().pin_memory()
-        Fbh = fbar.cpu().pin_memory()
-        out_h = torch.empty_like(rho_out, device="cpu").pin_memory()
-        coef_h = torch.empty(KDIR, dtype=torch.float64).pin_memory()
-        srel_h = torch.empty(1, dtype=torch.float64).pin_memory()
-        vbar_h = torch.empty_like(V, device="cpu").pin_memory()
-        ebar_h = torch.empty(ns, dtype=torch.float64).pin_memory()
-        obar_h = torch.empty(ns, dtype=torch.float64).pin_memory()
-        Vd = torch.empty_like(V)
-        Rd = torch.empty_like(R)
-        Fbd = torch.empty_like(fbar)
-
-        def e2e_step():
-            Vd.copy_(Vh, non_blocking=True)
-            Rd.copy_(Rh, non_blocking=True)
-            Fbd.copy_(Fbh, non_blocking=True)
-            step(Vd, Rd, Fbd)
-            vbar, eb, ob = bwd_out
-            out_h.copy_(rho_out, non_blocking=True)
-            coef_h.copy_(coeff, non_blocking=True)
-            srel_h.copy_(srel, non_blocking=True)
-            vbar_h.copy_(vbar[0], non_blocking=True)
-            ebar_h.copy_(eb[0], non_blocking=True)
-            obar_h.copy_(ob[0], non_blocking=True)
-
-        e2e_step()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(steps):
-            e2e_step()
-        a1.record(stream)
-        torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        if dist:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        nb = lambda x: x.numel() * x.element_size()
-        h2d = nb(Vh) + nb(Rh) + nb(Fbh)
-        d2h = nb(out_h) + nb(coef_h) + nb(srel_h) + nb(vbar_h) + nb(ebar_h) + nb(obar_h)
-        e2e = {"value": total_gd / (ems / 1e3), "unit": "GD/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
-        if ctx.status() != 0:
-            raise RuntimeError("device status not ok after the end-to-end steps")
+        e2e = time_e2e(torch, ctx, step, lambda: bwd_out, V, R, fbar, rho_out, coeff, srel, ns,
+                       k_hi - k_lo, steps, total_gd, dist)
 
     # roofline of the dominant contraction
     peaks, peak_src = load_peaks()
@@ -952,7 +985,7 @@ def main():
     kshape = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kname != "k_gemm2_tc"
                else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
     avg_s = tms / max(nl, 1) / 1e3
-    alg_flops = KDIR * ng * ns * ns           # one launch: K directions, symmetric half
+    alg_flops = (k_hi - k_lo) * ng * ns * ns   # one launch: this rank's directions, symmetric half
     peak, bound, issue, note = dtype_peak(args.prec, peaks)
     issued = issue * alg_flops
     achieved = issued / avg_s / 1e12 if avg_s > 0 else None
@@ -981,7 +1014,7 @@ def main():
     # the uneven batch with its spin pair: 64 derivatives per call (one
     # grouped launch per contraction, graph replay), same precision
     batched = None
-    if not args.no_batched and args.prec in ("bf16x3", "tf32", "fp32"):
+    if not args.no_batched and not directions and args.prec in ("bf16x3", "tf32", "fp32"):
         ctx.close()
         F = fbar = bwd_out = None
         torch.cuda.empty_cache()
@@ -995,7 +1028,7 @@ def main():
         del cfgs3
 
     kpoint = None
-    if not args.no_kpoint:
+    if not args.no_kpoint and not directions:
         ctx.close()
         F = fbar = bwd_out = None
         torch.cuda.empty_cache()
@@ -1004,7 +1037,7 @@ def main():
             kpoint["cpu_baseline"] = time_kpoint_oracle()
 
     fp64_plain = None
-    if not args.no_fp64_plain:
+    if not args.no_fp64_plain and not directions:
         ctx.close()
         F = fbar = bwd_out = None
         torch.cuda.empty_cache()
@@ -1024,14 +1057,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GD/s", "n_gpus": world,
                 "steps": steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": args.prec, "data": "synthetic",
+                "higher_is_better": True, "scaling": "strong" if directions else "weak",
+                "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                 "config": {"workload": f"{args.grid}^3 grid, N_s={ns}, K={KDIR}, FP32 Psi, "
                                        f"{args.prec} contractions",
                            "grid": [args.grid] * 3, "n_s": ns, "K": KDIR,
                            "precision": args.prec,
                            "l2": "inputs larger than L2 (Psi operand copies > 14 GB)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"{'directions' if directions else 'replicas'} x{world}"},
                 "roofline": roofline, "tensor_pipe": tensor_pipe, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],

@@ -372,6 +372,7 @@ class Context:
             self.meta.append(dict(nspin=nspin, Ng=int(np.prod(d["n"])),
                                   ns=[int(p.shape[1]) for p in d["psi"]],
                                   k_max=int(d.get("k_max", 0)) or int(k_max)))
+        self.nsys = len(self.meta)
         st = self._stream(stream)
         code, h = lrdm_create(cs, o, st)
         _check("lrdm_create", code)

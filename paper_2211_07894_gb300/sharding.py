@@ -37,3 +37,35 @@ def gather_directions(local, K: int, group=None):
     parts = [torch.empty_like(pad) for _ in range(world)]
     dist.all_gather(parts, pad, group=group)
     return torch.cat([p[: b - a] for p, (a, b) in zip(parts, sizes)], dim=0)
+
+
+def sharded_step(ctx, V, R, alpha, rho=None, sys=0, group=None, coeff=None, s_rel=None):
+    """One least-squares preconditioning step (Eqs. plowrank, quasinewton)
+    over the K directions V of system `sys`, with the Gateaux derivatives
+    evaluated direction-sharded over the ranks of `group`.
+
+    Every rank holds its own context (its replica of the subspace) and passes
+    the same V ([K][nspin][N_g]) and R ([nspin][N_g]).  Rank r evaluates its
+    contiguous slice of the directions (shard_bounds) through ctx.gateaux (the
+    other systems of the context get no directions); the slices of f are
+    all-gathered, the one exchange; then every rank runs ctx.apply over all K
+    derivatives, so the coefficients, s_rel and the updated density rho are
+    the same on every rank (coeff / s_rel: optional output tensors).  Returns
+    (F, coeff, s_rel), F the gathered (K, nspin, N_g) derivatives.
+    """
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        world, rank = dist.get_world_size(group), dist.get_rank(group)
+    else:
+        world, rank = 1, 0                   # no process group: one rank owns every direction
+    K = int(V.shape[0])
+    a, b = shard_bounds(K, world, rank)
+    Vs = [None] * int(getattr(ctx, "nsys", 1))
+    Vs[sys] = V[a:b].contiguous()
+    F_parts, _ = ctx.gateaux(Vs)
+    F = gather_directions(F_parts[sys], K, group) if world > 1 else F_parts[sys]
+    if coeff is None and s_rel is None:
+        coeff, s_rel = ctx.apply(sys, R, V, F, alpha, rho=rho)
+    else:
+        coeff, s_rel = ctx.apply(sys, R, V, F, alpha, rho=rho, coeff=coeff, s_rel=s_rel)
+    return F, coeff, s_rel
