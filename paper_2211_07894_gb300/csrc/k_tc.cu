@@ -496,6 +496,7 @@ struct G1Params {
   int nch_lim;                      // > 0: reduce over the first nch_lim stages only (tuning)
   int stall;                        // test only: CTA 0 never publishes its first weighted stage
   int* status;
+  unsigned* sync;                   // pair form: round counter (zero at launch), or null
 };
 
 // Stages of the grid reduction: chunks of BK rows (nch_lim caps them for
@@ -977,6 +978,28 @@ __device__ __forceinline__ void issue_g1p_mmas(uint32_t tmem, uint32_t aslot, ui
   }
 }
 
+// Round alignment.  Pair p takes the items p, p + npairs, ...; the 16
+// directions of a tile are consecutive items, so a round's pairs share each
+// tile's Psi^T rows through L2 -- as long as they stream the same grid rows
+// at about the same time.  Over a long grid reduction (884,736 rows at 96^3)
+// the static assignment lets the pairs' start times drift apart by a sixth of
+// an item, far more rows than L2 holds, and the shared rows are read again
+// from HBM.  So both producers of every pair count the rounds whose loads
+// they have issued in one grid-wide counter and start a round only when every
+// CTA has issued the previous one.  The wait is bounded (ALIGN_NS); a CTA
+// whose wait expires stops aligning (results never depend on it).
+constexpr uint64_t ALIGN_NS = 20000000ull;
+
+// Arrivals the counter holds once rounds 0..r are issued by every CTA (two per pair).
+__device__ __forceinline__ unsigned g1p_round_target(int r, int items, int npairs) {
+  unsigned t = 0;
+  for (int q = 0; q <= r; ++q) {
+    const int a = items - q * npairs;
+    t += 2u * (unsigned)(a >= npairs ? npairs : (a > 0 ? a : 0));
+  }
+  return t;
+}
+
 template <int PREC>
 __device__ __forceinline__ void g1p_producer(const G1Params& P, uint8_t* smem, const Bars& B, int items,
                                              int rank, int pair, int npairs) {
@@ -993,7 +1016,12 @@ __device__ __forceinline__ void g1p_producer(const G1Params& P, uint8_t* smem, c
   int pending[STAGES];
   for (int i = 0; i < STAGES; ++i) pending[i] = -1;
   bool ok = true;
-  for (int item = pair; item < items && ok; item += npairs) {
+  bool align = P.sync != nullptr;
+  int round = 0;
+  for (int item = pair; item < items && ok; item += npairs, ++round) {
+    if (align && round > 0 && !ptx::counter_wait_geq(P.sync, g1p_round_target(round - 1, items, npairs),
+                                                     ALIGN_NS))
+      align = false;
     int q, k, I2, J, sp;
     const TcProblem* pr = g1p_item(P, item, q, k, I2, J, sp);
     int rb, re;
@@ -1016,6 +1044,7 @@ __device__ __forceinline__ void g1p_producer(const G1Params& P, uint8_t* smem, c
       pending[s] = (int)ph;
       if (++s == STAGES) { s = 0; ph ^= 1; }
     }
+    if (P.sync && ok) ptx::counter_add_release(P.sync, 1);     // this round's loads are issued
   }
   for (int i = 0; i < STAGES; ++i)
     if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
@@ -1427,7 +1456,7 @@ int pair_clusters() {
 
 template <int PREC>
 cudaError_t gemm1_pair_group(const TcEntry* e, int n, int* status, cudaStream_t st, int nch_lim,
-                             int stall) {
+                             int stall, unsigned* sync) {
   const int smem = G1PCfg<PREC>::SMEM;
   cudaError_t err = pair_attr<PREC>();
   if (err != cudaSuccess) return err;
@@ -1441,6 +1470,7 @@ cudaError_t gemm1_pair_group(const TcEntry* e, int n, int* status, cudaStream_t 
     P.dpt = 1;
     P.nch_lim = nch_lim;
     P.stall = base == 0 ? stall : 0;
+    P.sync = sync;
     int items = 0, q = 0;
     for (int u = 0; u < m; ++u) {
       const TcEntry& x = e[base + order[u]];
@@ -1459,6 +1489,7 @@ cudaError_t gemm1_pair_group(const TcEntry* e, int n, int* status, cudaStream_t 
     if (items == 0) continue;
     const int clusters = pair_clusters<PREC>();
     const int pairs = items < clusters ? items : clusters;
+    if (sync && (err = cudaMemsetAsync(sync, 0, sizeof(unsigned), st)) != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1623,10 +1654,10 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 }
 
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
-                                  const TcTune& t, int nch_lim, int stall) {
+                                  const TcTune& t, int nch_lim, int stall, unsigned* sync) {
   if (t.g1_nb == G1_PAIR)
-    return prec == LRDM_BF16X3 ? gemm1_pair_group<LRDM_BF16X3>(e, n, status, st, nch_lim, stall)
-                               : gemm1_pair_group<LRDM_TF32>(e, n, status, st, nch_lim, stall);
+    return prec == LRDM_BF16X3 ? gemm1_pair_group<LRDM_BF16X3>(e, n, status, st, nch_lim, stall, sync)
+                               : gemm1_pair_group<LRDM_TF32>(e, n, status, st, nch_lim, stall, sync);
   const bool wide = t.g1_nb == 256;
   if (prec == LRDM_BF16X3)
     return wide ? gemm1_group<LRDM_BF16X3, 256>(e, n, status, st, t, nch_lim, stall)

@@ -355,7 +355,7 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
   cudaError_t e;
   if (gemm == 1) {
     e = launch_gemm1_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n, ctx->d_status, st, ctx->tune,
-                              0, stall);
+                              0, stall, ctx->d_g1sync);
   } else {
     launches = 0;
     e = launch_gemm2_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n, ctx->opt.io_dtype, out_is_io,
@@ -545,7 +545,8 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
     t.g1_nb = c[0];
     t.g1_dpt = c[1];
     const float ms = time_launch([&] { return launch_gemm1_tc_group(ctx->opt.prec, g1.data(), (int)g1.size(),
-                                                                    ctx->d_status, st, t, G1_NCH_CAP); },
+                                                                    ctx->d_status, st, t, G1_NCH_CAP, 0,
+                                                                    ctx->d_g1sync); },
                                  st, REPS, err);
     if (err != cudaSuccess) return from_cuda(err);
     if (ms < tbest) { tbest = ms; best.g1_nb = c[0]; best.g1_dpt = c[1]; }
@@ -750,6 +751,7 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
   lrdm_status rc = LRDM_OK;
   do {
     if ((rc = dalloc(ctx, &ctx->d_status, 1)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->d_g1sync, 1)) != LRDM_OK) break;
     const int maxval = KMAX_LIMIT * (KMAX_LIMIT + 1) / 2 + KMAX_LIMIT + 1;
     if ((rc = dalloc(ctx, &ctx->ls_partial, (size_t)LS_BLOCKS * maxval)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->ls_coef, KMAX_LIMIT)) != LRDM_OK) break;

@@ -128,6 +128,7 @@ struct lrdm_ctx {
   int device = 0;
   lrdm::SysState* sys = nullptr;
   int* d_status = nullptr;
+  unsigned* d_g1sync = nullptr;      // round counter of the pair-tile projection (zeroed per launch)
   double* ls_partial = nullptr;      // [LS_BLOCKS][max values]
   double* ls_coef = nullptr;         // [KMAX_LIMIT]
   double* ls_scal = nullptr;         // [4]: r2, s_rel scratch
@@ -316,8 +317,12 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 // (GEMM2) per problem: partial work with the same item structure (tuning).
 // stall != 0 (test only): CTA 0 of the first launch never publishes its
 // first weighted stage, so its bounded wait expires (timeout status).
+// sync (may be null): a device counter the pair-tile form uses to start
+// each round of work items on all CTA pairs together (zeroed here before
+// every launch).
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
-                                  const TcTune& t, int nch_lim = 0, int stall = 0);
+                                  const TcTune& t, int nch_lim = 0, int stall = 0,
+                                  unsigned* sync = nullptr);
 // launches (may be null) counts the kernels enqueued: one per 16 problems, plus
 // one part-sum kernel per problem whose items were split (K = 1)
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,

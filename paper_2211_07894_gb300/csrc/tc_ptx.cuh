@@ -307,6 +307,22 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint64_t* b, uint32_t cta) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(b)), "r"(cta));
   asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
 }
+// Grid-wide counters in global memory (the pair projection's round alignment).
+__device__ __forceinline__ void counter_add_release(unsigned* c, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(c), "r"(v) : "memory");
+}
+// Waits (bounded) until *c >= target; false when the limit expired first.
+__device__ __forceinline__ bool counter_wait_geq(const unsigned* c, unsigned target, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v >= target) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+    __nanosleep(256);
+  }
+}
+
 // All threads of every CTA of the cluster (release / acquire).
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
