@@ -149,6 +149,32 @@ __device__ __forceinline__ void issue_stage_mmas(uint32_t d, uint32_t sa, uint32
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
+// Round alignment of the persistent grids.  A CTA (or CTA pair) takes the
+// items b, b + n, b + 2n, ... of a launch; the items of a round that stream
+// the same operand rows (the directions of one projection tile, the
+// direction group of one response row block) share them through L2 only
+// while they reach the same rows at about the same time.  Over long items
+// the static assignment lets the start times drift apart by a sixth of an
+// item (2.6 ms of 15.8 ms in the projection at 96^3), far more rows than L2
+// holds, and the shared rows are read again from HBM.  So the producers count
+// the rounds whose loads they have issued in one grid-wide counter (zeroed
+// before the launch) and start a round only when every producer has issued
+// the previous one.  The host enables it only when all items of a launch
+// have the same length; the wait is bounded (ALIGN_NS), after which a
+// producer stops aligning, so no result ever depends on it.
+constexpr uint64_t ALIGN_NS = 20000000ull;
+
+// Arrivals the counter holds once rounds 0..r are issued, for `items` items
+// over `units` grid units with `per_unit` producers each.
+__device__ __forceinline__ unsigned round_target(int r, int items, int units, int per_unit) {
+  unsigned t = 0;
+  for (int q = 0; q <= r; ++q) {
+    const int a = items - q * units;
+    t += (unsigned)per_unit * (unsigned)(a >= units ? units : (a > 0 ? a : 0));
+  }
+  return t;
+}
+
 // ===========================================================================
 // GEMM2: response contraction with the row-dot epilogue
 // ===========================================================================
@@ -177,6 +203,7 @@ struct G2Params {
   unsigned char jl[TC_MAX_SLOTS][G2_MAX_NJ];
   int out_io, out_is_io;
   int* status;
+  unsigned* sync;                   // round counter (zero at launch), or null: no alignment
 };
 
 __device__ __forceinline__ int find_slot(const int* begin, int nslot, int item) {
@@ -269,7 +296,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint32_t ph = 0;
     int pending[STAGES];
     for (int i = 0; i < STAGES; ++i) pending[i] = -1;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    // round alignment (equal-length items only, as set by the host): the
+    // CTAs of a direction group share their row block's Psi rows, and all
+    // row blocks of a direction its X'' tiles, through L2
+    bool align = P.sync != nullptr;
+    int round = 0;
+    for (int item = blockIdx.x; item < items; item += gridDim.x, ++round) {
+      if (align && round > 0 &&
+          !ptx::counter_wait_geq(P.sync, round_target(round - 1, items, gridDim.x, 1), ALIGN_NS))
+        align = false;
       int q, k, R, jp, j0, j1;
       const TcProblem* pr = g2_item<BN2>(P, item, q, k, R, jp, j0, j1);
       const int ns_pad = pr->ns_pad;
@@ -301,6 +336,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       if (!ok) break;
+      if (P.sync) ptx::counter_add_release(P.sync, 1);         // this round's loads are issued
     }
     for (int i = 0; i < STAGES; ++i)
       if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
@@ -978,28 +1014,6 @@ __device__ __forceinline__ void issue_g1p_mmas(uint32_t tmem, uint32_t aslot, ui
   }
 }
 
-// Round alignment.  Pair p takes the items p, p + npairs, ...; the 16
-// directions of a tile are consecutive items, so a round's pairs share each
-// tile's Psi^T rows through L2 -- as long as they stream the same grid rows
-// at about the same time.  Over a long grid reduction (884,736 rows at 96^3)
-// the static assignment lets the pairs' start times drift apart by a sixth of
-// an item, far more rows than L2 holds, and the shared rows are read again
-// from HBM.  So both producers of every pair count the rounds whose loads
-// they have issued in one grid-wide counter and start a round only when every
-// CTA has issued the previous one.  The wait is bounded (ALIGN_NS); a CTA
-// whose wait expires stops aligning (results never depend on it).
-constexpr uint64_t ALIGN_NS = 20000000ull;
-
-// Arrivals the counter holds once rounds 0..r are issued by every CTA (two per pair).
-__device__ __forceinline__ unsigned g1p_round_target(int r, int items, int npairs) {
-  unsigned t = 0;
-  for (int q = 0; q <= r; ++q) {
-    const int a = items - q * npairs;
-    t += 2u * (unsigned)(a >= npairs ? npairs : (a > 0 ? a : 0));
-  }
-  return t;
-}
-
 template <int PREC>
 __device__ __forceinline__ void g1p_producer(const G1Params& P, uint8_t* smem, const Bars& B, int items,
                                              int rank, int pair, int npairs) {
@@ -1019,8 +1033,7 @@ __device__ __forceinline__ void g1p_producer(const G1Params& P, uint8_t* smem, c
   bool align = P.sync != nullptr;
   int round = 0;
   for (int item = pair; item < items && ok; item += npairs, ++round) {
-    if (align && round > 0 && !ptx::counter_wait_geq(P.sync, g1p_round_target(round - 1, items, npairs),
-                                                     ALIGN_NS))
+    if (align && round > 0 && !ptx::counter_wait_geq(P.sync, round_target(round - 1, items, npairs, 2), ALIGN_NS))
       align = false;
     int q, k, I2, J, sp;
     const TcProblem* pr = g1p_item(P, item, q, k, I2, J, sp);
@@ -1470,8 +1483,9 @@ cudaError_t gemm1_pair_group(const TcEntry* e, int n, int* status, cudaStream_t 
     P.dpt = 1;
     P.nch_lim = nch_lim;
     P.stall = base == 0 ? stall : 0;
-    P.sync = sync;
     int items = 0, q = 0;
+    long long len0 = -1;
+    bool equal = true;                // all items of the launch equally long (round alignment)
     for (int u = 0; u < m; ++u) {
       const TcEntry& x = e[base + order[u]];
       if (x.K <= 0) continue;
@@ -1482,14 +1496,19 @@ cudaError_t gemm1_pair_group(const TcEntry* e, int n, int* status, cudaStream_t 
       P.nsplit[q] = x.split > 1 ? x.split : 1;
       P.begin[q] = items;
       items += x.host->ntiles_p * x.K * P.nsplit[q];
+      const long long nch = nch_lim > 0 && nch_lim < x.host->nch ? nch_lim : x.host->nch;
+      const long long len = nch * 1024 / P.nsplit[q];
+      if (len0 >= 0 && len != len0) equal = false;
+      len0 = len;
       ++q;
     }
     P.nslot = q;
     P.begin[q] = items;
     if (items == 0) continue;
+    P.sync = equal ? sync : nullptr;
     const int clusters = pair_clusters<PREC>();
     const int pairs = items < clusters ? items : clusters;
-    if (sync && (err = cudaMemsetAsync(sync, 0, sizeof(unsigned), st)) != cudaSuccess) return err;
+    if (P.sync && (err = cudaMemsetAsync(P.sync, 0, sizeof(unsigned), st)) != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1577,7 +1596,7 @@ int g2_partition(const TcProblem& pr, int K, int BN2, int* jb, unsigned char* jl
 
 template <int PREC, int BN2>
 cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int* status,
-                        cudaStream_t st, const TcTune& t, int nR_lim, int* launches) {
+                        cudaStream_t st, const TcTune& t, int nR_lim, int* launches, unsigned* sync) {
   static DevMask attr;
   const int smem = G2Cfg<PREC, BN2>::SMEM;
   cudaError_t err = set_smem(k_gemm2_tc<PREC, BN2>, smem, attr);
@@ -1616,6 +1635,9 @@ cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int*
     P.nslot = q;
     P.begin[q] = items;
     if (items == 0) continue;
+    // round alignment only where every item has the same length: one problem, unsplit items
+    P.sync = sync && q == 1 && P.nsplit[0] == 1 ? sync : nullptr;
+    if (P.sync && (err = cudaMemsetAsync(P.sync, 0, sizeof(unsigned), st)) != cudaSuccess) return err;
     const int grid = items < num_sms() ? items : num_sms();
     k_gemm2_tc<PREC, BN2><<<grid, NTHREADS, smem, st>>>(P);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -1668,13 +1690,13 @@ cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status
 
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
                                   int* status, cudaStream_t st, const TcTune& t, int nR_lim,
-                                  int* launches) {
+                                  int* launches, unsigned* sync) {
   const bool narrow = t.g2_bn == 128;
   if (prec == LRDM_BF16X3)
-    return narrow ? gemm2_group<LRDM_BF16X3, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches)
-                  : gemm2_group<LRDM_BF16X3, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches);
-  return narrow ? gemm2_group<LRDM_TF32, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches)
-                : gemm2_group<LRDM_TF32, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches);
+    return narrow ? gemm2_group<LRDM_BF16X3, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches, sync)
+                  : gemm2_group<LRDM_BF16X3, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches, sync);
+  return narrow ? gemm2_group<LRDM_TF32, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches, sync)
+                : gemm2_group<LRDM_TF32, 256>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches, sync);
 }
 
 }  // namespace lrdm

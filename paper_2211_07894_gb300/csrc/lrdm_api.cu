@@ -355,11 +355,11 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
   cudaError_t e;
   if (gemm == 1) {
     e = launch_gemm1_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n, ctx->d_status, st, ctx->tune,
-                              0, stall, ctx->d_g1sync);
+                              0, stall, ctx->d_round);
   } else {
     launches = 0;
     e = launch_gemm2_tc_group(ctx->opt.prec, ctx->tc_entries.data(), n, ctx->opt.io_dtype, out_is_io,
-                              ctx->d_status, st, ctx->tune, 0, &launches);
+                              ctx->d_status, st, ctx->tune, 0, &launches, ctx->d_round);
   }
   count(ctx, launches);
   prof_end(ctx, pi, st);
@@ -546,7 +546,7 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
     t.g1_dpt = c[1];
     const float ms = time_launch([&] { return launch_gemm1_tc_group(ctx->opt.prec, g1.data(), (int)g1.size(),
                                                                     ctx->d_status, st, t, G1_NCH_CAP, 0,
-                                                                    ctx->d_g1sync); },
+                                                                    ctx->d_round); },
                                  st, REPS, err);
     if (err != cudaSuccess) return from_cuda(err);
     if (ms < tbest) { tbest = ms; best.g1_nb = c[0]; best.g1_dpt = c[1]; }
@@ -559,7 +559,7 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
       t.g2_kgroup = kg;
       const float ms = time_launch([&] { return launch_gemm2_tc_group(ctx->opt.prec, g2.data(), (int)g2.size(),
                                                                       LRDM_DTYPE_F32, 0, ctx->d_status, st, t,
-                                                                      G2_NR_CAP); },
+                                                                      G2_NR_CAP, nullptr, ctx->d_round); },
                                    st, REPS, err);
       if (err != cudaSuccess) return from_cuda(err);
       if (ms < tbest) { tbest = ms; best.g2_bn = bn; best.g2_kgroup = kg; }
@@ -751,7 +751,7 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
   lrdm_status rc = LRDM_OK;
   do {
     if ((rc = dalloc(ctx, &ctx->d_status, 1)) != LRDM_OK) break;
-    if ((rc = dalloc(ctx, &ctx->d_g1sync, 1)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->d_round, 1)) != LRDM_OK) break;
     const int maxval = KMAX_LIMIT * (KMAX_LIMIT + 1) / 2 + KMAX_LIMIT + 1;
     if ((rc = dalloc(ctx, &ctx->ls_partial, (size_t)LS_BLOCKS * maxval)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->ls_coef, KMAX_LIMIT)) != LRDM_OK) break;

@@ -128,7 +128,7 @@ struct lrdm_ctx {
   int device = 0;
   lrdm::SysState* sys = nullptr;
   int* d_status = nullptr;
-  unsigned* d_g1sync = nullptr;      // round counter of the pair-tile projection (zeroed per launch)
+  unsigned* d_round = nullptr;       // round counter of the tensor-core contractions (zeroed per launch)
   double* ls_partial = nullptr;      // [LS_BLOCKS][max values]
   double* ls_coef = nullptr;         // [KMAX_LIMIT]
   double* ls_scal = nullptr;         // [4]: r2, s_rel scratch
@@ -317,9 +317,9 @@ bool build_tc_problem(int prec, const Channel& c, const SysState& S, int ch, TcP
 // (GEMM2) per problem: partial work with the same item structure (tuning).
 // stall != 0 (test only): CTA 0 of the first launch never publishes its
 // first weighted stage, so its bounded wait expires (timeout status).
-// sync (may be null): a device counter the pair-tile form uses to start
-// each round of work items on all CTA pairs together (zeroed here before
-// every launch).
+// sync (may be null): a device counter the launches use to start each round
+// of work items on all CTAs together (zeroed before every launch that uses
+// it; only launches whose items are all equally long use it).
 cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status, cudaStream_t st,
                                   const TcTune& t, int nch_lim = 0, int stall = 0,
                                   unsigned* sync = nullptr);
@@ -327,7 +327,7 @@ cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status
 // one part-sum kernel per problem whose items were split (K = 1)
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
                                   int* status, cudaStream_t st, const TcTune& t, int nR_lim = 0,
-                                  int* launches = nullptr);
+                                  int* launches = nullptr, unsigned* sync = nullptr);
 bool tc_supported();
 // CTA pairs the pair-tile projection kernel keeps resident on the current
 // device (its persistent grid is twice this many CTAs).

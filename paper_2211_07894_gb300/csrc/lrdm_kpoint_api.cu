@@ -431,7 +431,7 @@ lrdm_status lrdm_kp_create(lrdm_ctx** out, const lrdm_kpoint_system* sys, const 
   lrdm_status rc = LRDM_OK;
   do {
     if ((rc = dalloc(ctx, &ctx->d_status, 1)) != LRDM_OK) break;
-    if ((rc = dalloc(ctx, &ctx->d_g1sync, 1)) != LRDM_OK) break;
+    if ((rc = dalloc(ctx, &ctx->d_round, 1)) != LRDM_OK) break;
     const int maxval = KMAX_LIMIT * (KMAX_LIMIT + 1) / 2 + KMAX_LIMIT + 1;
     if ((rc = dalloc(ctx, &ctx->ls_partial, (size_t)LS_BLOCKS * maxval)) != LRDM_OK) break;
     if ((rc = dalloc(ctx, &ctx->ls_coef, KMAX_LIMIT)) != LRDM_OK) break;
