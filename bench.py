@@ -999,17 +999,23 @@ def main():
     # measured peak (live) and ncu's pipe-active share (recorded full-size capture)
     tensor_pipe = None
     if args.prec in ("bf16x3", "tf32"):
-        tensor_pipe = {"source": "rate_frac: issued MMA rate / peak (as roofline); ncu_pct_of_elapsed: "
+        tensor_pipe = {"source": "rate_frac: issued MMA rate / peak (as roofline), live; ncu_pct_of_elapsed: "
                                  "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed "
-                                 "from a one-pass capture of this workload under profiles/ (null "
-                                 "when none matches the current sources and shape)"}
+                                 "from a one-pass capture under profiles/ of this workload, else of the "
+                                 "48^3 / N_s = 1024 small case (ncu_workload says which; null when no "
+                                 "record matches the current sources and shape)"}
         for key, kn, (ms, n) in (("projection", g1_kernel, g1), ("response", "k_gemm2_tc", g2)):
             sh = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kn != "k_gemm2_tc"
                    else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
             sec = ms / max(n, 1) / 1e3
-            tensor_pipe[key] = {
-                "rate_frac": issued / sec / 1e12 / peak if sec > 0 else None,
-                "ncu_pct_of_elapsed": recorded_tensor_pipe(kn, f"{args.grid}^3/{ns}/K{KDIR}/{args.prec}", sh)}
+            pct, wl = None, None
+            for w in (f"{args.grid}^3/{ns}/K{KDIR}/{args.prec}", f"48^3/1024/K{KDIR}/{args.prec}"):
+                pct = recorded_tensor_pipe(kn, w, sh)
+                if pct is not None:
+                    wl = w
+                    break
+            tensor_pipe[key] = {"rate_frac": issued / sec / 1e12 / peak if sec > 0 else None,
+                                "ncu_pct_of_elapsed": pct, "ncu_workload": wl}
 
     # the uneven batch with its spin pair: 64 derivatives per call (one
     # grouped launch per contraction, graph replay), same precision
