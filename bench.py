@@ -981,8 +981,9 @@ def main():
     name, (tms, nl) = max((("projection GEMM (X_k)", g1), ("response GEMM (drho_k)", g2)),
                           key=lambda x: x[1][0])
     g1_kernel = "k_gemm1_pair" if tuning and tuning["g1_nb"] == 512 else "k_gemm1_tc"
-    kname = g1_kernel if name.startswith("projection") else "k_gemm2_tc"
-    kshape = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kname != "k_gemm2_tc"
+    g2_kernel = "k_gemm2_pair" if tuning and tuning["g2_bn"] == 512 else "k_gemm2_tc"
+    kname = g1_kernel if name.startswith("projection") else g2_kernel
+    kshape = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kname == g1_kernel
                else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
     avg_s = tms / max(nl, 1) / 1e3
     alg_flops = (k_hi - k_lo) * ng * ns * ns   # one launch: this rank's directions, symmetric half
@@ -1004,8 +1005,8 @@ def main():
                                  "from a one-pass capture under profiles/ of this workload, else of the "
                                  "48^3 / N_s = 1024 small case (ncu_workload says which; null when no "
                                  "record matches the current sources and shape)"}
-        for key, kn, (ms, n) in (("projection", g1_kernel, g1), ("response", "k_gemm2_tc", g2)):
-            sh = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kn != "k_gemm2_tc"
+        for key, kn, (ms, n) in (("projection", g1_kernel, g1), ("response", g2_kernel, g2)):
+            sh = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kn == g1_kernel
                    else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
             sec = ms / max(n, 1) / 1e3
             pct, wl = None, None

@@ -117,11 +117,12 @@ typedef struct lrdm_options {
   int use_graph;         /* replay lrdm_gateaux_batch from a captured CUDA graph  */
   int autotune;          /* tensor-core precisions: 0 -> default launch shape
                             (256 x 256 projection tiles on CTA pairs, response
-                            j-tile 256, direction group 4); 1 -> lrdm_create
+                            256-wide j-tiles over 256-row blocks on CTA pairs,
+                            direction group 4); 1 -> lrdm_create
                             times the candidates (projection: pair tiles,
                             128 x 256 tiles, or 128 x 128 tiles with 1 or 2
-                            directions; response: j-tile 128
-                            or 256 x group 1, 2, 4) on the context's
+                            directions; response: j-tile 128, 256
+                            or 256 on CTA pairs x group 1, 2, 4) on the context's
                             own problems and keeps the fastest; with the
                             environment variable LRDM_TUNE_CACHE naming a file,
                             results are read from / appended to it (one JSON
@@ -257,13 +258,14 @@ lrdm_status lrdm_profile_read(lrdm_ctx* ctx, double* gemm1_ms, long long* gemm1_
  * or the autotuner's choice): projection MMA width (128: square tiles; 256:
  * 128 x 256 tiles, one direction; 512: 256 x 256 tiles, one direction, each
  * computed by a pair of CTAs on neighbouring SMs with M = 256 pair MMAs),
- * directions per projection square tile, response j-tile width, response
+ * directions per projection square tile, response j-tile width (128, 256;
+ * 512: 256-wide j-tiles over 256-row blocks on a CTA pair), response
  * direction group.  Any pointer may be NULL. */
 lrdm_status lrdm_get_tuning(lrdm_ctx* ctx, int* g1_nb, int* g1_dpt, int* g2_bn, int* g2_kgroup);
 
 /* Sets the launch shape used by the following calls on ctx (values as
  * returned by lrdm_get_tuning: g1_nb 128, 256 or 512; g1_dpt 1, or 2 with
- * g1_nb = 128; g2_bn 128 or 256; g2_kgroup 1, 2 or 4).  Results depend on the
+ * g1_nb = 128; g2_bn 128, 256 or 512; g2_kgroup 1, 2 or 4).  Results depend on the
  * shape only through the blocking of the reductions.  A captured forward
  * graph is dropped and captured again by the next call.  Must not be called
  * while another host thread uses ctx.  Errors: INVALID_ARG (null ctx or a

@@ -45,6 +45,7 @@ constexpr int KSTEPS = ROWB / 32;       // 32-byte MMA K steps per row
 constexpr int TILE_A = BM * ROWB;       // 8 KB per operand part
 constexpr int NTHREADS = 192;           // warp 0 TMA, warp 1 MMA, warps 2-5 math / epilogue
 constexpr uint64_t WAIT_NS = 4000000000ull;
+constexpr uint16_t PAIR_MASK = 0x3;           // both CTAs of a pair (cluster ranks 0, 1)
 
 template <int PREC>
 struct Tr;
@@ -246,6 +247,68 @@ __device__ __forceinline__ int g2_tile(const G2Params& P, int q, int jj) {
   return P.nsplit[q] > 1 ? (int)P.jl[q][jj] : jj;
 }
 
+// Row-dot of one j-tile: sum over the tile's BN2 columns of this thread's
+// TMEM lane (row r of Psi X'') times Psi[r, j] (bf16 hi + lo, or FP32).
+template <int PREC, int BN2>
+__device__ __forceinline__ float g2_tile_dot(uint32_t tb, int J, long long r, long long Ng, int ns_pad,
+                                             const void* psi0, const void* psi1) {
+  float part = 0.f;
+#pragma unroll 1
+  for (int c = 0; c < BN2 / 32; ++c) {
+    float v[32];
+    ptx::tmem_ld32(tb + c * 32, v);
+    const int j0 = J * BN2 + c * 32;
+    if (r < Ng && j0 < ns_pad) {
+      const long long o = r * ns_pad + j0;
+      if (PREC == LRDM_BF16X3) {
+        const uint4* ph = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(psi0) + o);
+        const uint4* pl = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(psi1) + o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint4 h = __ldg(ph + u), l = __ldg(pl + u);
+          const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            part += v[u * 8 + 2 * e] * (bf_lo(hw[e]) + bf_lo(lw[e]));
+            part += v[u * 8 + 2 * e + 1] * (bf_hi(hw[e]) + bf_hi(lw[e]));
+          }
+        }
+      } else {
+        const float4* pf = reinterpret_cast<const float4*>(static_cast<const float*>(psi0) + o);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 x = __ldg(pf + u);
+          part += v[u * 4] * x.x + v[u * 4 + 1] * x.y + v[u * 4 + 2] * x.z + v[u * 4 + 3] * x.w;
+        }
+      }
+    }
+  }
+  return part;
+}
+
+// The epilogue's result for row r: out = factor * drho (- v) in the io dtype,
+// the FP32 sum, or (items split into j-tile parts) the FP64 part sum.
+__device__ __forceinline__ void g2_store(const G2Params& P, const TcProblem* pr, int q, int k, int jp,
+                                         long long r, double acc_row) {
+  const long long Ng = pr->Ng;
+  if (r >= Ng) return;
+  if (P.nsplit[q] > 1) {
+    pr->part[((long long)jp * P.K[q] + k) * Ng + r] = P.factor[q] * acc_row;
+    return;
+  }
+  const double d = P.factor[q] * acc_row;
+  const long long o = (long long)k * P.out_stride[q] + r;
+  if (P.out_is_io) {
+    const long long ov = (long long)k * P.v_stride[q] + r;
+    if (P.out_io == LRDM_DTYPE_F64)
+      static_cast<double*>(P.out[q])[o] = d - static_cast<const double*>(P.v[q])[ov];
+    else
+      static_cast<float*>(P.out[q])[o] = (float)(d - (double)static_cast<const float*>(P.v[q])[ov]);
+  } else {
+    static_cast<float*>(P.out[q])[o] = (float)d;
+  }
+}
+
 template <int PREC, int BN2>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_gemm2_tc(const __grid_constant__ G2Params P) {
@@ -391,38 +454,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int J = g2_tile(P, q, jj);
         if (!waitw(&B.acc_full[a], aph, B, P.status)) { ok = false; break; }
         ptx::tc_fence_after();
-        float part = 0.f;
         const uint32_t tb = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * BN2);
-#pragma unroll 1
-        for (int c = 0; c < BN2 / 32; ++c) {
-          float v[32];
-          ptx::tmem_ld32(tb + c * 32, v);
-          const int j0 = J * BN2 + c * 32;
-          if (r < Ng && j0 < ns_pad) {
-            const long long o = r * ns_pad + j0;
-            if (PREC == LRDM_BF16X3) {
-              const uint4* ph = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(psi0) + o);
-              const uint4* pl = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(psi1) + o);
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const uint4 h = __ldg(ph + u), l = __ldg(pl + u);
-                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  part += v[u * 8 + 2 * e] * (bf_lo(hw[e]) + bf_lo(lw[e]));
-                  part += v[u * 8 + 2 * e + 1] * (bf_hi(hw[e]) + bf_hi(lw[e]));
-                }
-              }
-            } else {
-              const float4* pf = reinterpret_cast<const float4*>(static_cast<const float*>(psi0) + o);
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const float4 x = __ldg(pf + u);
-                part += v[u * 4] * x.x + v[u * 4 + 1] * x.y + v[u * 4 + 2] * x.z + v[u * 4 + 3] * x.w;
-              }
-            }
-          }
-        }
+        const float part = g2_tile_dot<PREC, BN2>(tb, J, r, Ng, ns_pad, psi0, psi1);
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&B.acc_empty[a]);
@@ -430,21 +463,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (++a == 2) { a = 0; aph ^= 1; }
       }
       if (!ok) break;
-      if (r < Ng && P.nsplit[q] > 1) {
-        pr->part[((long long)jp * P.K[q] + k) * Ng + r] = P.factor[q] * acc_row;
-      } else if (r < Ng) {
-        const double d = P.factor[q] * acc_row;
-        const long long o = (long long)k * P.out_stride[q] + r;
-        if (P.out_is_io) {
-          const long long ov = (long long)k * P.v_stride[q] + r;
-          if (P.out_io == LRDM_DTYPE_F64)
-            static_cast<double*>(P.out[q])[o] = d - static_cast<const double*>(P.v[q])[ov];
-          else
-            static_cast<float*>(P.out[q])[o] = (float)(d - (double)static_cast<const float*>(P.v[q])[ov]);
-        } else {
-          static_cast<float*>(P.out[q])[o] = (float)d;
-        }
-      }
+      g2_store(P, pr, q, k, jp, r, acc_row);
     }
   }
   ptx::tc_fence_before();
@@ -452,6 +471,242 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, 2 * BN2);
+  }
+}
+
+// ===========================================================================
+// GEMM2 on CTA pairs (cta_group::2): 256 grid rows x 256-wide j-tiles
+// ===========================================================================
+//
+// A cluster of two CTAs on neighbouring SMs computes the response of a
+// 256-row block: CTA r loads (TMA) the Psi rows of the 128-row block
+// 2 R2 + r (the A rows) and the X'' rows of its half of each 256-wide j-tile
+// (states J 256 + 128 r .. + 127, the B rows); one thread of the even CTA
+// issues M = 256, N = 256 pair MMAs with both operands in shared memory, and
+// each CTA's tensor memory receives its 128 rows x 256 columns (two
+// accumulators, so the row-dot epilogue of one j-tile overlaps the MMAs of
+// the next).  Per SM that halves the X'' bytes loaded and read per MMA
+// against the single-CTA kernel.  The odd CTA's MMA thread relays its stage
+// arrivals: it waits for its own full barrier and arrives on the even CTA's
+// (pfull, one arrival); the MMA commits are multicast to both CTAs' empty and
+// acc-full barriers; the epilogue warps of both CTAs arrive on the even CTA's
+// acc-empty barrier (8 arrivals).  Items: as k_gemm2_tc with P.nR = the
+// number of 256-row blocks.
+
+template <int PREC>
+struct G2PCfg {
+  static constexpr int PARTS = Tr<PREC>::PARTS, BK = Tr<PREC>::BK;
+  static constexpr int SUB = PREC == LRDM_TF32 ? 2 : 1;
+  static constexpr int BN2 = 256;                       // j-tile width (both CTAs)
+  static constexpr int TILE_B = 128 * ROWB;             // this CTA's 128 X'' rows, one part
+  static constexpr int CHUNK = PARTS * (TILE_A + TILE_B);
+  static constexpr int SB = SUB * CHUNK;
+  static constexpr int STAGES = 6;
+  static constexpr int SMEM = STAGES * SB + 1024 + 512;
+  static constexpr uint32_t IDESC = ptx::idesc_make(PREC == LRDM_BF16X3 ? 1 : 2, 256, 256);
+  static_assert(SMEM <= 227 * 1024, "shared memory budget");
+};
+
+template <int PREC>
+__device__ __forceinline__ void issue_g2p_mmas(uint32_t d, uint32_t sa, uint32_t first) {
+  using C = G2PCfg<PREC>;
+  constexpr int PARTS = Tr<PREC>::PARTS;
+  const uint32_t a0 = sa, a1 = sa + TILE_A;
+  const uint32_t b0 = sa + PARTS * TILE_A, b1 = b0 + C::TILE_B;
+#pragma unroll
+  for (int kk = 0; kk < KSTEPS; ++kk) {
+    const uint32_t off = kk * 32;
+    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+    if (PREC == LRDM_BF16X3) {
+      ptx::mma_f16_pair(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), C::IDESC, acc);
+      ptx::mma_f16_pair(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b1 + off), C::IDESC, 1);
+      ptx::mma_f16_pair(d, ptx::desc_k_sw64(a1 + off), ptx::desc_k_sw64(b0 + off), C::IDESC, 1);
+    } else {
+      ptx::mma_tf32_pair(d, ptx::desc_k_sw64(a0 + off), ptx::desc_k_sw64(b0 + off), C::IDESC, acc);
+    }
+  }
+}
+
+// Launched in clusters of two CTAs.
+template <int PREC>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm2_pair(const __grid_constant__ G2Params P) {
+  using C = G2PCfg<PREC>;
+  constexpr int STAGES = C::STAGES, PARTS = C::PARTS, BK = C::BK, SB = C::SB, BN2 = C::BN2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const Bars B = carve<STAGES>(smem + STAGES * SB);   // ready[] serves as the relayed full barrier
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = P.begin[P.nslot];
+  const int rank = (int)ptx::cluster_ctarank();
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&B.full[s], 1);
+      ptx::mbar_init(&B.empty[s], 1);
+      ptx::mbar_init(&B.ready[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      ptx::mbar_init(&B.acc_full[a], 1);
+      ptx::mbar_init(&B.acc_empty[a], 8);
+    }
+    ptx::mbar_init(B.drain, 1);
+    *B.abort = 0;
+    ptx::fence_barrier_init();
+    ptx::fence_proxy_async_smem();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc_pair(B.tmem_slot, 2 * BN2);
+    ptx::tmem_relinquish_pair();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::cluster_sync();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *B.tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    for (int q = 0; q < P.nslot; ++q) {
+      const TcProblem* pr = P.probs + P.pid[q];
+      ptx::tmap_acquire(&pr->g2a0);
+      ptx::tmap_acquire(&pr->g2b0);
+      if (PARTS == 2) {
+        ptx::tmap_acquire(&pr->g2a1);
+        ptx::tmap_acquire(&pr->g2b1);
+      }
+    }
+    int s = 0;
+    uint32_t ph = 0;
+    int pending[STAGES];
+    for (int i = 0; i < STAGES; ++i) pending[i] = -1;
+    bool align = P.sync != nullptr;
+    int round = 0;
+    for (int item = pair; item < items; item += npairs, ++round) {
+      if (align && round > 0 &&
+          !ptx::counter_wait_geq(P.sync, round_target(round - 1, items, npairs, 2), ALIGN_NS))
+        align = false;
+      int q, k, R2, jp, j0, j1;
+      const TcProblem* pr = g2_item<BN2>(P, item, q, k, R2, jp, j0, j1);
+      const int ns_pad = pr->ns_pad;
+      const int rb = 2 * R2 + rank;                       // this CTA's 128-row block (past the end: zero fill)
+      bool ok = true;
+      for (int jj = j0; jj < j1 && ok; ++jj) {
+        const int J = g2_tile(P, q, jj);
+        const int nch = min((J + 1) * BN2, ns_pad) / (BK * C::SUB);
+        for (int ic = 0; ic < nch; ++ic) {
+          if (!wait1(&B.empty[s], ph ^ 1, B, P.status)) { ok = false; break; }
+          ptx::mbar_arrive_expect_tx(&B.full[s], SB);
+#pragma unroll
+          for (int c = 0; c < C::SUB; ++c) {
+            uint8_t* st = smem + s * SB + c * C::CHUNK;
+            const int i0 = (ic * C::SUB + c) * BK;
+            ptx::tma_load_2d(st, &pr->g2a0, &B.full[s], i0, rb * BM);
+            if (PARTS == 2) ptx::tma_load_2d(st + TILE_A, &pr->g2a1, &B.full[s], i0, rb * BM);
+            ptx::tma_load_3d(st + PARTS * TILE_A, &pr->g2b0, &B.full[s], i0, J * BN2 + rank * 128, k);
+            if (PARTS == 2)
+              ptx::tma_load_3d(st + PARTS * TILE_A + C::TILE_B, &pr->g2b1, &B.full[s], i0,
+                               J * BN2 + rank * 128, k);
+          }
+          pending[s] = (int)ph;
+          if (++s == STAGES) { s = 0; ph ^= 1; }
+        }
+      }
+      if (!ok) break;
+      if (P.sync) ptx::counter_add_release(P.sync, 1);
+    }
+    for (int i = 0; i < STAGES; ++i)
+      if (pending[i] >= 0) wait_drain(&B.full[i], (uint32_t)pending[i]);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---------------- MMA issuer (even CTA) ----------------
+    int s = 0, a = 0;
+    uint32_t ph = 0, aph = 0;
+    bool ok = true;
+    for (int item = pair; item < items && ok; item += npairs) {
+      int q, k, R2, jp, j0, j1;
+      const TcProblem* pr = g2_item<BN2>(P, item, q, k, R2, jp, j0, j1);
+      const int ns_pad = pr->ns_pad;
+      for (int jj = j0; jj < j1 && ok; ++jj) {
+        const int J = g2_tile(P, q, jj);
+        if (!wait1(&B.acc_empty[a], aph ^ 1, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * BN2);
+        const int nch = min((J + 1) * BN2, ns_pad) / (BK * C::SUB);
+        for (int ic = 0; ic < nch; ++ic) {
+          if (!wait1(&B.full[s], ph, B, P.status) || !wait1(&B.ready[s], ph, B, P.status)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+#pragma unroll
+          for (int c = 0; c < C::SUB; ++c)
+            issue_g2p_mmas<PREC>(d, ptx::smem_u32(smem + s * SB + c * C::CHUNK), ic == 0 && c == 0);
+          ptx::mma_commit_pair_mc(&B.empty[s], PAIR_MASK);
+          if (++s == STAGES) { s = 0; ph ^= 1; }
+        }
+        if (!ok) break;
+        ptx::mma_commit_pair_mc(&B.acc_full[a], PAIR_MASK);
+        if (++a == 2) { a = 0; aph ^= 1; }
+      }
+    }
+    ptx::mma_commit_pair(B.drain);
+    wait_drain(B.drain, 0);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- stage relay (odd CTA): its stages landed -> even CTA ----------------
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int item = pair; item < items && ok; item += npairs) {
+      int q, k, R2, jp, j0, j1;
+      const TcProblem* pr = g2_item<BN2>(P, item, q, k, R2, jp, j0, j1);
+      const int ns_pad = pr->ns_pad;
+      for (int jj = j0; jj < j1 && ok; ++jj) {
+        const int J = g2_tile(P, q, jj);
+        const int nch = min((J + 1) * BN2, ns_pad) / (BK * C::SUB);
+        for (int ic = 0; ic < nch; ++ic) {
+          if (!wait1(&B.full[s], ph, B, P.status)) { ok = false; break; }
+          ptx::mbar_arrive_cluster(&B.ready[s], 0);
+          if (++s == STAGES) { s = 0; ph ^= 1; }
+        }
+      }
+    }
+  } else if (warp >= 2) {
+    // ---------------- row-dot epilogue (both CTAs; TMEM lane quarter = warp % 4) ----------------
+    const int lq = warp & 3;
+    const int row = lq * 32 + lane;
+    int a = 0;
+    uint32_t aph = 0;
+    bool ok = true;
+    for (int item = pair; item < items && ok; item += npairs) {
+      int q, k, R2, jp, j0, j1;
+      const TcProblem* pr = g2_item<BN2>(P, item, q, k, R2, jp, j0, j1);
+      const int ns_pad = pr->ns_pad;
+      const long long Ng = pr->Ng;
+      const long long r = (long long)(2 * R2 + rank) * BM + row;
+      double acc_row = 0.0;
+      for (int jj = j0; jj < j1; ++jj) {
+        const int J = g2_tile(P, q, jj);
+        if (!waitw(&B.acc_full[a], aph, B, P.status)) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t tb = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * BN2);
+        const float part = g2_tile_dot<PREC, BN2>(tb, J, r, Ng, ns_pad, pr->psi0, pr->psi1);
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive_cluster(&B.acc_empty[a], 0);
+        acc_row += (double)part;
+        if (++a == 2) { a = 0; aph ^= 1; }
+      }
+      if (!ok) break;
+      g2_store(P, pr, q, k, jp, r, acc_row);
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::cluster_sync();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc_pair(tmem, 2 * BN2);
   }
 }
 
@@ -964,8 +1219,6 @@ struct G1PCfg {
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 
-constexpr uint16_t PAIR_MASK = 0x3;
-
 // Pair item -> slot q, row range `split`, direction k, tile (I2, J): row
 // ranges outermost, then tiles column by column (column J holds I2 = 0..J),
 // directions fastest (the pairs working on one tile stream the same Psi^T
@@ -1427,19 +1680,16 @@ cudaError_t gemm1_group(const TcEntry* e, int n, int* status, cudaStream_t st, c
 
 // Clusters of two that fit on the device at once with the pair kernel's
 // shared memory (one CTA per SM), per device.
-template <int PREC>
-cudaError_t pair_attr() {
-  static DevMask attr;
-  return set_smem(k_gemm1_pair<PREC>, G1PCfg<PREC>::SMEM, attr);
-}
-
-template <int PREC>
-int pair_clusters() {
-  static std::atomic<int> cache[MAX_DEV];
+// Clusters of two that fit on the device at once with a pair kernel's
+// shared memory and block size (one CTA per SM), per device (cache: one
+// entry per device for that kernel).
+template <typename Kern>
+int cluster_pairs(Kern kern, int smem, int threads, DevMask& attr, std::atomic<int>* cache,
+                  const char* what) {
   const int dev = cur_dev();
   int n = dev >= 0 && dev < MAX_DEV ? cache[dev].load(std::memory_order_relaxed) : 0;
   if (n > 0) return n;
-  if (pair_attr<PREC>() != cudaSuccess) {   // the occupancy query needs the shared-memory limit
+  if (set_smem(kern, smem, attr) != cudaSuccess) {   // the occupancy query needs the shared-memory limit
     cudaGetLastError();
     return num_sms() / 2 - 2;
   }
@@ -1450,21 +1700,51 @@ int pair_clusters() {
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(2 * (num_sms() / 2), 1, 1);
-  cfg.blockDim = dim3(G1_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = G1PCfg<PREC>::SMEM;
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (cudaOccupancyMaxActiveClusters(&n, k_gemm1_pair<PREC>, &cfg) != cudaSuccess || n <= 0) {
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n <= 0) {
     cudaGetLastError();
     n = num_sms() / 2 - 2;
   }
   if (n > num_sms() / 2) n = num_sms() / 2;
   if (dev >= 0 && dev < MAX_DEV) cache[dev].store(n, std::memory_order_relaxed);
-  // LRDM_DEBUG=1 in the environment reports the persistent grid of the pair kernel
+  // LRDM_DEBUG=1 in the environment reports the persistent grid of the pair kernels
   if (getenv("LRDM_DEBUG"))
-    fprintf(stderr, "liblrdm: device %d: pair projection grid of %d CTA pairs (%d SMs)\n", dev, n,
-            num_sms());
+    fprintf(stderr, "liblrdm: device %d: pair %s grid of %d CTA pairs (%d SMs)\n", dev, what, n, num_sms());
   return n;
+}
+
+template <int PREC>
+struct PairKernels {
+  static DevMask g1_attr, g2_attr;
+  static std::atomic<int> g1_cache[MAX_DEV], g2_cache[MAX_DEV];
+};
+template <int PREC>
+DevMask PairKernels<PREC>::g1_attr;
+template <int PREC>
+DevMask PairKernels<PREC>::g2_attr;
+template <int PREC>
+std::atomic<int> PairKernels<PREC>::g1_cache[MAX_DEV];
+template <int PREC>
+std::atomic<int> PairKernels<PREC>::g2_cache[MAX_DEV];
+
+template <int PREC>
+cudaError_t pair_attr() {
+  return set_smem(k_gemm1_pair<PREC>, G1PCfg<PREC>::SMEM, PairKernels<PREC>::g1_attr);
+}
+
+template <int PREC>
+int pair_clusters() {
+  return cluster_pairs(k_gemm1_pair<PREC>, G1PCfg<PREC>::SMEM, G1_THREADS, PairKernels<PREC>::g1_attr,
+                       PairKernels<PREC>::g1_cache, "projection");
+}
+
+template <int PREC>
+int pair_clusters_g2() {
+  return cluster_pairs(k_gemm2_pair<PREC>, G2PCfg<PREC>::SMEM, NTHREADS, PairKernels<PREC>::g2_attr,
+                       PairKernels<PREC>::g2_cache, "response");
 }
 
 template <int PREC>
@@ -1655,6 +1935,78 @@ cudaError_t gemm2_group(const TcEntry* e, int n, int out_io, int out_is_io, int*
   return cudaSuccess;
 }
 
+template <int PREC>
+cudaError_t gemm2_pair_group(const TcEntry* e, int n, int out_io, int out_is_io, int* status,
+                             cudaStream_t st, const TcTune& t, int nR_lim, int* launches, unsigned* sync) {
+  using C = G2PCfg<PREC>;
+  cudaError_t err = set_smem(k_gemm2_pair<PREC>, C::SMEM, PairKernels<PREC>::g2_attr);
+  if (err != cudaSuccess) return err;
+  const int kg = t.g2_kgroup == 1 || t.g2_kgroup == 4 ? t.g2_kgroup : 2;
+  for (int base = 0; base < n; base += TC_MAX_SLOTS) {
+    const int m = n - base < TC_MAX_SLOTS ? n - base : TC_MAX_SLOTS;
+    int order[TC_MAX_SLOTS];
+    order_slots(e + base, m, 2, order);
+    G2Params P;
+    memset(&P, 0, sizeof(P));
+    const TcProblem* hp[TC_MAX_SLOTS] = {};
+    P.out_io = out_io;
+    P.out_is_io = out_is_io;
+    P.status = status;
+    int items = 0, q = 0;
+    for (int u = 0; u < m; ++u) {
+      const TcEntry& x = e[base + order[u]];
+      if (x.K <= 0) continue;
+      P.probs = x.dev_base;
+      P.pid[q] = x.pid;
+      P.K[q] = x.K;
+      P.kgroup[q] = x.K < kg ? x.K : kg;
+      P.factor[q] = x.factor;
+      P.v[q] = x.v;
+      P.v_stride[q] = x.v_stride;
+      P.out[q] = x.out;
+      P.out_stride[q] = x.out_stride;
+      const int nr = nR_lim > 0 && nR_lim < x.host->nR ? nR_lim : x.host->nR;
+      P.nR[q] = (nr + 1) / 2;                   // 256-row blocks of the CTA pairs
+      P.nsplit[q] = g2_partition(*x.host, x.K, C::BN2, P.jb[q], P.jl[q]);
+      hp[q] = x.host;
+      P.begin[q] = items;
+      items += P.nR[q] * x.K * P.nsplit[q];
+      ++q;
+    }
+    P.nslot = q;
+    P.begin[q] = items;
+    if (items == 0) continue;
+    P.sync = sync && q == 1 && P.nsplit[0] == 1 ? sync : nullptr;
+    if (P.sync && (err = cudaMemsetAsync(P.sync, 0, sizeof(unsigned), st)) != cudaSuccess) return err;
+    const int clusters = pair_clusters_g2<PREC>();
+    const int pairs = items < clusters ? items : clusters;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * pairs, 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((err = cudaLaunchKernelEx(&cfg, k_gemm2_pair<PREC>, P)) != cudaSuccess) return err;
+    if (launches) ++*launches;
+    for (int u = 0; u < q; ++u) {
+      if (P.nsplit[u] <= 1) continue;
+      const long long nk = (long long)P.K[u] * hp[u]->Ng;
+      const int blocks = (int)std::min<long long>((nk + 255) / 256, 4LL * num_sms());
+      k_g2_combine<<<blocks, 256, 0, st>>>(hp[u]->part, P.nsplit[u], P.K[u], hp[u]->Ng, P.v[u],
+                                           P.v_stride[u], P.out[u], P.out_stride[u], out_io, out_is_io);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      if (launches) ++*launches;
+    }
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 bool tc_supported() {
@@ -1691,6 +2043,10 @@ cudaError_t launch_gemm1_tc_group(int prec, const TcEntry* e, int n, int* status
 cudaError_t launch_gemm2_tc_group(int prec, const TcEntry* e, int n, int out_io, int out_is_io,
                                   int* status, cudaStream_t st, const TcTune& t, int nR_lim,
                                   int* launches, unsigned* sync) {
+  if (t.g2_bn == G2_PAIR)
+    return prec == LRDM_BF16X3
+               ? gemm2_pair_group<LRDM_BF16X3>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches, sync)
+               : gemm2_pair_group<LRDM_TF32>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches, sync);
   const bool narrow = t.g2_bn == 128;
   if (prec == LRDM_BF16X3)
     return narrow ? gemm2_group<LRDM_BF16X3, 128>(e, n, out_io, out_is_io, status, st, t, nR_lim, launches, sync)

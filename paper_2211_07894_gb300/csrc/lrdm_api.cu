@@ -458,7 +458,7 @@ bool tune_cache_read(const char* path, const std::string& key, TcTune& t) {
         sscanf(a, "\"g1_dpt\": %d", &u.g1_dpt) == 1 &&
         sscanf(b, "\"g2_bn\": %d", &u.g2_bn) == 1 &&
         sscanf(c, "\"g2_kgroup\": %d", &u.g2_kgroup) == 1 && (u.g1_dpt == 1 || u.g1_dpt == 2) &&
-        (u.g2_bn == 128 || u.g2_bn == 256) &&
+        (u.g2_bn == 128 || u.g2_bn == 256 || u.g2_bn == G2_PAIR) &&
         (u.g2_kgroup == 1 || u.g2_kgroup == 2 || u.g2_kgroup == 4)) {
       t = u;
       found = true;                  // the last matching line wins
@@ -552,7 +552,7 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
     if (ms < tbest) { tbest = ms; best.g1_nb = c[0]; best.g1_dpt = c[1]; }
   }
   tbest = 1e30f;
-  for (int bn = 128; bn <= 256; bn *= 2)
+  for (int bn = 128; bn <= G2_PAIR; bn *= 2)          // 128, 256, and 256 on CTA pairs
     for (int kg = 1; kg <= 4; kg *= 2) {
       TcTune t = ctx->tune;
       t.g2_bn = bn;
@@ -1080,7 +1080,7 @@ lrdm_status lrdm_set_tuning(lrdm_ctx* ctx, int g1_nb, int g1_dpt, int g2_bn, int
   if (!is_tc(ctx->opt.prec)) return LRDM_ERR_UNSUPPORTED;
   const bool nb_ok = g1_nb == 128 || g1_nb == 256 || g1_nb == G1_PAIR;
   const bool dpt_ok = g1_dpt == 1 || (g1_dpt == 2 && g1_nb == 128);
-  const bool bn_ok = g2_bn == 128 || g2_bn == 256;
+  const bool bn_ok = g2_bn == 128 || g2_bn == 256 || g2_bn == G2_PAIR;
   const bool kg_ok = g2_kgroup == 1 || g2_kgroup == 2 || g2_kgroup == 4;
   if (!nb_ok || !dpt_ok || !bn_ok || !kg_ok) return LRDM_ERR_INVALID_ARG;
   ctx->tune.g1_nb = g1_nb;

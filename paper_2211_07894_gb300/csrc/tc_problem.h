@@ -33,14 +33,16 @@ constexpr int G2_MAX_NJ = 64;
 // the defaults): GEMM1 MMA width (128: square tiles with 1 or 2 directions;
 // 256: 128 x 256 tiles, one direction; G1_PAIR: 256 x 256 tiles, one
 // direction, on a CTA pair), directions per GEMM1 square tile,
-// GEMM2 j-tile width (128, 256) and GEMM2 direction group (directions sharing
-// one Psi row block: 1, 2, 4).
+// GEMM2 j-tile width (128, 256; G2_PAIR: 256-wide j-tiles over 256-row
+// blocks on a CTA pair) and GEMM2 direction group (directions sharing one Psi
+// row block: 1, 2, 4).
 constexpr int G1_PAIR = 512;
+constexpr int G2_PAIR = 512;           // g2_bn: 256-wide j-tiles on CTA pairs (256-row blocks)
 
 struct TcTune {
   int g1_nb = G1_PAIR;
   int g1_dpt = 1;
-  int g2_bn = 256;
+  int g2_bn = G2_PAIR;
   int g2_kgroup = 4;
 };
 

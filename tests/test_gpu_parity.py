@@ -240,7 +240,7 @@ def test_forced_launch_shapes(lib, prec, tmp_path, monkeypatch):
     from gpu_helpers import directions, make_context
     cfgs = workloads.config3(scale=8)[:3]
     io = IO[prec]
-    base, _ = make_context(cfgs, prec, io)          # default shape: pair tiles, j-tile 256, group 4
+    base, _ = make_context(cfgs, prec, io)          # default shape: pair tiles for both, group 4
     V = [directions(c, io) for c in cfgs]
     F0, _ = base.gateaux(V)
     X0 = base.projection(1, sys=1)
@@ -248,7 +248,7 @@ def test_forced_launch_shapes(lib, prec, tmp_path, monkeypatch):
     code = {"tf32": 2, "bf16x3": 3}[prec]
     Xr = oracle.gateaux(oracle_system(cfgs[1]), cfgs[1]["V"][1:2])["X"][0][0]
     for nb, dpt, bn, kg in [(128, 1, 128, 1), (128, 2, 128, 4), (128, 1, 256, 4), (256, 1, 256, 4),
-                            (512, 1, 256, 2)]:
+                            (512, 1, 256, 2), (512, 1, 512, 4)]:
         cache = tmp_path / f"tune_{nb}_{dpt}_{bn}_{kg}.jsonl"
         cache.write_text('{"key": "%s", "g1_nb": %d, "g1_dpt": %d, "g2_bn": %d, "g2_kgroup": %d}\n'
                          % (_tune_key(cfgs, code), nb, dpt, bn, kg))
@@ -272,8 +272,10 @@ def test_forced_launch_shapes(lib, prec, tmp_path, monkeypatch):
             ref = oracle.gateaux(oracle_system(c), c["V"])
             err = per_direction_rel_err(F[i].double().cpu().numpy(), ref["F"])
             check(prec, "forced_launch_shapes", err)
-            if bn == 256 and nb == 512:
-                assert torch.equal(F[i], F0[i])      # the direction group only reorders items
+            if bn in (256, 512) and nb == 512:
+                # the direction group only reorders items, and the pair response
+                # sums each row in the single-CTA kernel's order
+                assert torch.equal(F[i], F0[i])
         assert len(cache.read_text().splitlines()) == 1     # read, not re-tuned
 
 
@@ -288,7 +290,7 @@ def test_autotune_batched(lib, tmp_path, monkeypatch):
     t = ctx.tuning()
     print("autotuned launch shape (uneven batch):", t)
     assert t["g1_nb"] in (128, 256, 512) and t["g1_dpt"] in (1, 2)
-    assert t["g2_bn"] in (128, 256) and t["g2_kgroup"] in (1, 2, 4)
+    assert t["g2_bn"] in (128, 256, 512) and t["g2_kgroup"] in (1, 2, 4)
     lines = cache.read_text().splitlines()
     assert len(lines) == 1 and '"key": "sm' in lines[0]
     V = [directions(c, torch.float32) for c in cfgs]
@@ -656,7 +658,73 @@ def test_set_tuning_rejects_bad_shapes(lib, cfg1):
     from gpu_helpers import make_context
     from paper_2211_07894_gb300 import binding
     ctx, _ = make_context([cfg1], "bf16x3", torch.float32)
-    for bad in [(384, 1, 256, 4), (256, 2, 256, 4), (512, 2, 256, 4), (256, 1, 192, 4), (256, 1, 256, 3)]:
+    for bad in [(384, 1, 256, 4), (256, 2, 256, 4), (512, 2, 256, 4), (256, 1, 192, 4), (256, 1, 256, 3),
+                (256, 1, 1024, 4)]:
         assert binding.lrdm_set_tuning(ctx.handle, *bad) == 1      # LRDM_ERR_INVALID_ARG
     f64, _ = make_context([cfg1], "fp64", torch.float64)
     assert binding.lrdm_set_tuning(f64.handle, 256, 1, 256, 4) == 9   # LRDM_ERR_UNSUPPORTED
+
+
+# --- response on CTA pairs (256-row blocks, 256-wide j-tiles) ---------------
+
+@pytest.mark.parametrize("case", sorted(PAIR_CASES))
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_pair_response_tiles(lib, prec, case):
+    """The pair-tile response (lrdm_set_tuning g2_bn = 512) against the
+    oracle on f and drho: grids whose row blocks are odd in number (the odd
+    CTA of the last pair reads zero fill) and padded N_s = 384 (the odd
+    CTA's half of the last j-tile lies outside the matrix); the single-CTA
+    response on the same context agrees within the precision's tolerance."""
+    from gpu_helpers import directions, make_context
+    cid, n, ns, K, ne = PAIR_CASES[case]
+    cfg = _ragged(cfg_id=cid, n=n, ns=ns, K=K, ne=ne)
+    io = IO[prec]
+    ctx, _ = make_context([cfg], prec, io)
+    ctx.set_tuning(g1_nb=512, g2_bn=512)
+    V = directions(cfg, io)
+    (F,), dmu = ctx.gateaux([V])
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    Fh = F.double().cpu().numpy()
+    check(prec, "pair_response_tiles", per_direction_rel_err(Fh, ref["F"]))
+    check(prec, "pair_response_tiles", per_direction_rel_err(Fh + cfg["V"], ref["drho"]), "X")
+    ctx.set_tuning(g2_bn=256)
+    (F2,), _ = ctx.gateaux([V])
+    torch.cuda.synchronize()
+    d = per_direction_rel_err(F2.double().cpu().numpy(), Fh)
+    print(f"pair response {prec} {case}: vs single-CTA response {d:.2e}")
+    assert d < gate(prec, "pair_response_tiles")
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_pair_response_split_and_batch(lib, prec):
+    """The pair response with one direction at N_s = 2048 (items split into
+    j-tile parts, FP64 part sums added by the combine kernel) and over the
+    uneven batch with its spin pair (grouped launch); oracle tolerance, and
+    the batch equals separate calls bit for bit."""
+    from gpu_helpers import directions, make_context
+    io = IO[prec]
+    cfg = _ragged(cfg_id=24, n=(16, 14, 11), ns=2048, K=2, ne=1800)
+    ctx, _ = make_context([cfg], prec, io)
+    ctx.set_tuning(g2_bn=512)
+    V = directions(cfg, io)
+    (F1,), _ = ctx.gateaux([V[:1].contiguous()])
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"][:1])
+    check(prec, "pair_response_split_and_batch", per_direction_rel_err(F1.double().cpu().numpy(), ref["F"]))
+    cfgs = workloads.config3(scale=8)
+    bctx, _ = make_context(cfgs, prec, io)
+    bctx.set_tuning(g2_bn=512)
+    Vb = [directions(c, io) for c in cfgs]
+    F, _ = bctx.gateaux(Vb)
+    torch.cuda.synchronize()
+    assert bctx.status() == 0
+    for i, c in enumerate(cfgs):
+        sep, _ = make_context([c], prec, io)
+        sep.set_tuning(g2_bn=512)
+        (Fi,), _ = sep.gateaux([Vb[i]])
+        assert torch.equal(Fi, F[i])
+        refc = oracle.gateaux(oracle_system(c), c["V"])
+        check(prec, "pair_response_split_and_batch", per_direction_rel_err(F[i].double().cpu().numpy(), refc["F"]))
