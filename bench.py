@@ -125,14 +125,17 @@ def tc_source_hash():
     return h.hexdigest()
 
 
-def recorded_value(record, field, kernel, workload, shape):
+def recorded_value(record, field, kernel, workload, shape, same_tile=False):
     """A per-launch ncu figure of `kernel` on `workload` in launch shape
     `shape` (the kernel's own tuning fields, e.g. 'g1_nb=256,g1_dpt=1') from
     the summaries under profiles/ (lines '<record>: kernel=... workload=...
     shape=... source_sha256=... <field>=...'), or None when no record matches
-    the current kernel sources and shape."""
+    the current kernel sources and shape.  same_tile: a record whose shape
+    differs only after its first field (the tile width; the rest orders the
+    work items) also matches, when no exact one does."""
     import glob
     want = tc_source_hash()
+    near = None
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as fh:
             for line in fh:
@@ -140,11 +143,15 @@ def recorded_value(record, field, kernel, workload, shape):
                 if not line.startswith(record + ":"):
                     continue
                 f = dict(kv.split("=", 1) for kv in line.split()[1:] if "=" in kv)
-                if (f.get("kernel") == kernel and f.get("workload") == workload
-                        and f.get("shape") == shape and f.get("source_sha256") == want
-                        and field in f):
+                if (f.get("kernel") != kernel or f.get("workload") != workload
+                        or f.get("source_sha256") != want or field not in f):
+                    continue
+                if f.get("shape") == shape:
                     return float(f[field])
-    return None
+                if (same_tile and shape and f.get("shape", "").split(",")[0] == shape.split(",")[0]
+                        and near is None):
+                    near = float(f[field])
+    return near
 
 
 def recorded_traffic(kernel, workload, shape):
@@ -153,8 +160,9 @@ def recorded_traffic(kernel, workload, shape):
 
 
 def recorded_tensor_pipe(kernel, workload, shape):
-    """sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed, %."""
-    return recorded_value("tensor-pipe-record", "pct_of_elapsed", kernel, workload, shape)
+    """sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_elapsed, %
+    (a record of the same tile width when the work-item order differs)."""
+    return recorded_value("tensor-pipe-record", "pct_of_elapsed", kernel, workload, shape, same_tile=True)
 
 
 class ClockSampler:
