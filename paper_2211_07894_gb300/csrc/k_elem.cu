@@ -10,14 +10,6 @@
 namespace lrdm {
 namespace {
 
-__device__ __forceinline__ double ld_io(const void* p, int io, long long i) {
-  return io == LRDM_DTYPE_F64 ? static_cast<const double*>(p)[i]
-                              : (double)static_cast<const float*>(p)[i];
-}
-__device__ __forceinline__ void st_io(void* p, int io, long long i, double x) {
-  if (io == LRDM_DTYPE_F64) static_cast<double*>(p)[i] = x;
-  else static_cast<float*>(p)[i] = (float)x;
-}
 __device__ __forceinline__ double ld_c(const void* p, int fp64, long long i) {
   return fp64 ? static_cast<const double*>(p)[i] : (double)static_cast<const float*>(p)[i];
 }
@@ -37,13 +29,64 @@ inline int grid_for(long long n, int block) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (n); \
        e += (long long)gridDim.x * blockDim.x)
 
-__global__ void k_spin_sum(const void* __restrict__ v, int io, int K, int nspin, long long Ng,
-                           void* __restrict__ out, int fp64) {
-  GRID_STRIDE(e, (long long)K * Ng) {
-    long long k = e / Ng, r = e - k * Ng;
-    double s = 0.0;
-    for (int c = 0; c < nspin; ++c) s += ld_io(v, io, (k * nspin + c) * Ng + r);
-    st_c(out, fp64, e, s);
+// Grid-length element-wise kernels: one thread per four consecutive grid
+// points r0 .. r0 + 3, looping over the directions k (and spins s) so that
+// the per-point factors (f_x, the symbol) are read and converted once; every
+// row access of a warp is contiguous, 16-byte vector loads and stores when
+// `vec` (all row starts 16-byte aligned).  Arithmetic in the compute type C
+// (float in the FP32 / TF32 / BF16x3 modes, double in FP64 mode).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* __restrict__ p, int n, bool vec, T (&o)[4]) {
+  if (vec && n == 4) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p);
+      o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+      const double2 a = reinterpret_cast<const double2*>(p)[0];
+      const double2 b = reinterpret_cast<const double2*>(p)[1];
+      o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = e < n ? p[e] : T(0);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* __restrict__ p, int n, bool vec, const T (&v)[4]) {
+  if (vec && n == 4) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+      reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (e < n) p[e] = v[e];
+  }
+}
+__device__ __forceinline__ int quad_count(long long len, long long r0) {
+  const long long n = len - r0;
+  return n <= 0 ? 0 : (n >= 4 ? 4 : (int)n);
+}
+
+// out[k][r] = sum_s v[k][s][r]
+template <typename Ti, typename C>
+__global__ void k_spin_sum(const Ti* __restrict__ v, int K, int nspin, long long Ng,
+                           C* __restrict__ out, int vec) {
+  const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  const int n = quad_count(Ng, r0);
+  if (n == 0) return;
+  for (int k = 0; k < K; ++k) {
+    C acc[4] = {C(0), C(0), C(0), C(0)};
+    for (int s = 0; s < nspin; ++s) {
+      Ti x[4];
+      ld4(v + ((long long)k * nspin + s) * Ng + r0, n, vec, x);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] += (C)x[e];
+    }
+    st4(out + (long long)k * Ng + r0, n, vec, acc);
   }
 }
 
@@ -92,67 +135,120 @@ __global__ void k_poisson(void* __restrict__ cplx, int K, long long per,
       }
     } else {
       float2* z = static_cast<float2*>(cplx);
+      const float sf = (float)sm;
       for (int k = 0; k < K; ++k) {
         float2 v = z[(long long)k * per + m];
-        v.x = (float)(v.x * sm);
-        v.y = (float)(v.y * sm);
+        v.x *= sf;
+        v.y *= sf;
         z[(long long)k * per + m] = v;
       }
     }
   }
 }
 
-// a[k][s][r] = scale (V_H[k][r] + f_xs[r] v[k][s][r]); rows r >= Ng are zero
-__global__ void k_dv_weights(const void* __restrict__ v, int io, const void* __restrict__ VH,
+// a[k][s][r] = scale (V_H[k][r] + f_xs[r] v[k][s][r]) for r < Ng; rows
+// Ng <= r < Ng_pad are zero
+template <typename Ti, typename C>
+__global__ void k_dv_weights(const Ti* __restrict__ v, const C* __restrict__ VH,
                              const double* __restrict__ fx0, const double* __restrict__ fx1, int K,
-                             int nspin, long long Ng, long long Ng_pad, double scale,
-                             void* __restrict__ a, int fp64) {
-  GRID_STRIDE(e, (long long)K * nspin * Ng_pad) {
-    long long q = e / Ng_pad, r = e - q * Ng_pad;
-    int s = (int)(q % nspin);
-    long long k = q / nspin;
-    double val = 0.0;
-    if (r < Ng) {
-      const double* fx = s == 0 ? fx0 : fx1;
-      val = scale * (ld_c(VH, fp64, k * Ng + r) + fx[r] * ld_io(v, io, q * Ng + r));
+                             int nspin, long long Ng, long long Ng_pad, C scale,
+                             C* __restrict__ a, int vec) {
+  const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  const int n_out = quad_count(Ng_pad, r0);
+  if (n_out == 0) return;
+  const int n = quad_count(Ng, r0);
+  C fx[2][4];                            // nspin <= 2; unrolled so that fx stays in registers
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double* f = s == 0 ? fx0 : fx1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) fx[s][e] = e < n ? (C)f[r0 + e] : C(0);
+  }
+  for (int k = 0; k < K; ++k) {
+    C vh[4];
+    ld4(VH + (long long)k * Ng + r0, n, vec, vh);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (s >= nspin) break;
+      const long long q = (long long)k * nspin + s;
+      Ti x[4];
+      ld4(v + q * Ng + r0, n, vec, x);
+      C o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = e < n ? scale * (vh[e] + fx[s][e] * (C)x[e]) : C(0);
+      st4(a + q * Ng_pad + r0, n_out, vec, o);
     }
-    st_c(a, fp64, e, val);
   }
 }
 
 // vbar[k][s][r] = V_H[sum_s dVbar][k][r] + f_xs[r] dVbar[k][s][r] - fbar[k][s][r]
-__global__ void k_adjoint_potential(const void* __restrict__ dvbar, const void* __restrict__ VH,
+template <typename Ti, typename C>
+__global__ void k_adjoint_potential(const C* __restrict__ dvbar, const C* __restrict__ VH,
                                     const double* __restrict__ fx0, const double* __restrict__ fx1,
-                                    const void* __restrict__ fbar, int io, int K, int nspin,
-                                    long long Ng, long long Ng_pad, void* __restrict__ vbar,
-                                    int fp64) {
-  GRID_STRIDE(e, (long long)K * nspin * Ng) {
-    long long q = e / Ng, r = e - q * Ng;
-    int s = (int)(q % nspin);
-    long long k = q / nspin;
-    const double* fx = s == 0 ? fx0 : fx1;
-    double d = ld_c(dvbar, fp64, q * Ng_pad + r);
-    st_io(vbar, io, e, ld_c(VH, fp64, k * Ng + r) + fx[r] * d - ld_io(fbar, io, e));
+                                    const Ti* __restrict__ fbar, int K, int nspin, long long Ng,
+                                    long long Ng_pad, Ti* __restrict__ vbar, int vec) {
+  const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  const int n = quad_count(Ng, r0);
+  if (n == 0) return;
+  C fx[2][4];                            // nspin <= 2; unrolled so that fx stays in registers
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double* f = s == 0 ? fx0 : fx1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) fx[s][e] = e < n ? (C)f[r0 + e] : C(0);
+  }
+  for (int k = 0; k < K; ++k) {
+    C vh[4];
+    ld4(VH + (long long)k * Ng + r0, n, vec, vh);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (s >= nspin) break;
+      const long long q = (long long)k * nspin + s;
+      C d[4];
+      Ti fb[4], o[4];
+      ld4(dvbar + q * Ng_pad + r0, n, vec, d);
+      ld4(fbar + q * Ng + r0, n, vec, fb);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = (Ti)(vh[e] + fx[s][e] * d[e] - (C)fb[e]);
+      st4(vbar + q * Ng + r0, n, vec, o);
+    }
   }
 }
 
 // spin sum of the (padded) adjoint potential for the Hartree transform
-__global__ void k_spin_sum_padded(const void* __restrict__ d, int K, int nspin, long long Ng,
-                                  long long Ng_pad, void* __restrict__ out, int fp64) {
-  GRID_STRIDE(e, (long long)K * Ng) {
-    long long k = e / Ng, r = e - k * Ng;
-    double s = 0.0;
-    for (int c = 0; c < nspin; ++c) s += ld_c(d, fp64, (k * nspin + c) * Ng_pad + r);
-    st_c(out, fp64, e, s);
+template <typename C>
+__global__ void k_spin_sum_padded(const C* __restrict__ d, int K, int nspin, long long Ng,
+                                  long long Ng_pad, C* __restrict__ out, int vec) {
+  const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  const int n = quad_count(Ng, r0);
+  if (n == 0) return;
+  for (int k = 0; k < K; ++k) {
+    C acc[4] = {C(0), C(0), C(0), C(0)};
+    for (int s = 0; s < nspin; ++s) {
+      C x[4];
+      ld4(d + ((long long)k * nspin + s) * Ng_pad + r0, n, vec, x);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] += x[e];
+    }
+    st4(out + (long long)k * Ng + r0, n, vec, acc);
   }
 }
 
-__global__ void k_scale_weights(const void* __restrict__ fbar, int io, int K, int nspin,
-                                long long Ng, long long Ng_pad, double scale,
-                                void* __restrict__ a, int fp64) {
-  GRID_STRIDE(e, (long long)K * nspin * Ng_pad) {
-    long long q = e / Ng_pad, r = e - q * Ng_pad;
-    st_c(a, fp64, e, r < Ng ? scale * ld_io(fbar, io, q * Ng + r) : 0.0);
+// a[k][s][r] = scale fbar[k][s][r] for r < Ng, zero for Ng <= r < Ng_pad
+template <typename Ti, typename C>
+__global__ void k_scale_weights(const Ti* __restrict__ fbar, int K, int nspin, long long Ng,
+                                long long Ng_pad, C scale, C* __restrict__ a, int vec) {
+  const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  const int n_out = quad_count(Ng_pad, r0);
+  if (n_out == 0) return;
+  const int n = quad_count(Ng, r0);
+  for (int q = 0; q < K * nspin; ++q) {
+    Ti x[4];
+    ld4(fbar + (long long)q * Ng + r0, n, vec, x);
+    C o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = e < n ? scale * (C)x[e] : C(0);
+    st4(a + (long long)q * Ng_pad + r0, n_out, vec, o);
   }
 }
 
@@ -253,7 +349,8 @@ __global__ void k_loewner_scale(const void* __restrict__ X, int acc64, int nspli
 // TF32 (layout 1) or split into bf16 hi / lo (layout 2).  Off-diagonal products
 // in FP32 with the FP32 copy of L (the result is stored with at most 16
 // significant bits); the diagonal (mu' shift) in FP64.  One thread per four
-// consecutive columns: grid (column quads, rows, directions).
+// consecutive columns of one row, looping over the K directions so that the
+// row's L entries are read once: grid (column quads, rows).
 __global__ void k_loewner_scale_tc(const float* __restrict__ X, int nsplit, int K, int ns, int ld,
                                    const float* __restrict__ Lf, const double* __restrict__ L,
                                    const double* __restrict__ shift, int adjoint,
@@ -261,54 +358,61 @@ __global__ void k_loewner_scale_tc(const float* __restrict__ X, int nsplit, int 
                                    __nv_bfloat16* __restrict__ out_lo) {
   const int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int row = blockIdx.y;
-  const int k = blockIdx.z;
   if (c0 >= ld) return;
-  const long long o = ((long long)k * ld + row) * ld + c0;
-  // X: [nsplit][K][ld][ld] partial sums over grid-row ranges, added in order
-  float4 x4 = *reinterpret_cast<const float4*>(X + o);
-  for (int p = 1; p < nsplit; ++p) {
-    const float4 y = *reinterpret_cast<const float4*>(X + o + (long long)p * K * ld * ld);
-    x4.x += y.x;
-    x4.y += y.y;
-    x4.z += y.z;
-    x4.w += y.w;
-  }
-  const float4 l4 = *reinterpret_cast<const float4*>(Lf + (long long)row * ld + c0);
-  const float xs[4] = {x4.x, x4.y, x4.z, x4.w}, ls[4] = {l4.x, l4.y, l4.z, l4.w};
-  float v[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int i = c0 + e, j = row;
-    if (i < j && j < ns) {
-      v[e] = 2.f * ls[e] * xs[e];
-    } else if (i == j && j < ns) {
-      const double l = L[(long long)i * ns + i];
-      v[e] = (float)(adjoint ? l * (double)xs[e] - l * shift[k] * inv_trace
-                             : l * ((double)xs[e] - shift[k]));
-    } else {
-      v[e] = 0.f;
+  const long long mat = (long long)ld * ld;
+  const long long base = (long long)row * ld + c0;
+  const float4 l4 = *reinterpret_cast<const float4*>(Lf + base);
+  const float ls[4] = {l4.x, l4.y, l4.z, l4.w};
+  // column c0 + dg is the diagonal of this row when 0 <= dg < 4
+  const int dg = row - c0;
+  const double ldiag = (dg >= 0 && dg < 4 && row < ns) ? L[(long long)row * ns + row] : 0.0;
+#pragma unroll 2
+  for (int k = 0; k < K; ++k) {
+    const long long o = (long long)k * mat + base;
+    // X: [nsplit][K][ld][ld] partial sums over grid-row ranges, added in order
+    float4 x4 = *reinterpret_cast<const float4*>(X + o);
+    for (int p = 1; p < nsplit; ++p) {
+      const float4 y = *reinterpret_cast<const float4*>(X + o + (long long)p * K * mat);
+      x4.x += y.x;
+      x4.y += y.y;
+      x4.z += y.z;
+      x4.w += y.w;
     }
-  }
-  if (layout == 1) {
-    float4 t;
-    t.x = tf32_rna(v[0]);
-    t.y = tf32_rna(v[1]);
-    t.z = tf32_rna(v[2]);
-    t.w = tf32_rna(v[3]);
-    *reinterpret_cast<float4*>(static_cast<float*>(out) + o) = t;
-  } else {
-    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[0], v[1]);
-    const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[2], v[3]);
-    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[0] - f01.x, v[1] - f01.y);
-    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[2] - f23.x, v[3] - f23.y);
-    uint2 hw, lw;
-    hw.x = *reinterpret_cast<const uint32_t*>(&h01);
-    hw.y = *reinterpret_cast<const uint32_t*>(&h23);
-    lw.x = *reinterpret_cast<const uint32_t*>(&l01);
-    lw.y = *reinterpret_cast<const uint32_t*>(&l23);
-    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out) + o) = hw;
-    *reinterpret_cast<uint2*>(out_lo + o) = lw;
+    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+    float v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = c0 + e, j = row;
+      if (i < j && j < ns) {
+        v[e] = 2.f * ls[e] * xs[e];
+      } else if (i == j && j < ns) {
+        v[e] = (float)(adjoint ? ldiag * (double)xs[e] - ldiag * shift[k] * inv_trace
+                               : ldiag * ((double)xs[e] - shift[k]));
+      } else {
+        v[e] = 0.f;
+      }
+    }
+    if (layout == 1) {
+      float4 t;
+      t.x = tf32_rna(v[0]);
+      t.y = tf32_rna(v[1]);
+      t.z = tf32_rna(v[2]);
+      t.w = tf32_rna(v[3]);
+      *reinterpret_cast<float4*>(static_cast<float*>(out) + o) = t;
+    } else {
+      const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[0], v[1]);
+      const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[2], v[3]);
+      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+      const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[0] - f01.x, v[1] - f01.y);
+      const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[2] - f23.x, v[3] - f23.y);
+      uint2 hw, lw;
+      hw.x = *reinterpret_cast<const uint32_t*>(&h01);
+      hw.y = *reinterpret_cast<const uint32_t*>(&h23);
+      lw.x = *reinterpret_cast<const uint32_t*>(&l01);
+      lw.y = *reinterpret_cast<const uint32_t*>(&l23);
+      *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(out) + o) = hw;
+      *reinterpret_cast<uint2*>(out_lo + o) = lw;
+    }
   }
 }
 
@@ -342,56 +446,141 @@ __global__ void k_trace_bar(DmuArgs A, int acc64, double* __restrict__ tbar) {
 //   eps_bar_i = sum_{j != i, |de| > tau} 2 Lbar_ij (-L_ij / (eps_i - eps_j))
 //   occ_bar_i = sum_{j != i, |de| > tau} 2 Lbar_ij / (eps_i - eps_j)
 //             + sum_{j != i, |de| <= tau} 2 Lbar_ij (-(1 - 2 fbar)/(2 kT)) + Lbar_ii (-(1 - 2 f_i)/kT)
-__global__ void k_eps_occ_bar(const void* __restrict__ X, const void* __restrict__ G, int acc64,
-                              int nsplit, int K, int ns, int ldx, const double* __restrict__ L,
-                              const double* __restrict__ eps, const double* __restrict__ occ,
-                              const double* __restrict__ dmu, const double* __restrict__ tbar,
-                              double inv_trace, double kT, double tau,
-                              double* __restrict__ eps_bar, double* __restrict__ occ_bar) {
-  int i = blockIdx.x;
-  long long mat = (long long)ldx * ldx;
-  double eb = 0.0, ob = 0.0;
-  for (int j = threadIdx.x; j < ns; j += blockDim.x) {
-    double lb = 0.0;
-    if (acc64 || i == j) {
-      for (int k = 0; k < K; ++k) {
-        double x = 0.0, gg = 0.0;
-        for (int p = 0; p < nsplit; ++p) {
-          long long o = ((long long)p * K + k) * mat + (long long)i * ldx + j;
-          x += ld_c(X, acc64, o);
-          gg += ld_c(G, acc64, o);
-        }
-        if (i == j) lb += gg * (x - dmu[k]) - tbar[k] * inv_trace * (x - dmu[k]);
-        else lb += gg * x;
-      }
-    } else {
-      // FP32 partials: the off-diagonal sum over directions in FP32
-      const float* Xf = static_cast<const float*>(X);
-      const float* Gf = static_cast<const float*>(G);
-      float acc = 0.f;
-      for (int k = 0; k < K; ++k) {
-        float x = 0.f, gg = 0.f;
-        for (int p = 0; p < nsplit; ++p) {
-          long long o = ((long long)p * K + k) * mat + (long long)i * ldx + j;
-          x += Xf[o];
-          gg += Gf[o];
-        }
-        acc = fmaf(gg, x, acc);
-      }
-      lb = (double)acc;
+//
+// With FP32 partials (the tensor-core and FP32 modes) Lbar_ij (j != i) is
+// summed over the directions in FP32, four consecutive j per thread with
+// 16-byte loads when the leading dimension allows; where the FP32 copy of L
+// exists (Lf, leading dimension ldf: the tensor-core modes) the terms of a gap
+// above tau are formed in FP32 from the FP64 gap, summed per thread in FP32
+// and added to the FP64 sums once (Lbar itself carries FP32 rounding there).
+struct EobArgs {
+  const double* L;
+  const float* Lf;
+  int ldf;
+  const double* eps;
+  const double* occ;
+  double kT, tau;
+};
+
+__device__ __forceinline__ void eob_term(const EobArgs& a, int i, int j, double eps_i, double lb,
+                                         int ns, double& eb, double& ob, float& ebf, float& obf) {
+  const double de = eps_i - a.eps[j];
+  if (i == j) {
+    ob += lb * (-(1.0 - 2.0 * a.occ[i]) / a.kT);
+  } else if (fabs(de) > a.tau && a.Lf) {
+    const float t = 2.f * (float)lb / (float)de;
+    ebf = fmaf(-t, a.Lf[(long long)i * a.ldf + j], ebf);
+    obf += t;
+  } else if (fabs(de) > a.tau) {
+    const double rde = 1.0 / de;
+    eb += 2.0 * lb * (-a.L[(long long)i * ns + j] * rde);
+    ob += 2.0 * lb * rde;
+  } else {
+    const double fb = 0.5 * (a.occ[i] + a.occ[j]);
+    ob += 2.0 * lb * (-(1.0 - 2.0 * fb) / (2.0 * a.kT));
+  }
+}
+
+// Lbar_ij in FP64 (the FP64 mode, and the diagonal in every mode)
+__device__ __forceinline__ double eob_lbar64(const void* X, const void* G, int acc64, int nsplit,
+                                             int K, long long mat, long long row, int i, int j,
+                                             const double* dmu, const double* tbar,
+                                             double inv_trace) {
+  double lb = 0.0;
+  for (int k = 0; k < K; ++k) {
+    double x = 0.0, gg = 0.0;
+    for (int p = 0; p < nsplit; ++p) {
+      const long long o = ((long long)p * K + k) * mat + row + j;
+      x += ld_c(X, acc64, o);
+      gg += ld_c(G, acc64, o);
     }
-    double de = eps[i] - eps[j];
-    if (i == j) {
-      ob += lb * (-(1.0 - 2.0 * occ[i]) / kT);
-    } else if (fabs(de) > tau) {
-      const double rde = 1.0 / de;
-      eb += 2.0 * lb * (-L[(long long)i * ns + j] * rde);
-      ob += 2.0 * lb * rde;
-    } else {
-      double fb = 0.5 * (occ[i] + occ[j]);
-      ob += 2.0 * lb * (-(1.0 - 2.0 * fb) / (2.0 * kT));
+    if (i == j) lb += gg * (x - dmu[k]) - tbar[k] * inv_trace * (x - dmu[k]);
+    else lb += gg * x;
+  }
+  return lb;
+}
+
+__global__ void k_eps_occ_bar(const void* __restrict__ X, const void* __restrict__ G, int acc64,
+                              int nsplit, int K, int ns, int ldx, EobArgs a,
+                              const double* __restrict__ dmu, const double* __restrict__ tbar,
+                              double inv_trace, double* __restrict__ eps_bar,
+                              double* __restrict__ occ_bar) {
+  const int i = blockIdx.x;
+  const long long mat = (long long)ldx * ldx;
+  const long long row = (long long)i * ldx;
+  double eb = 0.0, ob = 0.0;
+  float ebf = 0.f, obf = 0.f;
+  const double eps_i = a.eps[i];
+  if (!acc64 && ldx % 4 == 0) {
+    // FP32 partials: rows of 16-byte quads (ldx is a multiple of 4, so a quad
+    // starting below ns stays inside the padded row)
+    const float* Xf = static_cast<const float*>(X);
+    const float* Gf = static_cast<const float*>(G);
+    for (int j0 = 4 * threadIdx.x; j0 < ns; j0 += 4 * blockDim.x) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      if (nsplit == 1) {
+        // one partial: unrolled so that several directions' loads are in flight
+#pragma unroll 4
+        for (int k = 0; k < K; ++k) {
+          const long long o = (long long)k * mat + row + j0;
+          const float4 x = *reinterpret_cast<const float4*>(Xf + o);
+          const float4 g = *reinterpret_cast<const float4*>(Gf + o);
+          acc[0] = fmaf(g.x, x.x, acc[0]);
+          acc[1] = fmaf(g.y, x.y, acc[1]);
+          acc[2] = fmaf(g.z, x.z, acc[2]);
+          acc[3] = fmaf(g.w, x.w, acc[3]);
+        }
+      } else {
+        for (int k = 0; k < K; ++k) {
+          float4 x = make_float4(0.f, 0.f, 0.f, 0.f), g = x;
+          for (int p = 0; p < nsplit; ++p) {
+            const long long o = ((long long)p * K + k) * mat + row + j0;
+            const float4 xv = *reinterpret_cast<const float4*>(Xf + o);
+            const float4 gv = *reinterpret_cast<const float4*>(Gf + o);
+            x.x += xv.x; x.y += xv.y; x.z += xv.z; x.w += xv.w;
+            g.x += gv.x; g.y += gv.y; g.z += gv.z; g.w += gv.w;
+          }
+          acc[0] = fmaf(g.x, x.x, acc[0]);
+          acc[1] = fmaf(g.y, x.y, acc[1]);
+          acc[2] = fmaf(g.z, x.z, acc[2]);
+          acc[3] = fmaf(g.w, x.w, acc[3]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = j0 + e;
+        if (j >= ns) break;
+        const double lb = j == i ? eob_lbar64(X, G, 0, nsplit, K, mat, row, i, j, dmu, tbar, inv_trace)
+                                 : (double)acc[e];
+        eob_term(a, i, j, eps_i, lb, ns, eb, ob, ebf, obf);
+      }
+    }
+  } else {
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+      double lb;
+      if (acc64 || i == j) {
+        lb = eob_lbar64(X, G, acc64, nsplit, K, mat, row, i, j, dmu, tbar, inv_trace);
+      } else {
+        // FP32 partials with an unaligned leading dimension
+        const float* Xf = static_cast<const float*>(X);
+        const float* Gf = static_cast<const float*>(G);
+        float acc = 0.f;
+        for (int k = 0; k < K; ++k) {
+          float x = 0.f, gg = 0.f;
+          for (int p = 0; p < nsplit; ++p) {
+            const long long o = ((long long)p * K + k) * mat + row + j;
+            x += Xf[o];
+            gg += Gf[o];
+          }
+          acc = fmaf(gg, x, acc);
+        }
+        lb = (double)acc;
+      }
+      eob_term(a, i, j, eps_i, lb, ns, eb, ob, ebf, obf);
     }
   }
+  eb += (double)ebf;
+  ob += (double)obf;
   __shared__ double se[32], so[32];
   for (int o = 16; o > 0; o >>= 1) {
     eb += __shfl_xor_sync(0xffffffffu, eb, o);
@@ -400,10 +589,10 @@ __global__ void k_eps_occ_bar(const void* __restrict__ X, const void* __restrict
   if ((threadIdx.x & 31) == 0) { se[threadIdx.x >> 5] = eb; so[threadIdx.x >> 5] = ob; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += se[w]; b += so[w]; }
-    if (eps_bar) eps_bar[i] = a;
-    if (occ_bar) occ_bar[i] = b;
+    double s0 = 0, s1 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s0 += se[w]; s1 += so[w]; }
+    if (eps_bar) eps_bar[i] = s0;
+    if (occ_bar) occ_bar[i] = s1;
   }
 }
 
@@ -430,10 +619,32 @@ cudaError_t launch_get_projection(const SysState& S, int s, int k, int acc_fp64,
   return cudaGetLastError();
 }
 
+// grid of the quad kernels: one thread per four consecutive points of `len`
+inline unsigned quad_grid(long long len) {
+  const long long quads = (len + 3) / 4;
+  return (unsigned)((quads + 255) / 256);
+}
+inline bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Instantiates kernel<Ti, C> for the io dtype (Ti) and compute precision (C).
+#define IO_C_DISPATCH(io, fp64, CALL)                              \
+  do {                                                             \
+    if (io == LRDM_DTYPE_F64) {                                    \
+      if (fp64) { using Ti = double; using C = double; CALL; }     \
+      else { using Ti = double; using C = float; CALL; }           \
+    } else {                                                       \
+      if (fp64) { using Ti = float; using C = double; CALL; }      \
+      else { using Ti = float; using C = float; CALL; }            \
+    }                                                              \
+  } while (0)
+
 cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long long Ng,
                             void* fft_real, int fp64, cudaStream_t st) {
-  k_spin_sum<<<grid_for((long long)K * Ng, 256), 256, 0, st>>>(v, io_dtype, K, nspin, Ng,
-                                                                fft_real, fp64);
+  if (K == 0 || Ng == 0) return cudaSuccess;
+  const int vec = Ng % 4 == 0 && al16(v) && al16(fft_real);
+  IO_C_DISPATCH(io_dtype, fp64,
+                (k_spin_sum<Ti, C><<<quad_grid(Ng), 256, 0, st>>>(
+                    static_cast<const Ti*>(v), K, nspin, Ng, static_cast<C*>(fft_real), vec)));
   return cudaGetLastError();
 }
 
@@ -454,8 +665,12 @@ cudaError_t launch_poisson_symbol(void* cplx, int K, long long per, const double
 cudaError_t launch_dv_weights(const void* v, int io_dtype, const void* VH, const double* fx0,
                               const double* fx1, int K, int nspin, long long Ng, long long Ng_pad,
                               double scale, void* a, int fp64, cudaStream_t st) {
-  k_dv_weights<<<grid_for((long long)K * nspin * Ng_pad, 256), 256, 0, st>>>(
-      v, io_dtype, VH, fx0, fx1, K, nspin, Ng, Ng_pad, scale, a, fp64);
+  if (K == 0 || Ng_pad == 0) return cudaSuccess;
+  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && al16(v) && al16(VH) && al16(a);
+  IO_C_DISPATCH(io_dtype, fp64,
+                (k_dv_weights<Ti, C><<<quad_grid(Ng_pad), 256, 0, st>>>(
+                    static_cast<const Ti*>(v), static_cast<const C*>(VH), fx0, fx1, K, nspin, Ng,
+                    Ng_pad, (C)scale, static_cast<C*>(a), vec)));
   return cudaGetLastError();
 }
 
@@ -463,23 +678,39 @@ cudaError_t launch_adjoint_potential(const void* dvbar, const void* VH, const do
                                      const double* fx1, const void* fbar, int io_dtype, int K,
                                      int nspin, long long Ng, long long Ng_pad, void* vbar,
                                      int fp64, cudaStream_t st) {
-  k_adjoint_potential<<<grid_for((long long)K * nspin * Ng, 256), 256, 0, st>>>(
-      dvbar, VH, fx0, fx1, fbar, io_dtype, K, nspin, Ng, Ng_pad, vbar, fp64);
+  if (K == 0 || Ng == 0) return cudaSuccess;
+  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && al16(dvbar) && al16(VH) && al16(fbar) &&
+                  al16(vbar);
+  IO_C_DISPATCH(io_dtype, fp64,
+                (k_adjoint_potential<Ti, C><<<quad_grid(Ng), 256, 0, st>>>(
+                    static_cast<const C*>(dvbar), static_cast<const C*>(VH), fx0, fx1,
+                    static_cast<const Ti*>(fbar), K, nspin, Ng, Ng_pad, static_cast<Ti*>(vbar),
+                    vec)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_spin_sum_padded(const void* d, int K, int nspin, long long Ng,
                                    long long Ng_pad, void* out, int fp64, cudaStream_t st) {
-  k_spin_sum_padded<<<grid_for((long long)K * Ng, 256), 256, 0, st>>>(d, K, nspin, Ng, Ng_pad,
-                                                                       out, fp64);
+  if (K == 0 || Ng == 0) return cudaSuccess;
+  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && al16(d) && al16(out);
+  if (fp64)
+    k_spin_sum_padded<double><<<quad_grid(Ng), 256, 0, st>>>(
+        static_cast<const double*>(d), K, nspin, Ng, Ng_pad, static_cast<double*>(out), vec);
+  else
+    k_spin_sum_padded<float><<<quad_grid(Ng), 256, 0, st>>>(
+        static_cast<const float*>(d), K, nspin, Ng, Ng_pad, static_cast<float*>(out), vec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_weights(const void* fbar, int io_dtype, int K, int nspin, long long Ng,
                                  long long Ng_pad, double scale, void* a, int fp64,
                                  cudaStream_t st) {
-  k_scale_weights<<<grid_for((long long)K * nspin * Ng_pad, 256), 256, 0, st>>>(
-      fbar, io_dtype, K, nspin, Ng, Ng_pad, scale, a, fp64);
+  if (K == 0 || Ng_pad == 0) return cudaSuccess;
+  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && al16(fbar) && al16(a);
+  IO_C_DISPATCH(io_dtype, fp64,
+                (k_scale_weights<Ti, C><<<quad_grid(Ng_pad), 256, 0, st>>>(
+                    static_cast<const Ti*>(fbar), K, nspin, Ng, Ng_pad, (C)scale,
+                    static_cast<C*>(a), vec)));
   return cudaGetLastError();
 }
 
@@ -520,7 +751,7 @@ cudaError_t launch_loewner_scale(const SysState& S, int s, const void* Xpart, in
   if (K == 0) return cudaSuccess;
   if (layout != 0) {
     const int ld = c.ns_pad;                     // multiple of 128
-    dim3 grid((ld / 4 + 127) / 128, ld, K);
+    dim3 grid((ld / 4 + 127) / 128, ld);
     k_loewner_scale_tc<<<grid, 128, 0, st>>>(static_cast<const float*>(Xpart), S.nsplit, K, c.ns, ld,
                                               c.Lf, c.L,
                                               shift, adjoint, inv_trace_L, layout, c.Xpp,
@@ -542,9 +773,10 @@ cudaError_t launch_eps_occ_bar(const SysState& S, int s, int K, int acc_fp64, do
   const Channel& c = S.ch[s];
   int tc = (c.psiR_hi || c.psiR32) ? 1 : 0;
   int ldx = tc ? c.ns_pad : c.ns;
-  k_eps_occ_bar<<<c.ns, 256, 0, st>>>(c.Xpart, c.Gpart, acc_fp64, S.nsplit, K, c.ns, ldx, c.L,
-                                      c.eps, c.occ, S.dmu, S.tbar, inv_trace_L, S.kT,
-                                      degen_tol * S.kT, eps_bar, occ_bar);
+  // the FP32 copy of L exists in the tensor-core modes (leading dimension ns_pad)
+  EobArgs a{c.L, acc_fp64 ? nullptr : c.Lf, c.ns_pad, c.eps, c.occ, S.kT, degen_tol * S.kT};
+  k_eps_occ_bar<<<c.ns, 256, 0, st>>>(c.Xpart, c.Gpart, acc_fp64, S.nsplit, K, c.ns, ldx, a, S.dmu,
+                                      S.tbar, inv_trace_L, eps_bar, occ_bar);
   return cudaGetLastError();
 }
 

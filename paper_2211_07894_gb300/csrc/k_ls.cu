@@ -1,6 +1,6 @@
 // The low-rank least-squares step (Eqs. plowrank, relativeError, quasinewton):
 //   S_kl = <f_k, f_l>, c_k = <f_k, R>, ||R||^2   (FP64 partial sums, fixed order)
-//   S = Q diag(lambda) Q^T by cyclic Jacobi rotations (FP64, one block)
+//   S = Q diag(lambda) Q^T by parallel cyclic Jacobi rotations (FP64, one block)
 //   a = Q diag(lambda^+) Q^T c  (lambda < rcond lambda_max dropped -> SINGULAR flag)
 //   Delta = sum_k a_k v_k, rho <- rho - alpha Delta, s_rel = ||F a - R|| / ||R||
 #include "lrdm_internal.h"
@@ -94,10 +94,19 @@ __global__ void __launch_bounds__(KMAX_LIMIT) k_ls_solve(const double* __restric
   const int nval = npair + K + 1;
   const int t = threadIdx.x;
   if (t == 0) bad = 0;
-  // fixed-order reduction of the per-block partials
+  // fixed-order reduction of the per-block partials: eight interleaved sums
+  // (block b into sum b % 8, so eight loads are in flight), added pairwise
   for (int idx = t; idx < nval; idx += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(long long)b * nval + idx];
+    double a8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int b = 0;
+    for (; b + 8 <= nblk; b += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a8[u] += partial[(long long)(b + u) * nval + idx];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (b + u < nblk) a8[u] += partial[(long long)(b + u) * nval + idx];
+    double s = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
     s *= w;
     if (idx < npair) {
       int k = 0, rem = idx;
@@ -124,49 +133,96 @@ __global__ void __launch_bounds__(KMAX_LIMIT) k_ls_solve(const double* __restric
     if (t == 0) { scal[0] = r2s; }
     return;
   }
-  // cyclic Jacobi sweeps
+  // Parallel cyclic Jacobi sweeps (round-robin ordering): a sweep is n - 1
+  // rounds (n = K rounded up to even; index K is a dummy when K is odd); a
+  // round rotates the n / 2 disjoint pairs (p, q) at once, A <- J^T A J and
+  // Q <- Q J, so every pair is rotated once per sweep.
+  __shared__ double rc[KMAX_LIMIT / 2], rs[KMAX_LIMIT / 2], rt[KMAX_LIMIT / 2];
+  __shared__ double rpq[KMAX_LIMIT / 2], rpp[KMAX_LIMIT / 2], rqq[KMAX_LIMIT / 2];
+  __shared__ int rp[KMAX_LIMIT / 2], rq[KMAX_LIMIT / 2];
+  __shared__ double red_o[KMAX_LIMIT / 32], red_d[KMAX_LIMIT / 32];
+  const int n_rr = K + (K & 1);
+  const int nrot = n_rr / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    __shared__ double off, diag;
-    if (t == 0) {
-      double o = 0.0, d = 0.0;
-      for (int i = 0; i < K; ++i)
-        for (int j = 0; j < K; ++j) {
-          if (i == j) d += A(i, i) * A(i, i);
-          else o += A(i, j) * A(i, j);
-        }
-      off = o;
-      diag = d;
-    }
-    __syncthreads();
-    if (!(off > 1e-30 * diag) || off == 0.0) break;
-    for (int p = 0; p < K - 1; ++p) {
-      for (int q = p + 1; q < K; ++q) {
-        double apq = A(p, q), app = A(p, p), aqq = A(q, q);
-        __syncthreads();
-        if (apq == 0.0 || fabs(apq) < 1e-300) continue;
-        double tau = (aqq - app) / (2.0 * apq);
-        double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
-        double akp = 0, akq = 0, qkp = 0, qkq = 0;
-        if (t < K) { akp = A(t, p); akq = A(t, q); qkp = Q(t, p); qkq = Q(t, q); }
-        __syncthreads();
-        if (t < K) {
-          if (t != p && t != q) {
-            double np = cs * akp - sn * akq, nq = sn * akp + cs * akq;
-            A(t, p) = np; A(p, t) = np;
-            A(t, q) = nq; A(q, t) = nq;
-          }
-          Q(t, p) = cs * qkp - sn * qkq;
-          Q(t, q) = sn * qkp + cs * qkq;
-        }
-        if (t == 0) {
-          A(p, p) = app - tt * apq;
-          A(q, q) = aqq + tt * apq;
-          A(p, q) = 0.0;
-          A(q, p) = 0.0;
-        }
-        __syncthreads();
+    // off-diagonal and diagonal Frobenius sums, fixed reduction order
+    double o = 0.0, d = 0.0;
+    if (t < K)
+      for (int j = 0; j < K; ++j) {
+        const double x = A(t, j);
+        if (j == t) d += x * x;
+        else o += x * x;
       }
+    for (int s = 16; s > 0; s >>= 1) {
+      o += __shfl_xor_sync(0xffffffffu, o, s);
+      d += __shfl_xor_sync(0xffffffffu, d, s);
+    }
+    if ((t & 31) == 0) { red_o[t >> 5] = o; red_d[t >> 5] = d; }
+    __syncthreads();
+    o = 0.0;
+    d = 0.0;
+    for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) { o += red_o[wi]; d += red_d[wi]; }
+    if (!(o > 1e-30 * d) || o == 0.0) break;
+    for (int r = 0; r < n_rr - 1; ++r) {
+      // the rotation of pair m (thread m)
+      if (t < nrot) {
+        int p, q;
+        if (t == 0) { p = r; q = n_rr - 1; }
+        else { p = (r + t) % (n_rr - 1); q = (r - t + n_rr - 1) % (n_rr - 1); }
+        if (p > q) { const int x = p; p = q; q = x; }
+        double cs = 1.0, sn = 0.0, tt = 0.0, apq = 0.0, app = 0.0, aqq = 0.0;
+        if (q < K) {
+          apq = A(p, q);
+          app = A(p, p);
+          aqq = A(q, q);
+          if (apq != 0.0 && fabs(apq) >= 1e-300) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            cs = 1.0 / sqrt(1.0 + tt * tt);
+            sn = tt * cs;
+          }
+        }
+        rp[t] = p; rq[t] = q; rc[t] = cs; rs[t] = sn; rt[t] = tt;
+        rpq[t] = apq; rpp[t] = app; rqq[t] = aqq;
+      }
+      __syncthreads();
+      // columns: B = A J, Q <- Q J (thread per row)
+      if (t < K)
+        for (int m = 0; m < nrot; ++m) {
+          const int p = rp[m], q = rq[m];
+          if (q >= K || rt[m] == 0.0) continue;
+          const double c = rc[m], s = rs[m];
+          const double ap = A(t, p), aq = A(t, q);
+          A(t, p) = c * ap - s * aq;
+          A(t, q) = s * ap + c * aq;
+          const double qp = Q(t, p), qq = Q(t, q);
+          Q(t, p) = c * qp - s * qq;
+          Q(t, q) = s * qp + c * qq;
+        }
+      __syncthreads();
+      // rows: A <- J^T B (thread per column)
+      if (t < K)
+        for (int m = 0; m < nrot; ++m) {
+          const int p = rp[m], q = rq[m];
+          if (q >= K || rt[m] == 0.0) continue;
+          const double c = rc[m], s = rs[m];
+          const double bp = A(p, t), bq = A(q, t);
+          A(p, t) = c * bp - s * bq;
+          A(q, t) = s * bp + c * bq;
+        }
+      __syncthreads();
+      // exact symmetry (the lower triangle mirrors the upper) and the closed
+      // form of each rotated 2 x 2 block
+      if (t < K)
+        for (int j = t + 1; j < K; ++j) A(j, t) = A(t, j);
+      __syncthreads();
+      if (t < nrot && rq[t] < K && rt[t] != 0.0) {
+        const int p = rp[t], q = rq[t];
+        A(p, p) = rpp[t] - rt[t] * rpq[t];
+        A(q, q) = rqq[t] + rt[t] * rpq[t];
+        A(p, q) = 0.0;
+        A(q, p) = 0.0;
+      }
+      __syncthreads();
     }
   }
   if (t < K) lam[t] = A(t, t);
