@@ -973,8 +973,20 @@ def main():
     if ctx.status() != 0:
         raise RuntimeError("device status not ok after the timed region")
     forward_only = forward_k1 = None
+    apply_ms = None
     if not directions:
         forward_only, forward_k1 = time_forward_calls(torch, ctx, V, F, dmu, prof, args, world)
+        # the least-squares step alone (Gram, K x K solve, update) on the step's own derivatives
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        rho_tmp = rho_out.clone()
+        a0.record(stream)
+        for _ in range(10):
+            ctx.apply(0, R, V, F, 0.0, rho=rho_tmp, coeff=coeff, s_rel=srel)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        apply_ms = a0.elapsed_time(a1) / 10
+        del rho_tmp
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -1090,6 +1102,7 @@ def main():
                 "breakdown_ms": {"gemm1_per_step": prof["gemm1_ms"] / steps,
                                  "gemm2_per_step": prof["gemm2_ms"] / steps,
                                  "poisson_per_step": prof["poisson_ms"] / steps,
+                                 "apply_per_call": apply_ms,
                                  "gemm1_launches_per_step": prof["gemm1_launches"] / steps,
                                  "gemm2_launches_per_step": prof["gemm2_launches"] / steps}}
         print(json.dumps(line), flush=True)

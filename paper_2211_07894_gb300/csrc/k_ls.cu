@@ -72,8 +72,10 @@ __global__ void __launch_bounds__(256) k_gram(const void* __restrict__ F,
   }
 }
 
-// One block of 64 threads: reduce partials, Jacobi eigendecomposition, a = S^+ c.
-__global__ void __launch_bounds__(KMAX_LIMIT) k_ls_solve(const double* __restrict__ partial,
+// One block of LS_SOLVE_THREADS threads: reduce partials, Jacobi
+// eigendecomposition, a = S^+ c.
+constexpr int LS_SOLVE_THREADS = 256;
+__global__ void __launch_bounds__(LS_SOLVE_THREADS, 1) k_ls_solve(const double* __restrict__ partial,
                                                          int nblk, int K, double w, double rcond,
                                                          double* __restrict__ coef,
                                                          double* __restrict__ coeff_out,
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(KMAX_LIMIT) k_ls_solve(const double* __restric
   __shared__ double rc[KMAX_LIMIT / 2], rs[KMAX_LIMIT / 2], rt[KMAX_LIMIT / 2];
   __shared__ double rpq[KMAX_LIMIT / 2], rpp[KMAX_LIMIT / 2], rqq[KMAX_LIMIT / 2];
   __shared__ int rp[KMAX_LIMIT / 2], rq[KMAX_LIMIT / 2];
-  __shared__ double red_o[KMAX_LIMIT / 32], red_d[KMAX_LIMIT / 32];
+  __shared__ double red_o[LS_SOLVE_THREADS / 32], red_d[LS_SOLVE_THREADS / 32];
   const int n_rr = K + (K & 1);
   const int nrot = n_rr / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
@@ -185,30 +187,31 @@ __global__ void __launch_bounds__(KMAX_LIMIT) k_ls_solve(const double* __restric
         rpq[t] = apq; rpp[t] = app; rqq[t] = aqq;
       }
       __syncthreads();
-      // columns: B = A J, Q <- Q J (thread per row)
-      if (t < K)
-        for (int m = 0; m < nrot; ++m) {
-          const int p = rp[m], q = rq[m];
-          if (q >= K || rt[m] == 0.0) continue;
-          const double c = rc[m], s = rs[m];
-          const double ap = A(t, p), aq = A(t, q);
-          A(t, p) = c * ap - s * aq;
-          A(t, q) = s * ap + c * aq;
-          const double qp = Q(t, p), qq = Q(t, q);
-          Q(t, p) = c * qp - s * qq;
-          Q(t, q) = s * qp + c * qq;
-        }
+      // columns: B = A J, Q <- Q J, one (row, pair) task per thread (each
+      // task owns the entries (i, p) and (i, q): no two tasks share one)
+      for (int task = t; task < K * nrot; task += blockDim.x) {
+        const int i = task % K, m = task / K;
+        const int p = rp[m], q = rq[m];
+        if (q >= K || rt[m] == 0.0) continue;
+        const double c = rc[m], s = rs[m];
+        const double ap = A(i, p), aq = A(i, q);
+        A(i, p) = c * ap - s * aq;
+        A(i, q) = s * ap + c * aq;
+        const double qp = Q(i, p), qq = Q(i, q);
+        Q(i, p) = c * qp - s * qq;
+        Q(i, q) = s * qp + c * qq;
+      }
       __syncthreads();
-      // rows: A <- J^T B (thread per column)
-      if (t < K)
-        for (int m = 0; m < nrot; ++m) {
-          const int p = rp[m], q = rq[m];
-          if (q >= K || rt[m] == 0.0) continue;
-          const double c = rc[m], s = rs[m];
-          const double bp = A(p, t), bq = A(q, t);
-          A(p, t) = c * bp - s * bq;
-          A(q, t) = s * bp + c * bq;
-        }
+      // rows: A <- J^T B, one (column, pair) task per thread
+      for (int task = t; task < K * nrot; task += blockDim.x) {
+        const int j = task % K, m = task / K;
+        const int p = rp[m], q = rq[m];
+        if (q >= K || rt[m] == 0.0) continue;
+        const double c = rc[m], s = rs[m];
+        const double bp = A(p, j), bq = A(q, j);
+        A(p, j) = c * bp - s * bq;
+        A(q, j) = s * bp + c * bq;
+      }
       __syncthreads();
       // exact symmetry (the lower triangle mirrors the upper) and the closed
       // form of each rotated 2 x 2 block
@@ -344,7 +347,7 @@ cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype,
     if (e != cudaSuccess) return e;
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
-  k_ls_solve<<<1, KMAX_LIMIT, smem, st>>>(partial, LS_BLOCKS, K, w, rcond, coef, coeff_out, scal,
+  k_ls_solve<<<1, LS_SOLVE_THREADS, smem, st>>>(partial, LS_BLOCKS, K, w, rcond, coef, coeff_out, scal,
                                           status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_update<<<UPD_BLOCKS, 256, 0, st>>>(v, f, R, io_dtype, K, n, alpha, coef, rho_inout,
@@ -430,7 +433,7 @@ cudaError_t launch_ls_static(const void* R, const void* v, const void* f, int io
   k_gram<<<LS_BLOCKS, 256, 0, st>>>(f, R, io_dtype, K, n, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = 2 * (size_t)K * (K + 1) * sizeof(double);   // <= 4352 bytes for K <= 16
-  k_ls_solve<<<1, KMAX_LIMIT, smem, st>>>(partial, LS_BLOCKS, K, w, rcond, coef, coeff_out, scal,
+  k_ls_solve<<<1, LS_SOLVE_THREADS, smem, st>>>(partial, LS_BLOCKS, K, w, rcond, coef, coeff_out, scal,
                                           status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_update<<<UPD_BLOCKS, 256, 0, st>>>(v, f, R, io_dtype, K, n, alpha, coef, rho_inout, upd);

@@ -368,6 +368,38 @@ def test_apply_step(lib, cfg1, prec):
     assert rel_err(rho.double().cpu().numpy(), want["rho_new"]) < tol
 
 
+@pytest.mark.parametrize("K", [1, 2, 3, 7, 16, 33, 64])
+def test_apply_solver_odd_and_large_k(lib, K):
+    """The K x K solve (parallel Jacobi rounds: an odd K pairs one index with
+    a dummy each round) on seeded derivatives whose singular values spread
+    over four decades, against the oracle's LS step and numpy's lstsq, FP64."""
+    cfg = _ragged(cfg_id=22, n=(12, 10, 14), ns=70, K=64, ne=50)
+    from gpu_helpers import make_context
+    ctx, _ = make_context([cfg], "fp64", torch.float64)
+    rng = workloads.rng_for(22, 40 + K)
+    ng = int(np.prod(cfg["n"]))
+    w = float(np.prod(cfg["h"]))
+    Fm = rng.standard_normal((K, ng)) * np.logspace(0, -4, K)[:, None]
+    Vm = rng.standard_normal((K, ng))
+    R = rng.standard_normal(ng)
+    rho = 1.0 + 0.1 * rng.random(ng)
+    dev = lambda x: torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+    rho_d = dev(rho[None, :])
+    coef, srel = ctx.apply(0, dev(R[None, :]), dev(Vm), dev(Fm), 0.5, rho=rho_d)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    want = oracle.lrdm_apply(R[None, :], Vm, Fm, w, 0.5, rho=rho[None, :])
+    a_ls = np.linalg.lstsq(np.sqrt(w) * Fm.T, np.sqrt(w) * R, rcond=None)[0]
+    a = coef.cpu().numpy()
+    print(f"K = {K}: coefficient error vs oracle {rel_err(a, want['a']):.2e}, vs lstsq "
+          f"{rel_err(a, a_ls):.2e}")
+    # cond(S) = 1e8: the coefficients carry cond(S) times the rounding of S
+    assert rel_err(a, want["a"]) < 1e-7
+    assert rel_err(a, a_ls) < 1e-7
+    assert abs(srel.item() - want["s_rel"]) < 1e-10
+    assert rel_err(rho_d.cpu().numpy(), want["rho_new"]) < 1e-10
+
+
 def test_apply_singular_flag_and_nonfinite(lib, cfg1):
     ctx, V, _, _ = _run([cfg1], "fp64")
     Fh = oracle.gateaux(oracle_system(cfg1), cfg1["V"])["F"]
