@@ -55,6 +55,8 @@ TF32 = {
     "pair_response_tiles:f": 4e-4,                        # [1.19e-4]
     "pair_response_tiles:X": 9e-4,                        # [2.88e-4] (drho)
     "pair_response_split_and_batch:f": 1.5e-3,            # [4.74e-4]
+    "sampled_rows_96cube:f": 1.5e-5,                      # [5.00e-6] (96^3 / 4096 / 16)
+    "sampled_rows_96cube:dmu": 9e-5,                      # [2.96e-5]
 }
 # until a case is measured (not expected in a committed table)
 TF32_UNMEASURED = 5e-3

@@ -6,7 +6,8 @@ checks (a) sampled entries of the projected perturbation X_k, each computed
 one by one in FP64 from its definition sum_r Psi_ri w dV_k(r) Psi_rj, with
 dV_k from the oracle's own density, xc kernel and Hartree solve; (b) the
 result f_k itself, element by element on 4096 seeded grid rows, for two of
-the 16 directions: the oracle forms the whole FP64 X_k (its projection summed
+the 16 directions, for the split-BF16x3 context and for a TF32 context on
+the same inputs: the oracle forms the whole FP64 X_k (its projection summed
 over row blocks of the grid, the sum over r that defines X_k), mu'_k, the
 subspace response L o (X_k - mu'_k I) and drho_k at the sampled rows (the
 response at a row needs only that row of Psi); and (c) properties of the
@@ -21,6 +22,7 @@ import pytest
 
 import oracle
 import workloads
+from gates import check
 
 torch = pytest.importorskip("torch")
 
@@ -46,6 +48,17 @@ def full():
     (F,), dmu = ctx.gateaux([Vd])
     torch.cuda.synchronize()
     assert ctx.status() == 0
+    # the same workload with TF32 contractions (its own context, closed after the call)
+    ctx32 = Context([dict(n=N, h=H, psi=[psi], eps=[torch.as_tensor(eps, device="cuda")],
+                          n_electrons=NE, kT=KT, g=2.0, rho_floor=1e-3, k_max=K)],
+                    prec="tf32", io_dtype=torch.float32, k_max=K)
+    (F32,), dmu32 = ctx32.gateaux([Vd])
+    torch.cuda.synchronize()
+    assert ctx32.status() == 0
+    F32 = F32.double().cpu().numpy()[:, 0]
+    dmu32 = dmu32.cpu().numpy()
+    ctx32.close()
+    del ctx32
     psi_h = psi.cpu().numpy()
     # oracle side: occupations, density (row blocks of the same per-row formula),
     # xc kernel and dV_k from the FP32 Psi values the device was given
@@ -57,7 +70,7 @@ def full():
     fx = oracle.lda_fx(rho)
     dV = np.stack([oracle.perturbation_potential([V[k, 0]], [fx], N, H)[0] for k in range(K)])
     return dict(ctx=ctx, psi=psi_h, V=V, F=F.double().cpu().numpy()[:, 0], dV=dV, mu=mu,
-                w=float(np.prod(H)), dmu=dmu.cpu().numpy(), eps=eps)
+                w=float(np.prod(H)), dmu=dmu.cpu().numpy(), eps=eps, F_tf32=F32, dmu_tf32=dmu32)
 
 
 def test_chemical_potential(full):
@@ -92,8 +105,9 @@ DIRS_CHECKED = (0, 15)
 
 
 def test_sampled_response_rows(full):
-    """f_k on 4096 seeded rows against the oracle's FP64 response (split-BF16x3
-    gate 1e-5 relative, as at the small sizes)."""
+    """f_k on 4096 seeded rows against the oracle's FP64 response: split-BF16x3
+    (gate 1e-5 relative, as at the small sizes) and TF32 (its measured-error
+    gate; the printout says whether it meets 1e-5)."""
     w = full["w"]
     psi = full["psi"]
     ng = psi.shape[0]
@@ -119,6 +133,11 @@ def test_sampled_response_rows(full):
               f"(max |err| / rms {peak:.2e}); dmu {full['dmu'][k]:.6e} vs {dmu:.6e}")
         worst = max(worst, err)
         assert abs(full["dmu"][k] - dmu) <= 1e-4 * np.max(np.abs(np.diag(X[k])))
+        got32 = full["F_tf32"][k, rows]
+        err32 = float(np.linalg.norm(got32 - f_ref) / np.linalg.norm(f_ref))
+        check("tf32", "sampled_rows_96cube", err32)
+        check("tf32", "sampled_rows_96cube",
+              abs(full["dmu_tf32"][k] - dmu) / np.max(np.abs(np.diag(X[k]))), "dmu")
     assert worst < 1e-5
 
 
