@@ -206,12 +206,11 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
  * held by every GPU that loads the library until the process exits), so
  * K is limited to 16: larger K returns LRDM_ERR_INVALID_ARG before anything is
  * enqueued.  The first call on each device looks the array's device address
- * up (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The address belongs to the device's primary
- * context: after cudaDeviceReset the library must be loaded again before
- * this entry point is used.  Every call shares the array: calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Asynchronous. */
+ * up (cudaGetSymbolAddress) with that device current.  The address belongs
+ * to the device's primary context: after cudaDeviceReset the library must be
+ * loaded again before this entry point is used.  Every call shares the
+ * array: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Asynchronous. */
 lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int io_dtype, int K,
                               long long n, double w, double alpha, double pinv_rcond,
                               void* rho_inout, double* coeff_out, double* s_rel_out,
