@@ -65,7 +65,8 @@ typedef enum lrdm_status {
   LRDM_ERR_SINGULAR = 6,         /* S rank-deficient: a = S^+ c was used     */
   LRDM_ERR_TIMEOUT = 7,          /* a bounded device wait expired            */
   LRDM_ERR_NONFINITE = 8,        /* NaN / Inf met on the device              */
-  LRDM_ERR_UNSUPPORTED = 9       /* precision / feature not available        */
+  LRDM_ERR_UNSUPPORTED = 9,      /* precision / feature not available        */
+  LRDM_ERR_COLLECTIVE = 10       /* the caller's allreduce (lrdm_rows) failed */
 } lrdm_status;
 
 /* Arithmetic of the two dense contractions (X_k and drho_k).  The Loewner
@@ -215,6 +216,56 @@ lrdm_status lrdm_apply_static(const void* R, const void* v, const void* f, int i
                               long long n, double w, double alpha, double pinv_rcond,
                               void* rho_inout, double* coeff_out, double* s_rel_out,
                               int* status_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Grid-row sharding (domain decomposition of one system over ranks).  Both
+ * contractions are sums over grid rows (X_k = sum_r Psi_r^T w dV_k(r) Psi_r)
+ * or row-local (drho_k(r) needs row r of Psi only, Eq. densityResponse), so
+ * each rank can hold a slab of Psi's rows; what couples the slabs is the
+ * Poisson solve of the directions, the sum of the slabs' X_k, and the
+ * least-squares sums over the grid (Eqs. plowrank, relativeError).
+ * ------------------------------------------------------------------------- */
+
+/* In-place sum over the ranks of `count` elements of `dtype` (lrdm_dtype) at
+ * the device address `buf`, ordered on `stream` (a cudaStream_t) after the
+ * work the library has enqueued there and before what it enqueues next;
+ * returns 0 on success.  Every rank calls it with the same count and dtype,
+ * in the same order.  A caller typically wraps an NCCL all-reduce. */
+typedef int (*lrdm_allreduce_fn)(void* user, void* buf, long long count, int dtype, void* stream);
+
+typedef struct lrdm_rows {
+  long long row_begin;          /* first grid row (flat index r) held, >= 0          */
+  long long n_rows;             /* rows held, >= 1, row_begin + n_rows <= N_g       */
+  lrdm_allreduce_fn allreduce;  /* the sum over the ranks (required)                */
+  void* user;                   /* passed to allreduce                              */
+} lrdm_rows;
+
+/* A context for one system (nsys = 1) of which this rank holds grid rows
+ * [row_begin, row_begin + n_rows): psi[c] is [n_rows][ld_psi] (those rows of
+ * Psi) and rho[c], if given, [n_rows]; every direction, derivative,
+ * residual, cotangent and density array of the calls on this context is
+ * [K][nspin][n_rows] (resp. [nspin][n_rows]) over the same rows.  All ranks
+ * create their contexts with the same system data (n, h, eps, occ, N_e, kT,
+ * g) and options, and then make the same calls in the same order: the calls
+ * are collective through `allreduce`, which each of them invokes on its
+ * stream between kernels:
+ *   lrdm_gateaux_batch -- the spin-summed directions, written into a zeroed
+ *     full-grid buffer at this rank's rows (K N_g values, so the sum is the
+ *     all-gather the replicated Poisson solve needs), and X_k per channel
+ *     (K N_s^2 values after the slab's grid reduction; tensor-core modes: the
+ *     padded K N_s,pad^2);
+ *   lrdm_apply -- the Gram, right-hand-side and ||R||^2 partial sums and the
+ *     residual partial sums behind s_rel (FP64), so every rank obtains the
+ *     same coefficients and s_rel and updates its rows of rho;
+ *   lrdm_backward -- the adjoint's projection (as X_k) and its spin-summed
+ *     Poisson input (as the directions); eps_bar and occ_bar come out equal
+ *     on every rank.
+ * The grid reduction is not split into row ranges, use_graph is ignored,
+ * and lrdm_krylov_step / lrdm_lrdma_step return LRDM_ERR_UNSUPPORTED on such
+ * a context.  A failed allreduce returns LRDM_ERR_COLLECTIVE (the stream
+ * holds the work enqueued before it). */
+lrdm_status lrdm_create_rows(lrdm_ctx** out, const lrdm_system* sys, const lrdm_rows* rows,
+                             const lrdm_options* opt, void* stream);
 
 /* Adjoint of the most recent lrdm_gateaux_batch on this context.
  *   f_bar[s]  : [K[s]][nspin][N_g] cotangents of f_out[s] (io dtype)

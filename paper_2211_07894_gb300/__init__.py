@@ -16,6 +16,7 @@ from .binding import (  # noqa: F401
     lrdm_apply,
     lrdm_backward,
     lrdm_create,
+    lrdm_create_rows,
     lrdm_default_options,
     lrdm_destroy,
     lrdm_gateaux_batch,
@@ -30,4 +31,6 @@ from .binding import (  # noqa: F401
     lrdm_profile_read,
     lrdm_status_query,
     lrdm_status_string,
+    rows_callback,
+    torch_allreduce,
 )

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "liblrdm.so")
 LRDM_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "shape", 3: "out of memory", 4: "cuda",
                 5: "mu not converged", 6: "singular", 7: "timeout", 8: "non-finite",
-                9: "unsupported"}
+                9: "unsupported", 10: "collective"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
 DTYPE_F64, DTYPE_F32 = 0, 1
 DEBUG_STALL_PROJECTION = 1      # lrdm_options.debug_flags bit (tests only)
@@ -48,6 +48,15 @@ class lrdm_options(ctypes.Structure):
                 ("fermi_T", c_int)]
 
 
+# int (*)(void* user, void* buf, long long count, int dtype, void* stream)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_void_p, ctypes.c_longlong, c_int, c_void_p)
+
+
+class lrdm_rows(ctypes.Structure):
+    _fields_ = [("row_begin", ctypes.c_longlong), ("n_rows", ctypes.c_longlong),
+                ("allreduce", ALLREDUCE_FN), ("user", c_void_p)]
+
+
 class lrdm_kpoint_system(ctypes.Structure):
     _fields_ = [("n", c_int * 3), ("h", c_double * 3), ("nk", c_int), ("ns", c_int),
                 ("ld_psi", c_int), ("psi_re", POINTER(c_void_p)), ("psi_im", POINTER(c_void_p)),
@@ -65,7 +74,7 @@ EXPORTS = ["lrdm_default_options", "lrdm_create", "lrdm_gateaux_batch", "lrdm_ap
            "lrdm_get_tuning", "lrdm_krylov_step", "lrdm_lrdma_default_params", "lrdm_lrdma_create",
            "lrdm_lrdma_step", "lrdm_lrdma_clear", "lrdm_lrdma_destroy", "lrdm_kp_create",
            "lrdm_kp_gateaux", "lrdm_lrdma_get_state", "lrdm_lrdma_export", "lrdm_lrdma_import",
-           "lrdm_kp_get_split", "lrdm_set_tuning"]
+           "lrdm_kp_get_split", "lrdm_set_tuning", "lrdm_create_rows"]
 
 
 class lrdm_lrdma_params(ctypes.Structure):
@@ -95,6 +104,9 @@ def load(path: Optional[str] = None):
     lib.lrdm_create.argtypes = [POINTER(c_void_p), POINTER(lrdm_system), c_int,
                                 POINTER(lrdm_options), c_void_p]
     lib.lrdm_create.restype = c_int
+    lib.lrdm_create_rows.argtypes = [POINTER(c_void_p), POINTER(lrdm_system), POINTER(lrdm_rows),
+                                     POINTER(lrdm_options), c_void_p]
+    lib.lrdm_create_rows.restype = c_int
     lib.lrdm_gateaux_batch.argtypes = [c_void_p, POINTER(c_void_p), POINTER(c_int),
                                        POINTER(c_void_p), c_void_p, c_void_p]
     lib.lrdm_gateaux_batch.restype = c_int
@@ -193,6 +205,54 @@ def lrdm_create(systems: Sequence[lrdm_system], options: lrdm_options, stream: i
     code = load().lrdm_create(ctypes.byref(h), arr, len(systems), ctypes.byref(options),
                               c_void_p(stream))
     return code, h
+
+
+def lrdm_create_rows(system: lrdm_system, rows: lrdm_rows, options: lrdm_options, stream: int = 0):
+    h = c_void_p()
+    code = load().lrdm_create_rows(ctypes.byref(h), ctypes.byref(system), ctypes.byref(rows),
+                                   ctypes.byref(options), c_void_p(stream))
+    return code, h
+
+
+class _DeviceArray:
+    """A device buffer of the library seen by torch (zero copy)."""
+
+    def __init__(self, ptr, count, dtype):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": (int(count),),
+                                         "typestr": "<f8" if dtype == DTYPE_F64 else "<f4",
+                                         "version": 3, "strides": None}
+
+
+def rows_callback(fn):
+    """The C callback of a row-sharded context around fn(tensor, stream):
+    tensor is the library's buffer as a 1-D torch tensor (summed in place over
+    the ranks by fn), stream the torch stream the library enqueued its work on."""
+    import torch
+
+    def cb(user, buf, count, dtype, stream):
+        try:
+            t = torch.as_tensor(_DeviceArray(buf, count, dtype), device="cuda")
+            st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                fn(t, st)
+            return 0
+        except Exception as e:          # reported to the library as a failed collective
+            import sys
+            print(f"lrdm rows allreduce failed: {e!r}", file=sys.stderr)
+            return 1
+
+    return ALLREDUCE_FN(cb)
+
+
+def torch_allreduce(group=None):
+    """fn(tensor, stream) for rows_callback: an in-place sum over the ranks of
+    `group` by torch.distributed (NCCL), ordered on the library's stream."""
+    import torch.distributed as dist
+
+    def fn(t, st):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+
+    return fn
 
 
 def lrdm_gateaux_batch(ctx, v_ptrs, K, f_ptrs, dmu_ptr, stream: int = 0) -> int:
@@ -313,11 +373,18 @@ class Context:
       rho_floor, k_max.
 
     Direction / result tensors are (K, nspin, N_g) in the io dtype.
+
+    rows = dict(row_begin, n_rows, allreduce) makes a grid-row-sharded
+    context (lrdm_create_rows) of the one system given, whose psi (and rho)
+    hold those grid rows only; every row-wise tensor is then (.., n_rows).
+    allreduce(tensor, stream) sums the library's buffer in place over the
+    ranks (torch_allreduce(group) for torch.distributed); all ranks make the
+    same calls in the same order.
     """
 
     def __init__(self, systems, prec="bf16x3", io_dtype=None, k_max=16, pinv_rcond=1e-12,
                  degen_tol=1e-5, poisson="spectral", use_graph=False, stream=None, fermi_T=0,
-                 autotune=False, debug_flags=0):
+                 autotune=False, debug_flags=0, rows=None):
         import torch
         self.torch = torch
         self.io_dtype = io_dtype or torch.float32
@@ -369,13 +436,22 @@ class Context:
             s.rho_floor = float(d.get("rho_floor", 0.0))
             s.k_max = int(d.get("k_max", 0))
             cs.append(s)
-            self.meta.append(dict(nspin=nspin, Ng=int(np.prod(d["n"])),
-                                  ns=[int(p.shape[1]) for p in d["psi"]],
+            ng = int(rows["n_rows"]) if rows is not None else int(np.prod(d["n"]))
+            self.meta.append(dict(nspin=nspin, Ng=ng, ns=[int(p.shape[1]) for p in d["psi"]],
                                   k_max=int(d.get("k_max", 0)) or int(k_max)))
         self.nsys = len(self.meta)
         st = self._stream(stream)
-        code, h = lrdm_create(cs, o, st)
-        _check("lrdm_create", code)
+        if rows is not None:
+            # one system whose grid rows [row_begin, row_begin + n_rows) this
+            # rank holds; rows["allreduce"] is fn(tensor, stream) (rows_callback)
+            assert len(cs) == 1
+            self._rows_cb = rows_callback(rows["allreduce"])
+            r = lrdm_rows(int(rows["row_begin"]), int(rows["n_rows"]), self._rows_cb, None)
+            code, h = lrdm_create_rows(cs[0], r, o, st)
+            _check("lrdm_create_rows", code)
+        else:
+            code, h = lrdm_create(cs, o, st)
+            _check("lrdm_create", code)
         self.handle = h
         del keep
 

@@ -71,10 +71,10 @@ __device__ __forceinline__ int quad_count(long long len, long long r0) {
   return n <= 0 ? 0 : (n >= 4 ? 4 : (int)n);
 }
 
-// out[k][r] = sum_s v[k][s][r]
+// out[k * ostride + r] = sum_s v[k][s][r]
 template <typename Ti, typename C>
 __global__ void k_spin_sum(const Ti* __restrict__ v, int K, int nspin, long long Ng,
-                           C* __restrict__ out, int vec) {
+                           C* __restrict__ out, long long ostride, int vec) {
   const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
   const int n = quad_count(Ng, r0);
   if (n == 0) return;
@@ -86,7 +86,7 @@ __global__ void k_spin_sum(const Ti* __restrict__ v, int K, int nspin, long long
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[e] += (C)x[e];
     }
-    st4(out + (long long)k * Ng + r0, n, vec, acc);
+    st4(out + (long long)k * ostride + r0, n, vec, acc);
   }
 }
 
@@ -152,7 +152,7 @@ template <typename Ti, typename C>
 __global__ void k_dv_weights(const Ti* __restrict__ v, const C* __restrict__ VH,
                              const double* __restrict__ fx0, const double* __restrict__ fx1, int K,
                              int nspin, long long Ng, long long Ng_pad, C scale,
-                             C* __restrict__ a, int vec) {
+                             C* __restrict__ a, long long vstride, int vec) {
   const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
   const int n_out = quad_count(Ng_pad, r0);
   if (n_out == 0) return;
@@ -166,7 +166,7 @@ __global__ void k_dv_weights(const Ti* __restrict__ v, const C* __restrict__ VH,
   }
   for (int k = 0; k < K; ++k) {
     C vh[4];
-    ld4(VH + (long long)k * Ng + r0, n, vec, vh);
+    ld4(VH + (long long)k * vstride + r0, n, vec, vh);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       if (s >= nspin) break;
@@ -186,7 +186,8 @@ template <typename Ti, typename C>
 __global__ void k_adjoint_potential(const C* __restrict__ dvbar, const C* __restrict__ VH,
                                     const double* __restrict__ fx0, const double* __restrict__ fx1,
                                     const Ti* __restrict__ fbar, int K, int nspin, long long Ng,
-                                    long long Ng_pad, Ti* __restrict__ vbar, int vec) {
+                                    long long Ng_pad, Ti* __restrict__ vbar, long long vstride,
+                                    int vec) {
   const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
   const int n = quad_count(Ng, r0);
   if (n == 0) return;
@@ -199,7 +200,7 @@ __global__ void k_adjoint_potential(const C* __restrict__ dvbar, const C* __rest
   }
   for (int k = 0; k < K; ++k) {
     C vh[4];
-    ld4(VH + (long long)k * Ng + r0, n, vec, vh);
+    ld4(VH + (long long)k * vstride + r0, n, vec, vh);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       if (s >= nspin) break;
@@ -218,7 +219,7 @@ __global__ void k_adjoint_potential(const C* __restrict__ dvbar, const C* __rest
 // spin sum of the (padded) adjoint potential for the Hartree transform
 template <typename C>
 __global__ void k_spin_sum_padded(const C* __restrict__ d, int K, int nspin, long long Ng,
-                                  long long Ng_pad, C* __restrict__ out, int vec) {
+                                  long long Ng_pad, C* __restrict__ out, long long ostride, int vec) {
   const long long r0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
   const int n = quad_count(Ng, r0);
   if (n == 0) return;
@@ -230,7 +231,7 @@ __global__ void k_spin_sum_padded(const C* __restrict__ d, int K, int nspin, lon
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[e] += x[e];
     }
-    st4(out + (long long)k * Ng + r0, n, vec, acc);
+    st4(out + (long long)k * ostride + r0, n, vec, acc);
   }
 }
 
@@ -639,12 +640,13 @@ inline bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) =
   } while (0)
 
 cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long long Ng,
-                            void* fft_real, int fp64, cudaStream_t st) {
+                            void* fft_real, int fp64, cudaStream_t st, long long out_stride) {
   if (K == 0 || Ng == 0) return cudaSuccess;
-  const int vec = Ng % 4 == 0 && al16(v) && al16(fft_real);
+  const int vec = Ng % 4 == 0 && out_stride % 4 == 0 && al16(v) && al16(fft_real);
   IO_C_DISPATCH(io_dtype, fp64,
                 (k_spin_sum<Ti, C><<<quad_grid(Ng), 256, 0, st>>>(
-                    static_cast<const Ti*>(v), K, nspin, Ng, static_cast<C*>(fft_real), vec)));
+                    static_cast<const Ti*>(v), K, nspin, Ng, static_cast<C*>(fft_real), out_stride,
+                    vec)));
   return cudaGetLastError();
 }
 
@@ -664,41 +666,45 @@ cudaError_t launch_poisson_symbol(void* cplx, int K, long long per, const double
 
 cudaError_t launch_dv_weights(const void* v, int io_dtype, const void* VH, const double* fx0,
                               const double* fx1, int K, int nspin, long long Ng, long long Ng_pad,
-                              double scale, void* a, int fp64, cudaStream_t st) {
+                              double scale, void* a, int fp64, cudaStream_t st, long long vh_stride) {
   if (K == 0 || Ng_pad == 0) return cudaSuccess;
-  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && al16(v) && al16(VH) && al16(a);
+  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && vh_stride % 4 == 0 && al16(v) && al16(VH) &&
+                  al16(a);
   IO_C_DISPATCH(io_dtype, fp64,
                 (k_dv_weights<Ti, C><<<quad_grid(Ng_pad), 256, 0, st>>>(
                     static_cast<const Ti*>(v), static_cast<const C*>(VH), fx0, fx1, K, nspin, Ng,
-                    Ng_pad, (C)scale, static_cast<C*>(a), vec)));
+                    Ng_pad, (C)scale, static_cast<C*>(a), vh_stride, vec)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_potential(const void* dvbar, const void* VH, const double* fx0,
                                      const double* fx1, const void* fbar, int io_dtype, int K,
                                      int nspin, long long Ng, long long Ng_pad, void* vbar,
-                                     int fp64, cudaStream_t st) {
+                                     int fp64, cudaStream_t st, long long vh_stride) {
   if (K == 0 || Ng == 0) return cudaSuccess;
-  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && al16(dvbar) && al16(VH) && al16(fbar) &&
-                  al16(vbar);
+  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && vh_stride % 4 == 0 && al16(dvbar) && al16(VH) &&
+                  al16(fbar) && al16(vbar);
   IO_C_DISPATCH(io_dtype, fp64,
                 (k_adjoint_potential<Ti, C><<<quad_grid(Ng), 256, 0, st>>>(
                     static_cast<const C*>(dvbar), static_cast<const C*>(VH), fx0, fx1,
                     static_cast<const Ti*>(fbar), K, nspin, Ng, Ng_pad, static_cast<Ti*>(vbar),
-                    vec)));
+                    vh_stride, vec)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_spin_sum_padded(const void* d, int K, int nspin, long long Ng,
-                                   long long Ng_pad, void* out, int fp64, cudaStream_t st) {
+                                   long long Ng_pad, void* out, int fp64, cudaStream_t st,
+                                   long long out_stride) {
   if (K == 0 || Ng == 0) return cudaSuccess;
-  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && al16(d) && al16(out);
+  const int vec = Ng % 4 == 0 && Ng_pad % 4 == 0 && out_stride % 4 == 0 && al16(d) && al16(out);
   if (fp64)
     k_spin_sum_padded<double><<<quad_grid(Ng), 256, 0, st>>>(
-        static_cast<const double*>(d), K, nspin, Ng, Ng_pad, static_cast<double*>(out), vec);
+        static_cast<const double*>(d), K, nspin, Ng, Ng_pad, static_cast<double*>(out), out_stride,
+        vec);
   else
     k_spin_sum_padded<float><<<quad_grid(Ng), 256, 0, st>>>(
-        static_cast<const float*>(d), K, nspin, Ng, Ng_pad, static_cast<float*>(out), vec);
+        static_cast<const float*>(d), K, nspin, Ng, Ng_pad, static_cast<float*>(out), out_stride,
+        vec);
   return cudaGetLastError();
 }
 

@@ -329,10 +329,18 @@ __global__ void k_srel(const double* __restrict__ upd_partial, int nblk, double 
 cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype, int K,
                       long long n, double w, double alpha, double rcond, void* rho_inout,
                       double* coef, double* coeff_out, double* s_rel_out, double* partial,
-                      double* scal, double* upd_partial, int* status, cudaStream_t st) {
+                      double* scal, double* upd_partial, int* status, cudaStream_t st,
+                      const AllReduce* ar, int* ar_failed) {
   k_gram<<<LS_BLOCKS, 256, 0, st>>>(f, R, io_dtype, K, n, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const int nval = K * (K + 1) / 2 + K + 1;
+  // grid-row sharding: each rank's per-block sums, summed over the ranks
+  // block by block, so that every rank reduces the same values in the same order
+  if (ar && ar->fn && ar->fn(ar->user, partial, (long long)LS_BLOCKS * nval, LRDM_DTYPE_F64, st) != 0) {
+    if (ar_failed) *ar_failed = 1;
+    return cudaSuccess;
+  }
   const size_t smem = 2 * (size_t)K * (K + 1) * sizeof(double);
   // the shared-memory limit is a per-device function attribute: one bit per
   // device ordinal records that it was raised (a racing first call from
@@ -353,6 +361,10 @@ cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype,
   k_update<<<UPD_BLOCKS, 256, 0, st>>>(v, f, R, io_dtype, K, n, alpha, coef, rho_inout,
                                        upd_partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ar && ar->fn && ar->fn(ar->user, upd_partial, (long long)UPD_BLOCKS, LRDM_DTYPE_F64, st) != 0) {
+    if (ar_failed) *ar_failed = 1;
+    return cudaSuccess;
+  }
   k_srel<<<1, 256, 0, st>>>(upd_partial, UPD_BLOCKS, w, scal, s_rel_out);
   return cudaGetLastError();
 }

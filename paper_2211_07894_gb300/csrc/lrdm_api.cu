@@ -119,13 +119,13 @@ lrdm_status setup_poisson(lrdm_ctx* ctx, SysState& S, cudaStream_t st) {
   const int fp64 = o.prec == LRDM_FP64;
   const size_t csz = fp64 ? sizeof(double) : sizeof(float);
   const long long nc = (long long)S.n[0] * S.n[1] * (S.n[2] / 2 + 1);
-  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_real), (size_t)S.kmax * S.Ng * csz));
+  LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_real), (size_t)S.kmax * S.Ngrid * csz));
   LRDM_CK(dalloc(ctx, reinterpret_cast<char**>(&S.fft_cplx), (size_t)S.kmax * nc * 2 * csz));
   int nn[3] = {S.n[0], S.n[1], S.n[2]};
-  LRDM_FFT(cufftPlanMany(&S.plan_r2c, 3, nn, nullptr, 1, (int)S.Ng, nullptr, 1, (int)nc,
+  LRDM_FFT(cufftPlanMany(&S.plan_r2c, 3, nn, nullptr, 1, (int)S.Ngrid, nullptr, 1, (int)nc,
                          fp64 ? CUFFT_D2Z : CUFFT_R2C, S.kmax));
   S.plans = true;
-  LRDM_FFT(cufftPlanMany(&S.plan_c2r, 3, nn, nullptr, 1, (int)nc, nullptr, 1, (int)S.Ng,
+  LRDM_FFT(cufftPlanMany(&S.plan_c2r, 3, nn, nullptr, 1, (int)nc, nullptr, 1, (int)S.Ngrid,
                          fp64 ? CUFFT_Z2D : CUFFT_C2R, S.kmax));
   LRDM_CK(dalloc(ctx, &S.sym, (size_t)nc, false));
   LRDM_CU(launch_poisson_table(S.n, S.h, o.poisson_symbol, S.sym, st));
@@ -142,7 +142,11 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
     S.n[d] = in.n[d];
     S.h[d] = in.h[d];
   }
-  S.Ng = (long long)in.n[0] * in.n[1] * in.n[2];
+  S.Ngrid = (long long)in.n[0] * in.n[1] * in.n[2];
+  // a row-sharded context holds rows [r0, r0 + Ng) of the grid; every
+  // row-wise array (Psi copies, rho, f_x, weights, directions) has Ng rows
+  S.Ng = ctx->rows ? ctx->rows_n : S.Ngrid;
+  S.r0 = ctx->rows ? ctx->rows_begin : 0;
   S.Ng_pad = is_tc(prec) ? (S.Ng + TC_PAD_GRID - 1) / TC_PAD_GRID * TC_PAD_GRID : S.Ng;
   S.nspin = in.nspin;
   S.kmax = in.k_max > 0 ? in.k_max : o.k_max;
@@ -237,7 +241,8 @@ lrdm_status setup_system(lrdm_ctx* ctx, int idx, const lrdm_system& in, cudaStre
     long long maxsplit = S.Ng / 256 > 0 ? S.Ng / 256 : 1;
     if (want > maxsplit) want = maxsplit;
     if (want > 64) want = 64;
-    S.nsplit = (int)(want < 1 ? 1 : want);
+    // row-sharded: one partial X per rank, summed over the ranks as it is
+    S.nsplit = ctx->rows ? 1 : (int)(want < 1 ? 1 : want);
   } else {
     S.nsplit = 1;
   }
@@ -377,7 +382,7 @@ lrdm_status tc_group(lrdm_ctx* ctx, int gemm, int out_is_io, cudaStream_t st) {
 // (1360 items, 0.994 of 9 waves, against 0.895 for 1-4 ranges).
 int choose_split(lrdm_ctx* ctx, int s, int K) {
   const SysState& S = ctx->sys[s];
-  if (!is_tc(ctx->opt.prec) || K <= 0 || ctx->tc_pid.empty()) return 1;
+  if (!is_tc(ctx->opt.prec) || K <= 0 || ctx->tc_pid.empty() || ctx->rows) return 1;
   const TcProblem& pr = ctx->tc_host[ctx->tc_pid[2 * s]];
   const bool pair = ctx->tune.g1_nb == G1_PAIR;
   const bool wide = ctx->tune.g1_nb == 256;
@@ -572,6 +577,42 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
 // The forward path of all systems: potentials and weights per system, then
 // one projection contraction over every (system, channel), mu' and the
 // Loewner scaling, then one response contraction over every (system, channel).
+// The caller's sum over the ranks of a row-sharded context (a no-op otherwise).
+lrdm_status allreduce(lrdm_ctx* ctx, void* buf, long long count, int dtype, cudaStream_t st) {
+  if (!ctx->rows || count == 0) return LRDM_OK;
+  return ctx->ar.fn(ctx->ar.user, buf, count, dtype, st) == 0 ? LRDM_OK : LRDM_ERR_COLLECTIVE;
+}
+
+// The K full-grid Poisson inputs of system S: `write(at, stride)` writes this
+// context's rows of field k at at + k * stride.  A row-sharded context writes
+// its rows into the zeroed full-grid buffer and sums it over the ranks.
+template <typename W>
+lrdm_status gather_fields(lrdm_ctx* ctx, SysState& S, int K, cudaStream_t st, W&& write) {
+  const int fp64 = ctx->opt.prec == LRDM_FP64;
+  const size_t csz = fp64 ? sizeof(double) : sizeof(float);
+  if (ctx->rows) LRDM_CU(cudaMemsetAsync(S.fft_real, 0, (size_t)K * S.Ngrid * csz, st));
+  LRDM_CU(write(static_cast<char*>(S.fft_real) + S.r0 * csz, S.Ngrid));
+  return allreduce(ctx, S.fft_real, (long long)K * S.Ngrid, fp64 ? LRDM_DTYPE_F64 : LRDM_DTYPE_F32, st);
+}
+
+// Row-sharded context: the projections of the slabs (X, or Gbar in the
+// adjoint) summed over the ranks; the buffers hold nsplit = 1 partials.
+lrdm_status reduce_projections(lrdm_ctx* ctx, const int* K, bool adjoint, cudaStream_t st) {
+  if (!ctx->rows) return LRDM_OK;
+  const int fp64 = ctx->opt.prec == LRDM_FP64;
+  for (int s = 0; s < ctx->nsys; ++s) {
+    SysState& S = ctx->sys[s];
+    if (K[s] == 0) continue;
+    for (int c = 0; c < S.nspin; ++c) {
+      const long long ld = is_tc(ctx->opt.prec) ? S.ch[c].ns_pad : S.ch[c].ns;
+      void* buf = adjoint ? S.ch[c].Gpart : S.ch[c].Xpart;
+      LRDM_CK(allreduce(ctx, buf, (long long)S.nsplit * K[s] * ld * ld,
+                        fp64 ? LRDM_DTYPE_F64 : LRDM_DTYPE_F32, st));
+    }
+  }
+  return LRDM_OK;
+}
+
 lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void* const* f,
                         double* dmu_out, cudaStream_t st) {
   const int prec = ctx->opt.prec;
@@ -579,14 +620,18 @@ lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void*
   const int io = ctx->opt.io_dtype;
   const size_t isz = io_size(io);
   const bool tc = is_tc(prec);
+  const size_t csz = fp64 ? sizeof(double) : sizeof(float);
   for (int s = 0; s < ctx->nsys; ++s) {
     SysState& S = ctx->sys[s];
     S.last_K = K[s];
     if (K[s] == 0) continue;
-    LRDM_CU(launch_spin_sum(v[s], io, K[s], S.nspin, S.Ng, S.fft_real, fp64, st));
+    LRDM_CK(gather_fields(ctx, S, K[s], st, [&](void* at, long long stride) {
+      return launch_spin_sum(v[s], io, K[s], S.nspin, S.Ng, at, fp64, st, stride);
+    }));
     LRDM_CK(hartree(ctx, S, K[s], st));
-    LRDM_CU(launch_dv_weights(v[s], io, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, K[s], S.nspin,
-                              S.Ng, S.Ng_pad, S.w, S.a, fp64, st));
+    LRDM_CU(launch_dv_weights(v[s], io, static_cast<char*>(S.fft_real) + S.r0 * csz, S.ch[0].fx,
+                              S.ch[S.nspin - 1].fx, K[s], S.nspin, S.Ng, S.Ng_pad, S.w, S.a, fp64, st,
+                              S.Ngrid));
     count(ctx, 3);
   }
   // projection X_k = Psi^T diag(w dV_k) Psi
@@ -607,6 +652,7 @@ lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void*
       for (int c = 0; c < ctx->sys[s].nspin && K[s] > 0; ++c)
         LRDM_CK(gemm1_simt(ctx, ctx->sys[s], c, K[s], ctx->sys[s].ch[c].Xpart, st));
   }
+  LRDM_CK(reduce_projections(ctx, K, false, st));
   // mu' and the Loewner scaling
   int off = 0;
   for (int s = 0; s < ctx->nsys; ++s) {
@@ -649,7 +695,7 @@ lrdm_status forward_all(lrdm_ctx* ctx, const void* const* v, const int* K, void*
 // (buffers, K's, stream), replayed afterwards.  Not used on the legacy
 // default stream or while profiling.
 bool use_graph(const lrdm_ctx* ctx, cudaStream_t st) {
-  return ctx->opt.use_graph && st != nullptr && !ctx->prof_on;
+  return ctx->opt.use_graph && st != nullptr && !ctx->prof_on && !ctx->rows;
 }
 
 // One forward call of the direction drivers (Krylov step, LRDMA): system sys
@@ -714,9 +760,9 @@ const char* lrdm_status_string(lrdm_status s) {
   return "unknown status";
 }
 
-lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
-                        const lrdm_options* opt, void* stream) {
-  NvtxRange nvtx_("lrdm_create");
+namespace {
+lrdm_status create_ctx(lrdm_ctx** out, const lrdm_system* sys, int nsys, const lrdm_options* opt,
+                       void* stream, const lrdm_rows* rows) {
   if (!out) return LRDM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!sys || nsys < 1) return LRDM_ERR_INVALID_ARG;
@@ -740,6 +786,13 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
   if (!ctx) return LRDM_ERR_OOM;
   ctx->nsys = nsys;
   ctx->opt = o;
+  if (rows) {
+    ctx->rows = true;
+    ctx->rows_begin = rows->row_begin;
+    ctx->rows_n = rows->n_rows;
+    ctx->ar.fn = rows->allreduce;
+    ctx->ar.user = rows->user;
+  }
   cudaGetDevice(&ctx->device);
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
   ctx->sys = new (std::nothrow) SysState[nsys];
@@ -817,6 +870,25 @@ lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
   *out = ctx;
   return LRDM_OK;
 }
+}  // namespace
+
+lrdm_status lrdm_create(lrdm_ctx** out, const lrdm_system* sys, int nsys,
+                        const lrdm_options* opt, void* stream) {
+  NvtxRange nvtx_("lrdm_create");
+  return create_ctx(out, sys, nsys, opt, stream, nullptr);
+}
+
+lrdm_status lrdm_create_rows(lrdm_ctx** out, const lrdm_system* sys, const lrdm_rows* rows,
+                             const lrdm_options* opt, void* stream) {
+  NvtxRange nvtx_("lrdm_create_rows");
+  if (!out) return LRDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!sys || !rows || !rows->allreduce) return LRDM_ERR_INVALID_ARG;
+  const long long ng = (long long)sys->n[0] * sys->n[1] * sys->n[2];
+  if (rows->row_begin < 0 || rows->n_rows < 1 || rows->row_begin + rows->n_rows > ng)
+    return LRDM_ERR_SHAPE;
+  return create_ctx(out, sys, 1, opt, stream, rows);
+}
 
 lrdm_status lrdm_gateaux_batch(lrdm_ctx* ctx, const void* const* v, const int* K,
                                void* const* f_out, double* dmu_out, void* stream) {
@@ -854,10 +926,13 @@ lrdm_status lrdm_apply(lrdm_ctx* ctx, int sys, const void* R, const void* v, con
   SysState& S = ctx->sys[sys];
   long long n = (long long)S.nspin * S.Ng;
   count(ctx, 4);
-  return from_cuda(launch_ls(R, v, f, ctx->opt.io_dtype, K, n, S.w, alpha, ctx->opt.pinv_rcond,
-                             rho_inout, ctx->ls_coef, coeff_out, s_rel_out, ctx->ls_partial,
-                             ctx->ls_scal, ctx->upd_partial, ctx->d_status,
-                             static_cast<cudaStream_t>(stream)));
+  int ar_failed = 0;
+  const lrdm_status rc = from_cuda(launch_ls(R, v, f, ctx->opt.io_dtype, K, n, S.w, alpha,
+                                             ctx->opt.pinv_rcond, rho_inout, ctx->ls_coef, coeff_out,
+                                             s_rel_out, ctx->ls_partial, ctx->ls_scal, ctx->upd_partial,
+                                             ctx->d_status, static_cast<cudaStream_t>(stream),
+                                             ctx->rows ? &ctx->ar : nullptr, &ar_failed));
+  return ar_failed ? LRDM_ERR_COLLECTIVE : rc;
 }
 
 lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol, int r_max,
@@ -865,6 +940,7 @@ lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol
                              double* s_rel_out, int* rank_out, double* r_norm_out, void* stream) {
   NvtxRange nvtx_("lrdm_krylov_step");
   if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !U || !T) return LRDM_ERR_INVALID_ARG;
+  if (ctx->rows) return LRDM_ERR_UNSUPPORTED;
   if (r_max < 1 || r_max > KMAX_LIMIT || !(s_tol >= 0.0) || !isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SysState& S = ctx->sys[sys];
@@ -975,6 +1051,11 @@ lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* 
       for (int c = 0; c < ctx->sys[s].nspin && ctx->sys[s].last_K > 0; ++c)
         LRDM_CK(gemm1_simt(ctx, ctx->sys[s], c, ctx->sys[s].last_K, ctx->sys[s].ch[c].Gpart, st));
   }
+  if (ctx->rows) {
+    std::vector<int> Ks(ctx->nsys);
+    for (int s = 0; s < ctx->nsys; ++s) Ks[s] = ctx->sys[s].last_K;
+    LRDM_CK(reduce_projections(ctx, Ks.data(), true, st));
+  }
   // Ybar = L o Gbar - diag(L) T / sum L;  dVbar = w diag(Psi Ybar Psi^T) into S.a
   if (tc) ctx->tc_entries.clear();
   for (int s = 0; s < ctx->nsys; ++s) {
@@ -1007,10 +1088,13 @@ lrdm_status lrdm_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* 
     const int K = S.last_K;
     const double inv_tr = ctx->inv_trace[s];
     if (K > 0) {
-      LRDM_CU(launch_spin_sum_padded(S.a, K, S.nspin, S.Ng, S.Ng_pad, S.fft_real, fp64, st));
+      LRDM_CK(gather_fields(ctx, S, K, st, [&](void* at, long long stride) {
+        return launch_spin_sum_padded(S.a, K, S.nspin, S.Ng, S.Ng_pad, at, fp64, st, stride);
+      }));
       LRDM_CK(hartree(ctx, S, K, st));
-      LRDM_CU(launch_adjoint_potential(S.a, S.fft_real, S.ch[0].fx, S.ch[S.nspin - 1].fx, f_bar[s],
-                                       io, K, S.nspin, S.Ng, S.Ng_pad, v_bar[s], fp64, st));
+      LRDM_CU(launch_adjoint_potential(S.a, static_cast<char*>(S.fft_real) + S.r0 * csz, S.ch[0].fx,
+                                       S.ch[S.nspin - 1].fx, f_bar[s], io, K, S.nspin, S.Ng,
+                                       S.Ng_pad, v_bar[s], fp64, st, S.Ngrid));
       count(ctx, 3);
     }
     for (int c = 0; c < S.nspin; ++c) {

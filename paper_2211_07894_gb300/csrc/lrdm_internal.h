@@ -97,7 +97,9 @@ struct Channel {
 struct SysState {
   int n[3] = {0, 0, 0};
   double h[3] = {0, 0, 0};
-  long long Ng = 0;
+  long long Ng = 0;                  // grid rows held (all N_g, or one slab of a row-sharded grid)
+  long long Ngrid = 0;               // points of the full grid (the Poisson solve's size)
+  long long r0 = 0;                  // first row held
   long long Ng_pad = 0;
   int nspin = 1;
   int kmax = 0;
@@ -111,13 +113,19 @@ struct SysState {
   // Poisson
   cufftHandle plan_r2c = 0, plan_c2r = 0;
   bool plans = false;
-  void* fft_real = nullptr;          // [kmax][Ng] compute type
+  void* fft_real = nullptr;          // [kmax][Ngrid] compute type
   void* fft_cplx = nullptr;          // [kmax][n0][n1][n2/2+1]
   double* sym = nullptr;             // [n0][n1][n2/2+1] Poisson symbol / N_g
   void* a = nullptr;                 // [kmax][nspin][Ng_pad] GEMM1 weights (compute type)
   double* dmu = nullptr;             // [kmax]
   double* tbar = nullptr;            // [kmax] backward trace terms
   int last_K = -1;                   // K of the most recent forward call
+};
+
+// The caller's sum over the ranks of a grid-row-sharded system.
+struct AllReduce {
+  lrdm_allreduce_fn fn = nullptr;
+  void* user = nullptr;
 };
 
 }  // namespace lrdm
@@ -145,6 +153,11 @@ struct lrdm_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key;
   lrdm::TcTune tune;                 // launch shape of the tensor-core contractions
+  // grid-row sharding (lrdm_create_rows): the rows this context holds and the
+  // caller's sum over the ranks
+  bool rows = false;
+  long long rows_begin = 0, rows_n = 0;
+  lrdm::AllReduce ar;
   int sm_count = 0;
   std::vector<double> inv_trace;     // per system 1 / sum_s sum_i L_ii
   // profiling (lrdm_profile_enable / lrdm_profile_read)
@@ -237,8 +250,10 @@ cudaError_t launch_kp_sum(const KpSumArgs& A, const void* v, int io, long long n
 
 // ---------------- element-wise / reduction kernels (k_elem.cu) ----------------
 // fft_real[k][r] = sum_s v[k][s][r]  (compute type = double if fp64 else float)
+// out[k * out_stride + r] = sum_s v[k][s][r] for r < Ng (out_stride = Ng, or the
+// full grid's N_g when the rows are one slab of it)
 cudaError_t launch_spin_sum(const void* v, int io_dtype, int K, int nspin, long long Ng,
-                            void* fft_real, int fp64, cudaStream_t st);
+                            void* fft_real, int fp64, cudaStream_t st, long long out_stride);
 // sym[m] = 4 pi / |G_m|^2 / N_g on the half-complex grid (G = 0 -> 0); kind 1
 // uses the second-order finite-difference symbol (once per system)
 cudaError_t launch_poisson_table(const int* n, const double* h, int kind, double* sym,
@@ -248,13 +263,14 @@ cudaError_t launch_poisson_symbol(void* cplx, int K, long long per, const double
                                   cudaStream_t st);
 // a[k][s][r] = scale * (VH[k][r] + fx_s[r] * v[k][s][r]);  mode 1 (adjoint):
 // out[k][s][r] = VH[k][r] + fx_s[r] * dvbar[k][s][r] - fbar[k][s][r] (io dtype)
+// (VH rows k at VH + k * vh_stride)
 cudaError_t launch_dv_weights(const void* v, int io_dtype, const void* VH, const double* fx0,
                               const double* fx1, int K, int nspin, long long Ng, long long Ng_pad,
-                              double scale, void* a, int fp64, cudaStream_t st);
+                              double scale, void* a, int fp64, cudaStream_t st, long long vh_stride);
 cudaError_t launch_adjoint_potential(const void* dvbar, const void* VH, const double* fx0,
                                      const double* fx1, const void* fbar, int io_dtype, int K,
                                      int nspin, long long Ng, long long Ng_pad, void* vbar,
-                                     int fp64, cudaStream_t st);
+                                     int fp64, cudaStream_t st, long long vh_stride);
 // a[k][s][r] = scale * fbar[k][s][r]
 cudaError_t launch_scale_weights(const void* fbar, int io_dtype, int K, int nspin, long long Ng,
                                  long long Ng_pad, double scale, void* a, int fp64, cudaStream_t st);
@@ -272,7 +288,7 @@ cudaError_t launch_get_projection(const SysState& S, int s, int k, int acc_fp64,
 cudaError_t launch_trace_bar(const SysState& S, const void* const* Gparts, int K, int acc_fp64,
                              double* tbar, cudaStream_t st);
 cudaError_t launch_spin_sum_padded(const void* d, int K, int nspin, long long Ng, long long Ng_pad,
-                                   void* out, int fp64, cudaStream_t st);
+                                   void* out, int fp64, cudaStream_t st, long long out_stride);
 cudaError_t launch_eps_occ_bar(const SysState& S, int s, int K, int acc_fp64,
                                double inv_trace_L, double degen_tol, double* eps_bar,
                                double* occ_bar, cudaStream_t st);
@@ -296,10 +312,14 @@ size_t gram_schmidt_scratch();
 // norm_out[0] = ||x||_w (scratch: gram_schmidt_scratch() doubles)
 cudaError_t launch_norm(const void* x, int io, long long n, double w, double* scratch,
                         double* norm_out, cudaStream_t st);
+// ar (may be null): the Gram partial sums and the residual partial sums are
+// summed over the ranks before they are reduced; *ar_failed = 1 (and an early
+// return) if the callback fails
 cudaError_t launch_ls(const void* R, const void* v, const void* f, int io_dtype, int K,
                       long long n, double w, double alpha, double rcond, void* rho_inout,
                       double* coef, double* coeff_out, double* s_rel_out, double* partial,
-                      double* scal, double* upd_partial, int* status, cudaStream_t st);
+                      double* scal, double* upd_partial, int* status, cudaStream_t st,
+                      const AllReduce* ar = nullptr, int* ar_failed = nullptr);
 
 // allocation-free least-squares step (k_ls.cu, static device scratch)
 int static_k_max();

@@ -179,10 +179,10 @@ lrdm_status kp_forward(lrdm_ctx* ctx, const void* v, int K, void* f_out, double*
   SysState& S = ctx->sys[0];
   const int fp64 = ctx->opt.prec == LRDM_FP64;
   const int io = ctx->opt.io_dtype;
-  LRDM_CU(launch_spin_sum(v, io, K, 1, S.Ng, S.fft_real, fp64, st));
+  LRDM_CU(launch_spin_sum(v, io, K, 1, S.Ng, S.fft_real, fp64, st, S.Ng));
   LRDM_CK(hartree(ctx, S, K, st));
   LRDM_CU(launch_dv_weights(v, io, S.fft_real, S.ch[0].fx, S.ch[0].fx, K, 1, S.Ng, S.Ng_pad, S.w, S.a,
-                            fp64, st));
+                            fp64, st, S.Ng));
   count(ctx, 3);
   LRDM_CK(kp_response(ctx, K, S.g, dmu_out, st));
   if (is_tc(ctx->opt.prec)) {
@@ -221,10 +221,10 @@ lrdm_status kp_backward(lrdm_ctx* ctx, const void* const* f_bar, void* const* v_
   } else {
     LRDM_CU(launch_kp_collect(nullptr, ctx->kp_drho, K, S.Ng, S.Ng_pad, S.a, fp64, st));
   }
-  LRDM_CU(launch_spin_sum_padded(S.a, K, 1, S.Ng, S.Ng_pad, S.fft_real, fp64, st));
+  LRDM_CU(launch_spin_sum_padded(S.a, K, 1, S.Ng, S.Ng_pad, S.fft_real, fp64, st, S.Ng));
   LRDM_CK(hartree(ctx, S, K, st));
   LRDM_CU(launch_adjoint_potential(S.a, S.fft_real, S.ch[0].fx, S.ch[0].fx, f_bar[0], io, K, 1, S.Ng,
-                                   S.Ng_pad, v_bar[0], fp64, st));
+                                   S.Ng_pad, v_bar[0], fp64, st, S.Ng));
   count(ctx, 5);
   return LRDM_OK;
 }
@@ -246,6 +246,7 @@ lrdm_status kp_setup(lrdm_ctx* ctx, const lrdm_kpoint_system& in, cudaStream_t s
     S.h[d] = in.h[d];
   }
   S.Ng = (long long)in.n[0] * in.n[1] * in.n[2];
+  S.Ngrid = S.Ng;
   S.Ng_pad = tc ? (S.Ng + TC_PAD_GRID - 1) / TC_PAD_GRID * TC_PAD_GRID : S.Ng;
   S.nspin = 1;
   S.kmax = in.k_max > 0 ? in.k_max : o.k_max;

@@ -172,6 +172,7 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
                             void* stream) {
   NvtxRange nvtx_("lrdm_lrdma_step");
   if (!a || !ctx || sys < 0 || sys >= ctx->nsys || !R) return LRDM_ERR_INVALID_ARG;
+  if (ctx->rows) return LRDM_ERR_UNSUPPORTED;
   lrdm_lrdma_params p;
   if (params) p = *params;
   else lrdm_lrdma_default_params(&p);

@@ -130,7 +130,8 @@ def test_no_cpu_fallback_without_a_gpu(lib):
         binding.load(os.path.join(ROOT, "no_such_dir", "liblrdm.so"))
 
 
-STRUCTS = ["lrdm_system", "lrdm_options", "lrdm_kpoint_system", "lrdm_lrdma_params", "lrdm_lrdma_report"]
+STRUCTS = ["lrdm_system", "lrdm_options", "lrdm_kpoint_system", "lrdm_lrdma_params", "lrdm_lrdma_report",
+           "lrdm_rows"]
 
 
 def test_binding_structs_match_the_header(tmp_path):
