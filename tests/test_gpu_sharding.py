@@ -1,8 +1,11 @@
 """Direction-sharded step (sharding.sharded_step) on the GPU with the real
 library context: with no process group and with a one-rank NCCL group (the
 all-gather runs on device tensors), it equals the unsharded forward and
-least-squares step bit for bit.  Several ranks are covered on the CPU
-(tests/test_sharding_gloo.py); each rank needs a GPU of its own."""
+least-squares step bit for bit; and a grid-row-sharded context whose
+exchanges go through torch_allreduce on a one-rank NCCL group.  Several
+ranks are covered on the CPU (tests/test_sharding_gloo.py,
+tests/test_rows_gloo.py) and as host threads on one GPU
+(tests/test_gpu_rows.py); NCCL ranks need a GPU each."""
 
 import socket
 
