@@ -259,11 +259,15 @@ typedef struct lrdm_rows {
  *     same coefficients and s_rel and updates its rows of rho;
  *   lrdm_backward -- the adjoint's projection (as X_k) and its spin-summed
  *     Poisson input (as the directions); eps_bar and occ_bar come out equal
- *     on every rank.
- * The grid reduction is not split into row ranges, use_graph is ignored,
- * and lrdm_krylov_step / lrdm_lrdma_step return LRDM_ERR_UNSUPPORTED on such
- * a context.  A failed allreduce returns LRDM_ERR_COLLECTIVE (the stream
- * holds the work enqueued before it). */
+ *     on every rank;
+ *   lrdm_krylov_step, lrdm_lrdma_step -- besides their forward and
+ *     least-squares calls, the per-block sums of every norm and Gram-Schmidt
+ *     inner product (FP64), so every rank takes the same decisions; their
+ *     directions and the LRDMA history hold this rank's rows (an lrdm_lrdma
+ *     created with n = nspin n_rows).
+ * The grid reduction is not split into row ranges and use_graph is ignored.
+ * A failed allreduce returns LRDM_ERR_COLLECTIVE (the stream holds the work
+ * enqueued before it). */
 lrdm_status lrdm_create_rows(lrdm_ctx** out, const lrdm_system* sys, const lrdm_rows* rows,
                              const lrdm_options* opt, void* stream);
 

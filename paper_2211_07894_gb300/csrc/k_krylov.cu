@@ -106,27 +106,41 @@ __global__ void k_norm_finish(const double* __restrict__ partial, int nblk, doub
 
 }  // namespace
 
+// Row-sharded systems: the per-block partial sums summed over the ranks
+// (block by block, so every rank reduces the same values in the same order).
+static bool sum_over_ranks(const AllReduce* ar, int* ar_failed, double* buf, long long count,
+                           cudaStream_t st) {
+  if (!ar || !ar->fn) return true;
+  if (ar->fn(ar->user, buf, count, LRDM_DTYPE_F64, st) == 0) return true;
+  if (ar_failed) *ar_failed = 1;
+  return false;
+}
+
 cudaError_t launch_norm(const void* x, int io, long long n, double w, double* scratch,
-                        double* norm_out, cudaStream_t st) {
+                        double* norm_out, cudaStream_t st, const AllReduce* ar, int* ar_failed) {
   k_dots<<<KR_BLOCKS, KR_THREADS, 0, st>>>(x, 1, x, io, n, scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (!sum_over_ranks(ar, ar_failed, scratch, KR_BLOCKS, st)) return cudaSuccess;
   k_norm_finish<<<1, KR_THREADS, 0, st>>>(scratch, KR_BLOCKS, w, norm_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_schmidt(const void* U, int K, const void* t, int io, long long n, double w,
-                                void* out, double* scratch, double* norm_out, cudaStream_t st) {
+                                void* out, double* scratch, double* norm_out, cudaStream_t st,
+                                const AllReduce* ar, int* ar_failed) {
   double* partial = scratch;                            // [KR_BLOCKS][K]
   double* npart = scratch + (size_t)KR_BLOCKS * KMAX_LIMIT;   // [KR_BLOCKS]
   if (K > 0) {
     k_dots<<<KR_BLOCKS, KR_THREADS, 0, st>>>(U, K, t, io, n, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (!sum_over_ranks(ar, ar_failed, partial, (long long)KR_BLOCKS * K, st)) return cudaSuccess;
   }
   k_gs_axpy<<<KR_BLOCKS, KR_THREADS, 0, st>>>(U, K, t, io, n, w, partial, KR_BLOCKS, out, npart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (!sum_over_ranks(ar, ar_failed, npart, KR_BLOCKS, st)) return cudaSuccess;
   k_normalize<<<KR_BLOCKS, KR_THREADS, 0, st>>>(out, io, n, w, npart, KR_BLOCKS, norm_out);
   return cudaGetLastError();
 }

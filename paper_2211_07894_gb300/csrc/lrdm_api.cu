@@ -940,15 +940,19 @@ lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol
                              double* s_rel_out, int* rank_out, double* r_norm_out, void* stream) {
   NvtxRange nvtx_("lrdm_krylov_step");
   if (!ctx || sys < 0 || sys >= ctx->nsys || !R || !U || !T) return LRDM_ERR_INVALID_ARG;
-  if (ctx->rows) return LRDM_ERR_UNSUPPORTED;
   if (r_max < 1 || r_max > KMAX_LIMIT || !(s_tol >= 0.0) || !isfinite(alpha)) return LRDM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SysState& S = ctx->sys[sys];
   const int io = ctx->opt.io_dtype;
   const long long n = (long long)S.nspin * S.Ng;
   const size_t vb = (size_t)n * io_size(io);
+  // row-sharded: every grid sum of the step is summed over the ranks
+  const AllReduce* ar = ctx->rows ? &ctx->ar : nullptr;
+  int ar_failed = 0;
   // u_1 = R / ||R||
-  LRDM_CU(launch_gram_schmidt(nullptr, 0, R, io, n, S.w, U, ctx->gs_scratch, ctx->gs_norm, st));
+  LRDM_CU(launch_gram_schmidt(nullptr, 0, R, io, n, S.w, U, ctx->gs_scratch, ctx->gs_norm, st, ar,
+                              &ar_failed));
+  if (ar_failed) return LRDM_ERR_COLLECTIVE;
   count(ctx, 2);
   double r_norm = 0.0;
   LRDM_CU(cudaMemcpyAsync(&r_norm, ctx->gs_norm, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -969,7 +973,8 @@ lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol
     // least squares on the first i + 1 directions (no update yet) -> s_rel
     LRDM_CU(launch_ls(R, U, T, io, rank, n, S.w, 0.0, ctx->opt.pinv_rcond, nullptr, ctx->ls_coef,
                       coeff_out, nullptr, ctx->ls_partial, ctx->ls_scal, ctx->upd_partial,
-                      ctx->d_status, st));
+                      ctx->d_status, st, ar, &ar_failed));
+    if (ar_failed) return LRDM_ERR_COLLECTIVE;
     count(ctx, 4);
     double s_rel = 0.0;
     LRDM_CU(cudaMemcpyAsync(&s_rel, ctx->ls_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -978,7 +983,9 @@ lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol
     if (s_rel < s_tol || rank == r_max) break;
     // u_{i+1} = t_i - sum_k <t_i, u_k> u_k, normalised
     LRDM_CU(launch_gram_schmidt(U, rank, static_cast<const char*>(T) + i * vb, io, n, S.w,
-                                static_cast<char*>(U) + rank * vb, ctx->gs_scratch, ctx->gs_norm, st));
+                                static_cast<char*>(U) + rank * vb, ctx->gs_scratch, ctx->gs_norm, st,
+                                ar, &ar_failed));
+    if (ar_failed) return LRDM_ERR_COLLECTIVE;
     count(ctx, 3);
   }
   if (rank_out) *rank_out = rank;
@@ -986,7 +993,8 @@ lrdm_status lrdm_krylov_step(lrdm_ctx* ctx, int sys, const void* R, double s_tol
     const double a = alpha < 0.0 ? (r_norm < 2.0 ? 0.5 : 0.1) : alpha;
     LRDM_CU(launch_ls(R, U, T, io, rank, n, S.w, a, ctx->opt.pinv_rcond, rho_inout, ctx->ls_coef,
                       coeff_out, nullptr, ctx->ls_partial, ctx->ls_scal, ctx->upd_partial,
-                      ctx->d_status, st));
+                      ctx->d_status, st, ar, &ar_failed));
+    if (ar_failed) return LRDM_ERR_COLLECTIVE;
     count(ctx, 4);
   }
   return LRDM_OK;

@@ -306,12 +306,15 @@ cudaError_t launch_gemm2_simt(int fp64, const void* psi, int ns, long long Ng, c
 // ---------------- least squares (k_ls.cu) ----------------
 // out = (t - sum_{k<K} <t, u_k> u_k) / ||.||_w (Krylov step, k_krylov.cu);
 // norm_out[0] = the norm before scaling.  scratch: gram_schmidt_scratch() doubles.
+// (ar, ar_failed as for launch_ls: the partial sums over the ranks of a row-sharded system)
 cudaError_t launch_gram_schmidt(const void* U, int K, const void* t, int io, long long n, double w,
-                                void* out, double* scratch, double* norm_out, cudaStream_t st);
+                                void* out, double* scratch, double* norm_out, cudaStream_t st,
+                                const AllReduce* ar = nullptr, int* ar_failed = nullptr);
 size_t gram_schmidt_scratch();
 // norm_out[0] = ||x||_w (scratch: gram_schmidt_scratch() doubles)
 cudaError_t launch_norm(const void* x, int io, long long n, double w, double* scratch,
-                        double* norm_out, cudaStream_t st);
+                        double* norm_out, cudaStream_t st, const AllReduce* ar = nullptr,
+                        int* ar_failed = nullptr);
 // ar (may be null): the Gram partial sums and the residual partial sums are
 // summed over the ranks before they are reduced; *ar_failed = 1 (and an early
 // return) if the callback fails

@@ -56,9 +56,12 @@ void lrdma_free(lrdm_lrdma* a) {
 // alpha != 0 also rho <- rho - alpha sum a_k v_k (v = U or, for the linear
 // prediction, T).  Host value of s_rel.
 lrdm_status lrdma_ls(lrdm_lrdma* a, const void* R, const void* v, int m, double alpha, void* rho,
-                     double rcond, double* s_rel, cudaStream_t st) {
+                     double rcond, double* s_rel, cudaStream_t st, const AllReduce* ar) {
+  int ar_failed = 0;
   LRDM_CU(launch_ls(R, v, a->T, a->io, m, a->n, a->w, alpha, rcond, rho, a->ls_coef, nullptr,
-                    nullptr, a->ls_partial, a->ls_scal, a->upd_partial, a->status, st));
+                    nullptr, a->ls_partial, a->ls_scal, a->upd_partial, a->status, st, ar,
+                    &ar_failed));
+  if (ar_failed) return LRDM_ERR_COLLECTIVE;
   LRDM_CU(cudaMemcpyAsync(s_rel, a->ls_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
   LRDM_CU(cudaStreamSynchronize(st));
   return LRDM_OK;
@@ -172,7 +175,6 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
                             void* stream) {
   NvtxRange nvtx_("lrdm_lrdma_step");
   if (!a || !ctx || sys < 0 || sys >= ctx->nsys || !R) return LRDM_ERR_INVALID_ARG;
-  if (ctx->rows) return LRDM_ERR_UNSUPPORTED;
   lrdm_lrdma_params p;
   if (params) p = *params;
   else lrdm_lrdma_default_params(&p);
@@ -188,9 +190,15 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
   const double rcond = ctx->opt.pinv_rcond;
   char* U = static_cast<char*>(a->U);
   char* T = static_cast<char*>(a->T);
+  // a row-sharded context: the history holds this rank's rows, and every grid
+  // sum of the step is summed over the ranks
+  const AllReduce* ar = ctx->rows ? &ctx->ar : nullptr;
+  int arf = 0;
   // ||R|| and, with a history, ||R_lin||
-  LRDM_CU(launch_norm(R, a->io, a->n, a->w, a->gs, a->norm, st));
-  if (a->m > 0 && a->have_lin) LRDM_CU(launch_norm(a->R_lin, a->io, a->n, a->w, a->gs, a->norm + 1, st));
+  LRDM_CU(launch_norm(R, a->io, a->n, a->w, a->gs, a->norm, st, ar, &arf));
+  if (a->m > 0 && a->have_lin)
+    LRDM_CU(launch_norm(a->R_lin, a->io, a->n, a->w, a->gs, a->norm + 1, st, ar, &arf));
+  if (arf) return LRDM_ERR_COLLECTIVE;
   double nrm[2] = {0.0, 0.0};
   LRDM_CU(cudaMemcpyAsync(nrm, a->norm, sizeof(nrm), cudaMemcpyDeviceToHost, st));
   LRDM_CU(cudaStreamSynchronize(st));
@@ -207,7 +215,7 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
       event = LRDMA_CLEAR_LINEARITY;
     } else {
       double s_hist = 0.0;
-      LRDM_CK(lrdma_ls(a, R, U, a->m, 0.0, nullptr, rcond, &s_hist, st));
+      LRDM_CK(lrdma_ls(a, R, U, a->m, 0.0, nullptr, rcond, &s_hist, st, ar));
       if (s_hist < p.s_tol) event = LRDMA_REUSE;
       else if (r_norm > p.r_norm_clear) event = LRDMA_CLEAR_RESIDUAL;
       else event = LRDMA_ACCUMULATE;
@@ -228,7 +236,9 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
       limit = p.r_max;
     }
     // first new direction: R normalised, or its complement to the history
-    LRDM_CU(launch_gram_schmidt(U, a->m, R, a->io, a->n, a->w, U + a->m * vb, a->gs, a->norm, st));
+    LRDM_CU(launch_gram_schmidt(U, a->m, R, a->io, a->n, a->w, U + a->m * vb, a->gs, a->norm, st, ar,
+                                &arf));
+    if (arf) return LRDM_ERR_COLLECTIVE;
     std::vector<const void*> v(ctx->nsys, nullptr);
     std::vector<void*> f(ctx->nsys, nullptr);
     std::vector<int> K(ctx->nsys, 0);
@@ -239,19 +249,20 @@ lrdm_status lrdm_lrdma_step(lrdm_lrdma* a, lrdm_ctx* ctx, int sys, const void* R
       LRDM_CK(forward_one(ctx, sys, v.data(), K.data(), f.data(), st));
       ++a->m;
       ++n_new;
-      LRDM_CK(lrdma_ls(a, R, U, a->m, 0.0, nullptr, rcond, &s_rel, st));
+      LRDM_CK(lrdma_ls(a, R, U, a->m, 0.0, nullptr, rcond, &s_rel, st, ar));
       if (s_rel < p.s_tol || n_new == limit) break;
       LRDM_CU(launch_gram_schmidt(U, a->m, T + (a->m - 1) * vb, a->io, a->n, a->w, U + a->m * vb,
-                                  a->gs, a->norm, st));
+                                  a->gs, a->norm, st, ar, &arf));
+      if (arf) return LRDM_ERR_COLLECTIVE;
     }
     if (!fresh && s_rel >= p.s_tol) a->clear_next = true;
   }
   const double alpha = p.alpha < 0.0 ? (r_norm < 2.0 ? 0.5 : 0.1) : p.alpha;
   // linear prediction of the next residual: R_lin = R - alpha sum a_k t_k
   LRDM_CU(cudaMemcpyAsync(a->R_lin, R, vb, cudaMemcpyDeviceToDevice, st));
-  LRDM_CK(lrdma_ls(a, R, T, a->m, alpha, a->R_lin, rcond, &s_rel, st));
+  LRDM_CK(lrdma_ls(a, R, T, a->m, alpha, a->R_lin, rcond, &s_rel, st, ar));
   a->have_lin = true;
-  if (rho_inout) LRDM_CK(lrdma_ls(a, R, U, a->m, alpha, rho_inout, rcond, &s_rel, st));
+  if (rho_inout) LRDM_CK(lrdma_ls(a, R, U, a->m, alpha, rho_inout, rcond, &s_rel, st, ar));
   if (report) {
     report->event = event;
     report->rank = a->m;

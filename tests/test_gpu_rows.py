@@ -8,8 +8,9 @@ Checked against one unsharded context on the same system, and against the
 FP64 oracle: the forward (Eq. densityResponse per row, with X_k the sum of
 the slabs' projections), the least-squares step (Eqs. plowrank,
 relativeError: the same coefficients and s_rel on every rank) and the
-adjoint; a failing collective returns LRDM_ERR_COLLECTIVE; the drivers
-refuse such a context.
+adjoint, and the drivers (the adaptive-rank LRDM step and LRDMA) whose
+norms, Gram-Schmidt inner products and least-squares sums run over the
+ranks; a failing collective returns LRDM_ERR_COLLECTIVE.
 """
 
 import threading
@@ -191,10 +192,6 @@ def test_row_sharded_failures(lib):
     (F2,), _ = plain.gateaux([V])
     torch.cuda.synchronize()
     assert per_direction_rel_err(F1.cpu().numpy(), F2.cpu().numpy()) < 1e-13
-    R = torch.as_tensor(cfg["R"], dtype=torch.float64, device="cuda")
-    with pytest.raises(LrdmError) as e:
-        solo.krylov_step(R, s_tol=0.3)
-    assert e.value.code == 9                  # LRDM_ERR_UNSUPPORTED
     # rows outside the grid are refused before anything is allocated
     with pytest.raises(LrdmError) as e:
         Context([_system(cfg, torch.float64, (0, 10))], prec="fp64", io_dtype=torch.float64,
@@ -202,3 +199,68 @@ def test_row_sharded_failures(lib):
     assert e.value.code == 2                  # LRDM_ERR_SHAPE
     for c in (ctx, solo, plain):
         c.close()
+
+
+def test_row_sharded_drivers_match_unsharded(lib):
+    """lrdm_krylov_step and lrdm_lrdma_step on two row slabs (FP64): rank,
+    s_rel, coefficients, directions and the density update against one
+    unsharded context."""
+    from paper_2211_07894_gb300 import Context, Lrdma
+    io = torch.float64
+    cfg = workloads.random_system(73, (20, 18, 22), 200, 150, 0.01, 1)
+    ng = int(np.prod(cfg["n"]))
+    w = float(np.prod(cfg["h"]))
+    cut = 3001
+    bounds = [(0, cut), (cut, ng)]
+    R = torch.as_tensor(cfg["R"], dtype=io, device="cuda")
+    rho0 = torch.full_like(R, 0.01)
+    full = Context([_system(cfg, io)], prec="fp64", io_dtype=io, k_max=8)
+    rho_k = rho0.clone()
+    ref = full.krylov_step(R, s_tol=0.05, r_max=6, alpha=0.5, rho=rho_k)
+    la = Lrdma(n=ng, io_dtype=io, w=w, capacity=8)
+    rho_l = rho0.clone()
+    rep = la.step(full, R, rho_l, s_tol=0.05, r_max=6)
+    torch.cuda.synchronize()
+    ts = ThreadSum(2)
+
+    def rank(r):
+        r0, r1 = bounds[r]
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            ctx = Context([_system(cfg, io, (r0, r1))], prec="fp64", io_dtype=io, k_max=8,
+                          rows=dict(row_begin=r0, n_rows=r1 - r0, allreduce=ts.member(r)))
+            Rs = R[:, r0:r1].clone()
+            rk = rho0[:, r0:r1].clone()
+            step = ctx.krylov_step(Rs, s_tol=0.05, r_max=6, alpha=0.5, rho=rk)
+            lr = Lrdma(n=r1 - r0, io_dtype=io, w=w, capacity=8)
+            rl = rho0[:, r0:r1].clone()
+            rp = lr.step(ctx, Rs, rl, s_tol=0.05, r_max=6)
+            st.synchronize()
+            code = ctx.status()
+            ctx.close()
+        return dict(rank=step["rank"], a=step["a"].cpu().numpy(), U=step["U"].cpu().numpy(),
+                    s_rel=np.asarray(step["s_rel"]), rho_k=rk.cpu().numpy(), rep=rep_dict(rp),
+                    rho_l=rl.cpu().numpy(), code=code)
+
+    def rep_dict(x):
+        return {k: x[k] for k in ("event", "rank", "s_rel")} if isinstance(x, dict) else x
+
+    out = _run_ranks([lambda: rank(0), lambda: rank(1)])
+    assert [o["code"] for o in out] == [0, 0]
+    for o in out:
+        assert o["rank"] == ref["rank"]
+        assert np.allclose(o["a"], ref["a"].cpu().numpy(), rtol=1e-9, atol=1e-12)
+        assert np.allclose(o["s_rel"], np.asarray(ref["s_rel"]), rtol=1e-9, atol=1e-12)
+    assert np.array_equal(out[0]["a"], out[1]["a"])
+    U = np.concatenate([o["U"] for o in out], axis=-1)
+    assert np.allclose(U, ref["U"].cpu().numpy(), rtol=1e-9, atol=1e-10)
+    rho = np.concatenate([o["rho_k"] for o in out], axis=-1)
+    assert np.allclose(rho, rho_k.cpu().numpy(), rtol=1e-10, atol=1e-14)
+    # LRDMA's first step (a fresh build) and its density update
+    assert out[0]["rep"] == out[1]["rep"]
+    ref_rep = rep_dict(rep)
+    assert out[0]["rep"]["event"] == ref_rep["event"] and out[0]["rep"]["rank"] == ref_rep["rank"]
+    assert abs(out[0]["rep"]["s_rel"] - ref_rep["s_rel"]) < 1e-10
+    rho = np.concatenate([o["rho_l"] for o in out], axis=-1)
+    assert np.allclose(rho, rho_l.cpu().numpy(), rtol=1e-10, atol=1e-14)
+    full.close()
