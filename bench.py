@@ -88,10 +88,12 @@ def parse():
                         "oracle timed on the host cores in full and the error of every precision")
     p.add_argument("--prec-list", default="",
                    help="with --config: comma-separated precisions instead of the config's own")
-    p.add_argument("--shard", default="replicas", choices=["replicas", "directions"],
-                   help="N > 1: an independent system per rank (weak scaling), or one system whose "
+    p.add_argument("--shard", default="replicas", choices=["replicas", "directions", "rows"],
+                   help="N > 1: an independent system per rank (weak scaling); one system whose "
                         "K directions are split over the ranks, f all-gathered before the "
-                        "least-squares step on every rank (strong scaling)")
+                        "least-squares step on every rank; or one system whose grid rows are "
+                        "split over the ranks (lrdm_create_rows: the Poisson input, X_k and the "
+                        "least-squares sums summed by NCCL) (both strong scaling)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip timing the uneven batch (64 derivatives per call) after the main step")
     p.add_argument("--compare-fp64", action="store_true",
@@ -662,7 +664,7 @@ def config_leg(args, torch):
         append_jsonl(args.jsonl, line)
     return 0
 
-def build_problem(torch, rank, prec, edge, ns, autotune=True):
+def build_problem(torch, rank, prec, edge, ns, autotune=True, rows=None):
     import numpy as np
     import workloads
     from paper_2211_07894_gb300 import Context
@@ -688,8 +690,15 @@ def build_problem(torch, rank, prec, edge, ns, autotune=True):
     if io == torch.float64:
         system["psi"] = [psi.double()]
         V, R = V.double(), R.double()
+    kw = {}
+    if rows is not None:
+        # grid rows [r0, r1) of the one shared system on this rank
+        r0, r1, fn = rows
+        system["psi"] = [system["psi"][0][r0:r1].contiguous()]
+        V, R = V[:, :, r0:r1].contiguous(), R[:, r0:r1].contiguous()
+        kw["rows"] = dict(row_begin=r0, n_rows=r1 - r0, allreduce=fn)
     ctx = Context([system], prec=prec, io_dtype=io, k_max=KDIR, use_graph=True,
-                  autotune=autotune and prec in ("bf16x3", "tf32"))
+                  autotune=autotune and prec in ("bf16x3", "tf32"), **kw)
     del psi, system
     torch.cuda.empty_cache()
     return ctx, V, R, ng
@@ -905,9 +914,18 @@ def main():
     _build.build()
 
     directions = args.shard == "directions"
-    seed_rank = 0 if directions else rank          # one shared system when the directions are split
+    rows_mode = args.shard == "rows"
+    shared = directions or rows_mode
+    seed_rank = 0 if shared else rank              # one shared system when it is split
+    rows = None
+    if rows_mode:
+        from paper_2211_07894_gb300 import torch_allreduce
+        from paper_2211_07894_gb300.sharding import shard_bounds
+        r0, r1 = shard_bounds(args.grid ** 3, world, rank)
+        rows = (r0, r1, torch_allreduce() if dist else (lambda t, st: None))
     ctx, V, R, ng = build_problem(torch, seed_rank, args.prec, args.grid, args.ns,
-                                  autotune=not args.no_autotune)
+                                  autotune=not args.no_autotune, rows=rows)
+    ng_local = rows[1] - rows[0] if rows else ng
     ns = args.ns
     tuning = ctx.tuning() if args.prec in ("bf16x3", "tf32") else None
     F = torch.empty_like(V)
@@ -968,13 +986,13 @@ def main():
         ms = float(t.item())
     steps = max(args.steps, 1)
     ms_step = ms / steps
-    total_gd = KDIR * steps * (1 if directions else world)
+    total_gd = KDIR * steps * (1 if shared else world)
     value = total_gd / (ms / 1e3)
     if ctx.status() != 0:
         raise RuntimeError("device status not ok after the timed region")
     forward_only = forward_k1 = None
     apply_ms = None
-    if not directions:
+    if not shared:
         forward_only, forward_k1 = time_forward_calls(torch, ctx, V, F, dmu, prof, args, world)
         # the least-squares step alone (Gram, K x K solve, update) on the step's own derivatives
         a0 = torch.cuda.Event(enable_timing=True)
@@ -1006,7 +1024,7 @@ def main():
     kshape = ((f"g1_nb={tuning['g1_nb']},g1_dpt={tuning['g1_dpt']}" if kname == g1_kernel
                else f"g2_bn={tuning['g2_bn']},g2_kgroup={tuning['g2_kgroup']}") if tuning else None)
     avg_s = tms / max(nl, 1) / 1e3
-    alg_flops = (k_hi - k_lo) * ng * ns * ns   # one launch: this rank's directions, symmetric half
+    alg_flops = (k_hi - k_lo) * ng_local * ns * ns   # one launch: this rank's directions and rows, symmetric half
     peak, bound, issue, note = dtype_peak(args.prec, peaks)
     issued = issue * alg_flops
     achieved = issued / avg_s / 1e12 if avg_s > 0 else None
@@ -1041,7 +1059,7 @@ def main():
     # the uneven batch with its spin pair: 64 derivatives per call (one
     # grouped launch per contraction, graph replay), same precision
     batched = None
-    if not args.no_batched and not directions and args.prec in ("bf16x3", "tf32", "fp32"):
+    if not args.no_batched and not shared and args.prec in ("bf16x3", "tf32", "fp32"):
         ctx.close()
         F = fbar = bwd_out = None
         torch.cuda.empty_cache()
@@ -1055,7 +1073,7 @@ def main():
         del cfgs3
 
     kpoint = None
-    if not args.no_kpoint and not directions:
+    if not args.no_kpoint and not shared:
         ctx.close()
         F = fbar = bwd_out = None
         torch.cuda.empty_cache()
@@ -1064,7 +1082,7 @@ def main():
             kpoint["cpu_baseline"] = time_kpoint_oracle()
 
     fp64_plain = None
-    if not args.no_fp64_plain and not directions:
+    if not args.no_fp64_plain and not shared:
         ctx.close()
         F = fbar = bwd_out = None
         torch.cuda.empty_cache()
@@ -1084,14 +1102,14 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GD/s", "n_gpus": world,
                 "steps": steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "strong" if directions else "weak",
+                "higher_is_better": True, "scaling": "strong" if shared else "weak",
                 "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                 "config": {"workload": f"{args.grid}^3 grid, N_s={ns}, K={KDIR}, FP32 Psi, "
                                        f"{args.prec} contractions",
                            "grid": [args.grid] * 3, "n_s": ns, "K": KDIR,
                            "precision": args.prec,
                            "l2": "inputs larger than L2 (Psi operand copies > 14 GB)",
-                           "parallelism": f"{'directions' if directions else 'replicas'} x{world}"},
+                           "parallelism": f"{args.shard} x{world}"},
                 "roofline": roofline, "tensor_pipe": tensor_pipe, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks,
                 "gpu_launches": prof["kernel_launches"],
