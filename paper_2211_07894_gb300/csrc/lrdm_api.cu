@@ -513,6 +513,7 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
   const std::string key = tune_key(ctx);
   if (cache && *cache && tune_cache_read(cache, key, ctx->tune)) return LRDM_OK;
   std::vector<TcEntry> g1, g2;
+  std::vector<int> g1_sys;                             // system of each projection entry (-1: k-point)
   for (size_t q = 0; q < ctx->kp_ch.size(); ++q) {     // k-point context: the stacked problems
     SysState& S = ctx->sys[0];
     TcEntry x;
@@ -522,6 +523,7 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
     x.K = S.kmax;
     x.X = ctx->kp_ch[q].Xpart;
     g1.push_back(x);
+    g1_sys.push_back(-1);
     x.X = nullptr;
     x.factor = 1.0;
     x.out = ctx->kp_out[q];
@@ -534,6 +536,7 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
       TcEntry x = tc_entry(ctx, s, c, S.kmax);
       x.X = S.ch[c].Xpart;
       g1.push_back(x);
+      g1_sys.push_back(s);
       TcEntry y = tc_entry(ctx, s, c, S.kmax);
       y.factor = 1.0;
       y.out = static_cast<float*>(S.a) + (size_t)c * S.Ng_pad;
@@ -545,10 +548,18 @@ lrdm_status autotune(lrdm_ctx* ctx, cudaStream_t st) {
   TcTune best = ctx->tune;
   float tbest = 1e30f;
   const int g1_cand[4][2] = {{G1_PAIR, 1}, {256, 1}, {128, 1}, {128, 2}};   // (MMA width, directions per tile)
+  const TcTune start = ctx->tune;
   for (const auto& c : g1_cand) {
-    TcTune t = ctx->tune;
+    TcTune t = start;
     t.g1_nb = c[0];
     t.g1_dpt = c[1];
+    // each candidate runs with the row-range split a call of k_max directions
+    // would take in that shape (the split fills the last wave differently
+    // for each tile shape)
+    ctx->tune = t;
+    for (size_t e = 0; e < g1.size(); ++e)
+      if (g1_sys[e] >= 0) g1[e].split = choose_split(ctx, g1_sys[e], g1[e].K);
+    ctx->tune = start;
     const float ms = time_launch([&] { return launch_gemm1_tc_group(ctx->opt.prec, g1.data(), (int)g1.size(),
                                                                     ctx->d_status, st, t, G1_NCH_CAP, 0,
                                                                     ctx->d_round); },
