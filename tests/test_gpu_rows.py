@@ -264,3 +264,54 @@ def test_row_sharded_drivers_match_unsharded(lib):
     rho = np.concatenate([o["rho_l"] for o in out], axis=-1)
     assert np.allclose(rho, rho_l.cpu().numpy(), rtol=1e-10, atol=1e-14)
     full.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_row_sharded_spin_pair(lib, prec):
+    """A collinear spin pair (two channels sharing mu and the Hartree term)
+    on two row slabs: f, mu' and the least-squares step against one
+    unsharded context and the oracle."""
+    from paper_2211_07894_gb300 import Context
+    io = IO[prec]
+    cfg = workloads.spin_pair_system(74, (16, 14, 18), 120, 100, 90, 0.01, 3)
+    ng = int(np.prod(cfg["n"]))
+    bounds = [(0, 1501), (1501, ng)]
+    V = torch.as_tensor(cfg["V"], dtype=io, device="cuda")
+    R = torch.as_tensor(cfg["R"], dtype=io, device="cuda")
+    full = Context([_system(cfg, io)], prec=prec, io_dtype=io, k_max=3)
+    (F,), dmu = full.gateaux([V])
+    torch.cuda.synchronize()
+    ts = ThreadSum(2)
+
+    def rank(r):
+        r0, r1 = bounds[r]
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            ctx = Context([_system(cfg, io, (r0, r1))], prec=prec, io_dtype=io, k_max=3,
+                          rows=dict(row_begin=r0, n_rows=r1 - r0, allreduce=ts.member(r)))
+            Vs = V[:, :, r0:r1].contiguous()
+            (Fs,), dmus = ctx.gateaux([Vs])
+            c_s, s_s = ctx.apply(0, R[:, r0:r1].contiguous(), Vs, Fs, 0.0)
+            st.synchronize()
+            code = ctx.status()
+            ctx.close()
+        return dict(F=Fs.double().cpu().numpy(), dmu=dmus.cpu().numpy(), coef=c_s.cpu().numpy(),
+                    srel=float(s_s.item()), code=code)
+
+    out = _run_ranks([lambda: rank(0), lambda: rank(1)])
+    assert [o["code"] for o in out] == [0, 0]
+    assert np.array_equal(out[0]["coef"], out[1]["coef"]) and out[0]["srel"] == out[1]["srel"]
+    Fs = np.concatenate([o["F"] for o in out], axis=-1)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    err = per_direction_rel_err(Fs, F.double().cpu().numpy())
+    print(f"rows spin {prec}: f vs unsharded {err:.2e}")
+    assert err < tol
+    dmu_ref = dmu.cpu().numpy()
+    assert np.allclose(out[0]["dmu"], dmu_ref, rtol=tol * 10, atol=tol * 10 * np.abs(dmu_ref).max())
+    coef, srel = full.apply(0, R, V, torch.as_tensor(Fs, dtype=io, device="cuda"), 0.0)
+    torch.cuda.synchronize()
+    assert np.allclose(out[0]["coef"], coef.cpu().numpy(), rtol=1e-9, atol=1e-12)
+    assert abs(out[0]["srel"] - srel.item()) < 1e-10
+    ref = oracle.gateaux(oracle_system(cfg), cfg["V"])
+    assert per_direction_rel_err(Fs, ref["F"]) < TOL[prec]
+    full.close()
